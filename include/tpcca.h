@@ -1,0 +1,208 @@
+/*
+ * tpcca.h -- C ABI of the B300 sector tracker (libtpcca.so).
+ *
+ * Per-sector TPC track finding as described in Sec. 2 of "Tracking
+ * performance in high multiplicities environment at ALICE" (arXiv
+ * 1709.00618): the TPC is split into 36 sectors tracked independently; a
+ * cellular automaton links adjacent hits close to a straight line (Fig. 1a)
+ * and concatenates the links into short candidates (Fig. 1b); track following
+ * fits each candidate and extends it row by row with a simplified Kalman
+ * filter (Fig. 1c); a final selection gives each cluster to at most one track.
+ * The field model is uniform Bz (Sec. 2: Bx and By are not used online).
+ * Several independent requests (events or timeframes) can be processed in one
+ * batch, as Sec. 2 does to fill a GPU.
+ *
+ * Conventions for every function:
+ *  - Return value: TPC_OK (0) or one of the TPC_E* codes; tpc_last_error()
+ *    gives a one-line description of the last failure on that context.
+ *  - Host pointers are owned by the caller and only read/written during the
+ *    call (tpc_load_* copies its input before returning when on_device == 0;
+ *    with on_device != 0 the device buffer must stay valid until the copy on
+ *    the context's stream has run, i.e. until the next tpc_sync/tpc_get_*).
+ *  - Device memory used by the pipeline belongs to the context (its arena).
+ *  - All work is enqueued on the context's CUDA stream in call order;
+ *    tpc_find_tracks / tpc_fit_tracks return without waiting.  Errors raised
+ *    on the device (bad input, capacity overflow, a bounded wait that ran
+ *    out) are reported by the next tpc_sync or tpc_get_* call.
+ *  - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef TPCCA_H
+#define TPCCA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+enum {
+  TPC_OK = 0,
+  TPC_EINVAL = 1,    /* bad argument or bad cluster (row >= 159, sector >= 36, non-finite y/z) */
+  TPC_ENOMEM = 2,    /* the request does not fit the context's HBM budget / arena */
+  TPC_ECUDA = 3,     /* a CUDA runtime call failed */
+  TPC_ETIMEOUT = 4,  /* a bounded device-side wait ran out (no GPU hang; the context stays usable) */
+  TPC_EOVERFLOW = 5, /* an output or internal capacity was too small; nothing was truncated silently,
+                        the call can be retried with a larger capacity (see tpc_reserve) */
+  TPC_EBUSY = 6      /* the serving queue is full */
+};
+
+/* ----------------------------------------------------------------- records */
+/* One cluster, 16 bytes.  (row, sector) address the pad row (0..158, radii
+ * linearly spaced 85.2..245.8 cm) and the sector (0..35; 0..17 z >= 0 side,
+ * 18..35 z < 0 side, centre angle (s mod 18)*20+10 degrees).  y and z are the
+ * local sector coordinates in cm (z may be a drift-time coordinate for
+ * continuous read-out, Sec. 5).  id is opaque and ignored. */
+typedef struct {
+  float y, z;
+  uint16_t row, sector;
+  uint32_t id;
+} tpc_cluster;
+
+/* One fitted sector track, 128 bytes.  par = (y, z, sin phi, dz/ds_T, q/pT)
+ * at local x (the radius of first_row); cov = packed lower triangle of the
+ * symmetric 5x5 covariance in row-major order ((0,0),(1,0),(1,1),(2,0),...).
+ * cluster_offset indexes the optional track_clusters output of
+ * tpc_get_tracks.  flags: TPC_TF_* bits. */
+typedef struct {
+  float x;
+  float par[5];
+  float cov[15];
+  int32_t reserved;
+  double chi2;
+  int32_t ndf, n_clusters, sector, request, first_row, last_row, cluster_offset, flags;
+} tpc_track;
+
+enum {
+  TPC_TF_TAINT_TIE = 1,   /* a pick had a second candidate within the divergence margin */
+  TPC_TF_TAINT_GATE = 2,  /* a candidate lay within the margin of the chi2 gate */
+  TPC_TF_TAINT_EDGE = 4,  /* a sector-edge stop test was within the margin */
+  TPC_TF_TAINT_SLIM = 8,  /* a |sin phi| limit test was within the margin */
+  TPC_TF_SEED_FAIL = 16,
+  TPC_TF_BACK_FAIL = 32,
+  TPC_TF_REFIT_FAIL = 64
+};
+
+/* Algorithm constants.  The paper prints none of them; the defaults are the
+ * documented reading (tpc_default_config). */
+typedef struct {
+  double bz_kg;        /* uniform field (kG); default 5 */
+  double sigma;        /* cluster resolution in y and z (cm); default 0.1 */
+  float d_max;         /* accepted squared straight-line deviation of a link (cm^2); 1.0 */
+  int32_t min_chain;   /* clusters of the shortest tracklet; 3 */
+  int32_t max_miss;    /* consecutive empty rows that end an extension; 5 */
+  int32_t n_min_track; /* clusters a selected track must own; 10 */
+  double gate;         /* chi2 gate of the pick-up; 16 */
+  double c0[5];        /* seed covariance diagonal; 100, 100, 1, 1, 100 */
+  double s_max;        /* |sin phi| limit of the propagation; 0.95 */
+  double edge;         /* cm beyond the sector edge that end an extension; 2 */
+  double taint_rel;    /* divergence margin for the taint flags; 2e-3 */
+  int32_t fp64_updates;/* Kalman updates after each seed done in FP64; 10 */
+  int32_t reserved;
+} tpc_config;
+
+/* Fills cfg with the defaults above. */
+int tpc_default_config(tpc_config *cfg);
+
+/* --------------------------------------------------------------- contexts */
+typedef struct tpc_ctx tpc_ctx;
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to
+ * enqueue on (NULL: the context creates its own non-blocking stream).
+ * hbm_budget: bytes the context may allocate for its arena (0: no limit
+ * beyond free memory).  cfg NULL: defaults. */
+int tpc_create(tpc_ctx **out, const tpc_config *cfg, int device, void *cuda_stream, size_t hbm_budget);
+
+/* Same, but the arena is caller-provided device memory (e.g. a PyTorch
+ * tensor) of `bytes` bytes, aligned to 256 bytes, that must outlive the
+ * context.  The context never allocates device memory beyond it. */
+int tpc_create_with_arena(tpc_ctx **out, const tpc_config *cfg, int device, void *cuda_stream, void *arena,
+                          size_t bytes);
+
+void tpc_destroy(tpc_ctx *ctx);
+const char *tpc_last_error(tpc_ctx *ctx);
+
+/* Arena bytes needed for batches of up to n_clusters clusters in up to
+ * n_requests requests (0 = library defaults for the internal capacities). */
+size_t tpc_arena_bytes(int64_t n_clusters, int32_t n_requests);
+
+/* Size the context for at least n_clusters / n_requests (and, when nonzero,
+ * the given grid-bin and tracklet capacities).  Called implicitly by the
+ * load functions; call it explicitly to retry after TPC_EOVERFLOW. */
+int tpc_reserve(tpc_ctx *ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets);
+
+/* ------------------------------------------------------------ the hot path */
+/* a1: copy n clusters (host or device pointer) into the context as one
+ * request.  Validation of each cluster happens on the device; a bad cluster
+ * makes the next tpc_sync / tpc_get_* return TPC_EINVAL. */
+int tpc_load_clusters(tpc_ctx *ctx, const tpc_cluster *clusters, int64_t n, int on_device);
+
+/* Same for a batch of n_req independent requests: request q is clusters
+ * [req_offsets[q], req_offsets[q+1]) (host array of n_req+1 entries,
+ * req_offsets[0] = 0, non-decreasing).  Requests never share tracks. */
+int tpc_load_batch(tpc_ctx *ctx, const tpc_cluster *clusters, const int64_t *req_offsets, int32_t n_req,
+                   int on_device);
+
+/* a2-a7: grid, CA neighbours, link cleaning, tracklets, Kalman following,
+ * selection and cluster assignment (Sec. 2 phase 1).  Asynchronous. */
+int tpc_find_tracks(tpc_ctx *ctx);
+
+/* a8: Kalman refit of every selected track on the clusters it owns (the
+ * final fit on the GPU of Sec. 2).  Asynchronous. */
+int tpc_fit_tracks(tpc_ctx *ctx);
+
+/* Both of the above as one CUDA-graph launch (captured on first use for the
+ * context's current capacity, then replayed).  Equivalent results. */
+int tpc_run_graph(tpc_ctx *ctx);
+
+/* a9: wait for the stream and copy the results out.  out: room for cap
+ * tracks; *n_out receives the number of tracks (also when cap is too small,
+ * in which case nothing is copied and TPC_EOVERFLOW is returned).
+ * cluster_track (optional, n entries): track index of every loaded cluster
+ * in load order, -1 when unassigned.  track_clusters (optional, sum of
+ * n_clusters entries): the load-order indices of each track's clusters at
+ * tracks[i].cluster_offset, innermost row first. */
+int tpc_get_tracks(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, int32_t *cluster_track,
+                   int32_t *track_clusters);
+
+/* Wait for the context's stream and report device-side errors. */
+int tpc_sync(tpc_ctx *ctx);
+
+/* Counters of the last run: [0] clusters, [1] requests, [2] row-sectors,
+ * [3] grid bins, [4] tracklets, [5] tracks, [6] device status word. */
+int tpc_get_counts(tpc_ctx *ctx, int64_t counts[8]);
+
+/* Intermediate results of the last run, for stage-by-stage parity checks:
+ * copies item `item` (TPC_ITEM_*) to host_out if cap_bytes suffices and
+ * stores its size in *n_bytes.  Waits for the stream. */
+enum {
+  TPC_ITEM_PERM = 1,       /* int32[n]   sorted position -> load index */
+  TPC_ITEM_RS_OF = 2,      /* int32[n]   sorted position -> row-sector (request*36+sector)*159+row */
+  TPC_ITEM_ROW_START = 3,  /* int32[nrs+1] */
+  TPC_ITEM_RS_PARAMS = 4,  /* nrs x {float z_lo, z_hi, inv_y, inv_z; int32 n_y, n_z, bin_base, count} */
+  TPC_ITEM_BIN_START = 5,  /* int32[n_bins+1] */
+  TPC_ITEM_UP = 6, TPC_ITEM_DN = 7, TPC_ITEM_TIE = 8, /* int32[n], int32[n], uint8[n] (sorted indexing) */
+  TPC_ITEM_UP_M = 9, TPC_ITEM_DN_M = 10,
+  TPC_ITEM_TL_START = 11, TPC_ITEM_TL_LEN = 12,       /* int32[n_tracklets] */
+  TPC_ITEM_F_N = 13, TPC_ITEM_F_NF = 14, TPC_ITEM_F_NB = 15, TPC_ITEM_F_FLAGS = 16, TPC_ITEM_F_ROW = 17,
+  TPC_ITEM_F_HITS = 18,    /* int32[n_tracklets*159] */
+  TPC_ITEM_F_PAR = 19,     /* float[n_tracklets*5], z absolute */
+  TPC_ITEM_F_COV = 20,     /* float[n_tracklets*15] */
+  TPC_ITEM_F_CHI2 = 21,    /* double[n_tracklets] */
+  TPC_ITEM_OWNER = 22,     /* uint64[n] */
+  TPC_ITEM_TL_TRACK = 23,  /* int32[n_tracklets] */
+  TPC_ITEM_SY = 24, TPC_ITEM_SZ = 25 /* float[n] sorted positions */
+};
+int tpc_get_stage(tpc_ctx *ctx, int item, void *host_out, int64_t cap_bytes, int64_t *n_bytes);
+
+/* ------------------------------------------------------ tuning (autotuner) */
+/* Threads per block of the cluster-, row-sector- and tracklet-parallel
+ * kernels and CTAs per SM of the persistent follow/refit launches.  0 keeps
+ * the current value.  Invalidates a captured graph. */
+int tpc_set_tuning(tpc_ctx *ctx, int block_clusters, int block_follow, int ctas_per_sm_follow, int reserved);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPCCA_H */

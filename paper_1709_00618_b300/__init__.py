@@ -1,0 +1,263 @@
+"""B300-native per-sector TPC track finding (arXiv 1709.00618, Sec. 2).
+
+Thin ctypes binding of libtpcca.so (declared in include/tpcca.h).  Every step
+of the path runs in the library's CUDA kernels; this module only marshals
+arguments.  PyTorch, when used, only provides device memory (the arena) and
+the CUDA stream.  There is no CPU fallback: without the compiled library and
+a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB_PATH, build  # noqa: F401
+
+__all__ = ["Tracker", "TpcError", "TRACK_DTYPE", "CLUSTER_DTYPE", "build", "load_library", "default_config",
+           "ITEMS"]
+
+CLUSTER_DTYPE = np.dtype([("y", "<f4"), ("z", "<f4"), ("row", "<u2"), ("sector", "<u2"), ("id", "<u4")])
+TRACK_DTYPE = np.dtype([("x", "<f4"), ("par", "<f4", (5,)), ("cov", "<f4", (15,)), ("reserved", "<i4"),
+                        ("chi2", "<f8"), ("ndf", "<i4"), ("n_clusters", "<i4"), ("sector", "<i4"),
+                        ("request", "<i4"), ("first_row", "<i4"), ("last_row", "<i4"),
+                        ("cluster_offset", "<i4"), ("flags", "<i4")])
+assert CLUSTER_DTYPE.itemsize == 16 and TRACK_DTYPE.itemsize == 128
+RS_PARAMS_DTYPE = np.dtype([("z_lo", "<f4"), ("z_hi", "<f4"), ("inv_y", "<f4"), ("inv_z", "<f4"), ("n_y", "<i4"),
+                            ("n_z", "<i4"), ("bin_base", "<i4"), ("count", "<i4")])
+
+TPC_OK, TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ETIMEOUT, TPC_EOVERFLOW, TPC_EBUSY = range(7)
+_CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW", 6: "EBUSY"}
+TF_TAINT_ANY = 1 | 2 | 4 | 8
+
+# item -> (numpy dtype, columns)
+ITEMS = {"perm": (1, np.int32), "rs_of": (2, np.int32), "row_start": (3, np.int32), "rs_params": (4, RS_PARAMS_DTYPE),
+         "bin_start": (5, np.int32), "up": (6, np.int32), "dn": (7, np.int32), "tie": (8, np.uint8),
+         "up_m": (9, np.int32), "dn_m": (10, np.int32), "tl_start": (11, np.int32), "tl_len": (12, np.int32),
+         "f_n": (13, np.int32), "f_nf": (14, np.int32), "f_nb": (15, np.int32), "f_flags": (16, np.int32),
+         "f_row": (17, np.int32), "f_hits": (18, np.int32), "f_par": (19, np.float32), "f_cov": (20, np.float32),
+         "f_chi2": (21, np.float64), "owner": (22, np.uint64), "tl_track": (23, np.int32), "sy": (24, np.float32),
+         "sz": (25, np.float32)}
+
+
+class TpcError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"TPC_{_CODES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class TpcConfig(ctypes.Structure):
+    _fields_ = [("bz_kg", ctypes.c_double), ("sigma", ctypes.c_double), ("d_max", ctypes.c_float),
+                ("min_chain", ctypes.c_int32), ("max_miss", ctypes.c_int32), ("n_min_track", ctypes.c_int32),
+                ("gate", ctypes.c_double), ("c0", ctypes.c_double * 5), ("s_max", ctypes.c_double),
+                ("edge", ctypes.c_double), ("taint_rel", ctypes.c_double), ("fp64_updates", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+_VP, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+
+
+def load_library(path: str | None = None):
+    """Load libtpcca.so (built in-tree by build()).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not found: run paper_1709_00618_b300.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "tpc_default_config": ([_VP], ctypes.c_int),
+        "tpc_create": ([_VP, _VP, ctypes.c_int, _VP, ctypes.c_size_t], ctypes.c_int),
+        "tpc_create_with_arena": ([_VP, _VP, ctypes.c_int, _VP, _VP, ctypes.c_size_t], ctypes.c_int),
+        "tpc_destroy": ([_VP], None),
+        "tpc_last_error": ([_VP], ctypes.c_char_p),
+        "tpc_arena_bytes": ([_I64, _I32], ctypes.c_size_t),
+        "tpc_reserve": ([_VP, _I64, _I32, _I64, _I64], ctypes.c_int),
+        "tpc_load_clusters": ([_VP, _VP, _I64, ctypes.c_int], ctypes.c_int),
+        "tpc_load_batch": ([_VP, _VP, _VP, _I32, ctypes.c_int], ctypes.c_int),
+        "tpc_find_tracks": ([_VP], ctypes.c_int),
+        "tpc_fit_tracks": ([_VP], ctypes.c_int),
+        "tpc_run_graph": ([_VP], ctypes.c_int),
+        "tpc_get_tracks": ([_VP, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
+        "tpc_sync": ([_VP], ctypes.c_int),
+        "tpc_get_counts": ([_VP, _VP], ctypes.c_int),
+        "tpc_get_stage": ([_VP, ctypes.c_int, _VP, _I64, _VP], ctypes.c_int),
+        "tpc_set_tuning": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def default_config(**overrides) -> TpcConfig:
+    cfg = TpcConfig()
+    load_library().tpc_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        if k == "c0":
+            for i in range(5):
+                cfg.c0[i] = v[i]
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Tracker:
+    """One tracking context on one CUDA device.
+
+    arena: None (the library allocates within hbm_budget), "torch" (a torch
+    uint8 tensor sized by tpc_arena_bytes for the first load), or a torch
+    tensor to use as the arena.  stream: None (library-owned stream), a
+    torch.cuda.Stream, or a raw cudaStream_t integer.
+    """
+
+    def __init__(self, device: int = 0, cfg: TpcConfig | None = None, stream=None, hbm_budget: int = 0,
+                 arena=None, arena_clusters: int = 0, arena_requests: int = 1):
+        self._lib = load_library()
+        self._ctx = ctypes.c_void_p()
+        self._arena_tensor = None
+        self._stream_obj = stream
+        sp = None
+        if stream is not None:
+            sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        if arena is None:
+            rc = self._lib.tpc_create(ctypes.byref(self._ctx), ctypes.byref(cfg) if cfg else None, device, sp,
+                                      hbm_budget)
+        else:
+            if isinstance(arena, str):
+                import torch
+                nbytes = self._lib.tpc_arena_bytes(max(arena_clusters, 1), max(arena_requests, 1))
+                arena = torch.empty(nbytes + 256, dtype=torch.uint8, device=f"cuda:{device}")
+            self._arena_tensor = arena
+            base = arena.data_ptr()
+            aligned = (base + 255) // 256 * 256
+            nbytes = arena.numel() * arena.element_size() - (aligned - base)
+            rc = self._lib.tpc_create_with_arena(ctypes.byref(self._ctx), ctypes.byref(cfg) if cfg else None, device,
+                                                 sp, aligned, nbytes)
+        if rc != 0:
+            raise TpcError(rc, "tpc_create failed")
+        self.n = 0
+
+    # -- error plumbing
+    def _ck(self, rc: int):
+        if rc != 0:
+            raise TpcError(rc, self._lib.tpc_last_error(self._ctx).decode())
+
+    def close(self):
+        if self._ctx:
+            self._lib.tpc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- the path
+    def load(self, clusters, req_offsets=None):
+        """clusters: numpy structured array (CLUSTER_DTYPE) on the host, or a
+        CUDA torch tensor holding the same 16-byte records."""
+        on_device = int(hasattr(clusters, "is_cuda") and clusters.is_cuda)
+        if not on_device:
+            clusters = np.ascontiguousarray(clusters)
+            n = len(clusters)
+        else:
+            n = clusters.numel() * clusters.element_size() // 16
+        self._keep_in = clusters
+        if req_offsets is None:
+            self._ck(self._lib.tpc_load_clusters(self._ctx, _ptr(clusters) if n else None, n, on_device))
+        else:
+            off = np.ascontiguousarray(np.asarray(req_offsets, dtype=np.int64))
+            self._ck(self._lib.tpc_load_batch(self._ctx, _ptr(clusters) if n else None, off.ctypes.data,
+                                              len(off) - 1, on_device))
+        self.n = n
+        return self
+
+    def find(self):
+        self._ck(self._lib.tpc_find_tracks(self._ctx))
+        return self
+
+    def fit(self):
+        self._ck(self._lib.tpc_fit_tracks(self._ctx))
+        return self
+
+    def run_graph(self):
+        self._ck(self._lib.tpc_run_graph(self._ctx))
+        return self
+
+    def sync(self):
+        self._ck(self._lib.tpc_sync(self._ctx))
+        return self
+
+    def reserve(self, n_clusters=0, n_requests=0, n_bins=0, n_tracklets=0):
+        self._ck(self._lib.tpc_reserve(self._ctx, n_clusters, n_requests, n_bins, n_tracklets))
+
+    def set_tuning(self, block_clusters=0, block_follow=0, ctas_per_sm_follow=0):
+        self._ck(self._lib.tpc_set_tuning(self._ctx, block_clusters, block_follow, ctas_per_sm_follow, 0))
+
+    def counts(self) -> dict:
+        c = np.zeros(8, np.int64)
+        self._ck(self._lib.tpc_get_counts(self._ctx, c.ctypes.data))
+        return dict(zip(("n", "n_req", "n_rs", "n_bins", "n_tracklets", "n_tracks", "status", "n_track_clusters"),
+                        (int(v) for v in c)))
+
+    def get(self, cluster_track: bool = True, track_clusters: bool = False, cap: int | None = None):
+        """Wait and copy out: (tracks, cluster_track, track_clusters)."""
+        nout = ctypes.c_int64()
+        if cap is None:
+            rc = self._lib.tpc_get_tracks(self._ctx, None, 0, ctypes.byref(nout), None, None)
+            if rc not in (0, TPC_EOVERFLOW):
+                self._ck(rc)
+            cap = nout.value
+        tracks = np.zeros(cap, TRACK_DTYPE)
+        ct = np.zeros(self.n, np.int32) if cluster_track else None
+        tc = None
+        if track_clusters:
+            tc = np.zeros(max(self.counts()["n_track_clusters"], 1), np.int32)
+        self._ck(self._lib.tpc_get_tracks(self._ctx, tracks.ctypes.data, cap, ctypes.byref(nout),
+                                          ct.ctypes.data if ct is not None and self.n else None,
+                                          tc.ctypes.data if tc is not None else None))
+        return tracks[:nout.value], ct, tc
+
+    def stage(self, name: str) -> np.ndarray:
+        item, dtype = ITEMS[name]
+        nb = ctypes.c_int64()
+        self._ck(self._lib.tpc_get_stage(self._ctx, item, None, 0, ctypes.byref(nb)))
+        out = np.zeros(nb.value // np.dtype(dtype).itemsize, dtype)
+        if nb.value:
+            self._ck(self._lib.tpc_get_stage(self._ctx, item, out.ctypes.data, nb.value, ctypes.byref(nb)))
+        if name == "f_hits":
+            out = out.reshape(-1, 159)
+        elif name == "f_par":
+            out = out.reshape(-1, 5)
+        elif name == "f_cov":
+            out = out.reshape(-1, 15)
+        return out
+
+    def track(self, clusters, req_offsets=None, graph: bool = False):
+        """load + find + fit (+ graph) + get."""
+        self.load(clusters, req_offsets)
+        if graph:
+            self.run_graph()
+        else:
+            self.find().fit()
+        return self.get()

@@ -1,0 +1,98 @@
+// Shared device definitions of the sector tracker kernels (sm_103a).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tpcca.h"
+
+namespace tpc {
+
+constexpr int NROW = 159;
+constexpr int NSEC = 36;
+
+// Device status word bits (host reads them at tpc_sync / tpc_get_*).
+enum : uint32_t {
+  ST_EINVAL = 1u,     // a cluster failed validation
+  ST_EOVERFLOW = 2u,  // a capacity was exceeded (grid bins, tracklets)
+  ST_ETIMEOUT = 4u,   // a bounded wait ran out
+};
+
+// Per row-sector grid parameters, 32 bytes (one sector-sized load).
+struct __align__(16) RsParams {
+  float z_lo, z_hi, inv_y, inv_z;
+  int32_t n_y, n_z, bin_base, count;
+};
+
+// Read-only 32-byte load of a row-sector's parameters.
+__device__ __forceinline__ RsParams load_params(const RsParams* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const int4 b = __ldg(reinterpret_cast<const int4*>(p) + 1);
+  RsParams r;
+  r.z_lo = a.x;
+  r.z_hi = a.y;
+  r.inv_y = a.z;
+  r.inv_z = a.w;
+  r.n_y = b.x;
+  r.n_z = b.y;
+  r.bin_base = b.z;
+  r.count = b.w;
+  return r;
+}
+
+// Scalars of a run that live in device memory so that graph-captured
+// kernels read the sizes of whatever batch is loaded.
+struct Counts {
+  int64_t n;          // clusters
+  int32_t n_req;      // requests
+  int32_t n_rs;       // row-sectors = n_req * 36 * 159
+  int32_t n_bins;     // total grid bins
+  int32_t n_tracklets;
+  int32_t n_tracks;
+  uint32_t status;    // ST_* bits
+  int32_t n_track_clusters;
+  int32_t follow_next; // work counter of the persistent follow launch
+  int32_t refit_next;
+  int32_t n32;         // clusters as int32 (length source of the per-cluster scans)
+  int32_t pad[4];
+};
+
+// Algorithm constants passed by value to every kernel (kernel parameter
+// space is read through the constant cache).
+struct KConst {
+  float K;          // 0.299792458e-3 * Bz[kG]
+  float V;          // sigma^2
+  double Vd;
+  float d_max;
+  float wy, wz;     // link windows
+  float gate;
+  float c0[5];
+  float s_max;
+  float edge;
+  float taint;      // divergence margin
+  int32_t min_chain, max_miss, n_min_track, fp64_updates;
+  int64_t bins_cap, tl_cap;
+};
+
+// Row radii X_r and active half-widths Y_r in binary32 (set once per device;
+// the library is a single translation unit).
+__device__ float g_row_x[NROW + 1];
+__device__ float g_row_yhi[NROW + 1];
+
+__device__ __forceinline__ bool fatal(const Counts* cn) {
+  return (*(volatile const uint32_t*)&cn->status) & (ST_EINVAL | ST_EOVERFLOW | ST_ETIMEOUT);
+}
+
+// Monotone map float -> uint32 so that unsigned min/max order equals float order.
+__device__ __forceinline__ uint32_t f2ord(float f) {
+  uint32_t u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(uint32_t u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7FFFFFFFu) : ~u);
+}
+
+// Grid-stride helper bounds.
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+}  // namespace tpc

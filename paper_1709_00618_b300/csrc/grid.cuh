@@ -1,0 +1,164 @@
+// a2: per-row (y, z) grid of every (request, sector, row) and the stable sort
+// of the clusters by (row-sector, bin, load index).
+//
+// The bin arithmetic decides integers (bin indices), so it is written with
+// explicitly rounded binary32 intrinsics (__fadd_rn & co. are never fused
+// into FMAs): the result is bit-identical to any IEEE binary32 evaluation of
+// the same expression sequence.
+#pragma once
+#include "common.cuh"
+
+namespace tpc {
+
+// Largest request q with off[q] <= i (empty requests are skipped naturally).
+__device__ __forceinline__ int find_request(const int64_t* __restrict__ off, int n_req, int64_t i) {
+  int lo = 0, hi = n_req - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(off + mid) <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_rs_init(int32_t* __restrict__ cnt, uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax,
+                          const Counts* cn) {
+  int32_t nrs = cn->n_rs;
+  for (int64_t i = gtid(); i < nrs; i += gstride()) {
+    cnt[i] = 0;
+    zmin[i] = 0xFFFFFFFFu;
+    zmax[i] = 0u;
+  }
+}
+
+// Count per row-sector and exact z range; validates every cluster.
+__global__ void k_grid_count(const tpc_cluster* __restrict__ in, const int64_t* __restrict__ req_off,
+                             Counts* cn, int32_t* __restrict__ rs_in, int32_t* __restrict__ cnt,
+                             uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax) {
+  const int64_t n = cn->n;
+  const int n_req = cn->n_req;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    int4 raw = __ldg(reinterpret_cast<const int4*>(in) + i);
+    float y = __int_as_float(raw.x), z = __int_as_float(raw.y);
+    uint32_t row = (uint32_t)raw.z & 0xFFFFu, sec = (uint32_t)raw.z >> 16;
+    if (row >= NROW || sec >= NSEC || !isfinite(y) || !isfinite(z)) {
+      atomicOr(&cn->status, ST_EINVAL);
+      rs_in[i] = -1;
+      continue;
+    }
+    int q = find_request(req_off, n_req, i);
+    int rs = (q * NSEC + (int)sec) * NROW + (int)row;
+    rs_in[i] = rs;
+    atomicAdd(&cnt[rs], 1);
+    uint32_t zo = f2ord(z);
+    atomicMin(&zmin[rs], zo);
+    atomicMax(&zmax[rs], zo);
+  }
+}
+
+// Bin parameters of one row-sector (same operation sequence as the reading).
+__global__ void k_grid_params(const int32_t* __restrict__ cnt, const uint32_t* __restrict__ zmin,
+                              const uint32_t* __restrict__ zmax, RsParams* __restrict__ par,
+                              int32_t* __restrict__ nbins, const Counts* cn) {
+  if (fatal(cn)) return;
+  int32_t nrs = cn->n_rs;
+  for (int64_t rs = gtid(); rs < nrs; rs += gstride()) {
+    int row = (int)(rs % NROW);
+    int n = cnt[rs];
+    float zl = n ? ord2f(zmin[rs]) : 0.0f, zh = n ? ord2f(zmax[rs]) : 0.0f;
+    float yh = g_row_yhi[row], yl = -yh;
+    float wy = __fsub_rn(yh, yl);
+    float dz = __fsub_rn(zh, zl);
+    float area = __fmul_rn(wy, fmaxf(dz, 1.0f));
+    float s = __fsqrt_rn(__fdiv_rn(__fmul_rn(area, 2.0f), __int2float_rn(n > 1 ? n : 1)));
+    s = fminf(fmaxf(s, 1.0f), 64.0f);
+    int ny = __float2int_rz(__fdiv_rn(wy, s)) + 1;
+    int nz = __float2int_rz(__fdiv_rn(dz, s)) + 1;
+    if (ny > 256) ny = 256;
+    if (nz > 4096) nz = 4096;
+    RsParams p;
+    p.z_lo = zl;
+    p.z_hi = zh;
+    p.inv_y = __fdiv_rn(__int2float_rn(ny), wy);
+    p.inv_z = __fdiv_rn(__int2float_rn(nz), fmaxf(dz, 1e-3f));
+    p.n_y = ny;
+    p.n_z = nz;
+    p.bin_base = 0;  // filled after the scan
+    p.count = n;
+    par[rs] = p;
+    nbins[rs] = ny * nz;
+  }
+}
+
+// After the scans: store bin_base into the params and check the capacity.
+__global__ void k_grid_finish_params(RsParams* __restrict__ par, const int32_t* __restrict__ bin_base,
+                                     Counts* cn, int64_t bins_cap, int32_t* __restrict__ bin_cnt) {
+  if (fatal(cn)) return;
+  int32_t nrs = cn->n_rs;
+  int32_t nb = bin_base[nrs];
+  if (gtid() == 0) cn->n_bins = nb;
+  if ((int64_t)nb > bins_cap) {
+    if (gtid() == 0) atomicOr(&cn->status, ST_EOVERFLOW);
+    return;
+  }
+  for (int64_t rs = gtid(); rs < nrs; rs += gstride()) par[rs].bin_base = bin_base[rs];
+  for (int64_t b = gtid(); b <= nb; b += gstride()) bin_cnt[b] = 0;
+}
+
+__device__ __forceinline__ int bin_coord(float v, float lo, float inv, int nb) {
+  float f = floorf(__fmul_rn(__fsub_rn(v, lo), inv));
+  if (!(f >= 0.0f)) return 0;
+  if (f > __int2float_rn(nb - 1)) return nb - 1;
+  return __float2int_rz(f);
+}
+
+// Global bin of every cluster and its (arrival-order) slot in that bin.
+__global__ void k_grid_bin(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ rs_in,
+                           const RsParams* __restrict__ par, int32_t* __restrict__ bin_cnt,
+                           int32_t* __restrict__ gbin, int32_t* __restrict__ slot, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int64_t n = cn->n;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    float2 yz = __ldg(reinterpret_cast<const float2*>(in + i));
+    int rs = rs_in[i];
+    RsParams p = par[rs];
+    int row = rs % NROW;
+    int iy = bin_coord(yz.x, -g_row_yhi[row], p.inv_y, p.n_y);
+    int iz = bin_coord(yz.y, p.z_lo, p.inv_z, p.n_z);
+    int gb = p.bin_base + iz * p.n_y + iy;
+    gbin[i] = gb;
+    slot[i] = atomicAdd(&bin_cnt[gb], 1);
+  }
+}
+
+__global__ void k_grid_scatter(const int32_t* __restrict__ gbin, const int32_t* __restrict__ slot,
+                               const int32_t* __restrict__ bin_start, int32_t* __restrict__ tmp,
+                               const Counts* cn) {
+  if (fatal(cn)) return;
+  const int64_t n = cn->n;
+  for (int64_t i = gtid(); i < n; i += gstride()) tmp[bin_start[gbin[i]] + slot[i]] = (int32_t)i;
+}
+
+// Stable order inside each bin: rank = number of bin members with a smaller
+// load index.  Bins hold about two clusters on average (the bin edge is
+// sqrt(2 A / n)); the count is quadratic only in the fullest bin.
+__global__ void k_grid_order(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ tmp,
+                             const int32_t* __restrict__ gbin, const int32_t* __restrict__ rs_in,
+                             const int32_t* __restrict__ bin_start, int32_t* __restrict__ perm,
+                             float2* __restrict__ yz, int32_t* __restrict__ rs_of, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int64_t n = cn->n;
+  for (int64_t p = gtid(); p < n; p += gstride()) {
+    int i = tmp[p];
+    int gb = gbin[i];
+    int a = bin_start[gb], b = bin_start[gb + 1];
+    int rank = 0;
+    for (int q = a; q < b; q++) rank += tmp[q] < i;
+    int dst = a + rank;
+    perm[dst] = i;
+    yz[dst] = __ldg(reinterpret_cast<const float2*>(in + i));
+    rs_of[dst] = rs_in[i];
+  }
+}
+
+}  // namespace tpc

@@ -1,0 +1,185 @@
+// Helix propagation and Kalman update of the 5-parameter track state
+// (y, z, sin phi, dz/ds_T, q/pT) in a uniform Bz field (Sec. 2, Fig. 1c).
+//
+// The state is binary32 with z kept relative to a per-track reference (the
+// seed cluster's z) so that drift-time coordinates of ~2.5e4 cm keep their
+// resolution.  The covariance is a packed lower triangle; it is held in FP64
+// for the first `fp64_updates` updates after every (re)seed, where the seed
+// covariance is large and the subtraction C -= G C[0:2,:] cancels, and in
+// FP32 afterwards.  chi2 is accumulated in FP64.
+#pragma once
+#include "common.cuh"
+
+namespace tpc {
+
+// packed index of (i, j), i >= j
+#define TPC_CI(i, j) ((i) * ((i) + 1) / 2 + (j))
+
+enum : uint32_t {
+  TF_TIE = TPC_TF_TAINT_TIE,
+  TF_GATE = TPC_TF_TAINT_GATE,
+  TF_EDGE = TPC_TF_TAINT_EDGE,
+  TF_SLIM = TPC_TF_TAINT_SLIM,
+  TF_SEED_FAIL = TPC_TF_SEED_FAIL,
+  TF_BACK_FAIL = TPC_TF_BACK_FAIL,
+  TF_REFIT_FAIL = TPC_TF_REFIT_FAIL
+};
+
+struct TrkState {
+  float x;   // row radius
+  int row;
+  float y, z, s, t, q;  // z relative to zref
+  float zref;
+};
+
+// C <- J C J^T for the sparse first-order Jacobian of one propagation step.
+template <typename T>
+__device__ __forceinline__ void cov_transport(T* C, T j02, T j04, T j24, T j12, T j13, T j14) {
+  const T c00 = C[0], c10 = C[1], c11 = C[2], c20 = C[3], c21 = C[4], c22 = C[5], c30 = C[6], c31 = C[7],
+          c32 = C[8], c33 = C[9], c40 = C[10], c41 = C[11], c42 = C[12], c43 = C[13], c44 = C[14];
+  // A = J C, rows 0..2
+  const T a00 = c00 + j02 * c20 + j04 * c40;
+  const T a02 = c20 + j02 * c22 + j04 * c42;
+  const T a04 = c40 + j02 * c42 + j04 * c44;
+  const T a10 = c10 + j12 * c20 + j13 * c30 + j14 * c40;
+  const T a11 = c11 + j12 * c21 + j13 * c31 + j14 * c41;
+  const T a12 = c21 + j12 * c22 + j13 * c32 + j14 * c42;
+  const T a13 = c31 + j12 * c32 + j13 * c33 + j14 * c43;
+  const T a14 = c41 + j12 * c42 + j13 * c43 + j14 * c44;
+  const T a20 = c20 + j24 * c40;
+  const T a21 = c21 + j24 * c41;
+  const T a22 = c22 + j24 * c42;
+  const T a23 = c32 + j24 * c43;
+  const T a24 = c42 + j24 * c44;
+  // C' = A J^T, lower triangle
+  C[0] = a00 + j02 * a02 + j04 * a04;
+  C[1] = a10 + j02 * a12 + j04 * a14;
+  C[2] = a11 + j12 * a12 + j13 * a13 + j14 * a14;
+  C[3] = a20 + j02 * a22 + j04 * a24;
+  C[4] = a21 + j12 * a22 + j13 * a23 + j14 * a24;
+  C[5] = a22 + j24 * a24;
+  C[6] = c30 + j02 * c32 + j04 * c43;
+  C[7] = c31 + j12 * c32 + j13 * c33 + j14 * c43;
+  C[8] = c32 + j24 * c43;
+  // C[9] = c33 unchanged
+  C[10] = c40 + j02 * c42 + j04 * c44;
+  C[11] = c41 + j12 * c42 + j13 * c43 + j14 * c44;
+  C[12] = c42 + j24 * c44;
+  // C[13], C[14] unchanged
+}
+
+// Kalman update with the measurement (my, mz_rel); returns the chi2 increment.
+template <typename T>
+__device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, float mz_rel, T V) {
+  const float r0 = my - p.y, r1 = mz_rel - p.z;
+  const T S00 = C[0] + V, S01 = C[1], S11 = C[2] + V;
+  const T idet = T(1) / (S00 * S11 - S01 * S01);
+  const T I00 = S11 * idet, I01 = -S01 * idet, I11 = S00 * idet;
+  const T k0[5] = {C[0], C[1], C[3], C[6], C[10]};  // column 0
+  const T k1[5] = {C[1], C[2], C[4], C[7], C[11]};  // column 1
+  T g0[5], g1[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    g0[i] = k0[i] * I00 + k1[i] * I01;
+    g1[i] = k0[i] * I01 + k1[i] * I11;
+  }
+  const T R0 = (T)r0, R1 = (T)r1;
+  p.y += (float)(g0[0] * R0 + g1[0] * R1);
+  p.z += (float)(g0[1] * R0 + g1[1] * R1);
+  p.s += (float)(g0[2] * R0 + g1[2] * R1);
+  p.t += (float)(g0[3] * R0 + g1[3] * R1);
+  p.q += (float)(g0[4] * R0 + g1[4] * R1);
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) C[TPC_CI(i, j)] -= g0[i] * k0[j] + g1[i] * k1[j];
+  const double d0 = r0, d1 = r1;
+  return d0 * ((double)I00 * d0 + (double)I01 * d1) + d1 * ((double)I01 * d0 + (double)I11 * d1);
+}
+
+// The filter: state, covariance in FP64 during the zone after a seed, FP32
+// afterwards; chi2 in FP64.
+struct Filter {
+  TrkState p;
+  float C[15];
+  double D[15];
+  double chi2;
+  int zone_left;  // FP64 updates left; 0 = FP32 mode
+  int nupd;
+
+  __device__ __forceinline__ void reset_cov(const KConst& kc) {
+    zone_left = kc.fp64_updates;
+#pragma unroll
+    for (int i = 0; i < 15; i++) {
+      C[i] = 0.0f;
+      D[i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; i++) {
+      C[TPC_CI(i, i)] = kc.c0[i];
+      D[TPC_CI(i, i)] = (double)kc.c0[i];
+    }
+    chi2 = 0.0;
+    nupd = 0;
+  }
+
+  // Propagate to row `row2`; returns false when |sin phi| reaches s_max.
+  // with_cov = false carries only the state.
+  __device__ __forceinline__ bool propagate(int row2, float x2, const KConst& kc, uint32_t& flags,
+                                            bool with_cov = true) {
+    const float dx = x2 - p.x;
+    const float kap = -kc.K * p.q;
+    const float s1 = p.s, s2 = s1 + kap * dx;
+    if (fabsf(fabsf(s1) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
+    if (!(fabsf(s1) < kc.s_max && fabsf(s2) < kc.s_max)) return false;
+    const float c1 = sqrtf(1.0f - s1 * s1), c2 = sqrtf(1.0f - s2 * s2);
+    const float icc = 1.0f / (c1 + c2);
+    const float ss = s1 + s2;
+    const float dy = dx * ss * icc;
+    // arc length: sin(phi2 - phi1) = kap*dx*g with g = c1 + s1 (s1+s2)/(c1+c2),
+    // so dS = dx*g*asin(a)/a, a = kap*dx*g, without the cancellation of
+    // asin(s2) - asin(s1) in binary32
+    const float g = c1 + s1 * ss * icc;
+    const float a = kap * dx * g;
+    const float dS = dx * g * (a != 0.0f ? asinf(a) / a : 1.0f);
+    if (with_cov) {
+      const float sm = 0.5f * ss, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
+      const float j02 = dx * icm3;
+      const float j04 = -kc.K * dx * dx * 0.5f * icm3;
+      const float j24 = -kc.K * dx;
+      const float j13 = dS;
+      const float j12 = p.t * dx * sm * icm3;
+      const float j14 = -p.t * kc.K * dx * dx * sm * 0.5f * icm3;
+      if (zone_left > 0) cov_transport<double>(D, j02, j04, j24, j12, j13, j14);
+      else cov_transport<float>(C, j02, j04, j24, j12, j13, j14);
+    }
+    p.y += dy;
+    p.z += p.t * dS;
+    p.s = s2;
+    p.x = x2;
+    p.row = row2;
+    return true;
+  }
+
+  __device__ __forceinline__ void update(float my, float mz_rel, const KConst& kc) {
+    if (zone_left > 0) {
+      chi2 += kalman_update<double>(p, D, my, mz_rel, kc.Vd);
+      if (--zone_left == 0) {
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      }
+    } else {
+      chi2 += kalman_update<float>(p, C, my, mz_rel, kc.V);
+    }
+    nupd++;
+  }
+
+  __device__ __forceinline__ float cyy() const { return zone_left > 0 ? (float)D[0] : C[0]; }
+  __device__ __forceinline__ float czz() const { return zone_left > 0 ? (float)D[2] : C[2]; }
+  __device__ __forceinline__ void cov_out(float* out) const {
+#pragma unroll
+    for (int i = 0; i < 15; i++) out[i] = zone_left > 0 ? (float)D[i] : C[i];
+  }
+};
+
+}  // namespace tpc

@@ -1,0 +1,763 @@
+// libtpcca: C ABI of the B300 sector tracker.  One translation unit: the
+// kernels are included from the headers beside this file.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "scan.cuh"
+#include "grid.cuh"
+#include "links.cuh"
+#include "kalman.cuh"
+#include "follow.cuh"
+#include "select.cuh"
+
+using namespace tpc;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+// Geometry of the reading: X_r = (float)(85.2 + r*((245.8-85.2)/158)),
+// Y_r = (float)(that double * tan 10 deg).
+void geometry_tables(float* x, float* yhi) {
+  for (int r = 0; r < NROW; r++) {
+    double xd = 85.2 + r * ((245.8 - 85.2) / 158.0);
+    x[r] = (float)xd;
+    yhi[r] = (float)(xd * 0.17632698070846498);
+  }
+  x[NROW] = x[NROW - 1];
+  yhi[NROW] = yhi[NROW - 1];
+}
+
+std::mutex g_dev_mutex;
+std::vector<int> g_dev_ready;
+
+cudaError_t ensure_device_tables(int device) {
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  if ((int)g_dev_ready.size() <= device) g_dev_ready.resize(device + 1, 0);
+  if (g_dev_ready[device]) return cudaSuccess;
+  float x[NROW + 1], y[NROW + 1];
+  geometry_tables(x, y);
+  cudaError_t e = cudaMemcpyToSymbol(g_row_x, x, sizeof(x));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_row_yhi, y, sizeof(y));
+  if (e == cudaSuccess) g_dev_ready[device] = 1;
+  return e;
+}
+
+struct Caps {
+  int64_t n = 0;      // clusters
+  int32_t req = 0;    // requests
+  int64_t bins = 0;   // grid bins
+  int64_t tl = 0;     // tracklets
+  int64_t tracks = 0; // tracks
+  int64_t nrs() const { return (int64_t)req * NSEC * NROW; }
+};
+
+Caps default_caps(int64_t n, int32_t req) {
+  Caps c;
+  c.n = std::max<int64_t>(n, 1024);
+  c.req = std::max<int32_t>(req, 1);
+  c.bins = 2 * c.n + 2048 * c.nrs();
+  c.tl = c.n / 3 + 16;  // chains are disjoint and hold >= 3 clusters: cannot overflow with min_chain >= 3
+  c.tracks = c.tl;      // tracks are a subset of the tracklets
+  return c;
+}
+
+// Offsets of every device array inside the arena.
+struct Layout {
+  size_t counts, req_off, in, rs_in, gbin, slot, tmp, perm, yz, rs_of, up, dn, up_m, dn_m, tie, flag, fidx, clen,
+      cend, owner, cluster_track, track_clusters;
+  size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
+  size_t bin_cnt, bin_start;
+  size_t tl_start, tl_len, tl_end, f_n, f_nf, f_nb, f_flags, f_row, hits, hrow, f_par, f_zref, f_cov, f_chi2, keep,
+      tidx, nown, tl_track, track_tl, tcount, toff, tracks;
+  size_t parts;
+  size_t total;
+};
+
+Layout make_layout(const Caps& c) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t N = (size_t)c.n, R = (size_t)c.req, NRS = (size_t)c.nrs(), B = (size_t)c.bins, T = (size_t)c.tl,
+               M = (size_t)c.tracks;
+  L.counts = take(sizeof(Counts));
+  L.req_off = take(8 * (R + 1));
+  L.in = take(16 * N);
+  L.rs_in = take(4 * N);
+  L.gbin = take(4 * N);
+  L.slot = take(4 * N);
+  L.tmp = take(4 * N);
+  L.perm = take(4 * N);
+  L.yz = take(8 * N);
+  L.rs_of = take(4 * N);
+  L.up = take(4 * N);
+  L.dn = take(4 * N);
+  L.up_m = take(4 * N);
+  L.dn_m = take(4 * N);
+  L.tie = take(N);
+  L.flag = take(4 * (N + 1));
+  L.fidx = take(4 * (N + 1));
+  L.clen = take(4 * N);
+  L.cend = take(4 * N);
+  L.owner = take(8 * N);
+  L.cluster_track = take(4 * N);
+  L.track_clusters = take(4 * N);
+  L.rs_cnt = take(4 * (NRS + 1));
+  L.rs_start = take(4 * (NRS + 1));
+  L.zmin = take(4 * NRS);
+  L.zmax = take(4 * NRS);
+  L.par = take(sizeof(RsParams) * NRS);
+  L.nbins = take(4 * (NRS + 1));
+  L.bin_base = take(4 * (NRS + 1));
+  L.bin_cnt = take(4 * (B + 1));
+  L.bin_start = take(4 * (B + 1));
+  L.tl_start = take(4 * T);
+  L.tl_len = take(4 * T);
+  L.tl_end = take(4 * T);
+  L.f_n = take(4 * T);
+  L.f_nf = take(4 * T);
+  L.f_nb = take(4 * T);
+  L.f_flags = take(4 * T);
+  L.f_row = take(4 * T);
+  L.hits = take(4 * T * NROW);
+  L.hrow = take(T * NROW);
+  L.f_par = take(4 * 5 * T);
+  L.f_zref = take(4 * T);
+  L.f_cov = take(4 * 15 * T);
+  L.f_chi2 = take(8 * T);
+  L.keep = take(4 * (T + 1));
+  L.tidx = take(4 * (T + 1));
+  L.nown = take(4 * T);
+  L.tl_track = take(4 * T);
+  L.track_tl = take(4 * M);
+  L.tcount = take(4 * (M + 1));
+  L.toff = take(4 * (M + 1));
+  L.tracks = take(sizeof(tpc_track) * M);
+  L.parts = take(4 * SCAN_PARTS);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct tpc_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  tpc_config cfg{};
+  KConst kc{};
+  Caps caps{};
+  Layout L{};
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  bool own_arena = false;
+  size_t budget = 0;
+  int n_sm = 148;
+  // current batch
+  int64_t n = 0;
+  int32_t n_req = 0;
+  bool loaded = false, found = false, fitted = false;
+  Counts* h_counts = nullptr;  // pinned mirror
+  int64_t* h_req = nullptr;    // pinned request offsets
+  int32_t h_req_cap = 0;
+  // tuning
+  int block_clusters = 256;
+  int block_follow = 128;
+  int ctas_follow = 4;
+  // graph
+  cudaGraphExec_t graph = nullptr;
+  std::string err;
+
+  template <typename T>
+  T* ptr(size_t off) const { return reinterpret_cast<T*>(arena + off); }
+};
+
+namespace {
+
+int fail(tpc_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(ctx, TPC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+KConst make_kconst(const tpc_config& c, const Caps& caps) {
+  KConst k{};
+  k.K = (float)(0.299792458e-3 * c.bz_kg);
+  k.V = (float)(c.sigma * c.sigma);
+  k.Vd = c.sigma * c.sigma;
+  k.d_max = c.d_max;
+  k.wy = (float)(2.0 * ((245.8 - 85.2) / 158.0) + 0.5);
+  k.wz = (float)(2.5 * ((245.8 - 85.2) / 158.0) + 0.5);
+  k.gate = (float)c.gate;
+  for (int i = 0; i < 5; i++) k.c0[i] = (float)c.c0[i];
+  k.s_max = (float)c.s_max;
+  k.edge = (float)c.edge;
+  k.taint = (float)c.taint_rel;
+  k.min_chain = c.min_chain;
+  k.max_miss = c.max_miss;
+  k.n_min_track = c.n_min_track;
+  k.fp64_updates = c.fp64_updates;
+  k.bins_cap = caps.bins;
+  k.tl_cap = caps.tl;
+  return k;
+}
+
+int grid_for(const tpc_ctx* ctx, int64_t items, int threads, int per_sm = 16) {
+  int64_t b = (items + threads - 1) / threads;
+  int64_t cap = (int64_t)ctx->n_sm * per_sm;
+  return (int)std::max<int64_t>(1, std::min(b, cap));
+}
+
+int do_reserve(tpc_ctx* ctx, const Caps& want) {
+  Caps c = ctx->caps;
+  bool grow = want.n > c.n || want.req > c.req || want.bins > c.bins || want.tl > c.tl || want.tracks > c.tracks ||
+              ctx->arena == nullptr;
+  if (!grow) return TPC_OK;
+  c.n = std::max(c.n, want.n);
+  c.req = std::max(c.req, want.req);
+  c.bins = std::max(c.bins, want.bins);
+  c.tl = std::max(c.tl, want.tl);
+  c.tracks = std::max(c.tracks, want.tracks);
+  Layout L = make_layout(c);
+  if (ctx->own_arena) {
+    if (ctx->budget && L.total > ctx->budget)
+      return fail(ctx, TPC_ENOMEM, "arena of %zu bytes exceeds the HBM budget of %zu bytes", L.total, ctx->budget);
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->arena) {
+      CK(cudaStreamSynchronize(ctx->stream));
+      CK(cudaFree(ctx->arena));
+      ctx->arena = nullptr;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, L.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, TPC_ENOMEM, "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+    }
+    ctx->arena = (char*)p;
+    ctx->arena_bytes = L.total;
+  } else if (L.total > ctx->arena_bytes) {
+    return fail(ctx, TPC_ENOMEM, "caller arena of %zu bytes is smaller than the %zu bytes needed", ctx->arena_bytes,
+                L.total);
+  }
+  ctx->caps = c;
+  ctx->L = L;
+  ctx->kc = make_kconst(ctx->cfg, c);
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  if (ctx->h_req_cap < c.req + 1) {
+    if (ctx->h_req) cudaFreeHost(ctx->h_req);
+    ctx->h_req = nullptr;
+    CK(cudaMallocHost(&ctx->h_req, sizeof(int64_t) * (c.req + 1)));
+    ctx->h_req_cap = c.req + 1;
+  }
+  return TPC_OK;
+}
+
+int create_common(tpc_ctx** out, const tpc_config* cfg, int device, void* stream) {
+  if (!out) return TPC_EINVAL;
+  *out = nullptr;
+  tpc_ctx* ctx = new tpc_ctx();
+  if (cfg) ctx->cfg = *cfg;
+  else tpc_default_config(&ctx->cfg);
+  ctx->device = device;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return TPC_ECUDA;
+  }
+  e = ensure_device_tables(device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return TPC_ECUDA;
+  }
+  cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (stream) {
+    ctx->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete ctx;
+      return TPC_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaMallocHost(&ctx->h_counts, sizeof(Counts)) != cudaSuccess) {
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return TPC_ECUDA;
+  }
+  memset(ctx->h_counts, 0, sizeof(Counts));
+  *out = ctx;
+  return TPC_OK;
+}
+
+// Validate the config (the same bounds the kernels assume).
+bool config_ok(const tpc_config& c) {
+  return std::isfinite(c.bz_kg) && c.sigma > 0 && c.d_max >= 0 && c.min_chain >= 2 && c.min_chain <= NROW &&
+         c.max_miss >= 1 && c.n_min_track >= 1 && c.n_min_track <= NROW && c.gate > 0 && c.s_max > 0 &&
+         c.s_max < 1 && c.fp64_updates >= 0 && c.taint_rel >= 0;
+}
+
+void scan(tpc_ctx* ctx, const int32_t* in, int32_t* out, LenSrc len, int32_t* total_out) {
+  Counts* cn = ctx->ptr<Counts>(ctx->L.counts);
+  int32_t* parts = ctx->ptr<int32_t>(ctx->L.parts);
+  k_scan_reduce<<<SCAN_PARTS, SCAN_THREADS, 0, ctx->stream>>>(in, len, parts, cn);
+  k_scan_parts<<<1, 1024, 0, ctx->stream>>>(parts, SCAN_PARTS, total_out, cn);
+  k_scan_down<<<SCAN_PARTS, SCAN_THREADS, 0, ctx->stream>>>(in, len, parts, out, cn);
+}
+
+GridView grid_view(tpc_ctx* ctx) {
+  const Layout& L = ctx->L;
+  GridView g;
+  g.yz = ctx->ptr<float2>(L.yz);
+  g.rs_of = ctx->ptr<int32_t>(L.rs_of);
+  g.par = ctx->ptr<RsParams>(L.par);
+  g.bin_start = ctx->ptr<int32_t>(L.bin_start);
+  return g;
+}
+
+FollowOut follow_out(tpc_ctx* ctx) {
+  const Layout& L = ctx->L;
+  FollowOut o;
+  o.n = ctx->ptr<int32_t>(L.f_n);
+  o.nf = ctx->ptr<int32_t>(L.f_nf);
+  o.nb = ctx->ptr<int32_t>(L.f_nb);
+  o.flags = ctx->ptr<int32_t>(L.f_flags);
+  o.row = ctx->ptr<int32_t>(L.f_row);
+  o.hits = ctx->ptr<int32_t>(L.hits);
+  o.hrow = ctx->ptr<uint8_t>(L.hrow);
+  o.par = ctx->ptr<float>(L.f_par);
+  o.zref = ctx->ptr<float>(L.f_zref);
+  o.cov = ctx->ptr<float>(L.f_cov);
+  o.chi2 = ctx->ptr<double>(L.f_chi2);
+  return o;
+}
+
+// a2..a7 on the context's stream (capacity-sized grids: graph-capturable).
+void enqueue_find(tpc_ctx* ctx) {
+  const Layout& L = ctx->L;
+  const Caps& C = ctx->caps;
+  cudaStream_t s = ctx->stream;
+  Counts* cn = ctx->ptr<Counts>(L.counts);
+  const int bc = ctx->block_clusters;
+  const int gN = grid_for(ctx, C.n, bc), gR = grid_for(ctx, C.nrs(), bc);
+  const int gT = grid_for(ctx, C.tl, bc);
+  int32_t* rs_cnt = ctx->ptr<int32_t>(L.rs_cnt);
+  int32_t* nbins = ctx->ptr<int32_t>(L.nbins);
+  int32_t* bin_base = ctx->ptr<int32_t>(L.bin_base);
+  int32_t* bin_cnt = ctx->ptr<int32_t>(L.bin_cnt);
+  int32_t* bin_start = ctx->ptr<int32_t>(L.bin_start);
+  // a2 grid
+  k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax), cn);
+  k_grid_count<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int64_t>(L.req_off), cn,
+                                 ctx->ptr<int32_t>(L.rs_in), rs_cnt, ctx->ptr<uint32_t>(L.zmin),
+                                 ctx->ptr<uint32_t>(L.zmax));
+  k_grid_params<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax),
+                                  ctx->ptr<RsParams>(L.par), nbins, cn);
+  LenSrc lrs{&cn->n_rs, 0, 0};
+  scan(ctx, rs_cnt, ctx->ptr<int32_t>(L.rs_start), lrs, nullptr);
+  scan(ctx, nbins, bin_base, lrs, nullptr);
+  k_grid_finish_params<<<gR, bc, 0, s>>>(ctx->ptr<RsParams>(L.par), bin_base, cn, C.bins, bin_cnt);
+  k_grid_bin<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.rs_in), ctx->ptr<RsParams>(L.par),
+                               bin_cnt, ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), cn);
+  LenSrc lb{&cn->n_bins, 0, 0};
+  scan(ctx, bin_cnt, bin_start, lb, nullptr);
+  k_grid_scatter<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
+                                   ctx->ptr<int32_t>(L.tmp), cn);
+  k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.tmp), ctx->ptr<int32_t>(L.gbin),
+                                 ctx->ptr<int32_t>(L.rs_in), bin_start, ctx->ptr<int32_t>(L.perm),
+                                 ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), cn);
+  // a3 neighbours
+  k_neighbours<<<gN, 256, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
+                                  bin_start, ctx->kc, ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn),
+                                  ctx->ptr<uint8_t>(L.tie), cn);
+  // a4 + a5
+  k_chains<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn), ctx->kc, ctx->ptr<int32_t>(L.up_m),
+                             ctx->ptr<int32_t>(L.dn_m), ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.clen),
+                             ctx->ptr<int32_t>(L.cend), cn);
+  scan(ctx, ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), LenSrc{&cn->n32, 0, 0}, nullptr);
+  k_tracklet_compact<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx),
+                                       ctx->ptr<int32_t>(L.clen), ctx->ptr<int32_t>(L.cend),
+                                       ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
+                                       ctx->ptr<int32_t>(L.tl_end), cn, C.tl);
+  // a6 follow
+  int gF = grid_for(ctx, C.tl, ctx->block_follow, ctx->ctas_follow);
+  k_follow<<<gF, ctx->block_follow, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start),
+                                            ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
+                                            ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), cn);
+  // a7 selection
+  k_zero64<<<gN, bc, 0, s>>>(ctx->ptr<uint64_t>(L.owner), cn);
+  k_fill32<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.cluster_track), -1, cn);
+  k_own<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, ctx->ptr<uint64_t>(L.owner),
+                          cn);
+  k_keep<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
+                           ctx->kc, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.nown), cn);
+  scan(ctx, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), LenSrc{&cn->n_tracklets, 0, 0}, nullptr);
+  k_assign<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
+                             ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), ctx->ptr<int32_t>(L.perm),
+                             ctx->ptr<int32_t>(L.tl_track), ctx->ptr<int32_t>(L.track_tl),
+                             ctx->ptr<int32_t>(L.cluster_track), cn);
+}
+
+// a8 on the context's stream.
+void enqueue_fit(tpc_ctx* ctx) {
+  const Layout& L = ctx->L;
+  const Caps& C = ctx->caps;
+  cudaStream_t s = ctx->stream;
+  Counts* cn = ctx->ptr<Counts>(L.counts);
+  const int bc = ctx->block_clusters;
+  const int gM = grid_for(ctx, C.tracks, bc);
+  k_track_counts<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.nown),
+                                   ctx->ptr<int32_t>(L.tcount), cn);
+  scan(ctx, ctx->ptr<int32_t>(L.tcount), ctx->ptr<int32_t>(L.toff), LenSrc{&cn->n_tracks, 0, 0},
+       &cn->n_track_clusters);
+  int gF = grid_for(ctx, C.tracks, ctx->block_follow, ctx->ctas_follow);
+  k_refit<<<gF, ctx->block_follow, 0, s>>>(
+      grid_view(ctx), ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.f_nf),
+      ctx->ptr<int32_t>(L.f_row), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint8_t>(L.hrow), ctx->ptr<float>(L.f_par),
+      ctx->ptr<float>(L.f_zref), ctx->ptr<float>(L.f_cov), ctx->ptr<double>(L.f_chi2),
+      ctx->ptr<uint64_t>(L.owner), ctx->ptr<int32_t>(L.toff), ctx->ptr<int32_t>(L.perm), ctx->kc,
+      ctx->ptr<tpc_track>(L.tracks), ctx->ptr<int32_t>(L.track_clusters), cn);
+  cudaMemcpyAsync(ctx->h_counts, cn, sizeof(Counts), cudaMemcpyDeviceToHost, s);
+}
+
+int check_status(tpc_ctx* ctx) {
+  uint32_t st = ctx->h_counts->status;
+  if (st & ST_EINVAL) return fail(ctx, TPC_EINVAL, "invalid cluster (row >= 159, sector >= 36 or non-finite y/z)");
+  if (st & ST_EOVERFLOW)
+    return fail(ctx, TPC_EOVERFLOW, "capacity exceeded (grid bins %d of %lld, tracklets %d of %lld); retry after "
+                "tpc_reserve with larger capacities",
+                ctx->h_counts->n_bins, (long long)ctx->caps.bins, ctx->h_counts->n_tracklets,
+                (long long)ctx->caps.tl);
+  if (st & ST_ETIMEOUT) return fail(ctx, TPC_ETIMEOUT, "a bounded device wait ran out");
+  return TPC_OK;
+}
+
+int load_common(tpc_ctx* ctx, const tpc_cluster* c, const int64_t* off, int32_t n_req, int on_device) {
+  if (!ctx) return TPC_EINVAL;
+  if (n_req < 1 || !off || off[0] != 0) return fail(ctx, TPC_EINVAL, "bad request offsets");
+  for (int32_t q = 0; q < n_req; q++)
+    if (off[q + 1] < off[q]) return fail(ctx, TPC_EINVAL, "request offsets must be non-decreasing");
+  int64_t n = off[n_req];
+  if (n < 0 || n >= 0x7FFFFFFF / 2) return fail(ctx, TPC_EINVAL, "cluster count %lld out of range", (long long)n);
+  if (n > 0 && !c) return fail(ctx, TPC_EINVAL, "null cluster pointer");
+  if ((int64_t)n_req * NSEC * NROW >= 0x7FFFFFFF / 2) return fail(ctx, TPC_EINVAL, "too many requests");
+  Caps want = default_caps(n, n_req);
+  want.bins = std::max(want.bins, ctx->caps.bins);
+  int rc = do_reserve(ctx, want);
+  if (rc) return rc;
+  CK(cudaSetDevice(ctx->device));
+  const Layout& L = ctx->L;
+  // host-side scalars of the batch: counts struct + request offsets
+  memcpy(ctx->h_req, off, sizeof(int64_t) * (n_req + 1));
+  Counts hc{};
+  hc.n = n;
+  hc.n_req = n_req;
+  hc.n_rs = n_req * NSEC * NROW;
+  hc.n32 = (int32_t)n;
+  CK(cudaStreamSynchronize(ctx->stream));  // the pinned staging buffers are reused
+  *ctx->h_counts = hc;
+  CK(cudaMemcpyAsync(ctx->ptr<Counts>(L.counts), ctx->h_counts, sizeof(Counts), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->ptr<int64_t>(L.req_off), ctx->h_req, sizeof(int64_t) * (n_req + 1),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  if (n > 0)
+    CK(cudaMemcpyAsync(ctx->ptr<tpc_cluster>(L.in), c, sizeof(tpc_cluster) * n,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  ctx->n = n;
+  ctx->n_req = n_req;
+  ctx->loaded = true;
+  ctx->found = ctx->fitted = false;
+  return TPC_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+extern "C" {
+
+int tpc_default_config(tpc_config* c) {
+  if (!c) return TPC_EINVAL;
+  memset(c, 0, sizeof(*c));
+  c->bz_kg = 5.0;
+  c->sigma = 0.1;
+  c->d_max = 1.0f;
+  c->min_chain = 3;
+  c->max_miss = 5;
+  c->n_min_track = 10;
+  c->gate = 16.0;
+  c->c0[0] = 100.0;
+  c->c0[1] = 100.0;
+  c->c0[2] = 1.0;
+  c->c0[3] = 1.0;
+  c->c0[4] = 100.0;
+  c->s_max = 0.95;
+  c->edge = 2.0;
+  c->taint_rel = 2e-3;
+  c->fp64_updates = 10;
+  return TPC_OK;
+}
+
+int tpc_create(tpc_ctx** out, const tpc_config* cfg, int device, void* cuda_stream, size_t hbm_budget) {
+  if (cfg && !config_ok(*cfg)) return TPC_EINVAL;
+  int rc = create_common(out, cfg, device, cuda_stream);
+  if (rc) return rc;
+  (*out)->own_arena = true;
+  (*out)->budget = hbm_budget;
+  return TPC_OK;
+}
+
+int tpc_create_with_arena(tpc_ctx** out, const tpc_config* cfg, int device, void* cuda_stream, void* arena,
+                          size_t bytes) {
+  if (cfg && !config_ok(*cfg)) return TPC_EINVAL;
+  if (!arena || ((uintptr_t)arena % ALIGN) != 0) return TPC_EINVAL;
+  int rc = create_common(out, cfg, device, cuda_stream);
+  if (rc) return rc;
+  (*out)->own_arena = false;
+  (*out)->arena = (char*)arena;
+  (*out)->arena_bytes = bytes;
+  return TPC_OK;
+}
+
+void tpc_destroy(tpc_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  if (ctx->own_arena && ctx->arena) cudaFree(ctx->arena);
+  if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
+  if (ctx->h_req) cudaFreeHost(ctx->h_req);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* tpc_last_error(tpc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+size_t tpc_arena_bytes(int64_t n_clusters, int32_t n_requests) {
+  return make_layout(default_caps(n_clusters, n_requests)).total;
+}
+
+int tpc_reserve(tpc_ctx* ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets) {
+  if (!ctx || n_clusters < 0 || n_requests < 0 || n_bins < 0 || n_tracklets < 0) return TPC_EINVAL;
+  Caps want = default_caps(std::max<int64_t>(n_clusters, ctx->caps.n), std::max(n_requests, ctx->caps.req));
+  if (n_bins) want.bins = n_bins;
+  if (n_tracklets) want.tl = n_tracklets;
+  want.tracks = std::max(want.tracks, want.tl);
+  return do_reserve(ctx, want);
+}
+
+int tpc_load_clusters(tpc_ctx* ctx, const tpc_cluster* c, int64_t n, int on_device) {
+  int64_t off[2] = {0, n};
+  return load_common(ctx, c, off, 1, on_device);
+}
+
+int tpc_load_batch(tpc_ctx* ctx, const tpc_cluster* c, const int64_t* req_offsets, int32_t n_req, int on_device) {
+  return load_common(ctx, c, req_offsets, n_req, on_device);
+}
+
+int tpc_find_tracks(tpc_ctx* ctx) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "no clusters loaded");
+  CK(cudaSetDevice(ctx->device));
+  enqueue_find(ctx);
+  CK(cudaGetLastError());
+  ctx->found = true;
+  return TPC_OK;
+}
+
+int tpc_fit_tracks(tpc_ctx* ctx) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->found) return fail(ctx, TPC_EINVAL, "tpc_find_tracks has not run on the loaded clusters");
+  CK(cudaSetDevice(ctx->device));
+  enqueue_fit(ctx);
+  CK(cudaGetLastError());
+  ctx->fitted = true;
+  return TPC_OK;
+}
+
+int tpc_run_graph(tpc_ctx* ctx) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "no clusters loaded");
+  CK(cudaSetDevice(ctx->device));
+  if (!ctx->graph) {
+    if (!ctx->own_stream && ctx->stream == nullptr)
+      return fail(ctx, TPC_EINVAL, "graph capture needs a non-default stream");
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_find(ctx);
+    enqueue_fit(ctx);
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess) return fail(ctx, TPC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      ctx->graph = nullptr;
+      return fail(ctx, TPC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+  }
+  CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+  ctx->found = ctx->fitted = true;
+  return TPC_OK;
+}
+
+int tpc_sync(tpc_ctx* ctx) {
+  if (!ctx) return TPC_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!ctx->fitted && ctx->found) {
+    CK(cudaMemcpy(ctx->h_counts, ctx->ptr<Counts>(ctx->L.counts), sizeof(Counts), cudaMemcpyDeviceToHost));
+  }
+  return check_status(ctx);
+}
+
+int tpc_get_tracks(tpc_ctx* ctx, tpc_track* out, int64_t cap, int64_t* n_out, int32_t* cluster_track,
+                   int32_t* track_clusters) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->fitted) return fail(ctx, TPC_EINVAL, "tpc_fit_tracks has not run");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_status(ctx);
+  if (rc) return rc;
+  const Counts& hc = *ctx->h_counts;
+  if (n_out) *n_out = hc.n_tracks;
+  if (hc.n_tracks > cap) return fail(ctx, TPC_EOVERFLOW, "%d tracks do not fit cap %lld", hc.n_tracks, (long long)cap);
+  const Layout& L = ctx->L;
+  if (out && hc.n_tracks)
+    CK(cudaMemcpyAsync(out, ctx->ptr<tpc_track>(L.tracks), sizeof(tpc_track) * hc.n_tracks, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  if (cluster_track && ctx->n)
+    CK(cudaMemcpyAsync(cluster_track, ctx->ptr<int32_t>(L.cluster_track), sizeof(int32_t) * ctx->n,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  if (track_clusters && hc.n_track_clusters)
+    CK(cudaMemcpyAsync(track_clusters, ctx->ptr<int32_t>(L.track_clusters), sizeof(int32_t) * hc.n_track_clusters,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return TPC_OK;
+}
+
+int tpc_get_counts(tpc_ctx* ctx, int64_t counts[8]) {
+  if (!ctx || !counts) return TPC_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  Counts hc{};
+  if (ctx->loaded) CK(cudaMemcpy(&hc, ctx->ptr<Counts>(ctx->L.counts), sizeof(Counts), cudaMemcpyDeviceToHost));
+  counts[0] = hc.n;
+  counts[1] = hc.n_req;
+  counts[2] = hc.n_rs;
+  counts[3] = hc.n_bins;
+  counts[4] = hc.n_tracklets;
+  counts[5] = hc.n_tracks;
+  counts[6] = hc.status;
+  counts[7] = hc.n_track_clusters;
+  return TPC_OK;
+}
+
+int tpc_get_stage(tpc_ctx* ctx, int item, void* host_out, int64_t cap_bytes, int64_t* n_bytes) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "nothing loaded");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  Counts hc{};
+  CK(cudaMemcpy(&hc, ctx->ptr<Counts>(ctx->L.counts), sizeof(Counts), cudaMemcpyDeviceToHost));
+  const Layout& L = ctx->L;
+  const int64_t n = hc.n, nrs = hc.n_rs, T = hc.n_tracklets;
+  size_t off = 0;
+  int64_t bytes = 0;
+  switch (item) {
+    case TPC_ITEM_PERM: off = L.perm; bytes = 4 * n; break;
+    case TPC_ITEM_RS_OF: off = L.rs_of; bytes = 4 * n; break;
+    case TPC_ITEM_ROW_START: off = L.rs_start; bytes = 4 * (nrs + 1); break;
+    case TPC_ITEM_RS_PARAMS: off = L.par; bytes = (int64_t)sizeof(RsParams) * nrs; break;
+    case TPC_ITEM_BIN_START: off = L.bin_start; bytes = 4 * ((int64_t)hc.n_bins + 1); break;
+    case TPC_ITEM_UP: off = L.up; bytes = 4 * n; break;
+    case TPC_ITEM_DN: off = L.dn; bytes = 4 * n; break;
+    case TPC_ITEM_TIE: off = L.tie; bytes = n; break;
+    case TPC_ITEM_UP_M: off = L.up_m; bytes = 4 * n; break;
+    case TPC_ITEM_DN_M: off = L.dn_m; bytes = 4 * n; break;
+    case TPC_ITEM_TL_START: off = L.tl_start; bytes = 4 * T; break;
+    case TPC_ITEM_TL_LEN: off = L.tl_len; bytes = 4 * T; break;
+    case TPC_ITEM_F_N: off = L.f_n; bytes = 4 * T; break;
+    case TPC_ITEM_F_NF: off = L.f_nf; bytes = 4 * T; break;
+    case TPC_ITEM_F_NB: off = L.f_nb; bytes = 4 * T; break;
+    case TPC_ITEM_F_FLAGS: off = L.f_flags; bytes = 4 * T; break;
+    case TPC_ITEM_F_ROW: off = L.f_row; bytes = 4 * T; break;
+    case TPC_ITEM_F_HITS: off = L.hits; bytes = 4 * T * NROW; break;
+    case TPC_ITEM_F_PAR: off = L.f_par; bytes = 4 * 5 * T; break;
+    case TPC_ITEM_F_COV: off = L.f_cov; bytes = 4 * 15 * T; break;
+    case TPC_ITEM_F_CHI2: off = L.f_chi2; bytes = 8 * T; break;
+    case TPC_ITEM_OWNER: off = L.owner; bytes = 8 * n; break;
+    case TPC_ITEM_TL_TRACK: off = L.tl_track; bytes = 4 * T; break;
+    case TPC_ITEM_SY:
+    case TPC_ITEM_SZ: off = L.yz; bytes = 4 * n; break;
+    default: return fail(ctx, TPC_EINVAL, "unknown item %d", item);
+  }
+  if (n_bytes) *n_bytes = bytes;
+  if (!host_out) return TPC_OK;
+  if (bytes > cap_bytes) return fail(ctx, TPC_EOVERFLOW, "item needs %lld bytes", (long long)bytes);
+  if (bytes == 0) return TPC_OK;
+  if (item == TPC_ITEM_SY || item == TPC_ITEM_SZ) {
+    std::vector<float> tmp(2 * n);
+    CK(cudaMemcpy(tmp.data(), ctx->arena + off, 8 * n, cudaMemcpyDeviceToHost));
+    float* o = (float*)host_out;
+    for (int64_t i = 0; i < n; i++) o[i] = tmp[2 * i + (item == TPC_ITEM_SZ)];
+    return TPC_OK;
+  }
+  if (item == TPC_ITEM_F_PAR) {
+    // z is kept relative to the per-tracklet reference on the device
+    std::vector<float> zr(T);
+    CK(cudaMemcpy(host_out, ctx->arena + off, bytes, cudaMemcpyDeviceToHost));
+    if (T) CK(cudaMemcpy(zr.data(), ctx->arena + L.f_zref, 4 * T, cudaMemcpyDeviceToHost));
+    float* o = (float*)host_out;
+    for (int64_t t = 0; t < T; t++) o[5 * t + 1] += zr[t];
+    return TPC_OK;
+  }
+  CK(cudaMemcpy(host_out, ctx->arena + off, bytes, cudaMemcpyDeviceToHost));
+  return TPC_OK;
+}
+
+int tpc_set_tuning(tpc_ctx* ctx, int block_clusters, int block_follow, int ctas_per_sm_follow, int reserved) {
+  (void)reserved;
+  if (!ctx) return TPC_EINVAL;
+  if (block_clusters && (block_clusters < 32 || block_clusters > 1024 || block_clusters % 32))
+    return fail(ctx, TPC_EINVAL, "block_clusters must be a multiple of 32 in [32, 1024]");
+  if (block_follow && (block_follow < 32 || block_follow > 128 || block_follow % 32))
+    return fail(ctx, TPC_EINVAL, "block_follow must be a multiple of 32 in [32, 128]");
+  if (ctas_per_sm_follow < 0 || ctas_per_sm_follow > 64) return fail(ctx, TPC_EINVAL, "ctas_per_sm out of range");
+  if (block_clusters) ctx->block_clusters = block_clusters;
+  if (block_follow) ctx->block_follow = block_follow;
+  if (ctas_per_sm_follow) ctx->ctas_follow = ctas_per_sm_follow;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return TPC_OK;
+}
+
+}  // extern "C"

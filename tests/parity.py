@@ -1,0 +1,181 @@
+"""Stage-by-stage comparison of the CUDA path with the FP64 oracle.
+
+Bit-exact: grid (order, bin parameters, bin starts), links, tie flags,
+tracklets.  Follow and selection: exact cluster lists and assignments except
+for tracklets flagged as tainted on either side (a decision within the
+divergence margin, taken in FP32 on the GPU and FP64 in the oracle) and the
+tracklets sharing clusters with them; parameters within 1e-4 relative
+(floors 1 cm, 1 cm, 0.01, 0.01, 0.01 c/GeV), covariances within 1e-3 relative
+(floor 1e-3 sqrt(C_ii C_jj)).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TAINT = 1 | 2 | 4 | 8
+PAR_FLOOR = np.array([1.0, 1.0, 0.01, 0.01, 0.01])
+PAR_TOL = 1e-4
+COV_TOL = 1e-3
+NROW = 159
+
+
+def tri_diag_index():
+    return [i * (i + 1) // 2 + i for i in range(5)]
+
+
+def par_rel_err(gpu, ref):
+    gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
+    return np.abs(gpu - ref) / np.maximum(np.abs(ref), PAR_FLOOR)
+
+
+def cov_rel_err(gpu, ref):
+    gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
+    d = tri_diag_index()
+    diag = np.abs(ref[..., d])
+    err = np.zeros_like(ref)
+    q = 0
+    for i in range(5):
+        for j in range(i + 1):
+            scale = np.maximum(np.abs(ref[..., q]), 1e-3 * np.sqrt(diag[..., i] * diag[..., j]))
+            err[..., q] = np.abs(gpu[..., q] - ref[..., q]) / np.maximum(scale, 1e-300)
+            q += 1
+    return err
+
+
+def compare_grid(trk, ref):
+    perm = trk.stage("perm")
+    assert np.array_equal(perm, ref["perm"]), "sorted order differs"
+    assert np.array_equal(trk.stage("rs_of"), ref["rs_of"])
+    assert np.array_equal(trk.stage("row_start"), ref["row_start"])
+    p = trk.stage("rs_params")
+    for k in ("z_lo", "z_hi"):
+        assert np.array_equal(p[k], ref[k]), k
+    for k in ("inv_y", "inv_z"):
+        assert np.array_equal(p[k].view(np.uint32), ref[k].view(np.uint32)), k
+    for k in ("n_y", "n_z"):
+        assert np.array_equal(p[k], ref[k]), k
+    assert np.array_equal(p["bin_base"], ref["bin_base"][:-1].astype(np.int32))
+    assert np.array_equal(p["count"], np.diff(ref["row_start"]))
+    assert np.array_equal(trk.stage("bin_start"), ref["bin_start"])
+
+
+def compare_links(trk, ref):
+    for k in ("up", "dn", "tie", "up_m", "dn_m"):
+        assert np.array_equal(trk.stage(k), ref[k]), k
+
+
+def compare_tracklets(trk, ref):
+    assert np.array_equal(trk.stage("tl_start"), ref["tl_start"])
+    assert np.array_equal(trk.stage("tl_len"), ref["tl_len"])
+
+
+def follow_result(trk):
+    return {k: trk.stage(k) for k in ("f_n", "f_nf", "f_nb", "f_flags", "f_row", "f_hits", "f_par", "f_cov",
+                                      "f_chi2", "owner", "tl_track")}
+
+
+def compare_follow(g, ref, stats):
+    """Exact cluster lists for untainted tracklets, tolerances on their state."""
+    T = len(ref["f_n"])
+    assert len(g["f_n"]) == T
+    taint = ((g["f_flags"] & TAINT) != 0) | ((ref["f_flags"] & TAINT) != 0)
+    same = (g["f_n"] == ref["f_n"]) & (g["f_nf"] == ref["f_nf"]) & (g["f_nb"] == ref["f_nb"])
+    for t in np.nonzero(same)[0]:
+        n = g["f_n"][t]
+        if not np.array_equal(g["f_hits"][t, :n], ref["f_hits"][t, :n]):
+            same[t] = False
+    bad = ~same & ~taint
+    assert not bad.any(), f"{bad.sum()} untainted tracklets differ, e.g. {np.nonzero(bad)[0][:10]}"
+    fail_mask = ((g["f_flags"] ^ ref["f_flags"]) & (16 | 32)) != 0
+    assert not (fail_mask & ~taint).any(), "seed/backward failure flags differ"
+    ok = same & ~taint & (g["f_n"] > 0)
+    assert np.array_equal(g["f_row"][ok], ref["f_row"][ok])
+    pe = par_rel_err(g["f_par"][ok], ref["f_par"][ok])
+    ce = cov_rel_err(g["f_cov"][ok], ref["f_cov"][ok])
+    stats.update(tracklets=T, tainted=int(taint.sum()), diverged=int((~same).sum()),
+                 follow_par_err_max=float(pe.max()) if pe.size else 0.0,
+                 follow_cov_err_max=float(ce.max()) if ce.size else 0.0,
+                 follow_par_err_p99=float(np.percentile(pe.max(1), 99)) if pe.size else 0.0)
+    return taint | ~same
+
+
+def compare_selection(g, gct, ref, excluded_tl, stats):
+    """Cluster -> tracklet-of-track assignment outside the divergence shadow."""
+    T = len(ref["f_n"])
+    hits_g, hits_r = g["f_hits"], ref["f_hits"]
+    n_g, n_r = g["f_n"], ref["f_n"]
+    shadow_clusters = set()
+    for t in np.nonzero(excluded_tl)[0]:
+        shadow_clusters.update(hits_g[t, :n_g[t]].tolist())
+        shadow_clusters.update(hits_r[t, :n_r[t]].tolist())
+    # tracklets touching those clusters, then all of their clusters
+    sc = np.zeros(len(ref["perm"]), bool)
+    if shadow_clusters:
+        sc[np.fromiter(shadow_clusters, np.int64)] = True
+    touched = np.zeros(T, bool)
+    for t in range(T):
+        if (n_g[t] and sc[hits_g[t, :n_g[t]]].any()) or (n_r[t] and sc[hits_r[t, :n_r[t]]].any()):
+            touched[t] = True
+    sc2 = sc.copy()
+    for t in np.nonzero(touched)[0]:
+        sc2[hits_g[t, :n_g[t]]] = True
+        sc2[hits_r[t, :n_r[t]]] = True
+    # map track index -> tracklet id on both sides, then compare per cluster (load order)
+    perm = ref["perm"]
+    g_tl_of_track = np.full(max(int(g["tl_track"].max(initial=-1)) + 1, 1), -1)
+    kept = np.nonzero(g["tl_track"] >= 0)[0]
+    g_tl_of_track[g["tl_track"][kept]] = kept
+    r_tl_of_track = np.full(max(int(ref["tl_track"].max(initial=-1)) + 1, 1), -1)
+    kept_r = np.nonzero(ref["tl_track"] >= 0)[0]
+    r_tl_of_track[ref["tl_track"][kept_r]] = kept_r
+    a = np.where(gct >= 0, g_tl_of_track[np.maximum(gct, 0)], -1)
+    b = np.where(ref["cluster_track"] >= 0, r_tl_of_track[np.maximum(ref["cluster_track"], 0)], -1)
+    shadow_load = np.zeros(len(perm), bool)
+    shadow_load[perm[sc2]] = True
+    diff = (a != b) & ~shadow_load
+    assert not diff.any(), f"{diff.sum()} cluster assignments differ outside the divergence shadow"
+    stats.update(clusters=len(perm), shadow_clusters=int(shadow_load.sum()),
+                 assigned_equal=int(((a == b) & ~shadow_load).sum()))
+    return touched | excluded_tl
+
+
+def compare_refit(tracks, ref, g, excluded, stats):
+    g_tl = np.nonzero(g["tl_track"] >= 0)[0]
+    r_tl = ref["t_tracklet"]
+    common = np.intersect1d(g_tl, r_tl)
+    common = common[~excluded[common]]
+    gi = g["tl_track"][common]
+    ri = ref["tl_track"][common]
+    tg, = (tracks[gi],)
+    assert np.array_equal(tg["n_clusters"], ref["t_n"][ri])
+    assert np.array_equal(tg["first_row"], np.where(ref["t_flags"][ri] & 64, tg["first_row"], ref["t_row_in"][ri]))
+    assert np.array_equal(tg["last_row"], ref["t_row_out"][ri])
+    assert np.array_equal(tg["ndf"], ref["t_ndf"][ri])
+    okf = (tg["flags"] & 64) == (ref["t_flags"][ri] & 64)
+    assert okf.all()
+    pe = par_rel_err(tg["par"], ref["t_par"][ri])
+    ce = cov_rel_err(tg["cov"], ref["t_cov"][ri])
+    chi = np.abs(tg["chi2"] - ref["t_chi2"][ri]) / np.maximum(ref["t_chi2"][ri], 1.0)
+    stats.update(tracks_compared=int(len(common)), tracks_gpu=int(len(tracks)), tracks_ref=int(len(r_tl)),
+                 refit_par_err_max=float(pe.max()) if pe.size else 0.0,
+                 refit_cov_err_max=float(ce.max()) if ce.size else 0.0,
+                 refit_chi2_err_max=float(chi.max()) if chi.size else 0.0)
+    assert (pe <= PAR_TOL).all(), f"refit params beyond 1e-4: max {pe.max()}"
+    assert (ce <= COV_TOL).all(), f"refit covariance beyond 1e-3: max {ce.max()}"
+
+
+def full_parity(trk, clusters, ref, req_offsets=None, graph=False):
+    """Run the CUDA path and compare every stage; returns the statistics."""
+    stats = {}
+    tracks, gct, _ = trk.track(clusters, req_offsets, graph=graph)
+    compare_grid(trk, ref)
+    compare_links(trk, ref)
+    compare_tracklets(trk, ref)
+    g = follow_result(trk)
+    excl = compare_follow(g, ref, stats)
+    excl2 = compare_selection(g, gct, ref, excl, stats)
+    if "follow_par_err_max" in stats:
+        assert stats["follow_par_err_max"] <= PAR_TOL, stats
+        assert stats["follow_cov_err_max"] <= COV_TOL, stats
+    compare_refit(tracks, ref, g, excl2, stats)
+    return stats
