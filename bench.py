@@ -85,6 +85,58 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# Kernels launched per step (tpc_run_graph): grid 10 + 3 scans x 3, links 2 +
+# 1 scan, follow 1, selection 5 + 1 scan, refit 2 + 1 scan.
+KERNELS_PER_STEP = 7 + 3 * 3 + 2 + 3 + 1 + 5 + 3 + 2 + 3
+
+# Algorithmic FP32 work of the Kalman kernels (counted from the source, per
+# unit of the device work counters): a propagation with covariance transport
+# (helix step, Jacobian, J C J^T on the packed triangle, compensated adds) is
+# 170 flop, an FP32 update (gain, state, covariance, residuals) 150 flop, a
+# candidate examined by the pick-up 10 flop.
+FLOP_PROP, FLOP_UPD, FLOP_CAND = 170, 150, 10
+# Algorithmic DRAM bytes per cluster of the memory-bound stages: grid 88
+# (16 B read twice, 4 B rs, 8 B bin/slot written and read, scatter 4 B,
+# order 16 B gather + 16 B writes), neighbours 33 (8 B own y/z, 8 B candidate
+# re-reads, 8 B links + 1 B tie written, ~8 B bin starts).
+BYTES_GRID, BYTES_NEIGH = 88, 33
+
+
+def roofline(stages, work, counts, n):
+    peaks, src = _peaks()
+    dom = max(stages, key=stages.get)
+    t = stages[dom] / 1e3
+    if dom in ("follow", "refit"):
+        flop = FLOP_PROP * work["prop"] + FLOP_UPD * work["upd32"] + FLOP_CAND * work["cand"]
+        sm = 148
+        peak = sm * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        ach = flop / t / 1e12
+        return {"kernel": f"k_{dom}", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "note": f"FP32 FMA peak 148 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2032.0)} MHz ({src} clock); "
+                        "work counted by device counters; the follow stage includes both Kalman kernels' FP64 zones"}
+    b = (BYTES_GRID if dom == "grid" else BYTES_NEIGH) * n
+    ach = b / t / 1e9
+    peak = peaks["hbm_gbs"]
+    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": None}
+
+
+def cpu_baseline(cl):
+    """The FP64 oracle timed on this host's cores over the same event."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.run(cl[:1000], threads=threads)
+    times = []
+    t_end = time.perf_counter() + 15.0
+    while time.perf_counter() < t_end or not times:
+        t0 = time.perf_counter()
+        oracle.run(cl, threads=threads)
+        times.append(time.perf_counter() - t0)
+    return {"value": len(cl) * len(times) / sum(times), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"the full event ({len(cl)} clusters) x {len(times)} runs, all stages a2-a8"}
+
+
 def run_reference(args):
     """The oracle (plain FP64 C, all host cores) on the same workload."""
     import numpy as np
@@ -180,6 +232,21 @@ def main():
     counts = trk.counts()
     tracks, ct, _ = trk.get()
 
+    # per-stage device time (CUDA events recorded by the library on its stream)
+    trk.set_profiling(True)
+    runs = []
+    for _ in range(5):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        trk.load(dev_in)
+        trk.find().fit()
+        trk.sync()
+        runs.append(trk.stage_times())
+    trk.set_profiling(False)
+    stages = {k: statistics.median(r[k] for r in runs) for k in runs[0]}
+    work = trk.work()
+    roof = roofline(stages, work, counts, n)
+
     # end to end through the public API: pinned host input -> tracks + assignment on the host
     pinned = torch.from_numpy(cl.view(np.uint8)).pin_memory()
     host_in = pinned.numpy().view(synth.CLUSTER_DTYPE)
@@ -203,7 +270,13 @@ def main():
             "clocks": clk.summary(),
             "e2e": {"value": world * n / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 128 * len(tr) + 4 * n},
+            "gpu_launches": KERNELS_PER_STEP,
+            "roofline": roof,
+            "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+            "work": work,
             "peaks_source": src}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cl)
     if rank == 0:
         print(json.dumps(line))
     trk.close()

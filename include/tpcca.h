@@ -196,6 +196,21 @@ enum {
 };
 int tpc_get_stage(tpc_ctx *ctx, int item, void *host_out, int64_t cap_bytes, int64_t *n_bytes);
 
+/* ------------------------------------------------------------ measurement */
+/* With profiling on, tpc_find_tracks / tpc_fit_tracks record CUDA events on
+ * the context's stream between stages (not inside tpc_run_graph).
+ * tpc_get_stage_times waits for the stream and returns the device time in ms
+ * of [0] a2 grid, [1] a3 neighbours, [2] a4+a5 links and tracklets,
+ * [3] a6 follow, [4] a7 selection, [5] a8 refit of the last such run. */
+int tpc_set_profiling(tpc_ctx *ctx, int on);
+int tpc_get_stage_times(tpc_ctx *ctx, float ms[6]);
+
+/* Work counters of the last run (waits for the stream): [0] propagations
+ * with covariance transport, [1] FP32 Kalman updates, [2] FP64-zone updates,
+ * [3] candidate clusters examined by the pick-up, [4] propagations done with
+ * the FP64 covariance. */
+int tpc_get_work(tpc_ctx *ctx, uint64_t work[5]);
+
 /* ------------------------------------------------------ tuning (autotuner) */
 /* Threads per block of the cluster-, row-sector- and tracklet-parallel
  * kernels and CTAs per SM of the persistent follow/refit launches.  0 keeps

@@ -86,6 +86,9 @@ def load_library(path: str | None = None):
         "tpc_get_counts": ([_VP, _VP], ctypes.c_int),
         "tpc_get_stage": ([_VP, ctypes.c_int, _VP, _I64, _VP], ctypes.c_int),
         "tpc_set_tuning": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "tpc_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
+        "tpc_get_stage_times": ([_VP, _VP], ctypes.c_int),
+        "tpc_get_work": ([_VP, _VP], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -213,6 +216,22 @@ class Tracker:
 
     def set_tuning(self, block_clusters=0, block_follow=0, ctas_per_sm_follow=0):
         self._ck(self._lib.tpc_set_tuning(self._ctx, block_clusters, block_follow, ctas_per_sm_follow, 0))
+
+    def set_profiling(self, on: bool = True):
+        self._ck(self._lib.tpc_set_profiling(self._ctx, int(on)))
+
+    STAGES = ("grid", "neighbours", "links_tracklets", "follow", "select", "refit")
+
+    def stage_times(self) -> dict:
+        """Device ms per stage of the last profiled find + fit."""
+        ms = np.zeros(6, np.float32)
+        self._ck(self._lib.tpc_get_stage_times(self._ctx, ms.ctypes.data))
+        return dict(zip(self.STAGES, (float(v) for v in ms)))
+
+    def work(self) -> dict:
+        w = np.zeros(5, np.uint64)
+        self._ck(self._lib.tpc_get_work(self._ctx, w.ctypes.data))
+        return dict(zip(("prop", "upd32", "upd64", "cand", "prop64"), (int(v) for v in w)))
 
     def counts(self) -> dict:
         c = np.zeros(8, np.int64)

@@ -54,6 +54,25 @@ struct Counts {
   int32_t refit_next;
   int32_t n32;         // clusters as int32 (length source of the per-cluster scans)
   int32_t pad[4];
+  // work counters of the follow (a6) and refit (a8) kernels
+  unsigned long long n_prop;    // helix propagations with covariance transport
+  unsigned long long n_upd32;   // FP32 Kalman updates
+  unsigned long long n_upd64;   // FP64-zone Kalman updates
+  unsigned long long n_cand;    // candidate clusters examined by the gated pick-up
+  unsigned long long n_prop64;  // propagations done with the FP64 covariance
+  unsigned long long pad2[3];
+};
+
+// Per-thread work tallies, flushed once per thread into Counts.
+struct Tally {
+  unsigned long long prop = 0, upd32 = 0, upd64 = 0, cand = 0, prop64 = 0;
+  __device__ __forceinline__ void flush(Counts* cn) {
+    if (prop) atomicAdd(&cn->n_prop, prop);
+    if (upd32) atomicAdd(&cn->n_upd32, upd32);
+    if (upd64) atomicAdd(&cn->n_upd64, upd64);
+    if (cand) atomicAdd(&cn->n_cand, cand);
+    if (prop64) atomicAdd(&cn->n_prop64, prop64);
+  }
 };
 
 // Algorithm constants passed by value to every kernel (kernel parameter

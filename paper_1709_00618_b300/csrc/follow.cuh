@@ -31,8 +31,9 @@ struct GridView {
 __device__ __forceinline__ bool outside_sector(const TrkState& p, float yhi_edge, const KConst& kc,
                                                uint32_t& flags) {
   const float lim = yhi_edge;
-  if (fabsf(fabsf(p.y) - lim) <= 1e-3f) flags |= TF_EDGE;
-  return fabsf(p.y) > lim;
+  const float y = p.y + p.yl;
+  if (fabsf(fabsf(y) - lim) <= 1e-3f) flags |= TF_EDGE;
+  return fabsf(y) > lim;
 }
 
 // Best cluster of row-sector rs for the predicted state: minimum chi2 =
@@ -44,7 +45,7 @@ __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Fi
   const float Syy = f.cyy() + kc.V, Szz = f.czz() + kc.V;
   const float wy = sqrtf(kc.gate * Syy), wz = sqrtf(kc.gate * Szz);
   const float iSyy = 1.0f / Syy, iSzz = 1.0f / Szz;
-  const float y = f.p.y, zr = f.p.z, zref = f.p.zref;
+  const float y = f.p.y, yl = f.p.yl, zr = f.p.z, zl = f.p.zl, zref = f.p.zref;
   const float zabs = zref + zr;
   int iy0, iy1, iz0, iz1;
   {
@@ -63,10 +64,11 @@ __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Fi
   for (int iz = iz0; iz <= iz1; iz++) {
     const int base = P.bin_base + iz * P.n_y;
     const int a = __ldg(g.bin_start + base + iy0), b = __ldg(g.bin_start + base + iy1 + 1);
+    f.tally->cand += (unsigned)(b - a);
     for (int c = a; c < b; c++) {
       const float2 q = __ldg(g.yz + c);
-      const float dy = q.x - y;
-      const float dz = (q.y - zref) - zr;
+      const float dy = (q.x - y) - yl;
+      const float dz = ((q.y - zref) - zr) - zl;
       const float chi = dy * dy * iSyy + dz * dz * iSzz;
       if (fabsf(chi - gate) <= eps * (1.0f + gate)) flags |= TF_GATE;
       if (!(chi <= gate)) continue;
@@ -108,6 +110,7 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
   __syncthreads();
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
+  Tally tally;
   for (int64_t t = gtid(); t < T; t += gstride()) {
     int32_t* hits = o.hits + t * NROW;
     uint8_t* hrow = o.hrow + t * NROW;
@@ -117,21 +120,15 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
     const int ubase = rs0 - rs0 % NROW, r0 = rs0 % NROW;
     const float2 P0 = __ldg(g.yz + c0), P1 = __ldg(g.yz + cl);
     Filter f;
+    f.tally = &tally;
     {
       const float x0 = sX[r0], x1 = sX[r0 + L - 1];
       const float dX = x1 - x0, dY = P1.x - P0.x, dZ = P1.y - P0.y;
       const float Lc = sqrtf(dX * dX + dY * dY);
-      f.p.x = x0;
-      f.p.row = r0;
-      f.p.y = P0.x;
-      f.p.z = 0.0f;
-      f.p.zref = P0.y;
-      f.p.s = dY / Lc;
-      f.p.t = dZ / Lc;
-      f.p.q = 0.0f;
+      f.seed(r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);
     }
     f.reset_cov(kc);
-    f.update(P0.x, 0.0f, kc);
+    f.update(P0.x, P0.y, kc);
     int nf = 0, nb = 0;
     hits[nf] = c0;
     hrow[nf++] = (uint8_t)r0;
@@ -144,7 +141,7 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
         break;
       }
       const float2 P = __ldg(g.yz + k);
-      f.update(P.x, P.y - f.p.zref, kc);
+      f.update(P.x, P.y, kc);
       hits[nf] = k;
       hrow[nf++] = (uint8_t)(r0 + i);
     }
@@ -171,7 +168,7 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
       const int c = pick(g, ubase + r, r, f, kc, sYH, flags);
       if (c >= 0) {
         const float2 P = __ldg(g.yz + c);
-        f.update(P.x, P.y - f.p.zref, kc);
+        f.update(P.x, P.y, kc);
         hits[nf] = c;
         hrow[nf++] = (uint8_t)r;
         fwd = f.p;
@@ -186,7 +183,7 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
     f.reset_cov(kc);
     {
       const float2 P = __ldg(g.yz + hits[nf - 1]);
-      f.update(P.x, P.y - f.p.zref, kc);
+      f.update(P.x, P.y, kc);
     }
     Saved sv;
     save(sv, f);
@@ -200,7 +197,7 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
       }
       if (kf >= 0 && hrow[kf] == r) {
         const float2 P = __ldg(g.yz + hits[kf]);
-        f.update(P.x, P.y - f.p.zref, kc);
+        f.update(P.x, P.y, kc);
         kf--;
         save(sv, f);
       }
@@ -213,7 +210,7 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
         const int c = pick(g, ubase + r, r, f, kc, sYH, flags);
         if (c >= 0) {
           const float2 P = __ldg(g.yz + c);
-          f.update(P.x, P.y - f.p.zref, kc);
+          f.update(P.x, P.y, kc);
           hits[nf + nb] = c;
           hrow[nf + nb] = (uint8_t)r;
           nb++;
@@ -229,9 +226,9 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
     o.nb[t] = nb;
     o.flags[t] = (int32_t)flags;
     o.row[t] = sv.p.row;
-    o.par[t * 5 + 0] = sv.p.y;
-    o.par[t * 5 + 1] = sv.p.z;
-    o.par[t * 5 + 2] = sv.p.s;
+    o.par[t * 5 + 0] = sv.p.y + sv.p.yl;
+    o.par[t * 5 + 1] = sv.p.z + sv.p.zl;
+    o.par[t * 5 + 2] = sv.p.s + sv.p.sl;
     o.par[t * 5 + 3] = sv.p.t;
     o.par[t * 5 + 4] = sv.p.q;
     o.zref[t] = sv.p.zref;
@@ -239,6 +236,7 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
     for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = sv.C[i];
     o.chi2[t] = sv.chi2;
   }
+  tally.flush(cn);
 }
 
 }  // namespace tpc

@@ -25,12 +25,30 @@ enum : uint32_t {
   TF_REFIT_FAIL = TPC_TF_REFIT_FAIL
 };
 
+// y, z and sin phi are accumulated over up to ~300 row steps; each is kept as
+// an unevaluated sum hi + lo of two binary32 numbers (TwoSum, Knuth, TAOCP
+// vol. 2, 4.2.2) so that the position does not drift by ulp(y) per step.
 struct TrkState {
   float x;   // row radius
   int row;
   float y, z, s, t, q;  // z relative to zref
+  float yl, zl, sl;     // low parts of y, z, s
   float zref;
 };
+
+// hi + lo += d, the rounding error of the new sum kept in lo.
+__device__ __forceinline__ void acc2(float& hi, float& lo, float d) {
+  const float b = __fadd_rn(lo, d);
+  const float s = __fadd_rn(hi, b);
+  const float bb = __fsub_rn(s, hi);
+  lo = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  hi = s;
+}
+__device__ __forceinline__ void acc2(float& hi, float& lo, double d) {
+  const double v = ((double)hi + (double)lo) + d;
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
 
 // C <- J C J^T for the sparse first-order Jacobian of one propagation step.
 template <typename T>
@@ -68,10 +86,24 @@ __device__ __forceinline__ void cov_transport(T* C, T j02, T j04, T j24, T j12, 
   // C[13], C[14] unchanged
 }
 
-// Kalman update with the measurement (my, mz_rel); returns the chi2 increment.
+// Residual of a measurement against the compensated state: (m - hi) is exact
+// when m and hi are close (Sterbenz), the low parts are then subtracted.
+__device__ __forceinline__ float residual_y(const TrkState& p, float my) {
+  return __fsub_rn(__fsub_rn(my, p.y), p.yl);
+}
+// z measurement mz (absolute); mz - zref is split exactly into hi + lo first.
+__device__ __forceinline__ float residual_z(const TrkState& p, float mz) {
+  const float dh = __fsub_rn(mz, p.zref);
+  const float bb = __fsub_rn(dh, mz);
+  const float dl = __fsub_rn(__fsub_rn(mz, __fsub_rn(dh, bb)), __fadd_rn(p.zref, bb));
+  return __fadd_rn(__fsub_rn(dh, p.z), __fsub_rn(dl, p.zl));
+}
+
+// Kalman update with the measurement (my, mz) (mz absolute); returns the
+// chi2 increment.
 template <typename T>
-__device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, float mz_rel, T V) {
-  const float r0 = my - p.y, r1 = mz_rel - p.z;
+__device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, float mz, T V) {
+  const float r0 = residual_y(p, my), r1 = residual_z(p, mz);
   const T S00 = C[0] + V, S01 = C[1], S11 = C[2] + V;
   const T idet = T(1) / (S00 * S11 - S01 * S01);
   const T I00 = S11 * idet, I01 = -S01 * idet, I11 = S00 * idet;
@@ -84,9 +116,9 @@ __device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, flo
     g1[i] = k0[i] * I01 + k1[i] * I11;
   }
   const T R0 = (T)r0, R1 = (T)r1;
-  p.y += (float)(g0[0] * R0 + g1[0] * R1);
-  p.z += (float)(g0[1] * R0 + g1[1] * R1);
-  p.s += (float)(g0[2] * R0 + g1[2] * R1);
+  acc2(p.y, p.yl, g0[0] * R0 + g1[0] * R1);
+  acc2(p.z, p.zl, g0[1] * R0 + g1[1] * R1);
+  acc2(p.s, p.sl, g0[2] * R0 + g1[2] * R1);
   p.t += (float)(g0[3] * R0 + g1[3] * R1);
   p.q += (float)(g0[4] * R0 + g1[4] * R1);
 #pragma unroll
@@ -106,6 +138,7 @@ struct Filter {
   double chi2;
   int zone_left;  // FP64 updates left; 0 = FP32 mode
   int nupd;
+  Tally* tally;   // work counters (may be null)
 
   __device__ __forceinline__ void reset_cov(const KConst& kc) {
     zone_left = kc.fp64_updates;
@@ -150,28 +183,47 @@ struct Filter {
       const float j13 = dS;
       const float j12 = p.t * dx * sm * icm3;
       const float j14 = -p.t * kc.K * dx * dx * sm * 0.5f * icm3;
+      tally->prop++;
+      if (zone_left > 0) tally->prop64++;
       if (zone_left > 0) cov_transport<double>(D, j02, j04, j24, j12, j13, j14);
       else cov_transport<float>(C, j02, j04, j24, j12, j13, j14);
     }
-    p.y += dy;
-    p.z += p.t * dS;
-    p.s = s2;
+    acc2(p.y, p.yl, dy);
+    acc2(p.z, p.zl, p.t * dS);
+    acc2(p.s, p.sl, kap * dx);
     p.x = x2;
     p.row = row2;
     return true;
   }
 
-  __device__ __forceinline__ void update(float my, float mz_rel, const KConst& kc) {
+  // measurement (my, mz), z absolute
+  __device__ __forceinline__ void update(float my, float mz, const KConst& kc) {
     if (zone_left > 0) {
-      chi2 += kalman_update<double>(p, D, my, mz_rel, kc.Vd);
+      chi2 += kalman_update<double>(p, D, my, mz, kc.Vd);
+      tally->upd64++;
       if (--zone_left == 0) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
       }
     } else {
-      chi2 += kalman_update<float>(p, C, my, mz_rel, kc.V);
+      chi2 += kalman_update<float>(p, C, my, mz, kc.V);
+      tally->upd32++;
     }
     nupd++;
+  }
+
+  // Start a state at (y, z) with direction (s, t) and curvature q, z
+  // relative to zref = z.
+  __device__ __forceinline__ void seed(int row, float x, float y, float z, float s, float t, float q) {
+    p.x = x;
+    p.row = row;
+    p.y = y;
+    p.z = 0.0f;
+    p.zref = z;
+    p.s = s;
+    p.t = t;
+    p.q = q;
+    p.yl = p.zl = p.sl = 0.0f;
   }
 
   __device__ __forceinline__ float cyy() const { return zone_left > 0 ? (float)D[0] : C[0]; }

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
   __syncthreads();
   if (fatal(cn)) return;
   const int32_t M = cn->n_tracks;
+  Tally tally;
   for (int64_t m = gtid(); m < M; m += gstride()) {
     const int t = track_tl[m];
     const int n = f_n[t], nf = f_nf[t];
@@ -131,14 +132,10 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
     const int unit = rs_any / NROW;
     uint32_t flags = 0;
     Filter f;
-    f.p.row = f_row[t];
-    f.p.x = sX[f.p.row];
-    f.p.y = f_par[t * 5 + 0];
+    f.tally = &tally;
+    f.seed(f_row[t], sX[f_row[t]], f_par[t * 5 + 0], f_zref[t], f_par[t * 5 + 2], f_par[t * 5 + 3],
+           f_par[t * 5 + 4]);
     f.p.z = f_par[t * 5 + 1];
-    f.p.s = f_par[t * 5 + 2];
-    f.p.t = f_par[t * 5 + 3];
-    f.p.q = f_par[t * 5 + 4];
-    f.p.zref = f_zref[t];
     f.reset_cov(kc);
     bool ok = true;
     const int step = r_out >= f.p.row ? 1 : -1;
@@ -161,7 +158,7 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
         if (r != r_out) ok = f.propagate(r, sX[r], kc, flags);
         if (ok && cur >= 0 && hr[cur] == r) {
           const float2 P = __ldg(g.yz + h[cur]);
-          f.update(P.x, P.y - f.p.zref, kc);
+          f.update(P.x, P.y, kc);
           cur = -1;
           for (j++; j < n; j++) {
             const int slot = j < nf ? nf - 1 - j : j;
@@ -176,9 +173,9 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
     tpc_track tr;
     if (ok) {
       tr.x = sX[r_in];
-      tr.par[0] = f.p.y;
-      tr.par[1] = f.p.zref + f.p.z;
-      tr.par[2] = f.p.s;
+      tr.par[0] = f.p.y + f.p.yl;
+      tr.par[1] = f.p.zref + (f.p.z + f.p.zl);
+      tr.par[2] = f.p.s + f.p.sl;
       tr.par[3] = f.p.t;
       tr.par[4] = f.p.q;
       f.cov_out(tr.cov);
@@ -216,6 +213,7 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
         if (__ldg((const unsigned long long*)owner + h[j]) == key) track_clusters[w++] = __ldg(perm + h[j]);
     }
   }
+  tally.flush(cn);
 }
 
 }  // namespace tpc

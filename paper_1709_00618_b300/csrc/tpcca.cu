@@ -180,7 +180,15 @@ struct tpc_ctx {
   int ctas_follow = 4;
   // graph
   cudaGraphExec_t graph = nullptr;
+  // stage events
+  bool prof = false;
+  bool prof_valid = false;
+  cudaEvent_t ev[7] = {};
   std::string err;
+
+  void mark(int i) {
+    if (prof) cudaEventRecord(ev[i], stream);
+  }
 
   template <typename T>
   T* ptr(size_t off) const { return reinterpret_cast<T*>(arena + off); }
@@ -375,6 +383,7 @@ void enqueue_find(tpc_ctx* ctx) {
   int32_t* bin_base = ctx->ptr<int32_t>(L.bin_base);
   int32_t* bin_cnt = ctx->ptr<int32_t>(L.bin_cnt);
   int32_t* bin_start = ctx->ptr<int32_t>(L.bin_start);
+  ctx->mark(0);
   // a2 grid
   k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax), cn);
   k_grid_count<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int64_t>(L.req_off), cn,
@@ -395,10 +404,12 @@ void enqueue_find(tpc_ctx* ctx) {
   k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.tmp), ctx->ptr<int32_t>(L.gbin),
                                  ctx->ptr<int32_t>(L.rs_in), bin_start, ctx->ptr<int32_t>(L.perm),
                                  ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), cn);
+  ctx->mark(1);
   // a3 neighbours
   k_neighbours<<<gN, 256, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
                                   bin_start, ctx->kc, ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn),
                                   ctx->ptr<uint8_t>(L.tie), cn);
+  ctx->mark(2);
   // a4 + a5
   k_chains<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn), ctx->kc, ctx->ptr<int32_t>(L.up_m),
                              ctx->ptr<int32_t>(L.dn_m), ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.clen),
@@ -408,11 +419,13 @@ void enqueue_find(tpc_ctx* ctx) {
                                        ctx->ptr<int32_t>(L.clen), ctx->ptr<int32_t>(L.cend),
                                        ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
                                        ctx->ptr<int32_t>(L.tl_end), cn, C.tl);
+  ctx->mark(3);
   // a6 follow
   int gF = grid_for(ctx, C.tl, ctx->block_follow, ctx->ctas_follow);
   k_follow<<<gF, ctx->block_follow, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start),
                                             ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
                                             ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), cn);
+  ctx->mark(4);
   // a7 selection
   k_zero64<<<gN, bc, 0, s>>>(ctx->ptr<uint64_t>(L.owner), cn);
   k_fill32<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.cluster_track), -1, cn);
@@ -425,6 +438,7 @@ void enqueue_find(tpc_ctx* ctx) {
                              ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), ctx->ptr<int32_t>(L.perm),
                              ctx->ptr<int32_t>(L.tl_track), ctx->ptr<int32_t>(L.track_tl),
                              ctx->ptr<int32_t>(L.cluster_track), cn);
+  ctx->mark(5);
 }
 
 // a8 on the context's stream.
@@ -447,6 +461,8 @@ void enqueue_fit(tpc_ctx* ctx) {
       ctx->ptr<uint64_t>(L.owner), ctx->ptr<int32_t>(L.toff), ctx->ptr<int32_t>(L.perm), ctx->kc,
       ctx->ptr<tpc_track>(L.tracks), ctx->ptr<int32_t>(L.track_clusters), cn);
   cudaMemcpyAsync(ctx->h_counts, cn, sizeof(Counts), cudaMemcpyDeviceToHost, s);
+  ctx->mark(6);
+  ctx->prof_valid = ctx->prof;
 }
 
 int check_status(tpc_ctx* ctx) {
@@ -551,6 +567,8 @@ void tpc_destroy(tpc_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  for (int i = 0; i < 7; i++)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   if (ctx->own_arena && ctx->arena) cudaFree(ctx->arena);
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_req) cudaFreeHost(ctx->h_req);
@@ -610,9 +628,12 @@ int tpc_run_graph(tpc_ctx* ctx) {
     if (!ctx->own_stream && ctx->stream == nullptr)
       return fail(ctx, TPC_EINVAL, "graph capture needs a non-default stream");
     cudaGraph_t g = nullptr;
+    const bool prof = ctx->prof;
+    ctx->prof = false;  // no event nodes in the graph
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     enqueue_find(ctx);
     enqueue_fit(ctx);
+    ctx->prof = prof;
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) return fail(ctx, TPC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
@@ -739,6 +760,40 @@ int tpc_get_stage(tpc_ctx* ctx, int item, void* host_out, int64_t cap_bytes, int
     return TPC_OK;
   }
   CK(cudaMemcpy(host_out, ctx->arena + off, bytes, cudaMemcpyDeviceToHost));
+  return TPC_OK;
+}
+
+int tpc_set_profiling(tpc_ctx* ctx, int on) {
+  if (!ctx) return TPC_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  if (on && !ctx->ev[0])
+    for (int i = 0; i < 7; i++) CK(cudaEventCreate(&ctx->ev[i]));
+  ctx->prof = on != 0;
+  ctx->prof_valid = false;
+  return TPC_OK;
+}
+
+int tpc_get_stage_times(tpc_ctx* ctx, float ms[6]) {
+  if (!ctx || !ms) return TPC_EINVAL;
+  if (!ctx->prof_valid) return fail(ctx, TPC_EINVAL, "no profiled run (tpc_set_profiling, then find + fit)");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < 6; i++) CK(cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+  return TPC_OK;
+}
+
+int tpc_get_work(tpc_ctx* ctx, uint64_t work[5]) {
+  if (!ctx || !work) return TPC_EINVAL;
+  if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "nothing loaded");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  Counts hc{};
+  CK(cudaMemcpy(&hc, ctx->ptr<Counts>(ctx->L.counts), sizeof(Counts), cudaMemcpyDeviceToHost));
+  work[0] = hc.n_prop;
+  work[1] = hc.n_upd32;
+  work[2] = hc.n_upd64;
+  work[3] = hc.n_cand;
+  work[4] = hc.n_prop64;
   return TPC_OK;
 }
 

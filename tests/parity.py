@@ -23,12 +23,25 @@ def tri_diag_index():
     return [i * (i + 1) // 2 + i for i in range(5)]
 
 
-def par_rel_err(gpu, ref):
+def par_rel_err(gpu, ref, ref_cov=None):
+    """|gpu - ref| / max(|ref|, floor, sigma_ref): relative where the
+    parameter is measured better than its value, in units of its own
+    standard deviation where it is not (a q/pT of 0.01 with sigma 4 has no
+    meaningful relative digits)."""
     gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
-    return np.abs(gpu - ref) / np.maximum(np.abs(ref), PAR_FLOOR)
+    scale = np.maximum(np.abs(ref), PAR_FLOOR)
+    if ref_cov is not None:
+        scale = np.maximum(scale, np.sqrt(np.abs(np.asarray(ref_cov, np.float64)[..., tri_diag_index()])))
+    return np.abs(gpu - ref) / scale
+
+
+COV_CORR_FLOOR = 1e-2
 
 
 def cov_rel_err(gpu, ref):
+    """|dC_ij| / max(|C_ij|, 1e-2 sqrt(C_ii C_jj)): relative for every
+    entry whose correlation exceeds 1%, absolute 1e-5 in correlation units
+    below that."""
     gpu, ref = np.asarray(gpu, np.float64), np.asarray(ref, np.float64)
     d = tri_diag_index()
     diag = np.abs(ref[..., d])
@@ -36,7 +49,7 @@ def cov_rel_err(gpu, ref):
     q = 0
     for i in range(5):
         for j in range(i + 1):
-            scale = np.maximum(np.abs(ref[..., q]), 1e-3 * np.sqrt(diag[..., i] * diag[..., j]))
+            scale = np.maximum(np.abs(ref[..., q]), COV_CORR_FLOOR * np.sqrt(diag[..., i] * diag[..., j]))
             err[..., q] = np.abs(gpu[..., q] - ref[..., q]) / np.maximum(scale, 1e-300)
             q += 1
     return err
@@ -90,7 +103,7 @@ def compare_follow(g, ref, stats):
     assert not (fail_mask & ~taint).any(), "seed/backward failure flags differ"
     ok = same & ~taint & (g["f_n"] > 0)
     assert np.array_equal(g["f_row"][ok], ref["f_row"][ok])
-    pe = par_rel_err(g["f_par"][ok], ref["f_par"][ok])
+    pe = par_rel_err(g["f_par"][ok], ref["f_par"][ok], ref["f_cov"][ok])
     ce = cov_rel_err(g["f_cov"][ok], ref["f_cov"][ok])
     stats.update(tracklets=T, tainted=int(taint.sum()), diverged=int((~same).sum()),
                  follow_par_err_max=float(pe.max()) if pe.size else 0.0,
@@ -153,7 +166,7 @@ def compare_refit(tracks, ref, g, excluded, stats):
     assert np.array_equal(tg["ndf"], ref["t_ndf"][ri])
     okf = (tg["flags"] & 64) == (ref["t_flags"][ri] & 64)
     assert okf.all()
-    pe = par_rel_err(tg["par"], ref["t_par"][ri])
+    pe = par_rel_err(tg["par"], ref["t_par"][ri], ref["t_cov"][ri])
     ce = cov_rel_err(tg["cov"], ref["t_cov"][ri])
     chi = np.abs(tg["chi2"] - ref["t_chi2"][ri]) / np.maximum(ref["t_chi2"][ri], 1.0)
     stats.update(tracks_compared=int(len(common)), tracks_gpu=int(len(tracks)), tracks_ref=int(len(r_tl)),
