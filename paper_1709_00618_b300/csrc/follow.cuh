@@ -2,6 +2,13 @@
 // registers.  Seed from the chain chord, forward pass over the chain and
 // outward with gated pick-up, fresh backward pass refitting the forward
 // clusters and extending inward.
+//
+// Each pass runs as two loops: the first `fp64_updates` Kalman updates with
+// the covariance in FP64, then the rest in FP32.  A warp therefore never
+// mixes lanes in the two precisions (FP64 issues at 1/64 of the FP32 rate on
+// this part, so a mixed warp pays the FP64 path for every straggler), and
+// the lanes of a warp -- consecutive tracklets, which start on neighbouring
+// rows -- stay in the same phase.
 #pragma once
 #include "kalman.cuh"
 
@@ -28,47 +35,48 @@ struct GridView {
   const int32_t* bin_start;
 };
 
-__device__ __forceinline__ bool outside_sector(const TrkState& p, float yhi_edge, const KConst& kc,
-                                               uint32_t& flags) {
-  const float lim = yhi_edge;
+__device__ __forceinline__ bool outside_sector(const TrkState& p, const KConst& kc, uint32_t& flags) {
+  const float lim = p.x * 0.17632698070846498f + kc.edge;
   const float y = p.y + p.yl;
   if (fabsf(fabsf(y) - lim) <= 1e-3f) flags |= TF_EDGE;
   return fabsf(y) > lim;
 }
 
+// Index range of the bins of one row-sector axis covering [v - w, v + w];
+// the window is widened by a margin far above the binary32 rounding of its
+// edges, and the caller applies the exact test to every candidate.
+__device__ __forceinline__ void axis_range(float v, float w, float lo, float inv, int nb, int& i0, int& i1) {
+  const float m = w + 1e-3f + 2e-6f * fabsf(v);
+  const float f0 = floorf((v - m - lo) * inv), f1 = floorf((v + m - lo) * inv);
+  const float top = (float)(nb - 1);
+  i0 = !(f0 >= 0.0f) ? 0 : (f0 > top ? nb - 1 : (int)f0);
+  i1 = !(f1 >= 0.0f) ? 0 : (f1 > top ? nb - 1 : (int)f1);
+}
+
 // Best cluster of row-sector rs for the predicted state: minimum chi2 =
 // dy^2/Syy + dz^2/Szz within the gate, ties to the lower sorted index.
-__device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Filter& f, const KConst& kc,
-                                    const float* sYH, uint32_t& flags) {
+// Near-ties and near-gate candidates raise the taint flags.
+__device__ __forceinline__ int pick(const GridView& g, int rs, int row, const TrkState& p, float cyy, float czz,
+                                    const KConst& kc, const float* sYH, uint32_t& flags, unsigned& ncand) {
   const RsParams P = load_params(g.par + rs);
   if (P.count == 0) return -1;
-  const float Syy = f.cyy() + kc.V, Szz = f.czz() + kc.V;
+  const float Syy = cyy + kc.V, Szz = czz + kc.V;
   const float wy = sqrtf(kc.gate * Syy), wz = sqrtf(kc.gate * Szz);
   const float iSyy = 1.0f / Syy, iSzz = 1.0f / Szz;
-  const float y = f.p.y, yl = f.p.yl, zr = f.p.z, zl = f.p.zl, zref = f.p.zref;
-  const float zabs = zref + zr;
   int iy0, iy1, iz0, iz1;
-  {
-    const float yl = -sYH[row];
-    float a0 = floorf((y - wy - yl) * P.inv_y) - 1.0f, a1 = floorf((y + wy - yl) * P.inv_y) + 1.0f;
-    float b0 = floorf((zabs - wz - P.z_lo) * P.inv_z) - 1.0f, b1 = floorf((zabs + wz - P.z_lo) * P.inv_z) + 1.0f;
-    const float ty = (float)(P.n_y - 1), tz = (float)(P.n_z - 1);
-    iy0 = !(a0 >= 0.0f) ? 0 : (a0 > ty ? P.n_y - 1 : (int)a0);
-    iy1 = !(a1 >= 0.0f) ? 0 : (a1 > ty ? P.n_y - 1 : (int)a1);
-    iz0 = !(b0 >= 0.0f) ? 0 : (b0 > tz ? P.n_z - 1 : (int)b0);
-    iz1 = !(b1 >= 0.0f) ? 0 : (b1 > tz ? P.n_z - 1 : (int)b1);
-  }
+  axis_range(p.y + p.yl, wy, -sYH[row], P.inv_y, P.n_y, iy0, iy1);
+  axis_range(p.zref + (p.z + p.zl), wz, P.z_lo, P.inv_z, P.n_z, iz0, iz1);
   const float gate = kc.gate, eps = kc.taint;
   float b1v = __int_as_float(0x7F800000), b2v = b1v;
   int best = -1;
   for (int iz = iz0; iz <= iz1; iz++) {
     const int base = P.bin_base + iz * P.n_y;
     const int a = __ldg(g.bin_start + base + iy0), b = __ldg(g.bin_start + base + iy1 + 1);
-    f.tally->cand += (unsigned)(b - a);
+    ncand += (unsigned)(b - a);
     for (int c = a; c < b; c++) {
       const float2 q = __ldg(g.yz + c);
-      const float dy = (q.x - y) - yl;
-      const float dz = ((q.y - zref) - zr) - zl;
+      const float dy = (q.x - p.y) - p.yl;
+      const float dz = ((q.y - p.zref) - p.z) - p.zl;
       const float chi = dy * dy * iSyy + dz * dz * iSzz;
       if (fabsf(chi - gate) <= eps * (1.0f + gate)) flags |= TF_GATE;
       if (!(chi <= gate)) continue;
@@ -85,16 +93,102 @@ __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Fi
   return best;
 }
 
-struct Saved {
-  TrkState p;
-  float C[15];
-  double chi2;
+// Per-lane bookkeeping of one tracklet.
+struct Lane {
+  int32_t* hits;
+  uint8_t* hrow;
+  int ubase, r0, L;
+  int nf, nb;
+  int k;        // current chain cluster (forward)
+  int i;        // next chain index (forward)
+  int r_last;   // row of the last forward update
+  int kf;       // next forward hit to refit (backward)
+  int misses;
+  int nupd;     // updates since the last (re)seed
+  uint32_t flags;
+  bool seed_fail;
+  TrkState fwd;  // forward state after its last update
+  // backward output: state after the last update
+  TrkState sp;
+  float sC[15];
+  double schi2;
 };
 
-__device__ __forceinline__ void save(Saved& s, const Filter& f) {
-  s.p = f.p;
-  f.cov_out(s.C);
-  s.chi2 = f.chi2;
+template <typename T>
+__device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, const T* C, double chi2) {
+  w.sp = p;
+#pragma unroll
+  for (int i = 0; i < 15; i++) w.sC[i] = (float)C[i];
+  w.schi2 = chi2;
+}
+
+// One forward row step in covariance precision T; false ends the pass.
+template <typename T>
+__device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __restrict__ up_m, const KConst& kc,
+                                         const float* sX, const float* sYH, Lane& w, TrkState& p, T* C,
+                                         double& chi2, LocalTally& tl) {
+  const int r = p.row + 1;
+  if (r >= NROW) return false;
+  const bool chain = w.i < w.L;
+  if (!propagate<T>(p, C, r, sX[r], kc, w.flags)) {
+    if (chain) w.seed_fail = true;
+    return false;
+  }
+  tl.on_prop<T>();
+  int c;
+  if (chain) {
+    w.k = __ldg(up_m + w.k);
+    w.i++;
+    c = w.k;
+  } else {
+    if (outside_sector(p, kc, w.flags)) return false;
+    c = pick(g, w.ubase + r, r, p, (float)C[0], (float)C[2], kc, sYH, w.flags, tl.cand);
+    if (c < 0) return ++w.misses < kc.max_miss;
+  }
+  const float2 P = __ldg(g.yz + c);
+  chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
+  tl.on_upd<T>();
+  w.nupd++;
+  w.hits[w.nf] = c;
+  w.hrow[w.nf] = (uint8_t)r;
+  w.nf++;
+  w.fwd = p;
+  w.r_last = r;
+  w.misses = 0;
+  return true;
+}
+
+// One backward row step in covariance precision T; false ends the pass.
+template <typename T>
+__device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, const float* sX, const float* sYH,
+                                         Lane& w, TrkState& p, T* C, double& chi2, LocalTally& tl) {
+  const int r = p.row - 1;
+  if (r < 0) return false;
+  if (!propagate<T>(p, C, r, sX[r], kc, w.flags)) {
+    if (r >= w.r0) w.flags |= TF_BACK_FAIL;
+    return false;
+  }
+  tl.on_prop<T>();
+  int c;
+  if (r >= w.r0) {
+    if (!(w.kf >= 0 && w.hrow[w.kf] == r)) return true;
+    c = w.hits[w.kf];
+    w.kf--;
+  } else {
+    if (outside_sector(p, kc, w.flags)) return false;
+    c = pick(g, w.ubase + r, r, p, (float)C[0], (float)C[2], kc, sYH, w.flags, tl.cand);
+    if (c < 0) return ++w.misses < kc.max_miss;
+    w.hits[w.nf + w.nb] = c;
+    w.hrow[w.nf + w.nb] = (uint8_t)r;
+    w.nb++;
+    w.misses = 0;
+  }
+  const float2 P = __ldg(g.yz + c);
+  chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
+  tl.on_upd<T>();
+  w.nupd++;
+  keep_output<T>(w, p, C, chi2);
+  return true;
 }
 
 __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __restrict__ tl_start,
@@ -110,47 +204,65 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
   __syncthreads();
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
-  Tally tally;
+  const int ZONE = kc.fp64_updates;
+  LocalTally tl;
   for (int64_t t = gtid(); t < T; t += gstride()) {
-    int32_t* hits = o.hits + t * NROW;
-    uint8_t* hrow = o.hrow + t * NROW;
-    uint32_t flags = 0;
-    const int c0 = tl_start[t], L = tl_len[t], cl = tl_end[t];
+    Lane w;
+    w.hits = o.hits + t * NROW;
+    w.hrow = o.hrow + t * NROW;
+    w.flags = 0;
+    w.seed_fail = false;
+    const int c0 = tl_start[t], cl = tl_end[t];
+    w.L = tl_len[t];
     const int rs0 = __ldg(g.rs_of + c0);
-    const int ubase = rs0 - rs0 % NROW, r0 = rs0 % NROW;
+    w.ubase = rs0 - rs0 % NROW;
+    w.r0 = rs0 % NROW;
     const float2 P0 = __ldg(g.yz + c0), P1 = __ldg(g.yz + cl);
-    Filter f;
-    f.tally = &tally;
+    TrkState p;
     {
-      const float x0 = sX[r0], x1 = sX[r0 + L - 1];
+      const float x0 = sX[w.r0], x1 = sX[w.r0 + w.L - 1];
       const float dX = x1 - x0, dY = P1.x - P0.x, dZ = P1.y - P0.y;
       const float Lc = sqrtf(dX * dX + dY * dY);
-      f.seed(r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);
+      seed_state(p, w.r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);
     }
-    f.reset_cov(kc);
-    f.update(P0.x, P0.y, kc);
-    int nf = 0, nb = 0;
-    hits[nf] = c0;
-    hrow[nf++] = (uint8_t)r0;
-    bool seed_ok = true;
-    int k = c0;
-    for (int i = 1; i < L; i++) {
-      k = __ldg(up_m + k);
-      if (!f.propagate(r0 + i, sX[r0 + i], kc, flags)) {
-        seed_ok = false;
-        break;
+    w.nf = w.nb = 0;
+    w.k = c0;
+    w.i = 1;
+    w.misses = 0;
+    w.r_last = w.r0;
+    w.hits[0] = c0;
+    w.hrow[0] = (uint8_t)w.r0;
+    w.nf = 1;
+    double chi2 = 0.0;
+    // ---- forward pass
+    bool go = true;
+    {
+      float C[15];
+      if (ZONE > 0) {
+        double D[15];
+        cov_seed<double>(D, kc);
+        chi2 += kalman_update<double>(p, D, P0.x, P0.y, kc.Vd);
+        tl.on_upd<double>();
+        w.nupd = 1;
+        w.fwd = p;
+        while (go && w.nupd < ZONE) go = fwd_step<double>(g, up_m, kc, sX, sYH, w, p, D, chi2, tl);
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      } else {
+        cov_seed<float>(C, kc);
+        chi2 += kalman_update<float>(p, C, P0.x, P0.y, kc.V);
+        tl.on_upd<float>();
+        w.nupd = 1;
+        w.fwd = p;
       }
-      const float2 P = __ldg(g.yz + k);
-      f.update(P.x, P.y, kc);
-      hits[nf] = k;
-      hrow[nf++] = (uint8_t)(r0 + i);
+      while (go) go = fwd_step<float>(g, up_m, kc, sX, sYH, w, p, C, chi2, tl);
     }
-    if (!seed_ok) {
+    if (w.seed_fail) {
       o.n[t] = 0;
       o.nf[t] = 0;
       o.nb[t] = 0;
-      o.flags[t] = (int32_t)(flags | TF_SEED_FAIL);
-      o.row[t] = r0;
+      o.flags[t] = (int32_t)(w.flags | TF_SEED_FAIL);
+      o.row[t] = w.r0;
 #pragma unroll
       for (int i = 0; i < 5; i++) o.par[t * 5 + i] = 0.0f;
 #pragma unroll
@@ -159,84 +271,50 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
       o.chi2[t] = 0.0;
       continue;
     }
-    // forward extension
-    TrkState fwd = f.p;
-    int r_last = r0 + L - 1, misses = 0;
-    for (int r = r_last + 1; r < NROW; r++) {
-      if (!f.propagate(r, sX[r], kc, flags)) break;
-      if (outside_sector(f.p, f.p.x * 0.17632698070846498f + kc.edge, kc, flags)) break;
-      const int c = pick(g, ubase + r, r, f, kc, sYH, flags);
-      if (c >= 0) {
-        const float2 P = __ldg(g.yz + c);
-        f.update(P.x, P.y, kc);
-        hits[nf] = c;
-        hrow[nf++] = (uint8_t)r;
-        fwd = f.p;
-        r_last = r;
-        misses = 0;
-      } else if (++misses >= kc.max_miss) {
-        break;
-      }
-    }
-    // backward pass: forward state at the outermost cluster, fresh covariance
-    f.p = fwd;
-    f.reset_cov(kc);
+    // ---- backward pass: forward state at the outermost cluster, fresh covariance
+    p = w.fwd;
+    chi2 = 0.0;
+    w.kf = w.nf - 2;
+    w.misses = 0;
+    go = true;
     {
-      const float2 P = __ldg(g.yz + hits[nf - 1]);
-      f.update(P.x, P.y, kc);
-    }
-    Saved sv;
-    save(sv, f);
-    int kf = nf - 2;
-    bool ok = true;
-    for (int r = r_last - 1; r >= r0; r--) {
-      if (!f.propagate(r, sX[r], kc, flags)) {
-        ok = false;
-        flags |= TF_BACK_FAIL;
-        break;
-      }
-      if (kf >= 0 && hrow[kf] == r) {
-        const float2 P = __ldg(g.yz + hits[kf]);
-        f.update(P.x, P.y, kc);
-        kf--;
-        save(sv, f);
-      }
-    }
-    if (ok) {
-      misses = 0;
-      for (int r = r0 - 1; r >= 0; r--) {
-        if (!f.propagate(r, sX[r], kc, flags)) break;
-        if (outside_sector(f.p, f.p.x * 0.17632698070846498f + kc.edge, kc, flags)) break;
-        const int c = pick(g, ubase + r, r, f, kc, sYH, flags);
-        if (c >= 0) {
-          const float2 P = __ldg(g.yz + c);
-          f.update(P.x, P.y, kc);
-          hits[nf + nb] = c;
-          hrow[nf + nb] = (uint8_t)r;
-          nb++;
-          save(sv, f);
-          misses = 0;
-        } else if (++misses >= kc.max_miss) {
-          break;
-        }
-      }
-    }
-    o.n[t] = nf + nb;
-    o.nf[t] = nf;
-    o.nb[t] = nb;
-    o.flags[t] = (int32_t)flags;
-    o.row[t] = sv.p.row;
-    o.par[t * 5 + 0] = sv.p.y + sv.p.yl;
-    o.par[t * 5 + 1] = sv.p.z + sv.p.zl;
-    o.par[t * 5 + 2] = sv.p.s + sv.p.sl;
-    o.par[t * 5 + 3] = sv.p.t;
-    o.par[t * 5 + 4] = sv.p.q;
-    o.zref[t] = sv.p.zref;
+      const float2 P = __ldg(g.yz + w.hits[w.nf - 1]);
+      float C[15];
+      if (ZONE > 0) {
+        double D[15];
+        cov_seed<double>(D, kc);
+        chi2 += kalman_update<double>(p, D, P.x, P.y, kc.Vd);
+        tl.on_upd<double>();
+        w.nupd = 1;
+        keep_output<double>(w, p, D, chi2);
+        while (go && w.nupd < ZONE) go = bwd_step<double>(g, kc, sX, sYH, w, p, D, chi2, tl);
 #pragma unroll
-    for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = sv.C[i];
-    o.chi2[t] = sv.chi2;
+        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      } else {
+        cov_seed<float>(C, kc);
+        chi2 += kalman_update<float>(p, C, P.x, P.y, kc.V);
+        tl.on_upd<float>();
+        w.nupd = 1;
+        keep_output<float>(w, p, C, chi2);
+      }
+      while (go) go = bwd_step<float>(g, kc, sX, sYH, w, p, C, chi2, tl);
+    }
+    o.n[t] = w.nf + w.nb;
+    o.nf[t] = w.nf;
+    o.nb[t] = w.nb;
+    o.flags[t] = (int32_t)w.flags;
+    o.row[t] = w.sp.row;
+    o.par[t * 5 + 0] = w.sp.y + w.sp.yl;
+    o.par[t * 5 + 1] = w.sp.z + w.sp.zl;
+    o.par[t * 5 + 2] = w.sp.s + w.sp.sl;
+    o.par[t * 5 + 3] = w.sp.t;
+    o.par[t * 5 + 4] = w.sp.q;
+    o.zref[t] = w.sp.zref;
+#pragma unroll
+    for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = w.sC[i];
+    o.chi2[t] = w.schi2;
   }
-  tally.flush(cn);
+  tl.flush(cn);
 }
 
 }  // namespace tpc

@@ -129,108 +129,107 @@ __device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, flo
   return d0 * ((double)I00 * d0 + (double)I01 * d1) + d1 * ((double)I01 * d0 + (double)I11 * d1);
 }
 
-// The filter: state, covariance in FP64 during the zone after a seed, FP32
-// afterwards; chi2 in FP64.
-struct Filter {
-  TrkState p;
-  float C[15];
-  double D[15];
-  double chi2;
-  int zone_left;  // FP64 updates left; 0 = FP32 mode
-  int nupd;
-  Tally* tally;   // work counters (may be null)
+// Propagation of the state to row2 at radius x2.  Returns false when
+// |sin phi| reaches s_max; otherwise fills the non-identity entries of the
+// first-order Jacobian (J[y,s], J[y,q], J[s,q], J[z,s], J[z,t], J[z,q]).
+struct Jac {
+  float j02, j04, j24, j12, j13, j14;
+};
 
-  __device__ __forceinline__ void reset_cov(const KConst& kc) {
-    zone_left = kc.fp64_updates;
-#pragma unroll
-    for (int i = 0; i < 15; i++) {
-      C[i] = 0.0f;
-      D[i] = 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < 5; i++) {
-      C[TPC_CI(i, i)] = kc.c0[i];
-      D[TPC_CI(i, i)] = (double)kc.c0[i];
-    }
-    chi2 = 0.0;
-    nupd = 0;
+__device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, const KConst& kc, uint32_t& flags,
+                                           Jac* J) {
+  const float dx = x2 - p.x;
+  const float kap = -kc.K * p.q;
+  const float s1 = p.s, s2 = s1 + kap * dx;
+  if (fabsf(fabsf(s1) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
+  if (!(fabsf(s1) < kc.s_max && fabsf(s2) < kc.s_max)) return false;
+  const float c1 = sqrtf(1.0f - s1 * s1), c2 = sqrtf(1.0f - s2 * s2);
+  const float icc = 1.0f / (c1 + c2);
+  const float ss = s1 + s2;
+  const float dy = dx * ss * icc;
+  // arc length: sin(phi2 - phi1) = kap*dx*g with g = c1 + s1 (s1+s2)/(c1+c2),
+  // so dS = dx*g*asin(a)/a, a = kap*dx*g, free of the cancellation of
+  // asin(s2) - asin(s1) in binary32
+  const float g = c1 + s1 * ss * icc;
+  const float a = kap * dx * g;
+  const float dS = dx * g * (a != 0.0f ? asinf(a) / a : 1.0f);
+  if (J) {
+    const float sm = 0.5f * ss, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
+    J->j02 = dx * icm3;
+    J->j04 = -kc.K * dx * dx * 0.5f * icm3;
+    J->j24 = -kc.K * dx;
+    J->j13 = dS;
+    J->j12 = p.t * dx * sm * icm3;
+    J->j14 = -p.t * kc.K * dx * dx * sm * 0.5f * icm3;
   }
+  acc2(p.y, p.yl, dy);
+  acc2(p.z, p.zl, p.t * dS);
+  acc2(p.s, p.sl, kap * dx);
+  p.x = x2;
+  p.row = row2;
+  return true;
+}
 
-  // Propagate to row `row2`; returns false when |sin phi| reaches s_max.
-  // with_cov = false carries only the state.
-  __device__ __forceinline__ bool propagate(int row2, float x2, const KConst& kc, uint32_t& flags,
-                                            bool with_cov = true) {
-    const float dx = x2 - p.x;
-    const float kap = -kc.K * p.q;
-    const float s1 = p.s, s2 = s1 + kap * dx;
-    if (fabsf(fabsf(s1) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
-    if (!(fabsf(s1) < kc.s_max && fabsf(s2) < kc.s_max)) return false;
-    const float c1 = sqrtf(1.0f - s1 * s1), c2 = sqrtf(1.0f - s2 * s2);
-    const float icc = 1.0f / (c1 + c2);
-    const float ss = s1 + s2;
-    const float dy = dx * ss * icc;
-    // arc length: sin(phi2 - phi1) = kap*dx*g with g = c1 + s1 (s1+s2)/(c1+c2),
-    // so dS = dx*g*asin(a)/a, a = kap*dx*g, without the cancellation of
-    // asin(s2) - asin(s1) in binary32
-    const float g = c1 + s1 * ss * icc;
-    const float a = kap * dx * g;
-    const float dS = dx * g * (a != 0.0f ? asinf(a) / a : 1.0f);
-    if (with_cov) {
-      const float sm = 0.5f * ss, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
-      const float j02 = dx * icm3;
-      const float j04 = -kc.K * dx * dx * 0.5f * icm3;
-      const float j24 = -kc.K * dx;
-      const float j13 = dS;
-      const float j12 = p.t * dx * sm * icm3;
-      const float j14 = -p.t * kc.K * dx * dx * sm * 0.5f * icm3;
-      tally->prop++;
-      if (zone_left > 0) tally->prop64++;
-      if (zone_left > 0) cov_transport<double>(D, j02, j04, j24, j12, j13, j14);
-      else cov_transport<float>(C, j02, j04, j24, j12, j13, j14);
-    }
-    acc2(p.y, p.yl, dy);
-    acc2(p.z, p.zl, p.t * dS);
-    acc2(p.s, p.sl, kap * dx);
-    p.x = x2;
-    p.row = row2;
-    return true;
-  }
+// Propagation with covariance transport in precision T.
+template <typename T>
+__device__ __forceinline__ bool propagate(TrkState& p, T* C, int row2, float x2, const KConst& kc, uint32_t& flags) {
+  Jac J;
+  if (!prop_state(p, row2, x2, kc, flags, &J)) return false;
+  cov_transport<T>(C, J.j02, J.j04, J.j24, J.j12, J.j13, J.j14);
+  return true;
+}
 
-  // measurement (my, mz), z absolute
-  __device__ __forceinline__ void update(float my, float mz, const KConst& kc) {
-    if (zone_left > 0) {
-      chi2 += kalman_update<double>(p, D, my, mz, kc.Vd);
-      tally->upd64++;
-      if (--zone_left == 0) {
+template <typename T>
+__device__ __forceinline__ void cov_seed(T* C, const KConst& kc) {
 #pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
-      }
-    } else {
-      chi2 += kalman_update<float>(p, C, my, mz, kc.V);
-      tally->upd32++;
-    }
-    nupd++;
-  }
-
-  // Start a state at (y, z) with direction (s, t) and curvature q, z
-  // relative to zref = z.
-  __device__ __forceinline__ void seed(int row, float x, float y, float z, float s, float t, float q) {
-    p.x = x;
-    p.row = row;
-    p.y = y;
-    p.z = 0.0f;
-    p.zref = z;
-    p.s = s;
-    p.t = t;
-    p.q = q;
-    p.yl = p.zl = p.sl = 0.0f;
-  }
-
-  __device__ __forceinline__ float cyy() const { return zone_left > 0 ? (float)D[0] : C[0]; }
-  __device__ __forceinline__ float czz() const { return zone_left > 0 ? (float)D[2] : C[2]; }
-  __device__ __forceinline__ void cov_out(float* out) const {
+  for (int i = 0; i < 15; i++) C[i] = T(0);
 #pragma unroll
-    for (int i = 0; i < 15; i++) out[i] = zone_left > 0 ? (float)D[i] : C[i];
+  for (int i = 0; i < 5; i++) C[TPC_CI(i, i)] = (T)kc.c0[i];
+}
+
+template <typename T>
+__device__ __forceinline__ T meas_var(const KConst& kc);
+template <>
+__device__ __forceinline__ float meas_var<float>(const KConst& kc) { return kc.V; }
+template <>
+__device__ __forceinline__ double meas_var<double>(const KConst& kc) { return kc.Vd; }
+
+// Start a state at (y, z) with direction (s, t) and curvature q, z kept
+// relative to zref = z.
+__device__ __forceinline__ void seed_state(TrkState& p, int row, float x, float y, float z, float s, float t,
+                                           float q) {
+  p.x = x;
+  p.row = row;
+  p.y = y;
+  p.z = 0.0f;
+  p.zref = z;
+  p.s = s;
+  p.t = t;
+  p.q = q;
+  p.yl = p.zl = p.sl = 0.0f;
+}
+
+// Work tallies kept in registers by one thread.
+struct LocalTally {
+  unsigned prop = 0, prop64 = 0, upd32 = 0, upd64 = 0, cand = 0;
+  template <typename T>
+  __device__ __forceinline__ void on_prop() {
+    prop++;
+    if (sizeof(T) == 8) prop64++;
+  }
+  template <typename T>
+  __device__ __forceinline__ void on_upd() {
+    if (sizeof(T) == 8) upd64++;
+    else upd32++;
+  }
+  __device__ __forceinline__ void flush(Counts* cn) {
+    Tally t;
+    t.prop = prop;
+    t.prop64 = prop64;
+    t.upd32 = upd32;
+    t.upd64 = upd64;
+    t.cand = cand;
+    t.flush(cn);
   }
 };
 

@@ -5,11 +5,12 @@
 
 namespace tpc {
 
-// Bin index range of a row-sector covering [v0, v1], widened by one bin on
-// each side so that rounding of the window edges can never drop a cluster
-// inside it (the caller applies the exact test to every candidate).
+// Bin index range of a row-sector covering [v0, v1], both edges moved out by
+// a margin far above their binary32 rounding so that no cluster inside the
+// window is dropped (the caller applies the exact test to every candidate).
 __device__ __forceinline__ void bin_range(float v0, float v1, float lo, float inv, int nb, int& i0, int& i1) {
-  float f0 = floorf((v0 - lo) * inv) - 1.0f, f1 = floorf((v1 - lo) * inv) + 1.0f;
+  const float m = 1e-3f + 2e-6f * fmaxf(fabsf(v0), fabsf(v1));
+  float f0 = floorf((v0 - m - lo) * inv), f1 = floorf((v1 + m - lo) * inv);
   float top = (float)(nb - 1);
   i0 = !(f0 >= 0.0f) ? 0 : (f0 > top ? nb - 1 : (int)f0);
   i1 = !(f1 >= 0.0f) ? 0 : (f1 > top ? nb - 1 : (int)f1);

@@ -89,7 +89,50 @@ __global__ void k_track_counts(const int32_t* __restrict__ track_tl, const int32
 }
 
 // a8: refit of each kept track over its owned clusters, outermost to
-// innermost, seeded by the follow state carried to the outermost owned row.
+// innermost, seeded by the follow state carried (state only) to the
+// outermost owned row.  The owned hits are visited in update order: forward
+// hits from the last to the first, then the backward-extension hits as
+// stored; rows strictly decrease along it.
+struct RefitLane {
+  const int32_t* h;
+  const uint8_t* hr;
+  int n, nf, j, cur, r_in;
+  uint64_t key;
+  const unsigned long long* owner;
+  __device__ __forceinline__ void advance() {
+    cur = -1;
+    for (; j < n; j++) {
+      const int slot = j < nf ? nf - 1 - j : j;
+      if (__ldg(owner + h[slot]) == key) {
+        cur = slot;
+        return;
+      }
+    }
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, const float* sX, RefitLane& w,
+                                           TrkState& p, T* C, double& chi2, int& nupd, bool& ok, uint32_t& flags,
+                                           LocalTally& tl) {
+  const int r = p.row - 1;
+  if (r < w.r_in) return false;
+  if (!propagate<T>(p, C, r, sX[r], kc, flags)) {
+    ok = false;
+    return false;
+  }
+  tl.on_prop<T>();
+  if (w.cur >= 0 && w.hr[w.cur] == r) {
+    const float2 P = __ldg(g.yz + w.h[w.cur]);
+    chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
+    tl.on_upd<T>();
+    nupd++;
+    w.j++;
+    w.advance();
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __restrict__ track_tl,
                                                const int32_t* __restrict__ f_n, const int32_t* __restrict__ f_nf,
                                                const int32_t* __restrict__ f_row, const int32_t* __restrict__ hits,
@@ -105,82 +148,77 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
   __syncthreads();
   if (fatal(cn)) return;
   const int32_t M = cn->n_tracks;
-  Tally tally;
+  const int ZONE = kc.fp64_updates;
+  LocalTally tl;
   for (int64_t m = gtid(); m < M; m += gstride()) {
     const int t = track_tl[m];
-    const int n = f_n[t], nf = f_nf[t];
-    const uint64_t key = track_key(n, t);
-    const int32_t* h = hits + (int64_t)t * NROW;
-    const uint8_t* hr = hrow + (int64_t)t * NROW;
-    // owned list in update order (outermost first): forward hits descending,
-    // then backward-extension hits in stored (descending-row) order
-    int order_cnt = 0;
-    int r_out = -1, r_in = NROW;
-    for (int i = nf - 1; i >= 0; i--)
-      if (__ldg((const unsigned long long*)owner + h[i]) == key) {
-        r_out = max(r_out, (int)hr[i]);
-        r_in = min(r_in, (int)hr[i]);
-        order_cnt++;
+    RefitLane w;
+    w.n = f_n[t];
+    w.nf = f_nf[t];
+    w.key = track_key(w.n, t);
+    w.h = hits + (int64_t)t * NROW;
+    w.hr = hrow + (int64_t)t * NROW;
+    w.owner = (const unsigned long long*)owner;
+    // owned rows
+    int nown = 0, r_out = -1;
+    w.r_in = NROW;
+    for (int i = 0; i < w.n; i++)
+      if (__ldg(w.owner + w.h[i]) == w.key) {
+        r_out = max(r_out, (int)w.hr[i]);
+        w.r_in = min(w.r_in, (int)w.hr[i]);
+        nown++;
       }
-    for (int i = nf; i < n; i++)
-      if (__ldg((const unsigned long long*)owner + h[i]) == key) {
-        r_out = max(r_out, (int)hr[i]);
-        r_in = min(r_in, (int)hr[i]);
-        order_cnt++;
-      }
-    const int rs_any = __ldg(g.rs_of + h[0]);
-    const int unit = rs_any / NROW;
+    const int unit = __ldg(g.rs_of + w.h[0]) / NROW;
     uint32_t flags = 0;
-    Filter f;
-    f.tally = &tally;
-    f.seed(f_row[t], sX[f_row[t]], f_par[t * 5 + 0], f_zref[t], f_par[t * 5 + 2], f_par[t * 5 + 3],
-           f_par[t * 5 + 4]);
-    f.p.z = f_par[t * 5 + 1];
-    f.reset_cov(kc);
+    TrkState p;
+    seed_state(p, f_row[t], sX[f_row[t]], f_par[t * 5 + 0], f_zref[t], f_par[t * 5 + 2], f_par[t * 5 + 3],
+               f_par[t * 5 + 4]);
+    p.z = f_par[t * 5 + 1];
     bool ok = true;
-    const int step = r_out >= f.p.row ? 1 : -1;
-    for (int r = f.p.row + step; ok && (step > 0 ? r <= r_out : r >= r_out); r += step)
-      ok = f.propagate(r, sX[r], kc, flags, false);
+    const int step = r_out >= p.row ? 1 : -1;
+    for (int r = p.row + step; ok && (step > 0 ? r <= r_out : r >= r_out); r += step)
+      ok = prop_state(p, r, sX[r], kc, flags, nullptr);
+    double chi2 = 0.0;
+    float C[15];
     if (ok) {
-      f.reset_cov(kc);
-      // update order j = 0..n-1 visits slot nf-1-j for j < nf (forward hits,
-      // rows descending) and slot j after that (backward hits, rows
-      // descending); rows strictly decrease along it
-      int j = 0, cur = -1;
-      for (; j < n; j++) {
-        const int slot = j < nf ? nf - 1 - j : j;
-        if (__ldg((const unsigned long long*)owner + h[slot]) == key) {
-          cur = slot;
-          break;
-        }
+      w.j = 0;
+      w.advance();  // the outermost owned hit, on row r_out
+      int nupd = 0;
+      bool go = true;
+      const float2 P = __ldg(g.yz + w.h[w.cur]);
+      if (ZONE > 0) {
+        double D[15];
+        cov_seed<double>(D, kc);
+        chi2 += kalman_update<double>(p, D, P.x, P.y, kc.Vd);
+        tl.on_upd<double>();
+        nupd = 1;
+        w.j++;
+        w.advance();
+        while (go && nupd < ZONE) go = refit_step<double>(g, kc, sX, w, p, D, chi2, nupd, ok, flags, tl);
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      } else {
+        cov_seed<float>(C, kc);
+        chi2 += kalman_update<float>(p, C, P.x, P.y, kc.V);
+        tl.on_upd<float>();
+        nupd = 1;
+        w.j++;
+        w.advance();
       }
-      for (int r = r_out; ok && r >= r_in; r--) {
-        if (r != r_out) ok = f.propagate(r, sX[r], kc, flags);
-        if (ok && cur >= 0 && hr[cur] == r) {
-          const float2 P = __ldg(g.yz + h[cur]);
-          f.update(P.x, P.y, kc);
-          cur = -1;
-          for (j++; j < n; j++) {
-            const int slot = j < nf ? nf - 1 - j : j;
-            if (__ldg((const unsigned long long*)owner + h[slot]) == key) {
-              cur = slot;
-              break;
-            }
-          }
-        }
-      }
+      while (go) go = refit_step<float>(g, kc, sX, w, p, C, chi2, nupd, ok, flags, tl);
     }
     tpc_track tr;
     if (ok) {
-      tr.x = sX[r_in];
-      tr.par[0] = f.p.y + f.p.yl;
-      tr.par[1] = f.p.zref + (f.p.z + f.p.zl);
-      tr.par[2] = f.p.s + f.p.sl;
-      tr.par[3] = f.p.t;
-      tr.par[4] = f.p.q;
-      f.cov_out(tr.cov);
-      tr.chi2 = f.chi2;
-      tr.first_row = r_in;
+      tr.x = sX[w.r_in];
+      tr.par[0] = p.y + p.yl;
+      tr.par[1] = p.zref + (p.z + p.zl);
+      tr.par[2] = p.s + p.sl;
+      tr.par[3] = p.t;
+      tr.par[4] = p.q;
+#pragma unroll
+      for (int j = 0; j < 15; j++) tr.cov[j] = C[j];
+      tr.chi2 = chi2;
+      tr.first_row = w.r_in;
     } else {
       const int fr = f_row[t];
       tr.x = sX[fr];
@@ -195,8 +233,8 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
       flags = TF_REFIT_FAIL;
     }
     tr.reserved = 0;
-    tr.ndf = 2 * order_cnt - 5;
-    tr.n_clusters = order_cnt;
+    tr.ndf = 2 * nown - 5;
+    tr.n_clusters = nown;
     tr.sector = unit % NSEC;
     tr.request = unit / NSEC;
     tr.last_row = r_out;
@@ -206,14 +244,14 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
     // owned clusters in load order, innermost row first: backward list from
     // its end, then forward list from its start
     if (track_clusters) {
-      int w = toff[m];
-      for (int j = n - 1; j >= nf; j--)
-        if (__ldg((const unsigned long long*)owner + h[j]) == key) track_clusters[w++] = __ldg(perm + h[j]);
-      for (int j = 0; j < nf; j++)
-        if (__ldg((const unsigned long long*)owner + h[j]) == key) track_clusters[w++] = __ldg(perm + h[j]);
+      int wpos = toff[m];
+      for (int j = w.n - 1; j >= w.nf; j--)
+        if (__ldg(w.owner + w.h[j]) == w.key) track_clusters[wpos++] = __ldg(perm + w.h[j]);
+      for (int j = 0; j < w.nf; j++)
+        if (__ldg(w.owner + w.h[j]) == w.key) track_clusters[wpos++] = __ldg(perm + w.h[j]);
     }
   }
-  tally.flush(cn);
+  tl.flush(cn);
 }
 
 }  // namespace tpc
