@@ -211,6 +211,16 @@ int tpc_get_stage_times(tpc_ctx *ctx, float ms[6]);
  * the FP64 covariance. */
 int tpc_get_work(tpc_ctx *ctx, uint64_t work[5]);
 
+/* Debug trace of one tracklet's Kalman updates (a6): after
+ * tpc_set_trace(ctx, t) every following tpc_find_tracks records, for each
+ * update of tracklet t (numbered as in TPC_ITEM_TL_START), 16 floats: pass
+ * (0 forward, 1 backward), row, updates since the (re)seed, y, z, sin phi,
+ * dz/ds_T, q/pT, C_yy, C_zz, C_ss, C_tt, C_qq, chi2, residual y, residual z
+ * (the residuals before the update).  t < 0 switches it off.  At most 2048
+ * records are kept; *n_records reports how many were produced. */
+int tpc_set_trace(tpc_ctx *ctx, int32_t tracklet);
+int tpc_get_trace(tpc_ctx *ctx, float *out, int32_t cap_records, int32_t *n_records);
+
 /* ------------------------------------------------------ tuning (autotuner) */
 /* Threads per block of the cluster-, row-sector- and tracklet-parallel
  * kernels and CTAs per SM of the persistent follow/refit launches.  0 keeps

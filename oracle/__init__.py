@@ -43,7 +43,7 @@ class Config(ctypes.Structure):
     _fields_ = [("bz_kg", ctypes.c_double), ("sigma", ctypes.c_double), ("d_max", ctypes.c_float),
                 ("min_chain", ctypes.c_int), ("max_miss", ctypes.c_int), ("n_min_track", ctypes.c_int),
                 ("gate", ctypes.c_double), ("c0", ctypes.c_double * 5), ("s_max", ctypes.c_double),
-                ("edge", ctypes.c_double), ("taint_rel", ctypes.c_double)]
+                ("edge", ctypes.c_double), ("taint_rel", ctypes.c_double), ("trace_t", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -57,7 +57,8 @@ class _Result(ctypes.Structure):
                    "rs_of", "sy", "sz", "up", "dn", "up_m", "dn_m", "tie", "tl_start", "tl_len",
                    "f_n", "f_nf", "f_nb", "f_flags", "f_row", "f_hits", "f_par", "f_cov", "f_chi2",
                    "owner", "tl_track", "cluster_track",
-                   "t_tracklet", "t_n", "t_ndf", "t_flags", "t_row_in", "t_row_out", "t_par", "t_cov", "t_chi2")]
+                   "t_tracklet", "t_n", "t_ndf", "t_flags", "t_row_in", "t_row_out", "t_par", "t_cov", "t_chi2",
+                   "trace")] + [("n_trace", ctypes.c_int32)]
 
 
 _lib = None
@@ -158,6 +159,8 @@ def run(clusters: np.ndarray, req_offsets=None, stop_after: str = "refit", brute
                        t_par=_arr(res.t_par, np.float64, m * 5).reshape(m, 5),
                        t_cov=_arr(res.t_cov, np.float64, m * 15).reshape(m, 15),
                        t_chi2=_arr(res.t_chi2, np.float64, m))
+        if res.trace:
+            out["trace"] = _arr(res.trace, np.float64, 16 * res.n_trace).reshape(-1, 16)
         return out
     finally:
         lib.orc_free(ctypes.byref(res))

@@ -54,6 +54,7 @@ typedef struct {
   double s_max;      /* |sin phi| limit of the propagation */
   double edge;       /* cm beyond the sector edge that ends an extension */
   double taint_rel;  /* margin of the near-tie / near-gate flags */
+  int trace_t;       /* tracklet whose updates are recorded (-1: none) */
 } orc_config;
 
 void orc_default_config(orc_config *c) {
@@ -68,6 +69,7 @@ void orc_default_config(orc_config *c) {
   c->s_max = 0.95;
   c->edge = 2.0;
   c->taint_rel = 2e-3;
+  c->trace_t = -1;
 }
 
 /* ------------------------------------------------------------- geometry */
@@ -121,6 +123,9 @@ typedef struct {
   /* refit (a8) per track */
   int32_t *t_tracklet, *t_n, *t_ndf, *t_flags, *t_row_in, *t_row_out; /* [n_tracks] */
   double *t_par, *t_cov, *t_chi2;  /* [n_tracks*5], [*15], [n_tracks] */
+  /* trace of one tracklet's updates (16 values per record, see follow) */
+  double *trace;
+  int32_t n_trace;
 } orc_result;
 
 enum {
@@ -504,6 +509,21 @@ static void pack_cov(const double C[5][5], double *out15) {
     for (int j = 0; j <= i; j++) out15[q++] = C[i][j];
 }
 
+/* Update, recording (pass, row, updates since seed, y, z, sin phi, dz/ds,
+   q/pT, C_yy, C_zz, C_ss, C_tt, C_qq, chi2, residual y, residual z) when
+   tracklet t is the traced one. */
+#define ORC_TRACE_MAX 2048
+static void traced_update(const kctx *k, orc_result *R, int32_t t, int pass, int row, kstate *s, double my,
+                          double mz) {
+  double r0 = my - s->p[0], r1 = mz - s->p[1];
+  update(k, s, my, mz);
+  if (t != k->cfg->trace_t || !R->trace || R->n_trace >= ORC_TRACE_MAX) return;
+  double *o = R->trace + 16 * (int64_t)R->n_trace++;
+  double v[16] = {pass, row, s->nupd, s->p[0], s->p[1], s->p[2], s->p[3], s->p[4], s->C[0][0], s->C[1][1],
+                  s->C[2][2], s->C[3][3], s->C[4][4], s->chi2, r0, r1};
+  memcpy(o, v, sizeof(v));
+}
+
 /* Follow one tracklet (forward over the chain and outward, then a fresh
    backward pass that refits the forward clusters and extends inward). */
 static void follow_one(const kctx *k, orc_result *R, int32_t t) {
@@ -529,7 +549,7 @@ static void follow_one(const kctx *k, orc_result *R, int32_t t) {
   s.p[3] = dZ / Lc;
   s.p[4] = 0.0;
   reset_cov(k, &s);
-  update(k, &s, R->sy[c0], R->sz[c0]);
+  traced_update(k, R, t, 0, r0, &s, R->sy[c0], R->sz[c0]);
   hits[nf++] = c0;
   for (int i = 1; i < L; i++) {
     if (!propagate(k, &s, X32[r0 + i], &flags)) {
@@ -539,7 +559,7 @@ static void follow_one(const kctx *k, orc_result *R, int32_t t) {
       R->f_chi2[t] = 0;
       return;
     }
-    update(k, &s, R->sy[chain[i]], R->sz[chain[i]]);
+    traced_update(k, R, t, 0, r0 + i, &s, R->sy[chain[i]], R->sz[chain[i]]);
     hits[nf++] = chain[i];
   }
   kstate saved = s;
@@ -549,7 +569,7 @@ static void follow_one(const kctx *k, orc_result *R, int32_t t) {
     if (outside_sector(k, &s, &flags)) break;
     int32_t c = pick(k, R, unit_base + r, &s, &flags);
     if (c >= 0) {
-      update(k, &s, R->sy[c], R->sz[c]);
+      traced_update(k, R, t, 0, r, &s, R->sy[c], R->sz[c]);
       hits[nf++] = c;
       saved = s;
       r_last = r;
@@ -561,13 +581,13 @@ static void follow_one(const kctx *k, orc_result *R, int32_t t) {
   /* backward pass: re-seed with the forward state at the outermost cluster */
   s = saved;
   reset_cov(k, &s);
-  update(k, &s, R->sy[hits[nf - 1]], R->sz[hits[nf - 1]]);
+  traced_update(k, R, t, 1, r_last, &s, R->sy[hits[nf - 1]], R->sz[hits[nf - 1]]);
   saved = s;
   int kf = nf - 2, ok = 1;
   for (int r = r_last - 1; r >= r0; r--) {
     if (!propagate(k, &s, X32[r], &flags)) { ok = 0; flags |= F_BACK_FAIL; break; }
     if (kf >= 0 && R->rs_of[hits[kf]] % NROW == r) {
-      update(k, &s, R->sy[hits[kf]], R->sz[hits[kf]]);
+      traced_update(k, R, t, 1, r, &s, R->sy[hits[kf]], R->sz[hits[kf]]);
       kf--;
       saved = s;
     }
@@ -579,7 +599,7 @@ static void follow_one(const kctx *k, orc_result *R, int32_t t) {
       if (outside_sector(k, &s, &flags)) break;
       int32_t c = pick(k, R, unit_base + r, &s, &flags);
       if (c >= 0) {
-        update(k, &s, R->sy[c], R->sz[c]);
+        traced_update(k, R, t, 1, r, &s, R->sy[c], R->sz[c]);
         hits[nf + nb++] = c;
         saved = s;
         misses = 0;
@@ -743,7 +763,7 @@ void orc_free(orc_result *R) {
                   R->perm, R->rs_of, R->sy, R->sz, R->up, R->dn, R->up_m, R->dn_m, R->tie, R->tl_start,
                   R->tl_len, R->f_n, R->f_nf, R->f_nb, R->f_flags, R->f_row, R->f_hits, R->f_par, R->f_cov,
                   R->f_chi2, R->owner, R->tl_track, R->cluster_track, R->t_tracklet, R->t_n, R->t_ndf,
-                  R->t_flags, R->t_row_in, R->t_row_out, R->t_par, R->t_cov, R->t_chi2};
+                  R->t_flags, R->t_row_in, R->t_row_out, R->t_par, R->t_cov, R->t_chi2, R->trace};
   for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); i++) free(ptrs[i]);
   memset(R, 0, sizeof(*R));
 }
@@ -789,6 +809,10 @@ int orc_run(const orc_config *cfg_in, const orc_cluster *c, int64_t n, const int
       !R->f_chi2) return ORC_ENOMEM;
   for (size_t i = 0; i < nt * NROW; i++) R->f_hits[i] = -1;
   kctx k = {&cfg, 0.299792458e-3 * cfg.bz_kg, cfg.sigma * cfg.sigma};
+  if (cfg.trace_t >= 0) {
+    R->trace = (double *)calloc(16 * ORC_TRACE_MAX, sizeof(double));
+    if (!R->trace) return ORC_ENOMEM;
+  }
   run_parallel(follow_range, &k, R, R->n_tracklets, threads);
   if (stop_after <= 6) return ORC_OK;
   rc = select_tracks(&cfg, R);

@@ -89,6 +89,8 @@ def load_library(path: str | None = None):
         "tpc_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
         "tpc_get_stage_times": ([_VP, _VP], ctypes.c_int),
         "tpc_get_work": ([_VP, _VP], ctypes.c_int),
+        "tpc_set_trace": ([_VP, _I32], ctypes.c_int),
+        "tpc_get_trace": ([_VP, _VP, _I32, _VP], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -216,6 +218,19 @@ class Tracker:
 
     def set_tuning(self, block_clusters=0, block_follow=0, ctas_per_sm_follow=0):
         self._ck(self._lib.tpc_set_tuning(self._ctx, block_clusters, block_follow, ctas_per_sm_follow, 0))
+
+    TRACE_FIELDS = ("pass", "row", "nupd", "y", "z", "sphi", "tgl", "qpt", "Cyy", "Czz", "Css", "Ctt", "Cqq",
+                    "chi2", "ry", "rz")
+
+    def set_trace(self, tracklet: int):
+        """Record every Kalman update of one tracklet in the next find."""
+        self._ck(self._lib.tpc_set_trace(self._ctx, tracklet))
+
+    def trace(self) -> np.ndarray:
+        n = ctypes.c_int32()
+        out = np.zeros((2048, 16), np.float32)
+        self._ck(self._lib.tpc_get_trace(self._ctx, out.ctypes.data, 2048, ctypes.byref(n)))
+        return out[:min(n.value, 2048)]
 
     def set_profiling(self, on: bool = True):
         self._ck(self._lib.tpc_set_profiling(self._ctx, int(on)))

@@ -60,7 +60,9 @@ struct Counts {
   unsigned long long n_upd64;   // FP64-zone Kalman updates
   unsigned long long n_cand;    // candidate clusters examined by the gated pick-up
   unsigned long long n_prop64;  // propagations done with the FP64 covariance
-  unsigned long long pad2[3];
+  int32_t trace_n;              // trace records written
+  int32_t pad3;
+  unsigned long long pad2[2];
 };
 
 // Per-thread work tallies, flushed once per thread into Counts.
@@ -90,7 +92,16 @@ struct KConst {
   float taint;      // divergence margin
   int32_t min_chain, max_miss, n_min_track, fp64_updates;
   int64_t bins_cap, tl_cap;
+  // per-update trace of one tracklet (trace_t < 0: off)
+  int32_t trace_t;
+  int32_t trace_cap;
+  float* trace;  // trace_cap records of TRACE_W floats
 };
+
+// Trace record: pass (0 forward, 1 backward), row, updates since seed, then
+// y, z (absolute), sin phi, dz/ds, q/pT, C_yy, C_zz, C_ss, C_tt, C_qq, chi2,
+// residual y, residual z.
+constexpr int TRACE_W = 16;
 
 // Row radii X_r and active half-widths Y_r in binary32 (set once per device;
 // the library is a single translation unit).

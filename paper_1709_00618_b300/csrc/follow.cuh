@@ -107,12 +107,37 @@ struct Lane {
   int nupd;     // updates since the last (re)seed
   uint32_t flags;
   bool seed_fail;
+  bool tr;       // this tracklet is traced
+  Counts* cn;
   TrkState fwd;  // forward state after its last update
   // backward output: state after the last update
   TrkState sp;
   float sC[15];
   double schi2;
 };
+
+// Kalman update of the lane's state; records a trace line when traced.
+template <typename T>
+__device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState& p, T* C, float2 P, double& chi2,
+                                            int pass) {
+  float r0 = 0.0f, r1 = 0.0f;
+  if (w.tr) {
+    r0 = residual_y(p, P.x);
+    r1 = residual_z(p, P.y);
+  }
+  chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
+  if (w.tr) {
+    const int k = atomicAdd(&w.cn->trace_n, 1);
+    if (k < kc.trace_cap) {
+      float* o = kc.trace + (size_t)k * TRACE_W;
+      const float v[TRACE_W] = {(float)pass, (float)p.row, (float)(w.nupd + 1), p.y + p.yl,
+                                p.zref + (p.z + p.zl), p.s + p.sl, p.t, p.q, (float)C[0], (float)C[2],
+                                (float)C[5], (float)C[9], (float)C[14], (float)chi2, r0, r1};
+#pragma unroll
+      for (int i = 0; i < TRACE_W; i++) o[i] = v[i];
+    }
+  }
+}
 
 template <typename T>
 __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, const T* C, double chi2) {
@@ -146,7 +171,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
     if (c < 0) return ++w.misses < kc.max_miss;
   }
   const float2 P = __ldg(g.yz + c);
-  chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
+  lane_update<T>(w, kc, p, C, P, chi2, 0);
   tl.on_upd<T>();
   w.nupd++;
   w.hits[w.nf] = c;
@@ -184,7 +209,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
     w.misses = 0;
   }
   const float2 P = __ldg(g.yz + c);
-  chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
+  lane_update<T>(w, kc, p, C, P, chi2, 1);
   tl.on_upd<T>();
   w.nupd++;
   keep_output<T>(w, p, C, chi2);
@@ -212,6 +237,8 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
     w.hrow = o.hrow + t * NROW;
     w.flags = 0;
     w.seed_fail = false;
+    w.tr = (t == kc.trace_t);
+    w.cn = cn;
     const int c0 = tl_start[t], cl = tl_end[t];
     w.L = tl_len[t];
     const int rs0 = __ldg(g.rs_of + c0);
@@ -241,7 +268,8 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
       if (ZONE > 0) {
         double D[15];
         cov_seed<double>(D, kc);
-        chi2 += kalman_update<double>(p, D, P0.x, P0.y, kc.Vd);
+        w.nupd = 0;
+        lane_update<double>(w, kc, p, D, P0, chi2, 0);
         tl.on_upd<double>();
         w.nupd = 1;
         w.fwd = p;
@@ -250,7 +278,8 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
       } else {
         cov_seed<float>(C, kc);
-        chi2 += kalman_update<float>(p, C, P0.x, P0.y, kc.V);
+        w.nupd = 0;
+        lane_update<float>(w, kc, p, C, P0, chi2, 0);
         tl.on_upd<float>();
         w.nupd = 1;
         w.fwd = p;
@@ -283,7 +312,8 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
       if (ZONE > 0) {
         double D[15];
         cov_seed<double>(D, kc);
-        chi2 += kalman_update<double>(p, D, P.x, P.y, kc.Vd);
+        w.nupd = 0;
+        lane_update<double>(w, kc, p, D, P, chi2, 1);
         tl.on_upd<double>();
         w.nupd = 1;
         keep_output<double>(w, p, D, chi2);
@@ -292,7 +322,8 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
       } else {
         cov_seed<float>(C, kc);
-        chi2 += kalman_update<float>(p, C, P.x, P.y, kc.V);
+        w.nupd = 0;
+        lane_update<float>(w, kc, p, C, P, chi2, 1);
         tl.on_upd<float>();
         w.nupd = 1;
         keep_output<float>(w, p, C, chi2);

@@ -50,6 +50,57 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, double d) {
   lo = (float)(v - (double)hi);
 }
 
+// Double-float arithmetic (an unevaluated sum hi + lo of binary32 numbers,
+// ~44 significant bits) after Dekker, "A floating-point technique for
+// extending the available precision", Numer. Math. 18 (1971): error-free
+// sums and products, one Newton correction for quotient and square root.
+// The helix increments of a row step are evaluated this way: rounding
+// errors of ~1e-7 per row in dy are systematic along a smooth track and
+// would read as a curvature of ~1e-4 in q/pT.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_addf(ff a, float b) {
+  const ff s = two_sum(a.hi, b);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return quick_two_sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
+}
+__device__ __forceinline__ ff ff_mulf(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.hi, b, -p);
+  return quick_two_sum(p, __fmaf_rn(a.lo, b, e));
+}
+__device__ __forceinline__ ff ff_div(ff a, ff b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const ff r = ff_add(a, ff_mulf(b, -q1));  // a - q1 b
+  return quick_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+// sqrt(1 - s^2) for |s| < 1
+__device__ __forceinline__ ff ff_cos_from_sin(ff s) {
+  const ff one_m = ff_addf(ff_mul(s, {-s.hi, -s.lo}), 1.0f);
+  const float r = __fsqrt_rn(one_m.hi);
+  const float e = __fmaf_rn(r, r, -__fmul_rn(r, r));
+  const ff d = ff_add(one_m, {-__fmul_rn(r, r), -e});  // one_m - r^2
+  return quick_two_sum(r, __fdiv_rn(d.hi, __fmul_rn(2.0f, r)));
+}
+
 // C <- J C J^T for the sparse first-order Jacobian of one propagation step.
 template <typename T>
 __device__ __forceinline__ void cov_transport(T* C, T j02, T j04, T j24, T j12, T j13, T j14) {
@@ -138,33 +189,47 @@ struct Jac {
 
 __device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, const KConst& kc, uint32_t& flags,
                                            Jac* J) {
-  const float dx = x2 - p.x;
+  const float dx = x2 - p.x;  // exact for neighbouring rows (Sterbenz)
   const float kap = -kc.K * p.q;
-  const float s1 = p.s, s2 = s1 + kap * dx;
-  if (fabsf(fabsf(s1) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
-  if (!(fabsf(s1) < kc.s_max && fabsf(s2) < kc.s_max)) return false;
-  const float c1 = sqrtf(1.0f - s1 * s1), c2 = sqrtf(1.0f - s2 * s2);
-  const float icc = 1.0f / (c1 + c2);
-  const float ss = s1 + s2;
-  const float dy = dx * ss * icc;
+  const ff s1 = {p.s, p.sl};
+  const ff s2 = ff_addf(s1, kap * dx);
+  if (fabsf(fabsf(s1.hi) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2.hi) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
+  if (!(fabsf(s1.hi) < kc.s_max && fabsf(s2.hi) < kc.s_max)) return false;
+  const ff c1 = ff_cos_from_sin(s1), c2 = ff_cos_from_sin(s2);
+  const ff ss = ff_add(s1, s2);
+  const ff tm = ff_div(ss, ff_add(c1, c2));  // (s1 + s2) / (c1 + c2)
+  const ff dy = ff_mulf(tm, dx);
   // arc length: sin(phi2 - phi1) = kap*dx*g with g = c1 + s1 (s1+s2)/(c1+c2),
   // so dS = dx*g*asin(a)/a, a = kap*dx*g, free of the cancellation of
-  // asin(s2) - asin(s1) in binary32
-  const float g = c1 + s1 * ss * icc;
-  const float a = kap * dx * g;
-  const float dS = dx * g * (a != 0.0f ? asinf(a) / a : 1.0f);
+  // asin(s2) - asin(s1); asin(a)/a from its Taylor series
+  // 1 + a^2/6 + 3a^4/40 + 5a^6/112 + 35a^8/1152 (+ O(a^10)) for |a| < 0.1
+  const ff g = ff_add(c1, ff_mul(s1, tm));
+  const float a = kap * dx * g.hi;
+  float corr;
+  if (fabsf(a) < 0.1f) {
+    const float a2 = a * a;
+    corr = a2 * (1.0f / 6.0f + a2 * (3.0f / 40.0f + a2 * (5.0f / 112.0f + a2 * (35.0f / 1152.0f))));
+  } else {
+    corr = asinf(a) / a - 1.0f;
+  }
+  const ff gdx = ff_mulf(g, dx);
+  const ff dS = ff_add(gdx, ff_mulf(gdx, corr));
+  const ff dz = ff_mulf(dS, p.t);
   if (J) {
-    const float sm = 0.5f * ss, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
+    const float sm = 0.5f * ss.hi, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
     J->j02 = dx * icm3;
     J->j04 = -kc.K * dx * dx * 0.5f * icm3;
     J->j24 = -kc.K * dx;
-    J->j13 = dS;
+    J->j13 = dS.hi;
     J->j12 = p.t * dx * sm * icm3;
     J->j14 = -p.t * kc.K * dx * dx * sm * 0.5f * icm3;
   }
-  acc2(p.y, p.yl, dy);
-  acc2(p.z, p.zl, p.t * dS);
-  acc2(p.s, p.sl, kap * dx);
+  acc2(p.y, p.yl, dy.hi);
+  p.yl = __fadd_rn(p.yl, dy.lo);
+  acc2(p.z, p.zl, dz.hi);
+  p.zl = __fadd_rn(p.zl, dz.lo);
+  p.s = s2.hi;
+  p.sl = s2.lo;
   p.x = x2;
   p.row = row2;
   return true;

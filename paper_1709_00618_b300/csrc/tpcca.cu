@@ -81,8 +81,11 @@ struct Layout {
   size_t tl_start, tl_len, tl_end, f_n, f_nf, f_nb, f_flags, f_row, hits, hrow, f_par, f_zref, f_cov, f_chi2, keep,
       tidx, nown, tl_track, track_tl, tcount, toff, tracks;
   size_t parts;
+  size_t trace;
   size_t total;
 };
+
+constexpr int TRACE_RECORDS = 2048;
 
 Layout make_layout(const Caps& c) {
   Layout L{};
@@ -148,6 +151,7 @@ Layout make_layout(const Caps& c) {
   L.toff = take(4 * (M + 1));
   L.tracks = take(sizeof(tpc_track) * M);
   L.parts = take(4 * SCAN_PARTS);
+  L.trace = take(4 * TRACE_W * TRACE_RECORDS);
   L.total = off;
   return L;
 }
@@ -180,6 +184,7 @@ struct tpc_ctx {
   int ctas_follow = 4;
   // graph
   cudaGraphExec_t graph = nullptr;
+  int32_t trace_t = -1;  // traced tracklet
   // stage events
   bool prof = false;
   bool prof_valid = false;
@@ -277,6 +282,9 @@ int do_reserve(tpc_ctx* ctx, const Caps& want) {
   ctx->caps = c;
   ctx->L = L;
   ctx->kc = make_kconst(ctx->cfg, c);
+  ctx->kc.trace_t = ctx->trace_t;
+  ctx->kc.trace_cap = TRACE_RECORDS;
+  ctx->kc.trace = ctx->ptr<float>(L.trace);
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
@@ -760,6 +768,31 @@ int tpc_get_stage(tpc_ctx* ctx, int item, void* host_out, int64_t cap_bytes, int
     return TPC_OK;
   }
   CK(cudaMemcpy(host_out, ctx->arena + off, bytes, cudaMemcpyDeviceToHost));
+  return TPC_OK;
+}
+
+int tpc_set_trace(tpc_ctx* ctx, int32_t tracklet) {
+  if (!ctx) return TPC_EINVAL;
+  ctx->trace_t = tracklet < 0 ? -1 : tracklet;
+  ctx->kc.trace_t = ctx->trace_t;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return TPC_OK;
+}
+
+int tpc_get_trace(tpc_ctx* ctx, float* out, int32_t cap_records, int32_t* n_records) {
+  if (!ctx || cap_records < 0) return TPC_EINVAL;
+  if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "nothing loaded");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  Counts hc{};
+  CK(cudaMemcpy(&hc, ctx->ptr<Counts>(ctx->L.counts), sizeof(Counts), cudaMemcpyDeviceToHost));
+  if (n_records) *n_records = hc.trace_n;
+  const int32_t n = std::min(std::min(hc.trace_n, (int32_t)TRACE_RECORDS), cap_records);
+  if (out && n > 0)
+    CK(cudaMemcpy(out, ctx->ptr<float>(ctx->L.trace), sizeof(float) * TRACE_W * n, cudaMemcpyDeviceToHost));
   return TPC_OK;
 }
 
