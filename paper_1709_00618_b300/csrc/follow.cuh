@@ -3,12 +3,11 @@
 // outward with gated pick-up, fresh backward pass refitting the forward
 // clusters and extending inward.
 //
-// Each pass runs as two loops: the first `fp64_updates` Kalman updates with
-// the covariance in FP64, then the rest in FP32.  A warp therefore never
-// mixes lanes in the two precisions (FP64 issues at 1/64 of the FP32 rate on
-// this part, so a mixed warp pays the FP64 path for every straggler), and
-// the lanes of a warp -- consecutive tracklets, which start on neighbouring
-// rows -- stay in the same phase.
+// The first `fp64_updates` Kalman updates after each (re)seed keep the
+// covariance in FP64; those operations are out of line (kalman.cuh) so that
+// the kernel body stays small enough for the instruction cache and the
+// binary32 path keeps its registers.  The lanes of a warp are consecutive
+// tracklets, which start on neighbouring rows, so their FP64 zones overlap.
 #pragma once
 #include "kalman.cuh"
 
@@ -116,50 +115,59 @@ struct Lane {
   double schi2;
 };
 
-// Kalman update of the lane's state; records a trace line when traced.
-template <typename T>
-__device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState& p, T* C, float2 P, double& chi2,
-                                            int pass) {
-  float r0 = 0.0f, r1 = 0.0f;
-  if (w.tr) {
-    r0 = residual_y(p, P.x);
-    r1 = residual_z(p, P.y);
-  }
-  chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
-  if (w.tr) {
-    const int k = atomicAdd(&w.cn->trace_n, 1);
-    if (k < kc.trace_cap) {
-      float* o = kc.trace + (size_t)k * TRACE_W;
-      const float v[TRACE_W] = {(float)pass, (float)p.row, (float)(w.nupd + 1), p.y + p.yl,
-                                p.zref + (p.z + p.zl), p.s + p.sl, p.t, p.q, (float)C[0], (float)C[2],
-                                (float)C[5], (float)C[9], (float)C[14], (float)chi2, r0, r1};
+// Trace line of one Kalman update (out of line: executed for one tracklet).
+__device__ __noinline__ void trace_line(Counts* cn, float* trace, int cap, float pass, float row, float nupd,
+                                        float y, float z, float s, float t, float q, float cyy, float czz,
+                                        float css, float ctt, float cqq, float chi2, float r0, float r1) {
+  const int k = atomicAdd(&cn->trace_n, 1);
+  if (k >= cap) return;
+  float* o = trace + (size_t)k * TRACE_W;
+  const float v[TRACE_W] = {pass, row, nupd, y, z, s, t, q, cyy, czz, css, ctt, cqq, chi2, r0, r1};
 #pragma unroll
-      for (int i = 0; i < TRACE_W; i++) o[i] = v[i];
-    }
-  }
+  for (int i = 0; i < TRACE_W; i++) o[i] = v[i];
 }
 
-template <typename T>
-__device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, const T* C, double chi2) {
+// Kalman update of the lane's state (covariance in D during the zone, else
+// in C); records a trace line when the lane is traced.
+__device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState& p, bool zone, double* D, float* C,
+                                            float2 P, double& chi2, int pass) {
+  const float r0 = residual_y(p, P.x), r1 = residual_z(p, P.y);
+  chi2 += update_any(p, zone, D, C, P.x, P.y, kc);
+  w.nupd++;
+  if (zone && w.nupd == kc.fp64_updates) {
+#pragma unroll
+    for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+  }
+  if (w.tr)
+    trace_line(w.cn, kc.trace, kc.trace_cap, (float)pass, (float)p.row, (float)w.nupd, p.y + p.yl,
+               p.zref + (p.z + p.zl), p.s + p.sl, p.t, p.q, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2],
+               zone ? (float)D[5] : C[5], zone ? (float)D[9] : C[9], zone ? (float)D[14] : C[14], (float)chi2, r0,
+               r1);
+}
+
+__device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zone, const double* D, const float* C,
+                                            double chi2) {
   w.sp = p;
 #pragma unroll
-  for (int i = 0; i < 15; i++) w.sC[i] = (float)C[i];
+  for (int i = 0; i < 15; i++) w.sC[i] = zone ? (float)D[i] : C[i];
   w.schi2 = chi2;
 }
 
-// One forward row step in covariance precision T; false ends the pass.
-template <typename T>
+// One forward row step; false ends the pass.  The covariance is in D while
+// fewer than fp64_updates updates have been made since the seed.
 __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __restrict__ up_m, const KConst& kc,
-                                         const float* sX, const float* sYH, Lane& w, TrkState& p, T* C,
-                                         double& chi2, LocalTally& tl) {
+                                         const float* sX, const float* sYH, Lane& w, TrkState& p, double* D,
+                                         float* C, double& chi2, LocalTally& tl) {
   const int r = p.row + 1;
   if (r >= NROW) return false;
   const bool chain = w.i < w.L;
-  if (!propagate<T>(p, C, r, sX[r], kc, w.flags)) {
+  const bool zone = w.nupd < kc.fp64_updates;
+  if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (chain) w.seed_fail = true;
     return false;
   }
-  tl.on_prop<T>();
+  tl.prop++;
+  tl.prop64 += zone;
   int c;
   if (chain) {
     w.k = __ldg(up_m + w.k);
@@ -167,13 +175,14 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
     c = w.k;
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
-    c = pick(g, w.ubase + r, r, p, (float)C[0], (float)C[2], kc, sYH, w.flags, tl.cand);
+    c = pick(g, w.ubase + r, r, p, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2], kc, sYH, w.flags,
+             tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
   }
   const float2 P = __ldg(g.yz + c);
-  lane_update<T>(w, kc, p, C, P, chi2, 0);
-  tl.on_upd<T>();
-  w.nupd++;
+  lane_update(w, kc, p, zone, D, C, P, chi2, 0);
+  if (zone) tl.upd64++;
+  else tl.upd32++;
   w.hits[w.nf] = c;
   w.hrow[w.nf] = (uint8_t)r;
   w.nf++;
@@ -183,17 +192,18 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
   return true;
 }
 
-// One backward row step in covariance precision T; false ends the pass.
-template <typename T>
+// One backward row step; false ends the pass.
 __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, const float* sX, const float* sYH,
-                                         Lane& w, TrkState& p, T* C, double& chi2, LocalTally& tl) {
+                                         Lane& w, TrkState& p, double* D, float* C, double& chi2, LocalTally& tl) {
   const int r = p.row - 1;
   if (r < 0) return false;
-  if (!propagate<T>(p, C, r, sX[r], kc, w.flags)) {
+  const bool zone = w.nupd < kc.fp64_updates;
+  if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (r >= w.r0) w.flags |= TF_BACK_FAIL;
     return false;
   }
-  tl.on_prop<T>();
+  tl.prop++;
+  tl.prop64 += zone;
   int c;
   if (r >= w.r0) {
     if (!(w.kf >= 0 && w.hrow[w.kf] == r)) return true;
@@ -201,7 +211,8 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
     w.kf--;
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
-    c = pick(g, w.ubase + r, r, p, (float)C[0], (float)C[2], kc, sYH, w.flags, tl.cand);
+    c = pick(g, w.ubase + r, r, p, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2], kc, sYH, w.flags,
+             tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
     w.hits[w.nf + w.nb] = c;
     w.hrow[w.nf + w.nb] = (uint8_t)r;
@@ -209,11 +220,17 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
     w.misses = 0;
   }
   const float2 P = __ldg(g.yz + c);
-  lane_update<T>(w, kc, p, C, P, chi2, 1);
-  tl.on_upd<T>();
-  w.nupd++;
-  keep_output<T>(w, p, C, chi2);
+  lane_update(w, kc, p, zone, D, C, P, chi2, 1);
+  if (zone) tl.upd64++;
+  else tl.upd32++;
+  keep_output(w, p, w.nupd <= kc.fp64_updates && w.nupd < kc.fp64_updates, D, C, chi2);
   return true;
+}
+
+// Fresh covariance for a (re)seed: diag(c0) in D (zone) or C.
+__device__ __forceinline__ void reseed_cov(const KConst& kc, double* D, float* C) {
+  cov_seed<double>(D, kc);
+  cov_seed<float>(C, kc);
 }
 
 __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __restrict__ tl_start,
@@ -229,8 +246,9 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
   __syncthreads();
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
-  const int ZONE = kc.fp64_updates;
   LocalTally tl;
+  double D[15];  // FP64-zone covariance (local memory: its operations are out of line)
+  float C[15];
   for (int64_t t = gtid(); t < T; t += gstride()) {
     Lane w;
     w.hits = o.hits + t * NROW;
@@ -252,7 +270,6 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
       const float Lc = sqrtf(dX * dX + dY * dY);
       seed_state(p, w.r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);
     }
-    w.nf = w.nb = 0;
     w.k = c0;
     w.i = 1;
     w.misses = 0;
@@ -260,31 +277,32 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
     w.hits[0] = c0;
     w.hrow[0] = (uint8_t)w.r0;
     w.nf = 1;
+    w.nb = 0;
     double chi2 = 0.0;
     // ---- forward pass
+    reseed_cov(kc, D, C);
+    w.nupd = 0;
+    lane_update(w, kc, p, kc.fp64_updates > 0, D, C, P0, chi2, 0);
+    if (kc.fp64_updates > 0) tl.upd64++;
+    else tl.upd32++;
+    w.fwd = p;
     bool go = true;
-    {
-      float C[15];
-      if (ZONE > 0) {
-        double D[15];
-        cov_seed<double>(D, kc);
-        w.nupd = 0;
-        lane_update<double>(w, kc, p, D, P0, chi2, 0);
-        tl.on_upd<double>();
-        w.nupd = 1;
-        w.fwd = p;
-        while (go && w.nupd < ZONE) go = fwd_step<double>(g, up_m, kc, sX, sYH, w, p, D, chi2, tl);
-#pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
-      } else {
-        cov_seed<float>(C, kc);
-        w.nupd = 0;
-        lane_update<float>(w, kc, p, C, P0, chi2, 0);
-        tl.on_upd<float>();
-        w.nupd = 1;
-        w.fwd = p;
-      }
-      while (go) go = fwd_step<float>(g, up_m, kc, sX, sYH, w, p, C, chi2, tl);
+    while (go) go = fwd_step(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+    // ---- backward pass: forward state at the outermost cluster, fresh covariance
+    if (!w.seed_fail) {
+      p = w.fwd;
+      chi2 = 0.0;
+      w.kf = w.nf - 2;
+      w.misses = 0;
+      reseed_cov(kc, D, C);
+      w.nupd = 0;
+      const bool zone0 = kc.fp64_updates > 0;
+      lane_update(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
+      if (zone0) tl.upd64++;
+      else tl.upd32++;
+      keep_output(w, p, w.nupd < kc.fp64_updates, D, C, chi2);
+      go = true;
+      while (go) go = bwd_step(g, kc, sX, sYH, w, p, D, C, chi2, tl);
     }
     if (w.seed_fail) {
       o.n[t] = 0;
@@ -299,36 +317,6 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
       o.zref[t] = P0.y;
       o.chi2[t] = 0.0;
       continue;
-    }
-    // ---- backward pass: forward state at the outermost cluster, fresh covariance
-    p = w.fwd;
-    chi2 = 0.0;
-    w.kf = w.nf - 2;
-    w.misses = 0;
-    go = true;
-    {
-      const float2 P = __ldg(g.yz + w.hits[w.nf - 1]);
-      float C[15];
-      if (ZONE > 0) {
-        double D[15];
-        cov_seed<double>(D, kc);
-        w.nupd = 0;
-        lane_update<double>(w, kc, p, D, P, chi2, 1);
-        tl.on_upd<double>();
-        w.nupd = 1;
-        keep_output<double>(w, p, D, chi2);
-        while (go && w.nupd < ZONE) go = bwd_step<double>(g, kc, sX, sYH, w, p, D, chi2, tl);
-#pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
-      } else {
-        cov_seed<float>(C, kc);
-        w.nupd = 0;
-        lane_update<float>(w, kc, p, C, P, chi2, 1);
-        tl.on_upd<float>();
-        w.nupd = 1;
-        keep_output<float>(w, p, C, chi2);
-      }
-      while (go) go = bwd_step<float>(g, kc, sX, sYH, w, p, C, chi2, tl);
     }
     o.n[t] = w.nf + w.nb;
     o.nf[t] = w.nf;

@@ -50,57 +50,6 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, double d) {
   lo = (float)(v - (double)hi);
 }
 
-// Double-float arithmetic (an unevaluated sum hi + lo of binary32 numbers,
-// ~44 significant bits) after Dekker, "A floating-point technique for
-// extending the available precision", Numer. Math. 18 (1971): error-free
-// sums and products, one Newton correction for quotient and square root.
-// The helix increments of a row step are evaluated this way: rounding
-// errors of ~1e-7 per row in dy are systematic along a smooth track and
-// would read as a curvature of ~1e-4 in q/pT.
-struct ff {
-  float hi, lo;
-};
-__device__ __forceinline__ ff two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ ff quick_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ ff ff_add(ff a, ff b) {
-  const ff s = two_sum(a.hi, b.hi);
-  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
-}
-__device__ __forceinline__ ff ff_addf(ff a, float b) {
-  const ff s = two_sum(a.hi, b);
-  return quick_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
-}
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  const float e = __fmaf_rn(a.hi, b.hi, -p);
-  return quick_two_sum(p, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e)));
-}
-__device__ __forceinline__ ff ff_mulf(ff a, float b) {
-  const float p = __fmul_rn(a.hi, b);
-  const float e = __fmaf_rn(a.hi, b, -p);
-  return quick_two_sum(p, __fmaf_rn(a.lo, b, e));
-}
-__device__ __forceinline__ ff ff_div(ff a, ff b) {
-  const float q1 = __fdiv_rn(a.hi, b.hi);
-  const ff r = ff_add(a, ff_mulf(b, -q1));  // a - q1 b
-  return quick_two_sum(q1, __fdiv_rn(r.hi, b.hi));
-}
-// sqrt(1 - s^2) for |s| < 1
-__device__ __forceinline__ ff ff_cos_from_sin(ff s) {
-  const ff one_m = ff_addf(ff_mul(s, {-s.hi, -s.lo}), 1.0f);
-  const float r = __fsqrt_rn(one_m.hi);
-  const float e = __fmaf_rn(r, r, -__fmul_rn(r, r));
-  const ff d = ff_add(one_m, {-__fmul_rn(r, r), -e});  // one_m - r^2
-  return quick_two_sum(r, __fdiv_rn(d.hi, __fmul_rn(2.0f, r)));
-}
-
 // C <- J C J^T for the sparse first-order Jacobian of one propagation step.
 template <typename T>
 __device__ __forceinline__ void cov_transport(T* C, T j02, T j04, T j24, T j12, T j13, T j14) {
@@ -166,18 +115,26 @@ __device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, flo
     g0[i] = k0[i] * I00 + k1[i] * I01;
     g1[i] = k0[i] * I01 + k1[i] * I11;
   }
-  const T R0 = (T)r0, R1 = (T)r1;
-  acc2(p.y, p.yl, g0[0] * R0 + g1[0] * R1);
-  acc2(p.z, p.zl, g0[1] * R0 + g1[1] * R1);
-  acc2(p.s, p.sl, g0[2] * R0 + g1[2] * R1);
-  p.t += (float)(g0[3] * R0 + g1[3] * R1);
-  p.q += (float)(g0[4] * R0 + g1[4] * R1);
+  // state increments G r in binary32 (the state is binary32; the gain is
+  // rounded once), covariance in T
+  float f0[5], f1[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    f0[i] = (float)g0[i];
+    f1[i] = (float)g1[i];
+  }
+  acc2(p.y, p.yl, f0[0] * r0 + f1[0] * r1);
+  acc2(p.z, p.zl, f0[1] * r0 + f1[1] * r1);
+  acc2(p.s, p.sl, f0[2] * r0 + f1[2] * r1);
+  p.t += f0[3] * r0 + f1[3] * r1;
+  p.q += f0[4] * r0 + f1[4] * r1;
 #pragma unroll
   for (int i = 0; i < 5; i++)
 #pragma unroll
     for (int j = 0; j <= i; j++) C[TPC_CI(i, j)] -= g0[i] * k0[j] + g1[i] * k1[j];
-  const double d0 = r0, d1 = r1;
-  return d0 * ((double)I00 * d0 + (double)I01 * d1) + d1 * ((double)I01 * d0 + (double)I11 * d1);
+  // chi2 increment r^T S^-1 r (binary32), accumulated by the caller in FP64
+  const float i00 = (float)I00, i01 = (float)I01, i11 = (float)I11;
+  return (double)(r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1));
 }
 
 // Propagation of the state to row2 at radius x2.  Returns false when
@@ -191,47 +148,108 @@ __device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, cons
                                            Jac* J) {
   const float dx = x2 - p.x;  // exact for neighbouring rows (Sterbenz)
   const float kap = -kc.K * p.q;
-  const ff s1 = {p.s, p.sl};
-  const ff s2 = ff_addf(s1, kap * dx);
-  if (fabsf(fabsf(s1.hi) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2.hi) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
-  if (!(fabsf(s1.hi) < kc.s_max && fabsf(s2.hi) < kc.s_max)) return false;
-  const ff c1 = ff_cos_from_sin(s1), c2 = ff_cos_from_sin(s2);
-  const ff ss = ff_add(s1, s2);
-  const ff tm = ff_div(ss, ff_add(c1, c2));  // (s1 + s2) / (c1 + c2)
-  const ff dy = ff_mulf(tm, dx);
+  const float s1 = p.s, s2 = s1 + kap * dx;
+  if (fabsf(fabsf(s1) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
+  if (!(fabsf(s1) < kc.s_max && fabsf(s2) < kc.s_max)) return false;
+  const float c1 = sqrtf(1.0f - s1 * s1), c2 = sqrtf(1.0f - s2 * s2);
+  const float icc = 1.0f / (c1 + c2);
+  const float ss = s1 + s2;
+  const float dy = dx * ss * icc;
   // arc length: sin(phi2 - phi1) = kap*dx*g with g = c1 + s1 (s1+s2)/(c1+c2),
   // so dS = dx*g*asin(a)/a, a = kap*dx*g, free of the cancellation of
-  // asin(s2) - asin(s1); asin(a)/a from its Taylor series
+  // asin(s2) - asin(s1) in binary32; asin(a)/a from its Taylor series
   // 1 + a^2/6 + 3a^4/40 + 5a^6/112 + 35a^8/1152 (+ O(a^10)) for |a| < 0.1
-  const ff g = ff_add(c1, ff_mul(s1, tm));
-  const float a = kap * dx * g.hi;
-  float corr;
+  const float g = c1 + s1 * ss * icc;
+  const float a = kap * dx * g;
+  float h;
   if (fabsf(a) < 0.1f) {
     const float a2 = a * a;
-    corr = a2 * (1.0f / 6.0f + a2 * (3.0f / 40.0f + a2 * (5.0f / 112.0f + a2 * (35.0f / 1152.0f))));
+    h = 1.0f + a2 * (1.0f / 6.0f + a2 * (3.0f / 40.0f + a2 * (5.0f / 112.0f + a2 * (35.0f / 1152.0f))));
   } else {
-    corr = asinf(a) / a - 1.0f;
+    h = asinf(a) / a;
   }
-  const ff gdx = ff_mulf(g, dx);
-  const ff dS = ff_add(gdx, ff_mulf(gdx, corr));
-  const ff dz = ff_mulf(dS, p.t);
+  const float dS = dx * g * h;
   if (J) {
-    const float sm = 0.5f * ss.hi, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
+    const float sm = 0.5f * ss, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
     J->j02 = dx * icm3;
     J->j04 = -kc.K * dx * dx * 0.5f * icm3;
     J->j24 = -kc.K * dx;
-    J->j13 = dS.hi;
+    J->j13 = dS;
     J->j12 = p.t * dx * sm * icm3;
     J->j14 = -p.t * kc.K * dx * dx * sm * 0.5f * icm3;
   }
-  acc2(p.y, p.yl, dy.hi);
-  p.yl = __fadd_rn(p.yl, dy.lo);
-  acc2(p.z, p.zl, dz.hi);
-  p.zl = __fadd_rn(p.zl, dz.lo);
-  p.s = s2.hi;
-  p.sl = s2.lo;
+  acc2(p.y, p.yl, dy);
+  acc2(p.z, p.zl, p.t * dS);
+  acc2(p.s, p.sl, kap * dx);
   p.x = x2;
   p.row = row2;
+  return true;
+}
+
+// The FP64-zone covariance operations are kept out of line: one copy of
+// the double-precision code, the covariance in (L1-resident) local memory,
+// so the binary32 loop that runs most rows keeps its registers.
+__device__ __noinline__ void cov_transport_d(double* D, float j02, float j04, float j24, float j12, float j13,
+                                             float j14) {
+  cov_transport<double>(D, j02, j04, j24, j12, j13, j14);
+}
+
+struct UpdOut {
+  float d0, d1, d2, d3, d4;  // state increments G r
+  float chi2;                // r^T S^-1 r
+};
+
+// Kalman update of the FP64 covariance D for residual (r0, r1).
+__device__ __noinline__ UpdOut kalman_update_d(double* D, float r0, float r1, double V) {
+  const double S00 = D[0] + V, S01 = D[1], S11 = D[2] + V;
+  const double idet = 1.0 / (S00 * S11 - S01 * S01);
+  const double I00 = S11 * idet, I01 = -S01 * idet, I11 = S00 * idet;
+  const double k0[5] = {D[0], D[1], D[3], D[6], D[10]};
+  const double k1[5] = {D[1], D[2], D[4], D[7], D[11]};
+  double g0[5], g1[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    g0[i] = k0[i] * I00 + k1[i] * I01;
+    g1[i] = k0[i] * I01 + k1[i] * I11;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) D[TPC_CI(i, j)] -= g0[i] * k0[j] + g1[i] * k1[j];
+  UpdOut o;
+  o.d0 = (float)g0[0] * r0 + (float)g1[0] * r1;
+  o.d1 = (float)g0[1] * r0 + (float)g1[1] * r1;
+  o.d2 = (float)g0[2] * r0 + (float)g1[2] * r1;
+  o.d3 = (float)g0[3] * r0 + (float)g1[3] * r1;
+  o.d4 = (float)g0[4] * r0 + (float)g1[4] * r1;
+  const float i00 = (float)I00, i01 = (float)I01, i11 = (float)I11;
+  o.chi2 = r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
+  return o;
+}
+
+// One Kalman update of the state with covariance in FP64 (zone) or FP32.
+__device__ __forceinline__ double update_any(TrkState& p, bool zone, double* D, float* C, float my, float mz,
+                                             const KConst& kc) {
+  if (zone) {
+    const float r0 = residual_y(p, my), r1 = residual_z(p, mz);
+    const UpdOut o = kalman_update_d(D, r0, r1, kc.Vd);
+    acc2(p.y, p.yl, o.d0);
+    acc2(p.z, p.zl, o.d1);
+    acc2(p.s, p.sl, o.d2);
+    p.t += o.d3;
+    p.q += o.d4;
+    return (double)o.chi2;
+  }
+  return kalman_update<float>(p, C, my, mz, kc.V);
+}
+
+// Propagation with the covariance in FP64 (zone) or FP32.
+__device__ __forceinline__ bool propagate_any(TrkState& p, bool zone, double* D, float* C, int row2, float x2,
+                                              const KConst& kc, uint32_t& flags) {
+  Jac J;
+  if (!prop_state(p, row2, x2, kc, flags, &J)) return false;
+  if (zone) cov_transport_d(D, J.j02, J.j04, J.j24, J.j12, J.j13, J.j14);
+  else cov_transport<float>(C, J.j02, J.j04, J.j24, J.j12, J.j13, J.j14);
   return true;
 }
 

@@ -35,23 +35,66 @@ __global__ void k_own(const int32_t* __restrict__ f_n, const int32_t* __restrict
   }
 }
 
-// keep[t] = 1 when tracklet t owns at least n_min_track of its clusters.
+// keep[t] = 1 when tracklet t owns at least n_min_track of its clusters;
+// for kept tracklets also the bit mask of owned hit slots (5 words) and the
+// owned row range (r_in | r_out << 16), so that the refit and the output
+// stage need no ownership loads.
+constexpr int OWN_WORDS = 5;
 __global__ void k_keep(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits,
-                       const uint64_t* __restrict__ owner, KConst kc, int32_t* __restrict__ keep,
-                       int32_t* __restrict__ nown, const Counts* cn) {
+                       const uint8_t* __restrict__ hrow, const uint64_t* __restrict__ owner, KConst kc,
+                       int32_t* __restrict__ keep, int32_t* __restrict__ nown, uint32_t* __restrict__ own_mask,
+                       int32_t* __restrict__ own_rng, const Counts* cn) {
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
   for (int64_t t = gtid(); t < T; t += gstride()) {
     const int n = f_n[t];
-    int kept = 0;
+    int kept = 0, r_in = NROW, r_out = -1;
+    uint32_t m[OWN_WORDS] = {0, 0, 0, 0, 0};
     if (n >= kc.n_min_track) {
       const uint64_t key = track_key(n, (int)t);
       const int32_t* h = hits + t * NROW;
-      for (int i = 0; i < n; i++) kept += __ldg((const unsigned long long*)owner + h[i]) == key;
+      const uint8_t* hr = hrow + t * NROW;
+      for (int i = 0; i < n; i++) {
+        if (__ldg((const unsigned long long*)owner + h[i]) != key) continue;
+        kept++;
+        m[i >> 5] |= 1u << (i & 31);
+        const int r = hr[i];
+        r_in = min(r_in, r);
+        r_out = max(r_out, r);
+      }
     }
     const int k = kept >= kc.n_min_track;
     keep[t] = k;
     nown[t] = k ? kept : 0;
+    if (k) {
+#pragma unroll
+      for (int w = 0; w < OWN_WORDS; w++) own_mask[t * OWN_WORDS + w] = m[w];
+      own_rng[t] = r_in | (r_out << 16);
+    }
+  }
+}
+
+// Load-order indices of each track's owned clusters, innermost row first
+// (backward-extension hits from the last stored, then forward hits).
+__global__ void k_track_clusters(const int32_t* __restrict__ track_tl, const int32_t* __restrict__ f_n,
+                                 const int32_t* __restrict__ f_nf, const int32_t* __restrict__ hits,
+                                 const uint32_t* __restrict__ own_mask, const int32_t* __restrict__ toff,
+                                 const int32_t* __restrict__ perm, int32_t* __restrict__ track_clusters,
+                                 const Counts* cn) {
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  for (int64_t m = gtid(); m < M; m += gstride()) {
+    const int t = track_tl[m];
+    const int n = f_n[t], nf = f_nf[t];
+    uint32_t mk[OWN_WORDS];
+#pragma unroll
+    for (int w = 0; w < OWN_WORDS; w++) mk[w] = own_mask[t * OWN_WORDS + w];
+    const int32_t* h = hits + (int64_t)t * NROW;
+    int wpos = toff[m];
+    for (int j = n - 1; j >= nf; j--)
+      if ((mk[j >> 5] >> (j & 31)) & 1u) track_clusters[wpos++] = __ldg(perm + h[j]);
+    for (int j = 0; j < nf; j++)
+      if ((mk[j >> 5] >> (j & 31)) & 1u) track_clusters[wpos++] = __ldg(perm + h[j]);
   }
 }
 
@@ -97,36 +140,55 @@ struct RefitLane {
   const int32_t* h;
   const uint8_t* hr;
   int n, nf, j, cur, r_in;
-  uint64_t key;
-  const unsigned long long* owner;
+  int cur_row;      // row of the next owned hit (prefetched)
+  float2 cur_yz;    // its position (prefetched)
+  uint32_t m[OWN_WORDS];
+  const float2* yz;
+  __device__ __forceinline__ bool owned(int slot) const {
+    uint32_t w = m[0];
+#pragma unroll
+    for (int k = 1; k < OWN_WORDS; k++)
+      if ((slot >> 5) == k) w = m[k];
+    return (w >> (slot & 31)) & 1u;
+  }
+  // next owned hit in update order, its row and position fetched ahead
   __device__ __forceinline__ void advance() {
     cur = -1;
+    cur_row = -1;
     for (; j < n; j++) {
       const int slot = j < nf ? nf - 1 - j : j;
-      if (__ldg(owner + h[slot]) == key) {
+      if (owned(slot)) {
         cur = slot;
+        cur_row = hr[slot];
+        cur_yz = __ldg(yz + h[slot]);
         return;
       }
     }
   }
 };
 
-template <typename T>
 __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, const float* sX, RefitLane& w,
-                                           TrkState& p, T* C, double& chi2, int& nupd, bool& ok, uint32_t& flags,
-                                           LocalTally& tl) {
+                                           TrkState& p, double* D, float* C, double& chi2, int& nupd, bool& ok,
+                                           uint32_t& flags, LocalTally& tl) {
   const int r = p.row - 1;
   if (r < w.r_in) return false;
-  if (!propagate<T>(p, C, r, sX[r], kc, flags)) {
+  const bool zone = nupd < kc.fp64_updates;
+  if (!propagate_any(p, zone, D, C, r, sX[r], kc, flags)) {
     ok = false;
     return false;
   }
-  tl.on_prop<T>();
-  if (w.cur >= 0 && w.hr[w.cur] == r) {
-    const float2 P = __ldg(g.yz + w.h[w.cur]);
-    chi2 += kalman_update<T>(p, C, P.x, P.y, meas_var<T>(kc));
-    tl.on_upd<T>();
+  tl.prop++;
+  tl.prop64 += zone;
+  if (w.cur_row == r) {
+    const float2 P = w.cur_yz;
+    chi2 += update_any(p, zone, D, C, P.x, P.y, kc);
+    if (zone) tl.upd64++;
+    else tl.upd32++;
     nupd++;
+    if (zone && nupd == kc.fp64_updates) {
+#pragma unroll
+      for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+    }
     w.j++;
     w.advance();
   }
@@ -139,10 +201,11 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
                                                const uint8_t* __restrict__ hrow, const float* __restrict__ f_par,
                                                const float* __restrict__ f_zref, const float* __restrict__ f_cov,
                                                const double* __restrict__ f_chi2,
-                                               const uint64_t* __restrict__ owner,
-                                               const int32_t* __restrict__ toff, const int32_t* __restrict__ perm,
-                                               KConst kc, tpc_track* __restrict__ out,
-                                               int32_t* __restrict__ track_clusters, Counts* cn) {
+                                               const uint32_t* __restrict__ own_mask,
+                                               const int32_t* __restrict__ own_rng,
+                                               const int32_t* __restrict__ nown_t,
+                                               const int32_t* __restrict__ toff, KConst kc,
+                                               tpc_track* __restrict__ out, Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
   __syncthreads();
@@ -150,24 +213,21 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
   const int32_t M = cn->n_tracks;
   const int ZONE = kc.fp64_updates;
   LocalTally tl;
+  double D[15];  // FP64-zone covariance (local memory: its operations are out of line)
+  float C[15];
   for (int64_t m = gtid(); m < M; m += gstride()) {
     const int t = track_tl[m];
     RefitLane w;
     w.n = f_n[t];
     w.nf = f_nf[t];
-    w.key = track_key(w.n, t);
     w.h = hits + (int64_t)t * NROW;
     w.hr = hrow + (int64_t)t * NROW;
-    w.owner = (const unsigned long long*)owner;
-    // owned rows
-    int nown = 0, r_out = -1;
-    w.r_in = NROW;
-    for (int i = 0; i < w.n; i++)
-      if (__ldg(w.owner + w.h[i]) == w.key) {
-        r_out = max(r_out, (int)w.hr[i]);
-        w.r_in = min(w.r_in, (int)w.hr[i]);
-        nown++;
-      }
+    w.yz = g.yz;
+#pragma unroll
+    for (int k = 0; k < OWN_WORDS; k++) w.m[k] = own_mask[t * OWN_WORDS + k];
+    const int rng = own_rng[t], nown = nown_t[t];
+    const int r_out = rng >> 16;
+    w.r_in = rng & 0xFFFF;
     const int unit = __ldg(g.rs_of + w.h[0]) / NROW;
     uint32_t flags = 0;
     TrkState p;
@@ -179,33 +239,29 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
     for (int r = p.row + step; ok && (step > 0 ? r <= r_out : r >= r_out); r += step)
       ok = prop_state(p, r, sX[r], kc, flags, nullptr);
     double chi2 = 0.0;
-    float C[15];
     if (ok) {
       w.j = 0;
       w.advance();  // the outermost owned hit, on row r_out
       int nupd = 0;
       bool go = true;
-      const float2 P = __ldg(g.yz + w.h[w.cur]);
-      if (ZONE > 0) {
-        double D[15];
-        cov_seed<double>(D, kc);
-        chi2 += kalman_update<double>(p, D, P.x, P.y, kc.Vd);
-        tl.on_upd<double>();
-        nupd = 1;
-        w.j++;
-        w.advance();
-        while (go && nupd < ZONE) go = refit_step<double>(g, kc, sX, w, p, D, chi2, nupd, ok, flags, tl);
+      cov_seed<double>(D, kc);
+      cov_seed<float>(C, kc);
+      const bool zone0 = ZONE > 0;
+      chi2 += update_any(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc);
+      if (zone0) tl.upd64++;
+      else tl.upd32++;
+      nupd = 1;
+      if (zone0 && nupd == ZONE) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
-      } else {
-        cov_seed<float>(C, kc);
-        chi2 += kalman_update<float>(p, C, P.x, P.y, kc.V);
-        tl.on_upd<float>();
-        nupd = 1;
-        w.j++;
-        w.advance();
       }
-      while (go) go = refit_step<float>(g, kc, sX, w, p, C, chi2, nupd, ok, flags, tl);
+      w.j++;
+      w.advance();
+      while (go) go = refit_step(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
+      if (nupd < ZONE) {
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      }
     }
     tpc_track tr;
     if (ok) {
@@ -241,15 +297,6 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
     tr.cluster_offset = toff[m];
     tr.flags = (int32_t)flags;
     out[m] = tr;
-    // owned clusters in load order, innermost row first: backward list from
-    // its end, then forward list from its start
-    if (track_clusters) {
-      int wpos = toff[m];
-      for (int j = w.n - 1; j >= w.nf; j--)
-        if (__ldg(w.owner + w.h[j]) == w.key) track_clusters[wpos++] = __ldg(perm + w.h[j]);
-      for (int j = 0; j < w.nf; j++)
-        if (__ldg(w.owner + w.h[j]) == w.key) track_clusters[wpos++] = __ldg(perm + w.h[j]);
-    }
   }
   tl.flush(cn);
 }

@@ -78,6 +78,7 @@ struct Layout {
       cend, owner, cluster_track, track_clusters;
   size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
   size_t bin_cnt, bin_start;
+  size_t own_mask, own_rng;
   size_t tl_start, tl_len, tl_end, f_n, f_nf, f_nb, f_flags, f_row, hits, hrow, f_par, f_zref, f_cov, f_chi2, keep,
       tidx, nown, tl_track, track_tl, tcount, toff, tracks;
   size_t parts;
@@ -145,6 +146,8 @@ Layout make_layout(const Caps& c) {
   L.keep = take(4 * (T + 1));
   L.tidx = take(4 * (T + 1));
   L.nown = take(4 * T);
+  L.own_mask = take(4 * OWN_WORDS * T);
+  L.own_rng = take(4 * T);
   L.tl_track = take(4 * T);
   L.track_tl = take(4 * M);
   L.tcount = take(4 * (M + 1));
@@ -439,8 +442,10 @@ void enqueue_find(tpc_ctx* ctx) {
   k_fill32<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.cluster_track), -1, cn);
   k_own<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, ctx->ptr<uint64_t>(L.owner),
                           cn);
-  k_keep<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
-                           ctx->kc, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.nown), cn);
+  k_keep<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint8_t>(L.hrow),
+                           ctx->ptr<uint64_t>(L.owner), ctx->kc, ctx->ptr<int32_t>(L.keep),
+                           ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.own_rng),
+                           cn);
   scan(ctx, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), LenSrc{&cn->n_tracklets, 0, 0}, nullptr);
   k_assign<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
                              ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), ctx->ptr<int32_t>(L.perm),
@@ -466,8 +471,12 @@ void enqueue_fit(tpc_ctx* ctx) {
       grid_view(ctx), ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.f_nf),
       ctx->ptr<int32_t>(L.f_row), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint8_t>(L.hrow), ctx->ptr<float>(L.f_par),
       ctx->ptr<float>(L.f_zref), ctx->ptr<float>(L.f_cov), ctx->ptr<double>(L.f_chi2),
-      ctx->ptr<uint64_t>(L.owner), ctx->ptr<int32_t>(L.toff), ctx->ptr<int32_t>(L.perm), ctx->kc,
-      ctx->ptr<tpc_track>(L.tracks), ctx->ptr<int32_t>(L.track_clusters), cn);
+      ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.own_rng), ctx->ptr<int32_t>(L.nown),
+      ctx->ptr<int32_t>(L.toff), ctx->kc, ctx->ptr<tpc_track>(L.tracks), cn);
+  k_track_clusters<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
+                                     ctx->ptr<int32_t>(L.f_nf), ctx->ptr<int32_t>(L.hits),
+                                     ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.toff),
+                                     ctx->ptr<int32_t>(L.perm), ctx->ptr<int32_t>(L.track_clusters), cn);
   cudaMemcpyAsync(ctx->h_counts, cn, sizeof(Counts), cudaMemcpyDeviceToHost, s);
   ctx->mark(6);
   ctx->prof_valid = ctx->prof;
