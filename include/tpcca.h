@@ -221,6 +221,29 @@ int tpc_get_work(tpc_ctx *ctx, uint64_t work[5]);
 int tpc_set_trace(tpc_ctx *ctx, int32_t tracklet);
 int tpc_get_trace(tpc_ctx *ctx, float *out, int32_t cap_records, int32_t *n_records);
 
+/* ------------------------------------------------- allocation-free variant */
+/* The paper has no counterpart to this entry point; it serves callers that
+ * must not allocate device memory (code running under a memory budget owned
+ * by someone else, inside an allocator hook, or in a server that forbids
+ * CUDA allocations once running).  It computes the per-row-sector records
+ * of the grid stage -- the same 32-byte {z_lo, z_hi, inv_y, inv_z, n_y, n_z,
+ * bin_base, count} records as TPC_ITEM_RS_PARAMS -- for the clusters at
+ * d_clusters (device memory, n records in load order, requests as in
+ * tpc_load_batch with host req_offsets), writing n_req*36*159 records to
+ * d_params_out (device memory, caller-allocated).  Its counters live in one
+ * file-scope device array of about 0.73 MB that every GPU loading the
+ * library keeps until exit; no call allocates or frees device memory.
+ * Limits: 1 <= n_req <= 8 (TPC_EINVAL beyond), n < 2^31 - 1.
+ * The first call on a device looks up the array's device address and
+ * uploads the row geometry with that device current; make that first call
+ * before any stream capture.  Work is enqueued on cuda_stream (NULL: the
+ * default stream) and the call waits for it: it returns TPC_EINVAL when a
+ * cluster fails validation, TPC_ECUDA on a CUDA error, TPC_OK otherwise.
+ * Every call clears and reuses the same array, so calls that overlap on the
+ * GPU (other streams, other host threads) race with each other. */
+int tpc_row_params_noalloc(const tpc_cluster *d_clusters, int64_t n, const int64_t *req_offsets, int32_t n_req,
+                           void *d_params_out, void *cuda_stream);
+
 /* ------------------------------------------------------ tuning (autotuner) */
 /* Threads per block of the cluster-, row-sector- and tracklet-parallel
  * kernels and CTAs per SM of the persistent follow/refit launches.  0 keeps

@@ -89,6 +89,7 @@ def load_library(path: str | None = None):
         "tpc_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
         "tpc_get_stage_times": ([_VP, _VP], ctypes.c_int),
         "tpc_get_work": ([_VP, _VP], ctypes.c_int),
+        "tpc_row_params_noalloc": ([_VP, _I64, _VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_set_trace": ([_VP, _I32], ctypes.c_int),
         "tpc_get_trace": ([_VP, _VP, _I32, _VP], ctypes.c_int),
     }
@@ -295,3 +296,19 @@ class Tracker:
         else:
             self.find().fit()
         return self.get()
+
+
+def row_params_noalloc(d_clusters, req_offsets=None, out=None, stream=None) -> int:
+    """Per-row-sector grid records of device-resident clusters without any
+    device allocation by the library (tpc_row_params_noalloc): for callers
+    that may not allocate, e.g. under a memory budget owned by their host
+    framework.  d_clusters and out are CUDA tensors (out: n_req*36*159*32
+    bytes, caller-allocated).  Returns the status code."""
+    lib = load_library()
+    n = d_clusters.numel() * d_clusters.element_size() // 16
+    off = np.ascontiguousarray(np.asarray(req_offsets if req_offsets is not None else [0, n], dtype=np.int64))
+    sp = None
+    if stream is not None:
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return lib.tpc_row_params_noalloc(d_clusters.data_ptr() if n else None, n, off.ctypes.data, len(off) - 1,
+                                      out.data_ptr(), sp)

@@ -858,3 +858,185 @@ int tpc_set_tuning(tpc_ctx* ctx, int block_clusters, int block_follow, int ctas_
 }
 
 }  // extern "C"
+
+// =========================================================== no-alloc variant
+//
+// tpc_row_params_noalloc: the per-row-sector pass of the grid stage (cluster
+// count, exact z range, bin parameters and bin bases of every (request,
+// sector, row)) for callers that cannot allocate device memory -- code that
+// runs inside a host-side memory budget it does not own, an allocator hook,
+// or a process whose CUDA allocations are forbidden once it is serving.  It
+// writes the same RsParams records as the grid stage of tpc_find_tracks,
+// but its counters live in the file-scope array below instead of an arena.
+namespace {
+
+constexpr int NOALLOC_MAX_REQ = 8;
+constexpr int NOALLOC_MAX_RS = NOALLOC_MAX_REQ * NSEC * NROW;  // 45,792 row-sectors
+
+struct NoallocScratch {
+  uint32_t status;
+  uint32_t pad[63];
+  int64_t req_off[NOALLOC_MAX_REQ + 1];
+  int64_t pad2[7];
+  int32_t cnt[NOALLOC_MAX_RS];
+  uint32_t zmin[NOALLOC_MAX_RS];
+  uint32_t zmax[NOALLOC_MAX_RS];
+  int32_t nbins[NOALLOC_MAX_RS];
+};
+
+}  // namespace
+
+// About 0.73 MB on every GPU that loads the library, kept until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoallocScratch)];
+
+namespace {
+
+__global__ void k_na_clear(NoallocScratch* s, int nrs) {
+  for (int64_t i = gtid(); i < nrs; i += gstride()) {
+    s->cnt[i] = 0;
+    s->zmin[i] = 0xFFFFFFFFu;
+    s->zmax[i] = 0u;
+  }
+  if (gtid() == 0) s->status = 0u;
+}
+
+__global__ void k_na_count(const tpc_cluster* __restrict__ in, int64_t n, int n_req, NoallocScratch* s) {
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const int4 raw = __ldg(reinterpret_cast<const int4*>(in) + i);
+    const float z = __int_as_float(raw.y), y = __int_as_float(raw.x);
+    const uint32_t row = (uint32_t)raw.z & 0xFFFFu, sec = (uint32_t)raw.z >> 16;
+    if (row >= NROW || sec >= NSEC || !isfinite(y) || !isfinite(z)) {
+      atomicOr(&s->status, ST_EINVAL);
+      continue;
+    }
+    int lo = 0, hi = n_req - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s->req_off[mid] <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const int rs = (lo * NSEC + (int)sec) * NROW + (int)row;
+    atomicAdd(&s->cnt[rs], 1);
+    const uint32_t zo = f2ord(z);
+    atomicMin(&s->zmin[rs], zo);
+    atomicMax(&s->zmax[rs], zo);
+  }
+}
+
+// Bin parameters, the same binary32 operation sequence as the grid stage.
+__global__ void k_na_params(NoallocScratch* s, int nrs, RsParams* __restrict__ out) {
+  for (int64_t rs = gtid(); rs < nrs; rs += gstride()) {
+    const int row = (int)(rs % NROW);
+    const int n = s->cnt[rs];
+    const float zl = n ? ord2f(s->zmin[rs]) : 0.0f, zh = n ? ord2f(s->zmax[rs]) : 0.0f;
+    const float yh = g_row_yhi[row], yl = -yh;
+    const float wy = __fsub_rn(yh, yl);
+    const float dz = __fsub_rn(zh, zl);
+    const float area = __fmul_rn(wy, fmaxf(dz, 1.0f));
+    float sz = __fsqrt_rn(__fdiv_rn(__fmul_rn(area, 2.0f), __int2float_rn(n > 1 ? n : 1)));
+    sz = fminf(fmaxf(sz, 1.0f), 64.0f);
+    int ny = __float2int_rz(__fdiv_rn(wy, sz)) + 1;
+    int nz = __float2int_rz(__fdiv_rn(dz, sz)) + 1;
+    if (ny > 256) ny = 256;
+    if (nz > 4096) nz = 4096;
+    RsParams p;
+    p.z_lo = zl;
+    p.z_hi = zh;
+    p.inv_y = __fdiv_rn(__int2float_rn(ny), wy);
+    p.inv_z = __fdiv_rn(__int2float_rn(nz), fmaxf(dz, 1e-3f));
+    p.n_y = ny;
+    p.n_z = nz;
+    p.bin_base = 0;
+    p.count = n;
+    out[rs] = p;
+    s->nbins[rs] = ny * nz;
+  }
+}
+
+// Exclusive prefix sum of the bin counts into bin_base (one block).
+__global__ void __launch_bounds__(1024) k_na_binbase(const NoallocScratch* s, int nrs, RsParams* __restrict__ out) {
+  __shared__ int ws[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int base = 0; base < nrs; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nrs ? s->nbins[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x += t;
+    }
+    if (lane == 31) ws[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      int w = ws[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xFFFFFFFFu, w, o);
+        if (lane >= o) w += t;
+      }
+      ws[lane] = w;
+    }
+    __syncthreads();
+    const int incl = x + (warp > 0 ? ws[warp - 1] : 0);
+    if (i < nrs) out[i].bin_base = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += ws[31];
+    __syncthreads();
+  }
+}
+
+std::mutex g_na_mutex;
+std::vector<void*> g_na_addr;  // device address of g_noalloc_scratch, per device
+
+}  // namespace
+
+extern "C" int tpc_row_params_noalloc(const tpc_cluster* d_clusters, int64_t n, const int64_t* req_offsets,
+                                      int32_t n_req, void* d_params_out, void* cuda_stream) {
+  if (n_req < 1 || n_req > NOALLOC_MAX_REQ || !req_offsets || req_offsets[0] != 0 || req_offsets[n_req] != n ||
+      n < 0 || n >= 0x7FFFFFFF || (n > 0 && !d_clusters) || !d_params_out)
+    return TPC_EINVAL;
+  for (int32_t q = 0; q < n_req; q++)
+    if (req_offsets[q + 1] < req_offsets[q]) return TPC_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TPC_ECUDA;
+  void* addr = nullptr;
+  {
+    // once per device, with that device current: the device address of the
+    // scratch array (its name is only a host-side stand-in in host code)
+    std::lock_guard<std::mutex> lk(g_na_mutex);
+    if ((int)g_na_addr.size() <= dev) g_na_addr.resize(dev + 1, nullptr);
+    if (!g_na_addr[dev]) {
+      if (ensure_device_tables(dev) != cudaSuccess) return TPC_ECUDA;
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TPC_ECUDA;
+      g_na_addr[dev] = p;
+    }
+    addr = g_na_addr[dev];
+  }
+  NoallocScratch* s = reinterpret_cast<NoallocScratch*>(addr);
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int nrs = n_req * NSEC * NROW;
+  RsParams* out = reinterpret_cast<RsParams*>(d_params_out);
+  int64_t off_host[NOALLOC_MAX_REQ + 1];
+  memcpy(off_host, req_offsets, sizeof(int64_t) * (n_req + 1));
+  if (cudaMemcpyAsync(s->req_off, off_host, sizeof(int64_t) * (n_req + 1), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return TPC_ECUDA;
+  k_na_clear<<<(nrs + 255) / 256, 256, 0, st>>>(s, nrs);
+  if (n > 0) {
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 148 * 16);
+    k_na_count<<<blocks, 256, 0, st>>>(d_clusters, n, n_req, s);
+  }
+  k_na_params<<<(nrs + 255) / 256, 256, 0, st>>>(s, nrs, out);
+  k_na_binbase<<<1, 1024, 0, st>>>(s, nrs, out);
+  if (cudaGetLastError() != cudaSuccess) return TPC_ECUDA;
+  uint32_t status = 0;
+  if (cudaMemcpyAsync(&status, &s->status, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return TPC_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TPC_ECUDA;
+  return (status & ST_EINVAL) ? TPC_EINVAL : TPC_OK;
+}
