@@ -85,9 +85,10 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# Kernels launched per step (tpc_run_graph): grid 10 + 3 scans x 3, links 2 +
-# 1 scan, follow 1, selection 5 + 1 scan, refit 2 + 1 scan.
-KERNELS_PER_STEP = 7 + 3 * 3 + 2 + 3 + 1 + 5 + 3 + 2 + 3
+# Kernels launched per step (tpc_run_graph): grid 7 + 3 scans x 3 kernels,
+# neighbours 1, links/tracklets 2 + 1 scan, follow 1, selection 5 + 1 scan,
+# refit 3 + 1 scan.
+KERNELS_PER_STEP = 7 + 9 + 1 + 2 + 3 + 1 + 5 + 3 + 3 + 3
 
 # Algorithmic FP32 work of the Kalman kernels (counted from the source, per
 # unit of the device work counters): a propagation with covariance transport
