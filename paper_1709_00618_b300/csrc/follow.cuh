@@ -112,7 +112,7 @@ struct Lane {
   // backward output: state after the last update
   TrkState sp;
   float sC[15];
-  double schi2;
+  Chi2Acc schi2;
 };
 
 // Trace line of one Kalman update (out of line: executed for one tracklet).
@@ -129,10 +129,12 @@ __device__ __noinline__ void trace_line(Counts* cn, float* trace, int cap, float
 
 // Kalman update of the lane's state (covariance in D during the zone, else
 // in C); records a trace line when the lane is traced.
+template <bool Z>
 __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState& p, bool zone, double* D, float* C,
-                                            float2 P, double& chi2, int pass) {
+                                            float2 P, Chi2Acc& chi2, int pass) {
+  zone = Z && zone;
   const float r0 = residual_y(p, P.x), r1 = residual_z(p, P.y);
-  chi2 += update_any(p, zone, D, C, P.x, P.y, kc);
+  chi2.add(update_any(p, zone, D, C, P.x, P.y, kc));
   w.nupd++;
   if (zone && w.nupd == kc.fp64_updates) {
 #pragma unroll
@@ -141,12 +143,14 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
   if (w.tr)
     trace_line(w.cn, kc.trace, kc.trace_cap, (float)pass, (float)p.row, (float)w.nupd, p.y + p.yl,
                p.zref + (p.z + p.zl), p.s + p.sl, p.t, p.q, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2],
-               zone ? (float)D[5] : C[5], zone ? (float)D[9] : C[9], zone ? (float)D[14] : C[14], (float)chi2, r0,
-               r1);
+               zone ? (float)D[5] : C[5], zone ? (float)D[9] : C[9], zone ? (float)D[14] : C[14],
+               (float)chi2.value(), r0, r1);
 }
 
+template <bool Z>
 __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zone, const double* D, const float* C,
-                                            double chi2) {
+                                            const Chi2Acc& chi2) {
+  zone = Z && zone;
   w.sp = p;
 #pragma unroll
   for (int i = 0; i < 15; i++) w.sC[i] = zone ? (float)D[i] : C[i];
@@ -155,13 +159,14 @@ __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zon
 
 // One forward row step; false ends the pass.  The covariance is in D while
 // fewer than fp64_updates updates have been made since the seed.
+template <bool Z>
 __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __restrict__ up_m, const KConst& kc,
                                          const float* sX, const float* sYH, Lane& w, TrkState& p, double* D,
-                                         float* C, double& chi2, LocalTally& tl) {
+                                         float* C, Chi2Acc& chi2, LocalTally& tl) {
   const int r = p.row + 1;
   if (r >= NROW) return false;
   const bool chain = w.i < w.L;
-  const bool zone = w.nupd < kc.fp64_updates;
+  const bool zone = Z && w.nupd < kc.fp64_updates;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (chain) w.seed_fail = true;
     return false;
@@ -180,7 +185,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
     if (c < 0) return ++w.misses < kc.max_miss;
   }
   const float2 P = __ldg(g.yz + c);
-  lane_update(w, kc, p, zone, D, C, P, chi2, 0);
+  lane_update<Z>(w, kc, p, zone, D, C, P, chi2, 0);
   if (zone) tl.upd64++;
   else tl.upd32++;
   w.hits[w.nf] = c;
@@ -193,11 +198,12 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
 }
 
 // One backward row step; false ends the pass.
+template <bool Z>
 __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, const float* sX, const float* sYH,
-                                         Lane& w, TrkState& p, double* D, float* C, double& chi2, LocalTally& tl) {
+                                         Lane& w, TrkState& p, double* D, float* C, Chi2Acc& chi2, LocalTally& tl) {
   const int r = p.row - 1;
   if (r < 0) return false;
-  const bool zone = w.nupd < kc.fp64_updates;
+  const bool zone = Z && w.nupd < kc.fp64_updates;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (r >= w.r0) w.flags |= TF_BACK_FAIL;
     return false;
@@ -220,10 +226,10 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
     w.misses = 0;
   }
   const float2 P = __ldg(g.yz + c);
-  lane_update(w, kc, p, zone, D, C, P, chi2, 1);
+  lane_update<Z>(w, kc, p, zone, D, C, P, chi2, 1);
   if (zone) tl.upd64++;
   else tl.upd32++;
-  keep_output(w, p, w.nupd <= kc.fp64_updates && w.nupd < kc.fp64_updates, D, C, chi2);
+  keep_output<Z>(w, p, w.nupd < kc.fp64_updates, D, C, chi2);
   return true;
 }
 
@@ -233,21 +239,63 @@ __device__ __forceinline__ void reseed_cov(const KConst& kc, double* D, float* C
   cov_seed<float>(C, kc);
 }
 
-__global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __restrict__ tl_start,
-                                                const int32_t* __restrict__ tl_len,
-                                                const int32_t* __restrict__ tl_end,
-                                                const int32_t* __restrict__ up_m, KConst kc, FollowOut o,
-                                                Counts* cn) {
-  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+// Tracklet state parked in global memory (L2-resident) between the phase
+// kernels of the follow stage.
+struct FollowWork {
+  Lane w;
+  TrkState p;
+  float C[15];
+  Chi2Acc chi2;
+  int32_t go;
+  int32_t pad[3];
+};
+
+__device__ __forceinline__ void work_store(FollowWork* W, int64_t t, const Lane& w, const TrkState& p,
+                                           const float* C, const Chi2Acc& chi2, bool go) {
+  FollowWork& s = W[t];
+  s.w = w;
+  s.p = p;
+#pragma unroll
+  for (int i = 0; i < 15; i++) s.C[i] = C[i];
+  s.chi2 = chi2;
+  s.go = go;
+}
+__device__ __forceinline__ bool work_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
+                                          Chi2Acc& chi2) {
+  const FollowWork& s = W[t];
+  w = s.w;
+  p = s.p;
+#pragma unroll
+  for (int i = 0; i < 15; i++) C[i] = s.C[i];
+  chi2 = s.chi2;
+  return s.go != 0;
+}
+
+// Tracklet index for a lane of a refilling (persistent) phase kernel.
+__device__ __forceinline__ int64_t fetch_work(int32_t* counter) { return (int64_t)atomicAdd(counter, 1); }
+
+__device__ __forceinline__ void load_tables(float* sX, float* sYH) {
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) {
     sX[i] = g_row_x[i];
     sYH[i] = g_row_yhi[i];
   }
   __syncthreads();
+}
+
+// Phase 1: seed and the forward pass while its covariance is in FP64 (all
+// lanes of a warp start their zone together).
+__global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __restrict__ tl_start,
+                                                   const int32_t* __restrict__ tl_len,
+                                                   const int32_t* __restrict__ tl_end,
+                                                   const int32_t* __restrict__ up_m, KConst kc, FollowOut o,
+                                                   FollowWork* W, Counts* cn) {
+  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  load_tables(sX, sYH);
   if (fatal(cn)) return;
+  if (gtid() == 0) cn->follow_next = 0;  // work counter of phase 2
   const int32_t T = cn->n_tracklets;
   LocalTally tl;
-  double D[15];  // FP64-zone covariance (local memory: its operations are out of line)
+  double D[15];
   float C[15];
   for (int64_t t = gtid(); t < T; t += gstride()) {
     Lane w;
@@ -278,60 +326,173 @@ __global__ void __launch_bounds__(128) k_follow(GridView g, const int32_t* __res
     w.hrow[0] = (uint8_t)w.r0;
     w.nf = 1;
     w.nb = 0;
-    double chi2 = 0.0;
-    // ---- forward pass
+    w.kf = 0;
+    Chi2Acc chi2;
+    chi2.reset();
     reseed_cov(kc, D, C);
     w.nupd = 0;
-    lane_update(w, kc, p, kc.fp64_updates > 0, D, C, P0, chi2, 0);
-    if (kc.fp64_updates > 0) tl.upd64++;
+    const bool zone0 = kc.fp64_updates > 0;
+    lane_update<true>(w, kc, p, zone0, D, C, P0, chi2, 0);
+    if (zone0) tl.upd64++;
     else tl.upd32++;
     w.fwd = p;
     bool go = true;
-    while (go) go = fwd_step(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
-    // ---- backward pass: forward state at the outermost cluster, fresh covariance
+    while (go && w.nupd < kc.fp64_updates) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+    if (w.nupd < kc.fp64_updates) {
+#pragma unroll
+      for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+    }
+    work_store(W, t, w, p, C, chi2, go);
+  }
+  tl.flush(cn);
+}
+
+// Phase 2: the rest of the forward pass (covariance in FP32); a lane that
+// finishes a tracklet takes the next one, so no lane idles while the longest
+// tracklet of its warp is still running.
+__global__ void __launch_bounds__(128) k_follow_p2(GridView g, const int32_t* __restrict__ up_m, KConst kc,
+                                                   FollowOut o, FollowWork* W, Counts* cn) {
+  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  load_tables(sX, sYH);
+  if (fatal(cn)) return;
+  const int32_t T = cn->n_tracklets;
+  LocalTally tl;
+  double D[15];  // unused in this phase (the zone is over)
+  float C[15];
+  Lane w;
+  TrkState p;
+  Chi2Acc chi2;
+  chi2.reset();
+  int64_t t = fetch_work(&cn->follow_next);
+  bool go = false;
+  if (t < T) go = work_load(W, t, w, p, C, chi2);
+  while (t < T) {
+    if (go) go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+    if (!go) {
+      work_store(W, t, w, p, C, chi2, false);
+      t = fetch_work(&cn->follow_next);
+      if (t < T) {
+        work_load(W, t, w, p, C, chi2);
+        w.hits = o.hits + t * NROW;
+        w.hrow = o.hrow + t * NROW;
+        w.cn = cn;
+        go = !w.seed_fail && W[t].go;
+      }
+    }
+  }
+  tl.flush(cn);
+}
+
+// Phase 3: re-seed at the outermost forward cluster and run the backward
+// pass while its covariance is in FP64.
+__global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W, Counts* cn) {
+  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  load_tables(sX, sYH);
+  if (fatal(cn)) return;
+  if (gtid() == 0) cn->follow_next = 0;  // work counter of phase 4
+  const int32_t T = cn->n_tracklets;
+  LocalTally tl;
+  double D[15];
+  float C[15];
+  for (int64_t t = gtid(); t < T; t += gstride()) {
+    Lane w;
+    TrkState p;
+    Chi2Acc chi2;
+    work_load(W, t, w, p, C, chi2);
+    w.hits = o.hits + t * NROW;
+    w.hrow = o.hrow + t * NROW;
+    w.cn = cn;
+    bool go = false;
     if (!w.seed_fail) {
       p = w.fwd;
-      chi2 = 0.0;
+      chi2.reset();
       w.kf = w.nf - 2;
       w.misses = 0;
       reseed_cov(kc, D, C);
       w.nupd = 0;
       const bool zone0 = kc.fp64_updates > 0;
-      lane_update(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
+      lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
       if (zone0) tl.upd64++;
       else tl.upd32++;
-      keep_output(w, p, w.nupd < kc.fp64_updates, D, C, chi2);
+      keep_output<true>(w, p, w.nupd < kc.fp64_updates, D, C, chi2);
       go = true;
-      while (go) go = bwd_step(g, kc, sX, sYH, w, p, D, C, chi2, tl);
+      while (go && w.nupd < kc.fp64_updates) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
+      if (w.nupd < kc.fp64_updates) {
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      }
     }
-    if (w.seed_fail) {
-      o.n[t] = 0;
-      o.nf[t] = 0;
-      o.nb[t] = 0;
-      o.flags[t] = (int32_t)(w.flags | TF_SEED_FAIL);
-      o.row[t] = w.r0;
+    work_store(W, t, w, p, C, chi2, go);
+  }
+  tl.flush(cn);
+}
+
+__device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t t, const Lane& w, float zref0) {
+  if (w.seed_fail) {
+    o.n[t] = 0;
+    o.nf[t] = 0;
+    o.nb[t] = 0;
+    o.flags[t] = (int32_t)(w.flags | TF_SEED_FAIL);
+    o.row[t] = w.r0;
 #pragma unroll
-      for (int i = 0; i < 5; i++) o.par[t * 5 + i] = 0.0f;
+    for (int i = 0; i < 5; i++) o.par[t * 5 + i] = 0.0f;
 #pragma unroll
-      for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = 0.0f;
-      o.zref[t] = P0.y;
-      o.chi2[t] = 0.0;
-      continue;
+    for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = 0.0f;
+    o.zref[t] = zref0;
+    o.chi2[t] = 0.0;
+    return;
+  }
+  o.n[t] = w.nf + w.nb;
+  o.nf[t] = w.nf;
+  o.nb[t] = w.nb;
+  o.flags[t] = (int32_t)w.flags;
+  o.row[t] = w.sp.row;
+  o.par[t * 5 + 0] = w.sp.y + w.sp.yl;
+  o.par[t * 5 + 1] = w.sp.z + w.sp.zl;
+  o.par[t * 5 + 2] = w.sp.s + w.sp.sl;
+  o.par[t * 5 + 3] = w.sp.t;
+  o.par[t * 5 + 4] = w.sp.q;
+  o.zref[t] = w.sp.zref;
+#pragma unroll
+  for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = w.sC[i];
+  o.chi2[t] = w.schi2.value();
+}
+
+// Phase 4: the rest of the backward pass (FP32, lanes refill) and the
+// outputs.
+__global__ void __launch_bounds__(128) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
+                                                   FollowOut o, FollowWork* W, Counts* cn) {
+  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  load_tables(sX, sYH);
+  if (fatal(cn)) return;
+  const int32_t T = cn->n_tracklets;
+  LocalTally tl;
+  double D[15];  // unused in this phase (the zone is over)
+  float C[15];
+  Lane w;
+  TrkState p;
+  Chi2Acc chi2;
+  chi2.reset();
+  int64_t t = fetch_work(&cn->follow_next);
+  bool go = false;
+  if (t < T) {
+    go = work_load(W, t, w, p, C, chi2);
+    w.hits = o.hits + t * NROW;
+    w.hrow = o.hrow + t * NROW;
+    w.cn = cn;
+  }
+  while (t < T) {
+    if (go) go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
+    if (!go) {
+      write_follow_output(o, t, w, __ldg(g.yz + tl_start[t]).y);
+      t = fetch_work(&cn->follow_next);
+      if (t < T) {
+        go = work_load(W, t, w, p, C, chi2);
+        w.hits = o.hits + t * NROW;
+        w.hrow = o.hrow + t * NROW;
+        w.cn = cn;
+      }
     }
-    o.n[t] = w.nf + w.nb;
-    o.nf[t] = w.nf;
-    o.nb[t] = w.nb;
-    o.flags[t] = (int32_t)w.flags;
-    o.row[t] = w.sp.row;
-    o.par[t * 5 + 0] = w.sp.y + w.sp.yl;
-    o.par[t * 5 + 1] = w.sp.z + w.sp.zl;
-    o.par[t * 5 + 2] = w.sp.s + w.sp.sl;
-    o.par[t * 5 + 3] = w.sp.t;
-    o.par[t * 5 + 4] = w.sp.q;
-    o.zref[t] = w.sp.zref;
-#pragma unroll
-    for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = w.sC[i];
-    o.chi2[t] = w.schi2;
   }
   tl.flush(cn);
 }

@@ -102,7 +102,7 @@ __device__ __forceinline__ float residual_z(const TrkState& p, float mz) {
 // Kalman update with the measurement (my, mz) (mz absolute); returns the
 // chi2 increment.
 template <typename T>
-__device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, float mz, T V) {
+__device__ __forceinline__ float kalman_update(TrkState& p, T* C, float my, float mz, T V) {
   const float r0 = residual_y(p, my), r1 = residual_z(p, mz);
   const T S00 = C[0] + V, S01 = C[1], S11 = C[2] + V;
   const T idet = T(1) / (S00 * S11 - S01 * S01);
@@ -134,7 +134,7 @@ __device__ __forceinline__ double kalman_update(TrkState& p, T* C, float my, flo
     for (int j = 0; j <= i; j++) C[TPC_CI(i, j)] -= g0[i] * k0[j] + g1[i] * k1[j];
   // chi2 increment r^T S^-1 r (binary32), accumulated by the caller in FP64
   const float i00 = (float)I00, i01 = (float)I01, i11 = (float)I11;
-  return (double)(r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1));
+  return r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
 }
 
 // Propagation of the state to row2 at radius x2.  Returns false when
@@ -228,7 +228,7 @@ __device__ __noinline__ UpdOut kalman_update_d(double* D, float r0, float r1, do
 }
 
 // One Kalman update of the state with covariance in FP64 (zone) or FP32.
-__device__ __forceinline__ double update_any(TrkState& p, bool zone, double* D, float* C, float my, float mz,
+__device__ __forceinline__ float update_any(TrkState& p, bool zone, double* D, float* C, float my, float mz,
                                              const KConst& kc) {
   if (zone) {
     const float r0 = residual_y(p, my), r1 = residual_z(p, mz);
@@ -238,7 +238,7 @@ __device__ __forceinline__ double update_any(TrkState& p, bool zone, double* D, 
     acc2(p.s, p.sl, o.d2);
     p.t += o.d3;
     p.q += o.d4;
-    return (double)o.chi2;
+    return o.chi2;
   }
   return kalman_update<float>(p, C, my, mz, kc.V);
 }
@@ -291,6 +291,29 @@ __device__ __forceinline__ void seed_state(TrkState& p, int row, float x, float 
   p.q = q;
   p.yl = p.zl = p.sl = 0.0f;
 }
+
+// chi2 accumulated in FP64 from binary32 increments: the increments of up to
+// 16 updates are summed in binary32 and then added to the FP64 total, so the
+// FP64 pipe (1/64 of the FP32 rate on this part) sees one add per 16 updates.
+struct Chi2Acc {
+  double total;
+  float part;
+  int n;
+  __device__ __forceinline__ void reset() {
+    total = 0.0;
+    part = 0.0f;
+    n = 0;
+  }
+  __device__ __forceinline__ void add(float x) {
+    part += x;
+    if (++n == 16) {
+      total += (double)part;
+      part = 0.0f;
+      n = 0;
+    }
+  }
+  __device__ __forceinline__ double value() const { return total + (double)part; }
+};
 
 // Work tallies kept in registers by one thread.
 struct LocalTally {

@@ -167,12 +167,13 @@ struct RefitLane {
   }
 };
 
+template <bool Z>
 __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, const float* sX, RefitLane& w,
-                                           TrkState& p, double* D, float* C, double& chi2, int& nupd, bool& ok,
+                                           TrkState& p, double* D, float* C, Chi2Acc& chi2, int& nupd, bool& ok,
                                            uint32_t& flags, LocalTally& tl) {
   const int r = p.row - 1;
   if (r < w.r_in) return false;
-  const bool zone = nupd < kc.fp64_updates;
+  const bool zone = Z && nupd < kc.fp64_updates;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, flags)) {
     ok = false;
     return false;
@@ -181,7 +182,7 @@ __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, 
   tl.prop64 += zone;
   if (w.cur_row == r) {
     const float2 P = w.cur_yz;
-    chi2 += update_any(p, zone, D, C, P.x, P.y, kc);
+    chi2.add(update_any(p, zone, D, C, P.x, P.y, kc));
     if (zone) tl.upd64++;
     else tl.upd32++;
     nupd++;
@@ -195,59 +196,84 @@ __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, 
   return true;
 }
 
-__global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __restrict__ track_tl,
-                                               const int32_t* __restrict__ f_n, const int32_t* __restrict__ f_nf,
-                                               const int32_t* __restrict__ f_row, const int32_t* __restrict__ hits,
-                                               const uint8_t* __restrict__ hrow, const float* __restrict__ f_par,
-                                               const float* __restrict__ f_zref, const float* __restrict__ f_cov,
-                                               const double* __restrict__ f_chi2,
-                                               const uint32_t* __restrict__ own_mask,
-                                               const int32_t* __restrict__ own_rng,
-                                               const int32_t* __restrict__ nown_t,
-                                               const int32_t* __restrict__ toff, KConst kc,
-                                               tpc_track* __restrict__ out, Counts* cn) {
+// Refit state parked between the two refit phases.
+struct RefitWork {
+  RefitLane w;
+  TrkState p;
+  float C[15];
+  Chi2Acc chi2;
+  int32_t nupd, ok, go, flags, r_out, nown, unit, t;
+};
+
+struct RefitIn {
+  const int32_t* track_tl;
+  const int32_t* f_n;
+  const int32_t* f_nf;
+  const int32_t* f_row;
+  const int32_t* hits;
+  const uint8_t* hrow;
+  const float* f_par;
+  const float* f_zref;
+  const float* f_cov;
+  const double* f_chi2;
+  const uint32_t* own_mask;
+  const int32_t* own_rng;
+  const int32_t* nown;
+  const int32_t* toff;
+};
+
+// Phase 1 of the refit: carry the follow state to the outermost owned row
+// (state only), then the updates with the covariance in FP64.
+__global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
   __syncthreads();
   if (fatal(cn)) return;
+  if (gtid() == 0) cn->refit_next = 0;
   const int32_t M = cn->n_tracks;
   const int ZONE = kc.fp64_updates;
   LocalTally tl;
-  double D[15];  // FP64-zone covariance (local memory: its operations are out of line)
+  double D[15];
   float C[15];
-  for (int64_t m = gtid(); m < M; m += gstride()) {
-    const int t = track_tl[m];
+  // warp-uniform loop: every lane runs the same iterations (lanes past the
+  // end idle) so that the warp can be reconverged before its FP64 zone
+  const int64_t stride = gstride();
+  for (int64_t base = gtid() - (threadIdx.x & 31); base < M; base += stride) {
+    const int64_t m = base + (threadIdx.x & 31);
+    const bool valid = m < M;
+    const int t = valid ? in.track_tl[m] : in.track_tl[base];
     RefitLane w;
-    w.n = f_n[t];
-    w.nf = f_nf[t];
-    w.h = hits + (int64_t)t * NROW;
-    w.hr = hrow + (int64_t)t * NROW;
+    w.n = in.f_n[t];
+    w.nf = in.f_nf[t];
+    w.h = in.hits + (int64_t)t * NROW;
+    w.hr = in.hrow + (int64_t)t * NROW;
     w.yz = g.yz;
 #pragma unroll
-    for (int k = 0; k < OWN_WORDS; k++) w.m[k] = own_mask[t * OWN_WORDS + k];
-    const int rng = own_rng[t], nown = nown_t[t];
+    for (int k = 0; k < OWN_WORDS; k++) w.m[k] = in.own_mask[t * OWN_WORDS + k];
+    const int rng = in.own_rng[t];
     const int r_out = rng >> 16;
     w.r_in = rng & 0xFFFF;
-    const int unit = __ldg(g.rs_of + w.h[0]) / NROW;
     uint32_t flags = 0;
     TrkState p;
-    seed_state(p, f_row[t], sX[f_row[t]], f_par[t * 5 + 0], f_zref[t], f_par[t * 5 + 2], f_par[t * 5 + 3],
-               f_par[t * 5 + 4]);
-    p.z = f_par[t * 5 + 1];
-    bool ok = true;
+    seed_state(p, in.f_row[t], sX[in.f_row[t]], in.f_par[t * 5 + 0], in.f_zref[t], in.f_par[t * 5 + 2],
+               in.f_par[t * 5 + 3], in.f_par[t * 5 + 4]);
+    p.z = in.f_par[t * 5 + 1];
+    bool ok = valid;
     const int step = r_out >= p.row ? 1 : -1;
     for (int r = p.row + step; ok && (step > 0 ? r <= r_out : r >= r_out); r += step)
       ok = prop_state(p, r, sX[r], kc, flags, nullptr);
-    double chi2 = 0.0;
+    Chi2Acc chi2;
+    chi2.reset();
+    int nupd = 0;
+    bool go = false;
+    __syncwarp();  // start the FP64 zone with the whole warp
     if (ok) {
       w.j = 0;
       w.advance();  // the outermost owned hit, on row r_out
-      int nupd = 0;
-      bool go = true;
       cov_seed<double>(D, kc);
       cov_seed<float>(C, kc);
       const bool zone0 = ZONE > 0;
-      chi2 += update_any(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc);
+      chi2.add(update_any(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc));
       if (zone0) tl.upd64++;
       else tl.upd32++;
       nupd = 1;
@@ -257,46 +283,110 @@ __global__ void __launch_bounds__(128) k_refit(GridView g, const int32_t* __rest
       }
       w.j++;
       w.advance();
-      while (go) go = refit_step(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
+      go = true;
+      while (go && nupd < ZONE) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
       if (nupd < ZONE) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
       }
     }
-    tpc_track tr;
-    if (ok) {
-      tr.x = sX[w.r_in];
-      tr.par[0] = p.y + p.yl;
-      tr.par[1] = p.zref + (p.z + p.zl);
-      tr.par[2] = p.s + p.sl;
-      tr.par[3] = p.t;
-      tr.par[4] = p.q;
+    if (!valid) continue;
+    RefitWork& s = RW[m];
+    s.w = w;
+    s.p = p;
 #pragma unroll
-      for (int j = 0; j < 15; j++) tr.cov[j] = C[j];
-      tr.chi2 = chi2;
-      tr.first_row = w.r_in;
-    } else {
-      const int fr = f_row[t];
-      tr.x = sX[fr];
-      tr.par[0] = f_par[t * 5 + 0];
-      tr.par[1] = f_zref[t] + f_par[t * 5 + 1];
-      tr.par[2] = f_par[t * 5 + 2];
-      tr.par[3] = f_par[t * 5 + 3];
-      tr.par[4] = f_par[t * 5 + 4];
-      for (int j = 0; j < 15; j++) tr.cov[j] = f_cov[t * 15 + j];
-      tr.chi2 = f_chi2[t];
-      tr.first_row = fr;
-      flags = TF_REFIT_FAIL;
+    for (int i = 0; i < 15; i++) s.C[i] = C[i];
+    s.chi2 = chi2;
+    s.nupd = nupd;
+    s.ok = ok;
+    s.go = go && ok;
+    s.flags = (int32_t)flags;
+    s.r_out = r_out;
+    s.nown = in.nown[t];
+    s.unit = __ldg(g.rs_of + w.h[0]) / NROW;
+    s.t = t;
+  }
+  tl.flush(cn);
+}
+
+__device__ __forceinline__ void write_track(const RefitIn& in, const float* sX, int64_t m, const RefitWork& s,
+                                            const TrkState& p, const float* C, const Chi2Acc& chi2, bool ok,
+                                            uint32_t flags, tpc_track* __restrict__ out) {
+  const int t = s.t;
+  tpc_track tr;
+  if (ok) {
+    tr.x = sX[s.w.r_in];
+    tr.par[0] = p.y + p.yl;
+    tr.par[1] = p.zref + (p.z + p.zl);
+    tr.par[2] = p.s + p.sl;
+    tr.par[3] = p.t;
+    tr.par[4] = p.q;
+#pragma unroll
+    for (int j = 0; j < 15; j++) tr.cov[j] = C[j];
+    tr.chi2 = chi2.value();
+    tr.first_row = s.w.r_in;
+  } else {
+    const int fr = in.f_row[t];
+    tr.x = sX[fr];
+    tr.par[0] = in.f_par[t * 5 + 0];
+    tr.par[1] = in.f_zref[t] + in.f_par[t * 5 + 1];
+    tr.par[2] = in.f_par[t * 5 + 2];
+    tr.par[3] = in.f_par[t * 5 + 3];
+    tr.par[4] = in.f_par[t * 5 + 4];
+    for (int j = 0; j < 15; j++) tr.cov[j] = in.f_cov[t * 15 + j];
+    tr.chi2 = in.f_chi2[t];
+    tr.first_row = fr;
+    flags = TF_REFIT_FAIL;
+  }
+  tr.reserved = 0;
+  tr.ndf = 2 * s.nown - 5;
+  tr.n_clusters = s.nown;
+  tr.sector = s.unit % NSEC;
+  tr.request = s.unit / NSEC;
+  tr.last_row = s.r_out;
+  tr.cluster_offset = in.toff[m];
+  tr.flags = (int32_t)flags;
+  out[m] = tr;
+}
+
+// Phase 2 of the refit: the remaining updates in FP32; lanes refill.
+__global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst kc, RefitWork* RW,
+                                                  tpc_track* __restrict__ out, Counts* cn) {
+  __shared__ float sX[NROW + 1];
+  for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
+  __syncthreads();
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  LocalTally tl;
+  double D[15];  // unused in this phase
+  float C[15];
+  RefitLane w;
+  TrkState p;
+  Chi2Acc chi2;
+  int nupd = 0;
+  bool ok = true, go = false;
+  uint32_t flags = 0;
+  int64_t m = (int64_t)atomicAdd(&cn->refit_next, 1);
+  auto load = [&](int64_t mm) {
+    const RefitWork& s = RW[mm];
+    w = s.w;
+    p = s.p;
+#pragma unroll
+    for (int i = 0; i < 15; i++) C[i] = s.C[i];
+    chi2 = s.chi2;
+    nupd = s.nupd;
+    ok = s.ok != 0;
+    go = s.go != 0;
+    flags = (uint32_t)s.flags;
+  };
+  if (m < M) load(m);
+  while (m < M) {
+    if (go) go = refit_step<false>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
+    if (!go) {
+      write_track(in, sX, m, RW[m], p, C, chi2, ok, flags, out);
+      m = (int64_t)atomicAdd(&cn->refit_next, 1);
+      if (m < M) load(m);
     }
-    tr.reserved = 0;
-    tr.ndf = 2 * nown - 5;
-    tr.n_clusters = nown;
-    tr.sector = unit % NSEC;
-    tr.request = unit / NSEC;
-    tr.last_row = r_out;
-    tr.cluster_offset = toff[m];
-    tr.flags = (int32_t)flags;
-    out[m] = tr;
   }
   tl.flush(cn);
 }

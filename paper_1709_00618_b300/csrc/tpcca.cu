@@ -78,7 +78,7 @@ struct Layout {
       cend, owner, cluster_track, track_clusters;
   size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
   size_t bin_cnt, bin_start;
-  size_t own_mask, own_rng;
+  size_t own_mask, own_rng, fwork, rwork;
   size_t tl_start, tl_len, tl_end, f_n, f_nf, f_nb, f_flags, f_row, hits, hrow, f_par, f_zref, f_cov, f_chi2, keep,
       tidx, nown, tl_track, track_tl, tcount, toff, tracks;
   size_t parts;
@@ -147,6 +147,8 @@ Layout make_layout(const Caps& c) {
   L.tidx = take(4 * (T + 1));
   L.nown = take(4 * T);
   L.own_mask = take(4 * OWN_WORDS * T);
+  L.fwork = take(sizeof(FollowWork) * T);
+  L.rwork = take(sizeof(RefitWork) * M);
   L.own_rng = take(4 * T);
   L.tl_track = take(4 * T);
   L.track_tl = take(4 * M);
@@ -242,6 +244,15 @@ KConst make_kconst(const tpc_config& c, const Caps& caps) {
   k.bins_cap = caps.bins;
   k.tl_cap = caps.tl;
   return k;
+}
+
+// Blocks of a refilling follow phase: as many as are resident at once.
+int persistent_grid(tpc_ctx* ctx, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_follow_p2, threads, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return ctx->n_sm * per_sm;
 }
 
 int grid_for(const tpc_ctx* ctx, int64_t items, int threads, int per_sm = 16) {
@@ -433,9 +444,17 @@ void enqueue_find(tpc_ctx* ctx) {
   ctx->mark(3);
   // a6 follow
   int gF = grid_for(ctx, C.tl, ctx->block_follow, ctx->ctas_follow);
-  k_follow<<<gF, ctx->block_follow, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start),
-                                            ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
-                                            ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), cn);
+  {
+    FollowWork* W = ctx->ptr<FollowWork>(L.fwork);
+    const int bf = ctx->block_follow;
+    const int gP = persistent_grid(ctx, bf);
+    k_follow_p1<<<gF, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
+                                  ctx->ptr<int32_t>(L.tl_end), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx),
+                                  W, cn);
+    k_follow_p2<<<gP, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, cn);
+    k_follow_p3<<<gF, bf, 0, s>>>(grid_view(ctx), ctx->kc, follow_out(ctx), W, cn);
+    k_follow_p4<<<gP, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, cn);
+  }
   ctx->mark(4);
   // a7 selection
   k_zero64<<<gN, bc, 0, s>>>(ctx->ptr<uint64_t>(L.owner), cn);
@@ -467,12 +486,27 @@ void enqueue_fit(tpc_ctx* ctx) {
   scan(ctx, ctx->ptr<int32_t>(L.tcount), ctx->ptr<int32_t>(L.toff), LenSrc{&cn->n_tracks, 0, 0},
        &cn->n_track_clusters);
   int gF = grid_for(ctx, C.tracks, ctx->block_follow, ctx->ctas_follow);
-  k_refit<<<gF, ctx->block_follow, 0, s>>>(
-      grid_view(ctx), ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.f_nf),
-      ctx->ptr<int32_t>(L.f_row), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint8_t>(L.hrow), ctx->ptr<float>(L.f_par),
-      ctx->ptr<float>(L.f_zref), ctx->ptr<float>(L.f_cov), ctx->ptr<double>(L.f_chi2),
-      ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.own_rng), ctx->ptr<int32_t>(L.nown),
-      ctx->ptr<int32_t>(L.toff), ctx->kc, ctx->ptr<tpc_track>(L.tracks), cn);
+  {
+    RefitIn in;
+    in.track_tl = ctx->ptr<int32_t>(L.track_tl);
+    in.f_n = ctx->ptr<int32_t>(L.f_n);
+    in.f_nf = ctx->ptr<int32_t>(L.f_nf);
+    in.f_row = ctx->ptr<int32_t>(L.f_row);
+    in.hits = ctx->ptr<int32_t>(L.hits);
+    in.hrow = ctx->ptr<uint8_t>(L.hrow);
+    in.f_par = ctx->ptr<float>(L.f_par);
+    in.f_zref = ctx->ptr<float>(L.f_zref);
+    in.f_cov = ctx->ptr<float>(L.f_cov);
+    in.f_chi2 = ctx->ptr<double>(L.f_chi2);
+    in.own_mask = ctx->ptr<uint32_t>(L.own_mask);
+    in.own_rng = ctx->ptr<int32_t>(L.own_rng);
+    in.nown = ctx->ptr<int32_t>(L.nown);
+    in.toff = ctx->ptr<int32_t>(L.toff);
+    RefitWork* RW = ctx->ptr<RefitWork>(L.rwork);
+    k_refit_p1<<<gF, ctx->block_follow, 0, s>>>(grid_view(ctx), in, ctx->kc, RW, cn);
+    k_refit_p2<<<persistent_grid(ctx, ctx->block_follow), ctx->block_follow, 0, s>>>(
+        grid_view(ctx), in, ctx->kc, RW, ctx->ptr<tpc_track>(L.tracks), cn);
+  }
   k_track_clusters<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
                                      ctx->ptr<int32_t>(L.f_nf), ctx->ptr<int32_t>(L.hits),
                                      ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.toff),
