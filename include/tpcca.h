@@ -250,6 +250,67 @@ int tpc_row_params_noalloc(const tpc_cluster *d_clusters, int64_t n, const int64
  * the current value.  Invalidates a captured graph. */
 int tpc_set_tuning(tpc_ctx *ctx, int block_clusters, int block_follow, int ctas_per_sm_follow, int reserved);
 
+/* Autotuner: with a representative batch loaded, times tpc_find_tracks +
+ * tpc_fit_tracks (median of reps runs, CUDA events on the context's stream)
+ * for threads per block of the cluster-parallel kernels (128/256/512), of
+ * the Kalman kernels (64/96/128) and CTAs per SM of their static phases
+ * (2/4/8), by coordinate descent, keeps the fastest and reports it in
+ * choice[3] (same order as tpc_set_tuning) and *best_ms.  The results of
+ * the loaded batch are overwritten (rerun tpc_find_tracks before get). */
+int tpc_autotune(tpc_ctx *ctx, int32_t reps, int32_t choice[3], float *best_ms);
+
+/* ------------------------------------------------------ serving (requests) */
+/* Continuous-batching request loop: the serving form of tracking several
+ * events or continuous-readout timeframes (Sec. 2, Sec. 5) as they arrive.
+ * A server owns max_slots tracker contexts, each on its own CUDA stream of
+ * device `device`, and one worker thread.  Requests wait in submission
+ * order; the worker admits the head of the queue as soon as a slot is free
+ * and that slot's arena for the request (tpc_arena_bytes(n, 1)) fits both
+ * hbm_budget (bytes summed over all slots; 0: no budget) and the device's
+ * free memory, so requests admitted while others run overlap on the GPU.
+ * Slots keep their arenas (grid, links, tracklets, tracks) across requests
+ * and only grow them; idle slots drop theirs when the budget would block the
+ * head of the queue.  Each request runs the same graph as tpc_run_graph, so
+ * its result equals the one it gets alone.  queue_cap: requests that may
+ * wait (admitted ones excluded).  Errors: TPC_EINVAL for bad arguments,
+ * TPC_ECUDA when a stream or context cannot be created. */
+typedef struct tpc_server tpc_server;
+int tpc_server_create(tpc_server **out, const tpc_config *cfg, int device, int32_t max_slots, size_t hbm_budget,
+                      int32_t queue_cap);
+
+/* Queue n clusters (host memory, one request) under a caller-chosen id that
+ * no pending request uses.  The buffer is read when the request is admitted
+ * and must stay valid and unchanged until tpc_server_poll reports it
+ * finished; page-locked memory lets its copy overlap other slots' work.
+ * TPC_EBUSY: the queue is full (retry later).  TPC_ENOMEM: the request alone
+ * exceeds the budget.  TPC_EINVAL: bad argument or an id in use. */
+int tpc_server_submit(tpc_server *srv, int64_t request_id, const tpc_cluster *clusters, int64_t n);
+
+/* *state: 0 queued, 1 running, 2 finished, 3 failed, -1 unknown id. */
+int tpc_server_poll(tpc_server *srv, int64_t request_id, int *state);
+
+/* Results of a finished request, as tpc_get_tracks (track_clusters is not
+ * kept).  times_ms (optional): [0] queue wait, [1] admission to results on
+ * the host, [2] submission to results on the host.  With out and
+ * cluster_track both NULL only *n_out and times_ms are filled and the result
+ * is kept; otherwise it is copied and released.  TPC_EBUSY while the request
+ * is queued or running; TPC_EOVERFLOW when cap < *n_out (result kept); the
+ * request's own error code when it failed (result released). */
+int tpc_server_result(tpc_server *srv, int64_t request_id, tpc_track *out, int64_t cap, int64_t *n_out,
+                      int32_t *cluster_track, double times_ms[3]);
+
+/* Wait until no request is queued or running (timeout_s <= 0: no limit);
+ * TPC_ETIMEOUT when the limit ran out. */
+int tpc_server_drain(tpc_server *srv, double timeout_s);
+
+/* [0] admitted, [1] completed, [2] queued now, [3] arena bytes held by the
+ * slots, [4] most requests that ran at the same time. */
+int tpc_server_stats(tpc_server *srv, int64_t stats[5]);
+
+/* Stops the worker after its current step (requests still queued are
+ * dropped), waits for the slots' streams and frees everything. */
+void tpc_server_destroy(tpc_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,7 @@ import numpy as np
 
 from .build import LIB_PATH, build  # noqa: F401
 
-__all__ = ["Tracker", "TpcError", "TRACK_DTYPE", "CLUSTER_DTYPE", "build", "load_library", "default_config",
+__all__ = ["Tracker", "Server", "TpcError", "TRACK_DTYPE", "CLUSTER_DTYPE", "build", "load_library", "default_config",
            "ITEMS"]
 
 CLUSTER_DTYPE = np.dtype([("y", "<f4"), ("z", "<f4"), ("row", "<u2"), ("sector", "<u2"), ("id", "<u4")])
@@ -90,8 +90,16 @@ def load_library(path: str | None = None):
         "tpc_get_stage_times": ([_VP, _VP], ctypes.c_int),
         "tpc_get_work": ([_VP, _VP], ctypes.c_int),
         "tpc_row_params_noalloc": ([_VP, _I64, _VP, _I32, _VP, _VP], ctypes.c_int),
+        "tpc_autotune": ([_VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_set_trace": ([_VP, _I32], ctypes.c_int),
         "tpc_get_trace": ([_VP, _VP, _I32, _VP], ctypes.c_int),
+        "tpc_server_create": ([_VP, _VP, ctypes.c_int, _I32, ctypes.c_size_t, _I32], ctypes.c_int),
+        "tpc_server_submit": ([_VP, _I64, _VP, _I64], ctypes.c_int),
+        "tpc_server_poll": ([_VP, _I64, _VP], ctypes.c_int),
+        "tpc_server_result": ([_VP, _I64, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
+        "tpc_server_drain": ([_VP, ctypes.c_double], ctypes.c_int),
+        "tpc_server_stats": ([_VP, _VP], ctypes.c_int),
+        "tpc_server_destroy": ([_VP], None),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -233,6 +241,38 @@ class Tracker:
         self._ck(self._lib.tpc_get_trace(self._ctx, out.ctypes.data, 2048, ctypes.byref(n)))
         return out[:min(n.value, 2048)]
 
+    def autotune(self, clusters=None, req_offsets=None, reps: int = 3, cache: str | None = None, key: str = ""):
+        """Choose block/CTA shapes for the loaded (or given) batch with the
+        library's autotuner; with `cache`, reuse or store the choice under
+        `key` in that JSON file.  Returns (choice dict, best ms)."""
+        import json
+        if cache and os.path.exists(cache):
+            try:
+                entry = json.load(open(cache)).get(key)
+            except (OSError, ValueError):
+                entry = None
+            if entry:
+                self.set_tuning(*entry["choice"])
+                return dict(zip(("block_clusters", "block_follow", "ctas_per_sm_follow"), entry["choice"])), \
+                    entry["ms"]
+        if clusters is not None:
+            self.load(clusters, req_offsets)
+        ch = np.zeros(3, np.int32)
+        ms = ctypes.c_float()
+        self._ck(self._lib.tpc_autotune(self._ctx, reps, ch.ctypes.data, ctypes.byref(ms)))
+        choice = [int(v) for v in ch]
+        if cache:
+            data = {}
+            if os.path.exists(cache):
+                try:
+                    data = json.load(open(cache))
+                except (OSError, ValueError):
+                    data = {}
+            data[key] = {"choice": choice, "ms": ms.value}
+            with open(cache, "w") as f:
+                json.dump(data, f, indent=1)
+        return dict(zip(("block_clusters", "block_follow", "ctas_per_sm_follow"), choice)), ms.value
+
     def set_profiling(self, on: bool = True):
         self._ck(self._lib.tpc_set_profiling(self._ctx, int(on)))
 
@@ -289,13 +329,119 @@ class Tracker:
         return out
 
     def track(self, clusters, req_offsets=None, graph: bool = False):
-        """load + find + fit (+ graph) + get."""
-        self.load(clusters, req_offsets)
-        if graph:
-            self.run_graph()
+        """load + find + fit (+ graph) + get.  A capacity overflow (more
+        tracklets or grid bins than reserved; reported, never truncated) is
+        retried once with the worst-case capacities."""
+        for attempt in range(2):
+            self.load(clusters, req_offsets)
+            if graph:
+                self.run_graph()
+            else:
+                self.find().fit()
+            try:
+                return self.get()
+            except TpcError as e:
+                if e.code != TPC_EOVERFLOW or attempt:
+                    raise
+                n = self.n
+                nreq = 1 if req_offsets is None else len(req_offsets) - 1
+                c = self.counts()
+                self.reserve(n_clusters=n, n_requests=nreq, n_bins=max(2 * c["n_bins"], 0),
+                             n_tracklets=n // 3 + 16)
+        raise AssertionError("unreachable")
+
+
+class Server:
+    """Continuous-batching request loop (tpc_server_*): up to max_slots
+    requests run at once, each on its own context and stream, admitted in
+    arrival order while their arenas fit hbm_budget and free device memory.
+
+    submit() keeps a reference to the cluster array until result() returns,
+    since the library reads it when the request is admitted."""
+
+    STATES = {-1: "unknown", 0: "queued", 1: "running", 2: "finished", 3: "failed"}
+
+    def __init__(self, device: int = 0, cfg: TpcConfig | None = None, max_slots: int = 4, hbm_budget: int = 0,
+                 queue_cap: int = 1 << 20):
+        self._lib = load_library()
+        self._srv = ctypes.c_void_p()
+        rc = self._lib.tpc_server_create(ctypes.byref(self._srv), ctypes.byref(cfg) if cfg else None, device,
+                                         max_slots, hbm_budget, queue_cap)
+        if rc != 0:
+            raise TpcError(rc, "tpc_server_create failed")
+        self._inputs = {}
+
+    def close(self):
+        if self._srv:
+            self._lib.tpc_server_destroy(self._srv)
+            self._srv = ctypes.c_void_p()
+            self._inputs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, request_id: int, clusters) -> int:
+        """Queue one request (host clusters: numpy CLUSTER_DTYPE records or a
+        pinned CPU torch tensor of them).  Returns the status code: 0, or
+        TPC_EBUSY when the queue is full."""
+        if hasattr(clusters, "data_ptr"):
+            n = clusters.numel() * clusters.element_size() // 16
         else:
-            self.find().fit()
-        return self.get()
+            clusters = np.ascontiguousarray(clusters)
+            n = len(clusters)
+        rc = self._lib.tpc_server_submit(self._srv, request_id, _ptr(clusters) if n else None, n)
+        if rc == 0:
+            self._inputs[request_id] = (clusters, n)
+        elif rc != TPC_EBUSY:
+            raise TpcError(rc, f"tpc_server_submit({request_id})")
+        return rc
+
+    def poll(self, request_id: int) -> str:
+        st = ctypes.c_int()
+        self._lib.tpc_server_poll(self._srv, request_id, ctypes.byref(st))
+        return self.STATES[st.value]
+
+    def result(self, request_id: int):
+        """(tracks, cluster_track, times_ms) of a finished request, or None
+        while it is queued or running.  times_ms: queue wait, service and
+        total latency in ms.  Raises TpcError if the request failed."""
+        nt = ctypes.c_int64()
+        times = np.zeros(3, np.float64)
+        rc = self._lib.tpc_server_result(self._srv, request_id, None, 0, ctypes.byref(nt), None,
+                                         times.ctypes.data)
+        if rc == TPC_EBUSY:
+            return None
+        if rc != 0:
+            self._inputs.pop(request_id, None)
+            raise TpcError(rc, f"request {request_id} failed")
+        n = self._inputs[request_id][1]
+        tracks = np.zeros(nt.value, TRACK_DTYPE)
+        ct = np.zeros(n, np.int32)
+        rc = self._lib.tpc_server_result(self._srv, request_id, tracks.ctypes.data, nt.value, ctypes.byref(nt),
+                                         ct.ctypes.data if n else None, None)
+        if rc != 0:
+            raise TpcError(rc, f"request {request_id}: copying results")
+        self._inputs.pop(request_id, None)
+        return tracks, ct, times
+
+    def drain(self, timeout_s: float = 0.0):
+        rc = self._lib.tpc_server_drain(self._srv, timeout_s)
+        if rc != 0:
+            raise TpcError(rc, "drain timed out")
+
+    def stats(self) -> dict:
+        st = np.zeros(5, np.int64)
+        self._lib.tpc_server_stats(self._srv, st.ctypes.data)
+        return dict(zip(("admitted", "completed", "queued", "arena_bytes", "peak_running"), (int(v) for v in st)))
 
 
 def row_params_noalloc(d_clusters, req_offsets=None, out=None, stream=None) -> int:

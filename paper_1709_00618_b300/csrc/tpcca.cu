@@ -67,8 +67,12 @@ Caps default_caps(int64_t n, int32_t req) {
   c.n = std::max<int64_t>(n, 1024);
   c.req = std::max<int32_t>(req, 1);
   c.bins = 2 * c.n + 2048 * c.nrs();
-  c.tl = c.n / 3 + 16;  // chains are disjoint and hold >= 3 clusters: cannot overflow with min_chain >= 3
-  c.tracks = c.tl;      // tracks are a subset of the tracklets
+  // Tracklets: chains are disjoint and hold >= 3 clusters, so n/3 can never
+  // overflow; measured events and timeframes give 0.06 per cluster, so the
+  // default is n/6 and an overflow (reported, never truncated) is retried
+  // with tpc_reserve.
+  c.tl = c.n / 6 + 1024;
+  c.tracks = c.tl;  // tracks are a subset of the tracklets
   return c;
 }
 
@@ -812,6 +816,74 @@ int tpc_get_stage(tpc_ctx* ctx, int item, void* host_out, int64_t cap_bytes, int
   }
   CK(cudaMemcpy(host_out, ctx->arena + off, bytes, cudaMemcpyDeviceToHost));
   return TPC_OK;
+}
+
+int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[3], float* best_ms) {
+  if (!ctx || reps < 1 || reps > 100) return TPC_EINVAL;
+  if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "load a representative batch before tpc_autotune");
+  CK(cudaSetDevice(ctx->device));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  // median device time of `reps` find + fit runs on the loaded batch
+  auto measure = [&](float& ms) -> int {
+    std::vector<float> t;
+    for (int r = 0; r < reps + 1; r++) {
+      CK(cudaEventRecord(e0, ctx->stream));
+      enqueue_find(ctx);
+      enqueue_fit(ctx);
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      float v = 0.0f;
+      CK(cudaEventElapsedTime(&v, e0, e1));
+      if (r > 0) t.push_back(v);  // the first run warms caches and code
+    }
+    std::sort(t.begin(), t.end());
+    ms = t[t.size() / 2];
+    return check_status(ctx);
+  };
+  static const int kBlockClusters[] = {128, 256, 512};
+  static const int kBlockFollow[] = {64, 96, 128};
+  static const int kCtas[] = {2, 4, 8};
+  int best[3] = {ctx->block_clusters, ctx->block_follow, ctx->ctas_follow};
+  float best_t = 0.0f;
+  int rc = measure(best_t);
+  for (int dim = 0; dim < 3 && rc == TPC_OK; dim++) {  // coordinate descent
+    const int* cand = dim == 0 ? kBlockClusters : dim == 1 ? kBlockFollow : kCtas;
+    for (int k = 0; k < 3 && rc == TPC_OK; k++) {
+      int trial[3] = {best[0], best[1], best[2]};
+      trial[dim] = cand[k];
+      if (trial[dim] == best[dim]) continue;
+      ctx->block_clusters = trial[0];
+      ctx->block_follow = trial[1];
+      ctx->ctas_follow = trial[2];
+      float t = 0.0f;
+      rc = measure(t);
+      if (rc == TPC_OK && t < best_t) {
+        best_t = t;
+        best[dim] = trial[dim];
+      }
+    }
+  }
+  ctx->block_clusters = best[0];
+  ctx->block_follow = best[1];
+  ctx->ctas_follow = best[2];
+  ctx->prof = prof;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (choice) {
+    choice[0] = best[0];
+    choice[1] = best[1];
+    choice[2] = best[2];
+  }
+  if (best_ms) *best_ms = best_t;
+  return rc;
 }
 
 int tpc_set_trace(tpc_ctx* ctx, int32_t tracklet) {

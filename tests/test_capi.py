@@ -59,3 +59,22 @@ def test_create_without_gpu_reports_cuda_error():
         lib.tpc_destroy(ctx)
         pytest.skip("a GPU is present")
     assert rc == tpc.TPC_ECUDA
+
+
+def test_server_arguments_are_checked_without_a_device():
+    lib = tpc.load_library()
+    srv = ctypes.c_void_p()
+    assert lib.tpc_server_create(ctypes.byref(srv), None, 0, 0, 0, 16) == tpc.TPC_EINVAL
+    assert lib.tpc_server_create(ctypes.byref(srv), None, 0, 4, 0, 0) == tpc.TPC_EINVAL
+    assert lib.tpc_server_create(None, None, 0, 4, 0, 16) == tpc.TPC_EINVAL
+    assert lib.tpc_server_submit(None, 1, None, 0) == tpc.TPC_EINVAL
+    st = ctypes.c_int()
+    assert lib.tpc_server_poll(None, 1, ctypes.byref(st)) == tpc.TPC_EINVAL
+    assert lib.tpc_server_result(None, 1, None, 0, None, None, None) == tpc.TPC_EINVAL
+    assert lib.tpc_server_drain(None, 0.0) == tpc.TPC_EINVAL
+    lib.tpc_server_destroy(None)
+    rc = lib.tpc_server_create(ctypes.byref(srv), None, 0, 2, 0, 16)
+    if rc == 0:
+        lib.tpc_server_destroy(srv)
+        pytest.skip("a GPU is present")
+    assert rc == tpc.TPC_ECUDA
