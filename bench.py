@@ -85,42 +85,76 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# Kernels launched per step (tpc_run_graph): grid 7 + 3 scans x 3 kernels,
-# neighbours 1, links/tracklets 2 + 1 scan, follow 1, selection 5 + 1 scan,
-# refit 3 + 1 scan.
-KERNELS_PER_STEP = 7 + 9 + 1 + 2 + 3 + 1 + 5 + 3 + 3 + 3
-
-# Algorithmic FP32 work of the Kalman kernels (counted from the source, per
-# unit of the device work counters): a propagation with covariance transport
-# (helix step, Jacobian, J C J^T on the packed triangle, compensated adds) is
-# 170 flop, an FP32 update (gain, state, covariance, residuals) 150 flop, a
-# candidate examined by the pick-up 10 flop.
-FLOP_PROP, FLOP_UPD, FLOP_CAND = 170, 150, 10
+# Algorithmic work of the Kalman kernels, counted from the source per unit of
+# the device work counters (an FMA counts 2, an add, multiply, divide or
+# square root 1):
+#   helix step of the state with its Jacobian, binary32        76
+#   covariance transport J C J^T (51 FMA on the packed triangle) 102
+#   Kalman update, gain and covariance (in the covariance type)  99
+#   Kalman update, residuals, state and chi2 (binary32)          56
+#   candidate cluster examined by the gated pick-up              10
+# FP32-zone work is all binary32; in the FP64 zone the transport and the
+# covariance part of the update run in binary64.
+FLOP_STATE, FLOP_TRANSPORT, FLOP_UPD_COV, FLOP_UPD_STATE, FLOP_CAND = 76, 102, 99, 56, 10
 # Algorithmic DRAM bytes per cluster of the memory-bound stages: grid 88
 # (16 B read twice, 4 B rs, 8 B bin/slot written and read, scatter 4 B,
 # order 16 B gather + 16 B writes), neighbours 33 (8 B own y/z, 8 B candidate
 # re-reads, 8 B links + 1 B tie written, ~8 B bin starts).
 BYTES_GRID, BYTES_NEIGH = 88, 33
+# Issue rates per SM and clock: 128 FP32 lanes (an FMA is 2 flop) and, on
+# B300, 2 FP64 FMA units.
+FP32_FLOP_PER_CLK_SM, FP64_FLOP_PER_CLK_SM, N_SM = 256, 4, 148
 
 
-def roofline(stages, work, counts, n):
+def kalman_flops(w):
+    """(binary32 flop, binary64 flop) of one Kalman kernel's work counters."""
+    p32 = w["prop"] - w["prop64"]
+    f32 = (FLOP_STATE + FLOP_TRANSPORT) * p32 + FLOP_STATE * w["prop64"] + \
+        (FLOP_UPD_COV + FLOP_UPD_STATE) * w["upd32"] + FLOP_UPD_STATE * w["upd64"] + FLOP_CAND * w["cand"]
+    f64 = FLOP_TRANSPORT * w["prop64"] + FLOP_UPD_COV * w["upd64"]
+    return f32, f64
+
+
+def kernel_rooflines(stages, kalman, n):
+    """Roofline entry per timed kernel (Kalman kernels one by one, the
+    neighbour kernel, the grid stage as a whole); the largest is the
+    dominant kernel."""
     peaks, src = _peaks()
-    dom = max(stages, key=stages.get)
-    t = stages[dom] / 1e3
-    if dom in ("follow", "refit"):
-        flop = FLOP_PROP * work["prop"] + FLOP_UPD * work["upd32"] + FLOP_CAND * work["cand"]
-        sm = 148
-        peak = sm * 128 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
-        ach = flop / t / 1e12
-        return {"kernel": f"k_{dom}", "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "note": f"FP32 FMA peak 148 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2032.0)} MHz ({src} clock); "
-                        "work counted by device counters; the follow stage includes both Kalman kernels' FP64 zones"}
-    b = (BYTES_GRID if dom == "grid" else BYTES_NEIGH) * n
-    ach = b / t / 1e9
-    peak = peaks["hbm_gbs"]
-    return {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": None}
+    mhz = peaks.get("sm_max_mhz", 2032.0)
+    p32 = N_SM * FP32_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+    p64 = N_SM * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+    out = {}
+    for name, d in kalman.items():
+        t = d["ms"] / 1e3
+        f32, f64 = kalman_flops(d)
+        zone = name in ("k_follow_p1", "k_follow_p3", "k_refit_p1")
+        if zone:
+            ach = f64 / t / 1e12
+            e = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s (FP64)", "frac": ach / p64,
+                 "fp32_tflops": f32 / t / 1e12}
+        else:
+            ach = f32 / t / 1e12
+            e = {"bound": "alu", "achieved": ach, "peak": p32, "unit": "TFLOP/s (FP32)", "frac": ach / p32}
+        e["ms"] = d["ms"]
+        e["work"] = {k: d[k] for k in ("prop", "upd32", "upd64", "cand", "prop64")}
+        out[name] = e
+    for name, ms, per in (("k_neighbours", stages["neighbours"], BYTES_NEIGH), ("grid stage", stages["grid"],
+                                                                                  BYTES_GRID)):
+        ach = per * n / (ms / 1e3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": ach / peaks["hbm_gbs"], "ms": ms, "bytes_per_cluster": per}
+    return out, src
+
+
+def roofline(stages, kalman, n, traffic=None):
+    table, src = kernel_rooflines(stages, kalman, n)
+    dom = max((k for k in table if k != "grid stage"), key=lambda k: table[k]["ms"])
+    e = dict(table[dom])
+    line = {"kernel": dom, "bound": e["bound"], "achieved": e["achieved"], "peak": e["peak"], "unit": e["unit"],
+            "frac": e["frac"], "traffic": (traffic or {}).get(dom), "ms": e["ms"],
+            "peak_source": f"{src}: FP32 {N_SM} SM x {FP32_FLOP_PER_CLK_SM} flop/clk, FP64 {N_SM} SM x "
+                           f"{FP64_FLOP_PER_CLK_SM} flop/clk at the measured maximum SM clock; HBM measured copy"}
+    return line, table
 
 
 def cpu_baseline(cl):
@@ -167,6 +201,196 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v, dtype=np.float64), q)) if len(v) else None
+
+
+def batching_leg(local, flush, n_requests=256, reps=3):
+    """256 independent requests of uneven size (1-36 sectors of events with
+    50-8000 tracks, log-uniform) as one batch in one graph launch, against
+    the same requests as separate plain launches one after the other.
+    Inputs are resident on the device; the L2 is flushed before each run.
+    Latency of a request: from the start of the run to the completion of its
+    results on the device (all requests are there at the start)."""
+    import numpy as np
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    import synth
+    reqs = synth.batch_requests(seed=3, n_requests=n_requests)
+    sizes = np.array([len(r.clusters) for r in reqs], np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    cl = np.concatenate([r.clusters for r in reqs])
+    dev = torch.from_numpy(cl.view(np.uint8)).to(f"cuda:{local}")
+    views = [dev[16 * off[i]:16 * off[i + 1]] for i in range(n_requests)]
+    stream = torch.cuda.Stream()
+    out = {"workload": f"{n_requests} requests, 1-36 sectors of events with 50-8000 tracks (log-uniform), seed 3",
+           "clusters": int(off[-1]), "request_clusters_p50": int(np.median(sizes)),
+           "request_clusters_max": int(sizes.max())}
+
+    def flush_l2():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
+    # batched: one context, one load, one graph launch; shapes by the autotuner
+    bt = tpc.Tracker(device=local, stream=stream)
+    bt.load(dev, off)
+    choice, tuned_ms = bt.autotune(reps=3)
+    out["autotuned"] = dict(choice, ms=tuned_ms)
+    for _ in range(3):
+        bt.load(dev, off)
+        bt.run_graph()
+    bt.sync()
+    times = []
+    for _ in range(reps):
+        flush_l2()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.load(dev, off)
+        bt.run_graph()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    bt.sync()
+    t_b = statistics.median(times)
+    out["batched"] = {"clusters_per_s": off[-1] / (t_b / 1e3), "ms": t_b, "launches": 1,
+                      "kernels": bt.graph_kernels(), "latency_ms_p50": t_b, "latency_ms_p99": t_b}
+    bt.close()
+
+    # plain: one context, each request loaded, found and fitted on its own
+    pt = tpc.Tracker(device=local, stream=stream)
+    pt.reserve(n_clusters=int(sizes.max()), n_requests=1)
+    for i in range(min(8, n_requests)):
+        pt.load(views[i]).find().fit()
+    pt.sync()
+    tot, lat_all = [], []
+    for _ in range(reps):
+        flush_l2()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n_requests + 1)]
+        ev[0].record(stream)
+        for i in range(n_requests):
+            pt.load(views[i]).find().fit()
+            ev[i + 1].record(stream)
+        ev[-1].synchronize()
+        lat = [ev[0].elapsed_time(ev[i + 1]) for i in range(n_requests)]
+        tot.append(lat[-1])
+        lat_all.append(lat)
+    pt.sync()
+    k = int(np.argsort(tot)[len(tot) // 2])
+    t_p = tot[k]
+    out["plain"] = {"clusters_per_s": off[-1] / (t_p / 1e3), "ms": t_p, "launches": n_requests,
+                    "latency_ms_p50": _pct(lat_all[k], 50), "latency_ms_p99": _pct(lat_all[k], 99)}
+    pt.close()
+    out["batched_over_plain"] = out["batched"]["clusters_per_s"] / out["plain"]["clusters_per_s"]
+    return out
+
+
+def serving_leg(local, n_timeframes=24, pool=4, load=0.85, slots=4, budget_gb=120.0, ring=6, seed=4):
+    """Poisson stream of continuous-readout timeframes (lengths uniform in
+    1-20 ms at 50 kHz) through the continuous-batching server, against
+    sequential plain processing of the same stream.  Timeframes are drawn
+    from a pool of distinct seeded timeframes; inputs and result buffers are
+    page-locked host memory in both arms (`ring` result buffers for the
+    server: a request waits for a free one).  The arrival rate puts the
+    offered load at `load` times the sequential plain capacity (measured
+    first).  Latency: arrival to results (tracks and cluster assignment) in
+    host memory."""
+    import numpy as np
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    import synth
+    tfs = synth.timeframe_stream(seed=seed, n_distinct=pool)
+    pinned = [torch.from_numpy(t.clusters.view(np.uint8)).pin_memory() for t in tfs]
+    host = [p.numpy().view(synth.CLUSTER_DTYPE) for p in pinned]
+    sizes = [len(h) for h in host]
+    rng = np.random.default_rng(seed + 1)
+    order = rng.integers(0, pool, size=n_timeframes)
+
+    # sequential plain service time of each pool entry (after one warm run)
+    trk = tpc.Tracker(device=local)
+    trk.reserve(n_clusters=max(sizes), n_requests=1)
+    n_tracks = []
+    serv = []
+    big_tr = torch.zeros(max(sizes) // 10 + 1, 128, dtype=torch.uint8).pin_memory()
+    big_ct = torch.zeros(max(sizes), dtype=torch.int32).pin_memory()
+    for h in host:
+        trk.load(h).find().fit()
+        tr, _ = trk.get_into(big_tr, big_ct[:len(h)])
+        n_tracks.append(len(tr))
+        t0 = time.perf_counter()
+        trk.load(h).find().fit()
+        trk.get_into(big_tr, big_ct[:len(h)])
+        serv.append(time.perf_counter() - t0)
+    del big_tr
+    cap = int(1.25 * max(n_tracks)) + 1024
+    mean_s = float(np.mean([serv[i] for i in order]))
+    lam = load / mean_s
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_timeframes))
+    arrivals -= arrivals[0]
+
+    # plain: one request at a time in arrival order
+    out_tr = torch.zeros(cap, 128, dtype=torch.uint8).pin_memory()
+    lat_p = []
+    t_start = time.perf_counter()
+    for k in range(n_timeframes):
+        now = time.perf_counter() - t_start
+        if now < arrivals[k]:
+            time.sleep(arrivals[k] - now)
+        h = host[order[k]]
+        trk.load(h).find().fit()
+        trk.get_into(out_tr, big_ct[:len(h)])
+        lat_p.append(time.perf_counter() - t_start - arrivals[k])
+    span_p = time.perf_counter() - t_start
+    trk.close()
+    del big_ct, out_tr
+    total = int(sum(sizes[i] for i in order))
+
+    # served: submissions at the same arrival times into a ring of result
+    # buffers; results collected as they finish
+    bufs = [(torch.zeros(cap, 128, dtype=torch.uint8).pin_memory(),
+             torch.zeros(max(sizes), dtype=torch.int32).pin_memory()) for _ in range(ring)]
+    free = list(range(ring))
+    srv = tpc.Server(device=local, max_slots=slots, hbm_budget=int(budget_gb * 2**30))
+    lat_s, late, owner, pending = [], {}, {}, set()
+    t_start = time.perf_counter()
+    k = 0
+    while k < n_timeframes or pending:
+        now = time.perf_counter() - t_start
+        while k < n_timeframes and arrivals[k] <= now and free:
+            b = free.pop()
+            h = host[order[k]]
+            if srv.submit(k, pinned[order[k]], tracks_out=bufs[b][0], cluster_track_out=bufs[b][1][:len(h)]) != 0:
+                free.append(b)
+                break
+            late[k] = time.perf_counter() - t_start - arrivals[k]
+            owner[k] = b
+            pending.add(k)
+            k += 1
+        for j in sorted(pending):
+            r = srv.result(j)
+            if r is not None:
+                lat_s.append(late[j] + r[2][2] / 1e3)
+                pending.discard(j)
+                free.append(owner.pop(j))
+        time.sleep(0.0002)
+    span_s = time.perf_counter() - t_start
+    st = srv.stats()
+    srv.close()
+    return {"workload": f"Poisson stream of {n_timeframes} timeframes drawn from {pool} distinct seeded "
+                        f"timeframes of 1-20 ms at 50 kHz (seed {seed}); offered load {load} of the sequential "
+                        f"plain capacity; {slots} slots, {budget_gb:g} GB HBM budget; page-locked inputs and "
+                        f"outputs in both arms",
+            "timeframe_clusters": sizes, "timeframe_ms": [round(t.params.tf_length_us / 1e3, 3) for t in tfs],
+            "timeframe_tracks": n_tracks, "clusters": total, "arrival_rate_hz": lam,
+            "plain": {"latency_ms_p50": 1e3 * _pct(lat_p, 50), "latency_ms_p99": 1e3 * _pct(lat_p, 99),
+                      "clusters_per_s": total / span_p, "service_ms": [round(1e3 * v, 2) for v in serv]},
+            "served": {"latency_ms_p50": 1e3 * _pct(lat_s, 50), "latency_ms_p99": 1e3 * _pct(lat_s, 99),
+                       "clusters_per_s": total / span_s, "peak_running": st["peak_running"],
+                       "arena_gb": st["arena_bytes"] / 2**30}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -174,6 +398,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-timeframes", type=int, default=24)
+    ap.add_argument("--serving-pool", type=int, default=4)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -205,9 +433,11 @@ def main():
         trk.load(dev_in)
         trk.run_graph()
 
-    for _ in range(max(args.warmup, 3)):
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
         step_device()
     trk.sync()
+    kernels_per_step = trk.graph_kernels()
     torch.cuda.synchronize()
     times = []
     with ClockSampler(local) as clk:
@@ -233,9 +463,11 @@ def main():
     counts = trk.counts()
     tracks, ct, _ = trk.get()
 
-    # per-stage device time (CUDA events recorded by the library on its stream)
+    # per-stage and per-Kalman-kernel device time: CUDA events recorded by the
+    # library on its stream between the launches of plain (non-graph) runs of
+    # the same kernels, L2 flushed before each run; median of 5
     trk.set_profiling(True)
-    runs = []
+    runs, kruns = [], []
     for _ in range(5):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -243,23 +475,30 @@ def main():
         trk.find().fit()
         trk.sync()
         runs.append(trk.stage_times())
+        kruns.append(trk.kalman_profile())
     trk.set_profiling(False)
     stages = {k: statistics.median(r[k] for r in runs) for k in runs[0]}
+    kalman = {}
+    for name in kruns[0]:
+        d = dict(kruns[-1][name])
+        d["ms"] = statistics.median(r[name]["ms"] for r in kruns)
+        kalman[name] = d
     work = trk.work()
-    roof = roofline(stages, work, counts, n)
+    roof, kernel_table = roofline(stages, kalman, n)
 
     # end to end through the public API: pinned host input -> tracks + assignment on the host
     pinned = torch.from_numpy(cl.view(np.uint8)).pin_memory()
     host_in = pinned.numpy().view(synth.CLUSTER_DTYPE)
     e2e = []
-    for i in range(max(args.warmup, 3) + args.steps):
+    for i in range(warm + args.steps):
         t0 = time.perf_counter()
         trk.load(host_in)
         trk.run_graph()
         tr, c2, _ = trk.get()
-        if i >= max(args.warmup, 3):
+        if i >= warm:
             e2e.append(time.perf_counter() - t0)
     e2e_t = sum(e2e) / len(e2e)
+    trk.close()
 
     peaks, src = _peaks()
     line = {"metric": METRIC, "value": world * n / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -267,20 +506,27 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1",
                        "clusters": n, "tracklets": counts["n_tracklets"], "tracks": counts["n_tracks"],
-                       "l2": "flushed (256 MB write) between steps", "graph": True},
+                       "l2": "flushed (256 MB write) between steps", "graph": True,
+                       "kernels_per_step": kernels_per_step},
             "clocks": clk.summary(),
             "e2e": {"value": world * n / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 128 * len(tr) + 4 * n},
-            "gpu_launches": KERNELS_PER_STEP,
+            "gpu_launches": kernels_per_step * args.steps,
             "roofline": roof,
+            "kernels": kernel_table,
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
             "work": work,
             "peaks_source": src}
+    if world == 1 and not args.no_batching:
+        line["batching"] = batching_leg(local, flush)
+    if world == 1 and not args.no_serving:
+        del flush
+        torch.cuda.empty_cache()
+        line["serving"] = serving_leg(local, n_timeframes=args.serving_timeframes, pool=args.serving_pool)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cl)
     if rank == 0:
         print(json.dumps(line))
-    trk.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -132,6 +132,9 @@ size_t tpc_arena_bytes(int64_t n_clusters, int32_t n_requests);
  * load functions; call it explicitly to retry after TPC_EOVERFLOW. */
 int tpc_reserve(tpc_ctx *ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets);
 
+/* Device bytes the context's arena holds now (0 before the first load). */
+int tpc_get_arena_bytes(tpc_ctx *ctx, size_t *bytes);
+
 /* ------------------------------------------------------------ the hot path */
 /* a1: copy n clusters (host or device pointer) into the context as one
  * request.  Validation of each cluster happens on the device; a bad cluster
@@ -165,6 +168,17 @@ int tpc_run_graph(tpc_ctx *ctx);
  * tracks[i].cluster_offset, innermost row first. */
 int tpc_get_tracks(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, int32_t *cluster_track,
                    int32_t *track_clusters);
+
+/* Non-blocking form of tpc_get_tracks for a run that has completed (the
+ * caller has seen its stream idle, e.g. through an event recorded after
+ * tpc_run_graph): reports device-side errors and *n_out as tpc_get_tracks,
+ * then enqueues the copies of the tracks and of cluster_track (either may
+ * be NULL) on the context's stream and returns.  The copies have landed
+ * once the stream is idle again; with page-locked destinations they run
+ * without holding up the calling thread.  TPC_EBUSY: the run is still
+ * going.  TPC_EOVERFLOW: device capacities overflowed (*n_out untouched)
+ * or cap < *n_out (nothing copied). */
+int tpc_get_tracks_async(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, int32_t *cluster_track);
 
 /* Wait for the context's stream and report device-side errors. */
 int tpc_sync(tpc_ctx *ctx);
@@ -210,6 +224,19 @@ int tpc_get_stage_times(tpc_ctx *ctx, float ms[6]);
  * [3] candidate clusters examined by the pick-up, [4] propagations done with
  * the FP64 covariance. */
 int tpc_get_work(tpc_ctx *ctx, uint64_t work[5]);
+
+/* Per Kalman kernel, in launch order -- [0] follow seed + forward FP64 zone,
+ * [1] follow forward FP32, [2] follow backward re-seed + FP64 zone, [3]
+ * follow backward FP32 + output, [4] refit FP64 zone, [5] refit FP32 +
+ * output -- ms[k]: device time of the last profiled run (events between the
+ * launches; ms may be NULL), work[5k..5k+4]: that kernel's share of the
+ * counters of tpc_get_work in the same order (work may be NULL).  Waits for
+ * the stream. */
+int tpc_get_kalman_profile(tpc_ctx *ctx, float ms[6], uint64_t work[30]);
+
+/* Number of kernel launches in one tpc_run_graph (kernel nodes of the
+ * captured graph); TPC_EINVAL before the first capture. */
+int tpc_graph_kernels(tpc_ctx *ctx, int32_t *n);
 
 /* Debug trace of one tracklet's Kalman updates (a6): after
  * tpc_set_trace(ctx, t) every following tpc_find_tracks records, for each
@@ -279,25 +306,29 @@ int tpc_server_create(tpc_server **out, const tpc_config *cfg, int device, int32
                       int32_t queue_cap);
 
 /* Queue n clusters (host memory, one request) under a caller-chosen id that
- * no pending request uses.  The buffer is read when the request is admitted
- * and must stay valid and unchanged until tpc_server_poll reports it
- * finished; page-locked memory lets its copy overlap other slots' work.
- * TPC_EBUSY: the queue is full (retry later).  TPC_ENOMEM: the request alone
- * exceeds the budget.  TPC_EINVAL: bad argument or an id in use. */
-int tpc_server_submit(tpc_server *srv, int64_t request_id, const tpc_cluster *clusters, int64_t n);
+ * no pending request uses.  Results go straight to the caller's buffers:
+ * tracks_out (room for cap tracks; a track owns at least n_min_track
+ * clusters, so n / n_min_track + 1 always suffices) and cluster_track_out
+ * (n entries, or NULL), as tpc_get_tracks writes them.  All three buffers
+ * must stay valid, and the input unchanged, until tpc_server_poll reports
+ * the request finished or failed; page-locked buffers let the copies run
+ * while other requests compute.  TPC_EBUSY: the queue is full (retry
+ * later).  TPC_ENOMEM: the request alone exceeds the budget.  TPC_EINVAL:
+ * bad argument or an id in use. */
+int tpc_server_submit(tpc_server *srv, int64_t request_id, const tpc_cluster *clusters, int64_t n,
+                      tpc_track *tracks_out, int64_t cap, int32_t *cluster_track_out);
 
 /* *state: 0 queued, 1 running, 2 finished, 3 failed, -1 unknown id. */
 int tpc_server_poll(tpc_server *srv, int64_t request_id, int *state);
 
-/* Results of a finished request, as tpc_get_tracks (track_clusters is not
- * kept).  times_ms (optional): [0] queue wait, [1] admission to results on
- * the host, [2] submission to results on the host.  With out and
- * cluster_track both NULL only *n_out and times_ms are filled and the result
- * is kept; otherwise it is copied and released.  TPC_EBUSY while the request
- * is queued or running; TPC_EOVERFLOW when cap < *n_out (result kept); the
- * request's own error code when it failed (result released). */
-int tpc_server_result(tpc_server *srv, int64_t request_id, tpc_track *out, int64_t cap, int64_t *n_out,
-                      int32_t *cluster_track, double times_ms[3]);
+/* Outcome of a finished or failed request, which is then forgotten:
+ * *n_tracks (tracks written to tracks_out; the number found when cap was
+ * too small), times_ms (optional): [0] queue wait, [1] admission to results
+ * in the caller's buffers, [2] submission to results.  Returns the
+ * request's status (TPC_OK, or its error: TPC_EOVERFLOW when cap was too
+ * small, ...), TPC_EBUSY while it is queued or running (nothing changes),
+ * TPC_EINVAL for an unknown id. */
+int tpc_server_result(tpc_server *srv, int64_t request_id, int64_t *n_tracks, double times_ms[3]);
 
 /* Wait until no request is queued or running (timeout_s <= 0: no limit);
  * TPC_ETIMEOUT when the limit ran out. */

@@ -89,14 +89,18 @@ def load_library(path: str | None = None):
         "tpc_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
         "tpc_get_stage_times": ([_VP, _VP], ctypes.c_int),
         "tpc_get_work": ([_VP, _VP], ctypes.c_int),
+        "tpc_get_kalman_profile": ([_VP, _VP, _VP], ctypes.c_int),
+        "tpc_graph_kernels": ([_VP, _VP], ctypes.c_int),
         "tpc_row_params_noalloc": ([_VP, _I64, _VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_autotune": ([_VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_set_trace": ([_VP, _I32], ctypes.c_int),
         "tpc_get_trace": ([_VP, _VP, _I32, _VP], ctypes.c_int),
         "tpc_server_create": ([_VP, _VP, ctypes.c_int, _I32, ctypes.c_size_t, _I32], ctypes.c_int),
-        "tpc_server_submit": ([_VP, _I64, _VP, _I64], ctypes.c_int),
+        "tpc_server_submit": ([_VP, _I64, _VP, _I64, _VP, _I64, _VP], ctypes.c_int),
         "tpc_server_poll": ([_VP, _I64, _VP], ctypes.c_int),
-        "tpc_server_result": ([_VP, _I64, _VP, _I64, _VP, _VP, _VP], ctypes.c_int),
+        "tpc_server_result": ([_VP, _I64, _VP, _VP], ctypes.c_int),
+        "tpc_get_tracks_async": ([_VP, _VP, _I64, _VP, _VP], ctypes.c_int),
+        "tpc_get_arena_bytes": ([_VP, _VP], ctypes.c_int),
         "tpc_server_drain": ([_VP, ctypes.c_double], ctypes.c_int),
         "tpc_server_stats": ([_VP, _VP], ctypes.c_int),
         "tpc_server_destroy": ([_VP], None),
@@ -289,11 +293,48 @@ class Tracker:
         self._ck(self._lib.tpc_get_work(self._ctx, w.ctypes.data))
         return dict(zip(("prop", "upd32", "upd64", "cand", "prop64"), (int(v) for v in w)))
 
+    KALMAN_KERNELS = ("k_follow_p1", "k_follow_p2", "k_follow_p3", "k_follow_p4", "k_refit_p1", "k_refit_p2")
+
+    def kalman_profile(self, times: bool = True) -> dict:
+        """Per Kalman kernel: device ms of the last profiled run (when
+        times) and its work counters."""
+        ms = np.zeros(6, np.float32)
+        w = np.zeros(30, np.uint64)
+        self._ck(self._lib.tpc_get_kalman_profile(self._ctx, ms.ctypes.data if times else None, w.ctypes.data))
+        out = {}
+        for k, name in enumerate(self.KALMAN_KERNELS):
+            d = dict(zip(("prop", "upd32", "upd64", "cand", "prop64"), (int(v) for v in w[5 * k:5 * k + 5])))
+            if times:
+                d["ms"] = float(ms[k])
+            out[name] = d
+        return out
+
+    def graph_kernels(self) -> int:
+        n = ctypes.c_int32()
+        self._ck(self._lib.tpc_graph_kernels(self._ctx, ctypes.byref(n)))
+        return n.value
+
     def counts(self) -> dict:
         c = np.zeros(8, np.int64)
         self._ck(self._lib.tpc_get_counts(self._ctx, c.ctypes.data))
         return dict(zip(("n", "n_req", "n_rs", "n_bins", "n_tracklets", "n_tracks", "status", "n_track_clusters"),
                         (int(v) for v in c)))
+
+    def get_into(self, tracks_out, cluster_track_out=None):
+        """Wait and copy the results into caller buffers (numpy arrays or
+        pinned CPU torch tensors); returns (tracks view, cluster_track)."""
+        tr = _records(tracks_out, TRACK_DTYPE, 0)
+        ct = _records(cluster_track_out, np.int32, self.n)
+        nout = ctypes.c_int64()
+        self._ck(self._lib.tpc_get_tracks(self._ctx, tr.ctypes.data if len(tr) else None, len(tr),
+                                          ctypes.byref(nout), ct.ctypes.data if ct is not None and self.n else None,
+                                          None))
+        return tr[:nout.value], ct
+
+    def arena_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        self._ck(self._lib.tpc_get_arena_bytes(self._ctx, ctypes.byref(b)))
+        return b.value
 
     def get(self, cluster_track: bool = True, track_clusters: bool = False, cap: int | None = None):
         """Wait and copy out: (tracks, cluster_track, track_clusters)."""
@@ -351,13 +392,28 @@ class Tracker:
         raise AssertionError("unreachable")
 
 
+def _records(buf, dtype, n):
+    """A numpy view of n `dtype` records over a numpy array or a (pinned)
+    CPU torch tensor; None stays None."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        buf = buf.numpy()
+    v = buf.view(np.uint8).reshape(-1).view(dtype)
+    if len(v) < n:
+        raise ValueError(f"buffer holds {len(v)} records, {n} needed")
+    return v
+
+
 class Server:
     """Continuous-batching request loop (tpc_server_*): up to max_slots
     requests run at once, each on its own context and stream, admitted in
     arrival order while their arenas fit hbm_budget and free device memory.
 
-    submit() keeps a reference to the cluster array until result() returns,
-    since the library reads it when the request is admitted."""
+    Results are written straight into buffers given at submission (numpy
+    arrays or pinned CPU torch tensors; page-locked ones let the copies
+    overlap other requests' kernels); without them, numpy buffers are
+    allocated.  Inputs and buffers are referenced until result() returns."""
 
     STATES = {-1: "unknown", 0: "queued", 1: "running", 2: "finished", 3: "failed"}
 
@@ -365,17 +421,18 @@ class Server:
                  queue_cap: int = 1 << 20):
         self._lib = load_library()
         self._srv = ctypes.c_void_p()
+        self._n_min = (cfg or default_config()).n_min_track
         rc = self._lib.tpc_server_create(ctypes.byref(self._srv), ctypes.byref(cfg) if cfg else None, device,
                                          max_slots, hbm_budget, queue_cap)
         if rc != 0:
             raise TpcError(rc, "tpc_server_create failed")
-        self._inputs = {}
+        self._live = {}
 
     def close(self):
         if self._srv:
             self._lib.tpc_server_destroy(self._srv)
             self._srv = ctypes.c_void_p()
-            self._inputs.clear()
+            self._live.clear()
 
     def __del__(self):
         try:
@@ -389,18 +446,23 @@ class Server:
     def __exit__(self, *a):
         self.close()
 
-    def submit(self, request_id: int, clusters) -> int:
-        """Queue one request (host clusters: numpy CLUSTER_DTYPE records or a
-        pinned CPU torch tensor of them).  Returns the status code: 0, or
-        TPC_EBUSY when the queue is full."""
-        if hasattr(clusters, "data_ptr"):
-            n = clusters.numel() * clusters.element_size() // 16
-        else:
-            clusters = np.ascontiguousarray(clusters)
-            n = len(clusters)
-        rc = self._lib.tpc_server_submit(self._srv, request_id, _ptr(clusters) if n else None, n)
+    def submit(self, request_id: int, clusters, tracks_out=None, cluster_track_out=None) -> int:
+        """Queue one request (host clusters: CLUSTER_DTYPE records, numpy or
+        a pinned CPU torch tensor).  Returns 0, or TPC_EBUSY when the queue
+        is full."""
+        cl = _records(clusters, CLUSTER_DTYPE, 0)
+        n = len(cl)
+        if tracks_out is None:
+            tracks_out = np.zeros(n // max(self._n_min, 1) + 1, TRACK_DTYPE)
+        if cluster_track_out is None:
+            cluster_track_out = np.zeros(n, np.int32)
+        tr = _records(tracks_out, TRACK_DTYPE, 0)
+        ct = _records(cluster_track_out, np.int32, n)
+        rc = self._lib.tpc_server_submit(self._srv, request_id, cl.ctypes.data if n else None, n,
+                                         tr.ctypes.data if len(tr) else None, len(tr),
+                                         ct.ctypes.data if n else None)
         if rc == 0:
-            self._inputs[request_id] = (clusters, n)
+            self._live[request_id] = (clusters, cl, tr, ct, tracks_out, cluster_track_out)
         elif rc != TPC_EBUSY:
             raise TpcError(rc, f"tpc_server_submit({request_id})")
         return rc
@@ -411,27 +473,20 @@ class Server:
         return self.STATES[st.value]
 
     def result(self, request_id: int):
-        """(tracks, cluster_track, times_ms) of a finished request, or None
-        while it is queued or running.  times_ms: queue wait, service and
-        total latency in ms.  Raises TpcError if the request failed."""
+        """(tracks, cluster_track, times_ms) of a finished request -- views
+        of the buffers given at submission -- or None while it is queued or
+        running.  times_ms: queue wait, service and total latency in ms.
+        Raises TpcError if the request failed."""
         nt = ctypes.c_int64()
         times = np.zeros(3, np.float64)
-        rc = self._lib.tpc_server_result(self._srv, request_id, None, 0, ctypes.byref(nt), None,
-                                         times.ctypes.data)
+        rc = self._lib.tpc_server_result(self._srv, request_id, ctypes.byref(nt), times.ctypes.data)
         if rc == TPC_EBUSY:
             return None
+        live = self._live.pop(request_id, None)
         if rc != 0:
-            self._inputs.pop(request_id, None)
-            raise TpcError(rc, f"request {request_id} failed")
-        n = self._inputs[request_id][1]
-        tracks = np.zeros(nt.value, TRACK_DTYPE)
-        ct = np.zeros(n, np.int32)
-        rc = self._lib.tpc_server_result(self._srv, request_id, tracks.ctypes.data, nt.value, ctypes.byref(nt),
-                                         ct.ctypes.data if n else None, None)
-        if rc != 0:
-            raise TpcError(rc, f"request {request_id}: copying results")
-        self._inputs.pop(request_id, None)
-        return tracks, ct, times
+            raise TpcError(rc, f"request {request_id} failed ({nt.value} tracks found)")
+        _, _, tr, ct, _, _ = live
+        return tr[:nt.value], ct, times
 
     def drain(self, timeout_s: float = 0.0):
         rc = self._lib.tpc_server_drain(self._srv, timeout_s)

@@ -63,17 +63,23 @@ struct Counts {
   int32_t trace_n;              // trace records written
   int32_t pad3;
   unsigned long long pad2[2];
+  // the same counters per Kalman kernel (PH_*): {prop, upd32, upd64, cand, prop64}
+  unsigned long long phase_work[6][5];
 };
+
+// Kalman kernels, in launch order, for the per-kernel work counters.
+enum { PH_FOLLOW_P1 = 0, PH_FOLLOW_P2, PH_FOLLOW_P3, PH_FOLLOW_P4, PH_REFIT_P1, PH_REFIT_P2, PH_COUNT };
 
 // Per-thread work tallies, flushed once per thread into Counts.
 struct Tally {
   unsigned long long prop = 0, upd32 = 0, upd64 = 0, cand = 0, prop64 = 0;
-  __device__ __forceinline__ void flush(Counts* cn) {
-    if (prop) atomicAdd(&cn->n_prop, prop);
-    if (upd32) atomicAdd(&cn->n_upd32, upd32);
-    if (upd64) atomicAdd(&cn->n_upd64, upd64);
-    if (cand) atomicAdd(&cn->n_cand, cand);
-    if (prop64) atomicAdd(&cn->n_prop64, prop64);
+  __device__ __forceinline__ void flush(Counts* cn, int phase) {
+    unsigned long long* w = cn->phase_work[phase];
+    if (prop) atomicAdd(&cn->n_prop, prop), atomicAdd(&w[0], prop);
+    if (upd32) atomicAdd(&cn->n_upd32, upd32), atomicAdd(&w[1], upd32);
+    if (upd64) atomicAdd(&cn->n_upd64, upd64), atomicAdd(&w[2], upd64);
+    if (cand) atomicAdd(&cn->n_cand, cand), atomicAdd(&w[3], cand);
+    if (prop64) atomicAdd(&cn->n_prop64, prop64), atomicAdd(&w[4], prop64);
   }
 };
 

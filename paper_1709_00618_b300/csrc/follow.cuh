@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
     }
     work_store(W, t, w, p, C, chi2, go);
   }
-  tl.flush(cn);
+  tl.flush(cn, PH_FOLLOW_P1);
 }
 
 // Phase 2: the rest of the forward pass (covariance in FP32); a lane that
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(128) k_follow_p2(GridView g, const int32_t* __
       }
     }
   }
-  tl.flush(cn);
+  tl.flush(cn, PH_FOLLOW_P2);
 }
 
 // Phase 3: re-seed at the outermost forward cluster and run the backward
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
     }
     work_store(W, t, w, p, C, chi2, go);
   }
-  tl.flush(cn);
+  tl.flush(cn, PH_FOLLOW_P3);
 }
 
 __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t t, const Lane& w, float zref0) {
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(128) k_follow_p4(GridView g, const int32_t* __
       }
     }
   }
-  tl.flush(cn);
+  tl.flush(cn, PH_FOLLOW_P4);
 }
 
 }  // namespace tpc

@@ -328,14 +328,14 @@ struct LocalTally {
     if (sizeof(T) == 8) upd64++;
     else upd32++;
   }
-  __device__ __forceinline__ void flush(Counts* cn) {
+  __device__ __forceinline__ void flush(Counts* cn, int phase) {
     Tally t;
     t.prop = prop;
     t.prop64 = prop64;
     t.upd32 = upd32;
     t.upd64 = upd64;
     t.cand = cand;
-    t.flush(cn);
+    t.flush(cn, phase);
   }
 };
 

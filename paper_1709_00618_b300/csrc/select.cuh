@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst
     s.unit = __ldg(g.rs_of + w.h[0]) / NROW;
     s.t = t;
   }
-  tl.flush(cn);
+  tl.flush(cn, PH_REFIT_P1);
 }
 
 __device__ __forceinline__ void write_track(const RefitIn& in, const float* sX, int64_t m, const RefitWork& s,
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
       if (m < M) load(m);
     }
   }
-  tl.flush(cn);
+  tl.flush(cn, PH_REFIT_P2);
 }
 
 }  // namespace tpc

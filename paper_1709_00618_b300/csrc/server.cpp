@@ -8,17 +8,17 @@
 // context on its own CUDA stream, so a request admitted while others run
 // overlaps with them on the GPU.  A slot keeps its arena (grid, links,
 // tracklet and track buffers) between requests and grows it only for a
-// larger request; idle slots give their arenas back when the budget would
-// otherwise block the head of the queue.  Completion is seen through one
-// CUDA event per slot; the worker then copies the results to host memory
-// and frees the slot.
+// larger request (stream-ordered, so other slots keep running); idle slots
+// give their arenas back when the budget would otherwise block the head of
+// the queue.  The worker never waits on the GPU: it polls one CUDA event per
+// slot, then enqueues the copy of the results into the caller's buffers and
+// polls again, so one request's copies overlap the others' kernels.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
-#include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -41,19 +41,25 @@ struct Request {
   int64_t id = 0;
   const tpc_cluster* clusters = nullptr;
   int64_t n = 0;
+  tpc_track* out = nullptr;
+  int64_t cap = 0;
+  int32_t* cluster_track = nullptr;
   int state = RQ_QUEUED;
   int rc = TPC_OK;
+  int64_t n_tracks = -1;
+  bool retried = false;
   Clock::time_point t_submit, t_start, t_done;
-  std::vector<tpc_track> tracks;
-  std::vector<int32_t> cluster_track;
 };
+
+enum { SL_FREE = 0, SL_RUN = 1, SL_COPY = 2 };
 
 struct Slot {
   tpc_ctx* ctx = nullptr;
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
-  size_t arena = 0;   // device bytes held by this slot's context
-  Request* req = nullptr;  // running request (worker thread only)
+  size_t arena = 0;        // device bytes held by this slot's context
+  int phase = SL_FREE;     // worker thread only
+  Request* req = nullptr;  // worker thread only
 };
 
 constexpr size_t kHeadroom = size_t(256) << 20;  // free memory kept for other allocations
@@ -78,17 +84,21 @@ struct tpc_server {
   void loop();
   int pick_slot_locked(size_t need, bool* any_busy);
   bool admit_one();
-  void finish(Slot& s);
-  void complete_locked(Request* r, int rc);
+  void advance(Slot& s);
+  void complete(Slot& s, int rc);
   int trim_idle_locked(size_t want);
+  int launch(Slot& s);
+  void account(Slot& s);
 };
 
-void tpc_server::complete_locked(Request* r, int rc) {
-  r->rc = rc;
-  r->state = rc == TPC_OK ? RQ_DONE : RQ_FAILED;
-  r->t_done = Clock::now();
-  completed++;
-  cv_done.notify_all();
+// Book the slot's actual arena size (capacities only grow, and may exceed
+// tpc_arena_bytes after a retry with larger tracklet capacity).
+void tpc_server::account(Slot& s) {
+  size_t b = 0;
+  tpc_get_arena_bytes(s.ctx, &b);
+  std::lock_guard<std::mutex> lk(mu);
+  reserved = reserved - s.arena + b;
+  s.arena = b;
 }
 
 // Recreate idle slots' contexts (dropping their arenas) until `want` more
@@ -97,31 +107,33 @@ int tpc_server::trim_idle_locked(size_t want) {
   int trimmed = 0;
   for (Slot& s : slots) {
     if (budget == 0 || reserved + want <= budget) break;
-    if (s.req || s.arena == 0) continue;
-    tpc_ctx* fresh = nullptr;
+    if (s.phase != SL_FREE || s.arena == 0) continue;
     tpc_destroy(s.ctx);
     s.ctx = nullptr;
     reserved -= s.arena;
     s.arena = 0;
+    tpc_ctx* fresh = nullptr;
     if (tpc_create(&fresh, &cfg, device, s.stream, 0) == TPC_OK) s.ctx = fresh;
     trimmed++;
   }
   return trimmed;
 }
 
-// A free slot for a request needing `need` arena bytes: one that already
-// holds enough, else one that may grow within the budget and free memory.
+// A free slot for a request needing `need` arena bytes: the smallest one
+// that already holds enough, else the largest one, grown within the budget
+// and the free device memory.
 int tpc_server::pick_slot_locked(size_t need, bool* any_busy) {
   *any_busy = false;
   int fits = -1, grows = -1;
   for (size_t i = 0; i < slots.size(); i++) {
-    if (slots[i].req) {
+    const Slot& s = slots[i];
+    if (s.phase != SL_FREE) {
       *any_busy = true;
       continue;
     }
-    if (!slots[i].ctx) continue;
-    if (slots[i].arena >= need && fits < 0) fits = (int)i;
-    if (grows < 0 || slots[i].arena > slots[grows].arena) grows = (int)i;
+    if (!s.ctx) continue;
+    if (s.arena >= need && (fits < 0 || s.arena < slots[fits].arena)) fits = (int)i;
+    if (grows < 0 || s.arena > slots[grows].arena) grows = (int)i;
   }
   if (fits >= 0) return fits;
   if (grows < 0) return -1;
@@ -135,6 +147,14 @@ int tpc_server::pick_slot_locked(size_t need, bool* any_busy) {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || grow + kHeadroom > free_b) return -1;
   return grows;
+}
+
+int tpc_server::launch(Slot& s) {
+  Request* r = s.req;
+  int rc = tpc_load_clusters(s.ctx, r->clusters, r->n, 0);
+  if (rc == TPC_OK) rc = tpc_run_graph(s.ctx);
+  if (rc == TPC_OK && cudaEventRecord(s.done, s.stream) != cudaSuccess) rc = TPC_ECUDA;
+  return rc;
 }
 
 bool tpc_server::admit_one() {
@@ -151,7 +171,11 @@ bool tpc_server::admit_one() {
     if (pick < 0) {
       if (!any_busy && budget && need > budget) {  // can never fit
         queue.pop_front();
-        complete_locked(r, TPC_ENOMEM);
+        r->rc = TPC_ENOMEM;
+        r->state = RQ_FAILED;
+        r->t_start = r->t_done = Clock::now();
+        completed++;
+        cv_done.notify_all();
         return true;
       }
       return false;
@@ -164,50 +188,60 @@ bool tpc_server::admit_one() {
     r->state = RQ_RUNNING;
     r->t_start = Clock::now();
     s->req = r;
+    s->phase = SL_RUN;
     admitted++;
     int64_t running = 0;
-    for (const Slot& t : slots) running += t.req != nullptr;
+    for (const Slot& t : slots) running += t.phase != SL_FREE;
     peak_running = std::max(peak_running, running);
   }
-  // enqueue outside the lock: reserve, copy in, graph launch, completion event
-  int rc = grow ? tpc_reserve(s->ctx, r->n, 1, 0, 0) : TPC_OK;
-  if (rc == TPC_OK) rc = tpc_load_clusters(s->ctx, r->clusters, r->n, 0);
-  if (rc == TPC_OK) rc = tpc_run_graph(s->ctx);
-  if (rc == TPC_OK && cudaEventRecord(s->done, s->stream) != cudaSuccess) rc = TPC_ECUDA;
-  if (rc != TPC_OK) {
-    std::lock_guard<std::mutex> lk(mu);
-    s->req = nullptr;
-    complete_locked(r, rc);
+  // enqueue outside the lock: arena growth, copy in, graph, completion event
+  int rc = TPC_OK;
+  if (grow) {
+    rc = tpc_reserve(s->ctx, r->n, 1, 0, 0);
+    account(*s);
   }
+  if (rc == TPC_OK) rc = launch(*s);
+  if (rc != TPC_OK) complete(*s, rc);
   return true;
 }
 
-void tpc_server::finish(Slot& s) {
+void tpc_server::complete(Slot& s, int rc) {
   Request* r = s.req;
-  int64_t nt = 0;
-  // size query (TPC_EOVERFLOW with *n_out set when tracks exist), then copy
-  int rc = tpc_get_tracks(s.ctx, nullptr, 0, &nt, nullptr, nullptr);
-  if (rc == TPC_OK || (rc == TPC_EOVERFLOW && nt > 0)) {
-    r->tracks.resize((size_t)nt);
-    r->cluster_track.resize((size_t)r->n);
-    rc = tpc_get_tracks(s.ctx, r->tracks.data(), nt, &nt, r->n ? r->cluster_track.data() : nullptr, nullptr);
-  }
-  if (rc == TPC_EOVERFLOW) {
-    // an internal capacity (tracklets) overflowed: rerun once with the
-    // worst-case capacity, synchronously on this slot
-    rc = tpc_reserve(s.ctx, r->n, 1, 0, r->n / 3 + 16);
-    if (rc == TPC_OK) rc = tpc_load_clusters(s.ctx, r->clusters, r->n, 0);
-    if (rc == TPC_OK) rc = tpc_run_graph(s.ctx);
-    if (rc == TPC_OK) rc = tpc_get_tracks(s.ctx, nullptr, 0, &nt, nullptr, nullptr);
-    if (rc == TPC_OK || (rc == TPC_EOVERFLOW && nt > 0)) {
-      r->tracks.resize((size_t)nt);
-      r->cluster_track.resize((size_t)r->n);
-      rc = tpc_get_tracks(s.ctx, r->tracks.data(), nt, &nt, r->n ? r->cluster_track.data() : nullptr, nullptr);
-    }
-  }
   std::lock_guard<std::mutex> lk(mu);
+  r->rc = rc;
+  r->state = rc == TPC_OK ? RQ_DONE : RQ_FAILED;
+  r->t_done = Clock::now();
   s.req = nullptr;
-  complete_locked(r, rc);
+  s.phase = SL_FREE;
+  completed++;
+  cv_done.notify_all();
+}
+
+// One step of a slot whose event has fired.
+void tpc_server::advance(Slot& s) {
+  Request* r = s.req;
+  if (s.phase == SL_COPY) {
+    complete(s, TPC_OK);
+    return;
+  }
+  int64_t nt = -1;
+  int rc = tpc_get_tracks_async(s.ctx, r->out, r->cap, &nt, r->cluster_track);
+  if (rc == TPC_EOVERFLOW && nt < 0 && !r->retried) {
+    // a device capacity (tracklets) overflowed: rerun once on this slot
+    // with the worst-case capacity, without waiting
+    r->retried = true;
+    rc = tpc_reserve(s.ctx, r->n, 1, 0, r->n / 3 + 16);
+    account(s);
+    if (rc == TPC_OK) rc = launch(s);
+    if (rc != TPC_OK) complete(s, rc);
+    return;
+  }
+  r->n_tracks = nt;
+  if (rc != TPC_OK || cudaEventRecord(s.done, s.stream) != cudaSuccess) {
+    complete(s, rc != TPC_OK ? rc : TPC_ECUDA);
+    return;
+  }
+  s.phase = SL_COPY;
 }
 
 void tpc_server::loop() {
@@ -215,12 +249,14 @@ void tpc_server::loop() {
   while (!stop.load()) {
     bool active = false;
     for (Slot& s : slots) {
-      if (!s.req) continue;
+      if (s.phase == SL_FREE) continue;
       active = true;
-      if (cudaEventQuery(s.done) != cudaErrorNotReady) finish(s);
+      const cudaError_t q = cudaEventQuery(s.done);
+      if (q == cudaSuccess) advance(s);
+      else if (q != cudaErrorNotReady) complete(s, TPC_ECUDA);
     }
     while (admit_one()) active = true;
-    std::this_thread::sleep_for(std::chrono::microseconds(active ? 20 : 100));
+    std::this_thread::sleep_for(std::chrono::microseconds(active ? 10 : 100));
   }
 }
 
@@ -254,8 +290,9 @@ int tpc_server_create(tpc_server** out, const tpc_config* cfg, int device, int32
   return TPC_OK;
 }
 
-int tpc_server_submit(tpc_server* srv, int64_t request_id, const tpc_cluster* clusters, int64_t n) {
-  if (!srv || n < 0 || (n > 0 && !clusters)) return TPC_EINVAL;
+int tpc_server_submit(tpc_server* srv, int64_t request_id, const tpc_cluster* clusters, int64_t n,
+                      tpc_track* tracks_out, int64_t cap, int32_t* cluster_track_out) {
+  if (!srv || n < 0 || (n > 0 && !clusters) || cap < 0 || (cap > 0 && !tracks_out)) return TPC_EINVAL;
   if (srv->budget && tpc_arena_bytes(n, 1) > srv->budget) return TPC_ENOMEM;
   std::lock_guard<std::mutex> lk(srv->mu);
   if ((int32_t)srv->queue.size() >= srv->queue_cap) return TPC_EBUSY;
@@ -264,6 +301,9 @@ int tpc_server_submit(tpc_server* srv, int64_t request_id, const tpc_cluster* cl
   r.id = request_id;
   r.clusters = clusters;
   r.n = n;
+  r.out = tracks_out;
+  r.cap = cap;
+  r.cluster_track = cluster_track_out;
   r.t_submit = Clock::now();
   srv->queue.push_back(&r);
   return TPC_OK;
@@ -277,31 +317,22 @@ int tpc_server_poll(tpc_server* srv, int64_t request_id, int* state) {
   return TPC_OK;
 }
 
-int tpc_server_result(tpc_server* srv, int64_t request_id, tpc_track* out, int64_t cap, int64_t* n_out,
-                      int32_t* cluster_track, double times_ms[3]) {
+int tpc_server_result(tpc_server* srv, int64_t request_id, int64_t* n_tracks, double times_ms[3]) {
   if (!srv) return TPC_EINVAL;
   std::lock_guard<std::mutex> lk(srv->mu);
   auto it = srv->reqs.find(request_id);
   if (it == srv->reqs.end()) return TPC_EINVAL;
   Request& r = it->second;
   if (r.state < RQ_DONE) return TPC_EBUSY;
-  if (n_out) *n_out = (int64_t)r.tracks.size();
+  if (n_tracks) *n_tracks = r.n_tracks;
   if (times_ms) {
     times_ms[0] = ms_between(r.t_submit, r.t_start);
     times_ms[1] = ms_between(r.t_start, r.t_done);
     times_ms[2] = ms_between(r.t_submit, r.t_done);
   }
-  if (r.state == RQ_FAILED) {
-    const int rc = r.rc;
-    srv->reqs.erase(it);
-    return rc;
-  }
-  if (!out && !cluster_track) return TPC_OK;  // size and time query
-  if ((int64_t)r.tracks.size() > cap) return TPC_EOVERFLOW;
-  if (out && !r.tracks.empty()) memcpy(out, r.tracks.data(), sizeof(tpc_track) * r.tracks.size());
-  if (cluster_track && r.n) memcpy(cluster_track, r.cluster_track.data(), sizeof(int32_t) * (size_t)r.n);
+  const int rc = r.rc;
   srv->reqs.erase(it);
-  return TPC_OK;
+  return rc;
 }
 
 int tpc_server_drain(tpc_server* srv, double timeout_s) {

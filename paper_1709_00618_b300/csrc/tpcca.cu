@@ -198,10 +198,15 @@ struct tpc_ctx {
   bool prof = false;
   bool prof_valid = false;
   cudaEvent_t ev[7] = {};
+  cudaEvent_t evk[6] = {};  // after follow p1, p2, p3; before refit p1; after refit p1, p2
+  int32_t graph_kernels = 0;  // kernel nodes of the captured graph
   std::string err;
 
   void mark(int i) {
     if (prof) cudaEventRecord(ev[i], stream);
+  }
+  void mark_k(int i) {
+    if (prof) cudaEventRecord(evk[i], stream);
   }
 
   template <typename T>
@@ -279,17 +284,21 @@ int do_reserve(tpc_ctx* ctx, const Caps& want) {
   if (ctx->own_arena) {
     if (ctx->budget && L.total > ctx->budget)
       return fail(ctx, TPC_ENOMEM, "arena of %zu bytes exceeds the HBM budget of %zu bytes", L.total, ctx->budget);
+    // stream-ordered: neither the free nor the allocation waits for other
+    // streams of the device (contexts of a server keep running meanwhile)
     CK(cudaSetDevice(ctx->device));
     if (ctx->arena) {
-      CK(cudaStreamSynchronize(ctx->stream));
-      CK(cudaFree(ctx->arena));
+      CK(cudaFreeAsync(ctx->arena, ctx->stream));
       ctx->arena = nullptr;
+      ctx->arena_bytes = 0;
     }
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, L.total);
+    cudaError_t e = cudaMallocAsync(&p, L.total, ctx->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
-      return fail(ctx, TPC_ENOMEM, "cudaMalloc(%zu): %s", L.total, cudaGetErrorString(e));
+      ctx->caps = Caps{};
+      ctx->loaded = ctx->found = ctx->fitted = false;
+      return fail(ctx, TPC_ENOMEM, "cudaMallocAsync(%zu): %s", L.total, cudaGetErrorString(e));
     }
     ctx->arena = (char*)p;
     ctx->arena_bytes = L.total;
@@ -455,8 +464,11 @@ void enqueue_find(tpc_ctx* ctx) {
     k_follow_p1<<<gF, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
                                   ctx->ptr<int32_t>(L.tl_end), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx),
                                   W, cn);
+    ctx->mark_k(0);
     k_follow_p2<<<gP, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, cn);
+    ctx->mark_k(1);
     k_follow_p3<<<gF, bf, 0, s>>>(grid_view(ctx), ctx->kc, follow_out(ctx), W, cn);
+    ctx->mark_k(2);
     k_follow_p4<<<gP, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, cn);
   }
   ctx->mark(4);
@@ -507,9 +519,12 @@ void enqueue_fit(tpc_ctx* ctx) {
     in.nown = ctx->ptr<int32_t>(L.nown);
     in.toff = ctx->ptr<int32_t>(L.toff);
     RefitWork* RW = ctx->ptr<RefitWork>(L.rwork);
+    ctx->mark_k(3);
     k_refit_p1<<<gF, ctx->block_follow, 0, s>>>(grid_view(ctx), in, ctx->kc, RW, cn);
+    ctx->mark_k(4);
     k_refit_p2<<<persistent_grid(ctx, ctx->block_follow), ctx->block_follow, 0, s>>>(
         grid_view(ctx), in, ctx->kc, RW, ctx->ptr<tpc_track>(L.tracks), cn);
+    ctx->mark_k(5);
   }
   k_track_clusters<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
                                      ctx->ptr<int32_t>(L.f_nf), ctx->ptr<int32_t>(L.hits),
@@ -518,6 +533,19 @@ void enqueue_fit(tpc_ctx* ctx) {
   cudaMemcpyAsync(ctx->h_counts, cn, sizeof(Counts), cudaMemcpyDeviceToHost, s);
   ctx->mark(6);
   ctx->prof_valid = ctx->prof;
+}
+
+int32_t count_kernel_nodes(cudaGraph_t g) {
+  size_t n = 0;
+  if (cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess || n == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (cudaGraphGetNodes(g, nodes.data(), &n) != cudaSuccess) return 0;
+  int32_t k = 0;
+  for (size_t i = 0; i < n; i++) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) k++;
+  }
+  return k;
 }
 
 int check_status(tpc_ctx* ctx) {
@@ -624,7 +652,12 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   for (int i = 0; i < 7; i++)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  if (ctx->own_arena && ctx->arena) cudaFree(ctx->arena);
+  for (int i = 0; i < 6; i++)
+    if (ctx->evk[i]) cudaEventDestroy(ctx->evk[i]);
+  if (ctx->own_arena && ctx->arena) {
+    cudaFreeAsync(ctx->arena, ctx->stream);
+    cudaStreamSynchronize(ctx->stream);
+  }
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_req) cudaFreeHost(ctx->h_req);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -691,6 +724,7 @@ int tpc_run_graph(tpc_ctx* ctx) {
     ctx->prof = prof;
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) return fail(ctx, TPC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    ctx->graph_kernels = count_kernel_nodes(g);
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -735,6 +769,34 @@ int tpc_get_tracks(tpc_ctx* ctx, tpc_track* out, int64_t cap, int64_t* n_out, in
     CK(cudaMemcpyAsync(track_clusters, ctx->ptr<int32_t>(L.track_clusters), sizeof(int32_t) * hc.n_track_clusters,
                        cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return TPC_OK;
+}
+
+int tpc_get_arena_bytes(tpc_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return TPC_EINVAL;
+  *bytes = ctx->arena ? ctx->arena_bytes : 0;
+  return TPC_OK;
+}
+
+int tpc_get_tracks_async(tpc_ctx* ctx, tpc_track* out, int64_t cap, int64_t* n_out, int32_t* cluster_track) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->fitted) return fail(ctx, TPC_EINVAL, "tpc_fit_tracks has not run");
+  CK(cudaSetDevice(ctx->device));
+  const cudaError_t q = cudaStreamQuery(ctx->stream);
+  if (q == cudaErrorNotReady) return fail(ctx, TPC_EBUSY, "the run has not completed");
+  if (q != cudaSuccess) return fail(ctx, TPC_ECUDA, "stream: %s", cudaGetErrorString(q));
+  int rc = check_status(ctx);
+  if (rc) return rc;
+  const Counts& hc = *ctx->h_counts;
+  if (n_out) *n_out = hc.n_tracks;
+  if (hc.n_tracks > cap) return fail(ctx, TPC_EOVERFLOW, "%d tracks do not fit cap %lld", hc.n_tracks, (long long)cap);
+  const Layout& L = ctx->L;
+  if (out && hc.n_tracks)
+    CK(cudaMemcpyAsync(out, ctx->ptr<tpc_track>(L.tracks), sizeof(tpc_track) * hc.n_tracks, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  if (cluster_track && ctx->n)
+    CK(cudaMemcpyAsync(cluster_track, ctx->ptr<int32_t>(L.cluster_track), sizeof(int32_t) * ctx->n,
+                       cudaMemcpyDeviceToHost, ctx->stream));
   return TPC_OK;
 }
 
@@ -914,8 +976,10 @@ int tpc_get_trace(tpc_ctx* ctx, float* out, int32_t cap_records, int32_t* n_reco
 int tpc_set_profiling(tpc_ctx* ctx, int on) {
   if (!ctx) return TPC_EINVAL;
   CK(cudaSetDevice(ctx->device));
-  if (on && !ctx->ev[0])
+  if (on && !ctx->ev[0]) {
     for (int i = 0; i < 7; i++) CK(cudaEventCreate(&ctx->ev[i]));
+    for (int i = 0; i < 6; i++) CK(cudaEventCreate(&ctx->evk[i]));
+  }
   ctx->prof = on != 0;
   ctx->prof_valid = false;
   return TPC_OK;
@@ -927,6 +991,33 @@ int tpc_get_stage_times(tpc_ctx* ctx, float ms[6]) {
   CK(cudaSetDevice(ctx->device));
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < 6; i++) CK(cudaEventElapsedTime(&ms[i], ctx->ev[i], ctx->ev[i + 1]));
+  return TPC_OK;
+}
+
+int tpc_get_kalman_profile(tpc_ctx* ctx, float ms[6], uint64_t work[30]) {
+  if (!ctx || (!ms && !work)) return TPC_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ms) {
+    if (!ctx->prof_valid) return fail(ctx, TPC_EINVAL, "no profiled run (tpc_set_profiling, then find + fit)");
+    const cudaEvent_t b[6] = {ctx->ev[3], ctx->evk[0], ctx->evk[1], ctx->evk[2], ctx->evk[3], ctx->evk[4]};
+    const cudaEvent_t e[6] = {ctx->evk[0], ctx->evk[1], ctx->evk[2], ctx->ev[4], ctx->evk[4], ctx->evk[5]};
+    for (int i = 0; i < 6; i++) CK(cudaEventElapsedTime(&ms[i], b[i], e[i]));
+  }
+  if (work) {
+    if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "nothing loaded");
+    Counts hc{};
+    CK(cudaMemcpy(&hc, ctx->ptr<Counts>(ctx->L.counts), sizeof(Counts), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < PH_COUNT; k++)
+      for (int j = 0; j < 5; j++) work[5 * k + j] = hc.phase_work[k][j];
+  }
+  return TPC_OK;
+}
+
+int tpc_graph_kernels(tpc_ctx* ctx, int32_t* n) {
+  if (!ctx || !n) return TPC_EINVAL;
+  if (!ctx->graph) return fail(ctx, TPC_EINVAL, "no graph captured yet (tpc_run_graph)");
+  *n = ctx->graph_kernels;
   return TPC_OK;
 }
 

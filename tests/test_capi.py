@@ -67,10 +67,12 @@ def test_server_arguments_are_checked_without_a_device():
     assert lib.tpc_server_create(ctypes.byref(srv), None, 0, 0, 0, 16) == tpc.TPC_EINVAL
     assert lib.tpc_server_create(ctypes.byref(srv), None, 0, 4, 0, 0) == tpc.TPC_EINVAL
     assert lib.tpc_server_create(None, None, 0, 4, 0, 16) == tpc.TPC_EINVAL
-    assert lib.tpc_server_submit(None, 1, None, 0) == tpc.TPC_EINVAL
+    assert lib.tpc_server_submit(None, 1, None, 0, None, 0, None) == tpc.TPC_EINVAL
     st = ctypes.c_int()
     assert lib.tpc_server_poll(None, 1, ctypes.byref(st)) == tpc.TPC_EINVAL
-    assert lib.tpc_server_result(None, 1, None, 0, None, None, None) == tpc.TPC_EINVAL
+    assert lib.tpc_server_result(None, 1, None, None) == tpc.TPC_EINVAL
+    assert lib.tpc_get_tracks_async(None, None, 0, None, None) == tpc.TPC_EINVAL
+    assert lib.tpc_get_arena_bytes(None, None) == tpc.TPC_EINVAL
     assert lib.tpc_server_drain(None, 0.0) == tpc.TPC_EINVAL
     lib.tpc_server_destroy(None)
     rc = lib.tpc_server_create(ctypes.byref(srv), None, 0, 2, 0, 16)

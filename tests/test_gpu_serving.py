@@ -85,7 +85,37 @@ def test_server_poll_and_unknown_ids():
         assert srv.poll(5) == "finished"
         tracks, ct, _ = srv.result(5)
         assert srv.poll(5) == "unknown"
+        # too small an output buffer: the request fails with the count found
+        assert srv.submit(6, c, tracks_out=np.zeros(3, tpc.TRACK_DTYPE)) == 0
+        srv.drain(timeout_s=120)
+        with pytest.raises(tpc.TpcError) as e:
+            srv.result(6)
+        assert e.value.code == tpc.TPC_EOVERFLOW and f"({len(tracks)} tracks found)" in str(e.value)
     assert len(tracks) > 50 and (ct >= 0).sum() > 0
+
+
+def test_server_pinned_buffers_and_plain_get_into():
+    """Page-locked inputs and outputs (asynchronous copies) give the same
+    bytes as the plain path writing into caller buffers."""
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    reqs = [r.clusters for r in synth.batch_requests(seed=25, n_requests=6, max_tracks=4000)]
+    pins = [torch.from_numpy(c.view(np.uint8)).pin_memory() for c in reqs]
+    outs = [(torch.zeros(len(c) // 10 + 1, 128, dtype=torch.uint8).pin_memory(),
+             torch.zeros(len(c), dtype=torch.int32).pin_memory()) for c in reqs]
+    with tpc.Server(device=0, max_slots=3) as srv:
+        for i, (p, (to, co)) in enumerate(zip(pins, outs)):
+            assert srv.submit(i, p, tracks_out=to, cluster_track_out=co) == 0
+        srv.drain(timeout_s=300)
+        got = [srv.result(i) for i in range(len(reqs))]
+    with tpc.Tracker(device=0) as t:
+        for c, (tb, cb, _) in zip(reqs, got):
+            t.load(c).find().fit()
+            tr = np.zeros(len(c) // 10 + 1, tpc.TRACK_DTYPE)
+            ct = np.zeros(len(c), np.int32)
+            ta, ca = t.get_into(tr, ct)
+            assert ta.tobytes() == tb.tobytes() and np.array_equal(ca, cb)
 
 
 def test_autotuned_shapes_give_the_same_result():
@@ -151,3 +181,30 @@ def test_tracklet_overflow_is_retried_not_truncated():
         srv.drain(timeout_s=300)
         tb, cb, _ = srv.result(0)
     assert tb.tobytes() == ref_tracks.tobytes() and np.array_equal(cb, ref_ct)
+
+
+def test_kernel_profile_adds_up():
+    """Per-Kalman-kernel counters sum to the totals; per-kernel times fit in
+    their stages; the captured graph's kernel count is stable."""
+    import paper_1709_00618_b300 as tpc
+    p = synth.GenParams(seed=11, n_primaries=1500, n_secondaries=300, sectors=(0, 1, 2, 18, 19, 20))
+    cl = synth.generate(p).clusters
+    with tpc.Tracker(device=0) as t:
+        t.set_profiling(True)
+        t.load(cl).find().fit().sync()
+        st = t.stage_times()
+        kp = t.kalman_profile()
+        work = t.work()
+        t.set_profiling(False)
+        t.load(cl).run_graph().sync()
+        nk = t.graph_kernels()
+        t.load(cl).run_graph().sync()
+        assert t.graph_kernels() == nk
+    for key in ("prop", "upd32", "upd64", "cand", "prop64"):
+        assert sum(d[key] for d in kp.values()) == work[key], key
+    assert kp["k_follow_p1"]["upd64"] > 0 and kp["k_follow_p2"]["upd32"] > 0 and kp["k_refit_p2"]["upd32"] > 0
+    assert kp["k_follow_p2"]["upd64"] == 0 and kp["k_follow_p4"]["upd64"] == 0 and kp["k_refit_p2"]["upd64"] == 0
+    follow = sum(kp[k]["ms"] for k in ("k_follow_p1", "k_follow_p2", "k_follow_p3", "k_follow_p4"))
+    assert abs(follow - st["follow"]) < 1e-3 + 1e-3 * st["follow"]
+    assert kp["k_refit_p1"]["ms"] + kp["k_refit_p2"]["ms"] <= st["refit"] + 1e-3
+    assert 30 <= nk <= 60
