@@ -272,19 +272,27 @@ int tpc_row_params_noalloc(const tpc_cluster *d_clusters, int64_t n, const int64
                            void *d_params_out, void *cuda_stream);
 
 /* ------------------------------------------------------ tuning (autotuner) */
-/* Threads per block of the cluster-, row-sector- and tracklet-parallel
- * kernels and CTAs per SM of the persistent follow/refit launches.  0 keeps
- * the current value.  Invalidates a captured graph. */
-int tpc_set_tuning(tpc_ctx *ctx, int block_clusters, int block_follow, int ctas_per_sm_follow, int reserved);
+/* Launch shapes (0 keeps the current value): threads per block of the
+ * cluster-, row-sector- and tracklet-parallel kernels (multiple of 32, at
+ * most 1024) and of the Kalman kernels (32..128); the most CTAs per SM of
+ * the persistent Kalman kernels -- those running the FP64 zones and those
+ * that refill lanes -- whose grids are one wave of resident CTAs (64: as
+ * many as fit); refill: idle lanes of a warp of a refilling Kalman kernel
+ * that trigger the warp's common fetch of new tracklets (1..32; 1: each
+ * lane refills at once).  Results do not depend on them.  Invalidates a
+ * captured graph. */
+int tpc_set_tuning(tpc_ctx *ctx, int block_clusters, int block_follow, int ctas_per_sm_zone, int ctas_per_sm_follow,
+                   int refill);
 
 /* Autotuner: with a representative batch loaded, times tpc_find_tracks +
  * tpc_fit_tracks (median of reps runs, CUDA events on the context's stream)
- * for threads per block of the cluster-parallel kernels (128/256/512), of
- * the Kalman kernels (64/96/128) and CTAs per SM of their static phases
- * (2/4/8), by coordinate descent, keeps the fastest and reports it in
- * choice[3] (same order as tpc_set_tuning) and *best_ms.  The results of
- * the loaded batch are overwritten (rerun tpc_find_tracks before get). */
-int tpc_autotune(tpc_ctx *ctx, int32_t reps, int32_t choice[3], float *best_ms);
+ * over block_clusters {128, 256, 512}, block_follow {64, 96, 128},
+ * ctas_per_sm_zone {1, 2, 3}, ctas_per_sm_follow {2, 3, 64} and refill
+ * {1, 4, 8, 16} by coordinate descent from the current shapes, keeps the
+ * fastest and reports it in choice[5] (the order of tpc_set_tuning) and
+ * *best_ms.  The results of the loaded batch are overwritten (rerun
+ * tpc_find_tracks before get). */
+int tpc_autotune(tpc_ctx *ctx, int32_t reps, int32_t choice[5], float *best_ms);
 
 /* ------------------------------------------------------ serving (requests) */
 /* Continuous-batching request loop: the serving form of tracking several

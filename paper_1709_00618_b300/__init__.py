@@ -85,7 +85,7 @@ def load_library(path: str | None = None):
         "tpc_sync": ([_VP], ctypes.c_int),
         "tpc_get_counts": ([_VP, _VP], ctypes.c_int),
         "tpc_get_stage": ([_VP, ctypes.c_int, _VP, _I64, _VP], ctypes.c_int),
-        "tpc_set_tuning": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "tpc_set_tuning": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "tpc_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
         "tpc_get_stage_times": ([_VP, _VP], ctypes.c_int),
         "tpc_get_work": ([_VP, _VP], ctypes.c_int),
@@ -229,8 +229,11 @@ class Tracker:
     def reserve(self, n_clusters=0, n_requests=0, n_bins=0, n_tracklets=0):
         self._ck(self._lib.tpc_reserve(self._ctx, n_clusters, n_requests, n_bins, n_tracklets))
 
-    def set_tuning(self, block_clusters=0, block_follow=0, ctas_per_sm_follow=0):
-        self._ck(self._lib.tpc_set_tuning(self._ctx, block_clusters, block_follow, ctas_per_sm_follow, 0))
+    TUNING = ("block_clusters", "block_follow", "ctas_per_sm_zone", "ctas_per_sm_follow", "refill")
+
+    def set_tuning(self, block_clusters=0, block_follow=0, ctas_per_sm_zone=0, ctas_per_sm_follow=0, refill=0):
+        self._ck(self._lib.tpc_set_tuning(self._ctx, block_clusters, block_follow, ctas_per_sm_zone,
+                                          ctas_per_sm_follow, refill))
 
     TRACE_FIELDS = ("pass", "row", "nupd", "y", "z", "sphi", "tgl", "qpt", "Cyy", "Czz", "Css", "Ctt", "Cqq",
                     "chi2", "ry", "rz")
@@ -257,11 +260,10 @@ class Tracker:
                 entry = None
             if entry:
                 self.set_tuning(*entry["choice"])
-                return dict(zip(("block_clusters", "block_follow", "ctas_per_sm_follow"), entry["choice"])), \
-                    entry["ms"]
+                return dict(zip(self.TUNING, entry["choice"])), entry["ms"]
         if clusters is not None:
             self.load(clusters, req_offsets)
-        ch = np.zeros(3, np.int32)
+        ch = np.zeros(5, np.int32)
         ms = ctypes.c_float()
         self._ck(self._lib.tpc_autotune(self._ctx, reps, ch.ctypes.data, ctypes.byref(ms)))
         choice = [int(v) for v in ch]
@@ -275,7 +277,7 @@ class Tracker:
             data[key] = {"choice": choice, "ms": ms.value}
             with open(cache, "w") as f:
                 json.dump(data, f, indent=1)
-        return dict(zip(("block_clusters", "block_follow", "ctas_per_sm_follow"), choice)), ms.value
+        return dict(zip(self.TUNING, choice)), ms.value
 
     def set_profiling(self, on: bool = True):
         self._ck(self._lib.tpc_set_profiling(self._ctx, int(on)))

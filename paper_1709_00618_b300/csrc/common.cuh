@@ -50,10 +50,8 @@ struct Counts {
   int32_t n_tracks;
   uint32_t status;    // ST_* bits
   int32_t n_track_clusters;
-  int32_t follow_next; // work counter of the persistent follow launch
-  int32_t refit_next;
   int32_t n32;         // clusters as int32 (length source of the per-cluster scans)
-  int32_t pad[4];
+  int32_t work_next[6];  // work counters of the persistent Kalman kernels (PH_*)
   // work counters of the follow (a6) and refit (a8) kernels
   unsigned long long n_prop;    // helix propagations with covariance transport
   unsigned long long n_upd32;   // FP32 Kalman updates
@@ -102,6 +100,9 @@ struct KConst {
   int32_t trace_t;
   int32_t trace_cap;
   float* trace;  // trace_cap records of TRACE_W floats
+  // lanes of a warp of a refilling Kalman kernel that must be idle before
+  // the warp fetches new work for them together (1: refill at once)
+  int32_t refill;
 };
 
 // Trace record: pass (0 forward, 1 backward), row, updates since seed, then

@@ -10,6 +10,7 @@
 // tracklets, which start on neighbouring rows, so their FP64 zones overlap.
 #pragma once
 #include "kalman.cuh"
+#include "order.cuh"
 
 namespace tpc {
 
@@ -271,8 +272,26 @@ __device__ __forceinline__ bool work_load(const FollowWork* W, int64_t t, Lane& 
   return s.go != 0;
 }
 
-// Tracklet index for a lane of a refilling (persistent) phase kernel.
-__device__ __forceinline__ int64_t fetch_work(int32_t* counter) { return (int64_t)atomicAdd(counter, 1); }
+// Work distribution of the persistent Kalman kernels: the lanes in `need`,
+// all of which make this call, take consecutive indices of *counter with one
+// atomic for the warp.
+__device__ __forceinline__ int64_t warp_fetch(int32_t* counter, unsigned need) {
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(need) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(need));
+  base = __shfl_sync(need, base, leader);
+  return (int64_t)base + __popc(need & ((1u << lane) - 1u));
+}
+
+// Refill decision of a refilling kernel: the mask of lanes to refill now --
+// the idle lanes that can still get work, once at least kc.refill of them
+// are idle or no lane has work left.
+__device__ __forceinline__ unsigned refill_mask(bool idle, bool busy, int refill) {
+  const unsigned m = __ballot_sync(FULL_MASK, idle);
+  const unsigned b = __ballot_sync(FULL_MASK, busy);
+  return (m && (__popc(m) >= refill || b == 0)) ? m : 0u;
+}
 
 __device__ __forceinline__ void load_tables(float* sX, float* sYH) {
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) {
@@ -282,76 +301,89 @@ __device__ __forceinline__ void load_tables(float* sX, float* sYH) {
   __syncthreads();
 }
 
-// Phase 1: seed and the forward pass while its covariance is in FP64 (all
-// lanes of a warp start their zone together).
+// Phase 1: seed and the forward pass while its covariance is in FP64.  A
+// warp takes 32 consecutive tracklets at a time and starts their zones
+// together; the grid is the resident capacity (one wave).
 __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __restrict__ tl_start,
                                                    const int32_t* __restrict__ tl_len,
                                                    const int32_t* __restrict__ tl_end,
                                                    const int32_t* __restrict__ up_m, KConst kc, FollowOut o,
-                                                   FollowWork* W, Counts* cn) {
+                                                   FollowWork* W, WorkOrder next, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
-  if (gtid() == 0) cn->follow_next = 0;  // work counter of phase 2
   const int32_t T = cn->n_tracklets;
   LocalTally tl;
   double D[15];
   float C[15];
-  for (int64_t t = gtid(); t < T; t += gstride()) {
+  for (;;) {
+    const int64_t t = warp_fetch(&cn->work_next[PH_FOLLOW_P1], FULL_MASK);
+    if (__shfl_sync(FULL_MASK, t, 0) >= T) break;
+    const bool valid = t < T;
     Lane w;
-    w.hits = o.hits + t * NROW;
-    w.hrow = o.hrow + t * NROW;
-    w.flags = 0;
-    w.seed_fail = false;
-    w.tr = (t == kc.trace_t);
-    w.cn = cn;
-    const int c0 = tl_start[t], cl = tl_end[t];
-    w.L = tl_len[t];
-    const int rs0 = __ldg(g.rs_of + c0);
-    w.ubase = rs0 - rs0 % NROW;
-    w.r0 = rs0 % NROW;
-    const float2 P0 = __ldg(g.yz + c0), P1 = __ldg(g.yz + cl);
     TrkState p;
-    {
-      const float x0 = sX[w.r0], x1 = sX[w.r0 + w.L - 1];
-      const float dX = x1 - x0, dY = P1.x - P0.x, dZ = P1.y - P0.y;
-      const float Lc = sqrtf(dX * dX + dY * dY);
-      seed_state(p, w.r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);
-    }
-    w.k = c0;
-    w.i = 1;
-    w.misses = 0;
-    w.r_last = w.r0;
-    w.hits[0] = c0;
-    w.hrow[0] = (uint8_t)w.r0;
-    w.nf = 1;
-    w.nb = 0;
-    w.kf = 0;
     Chi2Acc chi2;
-    chi2.reset();
-    reseed_cov(kc, D, C);
-    w.nupd = 0;
-    const bool zone0 = kc.fp64_updates > 0;
-    lane_update<true>(w, kc, p, zone0, D, C, P0, chi2, 0);
-    if (zone0) tl.upd64++;
-    else tl.upd32++;
-    w.fwd = p;
-    bool go = true;
-    while (go && w.nupd < kc.fp64_updates) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
-    if (w.nupd < kc.fp64_updates) {
-#pragma unroll
-      for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+    bool go = false;
+    if (valid) {
+      w.hits = o.hits + t * NROW;
+      w.hrow = o.hrow + t * NROW;
+      w.flags = 0;
+      w.seed_fail = false;
+      w.tr = (t == kc.trace_t);
+      w.cn = cn;
+      const int c0 = tl_start[t], cl = tl_end[t];
+      w.L = tl_len[t];
+      const int rs0 = __ldg(g.rs_of + c0);
+      w.ubase = rs0 - rs0 % NROW;
+      w.r0 = rs0 % NROW;
+      const float2 P0 = __ldg(g.yz + c0), P1 = __ldg(g.yz + cl);
+      {
+        const float x0 = sX[w.r0], x1 = sX[w.r0 + w.L - 1];
+        const float dX = x1 - x0, dY = P1.x - P0.x, dZ = P1.y - P0.y;
+        const float Lc = sqrtf(dX * dX + dY * dY);
+        seed_state(p, w.r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);
+      }
+      w.k = c0;
+      w.i = 1;
+      w.misses = 0;
+      w.r_last = w.r0;
+      w.hits[0] = c0;
+      w.hrow[0] = (uint8_t)w.r0;
+      w.nf = 1;
+      w.nb = 0;
+      w.kf = 0;
+      chi2.reset();
+      reseed_cov(kc, D, C);
+      w.nupd = 0;
     }
-    work_store(W, t, w, p, C, chi2, go);
+    __syncwarp();  // the zones of the warp's lanes start together
+    if (valid) {
+      const bool zone0 = kc.fp64_updates > 0;
+      lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + tl_start[t]), chi2, 0);
+      if (zone0) tl.upd64++;
+      else tl.upd32++;
+      w.fwd = p;
+      go = true;
+      while (go && w.nupd < kc.fp64_updates) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+      if (w.nupd < kc.fp64_updates) {
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      }
+      work_store(W, t, w, p, C, chi2, go);
+    }
+    order_count(next, t, valid, go ? NROW - 1 - p.row : 0);  // rows left outward
   }
   tl.flush(cn, PH_FOLLOW_P1);
 }
 
-// Phase 2: the rest of the forward pass (covariance in FP32); a lane that
-// finishes a tracklet takes the next one, so no lane idles while the longest
-// tracklet of its warp is still running.
-__global__ void __launch_bounds__(128) k_follow_p2(GridView g, const int32_t* __restrict__ up_m, KConst kc,
-                                                   FollowOut o, FollowWork* W, Counts* cn) {
+// Phase 2: the rest of the forward pass (covariance in FP32).  A lane
+// that finishes a tracklet idles until kc.refill lanes of its warp have,
+// then they store their results and take new tracklets together, so that
+// the refill runs with many lanes at once and no lane waits for the longest
+// tracklet of its warp.
+__global__ void __launch_bounds__(128, 4) k_follow_p2(GridView g, const int32_t* __restrict__ up_m, KConst kc,
+                                                   FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
+                                                   Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
@@ -363,66 +395,89 @@ __global__ void __launch_bounds__(128) k_follow_p2(GridView g, const int32_t* __
   TrkState p;
   Chi2Acc chi2;
   chi2.reset();
-  int64_t t = fetch_work(&cn->follow_next);
-  bool go = false;
-  if (t < T) go = work_load(W, t, w, p, C, chi2);
-  while (t < T) {
-    if (go) go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
-    if (!go) {
-      work_store(W, t, w, p, C, chi2, false);
-      t = fetch_work(&cn->follow_next);
+  int64_t t = -1;      // tracklet held by the lane (-1: none yet)
+  bool go = false;     // the lane's tracklet has steps left
+  bool live = true;    // the lane may still get work
+  bool dirty = false;  // the held tracklet advanced since it was loaded
+  for (;;) {
+    const unsigned need = refill_mask(live && !go, go, kc.refill);
+    if (need & (1u << (threadIdx.x & 31))) {
+      if (dirty) work_store(W, t, w, p, C, chi2, false);
+      const int64_t idx = warp_fetch(&cn->work_next[PH_FOLLOW_P2], need);
+      t = idx < T ? order[idx] : T;
+      dirty = false;
       if (t < T) {
         work_load(W, t, w, p, C, chi2);
         w.hits = o.hits + t * NROW;
         w.hrow = o.hrow + t * NROW;
         w.cn = cn;
         go = !w.seed_fail && W[t].go;
+      } else {
+        live = false;
       }
+    }
+    if (!__any_sync(FULL_MASK, go)) {
+      if (!__any_sync(FULL_MASK, live)) break;
+      continue;
+    }
+    if (go) {
+      go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+      dirty = true;
     }
   }
   tl.flush(cn, PH_FOLLOW_P2);
 }
 
 // Phase 3: re-seed at the outermost forward cluster and run the backward
-// pass while its covariance is in FP64.
-__global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W, Counts* cn) {
+// pass while its covariance is in FP64 (warps take 32 tracklets at a time,
+// as phase 1).
+__global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W,
+                                                   WorkOrder next, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
-  if (gtid() == 0) cn->follow_next = 0;  // work counter of phase 4
   const int32_t T = cn->n_tracklets;
   LocalTally tl;
   double D[15];
   float C[15];
-  for (int64_t t = gtid(); t < T; t += gstride()) {
+  for (;;) {
+    const int64_t t = warp_fetch(&cn->work_next[PH_FOLLOW_P3], FULL_MASK);
+    if (__shfl_sync(FULL_MASK, t, 0) >= T) break;
+    const bool valid = t < T;
     Lane w;
     TrkState p;
     Chi2Acc chi2;
-    work_load(W, t, w, p, C, chi2);
-    w.hits = o.hits + t * NROW;
-    w.hrow = o.hrow + t * NROW;
-    w.cn = cn;
     bool go = false;
-    if (!w.seed_fail) {
-      p = w.fwd;
-      chi2.reset();
-      w.kf = w.nf - 2;
-      w.misses = 0;
-      reseed_cov(kc, D, C);
-      w.nupd = 0;
+    if (valid) {
+      work_load(W, t, w, p, C, chi2);
+      w.hits = o.hits + t * NROW;
+      w.hrow = o.hrow + t * NROW;
+      w.cn = cn;
+      if (!w.seed_fail) {
+        p = w.fwd;
+        chi2.reset();
+        w.kf = w.nf - 2;
+        w.misses = 0;
+        reseed_cov(kc, D, C);
+        w.nupd = 0;
+        go = true;
+      }
+    }
+    __syncwarp();  // the zones of the warp's lanes start together
+    if (go) {
       const bool zone0 = kc.fp64_updates > 0;
       lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
       if (zone0) tl.upd64++;
       else tl.upd32++;
       keep_output<true>(w, p, w.nupd < kc.fp64_updates, D, C, chi2);
-      go = true;
       while (go && w.nupd < kc.fp64_updates) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
       if (w.nupd < kc.fp64_updates) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
       }
     }
-    work_store(W, t, w, p, C, chi2, go);
+    if (valid) work_store(W, t, w, p, C, chi2, go);
+    order_count(next, t, valid, go ? p.row : 0);  // rows left inward
   }
   tl.flush(cn, PH_FOLLOW_P3);
 }
@@ -458,10 +513,11 @@ __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t 
   o.chi2[t] = w.schi2.value();
 }
 
-// Phase 4: the rest of the backward pass (FP32, lanes refill) and the
-// outputs.
-__global__ void __launch_bounds__(128) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
-                                                   FollowOut o, FollowWork* W, Counts* cn) {
+// Phase 4: the rest of the backward pass (FP32, lanes refill as in phase
+// 2) and the outputs.
+__global__ void __launch_bounds__(128, 4) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
+                                                   FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
+                                                   Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
@@ -473,26 +529,28 @@ __global__ void __launch_bounds__(128) k_follow_p4(GridView g, const int32_t* __
   TrkState p;
   Chi2Acc chi2;
   chi2.reset();
-  int64_t t = fetch_work(&cn->follow_next);
-  bool go = false;
-  if (t < T) {
-    go = work_load(W, t, w, p, C, chi2);
-    w.hits = o.hits + t * NROW;
-    w.hrow = o.hrow + t * NROW;
-    w.cn = cn;
-  }
-  while (t < T) {
-    if (go) go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
-    if (!go) {
-      write_follow_output(o, t, w, __ldg(g.yz + tl_start[t]).y);
-      t = fetch_work(&cn->follow_next);
+  int64_t t = -1;
+  bool go = false, live = true;
+  for (;;) {
+    const unsigned need = refill_mask(live && !go, go, kc.refill);
+    if (need & (1u << (threadIdx.x & 31))) {
+      if (t >= 0) write_follow_output(o, t, w, __ldg(g.yz + tl_start[t]).y);
+      const int64_t idx = warp_fetch(&cn->work_next[PH_FOLLOW_P4], need);
+      t = idx < T ? order[idx] : T;
       if (t < T) {
         go = work_load(W, t, w, p, C, chi2);
         w.hits = o.hits + t * NROW;
         w.hrow = o.hrow + t * NROW;
         w.cn = cn;
+      } else {
+        live = false;
       }
     }
+    if (!__any_sync(FULL_MASK, go)) {
+      if (!__any_sync(FULL_MASK, live)) break;
+      continue;
+    }
+    if (go) go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
   }
   tl.flush(cn, PH_FOLLOW_P4);
 }

@@ -7,6 +7,7 @@
 // the same expression sequence.
 #pragma once
 #include "common.cuh"
+#include "order.cuh"
 
 namespace tpc {
 
@@ -22,7 +23,9 @@ __device__ __forceinline__ int find_request(const int64_t* __restrict__ off, int
 }
 
 __global__ void k_rs_init(int32_t* __restrict__ cnt, uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax,
-                          const Counts* cn) {
+                          int32_t* __restrict__ obins, Counts* cn) {
+  if (gtid() < PH_COUNT) cn->work_next[gtid()] = 0;  // work counters of the Kalman kernels
+  for (int64_t i = gtid(); i < ORD_WORDS; i += gstride()) obins[i] = 0;  // their work-order histograms
   int32_t nrs = cn->n_rs;
   for (int64_t i = gtid(); i < nrs; i += gstride()) {
     cnt[i] = 0;

@@ -224,22 +224,23 @@ struct RefitIn {
 
 // Phase 1 of the refit: carry the follow state to the outermost owned row
 // (state only), then the updates with the covariance in FP64.
-__global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, Counts* cn) {
+__global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, WorkOrder next,
+                                                  Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
   __syncthreads();
   if (fatal(cn)) return;
-  if (gtid() == 0) cn->refit_next = 0;
   const int32_t M = cn->n_tracks;
   const int ZONE = kc.fp64_updates;
   LocalTally tl;
   double D[15];
   float C[15];
-  // warp-uniform loop: every lane runs the same iterations (lanes past the
-  // end idle) so that the warp can be reconverged before its FP64 zone
-  const int64_t stride = gstride();
-  for (int64_t base = gtid() - (threadIdx.x & 31); base < M; base += stride) {
-    const int64_t m = base + (threadIdx.x & 31);
+  // a warp takes 32 consecutive tracks at a time (lanes past the end idle),
+  // so that it can be reconverged before the FP64 zone
+  for (;;) {
+    const int64_t m = warp_fetch(&cn->work_next[PH_REFIT_P1], FULL_MASK);
+    const int64_t base = __shfl_sync(FULL_MASK, m, 0);
+    if (base >= M) break;
     const bool valid = m < M;
     const int t = valid ? in.track_tl[m] : in.track_tl[base];
     RefitLane w;
@@ -290,6 +291,7 @@ __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
       }
     }
+    order_count(next, m, valid, go && ok ? p.row - w.r_in : 0);  // rows left inward
     if (!valid) continue;
     RefitWork& s = RW[m];
     s.w = w;
@@ -351,7 +353,8 @@ __device__ __forceinline__ void write_track(const RefitIn& in, const float* sX, 
 
 // Phase 2 of the refit: the remaining updates in FP32; lanes refill.
 __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst kc, RefitWork* RW,
-                                                  tpc_track* __restrict__ out, Counts* cn) {
+                                                  const int32_t* __restrict__ order, tpc_track* __restrict__ out,
+                                                  Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
   __syncthreads();
@@ -364,9 +367,9 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
   TrkState p;
   Chi2Acc chi2;
   int nupd = 0;
-  bool ok = true, go = false;
+  bool ok = true, go = false, live = true;
   uint32_t flags = 0;
-  int64_t m = (int64_t)atomicAdd(&cn->refit_next, 1);
+  int64_t m = -1;
   auto load = [&](int64_t mm) {
     const RefitWork& s = RW[mm];
     w = s.w;
@@ -379,14 +382,22 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
     go = s.go != 0;
     flags = (uint32_t)s.flags;
   };
-  if (m < M) load(m);
-  while (m < M) {
-    if (go) go = refit_step<false>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
-    if (!go) {
-      write_track(in, sX, m, RW[m], p, C, chi2, ok, flags, out);
-      m = (int64_t)atomicAdd(&cn->refit_next, 1);
+  // lanes refill together once kc.refill of them are idle (as the follow
+  // phases 2 and 4)
+  for (;;) {
+    const unsigned need = refill_mask(live && !go, go, kc.refill);
+    if (need & (1u << (threadIdx.x & 31))) {
+      if (m >= 0) write_track(in, sX, m, RW[m], p, C, chi2, ok, flags, out);
+      const int64_t idx = warp_fetch(&cn->work_next[PH_REFIT_P2], need);
+      m = idx < M ? order[idx] : M;
       if (m < M) load(m);
+      else live = false;
     }
+    if (!__any_sync(FULL_MASK, go)) {
+      if (!__any_sync(FULL_MASK, live)) break;
+      continue;
+    }
+    if (go) go = refit_step<false>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
   }
   tl.flush(cn, PH_REFIT_P2);
 }

@@ -82,7 +82,7 @@ struct Layout {
       cend, owner, cluster_track, track_clusters;
   size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
   size_t bin_cnt, bin_start;
-  size_t own_mask, own_rng, fwork, rwork;
+  size_t own_mask, own_rng, fwork, rwork, okey, order, obins;
   size_t tl_start, tl_len, tl_end, f_n, f_nf, f_nb, f_flags, f_row, hits, hrow, f_par, f_zref, f_cov, f_chi2, keep,
       tidx, nown, tl_track, track_tl, tcount, toff, tracks;
   size_t parts;
@@ -153,6 +153,9 @@ Layout make_layout(const Caps& c) {
   L.own_mask = take(4 * OWN_WORDS * T);
   L.fwork = take(sizeof(FollowWork) * T);
   L.rwork = take(sizeof(RefitWork) * M);
+  L.okey = take(std::max(T, M));
+  L.order = take(4 * std::max(T, M));
+  L.obins = take(4 * ORD_WORDS);
   L.own_rng = take(4 * T);
   L.tl_track = take(4 * T);
   L.track_tl = take(4 * M);
@@ -190,7 +193,9 @@ struct tpc_ctx {
   // tuning
   int block_clusters = 256;
   int block_follow = 128;
-  int ctas_follow = 4;
+  int ctas_zone = 2;     // cap on CTAs per SM of the FP64-zone Kalman kernels
+  int ctas_follow = 3;   // cap on CTAs per SM of the refilling Kalman kernels (64: occupancy)
+  int refill = 4;        // idle lanes that trigger a warp's refill
   // graph
   cudaGraphExec_t graph = nullptr;
   int32_t trace_t = -1;  // traced tracklet
@@ -255,13 +260,24 @@ KConst make_kconst(const tpc_config& c, const Caps& caps) {
   return k;
 }
 
-// Blocks of a refilling follow phase: as many as are resident at once.
-int persistent_grid(tpc_ctx* ctx, int threads) {
+WorkOrder work_order(tpc_ctx* ctx, int phase) {
+  const Layout& L = ctx->L;
+  WorkOrder o;
+  o.hist = ctx->ptr<int32_t>(L.obins) + phase * 2 * ORD_BINS;
+  o.cursor = o.hist + ORD_BINS;
+  o.key = ctx->ptr<uint8_t>(L.okey);
+  o.order = ctx->ptr<int32_t>(L.order);
+  return o;
+}
+
+// Blocks of a persistent Kalman kernel: as many as are resident at once
+// (one wave), at most ctas_follow per SM.
+template <typename Kernel>
+int persistent_grid(tpc_ctx* ctx, Kernel kernel, int threads, int cap) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_follow_p2, threads, 0) != cudaSuccess ||
-      per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
     per_sm = 1;
-  return ctx->n_sm * per_sm;
+  return ctx->n_sm * std::max(1, std::min(per_sm, cap));
 }
 
 int grid_for(const tpc_ctx* ctx, int64_t items, int threads, int per_sm = 16) {
@@ -309,6 +325,7 @@ int do_reserve(tpc_ctx* ctx, const Caps& want) {
   ctx->caps = c;
   ctx->L = L;
   ctx->kc = make_kconst(ctx->cfg, c);
+  ctx->kc.refill = ctx->refill;
   ctx->kc.trace_t = ctx->trace_t;
   ctx->kc.trace_cap = TRACE_RECORDS;
   ctx->kc.trace = ctx->ptr<float>(L.trace);
@@ -420,7 +437,8 @@ void enqueue_find(tpc_ctx* ctx) {
   int32_t* bin_start = ctx->ptr<int32_t>(L.bin_start);
   ctx->mark(0);
   // a2 grid
-  k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax), cn);
+  k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax),
+                              ctx->ptr<int32_t>(L.obins), cn);
   k_grid_count<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int64_t>(L.req_off), cn,
                                  ctx->ptr<int32_t>(L.rs_in), rs_cnt, ctx->ptr<uint32_t>(L.zmin),
                                  ctx->ptr<uint32_t>(L.zmax));
@@ -456,20 +474,23 @@ void enqueue_find(tpc_ctx* ctx) {
                                        ctx->ptr<int32_t>(L.tl_end), cn, C.tl);
   ctx->mark(3);
   // a6 follow
-  int gF = grid_for(ctx, C.tl, ctx->block_follow, ctx->ctas_follow);
   {
     FollowWork* W = ctx->ptr<FollowWork>(L.fwork);
     const int bf = ctx->block_follow;
-    const int gP = persistent_grid(ctx, bf);
-    k_follow_p1<<<gF, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
+    k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, ctx->ctas_zone), bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
                                   ctx->ptr<int32_t>(L.tl_end), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx),
-                                  W, cn);
+                                  W, work_order(ctx, 0), cn);
+    k_order<<<grid_for(ctx, C.tl, bc), bc, 0, s>>>(work_order(ctx, 0), &cn->n_tracklets, cn);
     ctx->mark_k(0);
-    k_follow_p2<<<gP, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, cn);
+    k_follow_p2<<<persistent_grid(ctx, k_follow_p2, bf, ctx->ctas_follow), bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.up_m),
+                                                                      ctx->kc, follow_out(ctx), W,
+                                                                      ctx->ptr<int32_t>(L.order), cn);
     ctx->mark_k(1);
-    k_follow_p3<<<gF, bf, 0, s>>>(grid_view(ctx), ctx->kc, follow_out(ctx), W, cn);
+    k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, ctx->ctas_zone), bf, 0, s>>>(grid_view(ctx), ctx->kc, follow_out(ctx), W,
+                                                                      work_order(ctx, 1), cn);
+    k_order<<<grid_for(ctx, C.tl, bc), bc, 0, s>>>(work_order(ctx, 1), &cn->n_tracklets, cn);
     ctx->mark_k(2);
-    k_follow_p4<<<gP, bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, cn);
+    k_follow_p4<<<persistent_grid(ctx, k_follow_p4, bf, ctx->ctas_follow), bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, ctx->ptr<int32_t>(L.order), cn);
   }
   ctx->mark(4);
   // a7 selection
@@ -501,8 +522,8 @@ void enqueue_fit(tpc_ctx* ctx) {
                                    ctx->ptr<int32_t>(L.tcount), cn);
   scan(ctx, ctx->ptr<int32_t>(L.tcount), ctx->ptr<int32_t>(L.toff), LenSrc{&cn->n_tracks, 0, 0},
        &cn->n_track_clusters);
-  int gF = grid_for(ctx, C.tracks, ctx->block_follow, ctx->ctas_follow);
   {
+    const int bf = ctx->block_follow;
     RefitIn in;
     in.track_tl = ctx->ptr<int32_t>(L.track_tl);
     in.f_n = ctx->ptr<int32_t>(L.f_n);
@@ -520,10 +541,13 @@ void enqueue_fit(tpc_ctx* ctx) {
     in.toff = ctx->ptr<int32_t>(L.toff);
     RefitWork* RW = ctx->ptr<RefitWork>(L.rwork);
     ctx->mark_k(3);
-    k_refit_p1<<<gF, ctx->block_follow, 0, s>>>(grid_view(ctx), in, ctx->kc, RW, cn);
+    k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, ctx->ctas_zone), bf, 0, s>>>(grid_view(ctx), in, ctx->kc, RW,
+                                                                    work_order(ctx, 2), cn);
+    k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, s>>>(work_order(ctx, 2), &cn->n_tracks, cn);
     ctx->mark_k(4);
-    k_refit_p2<<<persistent_grid(ctx, ctx->block_follow), ctx->block_follow, 0, s>>>(
-        grid_view(ctx), in, ctx->kc, RW, ctx->ptr<tpc_track>(L.tracks), cn);
+    k_refit_p2<<<persistent_grid(ctx, k_refit_p2, bf, ctx->ctas_follow), bf, 0, s>>>(grid_view(ctx), in, ctx->kc, RW,
+                                                                    ctx->ptr<int32_t>(L.order),
+                                                                    ctx->ptr<tpc_track>(L.tracks), cn);
     ctx->mark_k(5);
   }
   k_track_clusters<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
@@ -880,7 +904,7 @@ int tpc_get_stage(tpc_ctx* ctx, int item, void* host_out, int64_t cap_bytes, int
   return TPC_OK;
 }
 
-int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[3], float* best_ms) {
+int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[5], float* best_ms) {
   if (!ctx || reps < 1 || reps > 100) return TPC_EINVAL;
   if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "load a representative batch before tpc_autotune");
   CK(cudaSetDevice(ctx->device));
@@ -906,21 +930,25 @@ int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[3], float* best_ms) 
     ms = t[t.size() / 2];
     return check_status(ctx);
   };
-  static const int kBlockClusters[] = {128, 256, 512};
-  static const int kBlockFollow[] = {64, 96, 128};
-  static const int kCtas[] = {2, 4, 8};
-  int best[3] = {ctx->block_clusters, ctx->block_follow, ctx->ctas_follow};
+  auto apply = [&](const int* v) {
+    ctx->block_clusters = v[0];
+    ctx->block_follow = v[1];
+    ctx->ctas_zone = v[2];
+    ctx->ctas_follow = v[3];
+    ctx->refill = v[4];
+    ctx->kc.refill = v[4];
+  };
+  static const int kCand[5][4] = {{128, 256, 512, 0}, {64, 96, 128, 0}, {1, 2, 3, 0}, {2, 3, 64, 0}, {1, 4, 8, 16}};
+  static const int kNCand[5] = {3, 3, 3, 3, 4};
+  int best[5] = {ctx->block_clusters, ctx->block_follow, ctx->ctas_zone, ctx->ctas_follow, ctx->refill};
   float best_t = 0.0f;
   int rc = measure(best_t);
-  for (int dim = 0; dim < 3 && rc == TPC_OK; dim++) {  // coordinate descent
-    const int* cand = dim == 0 ? kBlockClusters : dim == 1 ? kBlockFollow : kCtas;
-    for (int k = 0; k < 3 && rc == TPC_OK; k++) {
-      int trial[3] = {best[0], best[1], best[2]};
-      trial[dim] = cand[k];
+  for (int dim = 0; dim < 5 && rc == TPC_OK; dim++) {  // coordinate descent
+    for (int k = 0; k < kNCand[dim] && rc == TPC_OK; k++) {
+      int trial[5] = {best[0], best[1], best[2], best[3], best[4]};
+      trial[dim] = kCand[dim][k];
       if (trial[dim] == best[dim]) continue;
-      ctx->block_clusters = trial[0];
-      ctx->block_follow = trial[1];
-      ctx->ctas_follow = trial[2];
+      apply(trial);
       float t = 0.0f;
       rc = measure(t);
       if (rc == TPC_OK && t < best_t) {
@@ -929,9 +957,7 @@ int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[3], float* best_ms) 
       }
     }
   }
-  ctx->block_clusters = best[0];
-  ctx->block_follow = best[1];
-  ctx->ctas_follow = best[2];
+  apply(best);
   ctx->prof = prof;
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
@@ -939,11 +965,8 @@ int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[3], float* best_ms) 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (choice) {
-    choice[0] = best[0];
-    choice[1] = best[1];
-    choice[2] = best[2];
-  }
+  if (choice)
+    for (int i = 0; i < 5; i++) choice[i] = best[i];
   if (best_ms) *best_ms = best_t;
   return rc;
 }
@@ -1036,9 +1059,11 @@ int tpc_get_work(tpc_ctx* ctx, uint64_t work[5]) {
   return TPC_OK;
 }
 
-int tpc_set_tuning(tpc_ctx* ctx, int block_clusters, int block_follow, int ctas_per_sm_follow, int reserved) {
-  (void)reserved;
+int tpc_set_tuning(tpc_ctx* ctx, int block_clusters, int block_follow, int ctas_per_sm_zone, int ctas_per_sm_follow,
+                   int refill) {
   if (!ctx) return TPC_EINVAL;
+  if (ctas_per_sm_zone < 0 || ctas_per_sm_zone > 64) return fail(ctx, TPC_EINVAL, "ctas_per_sm out of range");
+  if (refill < 0 || refill > 32) return fail(ctx, TPC_EINVAL, "refill must be in [1, 32]");
   if (block_clusters && (block_clusters < 32 || block_clusters > 1024 || block_clusters % 32))
     return fail(ctx, TPC_EINVAL, "block_clusters must be a multiple of 32 in [32, 1024]");
   if (block_follow && (block_follow < 32 || block_follow > 128 || block_follow % 32))
@@ -1046,7 +1071,9 @@ int tpc_set_tuning(tpc_ctx* ctx, int block_clusters, int block_follow, int ctas_
   if (ctas_per_sm_follow < 0 || ctas_per_sm_follow > 64) return fail(ctx, TPC_EINVAL, "ctas_per_sm out of range");
   if (block_clusters) ctx->block_clusters = block_clusters;
   if (block_follow) ctx->block_follow = block_follow;
+  if (ctas_per_sm_zone) ctx->ctas_zone = ctas_per_sm_zone;
   if (ctas_per_sm_follow) ctx->ctas_follow = ctas_per_sm_follow;
+  if (refill) ctx->refill = ctx->kc.refill = refill;
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;

@@ -127,11 +127,13 @@ def test_autotuned_shapes_give_the_same_result():
         choice, ms = t.autotune(cl, reps=1)
         assert choice["block_clusters"] in (128, 256, 512)
         assert choice["block_follow"] in (64, 96, 128)
-        assert choice["ctas_per_sm_follow"] in (2, 4, 8)
+        assert choice["ctas_per_sm_zone"] in (1, 2, 3)
+        assert choice["ctas_per_sm_follow"] in (2, 3, 64)
+        assert choice["refill"] in (1, 4, 8, 16)
         assert ms > 0
         tracks, ct, _ = t.track(cl)
         g_tracks, g_ct, _ = t.track(cl, graph=True)
-        for shape in ((512, 64, 2), (128, 128, 8)):
+        for shape in ((512, 64, 3, 2, 1), (128, 128, 1, 8, 32), (256, 96, 2, 1, 5)):
             t.set_tuning(*shape)
             s_tracks, s_ct, _ = t.track(cl)
             assert s_tracks.tobytes() == ref_tracks.tobytes() and np.array_equal(s_ct, ref_ct)
