@@ -96,13 +96,15 @@ class ClockSampler:
 # FP32-zone work is all binary32; in the FP64 zone the transport and the
 # covariance part of the update run in binary64.
 FLOP_STATE, FLOP_TRANSPORT, FLOP_UPD_COV, FLOP_UPD_STATE, FLOP_CAND = 76, 102, 99, 56, 10
-# Algorithmic DRAM bytes per cluster of the memory-bound stages: grid 88
-# (16 B read twice, 4 B rs, 8 B bin/slot written and read, scatter 4 B,
-# order 16 B gather + 16 B writes), neighbours 33 (8 B own y/z, 8 B candidate
-# re-reads, 8 B links + 1 B tie written, ~8 B bin starts).
-BYTES_GRID, BYTES_NEIGH = 88, 33
-# Issue rates per SM and clock: 128 FP32 lanes (an FMA is 2 flop) and, on
-# B300, 2 FP64 FMA units.
+# Algorithmic DRAM bytes per cluster of the memory-bound stages: grid 44
+# (the 16 B record read, 16 B of sorted output -- y/z, row-sector, input
+# index -- written, a 4 B bin index written and half of the records read
+# again), neighbours 45 (own y/z 8 B and row-sector 4 B, the two
+# neighbouring rows' y/z read once each 16 B, about two bin starts 8 B, up,
+# down and tie written 9 B).
+BYTES_GRID, BYTES_NEIGH = 44, 45
+# Nominal issue rates per SM and clock: 128 FP32 lanes (an FMA is 2 flop)
+# and, on B300, 2 FP64 FMA units; the roofline uses the measured probe.
 FP32_FLOP_PER_CLK_SM, FP64_FLOP_PER_CLK_SM, N_SM = 256, 4, 148
 
 
@@ -115,14 +117,12 @@ def kalman_flops(w):
     return f32, f64
 
 
-def kernel_rooflines(stages, kalman, n):
+def kernel_rooflines(stages, kalman, n, alu):
     """Roofline entry per timed kernel (Kalman kernels one by one, the
     neighbour kernel, the grid stage as a whole); the largest is the
-    dominant kernel."""
+    dominant kernel.  alu: the measured FMA-pipe rates (TFLOP/s)."""
     peaks, src = _peaks()
-    mhz = peaks.get("sm_max_mhz", 2032.0)
-    p32 = N_SM * FP32_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
-    p64 = N_SM * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12
+    p32, p64 = alu["fp32_tflops"], alu["fp64_tflops"]
     out = {}
     for name, d in kalman.items():
         t = d["ms"] / 1e3
@@ -146,19 +146,25 @@ def kernel_rooflines(stages, kalman, n):
     return out, src
 
 
-def roofline(stages, kalman, n, traffic=None):
-    table, src = kernel_rooflines(stages, kalman, n)
+def roofline(stages, kalman, n, alu, clocks, traffic=None):
+    table, src = kernel_rooflines(stages, kalman, n, alu)
     dom = max((k for k in table if k != "grid stage"), key=lambda k: table[k]["ms"])
     e = dict(table[dom])
+    mhz = clocks.get("sm_mhz") or 2032.0
     line = {"kernel": dom, "bound": e["bound"], "achieved": e["achieved"], "peak": e["peak"], "unit": e["unit"],
             "frac": e["frac"], "traffic": (traffic or {}).get(dom), "ms": e["ms"],
-            "peak_source": f"{src}: FP32 {N_SM} SM x {FP32_FLOP_PER_CLK_SM} flop/clk, FP64 {N_SM} SM x "
-                           f"{FP64_FLOP_PER_CLK_SM} flop/clk at the measured maximum SM clock; HBM measured copy"}
+            "peak_source": f"ALU: measured FMA-pipe probe (tpc_measure_alu_peaks: FP32 {alu['fp32_tflops']:.1f}, "
+                           f"FP64 {alu['fp64_tflops']:.2f} TFLOP/s; nominal at the sampled {mhz:.0f} MHz: FP32 "
+                           f"{N_SM * FP32_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12:.1f}, FP64 "
+                           f"{N_SM * FP64_FLOP_PER_CLK_SM * mhz * 1e6 / 1e12:.2f}); HBM: {src} copy bandwidth"}
     return line, table
 
 
 def cpu_baseline(cl):
-    """The FP64 oracle timed on this host's cores over the same event."""
+    """The FP64 oracle timed on this host's cores over the same event, and
+    on one core over six of its sectors."""
+    import numpy as np
+
     import oracle
     threads = os.cpu_count() or 1
     oracle.run(cl[:1000], threads=threads)
@@ -168,8 +174,14 @@ def cpu_baseline(cl):
         t0 = time.perf_counter()
         oracle.run(cl, threads=threads)
         times.append(time.perf_counter() - t0)
+    sub = cl[np.isin(cl["sector"], (0, 1, 2, 18, 19, 20))]
+    t0 = time.perf_counter()
+    oracle.run(sub, threads=1)
+    one = len(sub) / (time.perf_counter() - t0)
     return {"value": len(cl) * len(times) / sum(times), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"the full event ({len(cl)} clusters) x {len(times)} runs, all stages a2-a8"}
+            "sample": f"the full event ({len(cl)} clusters) x {len(times)} runs, all stages a2-a8",
+            "one_core": {"value": one, "sample": f"sectors 0-2 and 18-20 of the event ({len(sub)} clusters), "
+                                                 "1 thread"}}
 
 
 def run_reference(args):
@@ -286,16 +298,17 @@ def batching_leg(local, flush, n_requests=256, reps=3):
     return out
 
 
-def serving_leg(local, n_timeframes=24, pool=4, load=0.85, slots=4, budget_gb=120.0, ring=6, seed=4):
+def serving_leg(local, n_timeframes=24, pool=4, loads=(0.5, 0.8, 1.0), headline=0.8, slots=4,
+                budget_gb=120.0, ring=6, seed=4):
     """Poisson stream of continuous-readout timeframes (lengths uniform in
     1-20 ms at 50 kHz) through the continuous-batching server, against
-    sequential plain processing of the same stream.  Timeframes are drawn
-    from a pool of distinct seeded timeframes; inputs and result buffers are
-    page-locked host memory in both arms (`ring` result buffers for the
-    server: a request waits for a free one).  The arrival rate puts the
-    offered load at `load` times the sequential plain capacity (measured
-    first).  Latency: arrival to results (tracks and cluster assignment) in
-    host memory."""
+    sequential plain processing of the same stream, at several offered
+    loads (arrival rate = load x the sequential plain capacity, measured
+    first).  Timeframes are drawn from a pool of distinct seeded timeframes;
+    inputs and result buffers are page-locked host memory in both arms
+    (`ring` result buffers for the server: a request waits for a free one).
+    Latency: arrival to results (tracks and cluster assignment) in host
+    memory."""
     import numpy as np
     import torch
 
@@ -307,88 +320,95 @@ def serving_leg(local, n_timeframes=24, pool=4, load=0.85, slots=4, budget_gb=12
     sizes = [len(h) for h in host]
     rng = np.random.default_rng(seed + 1)
     order = rng.integers(0, pool, size=n_timeframes)
+    gaps = rng.exponential(1.0, size=n_timeframes)  # unit-rate gaps, scaled per load
 
     # sequential plain service time of each pool entry (after one warm run)
     trk = tpc.Tracker(device=local)
     trk.reserve(n_clusters=max(sizes), n_requests=1)
-    n_tracks = []
-    serv = []
-    big_tr = torch.zeros(max(sizes) // 10 + 1, 128, dtype=torch.uint8).pin_memory()
+    n_tracks, serv = [], []
     big_ct = torch.zeros(max(sizes), dtype=torch.int32).pin_memory()
+    tr_buf = torch.zeros(max(sizes) // 10 + 1, 128, dtype=torch.uint8).pin_memory()
     for h in host:
         trk.load(h).find().fit()
-        tr, _ = trk.get_into(big_tr, big_ct[:len(h)])
+        tr, _ = trk.get_into(tr_buf, big_ct[:len(h)])
         n_tracks.append(len(tr))
         t0 = time.perf_counter()
         trk.load(h).find().fit()
-        trk.get_into(big_tr, big_ct[:len(h)])
+        trk.get_into(tr_buf, big_ct[:len(h)])
         serv.append(time.perf_counter() - t0)
-    del big_tr
-    cap = int(1.25 * max(n_tracks)) + 1024
     mean_s = float(np.mean([serv[i] for i in order]))
-    lam = load / mean_s
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n_timeframes))
-    arrivals -= arrivals[0]
-
-    # plain: one request at a time in arrival order
-    out_tr = torch.zeros(cap, 128, dtype=torch.uint8).pin_memory()
-    lat_p = []
-    t_start = time.perf_counter()
-    for k in range(n_timeframes):
-        now = time.perf_counter() - t_start
-        if now < arrivals[k]:
-            time.sleep(arrivals[k] - now)
-        h = host[order[k]]
-        trk.load(h).find().fit()
-        trk.get_into(out_tr, big_ct[:len(h)])
-        lat_p.append(time.perf_counter() - t_start - arrivals[k])
-    span_p = time.perf_counter() - t_start
-    trk.close()
-    del big_ct, out_tr
     total = int(sum(sizes[i] for i in order))
-
-    # served: submissions at the same arrival times into a ring of result
-    # buffers; results collected as they finish
+    cap = int(1.25 * max(n_tracks)) + 1024
     bufs = [(torch.zeros(cap, 128, dtype=torch.uint8).pin_memory(),
              torch.zeros(max(sizes), dtype=torch.int32).pin_memory()) for _ in range(ring)]
-    free = list(range(ring))
-    srv = tpc.Server(device=local, max_slots=slots, hbm_budget=int(budget_gb * 2**30))
-    lat_s, late, owner, pending = [], {}, {}, set()
-    t_start = time.perf_counter()
-    k = 0
-    while k < n_timeframes or pending:
-        now = time.perf_counter() - t_start
-        while k < n_timeframes and arrivals[k] <= now and free:
-            b = free.pop()
+
+    def plain_arm(arrivals):
+        lat = []
+        t_start = time.perf_counter()
+        for k in range(n_timeframes):
+            now = time.perf_counter() - t_start
+            if now < arrivals[k]:
+                time.sleep(arrivals[k] - now)
             h = host[order[k]]
-            if srv.submit(k, pinned[order[k]], tracks_out=bufs[b][0], cluster_track_out=bufs[b][1][:len(h)]) != 0:
-                free.append(b)
-                break
-            late[k] = time.perf_counter() - t_start - arrivals[k]
-            owner[k] = b
-            pending.add(k)
-            k += 1
-        for j in sorted(pending):
-            r = srv.result(j)
-            if r is not None:
-                lat_s.append(late[j] + r[2][2] / 1e3)
-                pending.discard(j)
-                free.append(owner.pop(j))
-        time.sleep(0.0002)
-    span_s = time.perf_counter() - t_start
-    st = srv.stats()
-    srv.close()
-    return {"workload": f"Poisson stream of {n_timeframes} timeframes drawn from {pool} distinct seeded "
-                        f"timeframes of 1-20 ms at 50 kHz (seed {seed}); offered load {load} of the sequential "
-                        f"plain capacity; {slots} slots, {budget_gb:g} GB HBM budget; page-locked inputs and "
-                        f"outputs in both arms",
-            "timeframe_clusters": sizes, "timeframe_ms": [round(t.params.tf_length_us / 1e3, 3) for t in tfs],
-            "timeframe_tracks": n_tracks, "clusters": total, "arrival_rate_hz": lam,
+            trk.load(h).find().fit()
+            trk.get_into(tr_buf, big_ct[:len(h)])
+            lat.append(time.perf_counter() - t_start - arrivals[k])
+        return lat, time.perf_counter() - t_start
+
+    def served_arm(arrivals):
+        # latency = (submission - arrival) + the server's submission-to-results time
+        free = list(range(ring))
+        srv = tpc.Server(device=local, max_slots=slots, hbm_budget=int(budget_gb * 2**30))
+        lat, late, owner, pending = [], {}, {}, set()
+        t_start = time.perf_counter()
+        k = 0
+        while k < n_timeframes or pending:
+            now = time.perf_counter() - t_start
+            while k < n_timeframes and arrivals[k] <= now and free:
+                b = free.pop()
+                h = host[order[k]]
+                if srv.submit(k, pinned[order[k]], tracks_out=bufs[b][0], cluster_track_out=bufs[b][1][:len(h)]):
+                    free.append(b)
+                    break
+                late[k] = time.perf_counter() - t_start - arrivals[k]
+                owner[k] = b
+                pending.add(k)
+                k += 1
+            for j in sorted(pending):
+                r = srv.result(j)
+                if r is not None:
+                    lat.append(late[j] + r[2][2] / 1e3)
+                    pending.discard(j)
+                    free.append(owner.pop(j))
+            time.sleep(0.0002)
+        span = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        return lat, span, st
+
+    by_load = {}
+    for load in loads:
+        arrivals = np.cumsum(gaps) * (mean_s / load)
+        arrivals -= arrivals[0]
+        lat_p, span_p = plain_arm(arrivals)
+        lat_s, span_s, st = served_arm(arrivals)
+        by_load[str(load)] = {
+            "arrival_rate_hz": load / mean_s,
             "plain": {"latency_ms_p50": 1e3 * _pct(lat_p, 50), "latency_ms_p99": 1e3 * _pct(lat_p, 99),
-                      "clusters_per_s": total / span_p, "service_ms": [round(1e3 * v, 2) for v in serv]},
+                      "clusters_per_s": total / span_p},
             "served": {"latency_ms_p50": 1e3 * _pct(lat_s, 50), "latency_ms_p99": 1e3 * _pct(lat_s, 99),
                        "clusters_per_s": total / span_s, "peak_running": st["peak_running"],
                        "arena_gb": st["arena_bytes"] / 2**30}}
+    trk.close()
+    head = by_load[str(headline)]
+    return {"workload": f"Poisson stream of {n_timeframes} timeframes drawn from {pool} distinct seeded "
+                        f"timeframes of 1-20 ms at 50 kHz (seed {seed}); offered loads {list(loads)} of the "
+                        f"sequential plain capacity (headline {headline}); {slots} slots, {budget_gb:g} GB HBM "
+                        f"budget; page-locked inputs and outputs in both arms",
+            "timeframe_clusters": sizes, "timeframe_ms": [round(t.params.tf_length_us / 1e3, 3) for t in tfs],
+            "timeframe_tracks": n_tracks, "service_ms_plain": [round(1e3 * v, 2) for v in serv],
+            "clusters": total, "headline_load": headline, "plain": head["plain"], "served": head["served"],
+            "by_load": by_load}
 
 
 def main():
@@ -484,7 +504,7 @@ def main():
         d["ms"] = statistics.median(r[name]["ms"] for r in kruns)
         kalman[name] = d
     work = trk.work()
-    roof, kernel_table = roofline(stages, kalman, n)
+    alu = tpc.measure_alu_peaks(local)
 
     # end to end through the public API: pinned host input -> tracks + assignment on the host
     pinned = torch.from_numpy(cl.view(np.uint8)).pin_memory()
@@ -500,15 +520,19 @@ def main():
     e2e_t = sum(e2e) / len(e2e)
     trk.close()
 
+    clocks = clk.summary()
+    roof, kernel_table = roofline(stages, kalman, n, alu, clocks)
     peaks, src = _peaks()
     line = {"metric": METRIC, "value": world * n / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1",
                        "clusters": n, "tracklets": counts["n_tracklets"], "tracks": counts["n_tracks"],
+                       "tracklets_per_track": counts["n_tracklets"] / max(counts["n_tracks"], 1),
                        "l2": "flushed (256 MB write) between steps", "graph": True,
                        "kernels_per_step": kernels_per_step},
-            "clocks": clk.summary(),
+            "clocks": clocks,
+            "alu_peaks_measured": alu,
             "e2e": {"value": world * n / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 128 * len(tr) + 4 * n},
             "gpu_launches": kernels_per_step * args.steps,

@@ -234,6 +234,13 @@ int tpc_get_work(tpc_ctx *ctx, uint64_t work[5]);
  * the stream. */
 int tpc_get_kalman_profile(tpc_ctx *ctx, float ms[6], uint64_t work[30]);
 
+/* Measured issue rates of the FP32 and FP64 fused multiply-add pipes of
+ * device `device` (TFLOP/s, an FMA counting 2): 8 independent FMA chains
+ * per thread over 8 blocks of 256 threads per SM, best of two timed runs
+ * after a warm-up.  Either pointer may be NULL.  The denominators of the
+ * Kalman kernels' ALU rooflines. */
+int tpc_measure_alu_peaks(int device, double *fp32_tflops, double *fp64_tflops);
+
 /* Number of kernel launches in one tpc_run_graph (kernel nodes of the
  * captured graph); TPC_EINVAL before the first capture. */
 int tpc_graph_kernels(tpc_ctx *ctx, int32_t *n);
@@ -272,27 +279,38 @@ int tpc_row_params_noalloc(const tpc_cluster *d_clusters, int64_t n, const int64
                            void *d_params_out, void *cuda_stream);
 
 /* ------------------------------------------------------ tuning (autotuner) */
-/* Launch shapes (0 keeps the current value): threads per block of the
- * cluster-, row-sector- and tracklet-parallel kernels (multiple of 32, at
- * most 1024) and of the Kalman kernels (32..128); the most CTAs per SM of
- * the persistent Kalman kernels -- those running the FP64 zones and those
- * that refill lanes -- whose grids are one wave of resident CTAs (64: as
- * many as fit); refill: idle lanes of a warp of a refilling Kalman kernel
- * that trigger the warp's common fetch of new tracklets (1..32; 1: each
- * lane refills at once).  Results do not depend on them.  Invalidates a
- * captured graph. */
-int tpc_set_tuning(tpc_ctx *ctx, int block_clusters, int block_follow, int ctas_per_sm_zone, int ctas_per_sm_follow,
-                   int refill);
+/* Launch shapes of a context.  Results do not depend on them. */
+typedef struct {
+  int32_t block_clusters;     /* threads per block of the cluster-, row-sector- and tracklet-parallel kernels
+                                 (multiple of 32, at most 1024) */
+  int32_t block_follow;       /* threads per block of the Kalman kernels (multiple of 32, at most 128) */
+  int32_t ctas_per_sm_zone;   /* most CTAs per SM of the Kalman kernels running FP64 zones; their grids are
+                                 one wave of resident CTAs (64: as many as fit) */
+  int32_t ctas_per_sm_follow; /* the same for the Kalman kernels that refill lanes (FP32 phases); reported
+                                 as 0 while the default applies: 64 from 4 Mi loaded clusters on, else 2 */
+  int32_t refill;             /* idle lanes of a warp of a refilling kernel that trigger the warp's common
+                                 fetch of new work (1..32; 1: each lane refills at once) */
+  int32_t chunks;             /* 1, or 2: the Kalman stage splits its items in two halves whose kernels run
+                                 on two streams, one kernel apart, so that one half's FP64 zone shares the
+                                 SMs with the other half's FP32 phase (profiled runs use 1); reported as 0
+                                 while the default (1) applies */
+} tpc_tuning;
+
+int tpc_get_tuning(tpc_ctx *ctx, tpc_tuning *t);
+
+/* Fields <= 0 keep their current value.  TPC_EINVAL for out-of-range
+ * values.  Invalidates a captured graph. */
+int tpc_set_tuning(tpc_ctx *ctx, const tpc_tuning *t);
 
 /* Autotuner: with a representative batch loaded, times tpc_find_tracks +
  * tpc_fit_tracks (median of reps runs, CUDA events on the context's stream)
  * over block_clusters {128, 256, 512}, block_follow {64, 96, 128},
- * ctas_per_sm_zone {1, 2, 3}, ctas_per_sm_follow {2, 3, 64} and refill
- * {1, 4, 8, 16} by coordinate descent from the current shapes, keeps the
- * fastest and reports it in choice[5] (the order of tpc_set_tuning) and
- * *best_ms.  The results of the loaded batch are overwritten (rerun
+ * ctas_per_sm_zone {1, 2, 3}, ctas_per_sm_follow {2, 3, 64}, refill
+ * {1, 4, 8, 16} and chunks {1, 2} by coordinate descent from the current
+ * shapes, keeps the fastest and reports it in *best and *best_ms (either
+ * may be NULL).  The results of the loaded batch are overwritten (rerun
  * tpc_find_tracks before get). */
-int tpc_autotune(tpc_ctx *ctx, int32_t reps, int32_t choice[5], float *best_ms);
+int tpc_autotune(tpc_ctx *ctx, int32_t reps, tpc_tuning *best, float *best_ms);
 
 /* ------------------------------------------------------ serving (requests) */
 /* Continuous-batching request loop: the serving form of tracking several

@@ -47,6 +47,15 @@ class TpcError(RuntimeError):
         self.code = code
 
 
+class TpcTuning(ctypes.Structure):
+    _fields_ = [("block_clusters", ctypes.c_int32), ("block_follow", ctypes.c_int32),
+                ("ctas_per_sm_zone", ctypes.c_int32), ("ctas_per_sm_follow", ctypes.c_int32),
+                ("refill", ctypes.c_int32), ("chunks", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class TpcConfig(ctypes.Structure):
     _fields_ = [("bz_kg", ctypes.c_double), ("sigma", ctypes.c_double), ("d_max", ctypes.c_float),
                 ("min_chain", ctypes.c_int32), ("max_miss", ctypes.c_int32), ("n_min_track", ctypes.c_int32),
@@ -85,12 +94,14 @@ def load_library(path: str | None = None):
         "tpc_sync": ([_VP], ctypes.c_int),
         "tpc_get_counts": ([_VP, _VP], ctypes.c_int),
         "tpc_get_stage": ([_VP, ctypes.c_int, _VP, _I64, _VP], ctypes.c_int),
-        "tpc_set_tuning": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "tpc_set_tuning": ([_VP, _VP], ctypes.c_int),
+        "tpc_get_tuning": ([_VP, _VP], ctypes.c_int),
         "tpc_set_profiling": ([_VP, ctypes.c_int], ctypes.c_int),
         "tpc_get_stage_times": ([_VP, _VP], ctypes.c_int),
         "tpc_get_work": ([_VP, _VP], ctypes.c_int),
         "tpc_get_kalman_profile": ([_VP, _VP, _VP], ctypes.c_int),
         "tpc_graph_kernels": ([_VP, _VP], ctypes.c_int),
+        "tpc_measure_alu_peaks": ([ctypes.c_int, _VP, _VP], ctypes.c_int),
         "tpc_row_params_noalloc": ([_VP, _I64, _VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_autotune": ([_VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_set_trace": ([_VP, _I32], ctypes.c_int),
@@ -229,11 +240,19 @@ class Tracker:
     def reserve(self, n_clusters=0, n_requests=0, n_bins=0, n_tracklets=0):
         self._ck(self._lib.tpc_reserve(self._ctx, n_clusters, n_requests, n_bins, n_tracklets))
 
-    TUNING = ("block_clusters", "block_follow", "ctas_per_sm_zone", "ctas_per_sm_follow", "refill")
+    def set_tuning(self, **fields):
+        """Launch shapes (tpc_tuning fields; omitted ones keep their value)."""
+        t = TpcTuning()
+        for k, v in fields.items():
+            if not hasattr(t, k):
+                raise TypeError(f"unknown tuning field {k}")
+            setattr(t, k, int(v))
+        self._ck(self._lib.tpc_set_tuning(self._ctx, ctypes.byref(t)))
 
-    def set_tuning(self, block_clusters=0, block_follow=0, ctas_per_sm_zone=0, ctas_per_sm_follow=0, refill=0):
-        self._ck(self._lib.tpc_set_tuning(self._ctx, block_clusters, block_follow, ctas_per_sm_zone,
-                                          ctas_per_sm_follow, refill))
+    def tuning(self) -> dict:
+        t = TpcTuning()
+        self._ck(self._lib.tpc_get_tuning(self._ctx, ctypes.byref(t)))
+        return t.as_dict()
 
     TRACE_FIELDS = ("pass", "row", "nupd", "y", "z", "sphi", "tgl", "qpt", "Cyy", "Czz", "Css", "Ctt", "Cqq",
                     "chi2", "ry", "rz")
@@ -249,9 +268,9 @@ class Tracker:
         return out[:min(n.value, 2048)]
 
     def autotune(self, clusters=None, req_offsets=None, reps: int = 3, cache: str | None = None, key: str = ""):
-        """Choose block/CTA shapes for the loaded (or given) batch with the
+        """Choose launch shapes for the loaded (or given) batch with the
         library's autotuner; with `cache`, reuse or store the choice under
-        `key` in that JSON file.  Returns (choice dict, best ms)."""
+        `key` in that JSON file.  Returns (tuning dict, best ms)."""
         import json
         if cache and os.path.exists(cache):
             try:
@@ -259,14 +278,14 @@ class Tracker:
             except (OSError, ValueError):
                 entry = None
             if entry:
-                self.set_tuning(*entry["choice"])
-                return dict(zip(self.TUNING, entry["choice"])), entry["ms"]
+                self.set_tuning(**entry["tuning"])
+                return dict(entry["tuning"]), entry["ms"]
         if clusters is not None:
             self.load(clusters, req_offsets)
-        ch = np.zeros(5, np.int32)
+        best = TpcTuning()
         ms = ctypes.c_float()
-        self._ck(self._lib.tpc_autotune(self._ctx, reps, ch.ctypes.data, ctypes.byref(ms)))
-        choice = [int(v) for v in ch]
+        self._ck(self._lib.tpc_autotune(self._ctx, reps, ctypes.byref(best), ctypes.byref(ms)))
+        choice = best.as_dict()
         if cache:
             data = {}
             if os.path.exists(cache):
@@ -274,10 +293,10 @@ class Tracker:
                     data = json.load(open(cache))
                 except (OSError, ValueError):
                     data = {}
-            data[key] = {"choice": choice, "ms": ms.value}
+            data[key] = {"tuning": choice, "ms": ms.value}
             with open(cache, "w") as f:
                 json.dump(data, f, indent=1)
-        return dict(zip(self.TUNING, choice)), ms.value
+        return choice, ms.value
 
     def set_profiling(self, on: bool = True):
         self._ck(self._lib.tpc_set_profiling(self._ctx, int(on)))
@@ -499,6 +518,15 @@ class Server:
         st = np.zeros(5, np.int64)
         self._lib.tpc_server_stats(self._srv, st.ctypes.data)
         return dict(zip(("admitted", "completed", "queued", "arena_bytes", "peak_running"), (int(v) for v in st)))
+
+
+def measure_alu_peaks(device: int = 0) -> dict:
+    """Measured FP32 and FP64 FMA-pipe rates of the device in TFLOP/s."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    rc = load_library().tpc_measure_alu_peaks(device, ctypes.byref(f32), ctypes.byref(f64))
+    if rc != 0:
+        raise TpcError(rc, "tpc_measure_alu_peaks failed")
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
 
 
 def row_params_noalloc(d_clusters, req_offsets=None, out=None, stream=None) -> int:

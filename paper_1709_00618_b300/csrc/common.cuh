@@ -23,6 +23,10 @@ struct __align__(16) RsParams {
   int32_t n_y, n_z, bin_base, count;
 };
 
+// Hint: bring the line holding p into L1 ahead of its use (no register, no
+// fault on any address).
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
 // Read-only 32-byte load of a row-sector's parameters.
 __device__ __forceinline__ RsParams load_params(const RsParams* p) {
   const float4 a = __ldg(reinterpret_cast<const float4*>(p));
@@ -51,7 +55,7 @@ struct Counts {
   uint32_t status;    // ST_* bits
   int32_t n_track_clusters;
   int32_t n32;         // clusters as int32 (length source of the per-cluster scans)
-  int32_t work_next[6];  // work counters of the persistent Kalman kernels (PH_*)
+  int32_t work_next[12];  // work counters of the persistent Kalman kernels, [PH_* x chunk]
   // work counters of the follow (a6) and refit (a8) kernels
   unsigned long long n_prop;    // helix propagations with covariance transport
   unsigned long long n_upd32;   // FP32 Kalman updates
@@ -67,6 +71,20 @@ struct Counts {
 
 // Kalman kernels, in launch order, for the per-kernel work counters.
 enum { PH_FOLLOW_P1 = 0, PH_FOLLOW_P2, PH_FOLLOW_P3, PH_FOLLOW_P4, PH_REFIT_P1, PH_REFIT_P2, PH_COUNT };
+
+// The Kalman stage may split its items into chunks whose zone and FP32
+// kernels run concurrently on two streams (the FP64 pipe of one chunk's
+// zone beside the other's FP32 work); chunk c of nc covers [begin, end).
+constexpr int MAX_CHUNKS = 2;
+struct Chunk {
+  int32_t begin, end;
+};
+__device__ __forceinline__ Chunk chunk_range(int32_t n, int c, int nc) {
+  return {(int32_t)((int64_t)n * c / nc), (int32_t)((int64_t)n * (c + 1) / nc)};
+}
+__device__ __forceinline__ int32_t* work_counter(Counts* cn, int phase, int c) {
+  return &cn->work_next[phase * MAX_CHUNKS + c];
+}
 
 // Per-thread work tallies, flushed once per thread into Counts.
 struct Tally {

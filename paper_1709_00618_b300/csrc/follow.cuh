@@ -105,6 +105,9 @@ struct Lane {
   int kf;       // next forward hit to refit (backward)
   int misses;
   int nupd;     // updates since the last (re)seed
+  int nx_row;   // backward: row of forward hit kf (-1: none), its index and position, loaded a step ahead
+  int nx_c;
+  float2 nx_yz;
   uint32_t flags;
   bool seed_fail;
   bool tr;       // this tracklet is traced
@@ -115,6 +118,17 @@ struct Lane {
   float sC[15];
   Chi2Acc schi2;
 };
+
+// Loads forward hit kf for the backward refit, one step before its use.
+__device__ __forceinline__ void next_fwd_hit(Lane& w, const GridView& g) {
+  if (w.kf >= 0) {
+    w.nx_row = w.hrow[w.kf];
+    w.nx_c = w.hits[w.kf];
+    w.nx_yz = __ldg(g.yz + w.nx_c);
+  } else {
+    w.nx_row = -1;
+  }
+}
 
 // Trace line of one Kalman update (out of line: executed for one tracklet).
 __device__ __noinline__ void trace_line(Counts* cn, float* trace, int cap, float pass, float row, float nupd,
@@ -166,6 +180,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
                                          float* C, Chi2Acc& chi2, LocalTally& tl) {
   const int r = p.row + 1;
   if (r >= NROW) return false;
+  if (r + 1 < NROW) prefetch_l1(g.par + w.ubase + r + 1);  // the next step's row-sector parameters
   const bool chain = w.i < w.L;
   const bool zone = Z && w.nupd < kc.fp64_updates;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
@@ -204,6 +219,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
                                          Lane& w, TrkState& p, double* D, float* C, Chi2Acc& chi2, LocalTally& tl) {
   const int r = p.row - 1;
   if (r < 0) return false;
+  if (r >= 1 && r - 1 < w.r0) prefetch_l1(g.par + w.ubase + r - 1);  // the next step's row-sector parameters
   const bool zone = Z && w.nupd < kc.fp64_updates;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (r >= w.r0) w.flags |= TF_BACK_FAIL;
@@ -211,22 +227,23 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
   }
   tl.prop++;
   tl.prop64 += zone;
-  int c;
+  float2 P;
   if (r >= w.r0) {
-    if (!(w.kf >= 0 && w.hrow[w.kf] == r)) return true;
-    c = w.hits[w.kf];
+    if (w.nx_row != r) return true;
+    P = w.nx_yz;
     w.kf--;
+    next_fwd_hit(w, g);
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
-    c = pick(g, w.ubase + r, r, p, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2], kc, sYH, w.flags,
-             tl.cand);
+    const int c = pick(g, w.ubase + r, r, p, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2], kc, sYH,
+                       w.flags, tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
     w.hits[w.nf + w.nb] = c;
     w.hrow[w.nf + w.nb] = (uint8_t)r;
     w.nb++;
     w.misses = 0;
+    P = __ldg(g.yz + c);
   }
-  const float2 P = __ldg(g.yz + c);
   lane_update<Z>(w, kc, p, zone, D, C, P, chi2, 1);
   if (zone) tl.upd64++;
   else tl.upd32++;
@@ -308,18 +325,19 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
                                                    const int32_t* __restrict__ tl_len,
                                                    const int32_t* __restrict__ tl_end,
                                                    const int32_t* __restrict__ up_m, KConst kc, FollowOut o,
-                                                   FollowWork* W, WorkOrder next, Counts* cn) {
+                                                   FollowWork* W, WorkOrder next, int chunk, int nchunk,
+                                                   Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
-  const int32_t T = cn->n_tracklets;
+  const Chunk ch = chunk_range(cn->n_tracklets, chunk, nchunk);
   LocalTally tl;
   double D[15];
   float C[15];
   for (;;) {
-    const int64_t t = warp_fetch(&cn->work_next[PH_FOLLOW_P1], FULL_MASK);
-    if (__shfl_sync(FULL_MASK, t, 0) >= T) break;
-    const bool valid = t < T;
+    const int64_t t = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P1, chunk), FULL_MASK);
+    if (__shfl_sync(FULL_MASK, t, 0) >= ch.end) break;
+    const bool valid = t < ch.end;
     Lane w;
     TrkState p;
     Chi2Acc chi2;
@@ -383,11 +401,12 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
 // tracklet of its warp.
 __global__ void __launch_bounds__(128, 4) k_follow_p2(GridView g, const int32_t* __restrict__ up_m, KConst kc,
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
-                                                   Counts* cn) {
+                                                   int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
+  const Chunk ch = chunk_range(T, chunk, nchunk);
   LocalTally tl;
   double D[15];  // unused in this phase (the zone is over)
   float C[15];
@@ -403,8 +422,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p2(GridView g, const int32_t*
     const unsigned need = refill_mask(live && !go, go, kc.refill);
     if (need & (1u << (threadIdx.x & 31))) {
       if (dirty) work_store(W, t, w, p, C, chi2, false);
-      const int64_t idx = warp_fetch(&cn->work_next[PH_FOLLOW_P2], need);
-      t = idx < T ? order[idx] : T;
+      const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P2, chunk), need);
+      t = idx < ch.end ? order[idx] : T;
       dirty = false;
       if (t < T) {
         work_load(W, t, w, p, C, chi2);
@@ -432,18 +451,18 @@ __global__ void __launch_bounds__(128, 4) k_follow_p2(GridView g, const int32_t*
 // pass while its covariance is in FP64 (warps take 32 tracklets at a time,
 // as phase 1).
 __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W,
-                                                   WorkOrder next, Counts* cn) {
+                                                   WorkOrder next, int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
-  const int32_t T = cn->n_tracklets;
+  const Chunk ch = chunk_range(cn->n_tracklets, chunk, nchunk);
   LocalTally tl;
   double D[15];
   float C[15];
   for (;;) {
-    const int64_t t = warp_fetch(&cn->work_next[PH_FOLLOW_P3], FULL_MASK);
-    if (__shfl_sync(FULL_MASK, t, 0) >= T) break;
-    const bool valid = t < T;
+    const int64_t t = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P3, chunk), FULL_MASK);
+    if (__shfl_sync(FULL_MASK, t, 0) >= ch.end) break;
+    const bool valid = t < ch.end;
     Lane w;
     TrkState p;
     Chi2Acc chi2;
@@ -457,6 +476,7 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
         p = w.fwd;
         chi2.reset();
         w.kf = w.nf - 2;
+        next_fwd_hit(w, g);
         w.misses = 0;
         reseed_cov(kc, D, C);
         w.nupd = 0;
@@ -517,11 +537,12 @@ __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t 
 // 2) and the outputs.
 __global__ void __launch_bounds__(128, 4) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
-                                                   Counts* cn) {
+                                                   int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
+  const Chunk ch = chunk_range(T, chunk, nchunk);
   LocalTally tl;
   double D[15];  // unused in this phase (the zone is over)
   float C[15];
@@ -535,8 +556,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p4(GridView g, const int32_t*
     const unsigned need = refill_mask(live && !go, go, kc.refill);
     if (need & (1u << (threadIdx.x & 31))) {
       if (t >= 0) write_follow_output(o, t, w, __ldg(g.yz + tl_start[t]).y);
-      const int64_t idx = warp_fetch(&cn->work_next[PH_FOLLOW_P4], need);
-      t = idx < T ? order[idx] : T;
+      const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P4, chunk), need);
+      t = idx < ch.end ? order[idx] : T;
       if (t < T) {
         go = work_load(W, t, w, p, C, chi2);
         w.hits = o.hits + t * NROW;

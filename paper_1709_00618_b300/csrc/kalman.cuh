@@ -212,10 +212,12 @@ __device__ __noinline__ UpdOut kalman_update_d(double* D, float r0, float r1, do
     g0[i] = k0[i] * I00 + k1[i] * I01;
     g1[i] = k0[i] * I01 + k1[i] * I11;
   }
+  // C -= G C[0:2,:], two fused multiply-adds per entry (the FP64 pipe is
+  // the bound of the zone)
 #pragma unroll
   for (int i = 0; i < 5; i++)
 #pragma unroll
-    for (int j = 0; j <= i; j++) D[TPC_CI(i, j)] -= g0[i] * k0[j] + g1[i] * k1[j];
+    for (int j = 0; j <= i; j++) D[TPC_CI(i, j)] = fma(-g0[i], k0[j], fma(-g1[i], k1[j], D[TPC_CI(i, j)]));
   UpdOut o;
   o.d0 = (float)g0[0] * r0 + (float)g1[0] * r1;
   o.d1 = (float)g0[1] * r0 + (float)g1[1] * r1;

@@ -13,7 +13,7 @@ namespace tpc {
 constexpr unsigned FULL_MASK = 0xffffffffu;
 constexpr int ORD_BINS = NROW + 1;           // remaining-row classes (0: longest)
 constexpr int ORD_PHASES = 3;                // follow p2, follow p4, refit p2
-constexpr int ORD_WORDS = ORD_PHASES * 2 * ORD_BINS;
+constexpr int ORD_WORDS = ORD_PHASES * MAX_CHUNKS * 2 * ORD_BINS;
 
 struct WorkOrder {
   int32_t* hist;    // [ORD_BINS] items per class
@@ -31,9 +31,10 @@ __device__ __forceinline__ void order_count(const WorkOrder& o, int64_t i, bool 
   if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&o.hist[b], __popc(peers));
 }
 
-// Positions of all items: the exclusive prefix of the class histogram plus
-// a warp-aggregated running count per class.
-__global__ void k_order(WorkOrder o, const int32_t* __restrict__ n_items, const Counts* cn) {
+// Positions of the items of chunk c of nc: the exclusive prefix of the
+// chunk's class histogram plus a warp-aggregated running count per class,
+// within the chunk's own range of order[].
+__global__ void k_order(WorkOrder o, const int32_t* __restrict__ n_items, int c, int nc, const Counts* cn) {
   // after an overflow the item count exceeds the capacities: do nothing, as
   // every kernel of the pipeline
   if (fatal(cn)) return;
@@ -46,18 +47,19 @@ __global__ void k_order(WorkOrder o, const int32_t* __restrict__ n_items, const 
     }
   }
   __syncthreads();
-  const int32_t N = *n_items;
+  const Chunk ch = chunk_range(*n_items, c, nc);
+  const int32_t N = ch.end - ch.begin;
   const int lane = threadIdx.x & 31;
   for (int64_t base = gtid() - lane; base < N; base += gstride()) {
-    const int64_t i = base + lane;
-    const bool valid = i < N;
+    const int64_t i = ch.begin + base + lane;
+    const bool valid = base + lane < N;
     const int b = valid ? o.key[i] : -1;
     const unsigned peers = __match_any_sync(FULL_MASK, b);
     const int leader = __ffs(peers) - 1;
     int pos = 0;
     if (valid && lane == leader) pos = atomicAdd(&o.cursor[b], __popc(peers));
     pos = __shfl_sync(FULL_MASK, pos, leader);
-    if (valid) o.order[pre[b] + pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
+    if (valid) o.order[ch.begin + pre[b] + pos + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
   }
 }
 

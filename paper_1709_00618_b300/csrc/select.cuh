@@ -225,7 +225,7 @@ struct RefitIn {
 // Phase 1 of the refit: carry the follow state to the outermost owned row
 // (state only), then the updates with the covariance in FP64.
 __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, WorkOrder next,
-                                                  Counts* cn) {
+                                                  int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
   __syncthreads();
@@ -237,11 +237,12 @@ __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst
   float C[15];
   // a warp takes 32 consecutive tracks at a time (lanes past the end idle),
   // so that it can be reconverged before the FP64 zone
+  const Chunk ch = chunk_range(M, chunk, nchunk);
   for (;;) {
-    const int64_t m = warp_fetch(&cn->work_next[PH_REFIT_P1], FULL_MASK);
+    const int64_t m = ch.begin + warp_fetch(work_counter(cn, PH_REFIT_P1, chunk), FULL_MASK);
     const int64_t base = __shfl_sync(FULL_MASK, m, 0);
-    if (base >= M) break;
-    const bool valid = m < M;
+    if (base >= ch.end) break;
+    const bool valid = m < ch.end;
     const int t = valid ? in.track_tl[m] : in.track_tl[base];
     RefitLane w;
     w.n = in.f_n[t];
@@ -354,12 +355,13 @@ __device__ __forceinline__ void write_track(const RefitIn& in, const float* sX, 
 // Phase 2 of the refit: the remaining updates in FP32; lanes refill.
 __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst kc, RefitWork* RW,
                                                   const int32_t* __restrict__ order, tpc_track* __restrict__ out,
-                                                  Counts* cn) {
+                                                  int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
   __syncthreads();
   if (fatal(cn)) return;
   const int32_t M = cn->n_tracks;
+  const Chunk ch = chunk_range(M, chunk, nchunk);
   LocalTally tl;
   double D[15];  // unused in this phase
   float C[15];
@@ -388,8 +390,8 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
     const unsigned need = refill_mask(live && !go, go, kc.refill);
     if (need & (1u << (threadIdx.x & 31))) {
       if (m >= 0) write_track(in, sX, m, RW[m], p, C, chi2, ok, flags, out);
-      const int64_t idx = warp_fetch(&cn->work_next[PH_REFIT_P2], need);
-      m = idx < M ? order[idx] : M;
+      const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_REFIT_P2, chunk), need);
+      m = idx < ch.end ? order[idx] : M;
       if (m < M) load(m);
       else live = false;
     }

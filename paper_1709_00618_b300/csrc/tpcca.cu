@@ -18,6 +18,7 @@
 #include "kalman.cuh"
 #include "follow.cuh"
 #include "select.cuh"
+#include "probe.cuh"
 
 using namespace tpc;
 
@@ -194,8 +195,13 @@ struct tpc_ctx {
   int block_clusters = 256;
   int block_follow = 128;
   int ctas_zone = 2;     // cap on CTAs per SM of the FP64-zone Kalman kernels
-  int ctas_follow = 3;   // cap on CTAs per SM of the refilling Kalman kernels (64: occupancy)
+  int ctas_follow = 0;   // cap on CTAs per SM of the refilling Kalman kernels (64: occupancy; 0: by size)
   int refill = 4;        // idle lanes that trigger a warp's refill
+  int chunks = 0;        // Kalman-stage chunks (2: zone and FP32 kernels of different chunks overlap; 0: 1)
+  int graph_chunks = 0;  // chunks and refilling-kernel CTAs per SM of the captured graph
+  int graph_ctas = 0;
+  cudaStream_t aux = nullptr;       // second stream of the chunked Kalman stage
+  cudaEvent_t ev_chunk[4] = {};     // fork and join of the chunked follow and refit
   // graph
   cudaGraphExec_t graph = nullptr;
   int32_t trace_t = -1;  // traced tracklet
@@ -260,10 +266,22 @@ KConst make_kconst(const tpc_config& c, const Caps& caps) {
   return k;
 }
 
-WorkOrder work_order(tpc_ctx* ctx, int phase) {
+// Chunks of the Kalman stage: the tuned value, else 1 (measured on B300: the
+// overlap gains under 1% on 16 M clusters and loses on 1 M, where launch and
+// join costs weigh more; the autotuner tries both).
+constexpr int64_t kLargeBatch = int64_t(4) << 20;  // clusters from which the size default switches
+int effective_chunks(const tpc_ctx* ctx) { return ctx->chunks > 0 ? ctx->chunks : 1; }
+// CTAs per SM of the refilling Kalman kernels: the tuned value, or by size
+// (a small batch is bound by its longest tracklet, a large one by throughput).
+int effective_ctas_follow(const tpc_ctx* ctx) {
+  if (ctx->ctas_follow > 0) return ctx->ctas_follow;
+  return ctx->n >= kLargeBatch ? 64 : 2;
+}
+
+WorkOrder work_order(tpc_ctx* ctx, int phase, int chunk) {
   const Layout& L = ctx->L;
   WorkOrder o;
-  o.hist = ctx->ptr<int32_t>(L.obins) + phase * 2 * ORD_BINS;
+  o.hist = ctx->ptr<int32_t>(L.obins) + (phase * MAX_CHUNKS + chunk) * 2 * ORD_BINS;
   o.cursor = o.hist + ORD_BINS;
   o.key = ctx->ptr<uint8_t>(L.okey);
   o.order = ctx->ptr<int32_t>(L.order);
@@ -369,7 +387,12 @@ int create_common(tpc_ctx** out, const tpc_config* cfg, int device, void* stream
     }
     ctx->own_stream = true;
   }
-  if (cudaMallocHost(&ctx->h_counts, sizeof(Counts)) != cudaSuccess) {
+  bool ok = cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) == cudaSuccess;
+  for (int i = 0; i < 4 && ok; i++) ok = cudaEventCreateWithFlags(&ctx->ev_chunk[i], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok || cudaMallocHost(&ctx->h_counts, sizeof(Counts)) != cudaSuccess) {
+    for (int i = 0; i < 4; i++)
+      if (ctx->ev_chunk[i]) cudaEventDestroy(ctx->ev_chunk[i]);
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return TPC_ECUDA;
@@ -473,24 +496,41 @@ void enqueue_find(tpc_ctx* ctx) {
                                        ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
                                        ctx->ptr<int32_t>(L.tl_end), cn, C.tl);
   ctx->mark(3);
-  // a6 follow
+  // a6 follow: per chunk, zone (p1) -> order -> FP32 (p2) -> zone (p3) ->
+  // order -> FP32 (p4).  With two chunks the second runs on the auxiliary
+  // stream one kernel behind the first, so that one chunk's FP64 zone shares
+  // the SMs with the other's FP32 phase.
   {
     FollowWork* W = ctx->ptr<FollowWork>(L.fwork);
     const int bf = ctx->block_follow;
-    k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, ctx->ctas_zone), bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
-                                  ctx->ptr<int32_t>(L.tl_end), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx),
-                                  W, work_order(ctx, 0), cn);
-    k_order<<<grid_for(ctx, C.tl, bc), bc, 0, s>>>(work_order(ctx, 0), &cn->n_tracklets, cn);
-    ctx->mark_k(0);
-    k_follow_p2<<<persistent_grid(ctx, k_follow_p2, bf, ctx->ctas_follow), bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.up_m),
-                                                                      ctx->kc, follow_out(ctx), W,
-                                                                      ctx->ptr<int32_t>(L.order), cn);
-    ctx->mark_k(1);
-    k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, ctx->ctas_zone), bf, 0, s>>>(grid_view(ctx), ctx->kc, follow_out(ctx), W,
-                                                                      work_order(ctx, 1), cn);
-    k_order<<<grid_for(ctx, C.tl, bc), bc, 0, s>>>(work_order(ctx, 1), &cn->n_tracklets, cn);
-    ctx->mark_k(2);
-    k_follow_p4<<<persistent_grid(ctx, k_follow_p4, bf, ctx->ctas_follow), bf, 0, s>>>(grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, ctx->ptr<int32_t>(L.order), cn);
+    const int nc = ctx->prof ? 1 : effective_chunks(ctx);
+    int32_t* order = ctx->ptr<int32_t>(L.order);
+    auto follow_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
+      k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, ctx->ctas_zone), bf, 0, st>>>(
+          grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
+          ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, work_order(ctx, 0, c), c, nc, cn);
+      if (after_p1) cudaEventRecord(after_p1, st);
+      k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 0, c), &cn->n_tracklets, c, nc, cn);
+      if (nc == 1) ctx->mark_k(0);
+      k_follow_p2<<<persistent_grid(ctx, k_follow_p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
+          grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
+      if (nc == 1) ctx->mark_k(1);
+      k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, ctx->ctas_zone), bf, 0, st>>>(
+          grid_view(ctx), ctx->kc, follow_out(ctx), W, work_order(ctx, 1, c), c, nc, cn);
+      k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
+      if (nc == 1) ctx->mark_k(2);
+      k_follow_p4<<<persistent_grid(ctx, k_follow_p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
+          grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
+    };
+    if (nc == 1) {
+      follow_chunk(s, 0, nullptr);
+    } else {
+      follow_chunk(s, 0, ctx->ev_chunk[0]);
+      cudaStreamWaitEvent(ctx->aux, ctx->ev_chunk[0], 0);
+      follow_chunk(ctx->aux, 1, nullptr);
+      cudaEventRecord(ctx->ev_chunk[1], ctx->aux);
+      cudaStreamWaitEvent(s, ctx->ev_chunk[1], 0);
+    }
   }
   ctx->mark(4);
   // a7 selection
@@ -540,14 +580,26 @@ void enqueue_fit(tpc_ctx* ctx) {
     in.nown = ctx->ptr<int32_t>(L.nown);
     in.toff = ctx->ptr<int32_t>(L.toff);
     RefitWork* RW = ctx->ptr<RefitWork>(L.rwork);
+    const int nc = ctx->prof ? 1 : effective_chunks(ctx);
+    auto refit_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
+      k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, ctx->ctas_zone), bf, 0, st>>>(
+          grid_view(ctx), in, ctx->kc, RW, work_order(ctx, 2, c), c, nc, cn);
+      if (after_p1) cudaEventRecord(after_p1, st);
+      k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, st>>>(work_order(ctx, 2, c), &cn->n_tracks, c, nc, cn);
+      if (nc == 1) ctx->mark_k(4);
+      k_refit_p2<<<persistent_grid(ctx, k_refit_p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
+          grid_view(ctx), in, ctx->kc, RW, ctx->ptr<int32_t>(L.order), ctx->ptr<tpc_track>(L.tracks), c, nc, cn);
+    };
     ctx->mark_k(3);
-    k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, ctx->ctas_zone), bf, 0, s>>>(grid_view(ctx), in, ctx->kc, RW,
-                                                                    work_order(ctx, 2), cn);
-    k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, s>>>(work_order(ctx, 2), &cn->n_tracks, cn);
-    ctx->mark_k(4);
-    k_refit_p2<<<persistent_grid(ctx, k_refit_p2, bf, ctx->ctas_follow), bf, 0, s>>>(grid_view(ctx), in, ctx->kc, RW,
-                                                                    ctx->ptr<int32_t>(L.order),
-                                                                    ctx->ptr<tpc_track>(L.tracks), cn);
+    if (nc == 1) {
+      refit_chunk(s, 0, nullptr);
+    } else {
+      refit_chunk(s, 0, ctx->ev_chunk[2]);
+      cudaStreamWaitEvent(ctx->aux, ctx->ev_chunk[2], 0);
+      refit_chunk(ctx->aux, 1, nullptr);
+      cudaEventRecord(ctx->ev_chunk[3], ctx->aux);
+      cudaStreamWaitEvent(s, ctx->ev_chunk[3], 0);
+    }
     ctx->mark_k(5);
   }
   k_track_clusters<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
@@ -672,6 +724,7 @@ int tpc_create_with_arena(tpc_ctx** out, const tpc_config* cfg, int device, void
 void tpc_destroy(tpc_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
+  if (ctx->aux) cudaStreamSynchronize(ctx->aux);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   for (int i = 0; i < 7; i++)
@@ -684,6 +737,9 @@ void tpc_destroy(tpc_ctx* ctx) {
   }
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_req) cudaFreeHost(ctx->h_req);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  for (int i = 0; i < 4; i++)
+    if (ctx->ev_chunk[i]) cudaEventDestroy(ctx->ev_chunk[i]);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;
 }
@@ -736,6 +792,10 @@ int tpc_run_graph(tpc_ctx* ctx) {
   if (!ctx) return TPC_EINVAL;
   if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "no clusters loaded");
   CK(cudaSetDevice(ctx->device));
+  if (ctx->graph && (ctx->graph_chunks != effective_chunks(ctx) || ctx->graph_ctas != effective_ctas_follow(ctx))) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
   if (!ctx->graph) {
     if (!ctx->own_stream && ctx->stream == nullptr)
       return fail(ctx, TPC_EINVAL, "graph capture needs a non-default stream");
@@ -749,6 +809,8 @@ int tpc_run_graph(tpc_ctx* ctx) {
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess) return fail(ctx, TPC_ECUDA, "graph capture: %s", cudaGetErrorString(e));
     ctx->graph_kernels = count_kernel_nodes(g);
+    ctx->graph_chunks = effective_chunks(ctx);
+    ctx->graph_ctas = effective_ctas_follow(ctx);
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -904,7 +966,30 @@ int tpc_get_stage(tpc_ctx* ctx, int item, void* host_out, int64_t cap_bytes, int
   return TPC_OK;
 }
 
-int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[5], float* best_ms) {
+namespace {
+void get_tuning(const tpc_ctx* ctx, tpc_tuning* t) {
+  t->block_clusters = ctx->block_clusters;
+  t->block_follow = ctx->block_follow;
+  t->ctas_per_sm_zone = ctx->ctas_zone;
+  t->ctas_per_sm_follow = ctx->ctas_follow;
+  t->refill = ctx->refill;
+  t->chunks = ctx->chunks;
+}
+void apply_tuning(tpc_ctx* ctx, const tpc_tuning* t) {
+  if (t->block_clusters > 0) ctx->block_clusters = t->block_clusters;
+  if (t->block_follow > 0) ctx->block_follow = t->block_follow;
+  if (t->ctas_per_sm_zone > 0) ctx->ctas_zone = t->ctas_per_sm_zone;
+  if (t->ctas_per_sm_follow > 0) ctx->ctas_follow = t->ctas_per_sm_follow;
+  if (t->refill > 0) ctx->refill = ctx->kc.refill = t->refill;
+  if (t->chunks > 0) ctx->chunks = t->chunks;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+}
+}  // namespace
+
+int tpc_autotune(tpc_ctx* ctx, int32_t reps, tpc_tuning* best_out, float* best_ms) {
   if (!ctx || reps < 1 || reps > 100) return TPC_EINVAL;
   if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "load a representative batch before tpc_autotune");
   CK(cudaSetDevice(ctx->device));
@@ -930,43 +1015,50 @@ int tpc_autotune(tpc_ctx* ctx, int32_t reps, int32_t choice[5], float* best_ms) 
     ms = t[t.size() / 2];
     return check_status(ctx);
   };
-  auto apply = [&](const int* v) {
-    ctx->block_clusters = v[0];
-    ctx->block_follow = v[1];
-    ctx->ctas_zone = v[2];
-    ctx->ctas_follow = v[3];
-    ctx->refill = v[4];
-    ctx->kc.refill = v[4];
+  // candidates per field, in the order of tpc_tuning
+  static const int kCand[6][4] = {{128, 256, 512, 0}, {64, 96, 128, 0}, {1, 2, 3, 0},
+                                  {2, 3, 64, 0},      {1, 4, 8, 16},    {1, 2, 0, 0}};
+  static const int kNCand[6] = {3, 3, 3, 3, 4, 2};
+  tpc_tuning cur;
+  get_tuning(ctx, &cur);
+  if (cur.chunks <= 0) cur.chunks = effective_chunks(ctx);
+  if (cur.ctas_per_sm_follow <= 0) cur.ctas_per_sm_follow = effective_ctas_follow(ctx);
+  int best[6] = {cur.block_clusters, cur.block_follow, cur.ctas_per_sm_zone, cur.ctas_per_sm_follow, cur.refill,
+                 cur.chunks};
+  auto as_tuning = [](const int* v) {
+    tpc_tuning t;
+    t.block_clusters = v[0];
+    t.block_follow = v[1];
+    t.ctas_per_sm_zone = v[2];
+    t.ctas_per_sm_follow = v[3];
+    t.refill = v[4];
+    t.chunks = v[5];
+    return t;
   };
-  static const int kCand[5][4] = {{128, 256, 512, 0}, {64, 96, 128, 0}, {1, 2, 3, 0}, {2, 3, 64, 0}, {1, 4, 8, 16}};
-  static const int kNCand[5] = {3, 3, 3, 3, 4};
-  int best[5] = {ctx->block_clusters, ctx->block_follow, ctx->ctas_zone, ctx->ctas_follow, ctx->refill};
   float best_t = 0.0f;
   int rc = measure(best_t);
-  for (int dim = 0; dim < 5 && rc == TPC_OK; dim++) {  // coordinate descent
+  for (int dim = 0; dim < 6 && rc == TPC_OK; dim++) {  // coordinate descent
     for (int k = 0; k < kNCand[dim] && rc == TPC_OK; k++) {
-      int trial[5] = {best[0], best[1], best[2], best[3], best[4]};
+      int trial[6];
+      for (int i = 0; i < 6; i++) trial[i] = best[i];
       trial[dim] = kCand[dim][k];
       if (trial[dim] == best[dim]) continue;
-      apply(trial);
-      float t = 0.0f;
-      rc = measure(t);
-      if (rc == TPC_OK && t < best_t) {
-        best_t = t;
+      const tpc_tuning t = as_tuning(trial);
+      apply_tuning(ctx, &t);
+      float ms = 0.0f;
+      rc = measure(ms);
+      if (rc == TPC_OK && ms < best_t) {
+        best_t = ms;
         best[dim] = trial[dim];
       }
     }
   }
-  apply(best);
+  const tpc_tuning bt = as_tuning(best);
+  apply_tuning(ctx, &bt);
   ctx->prof = prof;
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (choice)
-    for (int i = 0; i < 5; i++) choice[i] = best[i];
+  if (best_out) *best_out = bt;
   if (best_ms) *best_ms = best_t;
   return rc;
 }
@@ -1059,26 +1151,65 @@ int tpc_get_work(tpc_ctx* ctx, uint64_t work[5]) {
   return TPC_OK;
 }
 
-int tpc_set_tuning(tpc_ctx* ctx, int block_clusters, int block_follow, int ctas_per_sm_zone, int ctas_per_sm_follow,
-                   int refill) {
-  if (!ctx) return TPC_EINVAL;
-  if (ctas_per_sm_zone < 0 || ctas_per_sm_zone > 64) return fail(ctx, TPC_EINVAL, "ctas_per_sm out of range");
-  if (refill < 0 || refill > 32) return fail(ctx, TPC_EINVAL, "refill must be in [1, 32]");
-  if (block_clusters && (block_clusters < 32 || block_clusters > 1024 || block_clusters % 32))
-    return fail(ctx, TPC_EINVAL, "block_clusters must be a multiple of 32 in [32, 1024]");
-  if (block_follow && (block_follow < 32 || block_follow > 128 || block_follow % 32))
-    return fail(ctx, TPC_EINVAL, "block_follow must be a multiple of 32 in [32, 128]");
-  if (ctas_per_sm_follow < 0 || ctas_per_sm_follow > 64) return fail(ctx, TPC_EINVAL, "ctas_per_sm out of range");
-  if (block_clusters) ctx->block_clusters = block_clusters;
-  if (block_follow) ctx->block_follow = block_follow;
-  if (ctas_per_sm_zone) ctx->ctas_zone = ctas_per_sm_zone;
-  if (ctas_per_sm_follow) ctx->ctas_follow = ctas_per_sm_follow;
-  if (refill) ctx->refill = ctx->kc.refill = refill;
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+int tpc_get_tuning(tpc_ctx* ctx, tpc_tuning* t) {
+  if (!ctx || !t) return TPC_EINVAL;
+  get_tuning(ctx, t);
   return TPC_OK;
+}
+
+int tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* t) {
+  if (!ctx || !t) return TPC_EINVAL;
+  if (t->block_clusters > 0 && (t->block_clusters < 32 || t->block_clusters > 1024 || t->block_clusters % 32))
+    return fail(ctx, TPC_EINVAL, "block_clusters must be a multiple of 32 in [32, 1024]");
+  if (t->block_follow > 0 && (t->block_follow < 32 || t->block_follow > 128 || t->block_follow % 32))
+    return fail(ctx, TPC_EINVAL, "block_follow must be a multiple of 32 in [32, 128]");
+  if (t->ctas_per_sm_zone > 64 || t->ctas_per_sm_follow > 64) return fail(ctx, TPC_EINVAL, "ctas_per_sm above 64");
+  if (t->refill > 32) return fail(ctx, TPC_EINVAL, "refill must be in [1, 32]");
+  if (t->chunks > MAX_CHUNKS) return fail(ctx, TPC_EINVAL, "chunks must be 1 or 2");
+  apply_tuning(ctx, t);
+  return TPC_OK;
+}
+
+int tpc_measure_alu_peaks(int device, double* fp32_tflops, double* fp64_tflops) {
+  if (!fp32_tflops && !fp64_tflops) return TPC_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return TPC_ECUDA;
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return TPC_ECUDA;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double* out = nullptr;
+  int rc = TPC_OK;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess || cudaMalloc(&out, sizeof(double)) != cudaSuccess)
+    rc = TPC_ECUDA;
+  const int threads = 256, blocks = n_sm * 8;
+  auto run = [&](bool dbl, int iters, double* tflops) {
+    if (rc != TPC_OK || !tflops) return;
+    float best = 0.0f;
+    for (int r = 0; r < 3; r++) {  // the first run warms up, the best of the rest counts
+      cudaEventRecord(e0, st);
+      if (dbl) k_fma_probe<double><<<blocks, threads, 0, st>>>(out, iters, 0.999999, 1e-7);
+      else k_fma_probe<float><<<blocks, threads, 0, st>>>((float*)out, iters, 0.999999f, 1e-7f);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = TPC_ECUDA;
+        return;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0 && (best == 0.0f || ms < best)) best = ms;
+    }
+    const double flop = 2.0 * PROBE_CHAINS * (double)iters * threads * blocks;
+    *tflops = flop / (best * 1e-3) / 1e12;
+  };
+  run(false, 1 << 12, fp32_tflops);
+  run(true, 1 << 7, fp64_tflops);
+  if (cudaGetLastError() != cudaSuccess) rc = TPC_ECUDA;
+  if (out) cudaFree(out);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  return rc;
 }
 
 }  // extern "C"

@@ -130,12 +130,17 @@ def test_autotuned_shapes_give_the_same_result():
         assert choice["ctas_per_sm_zone"] in (1, 2, 3)
         assert choice["ctas_per_sm_follow"] in (2, 3, 64)
         assert choice["refill"] in (1, 4, 8, 16)
+        assert choice["chunks"] in (1, 2)
+        assert t.tuning() == choice
         assert ms > 0
         tracks, ct, _ = t.track(cl)
         g_tracks, g_ct, _ = t.track(cl, graph=True)
-        for shape in ((512, 64, 3, 2, 1), (128, 128, 1, 8, 32), (256, 96, 2, 1, 5)):
-            t.set_tuning(*shape)
+        names = ("block_clusters", "block_follow", "ctas_per_sm_zone", "ctas_per_sm_follow", "refill", "chunks")
+        for shape in ((512, 64, 3, 2, 1, 1), (128, 128, 1, 8, 32, 2), (256, 96, 2, 1, 5, 2)):
+            t.set_tuning(**dict(zip(names, shape)))
             s_tracks, s_ct, _ = t.track(cl)
+            assert s_tracks.tobytes() == ref_tracks.tobytes() and np.array_equal(s_ct, ref_ct)
+            s_tracks, s_ct, _ = t.track(cl, graph=True)
             assert s_tracks.tobytes() == ref_tracks.tobytes() and np.array_equal(s_ct, ref_ct)
     assert tracks.tobytes() == ref_tracks.tobytes() and np.array_equal(ct, ref_ct)
     assert g_tracks.tobytes() == ref_tracks.tobytes() and np.array_equal(g_ct, ref_ct)
