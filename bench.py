@@ -108,6 +108,37 @@ BYTES_GRID, BYTES_NEIGH = 44, 45
 FP32_FLOP_PER_CLK_SM, FP64_FLOP_PER_CLK_SM, N_SM = 256, 4, 148
 
 
+def _source_hash():
+    import glob
+    import hashlib
+    m = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1709_00618_b300", "csrc", "*"))) + \
+            [os.path.join(ROOT, "include", "tpcca.h")]:
+        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
+            with open(f, "rb") as fh:
+                m.update(fh.read())
+    return m.hexdigest()
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of each profiled kernel from the committed ncu
+    summary, or {} when the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic_central_event.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return {}
+    tag = next((ln for ln in lines if ln.startswith("# sources:")), "")
+    if not tag.endswith(_source_hash()):
+        return {}
+    out = {}
+    for ln in lines:
+        if ln and not ln.startswith("#"):
+            name, rd, wr = ln.split()[:3]
+            out[name] = (float(rd) + float(wr)) * 1e6
+    return out
+
+
 def kalman_flops(w):
     """(binary32 flop, binary64 flop) of one Kalman kernel's work counters."""
     p32 = w["prop"] - w["prop64"]
@@ -184,6 +215,78 @@ def cpu_baseline(cl):
                                                  "1 thread"}}
 
 
+def all_configs(local):
+    """Per-config table (one sector, central event, 10 ms timeframe): GPU
+    device throughput (graph, inputs resident, L2 flushed), per-call latency
+    through the public API from page-locked host memory to results on the
+    host, and the oracle on one core and on all cores (the timeframe on a
+    subset of its sectors)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_1709_00618_b300 as tpc
+    import synth
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    cores = os.cpu_count() or 1
+    rows = {}
+    cases = [("config 1: one sector, 400 tracks, seed 0", lambda: synth.one_sector(seed=0).clusters, 50, None),
+             ("config 2: central Pb-Pb-like event, seed 1", lambda: synth.central_event(seed=1).clusters, 20,
+              None),
+             ("config 3: 10 ms timeframe at 50 kHz, seed 2", lambda: synth.timeframe(seed=2, length_ms=10.0).clusters,
+              3, (0, 18))]
+    for name, gen, reps, subset in cases:
+        cl = gen()
+        n = len(cl)
+        stream = torch.cuda.Stream()
+        trk = tpc.Tracker(device=local, stream=stream)
+        dev = torch.from_numpy(cl.view(np.uint8)).to(f"cuda:{local}")
+        for _ in range(3):
+            trk.load(dev).run_graph()
+        trk.sync()
+        dt = []
+        for _ in range(reps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            trk.load(dev).run_graph()
+            e1.record(stream)
+            e1.synchronize()
+            dt.append(e0.elapsed_time(e1))
+        host = torch.from_numpy(cl.view(np.uint8)).pin_memory().numpy().view(synth.CLUSTER_DTYPE)
+        counts = trk.counts()
+        tr_buf = torch.zeros(counts["n_tracks"] + 1024, 128, dtype=torch.uint8).pin_memory()
+        ct_buf = torch.zeros(n, dtype=torch.int32).pin_memory()
+        lat = []
+        for i in range(reps + 2):
+            t0 = time.perf_counter()
+            trk.load(host).run_graph()
+            trk.get_into(tr_buf, ct_buf)
+            if i >= 2:
+                lat.append(1e3 * (time.perf_counter() - t0))
+        trk.close()
+        del dev
+        sub = cl if subset is None else cl[np.isin(cl["sector"], subset)]
+        t0 = time.perf_counter()
+        oracle.run(sub, threads=cores)
+        t_all = time.perf_counter() - t0
+        one = sub if subset is None else sub[sub["sector"] == subset[0]]
+        one = one[: min(len(one), 500_000)]
+        t0 = time.perf_counter()
+        oracle.run(one, threads=1)
+        t_one = time.perf_counter() - t0
+        rows[name] = {"clusters": n, "tracks": counts["n_tracks"], "tracklets": counts["n_tracklets"],
+                      "gpu_device_clusters_per_s": n / (statistics.median(dt) / 1e3),
+                      "gpu_device_ms": statistics.median(dt),
+                      "gpu_api_latency_ms_p50": _pct(lat, 50), "gpu_api_latency_ms_p99": _pct(lat, 99),
+                      "oracle_all_cores_clusters_per_s": len(sub) / t_all, "oracle_cores": cores,
+                      "oracle_all_cores_sample": "all sectors" if subset is None else f"sectors {subset}",
+                      "oracle_one_core_clusters_per_s": len(one) / t_one,
+                      "oracle_one_core_sample": f"{len(one)} clusters"}
+    print(json.dumps({"all_configs": rows}))
+
+
 def run_reference(args):
     """The oracle (plain FP64 C, all host cores) on the same workload."""
     import numpy as np
@@ -211,6 +314,21 @@ def run_reference(args):
                              "sample": f"full event ({n} clusters) x {args.steps} runs"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def combine_ranks(t_step, n_clusters, world, device):
+    """Replicas: the job's step time is the slowest rank's, its work the sum
+    of every rank's clusters (each rank tracks its own event).  Returns
+    (max step time, total clusters)."""
+    if world <= 1:
+        return t_step, n_clusters
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_step], dtype=torch.float64, device=device)
+    c = torch.tensor([float(n_clusters)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
 
 
 def _pct(v, q):
@@ -422,6 +540,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-timeframes", type=int, default=24)
     ap.add_argument("--serving-pool", type=int, default=4)
+    ap.add_argument("--all-configs", action="store_true",
+                    help="print the per-config table (one sector, central event, 10 ms timeframe) instead")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -438,6 +558,10 @@ def main():
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    if args.all_configs:
+        if rank == 0:
+            all_configs(local)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
@@ -475,11 +599,7 @@ def main():
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
         torch.cuda.synchronize()
-    t_step = sum(times) / len(times)
-    if world > 1:
-        tt = torch.tensor([t_step], device=f"cuda:{local}")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(tt.item())
+    t_step, total_clusters = combine_ranks(sum(times) / len(times), n, world, f"cuda:{local}")
     counts = trk.counts()
     tracks, ct, _ = trk.get()
 
@@ -517,13 +637,16 @@ def main():
         tr, c2, _ = trk.get()
         if i >= warm:
             e2e.append(time.perf_counter() - t0)
-    e2e_t = sum(e2e) / len(e2e)
+    e2e_t, _ = combine_ranks(sum(e2e) / len(e2e), n, world, f"cuda:{local}")
     trk.close()
 
     clocks = clk.summary()
-    roof, kernel_table = roofline(stages, kalman, n, alu, clocks)
+    traffic = ncu_traffic()
+    roof, kernel_table = roofline(stages, kalman, n, alu, clocks, traffic if world == 1 else None)
+    for k, v in kernel_table.items():
+        v["traffic"] = traffic.get(k)
     peaks, src = _peaks()
-    line = {"metric": METRIC, "value": world * n / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": total_clusters / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1",
@@ -533,7 +656,7 @@ def main():
                        "kernels_per_step": kernels_per_step},
             "clocks": clocks,
             "alu_peaks_measured": alu,
-            "e2e": {"value": world * n / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+            "e2e": {"value": total_clusters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 128 * len(tr) + 4 * n},
             "gpu_launches": kernels_per_step * args.steps,
             "roofline": roof,
