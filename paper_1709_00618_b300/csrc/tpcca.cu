@@ -482,7 +482,7 @@ void enqueue_find(tpc_ctx* ctx) {
                                  ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), cn);
   ctx->mark(1);
   // a3 neighbours
-  k_neighbours<<<gN, 256, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
+  k_neighbours<<<grid_for(ctx, C.n * NB_G, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
                                   bin_start, ctx->kc, ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn),
                                   ctx->ptr<uint8_t>(L.tie), cn);
   ctx->mark(2);
