@@ -61,8 +61,8 @@ __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Tr
   const RsParams P = load_params(g.par + rs);
   if (P.count == 0) return -1;
   const float Syy = cyy + kc.V, Szz = czz + kc.V;
-  const float wy = sqrtf(kc.gate * Syy), wz = sqrtf(kc.gate * Szz);
-  const float iSyy = 1.0f / Syy, iSzz = 1.0f / Szz;
+  const float wy = ksqrt(kc.gate * Syy), wz = ksqrt(kc.gate * Szz);
+  const float iSyy = kinv(Syy), iSzz = kinv(Szz);
   int iy0, iy1, iz0, iz1;
   axis_range(p.y + p.yl, wy, -sYH[row], P.inv_y, P.n_y, iy0, iy1);
   axis_range(p.zref + (p.z + p.zl), wz, P.z_lo, P.inv_z, P.n_z, iz0, iz1);

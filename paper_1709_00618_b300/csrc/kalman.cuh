@@ -50,6 +50,14 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, double d) {
   lo = (float)(v - (double)hi);
 }
 
+// Square root and reciprocal of the binary32 Kalman arithmetic: the hardware
+// approximations (relative error about 1e-7, three orders below the parity
+// tolerances, and shorter dependency chains than the IEEE-rounded forms that
+// the grid and link stages keep).  ksqrt needs v > 0.
+__device__ __forceinline__ float ksqrt(float v) { return v * rsqrtf(v); }
+__device__ __forceinline__ float kinv(float v) { return __fdividef(1.0f, v); }
+__device__ __forceinline__ double kinv(double v) { return 1.0 / v; }
+
 // C <- J C J^T for the sparse first-order Jacobian of one propagation step.
 template <typename T>
 __device__ __forceinline__ void cov_transport(T* C, T j02, T j04, T j24, T j12, T j13, T j14) {
@@ -105,7 +113,7 @@ template <typename T>
 __device__ __forceinline__ float kalman_update(TrkState& p, T* C, float my, float mz, T V) {
   const float r0 = residual_y(p, my), r1 = residual_z(p, mz);
   const T S00 = C[0] + V, S01 = C[1], S11 = C[2] + V;
-  const T idet = T(1) / (S00 * S11 - S01 * S01);
+  const T idet = kinv(S00 * S11 - S01 * S01);
   const T I00 = S11 * idet, I01 = -S01 * idet, I11 = S00 * idet;
   const T k0[5] = {C[0], C[1], C[3], C[6], C[10]};  // column 0
   const T k1[5] = {C[1], C[2], C[4], C[7], C[11]};  // column 1
@@ -151,8 +159,8 @@ __device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, cons
   const float s1 = p.s, s2 = s1 + kap * dx;
   if (fabsf(fabsf(s1) - kc.s_max) <= 1e-5f || fabsf(fabsf(s2) - kc.s_max) <= 1e-5f) flags |= TF_SLIM;
   if (!(fabsf(s1) < kc.s_max && fabsf(s2) < kc.s_max)) return false;
-  const float c1 = sqrtf(1.0f - s1 * s1), c2 = sqrtf(1.0f - s2 * s2);
-  const float icc = 1.0f / (c1 + c2);
+  const float c1 = ksqrt(1.0f - s1 * s1), c2 = ksqrt(1.0f - s2 * s2);
+  const float icc = kinv(c1 + c2);
   const float ss = s1 + s2;
   const float dy = dx * ss * icc;
   // arc length: sin(phi2 - phi1) = kap*dx*g with g = c1 + s1 (s1+s2)/(c1+c2),
@@ -170,7 +178,7 @@ __device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, cons
   }
   const float dS = dx * g * h;
   if (J) {
-    const float sm = 0.5f * ss, cm = sqrtf(1.0f - sm * sm), icm3 = 1.0f / (cm * cm * cm);
+    const float sm = 0.5f * ss, cm = ksqrt(1.0f - sm * sm), icm3 = kinv(cm * cm * cm);
     J->j02 = dx * icm3;
     J->j04 = -kc.K * dx * dx * 0.5f * icm3;
     J->j24 = -kc.K * dx;
