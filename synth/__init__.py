@@ -64,6 +64,9 @@ def _load():
         lib.gen_free.argtypes = [ctypes.c_void_p]
         lib.gen_track_info.argtypes = [ctypes.POINTER(_Params), ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]
         lib.gen_track_info.restype = ctypes.c_int
+        lib.gen_track_table.argtypes = [ctypes.POINTER(_Params), ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_int64)]
+        lib.gen_track_table.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -135,6 +138,25 @@ def generate(p: GenParams, truth: bool = False) -> Event:
         if truth:
             lib.gen_free(pt)
     return Event(cl, tr, int(ntr.value), p)
+
+
+TRACK_TABLE_DTYPE = np.dtype([("xv", "<f8"), ("yv", "<f8"), ("phi0", "<f8"), ("pt", "<f8"), ("q", "<f8"),
+                              ("t", "<f8"), ("tc", "<f8")])
+
+
+def track_table(p: GenParams) -> np.ndarray:
+    """Kinematics of every track drawn with `p`, indexed by label (cluster
+    id): vertex (xv, yv), phi0, pT, charge, t = sinh(eta) and the collision
+    time tc in us (timeframes; 0 for events)."""
+    lib = _load()
+    cp = p._c()
+    n = ctypes.c_int64()
+    if lib.gen_track_table(ctypes.byref(cp), None, 0, ctypes.byref(n)) != 0:
+        raise RuntimeError("generator failed")
+    out = np.zeros(n.value, TRACK_TABLE_DTYPE)
+    if n.value and lib.gen_track_table(ctypes.byref(cp), out.ctypes.data, n.value, ctypes.byref(n)) != 0:
+        raise RuntimeError("generator failed")
+    return out
 
 
 def track_info(p: GenParams, label: int) -> dict:

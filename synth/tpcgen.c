@@ -220,15 +220,9 @@ static int64_t track_hits(const gen_params *p, const track_t *tr, int64_t label,
   return n;
 }
 
-/*
- * Generate one event (or one timeframe).  On success *clusters (and *truth
- * when truth != NULL) point to malloc'd arrays of *n entries, released with
- * gen_free.  Returns 0, or -1 on allocation failure / bad parameters.
- */
-int gen_run(const gen_params *p, gen_cluster **clusters, gen_truth **truth, int64_t *n_out,
-            int64_t *n_tracks_out) {
-  if (!p || !clusters || !n_out || p->pt_min <= 0 || p->pt_max <= p->pt_min) return -1;
-  /* 1. the track list */
+/* The track list of an event or timeframe (step 1 of gen_run): *tracks is
+   malloc'd with *ntr_out entries.  Returns 0, or -1 on allocation failure. */
+static int build_tracks(const gen_params *p, track_t **tracks_out, int64_t *ntr_out) {
   int64_t ntr = 0, cap = 0;
   track_t *tracks = NULL;
   if (!p->timeframe) {
@@ -258,6 +252,23 @@ int gen_run(const gen_params *p, gen_cluster **clusters, gen_truth **truth, int6
       for (int64_t i = 0; i < nsec; i++) sample_track(p, ntr, 1, tcoll, &tracks[ntr]), ntr++;
     }
   }
+  *tracks_out = tracks;
+  *ntr_out = ntr;
+  return 0;
+}
+
+/*
+ * Generate one event (or one timeframe).  On success *clusters (and *truth
+ * when truth != NULL) point to malloc'd arrays of *n entries, released with
+ * gen_free.  Returns 0, or -1 on allocation failure / bad parameters.
+ */
+int gen_run(const gen_params *p, gen_cluster **clusters, gen_truth **truth, int64_t *n_out,
+            int64_t *n_tracks_out) {
+  if (!p || !clusters || !n_out || p->pt_min <= 0 || p->pt_max <= p->pt_min) return -1;
+  /* 1. the track list */
+  int64_t ntr = 0;
+  track_t *tracks = NULL;
+  if (build_tracks(p, &tracks, &ntr) != 0) return -1;
   /* 2. count, scan, fill (deterministic for any thread count) */
   int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ntr + 1));
   if (!off) { free(tracks); return -1; }
@@ -313,6 +324,24 @@ int gen_run(const gen_params *p, gen_cluster **clusters, gen_truth **truth, int6
 }
 
 void gen_free(void *ptr) { free(ptr); }
+
+/* Kinematics of every track of an event or timeframe, in label order:
+   out[7*i..7*i+6] = {xv, yv, phi0, pt, q, t, tc} (tc: collision time in us,
+   0 for events).  With out == NULL only *n_out is set; otherwise at most cap
+   tracks are written.  Returns 0, or -1 on failure. */
+int gen_track_table(const gen_params *p, double *out, int64_t cap, int64_t *n_out) {
+  track_t *tracks = NULL;
+  int64_t ntr = 0;
+  if (!p || !n_out || build_tracks(p, &tracks, &ntr) != 0) return -1;
+  *n_out = ntr;
+  for (int64_t i = 0; out && i < ntr && i < cap; i++) {
+    const track_t *tr = &tracks[i];
+    double *o = out + 7 * i;
+    o[0] = tr->xv; o[1] = tr->yv; o[2] = tr->phi0; o[3] = tr->pt; o[4] = tr->q; o[5] = tr->t; o[6] = tr->tc;
+  }
+  free(tracks);
+  return 0;
+}
 
 /* Track kinematics for label i (as drawn by gen_run with the same params):
    out = {xv, yv, phi0, pt, q, t, tc}. Returns -1 if i is out of range. */
