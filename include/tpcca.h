@@ -312,6 +312,50 @@ int tpc_set_tuning(tpc_ctx *ctx, const tpc_tuning *t);
  * tpc_find_tracks before get). */
 int tpc_autotune(tpc_ctx *ctx, int32_t reps, tpc_tuning *best, float *best_ms);
 
+/* --------------------------------------------- vertices in the drift time */
+/* Continuous read-out (Sec. 5): the collision time is unknown before
+ * tracking, so a timeframe is tracked with z replaced by the drift
+ * coordinate z_t = v_d (t_collision - t_frame) + z_max - |z|, the collision
+ * times are estimated from the tracks, and z_t is then converted to space.
+ * Reading: a track extrapolated to its closest approach to the beam axis
+ * gives t = (z_t - z_max) / v_d; tracks with |distance| <= dca_max, at least
+ * min_clusters clusters and a z_t change of at most ext_max in the
+ * extrapolation take part; sorted in t they are cut wherever neighbours are
+ * more than gap apart; runs of at least min_tracks tracks are vertices with
+ * the mean t of their tracks; their tracks get z = side (z_max - (z_t -
+ * v_d t_vertex)) at the innermost row (side +1 for sectors 0..17, -1 for
+ * 18..35) and dz/ds_T = -side t. */
+typedef struct {
+  double vdrift_cm_us;  /* drift velocity; 2.5 */
+  double zmax_cm;       /* drift length; 250 */
+  double dca_max_cm;    /* largest transverse distance to the beam axis; 2 */
+  double ext_max_cm;    /* largest z_t change of the extrapolation; 300 */
+  double gap_us;        /* time gap that separates vertices; 0.5 */
+  int32_t min_tracks;   /* tracks of a vertex; 3 */
+  int32_t min_clusters; /* clusters of a participating track; 20 */
+} tpc_vertex_config;
+
+typedef struct {
+  double time_us;   /* mean time estimate of its tracks (frame time, us) */
+  int32_t n_tracks; /* tracks assigned */
+  int32_t request;  /* request index (0) */
+} tpc_vertex;
+
+int tpc_default_vertex_config(tpc_vertex_config *cfg);
+
+/* On the fitted tracks of the loaded request (one request per call;
+ * TPC_EINVAL otherwise or before tpc_fit_tracks).  cfg NULL: defaults.
+ * Asynchronous; results with tpc_get_vertices. */
+int tpc_find_vertices(tpc_ctx *ctx, const tpc_vertex_config *cfg);
+
+/* Waits and copies: vertices in time order (out: room for cap; *n_out the
+ * count; TPC_EOVERFLOW without copying when cap is too small, or when the
+ * tracks' time range exceeds the reserved 2^18 bins of gap/2), and per track
+ * (optional, n_tracks entries each): vertex index or -1, time estimate (us),
+ * spatial z (cm; NaN without a vertex) and spatial dz/ds_T. */
+int tpc_get_vertices(tpc_ctx *ctx, tpc_vertex *out, int64_t cap, int64_t *n_out, int32_t *track_vertex,
+                     float *track_time, float *track_z, float *track_tgl);
+
 /* ------------------------------------------------------ serving (requests) */
 /* Continuous-batching request loop: the serving form of tracking several
  * events or continuous-readout timeframes (Sec. 2, Sec. 5) as they arrive.

@@ -12,8 +12,9 @@ step, in FP64 with numpy:
    point of closest approach to the beam axis in the transverse plane;
    z_t there is v_d * t_coll + z_max for a track from a collision at z = 0,
    so t_est = (z_t(dca) - z_max) / v_d.
-2. A track takes part when |dca| <= dca_max and it has at least min_clusters
-   clusters.
+2. A track takes part when |dca| <= dca_max, it has at least min_clusters
+   clusters and its extrapolation moves z_t by at most ext_max (no track
+   from the beam line crosses more than the drift length).
 3. The participating tracks of a request, sorted by t_est, are cut wherever
    two neighbours are more than `gap` apart; a run of at least min_tracks
    tracks is a vertex, its time the mean t_est of its tracks.
@@ -33,8 +34,8 @@ NSEC = 36
 
 
 def default_params(**kw) -> dict:
-    p = {"vdrift": 2.5, "zmax": 250.0, "dca_max": 2.0, "gap": 0.5, "min_tracks": 3, "min_clusters": 20,
-         "bz_kg": 5.0}
+    p = {"vdrift": 2.5, "zmax": 250.0, "dca_max": 2.0, "ext_max": 300.0, "gap": 0.5, "min_tracks": 3,
+         "min_clusters": 20, "bz_kg": 5.0}
     p.update(kw)
     return p
 
@@ -73,12 +74,13 @@ def dca_path(x, y, s, q, K):
 
 
 def track_times(x, par, p: dict):
-    """Step 1: t_est and |dca| of tracks with state par (n x 5) at radii x."""
+    """Step 1: t_est, |dca| and the z_t change of the extrapolation of
+    tracks with state par (n x 5) at radii x."""
     K = 0.299792458e-3 * p["bz_kg"]
     with np.errstate(invalid="ignore", divide="ignore"):
         path, dist = dca_path(x, par[:, 0], par[:, 2], par[:, 4], K)
-        zt = par[:, 1] + par[:, 3] * path
-    return (zt - p["zmax"]) / p["vdrift"], dist
+        dzt = par[:, 3] * path
+    return ((par[:, 1] - p["zmax"]) + dzt) / p["vdrift"], dist, dzt
 
 
 def find_vertices(x, par, n_clusters, sector, request, p: dict | None = None) -> dict:
@@ -90,9 +92,10 @@ def find_vertices(x, par, n_clusters, sector, request, p: dict | None = None) ->
     p = default_params(**(p or {}))
     par = np.asarray(par, dtype=np.float64)
     m = len(par)
-    t_est, dca = track_times(np.asarray(x, dtype=np.float64), par, p)
+    t_est, dca, dzt = track_times(np.asarray(x, dtype=np.float64), par, p)
     with np.errstate(invalid="ignore"):
         use = (dca <= p["dca_max"]) & (np.asarray(n_clusters) >= p["min_clusters"]) & np.isfinite(t_est)
+        use &= np.abs(dzt) <= p["ext_max"]
     vid = np.full(m, -1, np.int64)
     v_req, v_time, v_n, v_margin = [], [], [], []
     request = np.asarray(request)
@@ -121,7 +124,9 @@ def find_vertices(x, par, n_clusters, sector, request, p: dict | None = None) ->
     tgl = -side * par[:, 3]
     z = np.where(vid >= 0, z, np.nan)
     tgl = np.where(vid >= 0, tgl, np.nan)
-    return {"t_est": t_est, "dca": dca, "use": use, "vertex": vid, "z": z, "tgl": tgl,
+    with np.errstate(invalid="ignore"):
+        use_margin = np.minimum(np.abs(dca - p["dca_max"]), np.abs(np.abs(dzt) - p["ext_max"]))
+    return {"t_est": t_est, "dca": dca, "use": use, "use_margin": use_margin, "vertex": vid, "z": z, "tgl": tgl,
             "v_request": np.asarray(v_req, np.int64), "v_time": v_time, "v_n": np.asarray(v_n, np.int64),
             "v_margin": np.asarray(v_margin, np.float64)}
 

@@ -56,6 +56,15 @@ class TpcTuning(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class VertexConfig(ctypes.Structure):
+    _fields_ = [("vdrift_cm_us", ctypes.c_double), ("zmax_cm", ctypes.c_double), ("dca_max_cm", ctypes.c_double),
+                ("ext_max_cm", ctypes.c_double), ("gap_us", ctypes.c_double), ("min_tracks", ctypes.c_int32),
+                ("min_clusters", ctypes.c_int32)]
+
+
+VERTEX_DTYPE = np.dtype([("time_us", "<f8"), ("n_tracks", "<i4"), ("request", "<i4")])
+
+
 class TpcConfig(ctypes.Structure):
     _fields_ = [("bz_kg", ctypes.c_double), ("sigma", ctypes.c_double), ("d_max", ctypes.c_float),
                 ("min_chain", ctypes.c_int32), ("max_miss", ctypes.c_int32), ("n_min_track", ctypes.c_int32),
@@ -102,6 +111,9 @@ def load_library(path: str | None = None):
         "tpc_get_kalman_profile": ([_VP, _VP, _VP], ctypes.c_int),
         "tpc_graph_kernels": ([_VP, _VP], ctypes.c_int),
         "tpc_measure_alu_peaks": ([ctypes.c_int, _VP, _VP], ctypes.c_int),
+        "tpc_default_vertex_config": ([_VP], ctypes.c_int),
+        "tpc_find_vertices": ([_VP, _VP], ctypes.c_int),
+        "tpc_get_vertices": ([_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "tpc_row_params_noalloc": ([_VP, _I64, _VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_autotune": ([_VP, _I32, _VP, _VP], ctypes.c_int),
         "tpc_set_trace": ([_VP, _I32], ctypes.c_int),
@@ -329,6 +341,34 @@ class Tracker:
                 d["ms"] = float(ms[k])
             out[name] = d
         return out
+
+    def find_vertices(self, **cfg):
+        """Vertex finding in the drift-time coordinate on the fitted tracks
+        of the loaded timeframe (tpc_find_vertices; keyword arguments
+        override tpc_vertex_config fields)."""
+        c = VertexConfig()
+        self._lib.tpc_default_vertex_config(ctypes.byref(c))
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise TypeError(f"unknown vertex option {k}")
+            setattr(c, k, v)
+        self._ck(self._lib.tpc_find_vertices(self._ctx, ctypes.byref(c)))
+        return self
+
+    def vertices(self) -> dict:
+        """Vertices (VERTEX_DTYPE, in time order) and per track: vertex index
+        (-1: none), time estimate (us), spatial z (cm) and dz/ds_T."""
+        nv = ctypes.c_int64()
+        self._ck(self._lib.tpc_get_vertices(self._ctx, None, 0, ctypes.byref(nv), None, None, None, None))
+        m = self.counts()["n_tracks"]
+        out = np.zeros(nv.value, VERTEX_DTYPE)
+        tv = np.zeros(m, np.int32)
+        tt, tz, tg = (np.zeros(m, np.float32) for _ in range(3))
+        self._ck(self._lib.tpc_get_vertices(self._ctx, out.ctypes.data if nv.value else None, nv.value,
+                                            ctypes.byref(nv), tv.ctypes.data if m else None,
+                                            tt.ctypes.data if m else None, tz.ctypes.data if m else None,
+                                            tg.ctypes.data if m else None))
+        return {"vertices": out, "track_vertex": tv, "track_time": tt, "track_z": tz, "track_tgl": tg}
 
     def graph_kernels(self) -> int:
         n = ctypes.c_int32()

@@ -19,6 +19,7 @@
 #include "follow.cuh"
 #include "select.cuh"
 #include "probe.cuh"
+#include "vertex.cuh"
 
 using namespace tpc;
 
@@ -201,6 +202,14 @@ struct tpc_ctx {
   int graph_chunks = 0;  // chunks and refilling-kernel CTAs per SM of the captured graph
   int graph_ctas = 0;
   cudaStream_t aux = nullptr;       // second stream of the chunked Kalman stage
+  // vertex finding (tpc_find_vertices): its own buffer, allocated on first use
+  void* vtx_mem = nullptr;
+  int64_t vtx_tracks_cap = 0;
+  VtxBuf vb{};
+  double* vtx_time = nullptr;
+  int32_t* vtx_ntr = nullptr;
+  int32_t* h_vtx_n = nullptr;  // pinned mirror of vb.n
+  bool vtx_valid = false;
   cudaEvent_t ev_chunk[4] = {};     // fork and join of the chunked follow and refit
   // graph
   cudaGraphExec_t graph = nullptr;
@@ -392,7 +401,9 @@ int create_common(tpc_ctx** out, const tpc_config* cfg, int device, void* stream
   if (!ok || cudaMallocHost(&ctx->h_counts, sizeof(Counts)) != cudaSuccess) {
     for (int i = 0; i < 4; i++)
       if (ctx->ev_chunk[i]) cudaEventDestroy(ctx->ev_chunk[i]);
-    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
+  if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return TPC_ECUDA;
@@ -737,6 +748,8 @@ void tpc_destroy(tpc_ctx* ctx) {
   }
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_req) cudaFreeHost(ctx->h_req);
+  if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
+  if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
   for (int i = 0; i < 4; i++)
     if (ctx->ev_chunk[i]) cudaEventDestroy(ctx->ev_chunk[i]);
@@ -1167,6 +1180,151 @@ int tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* t) {
   if (t->refill > 32) return fail(ctx, TPC_EINVAL, "refill must be in [1, 32]");
   if (t->chunks > MAX_CHUNKS) return fail(ctx, TPC_EINVAL, "chunks must be 1 or 2");
   apply_tuning(ctx, t);
+  return TPC_OK;
+}
+
+int tpc_default_vertex_config(tpc_vertex_config* c) {
+  if (!c) return TPC_EINVAL;
+  c->vdrift_cm_us = 2.5;
+  c->zmax_cm = 250.0;
+  c->dca_max_cm = 2.0;
+  c->ext_max_cm = 300.0;
+  c->gap_us = 0.5;
+  c->min_tracks = 3;
+  c->min_clusters = 20;
+  return TPC_OK;
+}
+
+namespace {
+constexpr int32_t kVtxBins = 1 << 18;  // 65 ms of time range at 0.25 us bins
+
+int vtx_reserve(tpc_ctx* ctx) {
+  const int64_t M = std::max<int64_t>(ctx->caps.tracks, 1);
+  if (ctx->vtx_mem && ctx->vtx_tracks_cap >= M) return TPC_OK;
+  if (ctx->vtx_mem) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->vtx_mem);
+    ctx->vtx_mem = nullptr;
+  }
+  const size_t B = kVtxBins;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t o_t = take(4 * M), o_use = take(M), o_vx = take(4 * M), o_z = take(4 * M), o_tgl = take(4 * M);
+  const size_t o_bc = take(4 * B), o_bmin = take(4 * B), o_bmax = take(4 * B), o_bvid = take(4 * B);
+  const size_t o_vc = take(4 * B), o_vs = take(8 * B), o_vk = take(4 * (B + 1)), o_vi = take(4 * (B + 1));
+  const size_t o_rng = take(8), o_n = take(16), o_time = take(8 * B), o_ntr = take(4 * B);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, off) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, TPC_ENOMEM, "vertex buffers of %zu bytes", off);
+  }
+  char* b = (char*)mem;
+  ctx->vtx_mem = mem;
+  ctx->vtx_tracks_cap = M;
+  VtxBuf& v = ctx->vb;
+  v.t = (float*)(b + o_t);
+  v.use = (uint8_t*)(b + o_use);
+  v.vertex = (int32_t*)(b + o_vx);
+  v.z = (float*)(b + o_z);
+  v.tgl = (float*)(b + o_tgl);
+  v.b_cnt = (int32_t*)(b + o_bc);
+  v.b_min = (uint32_t*)(b + o_bmin);
+  v.b_max = (uint32_t*)(b + o_bmax);
+  v.b_vid = (int32_t*)(b + o_bvid);
+  v.v_cnt = (int32_t*)(b + o_vc);
+  v.v_sum = (unsigned long long*)(b + o_vs);
+  v.v_keep = (int32_t*)(b + o_vk);
+  v.v_idx = (int32_t*)(b + o_vi);
+  v.range = (uint32_t*)(b + o_rng);
+  v.n = (int32_t*)(b + o_n);
+  ctx->vtx_time = (double*)(b + o_time);
+  ctx->vtx_ntr = (int32_t*)(b + o_ntr);
+  if (!ctx->h_vtx_n && cudaMallocHost(&ctx->h_vtx_n, 16) != cudaSuccess) return fail(ctx, TPC_ECUDA, "pinned buffer");
+  return TPC_OK;
+}
+}  // namespace
+
+int tpc_find_vertices(tpc_ctx* ctx, const tpc_vertex_config* cfg_in) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->fitted) return fail(ctx, TPC_EINVAL, "tpc_fit_tracks has not run");
+  if (ctx->n_req != 1) return fail(ctx, TPC_EINVAL, "vertex finding takes one request (one timeframe) per call");
+  tpc_vertex_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else tpc_default_vertex_config(&cfg);
+  if (!(cfg.vdrift_cm_us > 0) || !(cfg.gap_us > 0) || cfg.min_tracks < 1 || !(cfg.dca_max_cm >= 0) ||
+      !(cfg.ext_max_cm >= 0))
+    return fail(ctx, TPC_EINVAL, "bad vertex configuration");
+  CK(cudaSetDevice(ctx->device));
+  int rc = vtx_reserve(ctx);
+  if (rc) return rc;
+  VtxConst vc;
+  vc.K = (float)(0.299792458e-3 * ctx->cfg.bz_kg);
+  vc.vdrift = (float)cfg.vdrift_cm_us;
+  vc.zmax = (float)cfg.zmax_cm;
+  vc.dca_max = (float)cfg.dca_max_cm;
+  vc.ext_max = (float)cfg.ext_max_cm;
+  vc.gap = (float)cfg.gap_us;
+  vc.inv_w = (float)(2.0 / cfg.gap_us);
+  vc.min_tracks = cfg.min_tracks;
+  vc.min_clusters = cfg.min_clusters;
+  vc.bins_cap = kVtxBins;
+  const VtxBuf& vb = ctx->vb;
+  cudaStream_t s = ctx->stream;
+  Counts* cn = ctx->ptr<Counts>(ctx->L.counts);
+  const tpc_track* tr = ctx->ptr<tpc_track>(ctx->L.tracks);
+  const int bc = ctx->block_clusters;
+  const int gM = grid_for(ctx, ctx->caps.tracks, bc), gB = grid_for(ctx, kVtxBins, bc);
+  const uint32_t init[2] = {0xFFFFFFFFu, 0u};
+  CK(cudaMemcpyAsync(vb.range, init, sizeof(init), cudaMemcpyHostToDevice, s));
+  CK(cudaMemsetAsync(vb.n, 0, 16, s));
+  k_vtx_time<<<gM, bc, 0, s>>>(tr, vc, vb, cn);
+  k_vtx_clear<<<gB, bc, 0, s>>>(vc, vb);
+  k_vtx_bin<<<gM, bc, 0, s>>>(vc, vb, cn);
+  k_vtx_runs<<<1, VTX_RUN_THREADS, 0, s>>>(vc, vb);
+  k_vtx_accum<<<gM, bc, 0, s>>>(vc, vb, cn);
+  k_vtx_keep<<<gB, bc, 0, s>>>(vc, vb);
+  scan(ctx, vb.v_keep, vb.v_idx, LenSrc{vb.n + 1, 0, 0}, nullptr);
+  k_vtx_tracks<<<gM, bc, 0, s>>>(tr, vc, vb, cn);
+  k_vtx_records<<<gB, bc, 0, s>>>(vc, vb, ctx->vtx_time, ctx->vtx_ntr);
+  CK(cudaMemcpyAsync(ctx->h_vtx_n, vb.n, 16, cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
+  ctx->vtx_valid = true;
+  return TPC_OK;
+}
+
+int tpc_get_vertices(tpc_ctx* ctx, tpc_vertex* out, int64_t cap, int64_t* n_out, int32_t* track_vertex,
+                     float* track_time, float* track_z, float* track_tgl) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->vtx_valid) return fail(ctx, TPC_EINVAL, "tpc_find_vertices has not run");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_status(ctx);
+  if (rc) return rc;
+  if (ctx->h_vtx_n[3]) return fail(ctx, TPC_EOVERFLOW, "the tracks' time range needs %d bins, %d reserved",
+                                   ctx->h_vtx_n[0], kVtxBins);
+  const int32_t nv = ctx->h_vtx_n[2];
+  if (n_out) *n_out = nv;
+  if (nv > cap && out) return fail(ctx, TPC_EOVERFLOW, "%d vertices do not fit cap %lld", nv, (long long)cap);
+  const int32_t M = ctx->h_counts->n_tracks;
+  if (out && nv) {
+    std::vector<double> t(nv);
+    std::vector<int32_t> k(nv);
+    CK(cudaMemcpy(t.data(), ctx->vtx_time, sizeof(double) * nv, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(k.data(), ctx->vtx_ntr, sizeof(int32_t) * nv, cudaMemcpyDeviceToHost));
+    for (int32_t i = 0; i < nv; i++) {
+      out[i].time_us = t[i];
+      out[i].n_tracks = k[i];
+      out[i].request = 0;
+    }
+  }
+  if (track_vertex && M) CK(cudaMemcpy(track_vertex, ctx->vb.vertex, 4 * (size_t)M, cudaMemcpyDeviceToHost));
+  if (track_time && M) CK(cudaMemcpy(track_time, ctx->vb.t, 4 * (size_t)M, cudaMemcpyDeviceToHost));
+  if (track_z && M) CK(cudaMemcpy(track_z, ctx->vb.z, 4 * (size_t)M, cudaMemcpyDeviceToHost));
+  if (track_tgl && M) CK(cudaMemcpy(track_tgl, ctx->vb.tgl, 4 * (size_t)M, cudaMemcpyDeviceToHost));
   return TPC_OK;
 }
 
