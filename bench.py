@@ -254,8 +254,27 @@ def all_configs(local):
             e1.record(stream)
             e1.synchronize()
             dt.append(e0.elapsed_time(e1))
-        host = torch.from_numpy(cl.view(np.uint8)).pin_memory().numpy().view(synth.CLUSTER_DTYPE)
         counts = trk.counts()
+        vtx = None
+        if subset is not None:  # a timeframe: vertex finding in the drift time on its tracks
+            trk.find_vertices().vertices()
+            vt = []
+            for _ in range(5):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                trk.find_vertices()
+                e1.record(stream)
+                e1.synchronize()
+                vt.append(e0.elapsed_time(e1))
+            vres = trk.vertices()
+            vms = statistics.median(vt)
+            # algorithmic bytes per track: the 128-byte track read twice (time
+            # estimate, conversion) and 24 B of per-track outputs and scratch
+            vtx = {"ms": vms, "vertices": int(len(vres["vertices"])),
+                   "tracks_with_vertex": int((vres["track_vertex"] >= 0).sum()),
+                   "tracks_per_s": counts["n_tracks"] / (vms / 1e3),
+                   "hbm_gbs": counts["n_tracks"] * (2 * 128 + 24) / (vms / 1e3) / 1e9}
+        host = torch.from_numpy(cl.view(np.uint8)).pin_memory().numpy().view(synth.CLUSTER_DTYPE)
         tr_buf = torch.zeros(counts["n_tracks"] + 1024, 128, dtype=torch.uint8).pin_memory()
         ct_buf = torch.zeros(n, dtype=torch.int32).pin_memory()
         lat = []
@@ -284,6 +303,8 @@ def all_configs(local):
                       "oracle_all_cores_sample": "all sectors" if subset is None else f"sectors {subset}",
                       "oracle_one_core_clusters_per_s": len(one) / t_one,
                       "oracle_one_core_sample": f"{len(one)} clusters"}
+        if vtx is not None:
+            rows[name]["vertex_finding"] = vtx
     print(json.dumps({"all_configs": rows}))
 
 
