@@ -68,6 +68,11 @@ def _load():
     global _lib
     if _lib is None:
         lib = ctypes.CDLL(build())
+        lib.orc_codec.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int32] + [ctypes.c_void_p] * 9 + \
+            [ctypes.c_double, ctypes.c_void_p]
+        lib.orc_codec.restype = ctypes.c_int
+        lib.orc_quantise.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p]
+        lib.orc_quantise.restype = None
         lib.orc_default_config.argtypes = [ctypes.POINTER(Config)]
         lib.orc_run.argtypes = [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                 ctypes.c_int32, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_Result)]
@@ -164,6 +169,70 @@ def run(clusters: np.ndarray, req_offsets=None, stop_after: str = "refit", brute
         return out
     finally:
         lib.orc_free(ctypes.byref(res))
+
+
+def quantise(v, unit: float) -> np.ndarray:
+    """Fixed-point coordinate rint(v * (1/unit)) in binary32 (the lossy
+    format conversion ahead of the track-model compression)."""
+    lib = _load()
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float32))
+    q = np.zeros(len(v), np.int32)
+    if len(v):
+        lib.orc_quantise(len(v), v.ctypes.data, unit, q.ctypes.data)
+    return q
+
+
+def codec_input(ref: dict, clusters: np.ndarray, unit: float = 0.01, cfg: Config | None = None) -> dict:
+    """The oracle's compression input: per track the header -- the follow
+    state carried to the outermost owned row, as the refit starts -- and its
+    owned clusters outermost first (rows, fixed-point y and z)."""
+    m = ref["n_tracks"]
+    ct = ref["cluster_track"].astype(np.int64)
+    idx = np.nonzero(ct >= 0)[0]
+    rows_all = clusters["row"].astype(np.int64)
+    idx = idx[np.lexsort((-rows_all[idx], ct[idx]))]  # by track, outermost first
+    off = np.zeros(m + 1, np.int64)
+    np.add.at(off, ct[idx] + 1, 1)
+    off = np.cumsum(off)
+    head = np.zeros((m, 5), np.float64)
+    ok = np.ones(m, np.int32)
+    for tr in range(m):
+        t = ref["t_tracklet"][tr]
+        fr, ro = int(ref["f_row"][t]), int(ref["t_row_out"][tr])
+        step = 1 if ro >= fr else -1
+        path = np.arange(fr, ro + step, step, dtype=np.int32)
+        try:
+            head[tr] = propagate_rows(path, ref["f_par"][t], cfg)[-1]
+        except ValueError:
+            ok[tr] = 0
+    return {"row_out": ref["t_row_out"].astype(np.int32), "head": head, "ok": ok, "off": off,
+            "cluster": idx, "rows": rows_all[idx].astype(np.int32),
+            "qy": quantise(clusters["y"][idx], unit), "qz": quantise(clusters["z"][idx], unit), "unit": unit}
+
+
+def codec(inp: dict, decode: bool = False, ry=None, rz=None, cfg: Config | None = None) -> dict:
+    """Track-model compression (decode=False: residuals from the clusters) or
+    decompression (decode=True: clusters from the residuals) of codec_input
+    tracks.  Also returns, per cluster, the distance of the prediction (in
+    units) from the rounding boundary, and per track whether it ran."""
+    lib = _load()
+    m = len(inp["row_out"])
+    n = int(inp["off"][-1])
+    qy = inp["qy"].copy() if not decode else np.zeros(n, np.int32)
+    qz = inp["qz"].copy() if not decode else np.zeros(n, np.int32)
+    ry = np.zeros(n, np.int32) if not decode else np.ascontiguousarray(ry, dtype=np.int32)
+    rz = np.zeros(n, np.int32) if not decode else np.ascontiguousarray(rz, dtype=np.int32)
+    margin = np.zeros(n, np.float64)
+    ok = np.zeros(m, np.int32)
+    row_out = np.ascontiguousarray(inp["row_out"], dtype=np.int32)
+    head = np.ascontiguousarray(inp["head"], dtype=np.float64)
+    off = np.ascontiguousarray(inp["off"], dtype=np.int64)
+    rows = np.ascontiguousarray(inp["rows"], dtype=np.int32)
+    lib.orc_codec(ctypes.byref(cfg) if cfg is not None else None, int(decode), m, row_out.ctypes.data,
+                  head.ctypes.data, off.ctypes.data, rows.ctypes.data, qy.ctypes.data, qz.ctypes.data,
+                  ry.ctypes.data, rz.ctypes.data, margin.ctypes.data, inp["unit"], ok.ctypes.data)
+    ok &= inp["ok"]
+    return {"qy": qy, "qz": qz, "ry": ry, "rz": rz, "margin": margin, "ok": ok}
 
 
 def kalman_fit(rows, my, mz, p0, cfg: Config | None = None):

@@ -882,6 +882,74 @@ int orc_propagate_rows(const orc_config *cfg_in, int m, const int32_t *rows, con
   return 1;
 }
 
+/* ================================== track-model compression (next row) */
+/* The track-model compression of the paper's compression section: the
+   track is refitted over its own clusters, and at each cluster the residual
+   between the cluster and the extrapolated track position is stored; the
+   decompression repeats the same fit and adds the residuals back, which is
+   exact because both sides see the same (quantised) clusters.  The
+   distortion transform of the paper is the identity here (the synthetic
+   clusters carry no distortion).  Cluster coordinates are fixed point:
+   q = rint(v * (1/unit)) in binary32 (the lossy format conversion); the
+   stored residual is q - rint(prediction / unit), and the fit is updated
+   with the decoded value q * unit (binary32).
+   Per track: a header (row_out, the state at the outermost cluster) and
+   its clusters outermost first (rows, fixed-point y and z).  decode = 0:
+   qy/qz in, ry/rz out; decode = 1: ry/rz in, qy/qz out.  margin (out,
+   optional): distance of prediction / unit from the rounding boundary,
+   per cluster.  Returns 1, or 0 if a propagation fails (that track's
+   clusters are left as they are). */
+static int codec_one(const kctx *k, int decode, int32_t row_out, const double *head, int64_t n,
+                     const int32_t *rows, int32_t *qy, int32_t *qz, int32_t *ry, int32_t *rz, double *margin,
+                     double unit) {
+  kstate s;
+  int flags = 0;
+  s.x = X32[row_out];
+  memcpy(s.p, head, 5 * sizeof(double));
+  reset_cov(k, &s);
+  int row = row_out;
+  const float u32 = (float)unit;
+  for (int64_t i = 0; i < n; i++) {
+    while (row > rows[i]) {
+      row--;
+      if (!propagate(k, &s, X32[row], &flags)) return 0;
+    }
+    const double fy = s.p[0] / unit, fz = s.p[1] / unit;
+    const double py = rint(fy), pz = rint(fz);
+    if (margin) margin[i] = fmin(fabs(fabs(fy - floor(fy)) - 0.5), fabs(fabs(fz - floor(fz)) - 0.5));
+    if (decode) {
+      qy[i] = (int32_t)py + ry[i];
+      qz[i] = (int32_t)pz + rz[i];
+    } else {
+      ry[i] = qy[i] - (int32_t)py;
+      rz[i] = qz[i] - (int32_t)pz;
+    }
+    update(k, &s, (double)((float)qy[i] * u32), (double)((float)qz[i] * u32));
+  }
+  return 1;
+}
+
+int orc_codec(const orc_config *cfg_in, int decode, int32_t n_tracks, const int32_t *row_out, const double *head,
+              const int64_t *off, const int32_t *rows, int32_t *qy, int32_t *qz, int32_t *ry, int32_t *rz,
+              double *margin, double unit, int32_t *ok) {
+  orc_config cfg;
+  if (cfg_in) cfg = *cfg_in; else orc_default_config(&cfg);
+  init_tables();
+  kctx k = {&cfg, 0.299792458e-3 * cfg.bz_kg, cfg.sigma * cfg.sigma};
+  for (int32_t t = 0; t < n_tracks; t++) {
+    const int64_t a = off[t], n = off[t + 1] - off[t];
+    ok[t] = codec_one(&k, decode, row_out[t], head + 5 * (int64_t)t, n, rows + a, qy + a, qz + a, ry + a, rz + a,
+                      margin ? margin + a : NULL, unit);
+  }
+  return 0;
+}
+
+/* Fixed-point cluster coordinate: rint(v * (1/unit)) in binary32. */
+void orc_quantise(int64_t n, const float *v, double unit, int32_t *q) {
+  const float inv = (float)(1.0 / unit);
+  for (int64_t i = 0; i < n; i++) q[i] = (int32_t)rintf(v[i] * inv);
+}
+
 /* Row radii and half-widths as the oracle uses them (binary32). */
 void orc_tables(float *x, float *yhi) {
   init_tables();
