@@ -215,6 +215,16 @@ def cpu_baseline(cl):
                                                  "1 thread"}}
 
 
+def _entropy(v):
+    """Shannon entropy (bits per symbol) of an integer sample."""
+    import numpy as np
+    if len(v) == 0:
+        return 0.0
+    _, c = np.unique(v, return_counts=True)
+    p = c / c.sum()
+    return float(-(p * np.log2(p)).sum())
+
+
 def all_configs(local):
     """Per-config table (one sector, central event, 10 ms timeframe): GPU
     device throughput (graph, inputs resident, L2 flushed), per-call latency
@@ -274,6 +284,36 @@ def all_configs(local):
                    "tracks_with_vertex": int((vres["track_vertex"] >= 0).sum()),
                    "tracks_per_s": counts["n_tracks"] / (vms / 1e3),
                    "hbm_gbs": counts["n_tracks"] * (2 * 128 + 24) / (vms / 1e3) / 1e9}
+        codec = None
+        if n > 100_000:  # track-model compression of the event / timeframe
+            trk.compress(0.01)
+            ct_ms = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                trk._ck(trk._lib.tpc_compress(trk._ctx, 0.01))
+                e1.record(stream)
+                e1.synchronize()
+                ct_ms.append(e0.elapsed_time(e1))
+            c = trk.compress(0.01)
+            t0 = time.perf_counter()
+            qy, qz = trk.decompress(c["heads"], c["rows"], c["res_y"], c["res_z"], 0.01)
+            dec_s = time.perf_counter() - t0
+            ok = np.repeat(c["heads"]["ok"].astype(bool), c["heads"]["n_clusters"])
+            first = np.zeros(len(ok), bool)
+            first[np.concatenate([[0], np.cumsum(c["heads"]["n_clusters"])[:-1]])[c["heads"]["n_clusters"] > 0]] = True
+            steps = (c["rows"][:-1].astype(np.int64) - c["rows"][1:])[~first[1:]]
+            coded = _entropy(c["res_y"][ok]) + _entropy(c["res_z"][ok]) + _entropy(steps)
+            fixed = _entropy(c["q_y"][ok]) + _entropy(c["q_z"][ok])
+            head_bits = 32 * 5 + 8 + 8  # state, first row, cluster count per track
+            n_ok = int(ok.sum())
+            codec = {"encode_ms": statistics.median(ct_ms), "decode_api_ms": 1e3 * dec_s,
+                     "round_trip_exact": bool(np.array_equal(qy, c["q_y"]) and np.array_equal(qz, c["q_z"])),
+                     "track_clusters": int(len(ok)), "coded_clusters": n_ok,
+                     "bits_per_cluster_coded": coded + head_bits * int(c["heads"]["ok"].sum()) / max(n_ok, 1),
+                     "bits_per_cluster_fixed_point": fixed,
+                     "unit_cm": 0.01}
+            codec["factor"] = codec["bits_per_cluster_fixed_point"] / codec["bits_per_cluster_coded"]
         host = torch.from_numpy(cl.view(np.uint8)).pin_memory().numpy().view(synth.CLUSTER_DTYPE)
         tr_buf = torch.zeros(counts["n_tracks"] + 1024, 128, dtype=torch.uint8).pin_memory()
         ct_buf = torch.zeros(n, dtype=torch.int32).pin_memory()
@@ -305,6 +345,8 @@ def all_configs(local):
                       "oracle_one_core_sample": f"{len(one)} clusters"}
         if vtx is not None:
             rows[name]["vertex_finding"] = vtx
+        if codec is not None:
+            rows[name]["track_model_compression"] = codec
     print(json.dumps({"all_configs": rows}))
 
 

@@ -356,6 +356,46 @@ int tpc_find_vertices(tpc_ctx *ctx, const tpc_vertex_config *cfg);
 int tpc_get_vertices(tpc_ctx *ctx, tpc_vertex *out, int64_t cap, int64_t *n_out, int32_t *track_vertex,
                      float *track_time, float *track_z, float *track_tgl);
 
+/* ------------------------------------------------ track-model compression */
+/* The compression section's track-model coding: each selected track is
+ * refitted over its own clusters, outermost first; at each cluster the
+ * residual between the fixed-point cluster (rint(v / unit), binary32) and
+ * the rounded extrapolated track position is stored, and the fit is updated
+ * with the fixed-point value; decompression repeats the same fit from the
+ * same header and adds the residuals back, which restores every fixed-point
+ * cluster exactly.  The paper's distortion transform is the identity here.
+ * A track whose fit stops at the |sin phi| limit (ok = 0) carries its
+ * fixed-point clusters in the residual streams instead. */
+typedef struct {
+  float par[5];        /* y, z, sin phi, dz/ds_T, q/pT where the fit starts (the outermost cluster's row) */
+  int32_t row_out;     /* that row */
+  int32_t n_clusters;  /* the track's clusters */
+  int32_t ok;          /* 1: residuals; 0: fixed-point clusters */
+} tpc_codec_header;
+
+/* Encode the fitted tracks of the loaded batch (after tpc_fit_tracks).
+ * Asynchronous; results with tpc_get_compressed. */
+int tpc_compress(tpc_ctx *ctx, double unit_cm);
+
+/* Waits and copies: per track its header (tpc_get_tracks order); per cluster
+ * (tracks in that order, each outermost first) its row, residuals and --
+ * optional -- the fixed-point coordinates that were encoded.  Any pointer
+ * may be NULL; *n_tracks and *n_clusters receive the sizes (TPC_EOVERFLOW
+ * without copying when a capacity is too small). */
+int tpc_get_compressed(tpc_ctx *ctx, tpc_codec_header *heads, int64_t cap_tracks, uint8_t *rows, int32_t *res_y,
+                       int32_t *res_z, int32_t *q_y, int32_t *q_z, int64_t cap_clusters, int64_t *n_tracks,
+                       int64_t *n_clusters);
+
+/* Decode n_tracks tracks (host headers and streams, the layout of
+ * tpc_get_compressed) into fixed-point clusters q_y, q_z (host, n_clusters
+ * each), on the context's device with its configuration (the field and the
+ * FP64-zone length must be the encoder's).  Synchronous.  TPC_EINVAL when
+ * the headers' counts do not add up to n_clusters or a track's rows do not
+ * lie at or below its row_out. */
+int tpc_decompress(tpc_ctx *ctx, const tpc_codec_header *heads, int64_t n_tracks, const uint8_t *rows,
+                   const int32_t *res_y, const int32_t *res_z, int64_t n_clusters, double unit_cm, int32_t *q_y,
+                   int32_t *q_z);
+
 /* ------------------------------------------------------ serving (requests) */
 /* Continuous-batching request loop: the serving form of tracking several
  * events or continuous-readout timeframes (Sec. 2, Sec. 5) as they arrive.

@@ -62,6 +62,9 @@ class VertexConfig(ctypes.Structure):
                 ("min_clusters", ctypes.c_int32)]
 
 
+CODEC_HEADER_DTYPE = np.dtype([("par", "<f4", (5,)), ("row_out", "<i4"), ("n_clusters", "<i4"), ("ok", "<i4")])
+assert CODEC_HEADER_DTYPE.itemsize == 32
+
 VERTEX_DTYPE = np.dtype([("time_us", "<f8"), ("n_tracks", "<i4"), ("request", "<i4")])
 
 
@@ -112,6 +115,9 @@ def load_library(path: str | None = None):
         "tpc_graph_kernels": ([_VP, _VP], ctypes.c_int),
         "tpc_measure_alu_peaks": ([ctypes.c_int, _VP, _VP], ctypes.c_int),
         "tpc_default_vertex_config": ([_VP], ctypes.c_int),
+        "tpc_compress": ([_VP, ctypes.c_double], ctypes.c_int),
+        "tpc_get_compressed": ([_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP], ctypes.c_int),
+        "tpc_decompress": ([_VP, _VP, _I64, _VP, _VP, _VP, _I64, ctypes.c_double, _VP, _VP], ctypes.c_int),
         "tpc_find_vertices": ([_VP, _VP], ctypes.c_int),
         "tpc_get_vertices": ([_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "tpc_row_params_noalloc": ([_VP, _I64, _VP, _I32, _VP, _VP], ctypes.c_int),
@@ -369,6 +375,35 @@ class Tracker:
                                             tt.ctypes.data if m else None, tz.ctypes.data if m else None,
                                             tg.ctypes.data if m else None))
         return {"vertices": out, "track_vertex": tv, "track_time": tt, "track_z": tz, "track_tgl": tg}
+
+    def compress(self, unit_cm: float = 0.01) -> dict:
+        """Track-model compression of the fitted tracks (tpc_compress):
+        headers (CODEC_HEADER_DTYPE), per cluster rows, residuals and the
+        encoded fixed-point coordinates."""
+        self._ck(self._lib.tpc_compress(self._ctx, unit_cm))
+        m, n = ctypes.c_int64(), ctypes.c_int64()
+        self._ck(self._lib.tpc_get_compressed(self._ctx, None, 0, None, None, None, None, None, 0,
+                                              ctypes.byref(m), ctypes.byref(n)))
+        heads = np.zeros(m.value, CODEC_HEADER_DTYPE)
+        rows = np.zeros(n.value, np.uint8)
+        ry, rz, qy, qz = (np.zeros(n.value, np.int32) for _ in range(4))
+        p = lambda a: a.ctypes.data if len(a) else None  # noqa: E731
+        self._ck(self._lib.tpc_get_compressed(self._ctx, p(heads), m.value, p(rows), p(ry), p(rz), p(qy), p(qz),
+                                              n.value, ctypes.byref(m), ctypes.byref(n)))
+        return {"heads": heads, "rows": rows, "res_y": ry, "res_z": rz, "q_y": qy, "q_z": qz, "unit": unit_cm}
+
+    def decompress(self, heads, rows, res_y, res_z, unit_cm: float = 0.01):
+        """Fixed-point clusters (q_y, q_z) restored from a compressed stream."""
+        heads = np.ascontiguousarray(heads, dtype=CODEC_HEADER_DTYPE)
+        rows = np.ascontiguousarray(rows, dtype=np.uint8)
+        ry = np.ascontiguousarray(res_y, dtype=np.int32)
+        rz = np.ascontiguousarray(res_z, dtype=np.int32)
+        n = len(rows)
+        qy, qz = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        p = lambda a: a.ctypes.data if len(a) else None  # noqa: E731
+        self._ck(self._lib.tpc_decompress(self._ctx, p(heads), len(heads), p(rows), p(ry), p(rz), n, unit_cm,
+                                          p(qy), p(qz)))
+        return qy, qz
 
     def graph_kernels(self) -> int:
         n = ctypes.c_int32()

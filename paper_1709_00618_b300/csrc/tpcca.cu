@@ -20,6 +20,7 @@
 #include "select.cuh"
 #include "probe.cuh"
 #include "vertex.cuh"
+#include "codec.cuh"
 
 using namespace tpc;
 
@@ -210,6 +211,12 @@ struct tpc_ctx {
   int32_t* vtx_ntr = nullptr;
   int32_t* h_vtx_n = nullptr;  // pinned mirror of vb.n
   bool vtx_valid = false;
+  // track-model compression (tpc_compress / tpc_decompress): own buffer
+  void* codec_mem = nullptr;
+  int64_t codec_tracks_cap = 0, codec_clusters_cap = 0;
+  CodecIo cio{};
+  int32_t* codec_bad = nullptr;
+  bool codec_valid = false;
   cudaEvent_t ev_chunk[4] = {};     // fork and join of the chunked follow and refit
   // graph
   cudaGraphExec_t graph = nullptr;
@@ -402,6 +409,7 @@ int create_common(tpc_ctx** out, const tpc_config* cfg, int device, void* stream
     for (int i = 0; i < 4; i++)
       if (ctx->ev_chunk[i]) cudaEventDestroy(ctx->ev_chunk[i]);
     if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
+  if (ctx->codec_mem) cudaFree(ctx->codec_mem);
   if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -561,6 +569,26 @@ void enqueue_find(tpc_ctx* ctx) {
   ctx->mark(5);
 }
 
+RefitIn refit_in(tpc_ctx* ctx) {
+  const Layout& L = ctx->L;
+  RefitIn in;
+  in.track_tl = ctx->ptr<int32_t>(L.track_tl);
+  in.f_n = ctx->ptr<int32_t>(L.f_n);
+  in.f_nf = ctx->ptr<int32_t>(L.f_nf);
+  in.f_row = ctx->ptr<int32_t>(L.f_row);
+  in.hits = ctx->ptr<int32_t>(L.hits);
+  in.hrow = ctx->ptr<uint8_t>(L.hrow);
+  in.f_par = ctx->ptr<float>(L.f_par);
+  in.f_zref = ctx->ptr<float>(L.f_zref);
+  in.f_cov = ctx->ptr<float>(L.f_cov);
+  in.f_chi2 = ctx->ptr<double>(L.f_chi2);
+  in.own_mask = ctx->ptr<uint32_t>(L.own_mask);
+  in.own_rng = ctx->ptr<int32_t>(L.own_rng);
+  in.nown = ctx->ptr<int32_t>(L.nown);
+  in.toff = ctx->ptr<int32_t>(L.toff);
+  return in;
+}
+
 // a8 on the context's stream.
 void enqueue_fit(tpc_ctx* ctx) {
   const Layout& L = ctx->L;
@@ -575,21 +603,7 @@ void enqueue_fit(tpc_ctx* ctx) {
        &cn->n_track_clusters);
   {
     const int bf = ctx->block_follow;
-    RefitIn in;
-    in.track_tl = ctx->ptr<int32_t>(L.track_tl);
-    in.f_n = ctx->ptr<int32_t>(L.f_n);
-    in.f_nf = ctx->ptr<int32_t>(L.f_nf);
-    in.f_row = ctx->ptr<int32_t>(L.f_row);
-    in.hits = ctx->ptr<int32_t>(L.hits);
-    in.hrow = ctx->ptr<uint8_t>(L.hrow);
-    in.f_par = ctx->ptr<float>(L.f_par);
-    in.f_zref = ctx->ptr<float>(L.f_zref);
-    in.f_cov = ctx->ptr<float>(L.f_cov);
-    in.f_chi2 = ctx->ptr<double>(L.f_chi2);
-    in.own_mask = ctx->ptr<uint32_t>(L.own_mask);
-    in.own_rng = ctx->ptr<int32_t>(L.own_rng);
-    in.nown = ctx->ptr<int32_t>(L.nown);
-    in.toff = ctx->ptr<int32_t>(L.toff);
+    RefitIn in = refit_in(ctx);
     RefitWork* RW = ctx->ptr<RefitWork>(L.rwork);
     const int nc = ctx->prof ? 1 : effective_chunks(ctx);
     auto refit_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
@@ -749,6 +763,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_req) cudaFreeHost(ctx->h_req);
   if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
+  if (ctx->codec_mem) cudaFree(ctx->codec_mem);
   if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
   for (int i = 0; i < 4; i++)
@@ -1325,6 +1340,134 @@ int tpc_get_vertices(tpc_ctx* ctx, tpc_vertex* out, int64_t cap, int64_t* n_out,
   if (track_time && M) CK(cudaMemcpy(track_time, ctx->vb.t, 4 * (size_t)M, cudaMemcpyDeviceToHost));
   if (track_z && M) CK(cudaMemcpy(track_z, ctx->vb.z, 4 * (size_t)M, cudaMemcpyDeviceToHost));
   if (track_tgl && M) CK(cudaMemcpy(track_tgl, ctx->vb.tgl, 4 * (size_t)M, cudaMemcpyDeviceToHost));
+  return TPC_OK;
+}
+
+namespace {
+int codec_reserve(tpc_ctx* ctx, int64_t tracks, int64_t clusters) {
+  tracks = std::max<int64_t>(tracks, 1);
+  clusters = std::max<int64_t>(clusters, 1);
+  if (ctx->codec_mem && ctx->codec_tracks_cap >= tracks && ctx->codec_clusters_cap >= clusters) return TPC_OK;
+  tracks = std::max(tracks, ctx->codec_tracks_cap);
+  clusters = std::max(clusters, ctx->codec_clusters_cap);
+  if (ctx->codec_mem) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->codec_mem);
+    ctx->codec_mem = nullptr;
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t o_h = take(sizeof(CodecHeader) * tracks), o_off = take(8 * (tracks + 1)), o_rows = take(clusters);
+  const size_t o_qy = take(4 * clusters), o_qz = take(4 * clusters), o_ry = take(4 * clusters),
+               o_rz = take(4 * clusters), o_bad = take(4);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, off) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, TPC_ENOMEM, "codec buffers of %zu bytes", off);
+  }
+  char* b = (char*)mem;
+  ctx->codec_mem = mem;
+  ctx->codec_tracks_cap = tracks;
+  ctx->codec_clusters_cap = clusters;
+  ctx->cio.head = (CodecHeader*)(b + o_h);
+  ctx->cio.off = (const int64_t*)(b + o_off);
+  ctx->cio.rows = (uint8_t*)(b + o_rows);
+  ctx->cio.qy = (int32_t*)(b + o_qy);
+  ctx->cio.qz = (int32_t*)(b + o_qz);
+  ctx->cio.ry = (int32_t*)(b + o_ry);
+  ctx->cio.rz = (int32_t*)(b + o_rz);
+  ctx->codec_bad = (int32_t*)(b + o_bad);
+  return TPC_OK;
+}
+
+bool codec_unit_ok(double unit) { return unit >= 1e-6 && unit <= 10.0; }
+}  // namespace
+
+int tpc_compress(tpc_ctx* ctx, double unit_cm) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->fitted) return fail(ctx, TPC_EINVAL, "tpc_fit_tracks has not run");
+  if (!codec_unit_ok(unit_cm)) return fail(ctx, TPC_EINVAL, "fixed-point unit out of range");
+  CK(cudaSetDevice(ctx->device));
+  int rc = codec_reserve(ctx, ctx->caps.tracks, ctx->caps.n);
+  if (rc) return rc;
+  Counts* cn = ctx->ptr<Counts>(ctx->L.counts);
+  k_codec_encode<<<grid_for(ctx, ctx->caps.tracks, 128, 8), 128, 0, ctx->stream>>>(
+      ctx->ptr<tpc_track>(ctx->L.tracks), ctx->ptr<tpc_cluster>(ctx->L.in), refit_in(ctx),
+      ctx->ptr<int32_t>(ctx->L.track_clusters), ctx->kc, ctx->cio, (float)unit_cm, cn);
+  CK(cudaGetLastError());
+  ctx->codec_valid = true;
+  return TPC_OK;
+}
+
+int tpc_get_compressed(tpc_ctx* ctx, tpc_codec_header* heads, int64_t cap_tracks, uint8_t* rows, int32_t* res_y,
+                       int32_t* res_z, int32_t* q_y, int32_t* q_z, int64_t cap_clusters, int64_t* n_tracks,
+                       int64_t* n_clusters) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->codec_valid) return fail(ctx, TPC_EINVAL, "tpc_compress has not run");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_status(ctx);
+  if (rc) return rc;
+  const int64_t M = ctx->h_counts->n_tracks, N = ctx->h_counts->n_track_clusters;
+  if (n_tracks) *n_tracks = M;
+  if (n_clusters) *n_clusters = N;
+  if ((heads && M > cap_tracks) || ((rows || res_y || res_z || q_y || q_z) && N > cap_clusters))
+    return fail(ctx, TPC_EOVERFLOW, "%lld tracks / %lld clusters do not fit", (long long)M, (long long)N);
+  if (heads && M) CK(cudaMemcpy(heads, ctx->cio.head, sizeof(CodecHeader) * M, cudaMemcpyDeviceToHost));
+  if (rows && N) CK(cudaMemcpy(rows, ctx->cio.rows, N, cudaMemcpyDeviceToHost));
+  if (res_y && N) CK(cudaMemcpy(res_y, ctx->cio.ry, 4 * N, cudaMemcpyDeviceToHost));
+  if (res_z && N) CK(cudaMemcpy(res_z, ctx->cio.rz, 4 * N, cudaMemcpyDeviceToHost));
+  if (q_y && N) CK(cudaMemcpy(q_y, ctx->cio.qy, 4 * N, cudaMemcpyDeviceToHost));
+  if (q_z && N) CK(cudaMemcpy(q_z, ctx->cio.qz, 4 * N, cudaMemcpyDeviceToHost));
+  return TPC_OK;
+}
+
+int tpc_decompress(tpc_ctx* ctx, const tpc_codec_header* heads, int64_t n_tracks, const uint8_t* rows,
+                   const int32_t* res_y, const int32_t* res_z, int64_t n_clusters, double unit_cm, int32_t* q_y,
+                   int32_t* q_z) {
+  if (!ctx || n_tracks < 0 || n_clusters < 0 || (n_tracks && !heads) ||
+      (n_clusters && (!rows || !res_y || !res_z || !q_y || !q_z)))
+    return TPC_EINVAL;
+  if (!codec_unit_ok(unit_cm)) return fail(ctx, TPC_EINVAL, "fixed-point unit out of range");
+  std::vector<int64_t> off((size_t)n_tracks + 1, 0);
+  for (int64_t m = 0; m < n_tracks; m++) {
+    if (heads[m].n_clusters < 0) return fail(ctx, TPC_EINVAL, "negative cluster count in header %lld", (long long)m);
+    off[m + 1] = off[m] + heads[m].n_clusters;
+  }
+  if (off[n_tracks] != n_clusters) return fail(ctx, TPC_EINVAL, "headers count %lld clusters, %lld given",
+                                               (long long)off[n_tracks], (long long)n_clusters);
+  CK(cudaSetDevice(ctx->device));
+  int rc = codec_reserve(ctx, n_tracks, n_clusters);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const CodecIo& io = ctx->cio;
+  ctx->codec_valid = false;  // the buffers now hold this decompression
+  if (n_tracks) {
+    CK(cudaMemcpyAsync(io.head, heads, sizeof(CodecHeader) * n_tracks, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync((void*)io.off, off.data(), 8 * (n_tracks + 1), cudaMemcpyHostToDevice, s));
+  }
+  if (n_clusters) {
+    CK(cudaMemcpyAsync(io.rows, rows, n_clusters, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(io.ry, res_y, 4 * n_clusters, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(io.rz, res_z, 4 * n_clusters, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemsetAsync(ctx->codec_bad, 0, 4, s));
+  if (n_tracks)  // the context's configuration (field, FP64-zone length), whether or not it has loaded data
+    k_codec_decode<<<grid_for(ctx, n_tracks, 128, 8), 128, 0, s>>>(make_kconst(ctx->cfg, ctx->caps), io, n_tracks,
+                                                                     (float)unit_cm, ctx->codec_bad);
+  CK(cudaGetLastError());
+  int32_t bad = 0;
+  if (n_clusters) {
+    CK(cudaMemcpyAsync(q_y, io.qy, 4 * n_clusters, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(q_z, io.qz, 4 * n_clusters, cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaMemcpyAsync(&bad, ctx->codec_bad, 4, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (bad) return fail(ctx, TPC_EINVAL, "%d tracks could not be decoded (malformed headers or rows)", bad);
   return TPC_OK;
 }
 
