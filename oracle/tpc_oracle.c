@@ -950,6 +950,219 @@ void orc_quantise(int64_t n, const float *v, double unit, int32_t *q) {
   for (int64_t i = 0; i < n; i++) q[i] = (int32_t)rintf(v[i] * inv);
 }
 
+/* ======================================== sector-track merging (next row) */
+/* The second tracking phase of Sec. 2 merges the segments the sector
+   tracker found in different sectors and refits the merged tracks.  The
+   reading implemented here:
+   - a segment is a refitted sector track: state at its innermost row in its
+     sector's frame (centre angle (s mod 18)*20+10 degrees), covariance, its
+     clusters;
+   - an inner segment A (sector s) and an outer segment B (sector s' = s +-1
+     on the same side, A.row_out <= B.row_in + overlap) are compared at B's
+     innermost row: A's state is turned into B's frame and carried there,
+     chi2 = d^T (C_A + C_B)^-1 d over the five parameters; a pair with
+     chi2 <= chi2_max that is the best of both A's and B's candidates is
+     merged (chains follow the merges);
+   - a merged track is refitted from its outermost segment's start (the
+     refit's seed) inward over all its clusters, the state and covariance
+     turned into the next segment's frame between segments; the result is
+     given at the innermost cluster in the innermost segment's frame. */
+
+static double sector_angle(int s) { return ((s % 18) * 20.0 + 10.0) * M_PI / 180.0; }
+
+/* The state at x in a frame turned into the frame rotated by beta (new
+   frame = old frame rotated by +beta about the beam axis), kept on its own
+   point: x' = x cos b + y sin b, y' = -x sin b + y cos b, phi' = phi - b.
+   Covariance: derivatives at fixed x', J[y][y] = cos phi / cos phi',
+   J[s][s] = cos phi' / cos phi, J[z][y] = -t sin b / cos phi'.  Returns 0
+   if the direction would leave the frame's outward half-plane. */
+static int rotate(kstate *s, double beta) {
+  const double ca = cos(beta), sa = sin(beta);
+  const double sp = s->p[2], cp = sqrt(1.0 - sp * sp);
+  const double sp2 = sp * ca - cp * sa, cp2 = cp * ca + sp * sa;
+  if (!(cp2 > 0.05)) return 0;
+  double J[5][5] = {{0}};
+  for (int i = 0; i < 5; i++) J[i][i] = 1.0;
+  J[0][0] = cp / cp2;
+  J[2][2] = cp2 / cp;
+  J[1][0] = -s->p[3] * sa / cp2;
+  double T[5][5], N[5][5];
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) {
+      double a = 0;
+      for (int m = 0; m < 5; m++) a += J[i][m] * s->C[m][j];
+      T[i][j] = a;
+    }
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) {
+      double a = 0;
+      for (int m = 0; m < 5; m++) a += T[i][m] * J[j][m];
+      N[i][j] = a;
+    }
+  memcpy(s->C, N, sizeof(N));
+  const double x = s->x, y = s->p[0];
+  s->x = x * ca + y * sa;
+  s->p[0] = -x * sa + y * ca;
+  s->p[2] = sp2;
+  return 1;
+}
+
+/* Propagation to a radius that need not be a row's (row-by-row steps on
+   the way, as the filter does, then the last piece). */
+static int carry_to(const kctx *k, kstate *s, double x2, int *flags) {
+  return propagate(k, s, x2, flags);
+}
+
+/* chi2 of d with covariance S (5x5, Cholesky); -1 if S is not positive. */
+static double chi2_5(const double d[5], double S[5][5]) {
+  double L[5][5] = {{0}};
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j <= i; j++) {
+      double a = S[i][j];
+      for (int m = 0; m < j; m++) a -= L[i][m] * L[j][m];
+      if (i == j) {
+        if (!(a > 0)) return -1.0;
+        L[i][i] = sqrt(a);
+      } else {
+        L[i][j] = a / L[j][j];
+      }
+    }
+  double w[5], c = 0;
+  for (int i = 0; i < 5; i++) {
+    double a = d[i];
+    for (int m = 0; m < i; m++) a -= L[i][m] * w[m];
+    w[i] = a / L[i][i];
+    c += w[i] * w[i];
+  }
+  return c;
+}
+
+static void unpack_cov(const double *c15, double C[5][5]) {
+  int q = 0;
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j <= i; j++, q++) C[i][j] = C[j][i] = c15[q];
+}
+
+/* Pair chi2 of inner segment a with outer segment b (-1: not comparable). */
+static double pair_chi2(const kctx *k, const int32_t *sector, const int32_t *row_in, const double *par,
+                        const double *cov, int a, int b) {
+  kstate s;
+  int flags = 0;
+  s.x = X32[row_in[a]];
+  memcpy(s.p, par + 5 * (int64_t)a, 5 * sizeof(double));
+  unpack_cov(cov + 15 * (int64_t)a, s.C);
+  if (!rotate(&s, sector_angle(sector[b]) - sector_angle(sector[a]))) return -1.0;
+  if (!carry_to(k, &s, X32[row_in[b]], &flags)) return -1.0;
+  double d[5], Cb[5][5], S[5][5];
+  unpack_cov(cov + 15 * (int64_t)b, Cb);
+  for (int i = 0; i < 5; i++) {
+    d[i] = s.p[i] - par[5 * (int64_t)b + i];
+    for (int j = 0; j < 5; j++) S[i][j] = s.C[i][j] + Cb[i][j];
+  }
+  return chi2_5(d, S);
+}
+
+static int adjacent(int s1, int s2) {
+  if (s1 / 18 != s2 / 18) return 0;
+  const int d = ((s2 % 18) - (s1 % 18) + 18) % 18;
+  return d == 1 || d == 17;
+}
+
+/* Pairing: for every segment its best partner inward (best_in) and outward
+   (best_out) with the pair's chi2 and the second-best chi2 (for the taint
+   of near ties); a merge where both choose each other.  out_link[a] = b
+   (-1: none).  Segments: n_tracks, with request, sector, rows, state. */
+int orc_merge_pairs(const orc_config *cfg_in, int32_t n, const int32_t *request, const int32_t *sector,
+                    const int32_t *row_in, const int32_t *row_out, const int32_t *n_clusters, const double *par,
+                    const double *cov, double chi2_max, int32_t overlap, int32_t min_clusters, int32_t *out_link,
+                    double *out_chi2, double *out_second) {
+  orc_config cfg;
+  if (cfg_in) cfg = *cfg_in; else orc_default_config(&cfg);
+  init_tables();
+  kctx k = {&cfg, 0.299792458e-3 * cfg.bz_kg, cfg.sigma * cfg.sigma};
+  int32_t *bo = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t *bi = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  double *co = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *so = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double *ci = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!bo || !bi || !co || !so || !ci) { free(bo); free(bi); free(co); free(so); free(ci); return ORC_ENOMEM; }
+  for (int32_t a = 0; a < n; a++) {
+    bo[a] = bi[a] = -1;
+    co[a] = ci[a] = so[a] = INFINITY;
+  }
+  for (int32_t a = 0; a < n; a++) {
+    if (n_clusters[a] < min_clusters) continue;
+    for (int32_t b = 0; b < n; b++) {
+      if (b == a || request[b] != request[a] || n_clusters[b] < min_clusters) continue;
+      if (!adjacent(sector[a], sector[b])) continue;
+      if (!(row_in[a] < row_in[b] && row_out[a] <= row_in[b] + overlap)) continue; /* a inner, b outer */
+      const double c = pair_chi2(&k, sector, row_in, par, cov, a, b);
+      if (c < 0 || c > chi2_max) continue;
+      if (c < co[a] || (c == co[a] && b < bo[a])) {
+        so[a] = fmin(so[a], co[a]);
+        co[a] = c;
+        bo[a] = b;
+      } else {
+        so[a] = fmin(so[a], c);
+      }
+      if (c < ci[b] || (c == ci[b] && a < bi[b])) {
+        ci[b] = c;
+        bi[b] = a;
+      }
+    }
+  }
+  for (int32_t a = 0; a < n; a++) {
+    const int32_t b = bo[a];
+    out_link[a] = (b >= 0 && bi[b] == a) ? b : -1;
+    out_chi2[a] = co[a];
+    out_second[a] = so[a];
+  }
+  free(bo); free(bi); free(co); free(so); free(ci);
+  return ORC_OK;
+}
+
+/* Refit of a chain of segments, outermost first: chain[0..m) segment ids,
+   their clusters (rows, y, z in each segment's frame) outermost first in
+   one list with offsets; seed = the outermost segment's state at its
+   outermost row (the refit's seed).  Output at the innermost cluster in the
+   innermost segment's frame. */
+int orc_merge_refit(const orc_config *cfg_in, int32_t m, const int32_t *seg_sector, const int64_t *seg_off,
+                    const int32_t *rows, const double *y, const double *z, int32_t seed_row, const double *seed,
+                    double *par_out, double *cov_out, double *chi2_out, int32_t *row_out_inner) {
+  orc_config cfg;
+  if (cfg_in) cfg = *cfg_in; else orc_default_config(&cfg);
+  init_tables();
+  kctx k = {&cfg, 0.299792458e-3 * cfg.bz_kg, cfg.sigma * cfg.sigma};
+  kstate s;
+  int flags = 0;
+  s.x = X32[seed_row];
+  memcpy(s.p, seed, 5 * sizeof(double));
+  reset_cov(&k, &s);
+  int row = seed_row;
+  for (int32_t g = 0; g < m; g++) {
+    if (g > 0) {
+      if (!rotate(&s, sector_angle(seg_sector[g]) - sector_angle(seg_sector[g - 1]))) return 0;
+      row = NROW; /* the next propagation goes to the segment's first row, wherever x now is */
+    }
+    for (int64_t i = seg_off[g]; i < seg_off[g + 1]; i++) {
+      if (row == NROW) {
+        if (!carry_to(&k, &s, X32[rows[i]], &flags)) return 0;
+        row = rows[i];
+      }
+      while (row > rows[i]) {
+        row--;
+        if (!propagate(&k, &s, X32[row], &flags)) return 0;
+      }
+      update(&k, &s, y[i], z[i]);
+    }
+  }
+  memcpy(par_out, s.p, 5 * sizeof(double));
+  pack_cov(s.C, cov_out);
+  *chi2_out = s.chi2;
+  *row_out_inner = row;
+  return 1;
+}
+
 /* Row radii and half-widths as the oracle uses them (binary32). */
 void orc_tables(float *x, float *yhi) {
   init_tables();
