@@ -391,6 +391,24 @@ typedef struct {
   double V;   /* sigma^2 */
 } kctx;
 
+/* C <- J C J^T (full 5x5). */
+static void jcjt(const double J[5][5], double C[5][5]) {
+  double T[5][5], N[5][5];
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) {
+      double a = 0;
+      for (int m = 0; m < 5; m++) a += J[i][m] * C[m][j];
+      T[i][j] = a;
+    }
+  for (int i = 0; i < 5; i++)
+    for (int j = 0; j < 5; j++) {
+      double a = 0;
+      for (int m = 0; m < 5; m++) a += T[i][m] * J[j][m];
+      N[i][j] = a;
+    }
+  memcpy(C, N, sizeof(N));
+}
+
 /* Propagate to x2 along the helix (exact for the state), first-order
    Jacobian for C.  Returns 0 when |sin phi| would reach s_max. */
 static int propagate(const kctx *k, kstate *s, double x2, int *flags) {
@@ -416,20 +434,7 @@ static int propagate(const kctx *k, kstate *s, double x2, int *flags) {
   J[1][3] = dS;
   J[1][2] = t * dx * sm / cm3;
   J[1][4] = -t * k->K * dx * dx * sm / (2.0 * cm3);
-  double T[5][5], N[5][5];
-  for (int i = 0; i < 5; i++)
-    for (int j = 0; j < 5; j++) {
-      double a = 0;
-      for (int m = 0; m < 5; m++) a += J[i][m] * s->C[m][j];
-      T[i][j] = a;
-    }
-  for (int i = 0; i < 5; i++)
-    for (int j = 0; j < 5; j++) {
-      double a = 0;
-      for (int m = 0; m < 5; m++) a += T[i][m] * J[j][m];
-      N[i][j] = a;
-    }
-  memcpy(s->C, N, sizeof(N));
+  jcjt(J, s->C);
   s->p[0] += dy;
   s->p[1] += t * dS;
   s->p[2] = s2;
@@ -986,20 +991,7 @@ static int rotate(kstate *s, double beta) {
   J[0][0] = cp / cp2;
   J[2][2] = cp2 / cp;
   J[1][0] = -s->p[3] * sa / cp2;
-  double T[5][5], N[5][5];
-  for (int i = 0; i < 5; i++)
-    for (int j = 0; j < 5; j++) {
-      double a = 0;
-      for (int m = 0; m < 5; m++) a += J[i][m] * s->C[m][j];
-      T[i][j] = a;
-    }
-  for (int i = 0; i < 5; i++)
-    for (int j = 0; j < 5; j++) {
-      double a = 0;
-      for (int m = 0; m < 5; m++) a += T[i][m] * J[j][m];
-      N[i][j] = a;
-    }
-  memcpy(s->C, N, sizeof(N));
+  jcjt(J, s->C);
   const double x = s->x, y = s->p[0];
   s->x = x * ca + y * sa;
   s->p[0] = -x * sa + y * ca;
