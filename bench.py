@@ -284,6 +284,20 @@ def all_configs(local):
                    "tracks_with_vertex": int((vres["track_vertex"] >= 0).sum()),
                    "tracks_per_s": counts["n_tracks"] / (vms / 1e3),
                    "hbm_gbs": counts["n_tracks"] * (2 * 128 + 24) / (vms / 1e3) / 1e9}
+        merged = None
+        if n > 100_000:  # second tracking phase: merging sector segments
+            trk.merge()
+            mt = []
+            for _ in range(3):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                trk._ck(trk._lib.tpc_merge_tracks(trk._ctx, None))
+                e1.record(stream)
+                e1.synchronize()
+                mt.append(e0.elapsed_time(e1))
+            mg = trk.merge()
+            merged = {"ms": statistics.median(mt), "merged_tracks": int(len(mg["merged"])),
+                      "segments_merged": int((mg["chain"] >= 0).sum()), "segments": int(counts["n_tracks"])}
         codec = None
         if n > 100_000:  # track-model compression of the event / timeframe
             trk.compress(0.01)
@@ -347,6 +361,8 @@ def all_configs(local):
             rows[name]["vertex_finding"] = vtx
         if codec is not None:
             rows[name]["track_model_compression"] = codec
+        if merged is not None:
+            rows[name]["sector_merging"] = merged
     print(json.dumps({"all_configs": rows}))
 
 

@@ -396,6 +396,43 @@ int tpc_decompress(tpc_ctx *ctx, const tpc_codec_header *heads, int64_t n_tracks
                    const int32_t *res_y, const int32_t *res_z, int64_t n_clusters, double unit_cm, int32_t *q_y,
                    int32_t *q_z);
 
+/* ------------------------------------- merging sector segments (phase 2) */
+/* Sec. 2's second phase: the segments the sector tracker found in different
+ * sectors are merged into final tracks and refitted.  Reading: an inner
+ * segment A and an outer segment B in neighbouring sectors of one side
+ * (A's first row below B's, A's last row at most overlap_rows past B's first)
+ * are compared at B's first row -- A's fitted state and covariance turned
+ * into B's frame and carried there; chi2 = d^T (C_A + C_B)^-1 d over the five
+ * parameters; a pair within chi2_max that is the best choice of both is
+ * merged.  Chains of merges are refitted from the outermost segment's refit
+ * seed inward over all their clusters, the frame turned between segments
+ * (the FP64 zone as in the refit); a merged track is given at its innermost
+ * cluster in the innermost segment's frame.  Segments with a failed refit or
+ * fewer than min_clusters clusters take no part. */
+typedef struct {
+  double chi2_max;      /* 25 */
+  int32_t overlap_rows; /* 10 */
+  int32_t min_clusters; /* 10 */
+  int64_t reserved;
+} tpc_merge_config;
+
+int tpc_default_merge_config(tpc_merge_config *cfg);
+
+/* On the fitted tracks of the loaded batch (after tpc_fit_tracks); cfg NULL:
+ * defaults.  Asynchronous; results with tpc_get_merged. */
+int tpc_merge_tracks(tpc_ctx *ctx, const tpc_merge_config *cfg);
+
+/* Waits and copies the merged tracks (tpc_track records, in the order of
+ * their innermost segments: par/cov/chi2/ndf/n_clusters of the merged fit,
+ * sector/request and first_row of the innermost segment, last_row of the
+ * outermost, reserved = segments, cluster_offset = index of the innermost
+ * segment among the tracks of tpc_get_tracks, flags TPC_TF_REFIT_FAIL if
+ * the merged fit stopped); and per segment (optional, n_tracks entries
+ * each): its merged outer partner or -1, its merged track or -1, the chi2 of
+ * its best outer candidate and the second-best chi2 (infinity: none). */
+int tpc_get_merged(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, int32_t *track_link,
+                   int32_t *track_chain, float *pair_chi2, float *pair_second);
+
 /* ------------------------------------------------------ serving (requests) */
 /* Continuous-batching request loop: the serving form of tracking several
  * events or continuous-readout timeframes (Sec. 2, Sec. 5) as they arrive.

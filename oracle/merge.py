@@ -26,7 +26,7 @@ def _bind():
     if not _bound:
         P = ctypes.c_void_p
         lib.orc_merge_pairs.argtypes = [P, ctypes.c_int32] + [P] * 7 + [ctypes.c_double, ctypes.c_int32,
-                                                                         ctypes.c_int32, P, P, P]
+                                                                         ctypes.c_int32, P, P, P, P]
         lib.orc_merge_pairs.restype = ctypes.c_int
         lib.orc_merge_refit.argtypes = [P, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32, P, P, P, P, P]
         lib.orc_merge_refit.restype = ctypes.c_int
@@ -60,12 +60,13 @@ def pairs(seg: dict, p: dict | None = None) -> dict:
     link = np.zeros(n, np.int32)
     chi2 = np.zeros(n, np.float64)
     second = np.zeros(n, np.float64)
+    second_in = np.zeros(n, np.float64)
     c = lambda a: np.ascontiguousarray(a).ctypes.data  # noqa: E731
     if n:
         lib.orc_merge_pairs(None, n, c(seg["request"]), c(seg["sector"]), c(seg["row_in"]), c(seg["row_out"]),
                             c(ncl), c(seg["par"]), c(seg["cov"]), p["chi2_max"], p["overlap"], p["min_clusters"],
-                            link.ctypes.data, chi2.ctypes.data, second.ctypes.data)
-    return {"link": link, "chi2": chi2, "second": second}
+                            link.ctypes.data, chi2.ctypes.data, second.ctypes.data, second_in.ctypes.data)
+    return {"link": link, "chi2": chi2, "second": second, "second_in": second_in}
 
 
 def chains(link: np.ndarray) -> list:
@@ -116,6 +117,7 @@ def merge(ref: dict, clusters: np.ndarray, p: dict | None = None) -> dict:
             ctypes.byref(ri)))
         par[k], cov[k], chi2[k], ncl[k], row_in[k] = po, co, c2.value, len(idx), ri.value
     return {"segments": seg, "link": pr["link"], "pair_chi2": pr["chi2"], "pair_second": pr["second"],
+            "pair_second_in": pr["second_in"],
             "chains": ch, "par": par, "cov": cov, "chi2": chi2, "ndf": 2 * ncl - 5, "n": ncl, "ok": ok,
             "row_in": row_in}
 

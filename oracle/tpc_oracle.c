@@ -1067,7 +1067,7 @@ static int adjacent(int s1, int s2) {
 int orc_merge_pairs(const orc_config *cfg_in, int32_t n, const int32_t *request, const int32_t *sector,
                     const int32_t *row_in, const int32_t *row_out, const int32_t *n_clusters, const double *par,
                     const double *cov, double chi2_max, int32_t overlap, int32_t min_clusters, int32_t *out_link,
-                    double *out_chi2, double *out_second) {
+                    double *out_chi2, double *out_second, double *out_second_in) {
   orc_config cfg;
   if (cfg_in) cfg = *cfg_in; else orc_default_config(&cfg);
   init_tables();
@@ -1077,10 +1077,14 @@ int orc_merge_pairs(const orc_config *cfg_in, int32_t n, const int32_t *request,
   double *co = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *so = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
   double *ci = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-  if (!bo || !bi || !co || !so || !ci) { free(bo); free(bi); free(co); free(so); free(ci); return ORC_ENOMEM; }
+  double *si = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  if (!bo || !bi || !co || !so || !ci || !si) {
+    free(bo); free(bi); free(co); free(so); free(ci); free(si);
+    return ORC_ENOMEM;
+  }
   for (int32_t a = 0; a < n; a++) {
     bo[a] = bi[a] = -1;
-    co[a] = ci[a] = so[a] = INFINITY;
+    co[a] = ci[a] = so[a] = si[a] = INFINITY;
   }
   for (int32_t a = 0; a < n; a++) {
     if (n_clusters[a] < min_clusters) continue;
@@ -1098,8 +1102,11 @@ int orc_merge_pairs(const orc_config *cfg_in, int32_t n, const int32_t *request,
         so[a] = fmin(so[a], c);
       }
       if (c < ci[b] || (c == ci[b] && a < bi[b])) {
+        si[b] = fmin(si[b], ci[b]);
         ci[b] = c;
         bi[b] = a;
+      } else {
+        si[b] = fmin(si[b], c);
       }
     }
   }
@@ -1108,8 +1115,9 @@ int orc_merge_pairs(const orc_config *cfg_in, int32_t n, const int32_t *request,
     out_link[a] = (b >= 0 && bi[b] == a) ? b : -1;
     out_chi2[a] = co[a];
     out_second[a] = so[a];
+    out_second_in[a] = si[a];
   }
-  free(bo); free(bi); free(co); free(so); free(ci);
+  free(bo); free(bi); free(co); free(so); free(ci); free(si);
   return ORC_OK;
 }
 

@@ -62,6 +62,11 @@ class VertexConfig(ctypes.Structure):
                 ("min_clusters", ctypes.c_int32)]
 
 
+class MergeConfig(ctypes.Structure):
+    _fields_ = [("chi2_max", ctypes.c_double), ("overlap_rows", ctypes.c_int32), ("min_clusters", ctypes.c_int32),
+                ("reserved", ctypes.c_int64)]
+
+
 CODEC_HEADER_DTYPE = np.dtype([("par", "<f4", (5,)), ("row_out", "<i4"), ("n_clusters", "<i4"), ("ok", "<i4")])
 assert CODEC_HEADER_DTYPE.itemsize == 32
 
@@ -116,6 +121,9 @@ def load_library(path: str | None = None):
         "tpc_measure_alu_peaks": ([ctypes.c_int, _VP, _VP], ctypes.c_int),
         "tpc_default_vertex_config": ([_VP], ctypes.c_int),
         "tpc_compress": ([_VP, ctypes.c_double], ctypes.c_int),
+        "tpc_default_merge_config": ([_VP], ctypes.c_int),
+        "tpc_merge_tracks": ([_VP, _VP], ctypes.c_int),
+        "tpc_get_merged": ([_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "tpc_get_compressed": ([_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP], ctypes.c_int),
         "tpc_decompress": ([_VP, _VP, _I64, _VP, _VP, _VP, _I64, ctypes.c_double, _VP, _VP], ctypes.c_int),
         "tpc_find_vertices": ([_VP, _VP], ctypes.c_int),
@@ -375,6 +383,28 @@ class Tracker:
                                             tt.ctypes.data if m else None, tz.ctypes.data if m else None,
                                             tg.ctypes.data if m else None))
         return {"vertices": out, "track_vertex": tv, "track_time": tt, "track_z": tz, "track_tgl": tg}
+
+    def merge(self, **cfg) -> dict:
+        """Second tracking phase (tpc_merge_tracks): merged tracks and, per
+        sector track, its merged outer partner, its merged track and the
+        chi2 of its best and second-best outer candidates."""
+        c = MergeConfig()
+        self._lib.tpc_default_merge_config(ctypes.byref(c))
+        for k, v in cfg.items():
+            if not hasattr(c, k):
+                raise TypeError(f"unknown merge option {k}")
+            setattr(c, k, v)
+        self._ck(self._lib.tpc_merge_tracks(self._ctx, ctypes.byref(c)))
+        nm = ctypes.c_int64()
+        self._ck(self._lib.tpc_get_merged(self._ctx, None, 0, ctypes.byref(nm), None, None, None, None))
+        m = self.counts()["n_tracks"]
+        out = np.zeros(nm.value, TRACK_DTYPE)
+        link, chain = np.zeros(m, np.int32), np.zeros(m, np.int32)
+        c2, c2s = np.zeros(m, np.float32), np.zeros(m, np.float32)
+        p = lambda a: a.ctypes.data if len(a) else None  # noqa: E731
+        self._ck(self._lib.tpc_get_merged(self._ctx, p(out), nm.value, ctypes.byref(nm), p(link), p(chain), p(c2),
+                                          p(c2s)))
+        return {"merged": out, "link": link, "chain": chain, "pair_chi2": c2, "pair_second": c2s}
 
     def compress(self, unit_cm: float = 0.01) -> dict:
         """Track-model compression of the fitted tracks (tpc_compress):

@@ -1,0 +1,314 @@
+// Second tracking phase (Sec. 2): the segments found in different sectors
+// are merged and the merged tracks refitted.  An inner segment A and an
+// outer segment B in neighbouring sectors of one side are compared at B's
+// first row: A's fitted state and covariance are turned into B's frame and
+// carried there; chi2 = d^T (C_A + C_B)^-1 d over the five parameters.  A
+// pair within chi2_max that is the best choice of both A and B is merged;
+// chains of merges are refitted from the outermost segment's seed inward,
+// the frame turned between segments.  One thread per segment (pairing) and
+// per chain (refit).
+#pragma once
+#include "kalman.cuh"
+
+namespace tpc {
+
+constexpr int MERGE_MAX_SEG = 8;  // segments per chain (a longer chain is cut)
+
+struct MergeConst {
+  float chi2_max;
+  int32_t overlap, min_clusters;
+};
+
+struct MergeBuf {
+  int32_t* u_start;               // [units] first track of each (request, sector), -1: none
+  int32_t* u_end;                 // [units]
+  int32_t* best_out;              // [M] A's best outer partner
+  float* chi2_out;                // [M] its chi2
+  float* second_out;              // [M] A's second-best chi2 (for near ties)
+  unsigned long long* best_in;    // [M] B's best inner partner: (chi2 bits << 32) | A
+  int32_t* link;                  // [M] merged outer partner or -1
+  int32_t* has_inner;             // [M]
+  int32_t* head;                  // [M + 1] 1 for the innermost segment of a chain
+  int32_t* chain_of_head;         // [M + 1] exclusive scan of head
+  int32_t* chain;                 // [M] merged track of a segment, -1: none
+  tpc_track* merged;              // [M] merged tracks
+  int32_t* n;                     // [2] chains, status
+};
+
+__device__ __forceinline__ float sector_angle(int s) {
+  return (float)(((s % NSEC) % 18) * 20 + 10) * 0.017453292519943295f;
+}
+
+__device__ __forceinline__ bool sectors_adjacent(int s1, int s2) {
+  if ((s1 % NSEC) / 18 != (s2 % NSEC) / 18) return false;
+  const int d = ((s2 % 18) - (s1 % 18) + 18) % 18;
+  return d == 1 || d == 17;
+}
+
+// The state on its own point expressed in the frame rotated by +beta:
+// x' = x cos b + y sin b, y' = -x sin b + y cos b, phi' = phi - b; the
+// covariance with the derivatives at fixed x' (J[y][y] = cos phi/cos phi',
+// J[s][s] = cos phi'/cos phi, J[z][y] = -t sin b/cos phi').  False if the
+// direction would leave the new frame's outward half-plane.
+template <typename T>
+__device__ __forceinline__ bool rotate_state(TrkState& p, T* C, float beta) {
+  float sb, cb;
+  sincosf(beta, &sb, &cb);
+  const float s = p.s + p.sl, c = sqrtf(fmaxf(1.0f - s * s, 0.0f));
+  const float s2 = s * cb - c * sb, c2 = c * cb + s * sb;
+  if (!(c2 > 0.05f)) return false;
+  const T j00 = (T)(c / c2), j22 = (T)(c2 / c), j10 = (T)(-p.t * sb / c2);
+  // C' = J C J^T with J = I except (0,0), (2,2), (1,0)
+  T M[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j < 5; j++) M[i][j] = C[TPC_CI(i > j ? i : j, i > j ? j : i)];
+  T A[5][5];  // J M
+#pragma unroll
+  for (int j = 0; j < 5; j++) {
+    A[0][j] = j00 * M[0][j];
+    A[1][j] = M[1][j] + j10 * M[0][j];
+    A[2][j] = j22 * M[2][j];
+    A[3][j] = M[3][j];
+    A[4][j] = M[4][j];
+  }
+#pragma unroll
+  for (int i = 0; i < 5; i++) {  // (J M) J^T, lower triangle
+    const T r0 = A[i][0] * j00;
+    const T r1 = A[i][1] + A[i][0] * j10;
+    const T r2 = A[i][2] * j22;
+    const T row[5] = {r0, r1, r2, A[i][3], A[i][4]};
+#pragma unroll
+    for (int j = 0; j <= i; j++) C[TPC_CI(i, j)] = row[j];
+  }
+  const float x = p.x, y = p.y + p.yl;
+  p.x = x * cb + y * sb;
+  p.y = -x * sb + y * cb;
+  p.yl = 0.0f;
+  p.s = s2;
+  p.sl = 0.0f;
+  return true;
+}
+
+// Unit ranges: tracks are ordered by (request, sector).
+__global__ void k_merge_units(const tpc_track* __restrict__ tr, MergeBuf mb, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  for (int64_t m = gtid(); m < M; m += gstride()) {
+    const int u = tr[m].request * NSEC + tr[m].sector;
+    if (m == 0 || tr[m - 1].request * NSEC + tr[m - 1].sector != u) mb.u_start[u] = (int32_t)m;
+    if (m == M - 1 || tr[m + 1].request * NSEC + tr[m + 1].sector != u) mb.u_end[u] = (int32_t)m + 1;
+  }
+}
+
+// 5x5 chi2 d^T S^-1 d by Cholesky; negative if S is not positive definite.
+__device__ __forceinline__ float chi2_5(const float d[5], float S[15]) {
+  float L[15];
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) {
+      float a = S[TPC_CI(i, j)];
+#pragma unroll
+      for (int m = 0; m < j; m++) a -= L[TPC_CI(i, m)] * L[TPC_CI(j, m)];
+      if (i == j) {
+        if (!(a > 0.0f)) return -1.0f;
+        L[TPC_CI(i, i)] = sqrtf(a);
+      } else {
+        L[TPC_CI(i, j)] = a / L[TPC_CI(j, j)];
+      }
+    }
+  float w[5], c = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    float a = d[i];
+#pragma unroll
+    for (int m = 0; m < i; m++) a -= L[TPC_CI(i, m)] * w[m];
+    w[i] = a / L[TPC_CI(i, i)];
+    c += w[i] * w[i];
+  }
+  return c;
+}
+
+// Pairing: per segment A its best outer partner and the second-best chi2;
+// per segment B its best inner partner (packed atomic minimum).
+__global__ void __launch_bounds__(128) k_merge_pairs(const tpc_track* __restrict__ tr, KConst kc, MergeConst mc,
+                                                     MergeBuf mb, const Counts* cn) {
+  __shared__ float sX[NROW + 1];
+  for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
+  __syncthreads();
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  const float inf = __int_as_float(0x7F800000);
+  for (int64_t a = gtid(); a < M; a += gstride()) {
+    const tpc_track A = tr[a];
+    int32_t best = -1;
+    float bc = inf, sc = inf;
+    if (!(A.flags & TF_REFIT_FAIL) && A.n_clusters >= mc.min_clusters) {
+      const int side = A.sector / 18, sa = A.sector % 18;
+      for (int k = 0; k < 2; k++) {
+        const int sb = side * 18 + (sa + (k ? 17 : 1)) % 18;
+        const int u = A.request * NSEC + sb;
+        const int b0 = mb.u_start[u], b1 = mb.u_end[u];
+        for (int b = b0; b >= 0 && b < b1; b++) {
+          const tpc_track B = tr[b];
+          if ((B.flags & TF_REFIT_FAIL) || B.n_clusters < mc.min_clusters) continue;
+          if (!(A.first_row < B.first_row && A.last_row <= B.first_row + mc.overlap)) continue;
+          TrkState p;
+          seed_state(p, A.first_row, sX[A.first_row], A.par[0], A.par[1], A.par[2], A.par[3], A.par[4]);
+          float C[15];
+#pragma unroll
+          for (int i = 0; i < 15; i++) C[i] = A.cov[i];
+          uint32_t flags = 0;
+          if (!rotate_state<float>(p, C, sector_angle(B.sector) - sector_angle(A.sector))) continue;
+          Jac J;
+          if (!prop_state(p, B.first_row, sX[B.first_row], kc, flags, &J)) continue;
+          cov_transport<float>(C, J.j02, J.j04, J.j24, J.j12, J.j13, J.j14);
+          const float d[5] = {(p.y + p.yl) - B.par[0], (p.zref + (p.z + p.zl)) - B.par[1], (p.s + p.sl) - B.par[2],
+                              p.t - B.par[3], p.q - B.par[4]};
+#pragma unroll
+          for (int i = 0; i < 15; i++) C[i] += B.cov[i];
+          const float c = chi2_5(d, C);
+          if (!(c >= 0.0f) || !(c <= mc.chi2_max)) continue;
+          if (c < bc || (c == bc && b < best)) {
+            sc = fminf(sc, bc);
+            bc = c;
+            best = b;
+          } else {
+            sc = fminf(sc, c);
+          }
+          atomicMin(&mb.best_in[b], ((unsigned long long)__float_as_uint(c) << 32) | (unsigned long long)a);
+        }
+      }
+    }
+    mb.best_out[a] = best;
+    mb.chi2_out[a] = bc;
+    mb.second_out[a] = sc;
+  }
+}
+
+// Mutual best choices become links; the innermost segment of a chain is
+// its head.
+__global__ void k_merge_links(MergeBuf mb, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  for (int64_t a = gtid(); a < M; a += gstride()) {
+    const int32_t b = mb.best_out[a];
+    const bool ok = b >= 0 && (int64_t)(mb.best_in[b] & 0xFFFFFFFFull) == a;
+    mb.link[a] = ok ? b : -1;
+    if (ok) mb.has_inner[b] = 1;
+  }
+}
+
+__global__ void k_merge_heads(MergeBuf mb, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  for (int64_t a = gtid(); a < M; a += gstride()) {
+    mb.head[a] = mb.link[a] >= 0 && !mb.has_inner[a];
+    mb.chain[a] = -1;
+  }
+}
+
+// Refit of a chain: the outermost segment's refit seed (its follow state
+// carried to its outermost row), then every segment's clusters outermost
+// first, the frame turned between segments; the FP64 zone as in the refit.
+__global__ void __launch_bounds__(128) k_merge_refit(const tpc_track* __restrict__ tr,
+                                                     const tpc_cluster* __restrict__ in, RefitIn rin,
+                                                     const int32_t* __restrict__ track_clusters, KConst kc,
+                                                     MergeBuf mb, const Counts* cn) {
+  __shared__ float sX[NROW + 1];
+  for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
+  __syncthreads();
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  for (int64_t h = gtid(); h < M; h += gstride()) {
+    if (!mb.head[h]) continue;
+    const int32_t k = mb.chain_of_head[h];
+    int32_t seg[MERGE_MAX_SEG];
+    int ns = 0;
+    for (int32_t g = (int32_t)h; g >= 0 && ns < MERGE_MAX_SEG; g = mb.link[g]) seg[ns++] = g;
+    int32_t ncl = 0;
+    for (int i = 0; i < ns; i++) {
+      mb.chain[seg[i]] = k;
+      ncl += tr[seg[i]].n_clusters;
+    }
+    // seed: the outermost segment's follow state carried to its last row
+    const tpc_track O = tr[seg[ns - 1]];
+    const int t = rin.track_tl[seg[ns - 1]];
+    TrkState p;
+    const int fr = rin.f_row[t];
+    seed_state(p, fr, sX[fr], rin.f_par[t * 5 + 0], rin.f_zref[t], rin.f_par[t * 5 + 2], rin.f_par[t * 5 + 3],
+               rin.f_par[t * 5 + 4]);
+    p.z = rin.f_par[t * 5 + 1];
+    uint32_t flags = 0;
+    bool ok = true;
+    const int step = O.last_row >= p.row ? 1 : -1;
+    for (int r = p.row + step; ok && (step > 0 ? r <= O.last_row : r >= O.last_row); r += step)
+      ok = prop_state(p, r, sX[r], kc, flags, nullptr);
+    double D[15];
+    float C[15];
+    cov_seed<double>(D, kc);
+    cov_seed<float>(C, kc);
+    Chi2Acc chi2;
+    chi2.reset();
+    int nupd = 0;
+    int row = O.last_row;
+    for (int gi = ns - 1; ok && gi >= 0; gi--) {
+      const tpc_track S = tr[seg[gi]];
+      if (gi < ns - 1) {
+        const float beta = sector_angle(S.sector) - sector_angle(tr[seg[gi + 1]].sector);
+        ok = nupd < kc.fp64_updates ? rotate_state<double>(p, D, beta) : rotate_state<float>(p, C, beta);
+        row = NROW;  // the next step goes to this segment's first cluster row
+      }
+      const int64_t off = S.cluster_offset, n = S.n_clusters;
+      for (int64_t i = n - 1; ok && i >= 0; i--) {
+        const tpc_cluster c = in[track_clusters[off + i]];
+        if (row == NROW) {
+          const bool zone = nupd < kc.fp64_updates;
+          ok = propagate_any(p, zone, D, C, c.row, sX[c.row], kc, flags);
+          row = c.row;
+        }
+        while (ok && row > c.row) {
+          row--;
+          ok = propagate_any(p, nupd < kc.fp64_updates, D, C, row, sX[row], kc, flags);
+        }
+        if (!ok) break;
+        const bool zone = nupd < kc.fp64_updates;
+        chi2.add(update_any(p, zone, D, C, c.y, c.z, kc));
+        nupd++;
+        if (zone && nupd == kc.fp64_updates) {
+#pragma unroll
+          for (int q = 0; q < 15; q++) C[q] = (float)D[q];
+        }
+      }
+    }
+    if (ok && nupd < kc.fp64_updates) {
+#pragma unroll
+      for (int q = 0; q < 15; q++) C[q] = (float)D[q];
+    }
+    const tpc_track I = tr[seg[0]];
+    tpc_track out;
+    out.x = p.x;
+    out.par[0] = p.y + p.yl;
+    out.par[1] = p.zref + (p.z + p.zl);
+    out.par[2] = p.s + p.sl;
+    out.par[3] = p.t;
+    out.par[4] = p.q;
+#pragma unroll
+    for (int q = 0; q < 15; q++) out.cov[q] = C[q];
+    out.reserved = ns;
+    out.chi2 = chi2.value();
+    out.ndf = 2 * ncl - 5;
+    out.n_clusters = ncl;
+    out.sector = I.sector;
+    out.request = I.request;
+    out.first_row = row;
+    out.last_row = O.last_row;
+    out.cluster_offset = (int32_t)h;  // the chain's innermost segment
+    out.flags = ok ? 0 : TF_REFIT_FAIL;
+    mb.merged[k] = out;
+  }
+}
+
+}  // namespace tpc

@@ -21,6 +21,7 @@
 #include "probe.cuh"
 #include "vertex.cuh"
 #include "codec.cuh"
+#include "merge.cuh"
 
 using namespace tpc;
 
@@ -217,6 +218,12 @@ struct tpc_ctx {
   CodecIo cio{};
   int32_t* codec_bad = nullptr;
   bool codec_valid = false;
+  // sector merging (tpc_merge_tracks): own buffer
+  void* merge_mem = nullptr;
+  int64_t merge_tracks_cap = 0, merge_units_cap = 0;
+  MergeBuf mb{};
+  int32_t* h_merge_n = nullptr;  // pinned: merged tracks
+  bool merge_valid = false;
   cudaEvent_t ev_chunk[4] = {};     // fork and join of the chunked follow and refit
   // graph
   cudaGraphExec_t graph = nullptr;
@@ -410,6 +417,8 @@ int create_common(tpc_ctx** out, const tpc_config* cfg, int device, void* stream
       if (ctx->ev_chunk[i]) cudaEventDestroy(ctx->ev_chunk[i]);
     if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
   if (ctx->codec_mem) cudaFree(ctx->codec_mem);
+  if (ctx->merge_mem) cudaFree(ctx->merge_mem);
+  if (ctx->h_merge_n) cudaFreeHost(ctx->h_merge_n);
   if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -764,6 +773,8 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (ctx->h_req) cudaFreeHost(ctx->h_req);
   if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
   if (ctx->codec_mem) cudaFree(ctx->codec_mem);
+  if (ctx->merge_mem) cudaFree(ctx->merge_mem);
+  if (ctx->h_merge_n) cudaFreeHost(ctx->h_merge_n);
   if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
   for (int i = 0; i < 4; i++)
@@ -1468,6 +1479,120 @@ int tpc_decompress(tpc_ctx* ctx, const tpc_codec_header* heads, int64_t n_tracks
   CK(cudaMemcpyAsync(&bad, ctx->codec_bad, 4, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   if (bad) return fail(ctx, TPC_EINVAL, "%d tracks could not be decoded (malformed headers or rows)", bad);
+  return TPC_OK;
+}
+
+int tpc_default_merge_config(tpc_merge_config* c) {
+  if (!c) return TPC_EINVAL;
+  c->chi2_max = 25.0;
+  c->overlap_rows = 10;
+  c->min_clusters = 10;
+  c->reserved = 0;
+  return TPC_OK;
+}
+
+namespace {
+int merge_reserve(tpc_ctx* ctx) {
+  const int64_t M = std::max<int64_t>(ctx->caps.tracks, 1), U = (int64_t)std::max(ctx->caps.req, 1) * NSEC;
+  if (ctx->merge_mem && ctx->merge_tracks_cap >= M && ctx->merge_units_cap >= U) return TPC_OK;
+  if (ctx->merge_mem) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->merge_mem);
+    ctx->merge_mem = nullptr;
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + std::max<size_t>(bytes, 1));
+    return o;
+  };
+  const size_t o_us = take(4 * U), o_ue = take(4 * U), o_bo = take(4 * M), o_co = take(4 * M), o_so = take(4 * M);
+  const size_t o_bi = take(8 * M), o_ln = take(4 * M), o_hi = take(4 * M), o_hd = take(4 * (M + 1));
+  const size_t o_ch = take(4 * (M + 1)), o_c = take(4 * M), o_mg = take(sizeof(tpc_track) * M), o_n = take(8);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, off) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, TPC_ENOMEM, "merge buffers of %zu bytes", off);
+  }
+  char* b = (char*)mem;
+  ctx->merge_mem = mem;
+  ctx->merge_tracks_cap = M;
+  ctx->merge_units_cap = U;
+  MergeBuf& m = ctx->mb;
+  m.u_start = (int32_t*)(b + o_us);
+  m.u_end = (int32_t*)(b + o_ue);
+  m.best_out = (int32_t*)(b + o_bo);
+  m.chi2_out = (float*)(b + o_co);
+  m.second_out = (float*)(b + o_so);
+  m.best_in = (unsigned long long*)(b + o_bi);
+  m.link = (int32_t*)(b + o_ln);
+  m.has_inner = (int32_t*)(b + o_hi);
+  m.head = (int32_t*)(b + o_hd);
+  m.chain_of_head = (int32_t*)(b + o_ch);
+  m.chain = (int32_t*)(b + o_c);
+  m.merged = (tpc_track*)(b + o_mg);
+  m.n = (int32_t*)(b + o_n);
+  if (!ctx->h_merge_n && cudaMallocHost(&ctx->h_merge_n, 8) != cudaSuccess) return fail(ctx, TPC_ECUDA, "pinned buffer");
+  return TPC_OK;
+}
+}  // namespace
+
+int tpc_merge_tracks(tpc_ctx* ctx, const tpc_merge_config* cfg_in) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->fitted) return fail(ctx, TPC_EINVAL, "tpc_fit_tracks has not run");
+  tpc_merge_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else tpc_default_merge_config(&cfg);
+  if (!(cfg.chi2_max > 0) || cfg.overlap_rows < 0 || cfg.min_clusters < 0)
+    return fail(ctx, TPC_EINVAL, "bad merge configuration");
+  CK(cudaSetDevice(ctx->device));
+  int rc = merge_reserve(ctx);
+  if (rc) return rc;
+  MergeConst mc;
+  mc.chi2_max = (float)cfg.chi2_max;
+  mc.overlap = cfg.overlap_rows;
+  mc.min_clusters = cfg.min_clusters;
+  const MergeBuf& mb = ctx->mb;
+  cudaStream_t s = ctx->stream;
+  Counts* cn = ctx->ptr<Counts>(ctx->L.counts);
+  const tpc_track* tr = ctx->ptr<tpc_track>(ctx->L.tracks);
+  const int64_t M = ctx->caps.tracks, U = (int64_t)ctx->caps.req * NSEC;
+  const int bc = ctx->block_clusters, gM = grid_for(ctx, M, bc);
+  CK(cudaMemsetAsync(mb.u_start, 0xFF, 4 * U, s));
+  CK(cudaMemsetAsync(mb.u_end, 0, 4 * U, s));
+  CK(cudaMemsetAsync(mb.best_in, 0xFF, 8 * M, s));
+  CK(cudaMemsetAsync(mb.has_inner, 0, 4 * M, s));
+  CK(cudaMemsetAsync(mb.n, 0, 8, s));
+  k_merge_units<<<gM, bc, 0, s>>>(tr, mb, cn);
+  k_merge_pairs<<<grid_for(ctx, M, 128, 8), 128, 0, s>>>(tr, ctx->kc, mc, mb, cn);
+  k_merge_links<<<gM, bc, 0, s>>>(mb, cn);
+  k_merge_heads<<<gM, bc, 0, s>>>(mb, cn);
+  scan(ctx, mb.head, mb.chain_of_head, LenSrc{&cn->n_tracks, 0, 0}, mb.n);
+  k_merge_refit<<<grid_for(ctx, M, 128, 8), 128, 0, s>>>(tr, ctx->ptr<tpc_cluster>(ctx->L.in), refit_in(ctx),
+                                                         ctx->ptr<int32_t>(ctx->L.track_clusters), ctx->kc, mb, cn);
+  CK(cudaMemcpyAsync(ctx->h_merge_n, mb.n, 8, cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
+  ctx->merge_valid = true;
+  return TPC_OK;
+}
+
+int tpc_get_merged(tpc_ctx* ctx, tpc_track* out, int64_t cap, int64_t* n_out, int32_t* track_link,
+                   int32_t* track_chain, float* pair_chi2, float* pair_second) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->merge_valid) return fail(ctx, TPC_EINVAL, "tpc_merge_tracks has not run");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_status(ctx);
+  if (rc) return rc;
+  const int32_t nm = ctx->h_merge_n[0];
+  const int64_t M = ctx->h_counts->n_tracks;
+  if (n_out) *n_out = nm;
+  if (out && nm > cap) return fail(ctx, TPC_EOVERFLOW, "%d merged tracks do not fit cap %lld", nm, (long long)cap);
+  if (out && nm) CK(cudaMemcpy(out, ctx->mb.merged, sizeof(tpc_track) * nm, cudaMemcpyDeviceToHost));
+  if (track_link && M) CK(cudaMemcpy(track_link, ctx->mb.link, 4 * M, cudaMemcpyDeviceToHost));
+  if (track_chain && M) CK(cudaMemcpy(track_chain, ctx->mb.chain, 4 * M, cudaMemcpyDeviceToHost));
+  if (pair_chi2 && M) CK(cudaMemcpy(pair_chi2, ctx->mb.chi2_out, 4 * M, cudaMemcpyDeviceToHost));
+  if (pair_second && M) CK(cudaMemcpy(pair_second, ctx->mb.second_out, 4 * M, cudaMemcpyDeviceToHost));
   return TPC_OK;
 }
 
