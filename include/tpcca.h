@@ -402,9 +402,10 @@ int tpc_decompress(tpc_ctx *ctx, const tpc_codec_header *heads, int64_t n_tracks
  * segment A and an outer segment B in neighbouring sectors of one side
  * (A's first row below B's, A's last row at most overlap_rows past B's first)
  * are compared at B's first row -- A's fitted state and covariance turned
- * into B's frame and carried there; chi2 = d^T (C_A + C_B)^-1 d over the five
- * parameters; a pair within chi2_max that is the best choice of both is
- * merged.  Chains of merges are refitted from the outermost segment's refit
+ * into B's frame and carried there; if their z there differ by at most
+ * window_cm (a bound that lets the search visit only segments near the
+ * predicted z), chi2 = d^T (C_A + C_B)^-1 d over the five parameters; a pair
+ * within chi2_max that is the best choice of both is merged.  Chains of merges are refitted from the outermost segment's refit
  * seed inward over all their clusters, the frame turned between segments
  * (the FP64 zone as in the refit); a merged track is given at its innermost
  * cluster in the innermost segment's frame.  Segments with a failed refit or
@@ -413,7 +414,7 @@ typedef struct {
   double chi2_max;      /* 25 */
   int32_t overlap_rows; /* 10 */
   int32_t min_clusters; /* 10 */
-  int64_t reserved;
+  double window_cm;     /* 10; 1e-3 .. 1e6 */
 } tpc_merge_config;
 
 int tpc_default_merge_config(tpc_merge_config *cfg);

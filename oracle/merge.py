@@ -26,7 +26,7 @@ def _bind():
     if not _bound:
         P = ctypes.c_void_p
         lib.orc_merge_pairs.argtypes = [P, ctypes.c_int32] + [P] * 7 + [ctypes.c_double, ctypes.c_int32,
-                                                                         ctypes.c_int32, P, P, P, P]
+                                                                         ctypes.c_int32, ctypes.c_double, P, P, P, P]
         lib.orc_merge_pairs.restype = ctypes.c_int
         lib.orc_merge_refit.argtypes = [P, ctypes.c_int32, P, P, P, P, P, ctypes.c_int32, P, P, P, P, P]
         lib.orc_merge_refit.restype = ctypes.c_int
@@ -35,7 +35,7 @@ def _bind():
 
 
 def default_params(**kw) -> dict:
-    p = {"chi2_max": 25.0, "overlap": 10, "min_clusters": 10}
+    p = {"chi2_max": 25.0, "overlap": 10, "min_clusters": 10, "window_cm": 10.0}
     p.update(kw)
     return p
 
@@ -65,7 +65,7 @@ def pairs(seg: dict, p: dict | None = None) -> dict:
     if n:
         lib.orc_merge_pairs(None, n, c(seg["request"]), c(seg["sector"]), c(seg["row_in"]), c(seg["row_out"]),
                             c(ncl), c(seg["par"]), c(seg["cov"]), p["chi2_max"], p["overlap"], p["min_clusters"],
-                            link.ctypes.data, chi2.ctypes.data, second.ctypes.data, second_in.ctypes.data)
+                            p["window_cm"], link.ctypes.data, chi2.ctypes.data, second.ctypes.data, second_in.ctypes.data)
     return {"link": link, "chi2": chi2, "second": second, "second_in": second_in}
 
 

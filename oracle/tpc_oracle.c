@@ -964,7 +964,10 @@ void orc_quantise(int64_t n, const float *v, double unit, int32_t *q) {
      clusters;
    - an inner segment A (sector s) and an outer segment B (sector s' = s +-1
      on the same side, A.row_out <= B.row_in + overlap) are compared at B's
-     innermost row: A's state is turned into B's frame and carried there,
+     innermost row: A's state is turned into B's frame and carried there;
+     the pair is a candidate if the z of the two there differ by at most
+     window_cm (a bound far wider than any true pair's residual: it lets a
+     tracker look only at segments near the predicted z), and then
      chi2 = d^T (C_A + C_B)^-1 d over the five parameters; a pair with
      chi2 <= chi2_max that is the best of both A's and B's candidates is
      merged (chains follow the merges);
@@ -1035,9 +1038,10 @@ static void unpack_cov(const double *c15, double C[5][5]) {
     for (int j = 0; j <= i; j++, q++) C[i][j] = C[j][i] = c15[q];
 }
 
-/* Pair chi2 of inner segment a with outer segment b (-1: not comparable). */
+/* Pair chi2 of inner segment a with outer segment b (-1: not comparable,
+   or their z at b's first row further apart than window_cm). */
 static double pair_chi2(const kctx *k, const int32_t *sector, const int32_t *row_in, const double *par,
-                        const double *cov, int a, int b) {
+                        const double *cov, int a, int b, double window_cm) {
   kstate s;
   int flags = 0;
   s.x = X32[row_in[a]];
@@ -1045,6 +1049,7 @@ static double pair_chi2(const kctx *k, const int32_t *sector, const int32_t *row
   unpack_cov(cov + 15 * (int64_t)a, s.C);
   if (!rotate(&s, sector_angle(sector[b]) - sector_angle(sector[a]))) return -1.0;
   if (!carry_to(k, &s, X32[row_in[b]], &flags)) return -1.0;
+  if (!(fabs(s.p[1] - par[5 * (int64_t)b + 1]) <= window_cm)) return -1.0;
   double d[5], Cb[5][5], S[5][5];
   unpack_cov(cov + 15 * (int64_t)b, Cb);
   for (int i = 0; i < 5; i++) {
@@ -1066,7 +1071,8 @@ static int adjacent(int s1, int s2) {
    (-1: none).  Segments: n_tracks, with request, sector, rows, state. */
 int orc_merge_pairs(const orc_config *cfg_in, int32_t n, const int32_t *request, const int32_t *sector,
                     const int32_t *row_in, const int32_t *row_out, const int32_t *n_clusters, const double *par,
-                    const double *cov, double chi2_max, int32_t overlap, int32_t min_clusters, int32_t *out_link,
+                    const double *cov, double chi2_max, int32_t overlap, int32_t min_clusters, double window_cm,
+                    int32_t *out_link,
                     double *out_chi2, double *out_second, double *out_second_in) {
   orc_config cfg;
   if (cfg_in) cfg = *cfg_in; else orc_default_config(&cfg);
@@ -1092,7 +1098,7 @@ int orc_merge_pairs(const orc_config *cfg_in, int32_t n, const int32_t *request,
       if (b == a || request[b] != request[a] || n_clusters[b] < min_clusters) continue;
       if (!adjacent(sector[a], sector[b])) continue;
       if (!(row_in[a] < row_in[b] && row_out[a] <= row_in[b] + overlap)) continue; /* a inner, b outer */
-      const double c = pair_chi2(&k, sector, row_in, par, cov, a, b);
+      const double c = pair_chi2(&k, sector, row_in, par, cov, a, b, window_cm);
       if (c < 0 || c > chi2_max) continue;
       if (c < co[a] || (c == co[a] && b < bo[a])) {
         so[a] = fmin(so[a], co[a]);

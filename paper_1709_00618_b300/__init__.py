@@ -64,7 +64,7 @@ class VertexConfig(ctypes.Structure):
 
 class MergeConfig(ctypes.Structure):
     _fields_ = [("chi2_max", ctypes.c_double), ("overlap_rows", ctypes.c_int32), ("min_clusters", ctypes.c_int32),
-                ("reserved", ctypes.c_int64)]
+                ("window_cm", ctypes.c_double)]
 
 
 CODEC_HEADER_DTYPE = np.dtype([("par", "<f4", (5,)), ("row_out", "<i4"), ("n_clusters", "<i4"), ("ok", "<i4")])

@@ -2,11 +2,15 @@
 // are merged and the merged tracks refitted.  An inner segment A and an
 // outer segment B in neighbouring sectors of one side are compared at B's
 // first row: A's fitted state and covariance are turned into B's frame and
-// carried there; chi2 = d^T (C_A + C_B)^-1 d over the five parameters.  A
-// pair within chi2_max that is the best choice of both A and B is merged;
-// chains of merges are refitted from the outermost segment's seed inward,
-// the frame turned between segments.  One thread per segment (pairing) and
-// per chain (refit).
+// carried there; if their z there lie within the window, chi2 = d^T (C_A +
+// C_B)^-1 d over the five parameters.  A pair within chi2_max that is the
+// best choice of both A and B is merged; chains of merges are refitted from
+// the outermost segment's seed inward, the frame turned between segments.
+// Candidates: the segments of every (request, sector) are binned by the z
+// of their first row (bins one window wide, hashed into a power-of-two
+// count); a warp per segment A carries A over the rows a partner can start
+// on, and scans only the bins of the z range it sweeps (plus the window).
+// The refit is one thread per chain.
 #pragma once
 #include "kalman.cuh"
 
@@ -17,11 +21,25 @@ constexpr int MERGE_MAX_SEG = 8;  // segments per chain (a longer chain is cut)
 struct MergeConst {
   float chi2_max;
   int32_t overlap, min_clusters;
+  float window, inv_window;  // z window at B's first row (cm) and its inverse
+  int32_t nz_mask;           // z bins per unit - 1 (a power of two minus one)
 };
 
+// A segment in its (unit, z bin) cell: the fields the candidate tests read.
+struct MergeKey {
+  int32_t m;      // track index
+  int32_t rows;   // first_row | last_row << 16
+  float z, t, q;  // at the first row
+  float vt, vq;   // their variances
+  int32_t pad;
+};
+static_assert(sizeof(MergeKey) == 32, "one 32-byte sector per key");
+
 struct MergeBuf {
-  int32_t* u_start;               // [units] first track of each (request, sector), -1: none
-  int32_t* u_end;                 // [units]
+  int32_t* cell;                  // [M] cell of each segment, -1: takes no part
+  int32_t* cell_cnt;              // [units * bins] segments per cell (then the fill cursor)
+  int32_t* cell_start;            // [units * bins + 1] exclusive scan
+  MergeKey* keys;                 // [M] segments grouped by cell
   int32_t* best_out;              // [M] A's best outer partner
   float* chi2_out;                // [M] its chi2
   float* second_out;              // [M] A's second-best chi2 (for near ties)
@@ -91,14 +109,50 @@ __device__ __forceinline__ bool rotate_state(TrkState& p, T* C, float beta) {
   return true;
 }
 
-// Unit ranges: tracks are ordered by (request, sector).
-__global__ void k_merge_units(const tpc_track* __restrict__ tr, MergeBuf mb, const Counts* cn) {
+// z bin of a first-row z (clamped so the integer conversion is defined).
+__device__ __forceinline__ int64_t merge_zbin(float z, const MergeConst& mc) {
+  return (int64_t)floorf(fminf(fmaxf(z * mc.inv_window, -1e15f), 1e15f));
+}
+
+__device__ __forceinline__ bool merge_eligible(const tpc_track& T, const MergeConst& mc) {
+  return !(T.flags & TF_REFIT_FAIL) && T.n_clusters >= mc.min_clusters && isfinite(T.par[1]);
+}
+
+// Cells: every taking-part segment counted in its (request, sector, z bin).
+__global__ void k_merge_cells(const tpc_track* __restrict__ tr, MergeConst mc, MergeBuf mb, const Counts* cn) {
   if (fatal(cn)) return;
   const int32_t M = cn->n_tracks;
   for (int64_t m = gtid(); m < M; m += gstride()) {
-    const int u = tr[m].request * NSEC + tr[m].sector;
-    if (m == 0 || tr[m - 1].request * NSEC + tr[m - 1].sector != u) mb.u_start[u] = (int32_t)m;
-    if (m == M - 1 || tr[m + 1].request * NSEC + tr[m + 1].sector != u) mb.u_end[u] = (int32_t)m + 1;
+    const tpc_track T = tr[m];
+    int32_t c = -1;
+    if (merge_eligible(T, mc)) {
+      const int64_t u = (int64_t)T.request * NSEC + T.sector;
+      c = (int32_t)(u * (mc.nz_mask + 1) + (merge_zbin(T.par[1], mc) & mc.nz_mask));
+      atomicAdd(&mb.cell_cnt[c], 1);
+    }
+    mb.cell[m] = c;
+  }
+}
+
+// Keys grouped by cell (the order inside a cell is arbitrary: the pairing
+// below does not depend on it).
+__global__ void k_merge_scatter(const tpc_track* __restrict__ tr, MergeBuf mb, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int32_t M = cn->n_tracks;
+  for (int64_t m = gtid(); m < M; m += gstride()) {
+    const int32_t c = mb.cell[m];
+    if (c < 0) continue;
+    const tpc_track T = tr[m];
+    MergeKey k;
+    k.m = (int32_t)m;
+    k.rows = T.first_row | (T.last_row << 16);
+    k.z = T.par[1];
+    k.t = T.par[3];
+    k.q = T.par[4];
+    k.vt = T.cov[TPC_CI(3, 3)];
+    k.vq = T.cov[TPC_CI(4, 4)];
+    k.pad = 0;
+    mb.keys[mb.cell_start[c] + atomicSub(&mb.cell_cnt[c], 1) - 1] = k;
   }
 }
 
@@ -131,9 +185,26 @@ __device__ __forceinline__ float chi2_5(const float d[5], float S[15]) {
   return c;
 }
 
-// Pairing: per segment A its best outer partner and the second-best chi2;
-// per segment B its best inner partner (packed atomic minimum).
-__global__ void __launch_bounds__(128) k_merge_pairs(const tpc_track* __restrict__ tr, KConst kc, MergeConst mc,
+// Candidate (best, second) of one lane, merged across the warp: the best is
+// the least (chi2, index); the second the least of the rest.
+__device__ __forceinline__ void pick_merge(float& bc, int32_t& best, float& sc, float c, int32_t b) {
+  if (c < bc || (c == bc && b < best)) {
+    sc = fminf(sc, bc);
+    bc = c;
+    best = b;
+  } else {
+    sc = fminf(sc, c);
+  }
+}
+
+// Pairing: per segment A (one warp) its best outer partner and the
+// second-best chi2; per segment B its best inner partner (packed atomic
+// minimum).  Before the full chi2, a candidate must start on a row A may
+// meet, lie in the z range A sweeps over those rows (widened by the window),
+// and pass two exact bounds of the chi2: dz/ds_T and q/pT do not change when
+// A is turned and carried, and neither do their variances, so chi2 >=
+// d_t^2/(V_t,A + V_t,B) and the same for q/pT (taken with a 10% margin).
+__global__ void __launch_bounds__(256) k_merge_pairs(const tpc_track* __restrict__ tr, KConst kc, MergeConst mc,
                                                      MergeBuf mb, const Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
@@ -141,50 +212,93 @@ __global__ void __launch_bounds__(128) k_merge_pairs(const tpc_track* __restrict
   if (fatal(cn)) return;
   const int32_t M = cn->n_tracks;
   const float inf = __int_as_float(0x7F800000);
-  for (int64_t a = gtid(); a < M; a += gstride()) {
+  const int lane = threadIdx.x & 31;
+  const float cut = 1.1f * mc.chi2_max;
+  for (int64_t a = gtid() >> 5; a < M; a += gstride() >> 5) {
     const tpc_track A = tr[a];
     int32_t best = -1;
     float bc = inf, sc = inf;
-    if (!(A.flags & TF_REFIT_FAIL) && A.n_clusters >= mc.min_clusters) {
+    if (merge_eligible(A, mc)) {
       const int side = A.sector / 18, sa = A.sector % 18;
-      for (int k = 0; k < 2; k++) {
+      const int lo = max(A.first_row + 1, A.last_row - mc.overlap);
+      const float vtA = A.cov[TPC_CI(3, 3)], vqA = A.cov[TPC_CI(4, 4)];
+      for (int k = 0; k < 2 && lo < NROW; k++) {
         const int sb = side * 18 + (sa + (k ? 17 : 1)) % 18;
-        const int u = A.request * NSEC + sb;
-        const int b0 = mb.u_start[u], b1 = mb.u_end[u];
-        for (int b = b0; b >= 0 && b < b1; b++) {
-          const tpc_track B = tr[b];
-          if ((B.flags & TF_REFIT_FAIL) || B.n_clusters < mc.min_clusters) continue;
-          if (!(A.first_row < B.first_row && A.last_row <= B.first_row + mc.overlap)) continue;
-          TrkState p;
-          seed_state(p, A.first_row, sX[A.first_row], A.par[0], A.par[1], A.par[2], A.par[3], A.par[4]);
-          float C[15];
+        const int64_t u = (int64_t)A.request * NSEC + sb;
+        TrkState p0;
+        seed_state(p0, A.first_row, sX[A.first_row], A.par[0], A.par[1], A.par[2], A.par[3], A.par[4]);
+        float C0[15];
 #pragma unroll
-          for (int i = 0; i < 15; i++) C[i] = A.cov[i];
+        for (int i = 0; i < 15; i++) C0[i] = A.cov[i];
+        if (!rotate_state<float>(p0, C0, sector_angle(sb) - sector_angle(A.sector))) continue;  // warp-uniform
+        // the z A reaches on the rows lo..NROW-1 of B's sector
+        float zmin = inf, zmax = -inf;
+        for (int r = lo + lane; r < NROW; r += 32) {
+          TrkState p = p0;
           uint32_t flags = 0;
-          if (!rotate_state<float>(p, C, sector_angle(B.sector) - sector_angle(A.sector))) continue;
-          Jac J;
-          if (!prop_state(p, B.first_row, sX[B.first_row], kc, flags, &J)) continue;
-          cov_transport<float>(C, J.j02, J.j04, J.j24, J.j12, J.j13, J.j14);
-          const float d[5] = {(p.y + p.yl) - B.par[0], (p.zref + (p.z + p.zl)) - B.par[1], (p.s + p.sl) - B.par[2],
-                              p.t - B.par[3], p.q - B.par[4]};
-#pragma unroll
-          for (int i = 0; i < 15; i++) C[i] += B.cov[i];
-          const float c = chi2_5(d, C);
-          if (!(c >= 0.0f) || !(c <= mc.chi2_max)) continue;
-          if (c < bc || (c == bc && b < best)) {
-            sc = fminf(sc, bc);
-            bc = c;
-            best = b;
-          } else {
-            sc = fminf(sc, c);
+          if (prop_state(p, r, sX[r], kc, flags, nullptr)) {
+            const float z = p.zref + (p.z + p.zl);
+            zmin = fminf(zmin, z);
+            zmax = fmaxf(zmax, z);
           }
-          atomicMin(&mb.best_in[b], ((unsigned long long)__float_as_uint(c) << 32) | (unsigned long long)a);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          zmin = fminf(zmin, __shfl_xor_sync(FULL_MASK, zmin, o));
+          zmax = fmaxf(zmax, __shfl_xor_sync(FULL_MASK, zmax, o));
+        }
+        if (!(zmin <= zmax)) continue;  // no row reachable
+        const float margin = 0.01f + 1e-5f * fmaxf(fabsf(zmin), fabsf(zmax));
+        const float zlo = zmin - mc.window - margin, zhi = zmax + mc.window + margin;
+        int64_t b0 = merge_zbin(zlo, mc), nb = merge_zbin(zhi, mc) - b0 + 1;
+        if (nb > mc.nz_mask) {
+          b0 = 0;
+          nb = mc.nz_mask + 1;
+        }
+        for (int64_t i = 0; i < nb; i++) {
+          const int64_t c = u * (mc.nz_mask + 1) + ((b0 + i) & mc.nz_mask);
+          const int32_t e1 = mb.cell_start[c + 1];
+          for (int32_t e = mb.cell_start[c] + lane; e < e1; e += 32) {
+            const MergeKey K = mb.keys[e];
+            const int rin = K.rows & 0xFFFF;
+            if (rin < lo || !(K.z >= zlo && K.z <= zhi)) continue;
+            const float dt = A.par[3] - K.t, dq = A.par[4] - K.q;
+            if (dt * dt > cut * (vtA + K.vt) || dq * dq > cut * (vqA + K.vq)) continue;
+            const int32_t b = K.m;
+            const tpc_track B = tr[b];
+            TrkState p = p0;
+            float C[15];
+#pragma unroll
+            for (int q = 0; q < 15; q++) C[q] = C0[q];
+            uint32_t flags = 0;
+            Jac J;
+            if (!prop_state(p, B.first_row, sX[B.first_row], kc, flags, &J)) continue;
+            const float d[5] = {(p.y + p.yl) - B.par[0], (p.zref + (p.z + p.zl)) - B.par[1],
+                                (p.s + p.sl) - B.par[2], p.t - B.par[3], p.q - B.par[4]};
+            if (!(fabsf(d[1]) <= mc.window)) continue;
+            cov_transport<float>(C, J.j02, J.j04, J.j24, J.j12, J.j13, J.j14);
+#pragma unroll
+            for (int q = 0; q < 15; q++) C[q] += B.cov[q];
+            const float c2 = chi2_5(d, C);
+            if (!(c2 >= 0.0f) || !(c2 <= mc.chi2_max)) continue;
+            pick_merge(bc, best, sc, c2, b);
+            atomicMin(&mb.best_in[b], ((unsigned long long)__float_as_uint(c2) << 32) | (unsigned long long)a);
+          }
         }
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oc = __shfl_xor_sync(FULL_MASK, bc, o), os = __shfl_xor_sync(FULL_MASK, sc, o);
+        const int32_t ob = __shfl_xor_sync(FULL_MASK, best, o);
+        sc = fminf(sc, os);
+        pick_merge(bc, best, sc, oc, ob);
+      }
     }
-    mb.best_out[a] = best;
-    mb.chi2_out[a] = bc;
-    mb.second_out[a] = sc;
+    if (lane == 0) {
+      mb.best_out[a] = best;
+      mb.chi2_out[a] = bc;
+      mb.second_out[a] = sc;
+    }
   }
 }
 

@@ -220,7 +220,7 @@ struct tpc_ctx {
   bool codec_valid = false;
   // sector merging (tpc_merge_tracks): own buffer
   void* merge_mem = nullptr;
-  int64_t merge_tracks_cap = 0, merge_units_cap = 0;
+  int64_t merge_tracks_cap = 0, merge_cells_cap = 0;
   MergeBuf mb{};
   int32_t* h_merge_n = nullptr;  // pinned: merged tracks
   bool merge_valid = false;
@@ -1487,14 +1487,24 @@ int tpc_default_merge_config(tpc_merge_config* c) {
   c->chi2_max = 25.0;
   c->overlap_rows = 10;
   c->min_clusters = 10;
-  c->reserved = 0;
+  c->window_cm = 10.0;
   return TPC_OK;
 }
 
 namespace {
+// z bins per (request, sector) unit: about a quarter of the segments a unit
+// can hold, a power of two in [16, 4096].
+int64_t merge_zbins(const tpc_ctx* ctx) {
+  const int64_t M = std::max<int64_t>(ctx->caps.tracks, 1), U = (int64_t)std::max(ctx->caps.req, 1) * NSEC;
+  int64_t nz = 16;
+  while (nz < 4096 && nz * 4 * U < M) nz *= 2;
+  return nz;
+}
+
 int merge_reserve(tpc_ctx* ctx) {
   const int64_t M = std::max<int64_t>(ctx->caps.tracks, 1), U = (int64_t)std::max(ctx->caps.req, 1) * NSEC;
-  if (ctx->merge_mem && ctx->merge_tracks_cap >= M && ctx->merge_units_cap >= U) return TPC_OK;
+  const int64_t cells = U * merge_zbins(ctx);
+  if (ctx->merge_mem && ctx->merge_tracks_cap >= M && ctx->merge_cells_cap >= cells) return TPC_OK;
   if (ctx->merge_mem) {
     CK(cudaStreamSynchronize(ctx->stream));
     cudaFree(ctx->merge_mem);
@@ -1506,7 +1516,8 @@ int merge_reserve(tpc_ctx* ctx) {
     off = align_up(off + std::max<size_t>(bytes, 1));
     return o;
   };
-  const size_t o_us = take(4 * U), o_ue = take(4 * U), o_bo = take(4 * M), o_co = take(4 * M), o_so = take(4 * M);
+  const size_t o_cl = take(4 * M), o_cc = take(4 * cells), o_cs = take(4 * (cells + 1));
+  const size_t o_ky = take(sizeof(MergeKey) * M), o_bo = take(4 * M), o_co = take(4 * M), o_so = take(4 * M);
   const size_t o_bi = take(8 * M), o_ln = take(4 * M), o_hi = take(4 * M), o_hd = take(4 * (M + 1));
   const size_t o_ch = take(4 * (M + 1)), o_c = take(4 * M), o_mg = take(sizeof(tpc_track) * M), o_n = take(8);
   void* mem = nullptr;
@@ -1517,10 +1528,12 @@ int merge_reserve(tpc_ctx* ctx) {
   char* b = (char*)mem;
   ctx->merge_mem = mem;
   ctx->merge_tracks_cap = M;
-  ctx->merge_units_cap = U;
+  ctx->merge_cells_cap = cells;
   MergeBuf& m = ctx->mb;
-  m.u_start = (int32_t*)(b + o_us);
-  m.u_end = (int32_t*)(b + o_ue);
+  m.cell = (int32_t*)(b + o_cl);
+  m.cell_cnt = (int32_t*)(b + o_cc);
+  m.cell_start = (int32_t*)(b + o_cs);
+  m.keys = (MergeKey*)(b + o_ky);
   m.best_out = (int32_t*)(b + o_bo);
   m.chi2_out = (float*)(b + o_co);
   m.second_out = (float*)(b + o_so);
@@ -1543,7 +1556,8 @@ int tpc_merge_tracks(tpc_ctx* ctx, const tpc_merge_config* cfg_in) {
   tpc_merge_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else tpc_default_merge_config(&cfg);
-  if (!(cfg.chi2_max > 0) || cfg.overlap_rows < 0 || cfg.min_clusters < 0)
+  if (!(cfg.chi2_max > 0) || cfg.overlap_rows < 0 || cfg.min_clusters < 0 ||
+      !(cfg.window_cm >= 1e-3 && cfg.window_cm <= 1e6))
     return fail(ctx, TPC_EINVAL, "bad merge configuration");
   CK(cudaSetDevice(ctx->device));
   int rc = merge_reserve(ctx);
@@ -1552,19 +1566,25 @@ int tpc_merge_tracks(tpc_ctx* ctx, const tpc_merge_config* cfg_in) {
   mc.chi2_max = (float)cfg.chi2_max;
   mc.overlap = cfg.overlap_rows;
   mc.min_clusters = cfg.min_clusters;
+  mc.window = (float)cfg.window_cm;
+  mc.inv_window = 1.0f / mc.window;
+  const int64_t nz = merge_zbins(ctx);
+  mc.nz_mask = (int32_t)(nz - 1);
   const MergeBuf& mb = ctx->mb;
   cudaStream_t s = ctx->stream;
   Counts* cn = ctx->ptr<Counts>(ctx->L.counts);
   const tpc_track* tr = ctx->ptr<tpc_track>(ctx->L.tracks);
   const int64_t M = ctx->caps.tracks, U = (int64_t)ctx->caps.req * NSEC;
   const int bc = ctx->block_clusters, gM = grid_for(ctx, M, bc);
-  CK(cudaMemsetAsync(mb.u_start, 0xFF, 4 * U, s));
-  CK(cudaMemsetAsync(mb.u_end, 0, 4 * U, s));
+  const int64_t cells = U * nz;
+  CK(cudaMemsetAsync(mb.cell_cnt, 0, 4 * cells, s));
   CK(cudaMemsetAsync(mb.best_in, 0xFF, 8 * M, s));
   CK(cudaMemsetAsync(mb.has_inner, 0, 4 * M, s));
   CK(cudaMemsetAsync(mb.n, 0, 8, s));
-  k_merge_units<<<gM, bc, 0, s>>>(tr, mb, cn);
-  k_merge_pairs<<<grid_for(ctx, M, 128, 8), 128, 0, s>>>(tr, ctx->kc, mc, mb, cn);
+  k_merge_cells<<<gM, bc, 0, s>>>(tr, mc, mb, cn);
+  scan(ctx, mb.cell_cnt, mb.cell_start, LenSrc{nullptr, cells, 0}, nullptr);
+  k_merge_scatter<<<gM, bc, 0, s>>>(tr, mb, cn);
+  k_merge_pairs<<<grid_for(ctx, M * 32, 256, 8), 256, 0, s>>>(tr, ctx->kc, mc, mb, cn);
   k_merge_links<<<gM, bc, 0, s>>>(mb, cn);
   k_merge_heads<<<gM, bc, 0, s>>>(mb, cn);
   scan(ctx, mb.head, mb.chain_of_head, LenSrc{&cn->n_tracks, 0, 0}, mb.n);

@@ -2,7 +2,8 @@
 noiseless helix split over two sectors is refitted to its true parameters
 across the frame turn; on a smeared event the segments of one track in
 neighbouring sectors are merged (and of different tracks are not); the pair
-chi2 of true pairs follows five degrees of freedom."""
+chi2 of true pairs follows five degrees of freedom; the z window at the
+partner's first row only prunes (it changes no choice)."""
 import numpy as np
 import pytest
 
@@ -99,3 +100,19 @@ def test_merged_refit_matches_its_pieces(smeared):
         sig = np.sqrt(np.abs(seg["cov"][inner][[0, 2, 5, 9, 14]]))
         assert np.all(np.abs(mg["par"][k] - seg["par"][inner]) <= 5 * sig + 1e-6)
         assert np.all(np.sqrt(np.abs(mg["cov"][k][[0, 2, 5, 9, 14]])) <= sig * (1 + 1e-6))
+
+
+def test_z_window_only_prunes(smeared):
+    """A pair within the chi2 cut has |dz| <= 5 sigma_z at the partner's
+    first row, far inside the 10 cm window: pairing without the window, or
+    with a window of 2 cm, makes the same choices with the same chi2."""
+    ev, ref, mg = smeared
+    seg = mg["segments"]
+    wide = merge.pairs(seg, {"window_cm": 1e9})
+    narrow = merge.pairs(seg, {"window_cm": 2.0})
+    for other in (wide, narrow):
+        assert np.array_equal(other["link"], mg["link"])
+        assert np.array_equal(other["chi2"], mg["pair_chi2"])
+    # and a window below the residuals does cut true pairs
+    tiny = merge.pairs(seg, {"window_cm": 1e-3})
+    assert (tiny["link"] >= 0).sum() < 0.1 * (mg["link"] >= 0).sum()
