@@ -13,8 +13,10 @@ step, in FP64 with numpy:
    z_t there is v_d * t_coll + z_max for a track from a collision at z = 0,
    so t_est = (z_t(dca) - z_max) / v_d.
 2. A track takes part when |dca| <= dca_max, it has at least min_clusters
-   clusters and its extrapolation moves z_t by at most ext_max (no track
-   from the beam line crosses more than the drift length).
+   clusters, its extrapolation moves z_t by at most ext_max (no track
+   from the beam line crosses more than the drift length) and its pT is at
+   least min_pt (0: no cut; a cut above the looping momentum keeps the
+   further legs of loopers, whose times are shifted by whole turns, out).
 3. The participating tracks of a request, sorted by t_est, are cut wherever
    two neighbours are more than `gap` apart; a run of at least min_tracks
    tracks is a vertex, its time the mean t_est of its tracks.
@@ -35,7 +37,7 @@ NSEC = 36
 
 def default_params(**kw) -> dict:
     p = {"vdrift": 2.5, "zmax": 250.0, "dca_max": 2.0, "ext_max": 300.0, "gap": 0.5, "min_tracks": 3,
-         "min_clusters": 20, "bz_kg": 5.0}
+         "min_clusters": 20, "min_pt": 0.0, "bz_kg": 5.0}
     p.update(kw)
     return p
 
@@ -96,6 +98,8 @@ def find_vertices(x, par, n_clusters, sector, request, p: dict | None = None) ->
     with np.errstate(invalid="ignore"):
         use = (dca <= p["dca_max"]) & (np.asarray(n_clusters) >= p["min_clusters"]) & np.isfinite(t_est)
         use &= np.abs(dzt) <= p["ext_max"]
+        if p["min_pt"] > 0:
+            use &= np.abs(par[:, 4]) * p["min_pt"] <= 1.0
     vid = np.full(m, -1, np.int64)
     v_req, v_time, v_n, v_margin = [], [], [], []
     request = np.asarray(request)
@@ -126,6 +130,8 @@ def find_vertices(x, par, n_clusters, sector, request, p: dict | None = None) ->
     tgl = np.where(vid >= 0, tgl, np.nan)
     with np.errstate(invalid="ignore"):
         use_margin = np.minimum(np.abs(dca - p["dca_max"]), np.abs(np.abs(dzt) - p["ext_max"]))
+        if p["min_pt"] > 0:  # relative distance of pT from the cut
+            use_margin = np.minimum(use_margin, np.abs(np.abs(par[:, 4]) * p["min_pt"] - 1.0))
     return {"t_est": t_est, "dca": dca, "use": use, "use_margin": use_margin, "vertex": vid, "z": z, "tgl": tgl,
             "v_request": np.asarray(v_req, np.int64), "v_time": v_time, "v_n": np.asarray(v_n, np.int64),
             "v_margin": np.asarray(v_margin, np.float64)}

@@ -37,7 +37,7 @@ class _Params(ctypes.Structure):
                 ("row_eff", ctypes.c_double), ("noise_frac", ctypes.c_double), ("bz_kg", ctypes.c_double),
                 ("timeframe", ctypes.c_int32), ("tf_length_us", ctypes.c_double), ("rate_khz", ctypes.c_double),
                 ("vdrift", ctypes.c_double), ("mb_offset", ctypes.c_double), ("mb_max", ctypes.c_double),
-                ("n_threads", ctypes.c_int32)]
+                ("n_threads", ctypes.c_int32), ("legs", ctypes.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -97,6 +97,7 @@ class GenParams:
     mb_offset: float = 50.0
     mb_max: float = 8000.0
     n_threads: int = field(default_factory=lambda: min(os.cpu_count() or 1, 32))
+    legs: int = 1  # half-turns of a looper (1: only the first outgoing one)
 
     def _c(self) -> _Params:
         mask = 0
@@ -105,7 +106,7 @@ class GenParams:
         return _Params(self.seed, self.n_primaries, self.n_secondaries, self.pt_min, self.pt_max, self.eta_max,
                        self.phi_min, self.phi_max, self.phi_radius, self.sec_r_max, mask, self.sigma_y, self.sigma_z, self.row_eff,
                        self.noise_frac, self.bz_kg, int(self.timeframe), self.tf_length_us, self.rate_khz,
-                       self.vdrift, self.mb_offset, self.mb_max, self.n_threads)
+                       self.vdrift, self.mb_offset, self.mb_max, self.n_threads, self.legs)
 
 
 @dataclass
@@ -185,6 +186,20 @@ def central_event(seed: int = 1, n_primaries: int = 8000, n_secondaries: int = 1
                   **kw) -> Event:
     """Plain method, full TPC: one central Pb-Pb-like event (~1.3M clusters)."""
     p = GenParams(seed=seed, n_primaries=n_primaries, n_secondaries=n_secondaries)
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return generate(p, truth=truth)
+
+
+def looper_event(seed: int = 1, n_primaries: int = 16000, n_secondaries: int = 4000, truth: bool = False,
+                 **kw) -> Event:
+    """A central event in full acceptance for cluster rejection (~1.06M
+    clusters): |eta| < 1.5, pT from 40 MeV/c (the p^-3 spectrum), secondaries
+    born anywhere inside the outermost row radius (low-momentum ones among
+    them), and loopers followed for four half-turns; about half of the
+    clusters sit on further looper legs, below 50 MeV/c or at |dz/ds_T| > 2."""
+    p = GenParams(seed=seed, n_primaries=n_primaries, n_secondaries=n_secondaries, eta_max=1.5, pt_min=0.04,
+                  sec_r_max=200.0, legs=4)
     for k, v in kw.items():
         setattr(p, k, v)
     return generate(p, truth=truth)

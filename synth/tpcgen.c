@@ -29,7 +29,7 @@ typedef struct {
 
 typedef struct {
   int32_t track;  /* track label, -1 for noise */
-  int32_t flags;  /* bit0: local x decreases along the track at this crossing */
+  int32_t flags;  /* bit0: local x decreases along the track at this crossing; bits 1+: the leg */
   double y, z;    /* exact (unsmeared) local position; z in the stored coordinate */
   double sphi;    /* sin of the local direction angle */
   double tgl;     /* dz/ds_T in the stored z coordinate */
@@ -59,6 +59,7 @@ typedef struct {
   double mb_offset; /* track count density ~ 1/(N + mb_offset) */
   double mb_max;    /* on [0, mb_max] */
   int32_t n_threads;
+  int32_t legs; /* half-turns of a looper (a circle inside the outermost row radius); 1: the first */
 } gen_params;
 
 #define NROWS 159
@@ -135,8 +136,11 @@ static void sample_track(const gen_params *p, int64_t i, int secondary, double t
 
 /*
  * All row-plane crossings of one track inside the first outgoing half-turn
- * (from the vertex to the point of the circle farthest from the beam axis).
- * If out != NULL the clusters (and truth) are written; returns the count.
+ * (from the vertex to the point of the circle farthest from the beam axis)
+ * and, for a looper, inside legs-1 further half-turns (no energy loss: the
+ * particle stays on its helix).  The truth flags hold the leg (0: the first)
+ * in bits 1 and up.  If out != NULL the clusters (and truth) are written;
+ * returns the count.
  */
 static int64_t track_hits(const gen_params *p, const track_t *tr, int64_t label, gen_cluster *out,
                           gen_truth *truth) {
@@ -151,6 +155,9 @@ static int64_t track_hits(const gen_params *p, const track_t *tr, int64_t label,
   double period = 2.0 * PI * R;
   double phi_far = atan2(sgn * xc, -sgn * yc);
   double s_end = pmod((phi_far - tr->phi0) / kappa, period);
+  const int legs = (cn + R < X_LAST && p->legs > 1) ? p->legs : 1;
+  const double s_max = s_end + (legs - 1) * PI * R;
+  const int turns = (int)floor(s_max / period);
   uint64_t key = make_key(p->seed, DOM_HIT, (uint64_t)label);
   double tf_zmax = p->vdrift * p->tf_length_us;
   int64_t n = 0;
@@ -177,17 +184,19 @@ static int64_t track_hits(const gen_params *p, const track_t *tr, int64_t label,
       double A = xc * ca + yc * sa, B = -xc * sa + yc * ca;
       double w = kappa * (xr - A); /* sin of the local direction at the crossing */
       if (fabs(w) >= 1.0) continue;
-      for (int sol = 0; sol < 2; sol++) {
-        double ploc = sol ? PI - asin(w) : asin(w);
-        double s = pmod((alpha + ploc - tr->phi0) / kappa, period);
-        if (!(s > 0.0) || s > s_end) continue;
+      for (int sol = 0; sol < 2 * (turns + 1); sol++) {
+        const int j = sol >> 1; /* turn */
+        double ploc = (sol & 1) ? PI - asin(w) : asin(w);
+        double s = pmod((alpha + ploc - tr->phi0) / kappa, period) + j * period;
+        if (!(s > 0.0) || s > s_max) continue;
+        const int leg = s <= s_end ? 0 : 1 + (int)floor((s - s_end) / (PI * R));
         double yloc = B - cos(ploc) / kappa;
         if (fabs(yloc) > xr * TAN_HALF_SECTOR) continue;
         double z = tr->t * s;
         if (fabs(z) > ZMAX) continue;
         int sector = a + (z >= 0.0 ? 0 : NSEC_AZ);
         if (!((p->sector_mask >> sector) & 1ull)) continue;
-        uint64_t ctr = ((uint64_t)r * 64 + (uint64_t)a) * 2 + (uint64_t)sol;
+        uint64_t ctr = (((uint64_t)j * NROWS + (uint64_t)r) * 64 + (uint64_t)a) * 2 + (uint64_t)(sol & 1);
         if (uni(key, 8 * ctr) >= p->row_eff) continue;
         double zs = z, tgl = tr->t;
         if (p->timeframe) {
@@ -205,7 +214,7 @@ static int64_t track_hits(const gen_params *p, const track_t *tr, int64_t label,
           if (truth) {
             gen_truth *g = &truth[n];
             g->track = (int32_t)label;
-            g->flags = cos(ploc) < 0 ? 1 : 0;
+            g->flags = (cos(ploc) < 0 ? 1 : 0) | (leg << 1);
             g->y = yloc;
             g->z = zs;
             g->sphi = w;
