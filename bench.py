@@ -363,7 +363,67 @@ def all_configs(local):
             rows[name]["track_model_compression"] = codec
         if merged is not None:
             rows[name]["sector_merging"] = merged
+    rows["cluster rejection: central event with loopers, seed 1"] = cluster_rejection(local, flush)
     print(json.dumps({"all_configs": rows}))
+
+
+def cluster_rejection(local, flush):
+    """Cluster rejection on the central event with loopers (|eta| < 1.5,
+    pT from 40 MeV/c, low-momentum secondaries, loopers over four
+    half-turns): time of tpc_reject_clusters on the fitted tracks, the
+    rejected fractions, and the entropy-coded size of the track clusters
+    (track-model residuals, row steps and headers) with and without the
+    rejected tracks."""
+    import numpy as np
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    import synth
+    cl = synth.looper_event(seed=1).clusters
+    stream = torch.cuda.Stream()
+    trk = tpc.Tracker(device=local, stream=stream)
+    dev = torch.from_numpy(cl.view(np.uint8)).to(f"cuda:{local}")
+    trk.load(dev).run_graph()
+    res = trk.reject()
+    rt = []
+    for _ in range(5):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        trk._ck(trk._lib.tpc_reject_clusters(trk._ctx, None))
+        e1.record(stream)
+        e1.synchronize()
+        rt.append(e0.elapsed_time(e1))
+    c = trk.compress(0.01)
+    counts = trk.counts()
+    trk.close()
+    h = c["heads"]
+    nc = h["n_clusters"].astype(np.int64)
+    kept_track = res["track_class"][: len(h)] == 0
+    first = np.zeros(int(nc.sum()), bool)
+    first[np.concatenate([[0], np.cumsum(nc)[:-1]])[nc > 0]] = True
+    steps = np.zeros(len(first), np.int64)
+    steps[1:] = c["rows"][:-1].astype(np.int64) - c["rows"][1:]
+
+    def bits(track_mask):
+        cm = np.repeat(track_mask, nc)
+        ok = cm & np.repeat(h["ok"].astype(bool), nc)
+        raw = cm & ~ok
+        coded = (_entropy(c["res_y"][ok]) + _entropy(c["res_z"][ok]) + _entropy(steps[ok & ~first])) * ok.sum()
+        fixed = (_entropy(c["q_y"][raw]) + _entropy(c["q_z"][raw])) * raw.sum()
+        return coded + fixed + (32 * 5 + 8 + 8) * int(track_mask.sum())
+
+    b_all, b_kept = bits(np.ones(len(h), bool)), bits(kept_track)
+    cnt = res["counts"]
+    n = len(cl)
+    return {"clusters": n, "tracks": int(counts["n_tracks"]), "reject_ms": statistics.median(rt),
+            "tracks_per_s": counts["n_tracks"] / (statistics.median(rt) / 1e3),
+            "rejected_fraction": cnt["all"] / n,
+            "rejected_fraction_of_track_clusters": cnt["all"] / max(int(nc.sum()), 1),
+            "by_class_fraction": {k: cnt[k] / n for k in ("low_p", "inclined", "looper_leg")},
+            "coded_bits_track_clusters": b_all, "coded_bits_after_rejection": b_kept,
+            "compression_gain_from_rejection": b_all / max(b_kept, 1.0)}
 
 
 def run_reference(args):

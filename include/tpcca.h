@@ -319,8 +319,9 @@ int tpc_autotune(tpc_ctx *ctx, int32_t reps, tpc_tuning *best, float *best_ms);
  * times are estimated from the tracks, and z_t is then converted to space.
  * Reading: a track extrapolated to its closest approach to the beam axis
  * gives t = (z_t - z_max) / v_d; tracks with |distance| <= dca_max, at least
- * min_clusters clusters and a z_t change of at most ext_max in the
- * extrapolation take part; sorted in t they are cut wherever neighbours are
+ * min_clusters clusters, a z_t change of at most ext_max in the
+ * extrapolation and a pT of at least min_pt_gev (0: no cut; above the
+ * looping momentum it keeps the further legs of loopers out) take part; sorted in t they are cut wherever neighbours are
  * more than gap apart; runs of at least min_tracks tracks are vertices with
  * the mean t of their tracks; their tracks get z = side (z_max - (z_t -
  * v_d t_vertex)) at the innermost row (side +1 for sectors 0..17, -1 for
@@ -333,6 +334,7 @@ typedef struct {
   double gap_us;        /* time gap that separates vertices; 0.5 */
   int32_t min_tracks;   /* tracks of a vertex; 3 */
   int32_t min_clusters; /* clusters of a participating track; 20 */
+  double min_pt_gev;    /* smallest pT of a participating track; 0 (none) */
 } tpc_vertex_config;
 
 typedef struct {
@@ -433,6 +435,48 @@ int tpc_merge_tracks(tpc_ctx *ctx, const tpc_merge_config *cfg);
  * its best outer candidate and the second-best chi2 (infinity: none). */
 int tpc_get_merged(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, int32_t *track_link,
                    int32_t *track_chain, float *pair_chi2, float *pair_second);
+
+/* ------------------------------------------------------- cluster rejection */
+/* The compression section: before compression, the clusters of tracks that
+ * physics does not use are dropped (about half of all clusters in the
+ * paper's data).  Reading, per fitted sector track (its state at the
+ * innermost row): class TPC_RJ_LOW_P if its momentum sqrt(1 + t^2)/|q/pT|
+ * is below p_min_gev; TPC_RJ_INCLINED if |dz/ds_T| is above tgl_max;
+ * TPC_RJ_LOOPER_LEG if it is a looper (its circle's farthest point from the
+ * beam axis inside the outermost row radius) and its z at its closest
+ * approach to the beam axis lies more than dz_leg_cm from the collision --
+ * z_ref_cm for an event, or (use_vertices = 1, continuous read-out) the
+ * nearest vertex found by tpc_find_vertices on the current fit, the
+ * distance then being v_drift |t_track - t_vertex|.  Every leg of a helix
+ * from the collision passes the axis again after each full turn with z
+ * moved by 2 pi R dz/ds_T, so only a first leg points back to the collision.
+ * A track with any class is rejected, and so are its clusters; clusters of
+ * no track are kept. */
+typedef struct {
+  double p_min_gev;     /* 0.05 */
+  double tgl_max;       /* 2.0 */
+  double dz_leg_cm;     /* 10 */
+  double z_ref_cm;      /* 0 */
+  int32_t use_vertices; /* 0 */
+  int32_t reserved;
+} tpc_reject_config;
+
+enum { TPC_RJ_LOW_P = 1, TPC_RJ_INCLINED = 2, TPC_RJ_LOOPER_LEG = 4 };
+
+int tpc_default_reject_config(tpc_reject_config *cfg);
+
+/* On the fitted tracks of the loaded batch (after tpc_fit_tracks); cfg NULL:
+ * defaults.  TPC_EINVAL before a fit, for a bad configuration, or for
+ * use_vertices without vertices of the current fit.  Asynchronous; results
+ * with tpc_get_rejection. */
+int tpc_reject_clusters(tpc_ctx *ctx, const tpc_reject_config *cfg);
+
+/* Waits and copies (each optional): per track its class bits (n_tracks
+ * entries, the order of tpc_get_tracks), per loaded cluster its keep flag
+ * (1: stays; n_clusters entries, input order), and counts[4] = clusters
+ * rejected in all, of class LOW_P, INCLINED, LOOPER_LEG (a cluster of a
+ * track with several classes counts in each of them). */
+int tpc_get_rejection(tpc_ctx *ctx, uint8_t *track_class, uint8_t *cluster_keep, int64_t *counts);
 
 /* ------------------------------------------------------ serving (requests) */
 /* Continuous-batching request loop: the serving form of tracking several

@@ -59,7 +59,15 @@ class TpcTuning(ctypes.Structure):
 class VertexConfig(ctypes.Structure):
     _fields_ = [("vdrift_cm_us", ctypes.c_double), ("zmax_cm", ctypes.c_double), ("dca_max_cm", ctypes.c_double),
                 ("ext_max_cm", ctypes.c_double), ("gap_us", ctypes.c_double), ("min_tracks", ctypes.c_int32),
-                ("min_clusters", ctypes.c_int32)]
+                ("min_clusters", ctypes.c_int32), ("min_pt_gev", ctypes.c_double)]
+
+
+class RejectConfig(ctypes.Structure):
+    _fields_ = [("p_min_gev", ctypes.c_double), ("tgl_max", ctypes.c_double), ("dz_leg_cm", ctypes.c_double),
+                ("z_ref_cm", ctypes.c_double), ("use_vertices", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+RJ_LOW_P, RJ_INCLINED, RJ_LOOPER_LEG = 1, 2, 4
 
 
 class MergeConfig(ctypes.Structure):
@@ -122,6 +130,9 @@ def load_library(path: str | None = None):
         "tpc_default_vertex_config": ([_VP], ctypes.c_int),
         "tpc_compress": ([_VP, ctypes.c_double], ctypes.c_int),
         "tpc_default_merge_config": ([_VP], ctypes.c_int),
+        "tpc_default_reject_config": ([_VP], ctypes.c_int),
+        "tpc_reject_clusters": ([_VP, _VP], ctypes.c_int),
+        "tpc_get_rejection": ([_VP, _VP, _VP, _VP], ctypes.c_int),
         "tpc_merge_tracks": ([_VP, _VP], ctypes.c_int),
         "tpc_get_merged": ([_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
         "tpc_get_compressed": ([_VP, _VP, _I64, _VP, _VP, _VP, _VP, _VP, _I64, _VP, _VP], ctypes.c_int),
@@ -368,6 +379,27 @@ class Tracker:
             setattr(c, k, v)
         self._ck(self._lib.tpc_find_vertices(self._ctx, ctypes.byref(c)))
         return self
+
+    def reject(self, **cfg) -> dict:
+        """Cluster rejection (tpc_reject_clusters; keyword arguments override
+        tpc_reject_config fields): per track its class bits (RJ_*), per
+        loaded cluster its keep flag, and the rejected-cluster counts (all,
+        low momentum, inclined, further looper legs)."""
+        c = RejectConfig()
+        self._lib.tpc_default_reject_config(ctypes.byref(c))
+        for k, v in cfg.items():
+            if not hasattr(c, k) or k == "reserved":
+                raise TypeError(f"unknown rejection option {k}")
+            setattr(c, k, v)
+        self._ck(self._lib.tpc_reject_clusters(self._ctx, ctypes.byref(c)))
+        cnt = self.counts()
+        cls = np.zeros(cnt["n_tracks"], np.uint8)
+        keep = np.zeros(cnt["n"], np.uint8)
+        counts = np.zeros(4, np.int64)
+        self._ck(self._lib.tpc_get_rejection(self._ctx, cls.ctypes.data if len(cls) else None,
+                                             keep.ctypes.data if len(keep) else None, counts.ctypes.data))
+        return {"track_class": cls, "cluster_keep": keep,
+                "counts": dict(zip(("all", "low_p", "inclined", "looper_leg"), (int(v) for v in counts)))}
 
     def vertices(self) -> dict:
         """Vertices (VERTEX_DTYPE, in time order) and per track: vertex index

@@ -22,6 +22,7 @@
 #include "vertex.cuh"
 #include "codec.cuh"
 #include "merge.cuh"
+#include "reject.cuh"
 
 using namespace tpc;
 
@@ -224,6 +225,14 @@ struct tpc_ctx {
   MergeBuf mb{};
   int32_t* h_merge_n = nullptr;  // pinned: merged tracks
   bool merge_valid = false;
+  // cluster rejection (tpc_reject_clusters): own buffer
+  void* reject_mem = nullptr;
+  int64_t reject_tracks_cap = 0, reject_clusters_cap = 0;
+  RejBuf rb{};
+  bool reject_valid = false;
+  // fits enqueued so far, and the fit the vertices belong to
+  int64_t fit_gen = 0, vtx_gen = -1;
+  float vtx_vdrift = 2.5f;
   cudaEvent_t ev_chunk[4] = {};     // fork and join of the chunked follow and refit
   // graph
   cudaGraphExec_t graph = nullptr;
@@ -418,6 +427,7 @@ int create_common(tpc_ctx** out, const tpc_config* cfg, int device, void* stream
     if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
   if (ctx->codec_mem) cudaFree(ctx->codec_mem);
   if (ctx->merge_mem) cudaFree(ctx->merge_mem);
+  if (ctx->reject_mem) cudaFree(ctx->reject_mem);
   if (ctx->h_merge_n) cudaFreeHost(ctx->h_merge_n);
   if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
@@ -774,6 +784,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
   if (ctx->codec_mem) cudaFree(ctx->codec_mem);
   if (ctx->merge_mem) cudaFree(ctx->merge_mem);
+  if (ctx->reject_mem) cudaFree(ctx->reject_mem);
   if (ctx->h_merge_n) cudaFreeHost(ctx->h_merge_n);
   if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
@@ -824,6 +835,7 @@ int tpc_fit_tracks(tpc_ctx* ctx) {
   enqueue_fit(ctx);
   CK(cudaGetLastError());
   ctx->fitted = true;
+  ctx->fit_gen++;
   return TPC_OK;
 }
 
@@ -859,6 +871,7 @@ int tpc_run_graph(tpc_ctx* ctx) {
   }
   CK(cudaGraphLaunch(ctx->graph, ctx->stream));
   ctx->found = ctx->fitted = true;
+  ctx->fit_gen++;
   return TPC_OK;
 }
 
@@ -1218,6 +1231,7 @@ int tpc_default_vertex_config(tpc_vertex_config* c) {
   c->gap_us = 0.5;
   c->min_tracks = 3;
   c->min_clusters = 20;
+  c->min_pt_gev = 0.0;
   return TPC_OK;
 }
 
@@ -1282,7 +1296,7 @@ int tpc_find_vertices(tpc_ctx* ctx, const tpc_vertex_config* cfg_in) {
   if (cfg_in) cfg = *cfg_in;
   else tpc_default_vertex_config(&cfg);
   if (!(cfg.vdrift_cm_us > 0) || !(cfg.gap_us > 0) || cfg.min_tracks < 1 || !(cfg.dca_max_cm >= 0) ||
-      !(cfg.ext_max_cm >= 0))
+      !(cfg.ext_max_cm >= 0) || !(cfg.min_pt_gev >= 0 && cfg.min_pt_gev < 1e6))
     return fail(ctx, TPC_EINVAL, "bad vertex configuration");
   CK(cudaSetDevice(ctx->device));
   int rc = vtx_reserve(ctx);
@@ -1297,6 +1311,7 @@ int tpc_find_vertices(tpc_ctx* ctx, const tpc_vertex_config* cfg_in) {
   vc.inv_w = (float)(2.0 / cfg.gap_us);
   vc.min_tracks = cfg.min_tracks;
   vc.min_clusters = cfg.min_clusters;
+  vc.min_pt = (float)cfg.min_pt_gev;
   vc.bins_cap = kVtxBins;
   const VtxBuf& vb = ctx->vb;
   cudaStream_t s = ctx->stream;
@@ -1319,6 +1334,8 @@ int tpc_find_vertices(tpc_ctx* ctx, const tpc_vertex_config* cfg_in) {
   CK(cudaMemcpyAsync(ctx->h_vtx_n, vb.n, 16, cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   ctx->vtx_valid = true;
+  ctx->vtx_gen = ctx->fit_gen;
+  ctx->vtx_vdrift = vc.vdrift;
   return TPC_OK;
 }
 
@@ -1613,6 +1630,99 @@ int tpc_get_merged(tpc_ctx* ctx, tpc_track* out, int64_t cap, int64_t* n_out, in
   if (track_chain && M) CK(cudaMemcpy(track_chain, ctx->mb.chain, 4 * M, cudaMemcpyDeviceToHost));
   if (pair_chi2 && M) CK(cudaMemcpy(pair_chi2, ctx->mb.chi2_out, 4 * M, cudaMemcpyDeviceToHost));
   if (pair_second && M) CK(cudaMemcpy(pair_second, ctx->mb.second_out, 4 * M, cudaMemcpyDeviceToHost));
+  return TPC_OK;
+}
+
+int tpc_default_reject_config(tpc_reject_config* c) {
+  if (!c) return TPC_EINVAL;
+  c->p_min_gev = 0.05;
+  c->tgl_max = 2.0;
+  c->dz_leg_cm = 10.0;
+  c->z_ref_cm = 0.0;
+  c->use_vertices = 0;
+  c->reserved = 0;
+  return TPC_OK;
+}
+
+namespace {
+int reject_reserve(tpc_ctx* ctx) {
+  const int64_t M = std::max<int64_t>(ctx->caps.tracks, 1), N = std::max<int64_t>(ctx->caps.n, 1);
+  if (ctx->reject_mem && ctx->reject_tracks_cap >= M && ctx->reject_clusters_cap >= N) return TPC_OK;
+  if (ctx->reject_mem) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(ctx->reject_mem);
+    ctx->reject_mem = nullptr;
+  }
+  const size_t o_cnt = 0, o_cls = align_up(32), o_keep = align_up(o_cls + M), total = align_up(o_keep + N);
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, total) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, TPC_ENOMEM, "rejection buffers of %zu bytes", total);
+  }
+  char* b = (char*)mem;
+  ctx->reject_mem = mem;
+  ctx->reject_tracks_cap = M;
+  ctx->reject_clusters_cap = N;
+  ctx->rb.count = (unsigned long long*)(b + o_cnt);
+  ctx->rb.cls = (uint8_t*)(b + o_cls);
+  ctx->rb.keep = (uint8_t*)(b + o_keep);
+  return TPC_OK;
+}
+}  // namespace
+
+int tpc_reject_clusters(tpc_ctx* ctx, const tpc_reject_config* cfg_in) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->fitted) return fail(ctx, TPC_EINVAL, "tpc_fit_tracks has not run");
+  tpc_reject_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else tpc_default_reject_config(&cfg);
+  if (!(cfg.p_min_gev >= 0) || !(cfg.tgl_max >= 0) || !(cfg.dz_leg_cm >= 0) || !std::isfinite(cfg.z_ref_cm) ||
+      (cfg.use_vertices != 0 && cfg.use_vertices != 1))
+    return fail(ctx, TPC_EINVAL, "bad rejection configuration");
+  if (cfg.use_vertices && !(ctx->vtx_valid && ctx->vtx_gen == ctx->fit_gen))
+    return fail(ctx, TPC_EINVAL, "use_vertices needs tpc_find_vertices on the current fit");
+  CK(cudaSetDevice(ctx->device));
+  int rc = reject_reserve(ctx);
+  if (rc) return rc;
+  RejConst c;
+  c.p_min = (float)cfg.p_min_gev;
+  c.tgl_max = (float)cfg.tgl_max;
+  c.dz_leg = (float)cfg.dz_leg_cm;
+  c.z_ref = (float)cfg.z_ref_cm;
+  c.K = (float)(0.299792458e-3 * ctx->cfg.bz_kg);
+  c.x_out = (float)(85.2 + (NROW - 1) * ((245.8 - 85.2) / 158.0));
+  c.vdrift = ctx->vtx_vdrift;
+  c.use_vertices = cfg.use_vertices;
+  cudaStream_t s = ctx->stream;
+  const int64_t M = ctx->caps.tracks;
+  CK(cudaMemsetAsync(ctx->rb.count, 0, 32, s));
+  if (ctx->n) CK(cudaMemsetAsync(ctx->rb.keep, 1, ctx->n, s));
+  k_reject<<<grid_for(ctx, M, 256), 256, 0, s>>>(ctx->ptr<tpc_track>(ctx->L.tracks),
+                                                ctx->ptr<int32_t>(ctx->L.track_clusters), c,
+                                                cfg.use_vertices ? ctx->vtx_time : nullptr,
+                                                cfg.use_vertices ? ctx->vb.n + 2 : nullptr,
+                                                cfg.use_vertices ? ctx->vb.t : nullptr, ctx->rb,
+                                                ctx->ptr<Counts>(ctx->L.counts));
+  CK(cudaGetLastError());
+  ctx->reject_valid = true;
+  return TPC_OK;
+}
+
+int tpc_get_rejection(tpc_ctx* ctx, uint8_t* track_class, uint8_t* cluster_keep, int64_t* counts) {
+  if (!ctx) return TPC_EINVAL;
+  if (!ctx->reject_valid) return fail(ctx, TPC_EINVAL, "tpc_reject_clusters has not run");
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int rc = check_status(ctx);
+  if (rc) return rc;
+  const int64_t M = ctx->h_counts->n_tracks;
+  if (track_class && M) CK(cudaMemcpy(track_class, ctx->rb.cls, M, cudaMemcpyDeviceToHost));
+  if (cluster_keep && ctx->n) CK(cudaMemcpy(cluster_keep, ctx->rb.keep, ctx->n, cudaMemcpyDeviceToHost));
+  if (counts) {
+    unsigned long long c[4];
+    CK(cudaMemcpy(c, ctx->rb.count, sizeof(c), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 4; i++) counts[i] = (int64_t)c[i];
+  }
   return TPC_OK;
 }
 

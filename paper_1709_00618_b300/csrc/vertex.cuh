@@ -23,6 +23,7 @@ struct VtxConst {
   float inv_w;     // 1 / bin width (bin width = gap / 2)
   int32_t min_tracks, min_clusters;
   int32_t bins_cap;
+  float min_pt;    // GeV/c; 0: no cut
 };
 
 struct VtxBuf {
@@ -85,7 +86,7 @@ __global__ void k_vtx_time(const tpc_track* __restrict__ tr, VtxConst vc, VtxBuf
     const float dzt = t.par[3] * path;
     const float te = ((t.par[1] - vc.zmax) + dzt) / vc.vdrift;
     const bool use = dist <= vc.dca_max && fabsf(dzt) <= vc.ext_max && t.n_clusters >= vc.min_clusters &&
-                     isfinite(te);
+                     isfinite(te) && !(fabsf(t.par[4]) * vc.min_pt > 1.0f);
     vb.t[m] = te;
     vb.use[m] = use;
     if (use) {
