@@ -108,15 +108,17 @@ BYTES_GRID, BYTES_NEIGH = 44, 45
 FP32_FLOP_PER_CLK_SM, FP64_FLOP_PER_CLK_SM, N_SM = 256, 4, 148
 
 
+# The sources of the tracking path's kernels (the ones the traffic capture covers).
+PATH_KERNEL_SOURCES = ("common.cuh", "scan.cuh", "grid.cuh", "links.cuh", "kalman.cuh", "order.cuh", "follow.cuh",
+                       "select.cuh")
+
+
 def _source_hash():
-    import glob
     import hashlib
     m = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1709_00618_b300", "csrc", "*"))) + \
-            [os.path.join(ROOT, "include", "tpcca.h")]:
-        if f.endswith((".cu", ".cuh", ".cpp", ".h")):
-            with open(f, "rb") as fh:
-                m.update(fh.read())
+    for f in PATH_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1709_00618_b300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
     return m.hexdigest()
 
 

@@ -73,13 +73,12 @@ __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Tr
     const int base = P.bin_base + iz * P.n_y;
     const int a = __ldg(g.bin_start + base + iy0), b = __ldg(g.bin_start + base + iy1 + 1);
     ncand += (unsigned)(b - a);
-    for (int c = a; c < b; c++) {
-      const float2 q = __ldg(g.yz + c);
+    auto consider = [&](float2 q, int c) {
       const float dy = (q.x - p.y) - p.yl;
       const float dz = ((q.y - p.zref) - p.z) - p.zl;
       const float chi = dy * dy * iSyy + dz * dz * iSzz;
       if (fabsf(chi - gate) <= eps * (1.0f + gate)) flags |= TF_GATE;
-      if (!(chi <= gate)) continue;
+      if (!(chi <= gate)) return;
       if (chi < b1v || (chi == b1v && c < best)) {
         b2v = b1v;
         b1v = chi;
@@ -87,7 +86,14 @@ __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Tr
       } else if (chi < b2v) {
         b2v = chi;
       }
+    };
+    int c = a;  // two candidates' loads in flight at a time, taken in index order
+    for (; c + 1 < b; c += 2) {
+      const float2 q0 = __ldg(g.yz + c), q1 = __ldg(g.yz + c + 1);
+      consider(q0, c);
+      consider(q1, c + 1);
     }
+    if (c < b) consider(__ldg(g.yz + c), c);
   }
   if (best >= 0 && b2v != __int_as_float(0x7F800000) && b2v - b1v <= eps * (1.0f + b1v)) flags |= TF_TIE;
   return best;
@@ -100,6 +106,7 @@ struct Lane {
   int ubase, r0, L;
   int nf, nb;
   int k;        // current chain cluster (forward)
+  int nk;       // next chain cluster, loaded a step ahead (-1: none)
   int i;        // next chain index (forward)
   int r_last;   // row of the last forward update
   int kf;       // next forward hit to refit (backward)
@@ -183,24 +190,29 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
   if (r + 1 < NROW) prefetch_l1(g.par + w.ubase + r + 1);  // the next step's row-sector parameters
   const bool chain = w.i < w.L;
   const bool zone = Z && w.nupd < kc.fp64_updates;
+  float2 Pc;
+  int c = -1;
+  if (chain) {  // the chain's cluster and the one after it are loaded while the state propagates
+    c = w.nk;
+    Pc = __ldg(g.yz + c);
+    w.nk = w.i + 1 < w.L ? __ldg(up_m + c) : -1;
+  }
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (chain) w.seed_fail = true;
     return false;
   }
   tl.prop++;
   tl.prop64 += zone;
-  int c;
   if (chain) {
-    w.k = __ldg(up_m + w.k);
+    w.k = c;
     w.i++;
-    c = w.k;
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
     c = pick(g, w.ubase + r, r, p, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2], kc, sYH, w.flags,
              tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
   }
-  const float2 P = __ldg(g.yz + c);
+  const float2 P = chain ? Pc : __ldg(g.yz + c);
   lane_update<Z>(w, kc, p, zone, D, C, P, chi2, 0);
   if (zone) tl.upd64++;
   else tl.upd32++;
@@ -362,6 +374,7 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
         seed_state(p, w.r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);
       }
       w.k = c0;
+      w.nk = w.L > 1 ? __ldg(up_m + c0) : -1;
       w.i = 1;
       w.misses = 0;
       w.r_last = w.r0;

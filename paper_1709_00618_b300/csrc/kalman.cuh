@@ -194,10 +194,11 @@ __device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, cons
   return true;
 }
 
-// The FP64-zone covariance operations are kept out of line: one copy of
-// the double-precision code, the covariance in (L1-resident) local memory,
-// so the binary32 loop that runs most rows keeps its registers.
-__device__ __noinline__ void cov_transport_d(double* D, float j02, float j04, float j24, float j12, float j13,
+// The FP64-zone covariance operations.  Inline: in the zone kernels the
+// covariance stays in registers (out of line it went through local memory,
+// 5-13% slower); the binary32 kernels instantiate the row steps without the
+// zone path, so they do not carry this code.
+__device__ __forceinline__ void cov_transport_d(double* D, float j02, float j04, float j24, float j12, float j13,
                                              float j14) {
   cov_transport<double>(D, j02, j04, j24, j12, j13, j14);
 }
@@ -208,7 +209,7 @@ struct UpdOut {
 };
 
 // Kalman update of the FP64 covariance D for residual (r0, r1).
-__device__ __noinline__ UpdOut kalman_update_d(double* D, float r0, float r1, double V) {
+__device__ __forceinline__ UpdOut kalman_update_d(double* D, float r0, float r1, double V) {
   const double S00 = D[0] + V, S01 = D[1], S11 = D[2] + V;
   const double idet = 1.0 / (S00 * S11 - S01 * S01);
   const double I00 = S11 * idet, I01 = -S01 * idet, I11 = S00 * idet;

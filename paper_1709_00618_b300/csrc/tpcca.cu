@@ -200,7 +200,7 @@ struct tpc_ctx {
   int block_follow = 128;
   int ctas_zone = 2;     // cap on CTAs per SM of the FP64-zone Kalman kernels
   int ctas_follow = 0;   // cap on CTAs per SM of the refilling Kalman kernels (64: occupancy; 0: by size)
-  int refill = 4;        // idle lanes that trigger a warp's refill
+  int refill = 8;        // idle lanes that trigger a warp's refill
   int chunks = 0;        // Kalman-stage chunks (2: zone and FP32 kernels of different chunks overlap; 0: 1)
   int graph_chunks = 0;  // chunks and refilling-kernel CTAs per SM of the captured graph
   int graph_ctas = 0;
