@@ -21,17 +21,23 @@ __global__ void k_fill32(int32_t* __restrict__ a, int32_t v, const Counts* cn) {
   for (int64_t i = gtid(); i < n; i += gstride()) a[i] = v;
 }
 
-// owner[c] = max key over the tracklets holding c.
+// owner[c] = max key over the tracklets holding c.  W: one warp per
+// tracklet, the lanes over its hits (coalesced hit loads, 32 atomics in
+// flight; faster while the owner array is L2-resident); else one thread per
+// tracklet (a warp's 32 atomics then fall on neighbouring tracklets' rows:
+// better DRAM locality on inputs far larger than L2).
+template <bool W>
 __global__ void k_own(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits, KConst kc,
                       uint64_t* __restrict__ owner, const Counts* cn) {
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
-  for (int64_t t = gtid(); t < T; t += gstride()) {
+  const int lane = W ? (int)(threadIdx.x & 31) : 0, step = W ? 32 : 1;
+  for (int64_t t = W ? gtid() >> 5 : gtid(); t < T; t += W ? gstride() >> 5 : gstride()) {
     const int n = f_n[t];
     if (n < kc.n_min_track) continue;
     const uint64_t key = track_key(n, (int)t);
     const int32_t* h = hits + t * NROW;
-    for (int i = 0; i < n; i++) atomicMax((unsigned long long*)(owner + h[i]), (unsigned long long)key);
+    for (int i = lane; i < n; i += step) atomicMax((unsigned long long*)(owner + h[i]), (unsigned long long)key);
   }
 }
 
@@ -46,31 +52,38 @@ __global__ void k_keep(const int32_t* __restrict__ f_n, const int32_t* __restric
                        int32_t* __restrict__ own_rng, const Counts* cn) {
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
-  for (int64_t t = gtid(); t < T; t += gstride()) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t t = gtid() >> 5; t < T; t += gstride() >> 5) {  // one warp per tracklet, lanes over hits
     const int n = f_n[t];
-    int kept = 0, r_in = NROW, r_out = -1;
-    uint32_t m[OWN_WORDS] = {0, 0, 0, 0, 0};
+    int kept = 0;
+    unsigned r_in = NROW, r_out = 0;  // r_out: one past the outermost owned row
+    uint32_t mw = 0;                  // lane w < OWN_WORDS: mask word w
     if (n >= kc.n_min_track) {
       const uint64_t key = track_key(n, (int)t);
       const int32_t* h = hits + t * NROW;
       const uint8_t* hr = hrow + t * NROW;
-      for (int i = 0; i < n; i++) {
-        if (__ldg((const unsigned long long*)owner + h[i]) != key) continue;
-        kept++;
-        m[i >> 5] |= 1u << (i & 31);
-        const int r = hr[i];
-        r_in = min(r_in, r);
-        r_out = max(r_out, r);
+      for (int i0 = 0; i0 < n; i0 += 32) {
+        const int i = i0 + lane;
+        const bool own = i < n && __ldg((const unsigned long long*)owner + h[i]) == key;
+        const uint32_t b = __ballot_sync(FULL_MASK, own);
+        if (lane == (i0 >> 5)) mw = b;
+        kept += __popc(b);
+        if (own) {
+          const unsigned r = hr[i];
+          r_in = min(r_in, r);
+          r_out = max(r_out, r + 1);
+        }
       }
+      r_in = __reduce_min_sync(FULL_MASK, r_in);
+      r_out = __reduce_max_sync(FULL_MASK, r_out);
     }
     const int k = kept >= kc.n_min_track;
-    keep[t] = k;
-    nown[t] = k ? kept : 0;
-    if (k) {
-#pragma unroll
-      for (int w = 0; w < OWN_WORDS; w++) own_mask[t * OWN_WORDS + w] = m[w];
-      own_rng[t] = r_in | (r_out << 16);
+    if (lane == 0) {
+      keep[t] = k;
+      nown[t] = k ? kept : 0;
+      if (k) own_rng[t] = (int)r_in | (((int)r_out - 1) << 16);
     }
+    if (k && lane < OWN_WORDS) own_mask[t * OWN_WORDS + lane] = mw;
   }
 }
 
@@ -83,22 +96,29 @@ __global__ void k_track_clusters(const int32_t* __restrict__ track_tl, const int
                                  const Counts* cn) {
   if (fatal(cn)) return;
   const int32_t M = cn->n_tracks;
-  for (int64_t m = gtid(); m < M; m += gstride()) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t m = gtid() >> 5; m < M; m += gstride() >> 5) {  // one warp per track, lanes over slots
     const int t = track_tl[m];
     const int n = f_n[t], nf = f_nf[t];
-    uint32_t mk[OWN_WORDS];
-#pragma unroll
-    for (int w = 0; w < OWN_WORDS; w++) mk[w] = own_mask[t * OWN_WORDS + w];
+    const uint32_t mw = lane < OWN_WORDS ? own_mask[t * OWN_WORDS + lane] : 0u;
     const int32_t* h = hits + (int64_t)t * NROW;
     int wpos = toff[m];
-    for (int j = n - 1; j >= nf; j--)
-      if ((mk[j >> 5] >> (j & 31)) & 1u) track_clusters[wpos++] = __ldg(perm + h[j]);
-    for (int j = 0; j < nf; j++)
-      if ((mk[j >> 5] >> (j & 31)) & 1u) track_clusters[wpos++] = __ldg(perm + h[j]);
+    // output position j: slots n-1 .. nf (backward extension, innermost first), then 0 .. nf-1
+    for (int j0 = 0; j0 < n; j0 += 32) {
+      const int j = j0 + lane;
+      const int slot = j < n - nf ? n - 1 - j : j - (n - nf);
+      const uint32_t word = __shfl_sync(FULL_MASK, mw, j < n ? slot >> 5 : 0);
+      const bool own = j < n && ((word >> (slot & 31)) & 1u);
+      const uint32_t b = __ballot_sync(FULL_MASK, own);
+      if (own) track_clusters[wpos + __popc(b & ((1u << lane) - 1u))] = __ldg(perm + h[slot]);
+      wpos += __popc(b);
+    }
   }
 }
 
-// Track numbering in tracklet order; per-cluster assignment in load order.
+// Track numbering in tracklet order; per-cluster assignment in load order
+// (W: one warp per tracklet, as k_own).
+template <bool W>
 __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits,
                          const uint64_t* __restrict__ owner, const int32_t* __restrict__ keep,
                          const int32_t* __restrict__ tidx, const int32_t* __restrict__ perm,
@@ -107,18 +127,21 @@ __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restr
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
   if (gtid() == 0) cn->n_tracks = tidx[T];
-  for (int64_t t = gtid(); t < T; t += gstride()) {
+  const int lane = W ? (int)(threadIdx.x & 31) : 0, step = W ? 32 : 1;
+  for (int64_t t = W ? gtid() >> 5 : gtid(); t < T; t += W ? gstride() >> 5 : gstride()) {
     if (!keep[t]) {
-      tl_track[t] = -1;
+      if (lane == 0) tl_track[t] = -1;
       continue;
     }
     const int idx = tidx[t];
-    tl_track[t] = idx;
-    track_tl[idx] = (int32_t)t;
+    if (lane == 0) {
+      tl_track[t] = idx;
+      track_tl[idx] = (int32_t)t;
+    }
     const int n = f_n[t];
     const uint64_t key = track_key(n, (int)t);
     const int32_t* h = hits + t * NROW;
-    for (int i = 0; i < n; i++)
+    for (int i = lane; i < n; i += step)
       if (__ldg((const unsigned long long*)owner + h[i]) == key) cluster_track[__ldg(perm + h[i])] = idx;
   }
 }

@@ -204,6 +204,7 @@ struct tpc_ctx {
   int chunks = 0;        // Kalman-stage chunks (2: zone and FP32 kernels of different chunks overlap; 0: 1)
   int graph_chunks = 0;  // chunks and refilling-kernel CTAs per SM of the captured graph
   int graph_ctas = 0;
+  bool graph_large = false;  // the size class the graph's kernel variants were chosen for
   cudaStream_t aux = nullptr;       // second stream of the chunked Kalman stage
   // vertex finding (tpc_find_vertices): its own buffer, allocated on first use
   void* vtx_mem = nullptr;
@@ -491,6 +492,7 @@ void enqueue_find(tpc_ctx* ctx) {
   const int bc = ctx->block_clusters;
   const int gN = grid_for(ctx, C.n, bc), gR = grid_for(ctx, C.nrs(), bc);
   const int gT = grid_for(ctx, C.tl, bc);
+  const int gTw = grid_for(ctx, C.tl * 32, bc);  // warp-per-tracklet kernels
   int32_t* rs_cnt = ctx->ptr<int32_t>(L.rs_cnt);
   int32_t* nbins = ctx->ptr<int32_t>(L.nbins);
   int32_t* bin_base = ctx->ptr<int32_t>(L.bin_base);
@@ -574,14 +576,15 @@ void enqueue_find(tpc_ctx* ctx) {
   // a7 selection
   k_zero64<<<gN, bc, 0, s>>>(ctx->ptr<uint64_t>(L.owner), cn);
   k_fill32<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.cluster_track), -1, cn);
-  k_own<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, ctx->ptr<uint64_t>(L.owner),
+  const bool warp_sel = ctx->n < kLargeBatch;  // warp per tracklet while the owner array stays in L2
+  (warp_sel ? k_own<true> : k_own<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, ctx->ptr<uint64_t>(L.owner),
                           cn);
-  k_keep<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint8_t>(L.hrow),
+  k_keep<<<gTw, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint8_t>(L.hrow),
                            ctx->ptr<uint64_t>(L.owner), ctx->kc, ctx->ptr<int32_t>(L.keep),
                            ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.own_rng),
                            cn);
   scan(ctx, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), LenSrc{&cn->n_tracklets, 0, 0}, nullptr);
-  k_assign<<<gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
+  (warp_sel ? k_assign<true> : k_assign<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
                              ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), ctx->ptr<int32_t>(L.perm),
                              ctx->ptr<int32_t>(L.tl_track), ctx->ptr<int32_t>(L.track_tl),
                              ctx->ptr<int32_t>(L.cluster_track), cn);
@@ -646,7 +649,7 @@ void enqueue_fit(tpc_ctx* ctx) {
     }
     ctx->mark_k(5);
   }
-  k_track_clusters<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
+  k_track_clusters<<<grid_for(ctx, C.tracks * 32, bc), bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
                                      ctx->ptr<int32_t>(L.f_nf), ctx->ptr<int32_t>(L.hits),
                                      ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.toff),
                                      ctx->ptr<int32_t>(L.perm), ctx->ptr<int32_t>(L.track_clusters), cn);
@@ -843,7 +846,8 @@ int tpc_run_graph(tpc_ctx* ctx) {
   if (!ctx) return TPC_EINVAL;
   if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "no clusters loaded");
   CK(cudaSetDevice(ctx->device));
-  if (ctx->graph && (ctx->graph_chunks != effective_chunks(ctx) || ctx->graph_ctas != effective_ctas_follow(ctx))) {
+  if (ctx->graph && (ctx->graph_chunks != effective_chunks(ctx) || ctx->graph_ctas != effective_ctas_follow(ctx) ||
+                     ctx->graph_large != (ctx->n >= kLargeBatch))) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
   }
@@ -862,6 +866,7 @@ int tpc_run_graph(tpc_ctx* ctx) {
     ctx->graph_kernels = count_kernel_nodes(g);
     ctx->graph_chunks = effective_chunks(ctx);
     ctx->graph_ctas = effective_ctas_follow(ctx);
+    ctx->graph_large = ctx->n >= kLargeBatch;
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
