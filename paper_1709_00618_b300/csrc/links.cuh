@@ -206,26 +206,31 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
   }
 }
 
-// a4 + a5: keep links both ends agree on; a cluster with a kept upward link
-// and no kept downward link starts a chain; walk it and flag chains of at
-// least min_chain clusters.
-__global__ void k_chains(const int32_t* __restrict__ up, const int32_t* __restrict__ dn, KConst kc,
-                         int32_t* __restrict__ up_m, int32_t* __restrict__ dn_m, int32_t* __restrict__ flag,
-                         int32_t* __restrict__ clen, int32_t* __restrict__ cend, const Counts* cn) {
+// a4: keep the links both ends agree on.
+__global__ void k_clean(const int32_t* __restrict__ up, const int32_t* __restrict__ dn, int32_t* __restrict__ up_m,
+                        int32_t* __restrict__ dn_m, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t c = gtid(); c < n; c += gstride()) {
-    int u = up[c], d = dn[c];
-    int um = (u >= 0 && __ldg(dn + u) == (int)c) ? u : -1;
-    int dm = (d >= 0 && __ldg(up + d) == (int)c) ? d : -1;
-    up_m[c] = um;
-    dn_m[c] = dm;
+    const int u = up[c], d = dn[c];
+    up_m[c] = (u >= 0 && __ldg(dn + u) == (int)c) ? u : -1;
+    dn_m[c] = (d >= 0 && __ldg(up + d) == (int)c) ? d : -1;
+  }
+}
+
+// a5: a cluster with a kept upward link and no kept downward link starts a
+// chain; walk it over the kept links (one dependent load per cluster) and
+// flag chains of at least min_chain clusters.
+__global__ void k_chains(const int32_t* __restrict__ up_m, const int32_t* __restrict__ dn_m, KConst kc,
+                         int32_t* __restrict__ flag, int32_t* __restrict__ clen, int32_t* __restrict__ cend,
+                         const Counts* cn) {
+  if (fatal(cn)) return;
+  const int64_t n = cn->n;
+  for (int64_t c = gtid(); c < n; c += gstride()) {
     int f = 0;
-    if (um >= 0 && dm < 0) {
+    if (up_m[c] >= 0 && dn_m[c] < 0) {
       int len = 1, k = (int)c;
-      for (;;) {
-        int uk = __ldg(up + k);
-        if (uk < 0 || __ldg(dn + uk) != k) break;
+      for (int uk = __ldg(up_m + k); uk >= 0; uk = __ldg(up_m + k)) {
         k = uk;
         len++;
       }

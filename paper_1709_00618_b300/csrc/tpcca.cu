@@ -527,9 +527,10 @@ void enqueue_find(tpc_ctx* ctx) {
                                   ctx->ptr<uint8_t>(L.tie), cn);
   ctx->mark(2);
   // a4 + a5
-  k_chains<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn), ctx->kc, ctx->ptr<int32_t>(L.up_m),
-                             ctx->ptr<int32_t>(L.dn_m), ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.clen),
-                             ctx->ptr<int32_t>(L.cend), cn);
+  k_clean<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn), ctx->ptr<int32_t>(L.up_m),
+                            ctx->ptr<int32_t>(L.dn_m), cn);
+  k_chains<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up_m), ctx->ptr<int32_t>(L.dn_m), ctx->kc, ctx->ptr<int32_t>(L.flag),
+                             ctx->ptr<int32_t>(L.clen), ctx->ptr<int32_t>(L.cend), cn);
   scan(ctx, ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), LenSrc{&cn->n32, 0, 0}, nullptr);
   k_tracklet_compact<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx),
                                        ctx->ptr<int32_t>(L.clen), ctx->ptr<int32_t>(L.cend),
