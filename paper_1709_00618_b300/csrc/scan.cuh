@@ -53,6 +53,39 @@ __device__ __forceinline__ void chunk_of(int64_t len, int64_t& a, int64_t& b) {
   if (a > len) a = len;
 }
 
+// The whole scan in one block, tile after tile with a running carry: for
+// short arrays (a few tiles), where the three-kernel scan's launches cost
+// more than the work.  out may alias in; out[len] = total.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_small(const int32_t* in, LenSrc L, int32_t* out,
+                                                             int32_t* total_out, const Counts* cn) {
+  __shared__ int ws[32];
+  if (fatal(cn)) return;
+  const int64_t len = L.get();
+  int carry = 0;
+  for (int64_t base = 0; base < len; base += SCAN_TILE) {
+    int v[SCAN_ITEMS], sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+      const int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+      v[k] = i < len ? in[i] : 0;
+      sum += v[k];
+    }
+    int tot;
+    int run = carry + block_incl_scan(sum, ws, tot) - sum;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+      const int64_t i = base + (int64_t)threadIdx.x * SCAN_ITEMS + k;
+      if (i < len) out[i] = run;
+      run += v[k];
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    out[len] = carry;
+    if (total_out) *total_out = carry;
+  }
+}
+
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t* __restrict__ in, LenSrc L,
                                                               int32_t* __restrict__ part, const Counts* cn) {
   __shared__ int ws[32];

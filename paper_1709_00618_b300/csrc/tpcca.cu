@@ -448,8 +448,14 @@ bool config_ok(const tpc_config& c) {
          c.s_max < 1 && c.fp64_updates >= 0 && c.taint_rel >= 0;
 }
 
-void scan(tpc_ctx* ctx, const int32_t* in, int32_t* out, LenSrc len, int32_t* total_out) {
+// Exclusive scan of a device-resident length; cap: an upper bound of the
+// length (a short array is scanned by one block).
+void scan(tpc_ctx* ctx, const int32_t* in, int32_t* out, LenSrc len, int32_t* total_out, int64_t cap = -1) {
   Counts* cn = ctx->ptr<Counts>(ctx->L.counts);
+  if (cap >= 0 && cap <= 8 * SCAN_TILE) {
+    k_scan_small<<<1, SCAN_THREADS, 0, ctx->stream>>>(in, len, out, total_out, cn);
+    return;
+  }
   int32_t* parts = ctx->ptr<int32_t>(ctx->L.parts);
   k_scan_reduce<<<SCAN_PARTS, SCAN_THREADS, 0, ctx->stream>>>(in, len, parts, cn);
   k_scan_parts<<<1, 1024, 0, ctx->stream>>>(parts, SCAN_PARTS, total_out, cn);
@@ -508,8 +514,8 @@ void enqueue_find(tpc_ctx* ctx) {
   k_grid_params<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax),
                                   ctx->ptr<RsParams>(L.par), nbins, cn);
   LenSrc lrs{&cn->n_rs, 0, 0};
-  scan(ctx, rs_cnt, ctx->ptr<int32_t>(L.rs_start), lrs, nullptr);
-  scan(ctx, nbins, bin_base, lrs, nullptr);
+  scan(ctx, rs_cnt, ctx->ptr<int32_t>(L.rs_start), lrs, nullptr, C.nrs());
+  scan(ctx, nbins, bin_base, lrs, nullptr, C.nrs());
   k_grid_finish_params<<<gR, bc, 0, s>>>(ctx->ptr<RsParams>(L.par), bin_base, cn, C.bins, bin_cnt);
   k_grid_bin<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.rs_in), ctx->ptr<RsParams>(L.par),
                                bin_cnt, ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), cn);
