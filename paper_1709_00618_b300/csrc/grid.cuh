@@ -144,11 +144,14 @@ __global__ void k_grid_scatter(const int32_t* __restrict__ gbin, const int32_t* 
 
 // Stable order inside each bin: rank = number of bin members with a smaller
 // load index.  Bins hold about two clusters on average (the bin edge is
-// sqrt(2 A / n)); the count is quadratic only in the fullest bin.
+// sqrt(2 A / n)); the count is quadratic only in the fullest bin.  Also
+// clears the selection stage's per-cluster arrays (owner keys to 0, the
+// cluster-to-track map to -1), which are as long as the cluster list.
 __global__ void k_grid_order(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ tmp,
                              const int32_t* __restrict__ gbin, const int32_t* __restrict__ rs_in,
                              const int32_t* __restrict__ bin_start, int32_t* __restrict__ perm,
-                             float2* __restrict__ yz, int32_t* __restrict__ rs_of, const Counts* cn) {
+                             float2* __restrict__ yz, int32_t* __restrict__ rs_of, uint64_t* __restrict__ owner,
+                             int32_t* __restrict__ cluster_track, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t p = gtid(); p < n; p += gstride()) {
@@ -161,6 +164,8 @@ __global__ void k_grid_order(const tpc_cluster* __restrict__ in, const int32_t* 
     perm[dst] = i;
     yz[dst] = __ldg(reinterpret_cast<const float2*>(in + i));
     rs_of[dst] = rs_in[i];
+    owner[p] = 0ull;
+    cluster_track[p] = -1;
   }
 }
 

@@ -11,16 +11,6 @@ __device__ __forceinline__ uint64_t track_key(int n, int t) {
   return ((uint64_t)(uint32_t)n << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)t);
 }
 
-__global__ void k_zero64(uint64_t* __restrict__ a, const Counts* cn) {
-  const int64_t n = cn->n;
-  for (int64_t i = gtid(); i < n; i += gstride()) a[i] = 0ull;
-}
-
-__global__ void k_fill32(int32_t* __restrict__ a, int32_t v, const Counts* cn) {
-  const int64_t n = cn->n;
-  for (int64_t i = gtid(); i < n; i += gstride()) a[i] = v;
-}
-
 // owner[c] = max key over the tracklets holding c.  W: one warp per
 // tracklet, the lanes over its hits (coalesced hit loads, 32 atomics in
 // flight; faster while the owner array is L2-resident); else one thread per

@@ -525,7 +525,8 @@ void enqueue_find(tpc_ctx* ctx) {
                                    ctx->ptr<int32_t>(L.tmp), cn);
   k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.tmp), ctx->ptr<int32_t>(L.gbin),
                                  ctx->ptr<int32_t>(L.rs_in), bin_start, ctx->ptr<int32_t>(L.perm),
-                                 ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), cn);
+                                 ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<uint64_t>(L.owner),
+                                 ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(1);
   // a3 neighbours
   k_neighbours<<<grid_for(ctx, C.n * NB_G, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
@@ -581,8 +582,6 @@ void enqueue_find(tpc_ctx* ctx) {
   }
   ctx->mark(4);
   // a7 selection
-  k_zero64<<<gN, bc, 0, s>>>(ctx->ptr<uint64_t>(L.owner), cn);
-  k_fill32<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.cluster_track), -1, cn);
   const bool warp_sel = ctx->n < kLargeBatch;  // warp per tracklet while the owner array stays in L2
   (warp_sel ? k_own<true> : k_own<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, ctx->ptr<uint64_t>(L.owner),
                           cn);
