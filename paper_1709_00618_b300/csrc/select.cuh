@@ -112,7 +112,8 @@ template <bool W>
 __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits,
                          const uint64_t* __restrict__ owner, const int32_t* __restrict__ keep,
                          const int32_t* __restrict__ tidx, const int32_t* __restrict__ perm,
-                         int32_t* __restrict__ tl_track, int32_t* __restrict__ track_tl,
+                         const int32_t* __restrict__ nown, int32_t* __restrict__ tl_track,
+                         int32_t* __restrict__ track_tl, int32_t* __restrict__ tcount,
                          int32_t* __restrict__ cluster_track, Counts* cn) {
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
@@ -127,6 +128,7 @@ __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restr
     if (lane == 0) {
       tl_track[t] = idx;
       track_tl[idx] = (int32_t)t;
+      tcount[idx] = nown[t];  // owned clusters per track, for the offsets of the refit's output
     }
     const int n = f_n[t];
     const uint64_t key = track_key(n, (int)t);
@@ -134,14 +136,6 @@ __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restr
     for (int i = lane; i < n; i += step)
       if (__ldg((const unsigned long long*)owner + h[i]) == key) cluster_track[__ldg(perm + h[i])] = idx;
   }
-}
-
-// Scatter the owned counts of the tracks (in track order) for the offset scan.
-__global__ void k_track_counts(const int32_t* __restrict__ track_tl, const int32_t* __restrict__ nown,
-                               int32_t* __restrict__ tcount, const Counts* cn) {
-  if (fatal(cn)) return;
-  const int32_t M = cn->n_tracks;
-  for (int64_t i = gtid(); i < M; i += gstride()) tcount[i] = nown[track_tl[i]];
 }
 
 // a8: refit of each kept track over its owned clusters, outermost to

@@ -592,8 +592,8 @@ void enqueue_find(tpc_ctx* ctx) {
   scan(ctx, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), LenSrc{&cn->n_tracklets, 0, 0}, nullptr);
   (warp_sel ? k_assign<true> : k_assign<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
                              ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), ctx->ptr<int32_t>(L.perm),
-                             ctx->ptr<int32_t>(L.tl_track), ctx->ptr<int32_t>(L.track_tl),
-                             ctx->ptr<int32_t>(L.cluster_track), cn);
+                             ctx->ptr<int32_t>(L.nown), ctx->ptr<int32_t>(L.tl_track), ctx->ptr<int32_t>(L.track_tl),
+                             ctx->ptr<int32_t>(L.tcount), ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(5);
 }
 
@@ -624,9 +624,6 @@ void enqueue_fit(tpc_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   Counts* cn = ctx->ptr<Counts>(L.counts);
   const int bc = ctx->block_clusters;
-  const int gM = grid_for(ctx, C.tracks, bc);
-  k_track_counts<<<gM, bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.nown),
-                                   ctx->ptr<int32_t>(L.tcount), cn);
   scan(ctx, ctx->ptr<int32_t>(L.tcount), ctx->ptr<int32_t>(L.toff), LenSrc{&cn->n_tracks, 0, 0},
        &cn->n_track_clusters);
   {
