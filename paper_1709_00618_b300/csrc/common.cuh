@@ -121,6 +121,10 @@ struct KConst {
   // lanes of a warp of a refilling Kalman kernel that must be idle before
   // the warp fetches new work for them together (1: refill at once)
   int32_t refill;
+  // row steps a refilling Kalman kernel's lanes take between the warp's
+  // refill checks (fewer warp-wide votes on inputs bound by the longest
+  // tracklet; 1 on large inputs, where idle lanes cost throughput)
+  int32_t inner_steps;
 };
 
 // Trace record: pass (0 forward, 1 backward), row, updates since seed, then

@@ -453,7 +453,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p2(GridView g, const int32_t*
       continue;
     }
     if (go) {
-      go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+      for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
+        go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
       dirty = true;
     }
   }
@@ -584,7 +585,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p4(GridView g, const int32_t*
       if (!__any_sync(FULL_MASK, live)) break;
       continue;
     }
-    if (go) go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
+    for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
+      go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
   }
   tl.flush(cn, PH_FOLLOW_P4);
 }

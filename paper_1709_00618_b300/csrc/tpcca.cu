@@ -279,6 +279,7 @@ int fail(tpc_ctx* c, int code, const char* fmt, ...) {
 
 KConst make_kconst(const tpc_config& c, const Caps& caps) {
   KConst k{};
+  k.inner_steps = 1;
   k.K = (float)(0.299792458e-3 * c.bz_kg);
   k.V = (float)(c.sigma * c.sigma);
   k.Vd = c.sigma * c.sigma;
@@ -504,6 +505,7 @@ void enqueue_find(tpc_ctx* ctx) {
   int32_t* bin_base = ctx->ptr<int32_t>(L.bin_base);
   int32_t* bin_cnt = ctx->ptr<int32_t>(L.bin_cnt);
   int32_t* bin_start = ctx->ptr<int32_t>(L.bin_start);
+  ctx->kc.inner_steps = ctx->n < kLargeBatch ? 16 : 1;
   ctx->mark(0);
   // a2 grid
   k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax),
