@@ -407,12 +407,16 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
   tl.flush(cn, PH_FOLLOW_P1);
 }
 
-// Phase 2: the rest of the forward pass (covariance in FP32).  A lane
+// Phase 2: the rest of the forward pass (covariance in FP32).  MINB: CTAs
+// per SM the registers are budgeted for -- 4 (128 registers, no spills)
+// where the longest tracklet bounds the kernel, 8 (64 registers, a few
+// spills, twice the resident warps) on inputs that fill the GPU.  A lane
 // that finishes a tracklet idles until kc.refill lanes of its warp have,
 // then they store their results and take new tracklets together, so that
 // the refill runs with many lanes at once and no lane waits for the longest
 // tracklet of its warp.
-__global__ void __launch_bounds__(128, 4) k_follow_p2(GridView g, const int32_t* __restrict__ up_m, KConst kc,
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32_t* __restrict__ up_m, KConst kc,
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
                                                    int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
@@ -549,7 +553,8 @@ __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t 
 
 // Phase 4: the rest of the backward pass (FP32, lanes refill as in phase
 // 2) and the outputs.
-__global__ void __launch_bounds__(128, 4) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
                                                    int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];

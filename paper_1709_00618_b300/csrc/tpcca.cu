@@ -562,14 +562,16 @@ void enqueue_find(tpc_ctx* ctx) {
       if (after_p1) cudaEventRecord(after_p1, st);
       k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 0, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(0);
-      k_follow_p2<<<persistent_grid(ctx, k_follow_p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
+      auto p2 = ctx->n >= kLargeBatch ? k_follow_p2<8> : k_follow_p2<4>;
+      p2<<<persistent_grid(ctx, p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
       if (nc == 1) ctx->mark_k(1);
       k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, ctx->ctas_zone), bf, 0, st>>>(
           grid_view(ctx), ctx->kc, follow_out(ctx), W, work_order(ctx, 1, c), c, nc, cn);
       k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(2);
-      k_follow_p4<<<persistent_grid(ctx, k_follow_p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
+      auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<8> : k_follow_p4<4>;
+      p4<<<persistent_grid(ctx, p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
     };
     if (nc == 1) {
