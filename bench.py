@@ -369,6 +369,48 @@ def all_configs(local):
     print(json.dumps({"all_configs": rows}))
 
 
+def events_through_server(host_in, n, local, events=16, slots=4):
+    """The same event as a stream through the serving API (tpc_server_*):
+    `slots` events in flight, each copied in from page-locked host memory
+    and its tracks and cluster assignment copied back into page-locked
+    buffers; wall time from the first submission to the last result.  One
+    event alone is bound by its longest tracklet; several in flight fill the
+    GPU (the paper runs several events at once for the same reason)."""
+    import numpy as np
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    ring = slots + 2
+    with tpc.Server(device=local, max_slots=slots) as srv:
+        bufs = [(torch.zeros(n // 10 + 4096, 128, dtype=torch.uint8).pin_memory(),
+                 torch.zeros(n, dtype=torch.int32).pin_memory()) for _ in range(ring)]
+
+        def run(first, count):
+            nxt, done, inflight, tracks = 0, 0, [], 0
+            while done < count:
+                while nxt < count and len(inflight) < ring:
+                    if srv.submit(first + nxt, host_in, *bufs[nxt % ring]) != 0:
+                        break
+                    inflight.append(first + nxt)
+                    nxt += 1
+                r = srv.result(inflight[0])
+                if r is None:
+                    time.sleep(5e-5)
+                    continue
+                tracks = len(r[0])
+                inflight.pop(0)
+                done += 1
+            return tracks
+
+        run(0, ring)  # warm-up: arenas, graphs
+        t0 = time.perf_counter()
+        tracks = run(1000, events)
+        dt = time.perf_counter() - t0
+    return {"value": events * n / dt, "unit": UNIT, "events": events, "slots": slots,
+            "ms_per_event": 1e3 * dt / events, "h2d_bytes_per_event": 16 * n,
+            "d2h_bytes_per_event": 128 * tracks + 4 * n}
+
+
 def cluster_rejection(local, flush):
     """Cluster rejection on the central event with loopers (|eta| < 1.5,
     pT from 40 MeV/c, low-momentum secondaries, loopers over four
@@ -782,6 +824,7 @@ def main():
             e2e.append(time.perf_counter() - t0)
     e2e_t, _ = combine_ranks(sum(e2e) / len(e2e), n, world, f"cuda:{local}")
     trk.close()
+    served = events_through_server(host_in, n, local, events=max(4 * args.steps, 16), slots=4) if world == 1 else None
 
     clocks = clk.summary()
     traffic = ncu_traffic()
@@ -801,6 +844,7 @@ def main():
             "alu_peaks_measured": alu,
             "e2e": {"value": total_clusters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 128 * len(tr) + 4 * n},
+            "e2e_server": served,
             "gpu_launches": kernels_per_step * args.steps,
             "roofline": roof,
             "kernels": kernel_table,
