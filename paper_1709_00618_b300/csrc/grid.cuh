@@ -134,36 +134,48 @@ __global__ void k_grid_bin(const tpc_cluster* __restrict__ in, const int32_t* __
   }
 }
 
-__global__ void k_grid_scatter(const int32_t* __restrict__ gbin, const int32_t* __restrict__ slot,
-                               const int32_t* __restrict__ bin_start, int32_t* __restrict__ tmp,
-                               const Counts* cn) {
+// Each cluster's record {load index, y, z, row-sector} written at its place
+// in its bin (arrival order inside the bin), so that the ordering below
+// reads every record it needs from around its own position.
+__global__ void k_grid_scatter(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ rs_in,
+                               const int32_t* __restrict__ gbin, const int32_t* __restrict__ slot,
+                               const int32_t* __restrict__ bin_start, int4* __restrict__ rec, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
-  for (int64_t i = gtid(); i < n; i += gstride()) tmp[bin_start[gbin[i]] + slot[i]] = (int32_t)i;
+  for (int64_t i = gtid(); i < n; i += gstride()) {
+    const int4 raw = __ldg(reinterpret_cast<const int4*>(in) + i);
+    rec[bin_start[gbin[i]] + slot[i]] = make_int4((int32_t)i, raw.x, raw.y, rs_in[i]);
+  }
 }
 
 // Stable order inside each bin: rank = number of bin members with a smaller
 // load index.  Bins hold about two clusters on average (the bin edge is
-// sqrt(2 A / n)); the count is quadratic only in the fullest bin.  Also
-// clears the selection stage's per-cluster arrays (owner keys to 0, the
-// cluster-to-track map to -1), which are as long as the cluster list.
-__global__ void k_grid_order(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ tmp,
-                             const int32_t* __restrict__ gbin, const int32_t* __restrict__ rs_in,
+// sqrt(2 A / n)); the count is quadratic only in the fullest bin.  The bin
+// of a record is recomputed from its position with the binning arithmetic
+// of k_grid_bin.  Also clears the selection stage's per-cluster arrays
+// (owner keys to 0, the cluster-to-track map to -1), which are as long as the
+// cluster list.
+__global__ void k_grid_order(const int4* __restrict__ rec, const RsParams* __restrict__ par,
                              const int32_t* __restrict__ bin_start, int32_t* __restrict__ perm,
                              float2* __restrict__ yz, int32_t* __restrict__ rs_of, uint64_t* __restrict__ owner,
                              int32_t* __restrict__ cluster_track, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t p = gtid(); p < n; p += gstride()) {
-    int i = tmp[p];
-    int gb = gbin[i];
-    int a = bin_start[gb], b = bin_start[gb + 1];
+    const int4 r = rec[p];
+    const int i = r.x, rs = r.w;
+    const float y = __int_as_float(r.y), z = __int_as_float(r.z);
+    const RsParams P = load_params(par + rs);
+    const int row = rs % NROW;
+    const int gb = P.bin_base + bin_coord(z, P.z_lo, P.inv_z, P.n_z) * P.n_y +
+                   bin_coord(y, -g_row_yhi[row], P.inv_y, P.n_y);
+    const int a = bin_start[gb], b = bin_start[gb + 1];
     int rank = 0;
-    for (int q = a; q < b; q++) rank += tmp[q] < i;
-    int dst = a + rank;
+    for (int q = a; q < b; q++) rank += rec[q].x < i;
+    const int dst = a + rank;
     perm[dst] = i;
-    yz[dst] = __ldg(reinterpret_cast<const float2*>(in + i));
-    rs_of[dst] = rs_in[i];
+    yz[dst] = make_float2(y, z);
+    rs_of[dst] = rs;
     owner[p] = 0ull;
     cluster_track[p] = -1;
   }

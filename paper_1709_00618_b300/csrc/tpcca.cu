@@ -113,7 +113,7 @@ Layout make_layout(const Caps& c) {
   L.rs_in = take(4 * N);
   L.gbin = take(4 * N);
   L.slot = take(4 * N);
-  L.tmp = take(4 * N);
+  L.tmp = take(16 * N);  // records of the grid's counting sort
   L.perm = take(4 * N);
   L.yz = take(8 * N);
   L.rs_of = take(4 * N);
@@ -523,12 +523,12 @@ void enqueue_find(tpc_ctx* ctx) {
                                bin_cnt, ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), cn);
   LenSrc lb{&cn->n_bins, 0, 0};
   scan(ctx, bin_cnt, bin_start, lb, nullptr);
-  k_grid_scatter<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
-                                   ctx->ptr<int32_t>(L.tmp), cn);
-  k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.tmp), ctx->ptr<int32_t>(L.gbin),
-                                 ctx->ptr<int32_t>(L.rs_in), bin_start, ctx->ptr<int32_t>(L.perm),
-                                 ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<uint64_t>(L.owner),
-                                 ctx->ptr<int32_t>(L.cluster_track), cn);
+  k_grid_scatter<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.rs_in),
+                                   ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
+                                   ctx->ptr<int4>(L.tmp), cn);
+  k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<int4>(L.tmp), ctx->ptr<RsParams>(L.par), bin_start,
+                                 ctx->ptr<int32_t>(L.perm), ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
+                                 ctx->ptr<uint64_t>(L.owner), ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(1);
   // a3 neighbours
   k_neighbours<<<grid_for(ctx, C.n * NB_G, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
