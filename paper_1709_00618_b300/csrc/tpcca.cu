@@ -1617,8 +1617,9 @@ int tpc_merge_tracks(tpc_ctx* ctx, const tpc_merge_config* cfg_in) {
   k_merge_links<<<gM, bc, 0, s>>>(mb, cn);
   k_merge_heads<<<gM, bc, 0, s>>>(mb, cn);
   scan(ctx, mb.head, mb.chain_of_head, LenSrc{&cn->n_tracks, 0, 0}, mb.n);
-  k_merge_refit<<<grid_for(ctx, M, 128, 8), 128, 0, s>>>(tr, ctx->ptr<tpc_cluster>(ctx->L.in), refit_in(ctx),
-                                                         ctx->ptr<int32_t>(ctx->L.track_clusters), ctx->kc, mb, cn);
+  // a thread per segment, so that the chains of a warp start together
+  k_merge_refit<<<(int)((M + 127) / 128), 128, 0, s>>>(tr, ctx->ptr<tpc_cluster>(ctx->L.in), refit_in(ctx),
+                                                      ctx->ptr<int32_t>(ctx->L.track_clusters), ctx->kc, mb, cn);
   CK(cudaMemcpyAsync(ctx->h_merge_n, mb.n, 8, cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   ctx->merge_valid = true;
