@@ -6,9 +6,12 @@ for tracklets flagged as tainted on either side (a decision within the
 divergence margin, taken in FP32 on the GPU and FP64 in the oracle) and the
 tracklets sharing clusters with them; parameters within 1e-4 relative
 (floors 1 cm, 1 cm, 0.01, 0.01, 0.01 c/GeV), covariances within 1e-3 relative
-(floor 1e-3 sqrt(C_ii C_jj)).
+(to 0.1 sqrt(C_ii C_jj) where the entry is smaller than that).
 """
 from __future__ import annotations
+
+import json
+import os
 
 import numpy as np
 
@@ -312,3 +315,15 @@ def full_parity(trk, clusters, ref, req_offsets=None, graph=False, vertices=None
     if vertices is not None:
         compare_vertices(trk, tracks, ref, g, excl2, stats, **vertices)
     return stats
+
+
+# Where the GPU tests append their per-case error statistics (one JSON line
+# per case): TPC_PARITY_STATS_DIR, or parity_stats/ at the top of the repo.
+STATS_DIR = os.environ.get("TPC_PARITY_STATS_DIR",
+                           os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "parity_stats"))
+
+
+def record_stats(name, stats):
+    os.makedirs(STATS_DIR, exist_ok=True)
+    with open(os.path.join(STATS_DIR, "parity_stats.jsonl"), "a") as f:
+        f.write(json.dumps({"case": name, **stats}) + "\n")

@@ -1,26 +1,16 @@
 """Track-model compression on the GPU: the decompression restores every
 fixed-point cluster exactly (in the same and in a fresh context), and the
 encoding matches the FP64 oracle's up to rounding flips of the prediction."""
-import json
-import os
 
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from parity import compare_follow, compare_selection, follow_result
+from parity import compare_follow, compare_selection, follow_result, record_stats
 
 pytestmark = pytest.mark.gpu
 UNIT = 0.01
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-
-
-def _record(name, stats):
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "parity_stats.jsonl"), "a") as f:
-        f.write(json.dumps({"case": name, **stats}) + "\n")
-
 
 def _fixed_point(v):
     return np.rint(np.asarray(v, np.float32) * np.float32(1.0 / UNIT)).astype(np.int32)
@@ -75,7 +65,7 @@ def test_round_trip_is_exact_and_matches_the_oracle(which):
     hp = np.abs(c["heads"]["par"][gi] - inp["head"][ri])
     stats.update(codec_tracks=int(len(gi)), codec_clusters=int(len(gsel)), codec_flips=int(flips.sum()),
                  codec_head_abs_err_max=[float(v) for v in hp.max(0)] if len(hp) else [])
-    _record(f"codec_{which}", stats)
+    record_stats(f"codec_{which}", stats)
 
 
 def test_malformed_streams_are_rejected():

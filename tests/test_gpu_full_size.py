@@ -5,25 +5,18 @@ assignments of a few sectors of the full 10 ms timeframe (90 M clusters),
 and of a few requests of the 256-request batch, must be exactly those of
 the same sectors or requests tracked alone; those are then compared with
 the oracle stage by stage."""
-import json
-import os
 
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from parity import full_parity
+from parity import full_parity, record_stats
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+
+
 FIELDS = ("par", "cov", "chi2", "ndf", "n_clusters", "first_row", "last_row", "sector", "flags")
-
-
-def _record(name, stats):
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "parity_stats.jsonl"), "a") as f:
-        f.write(json.dumps({"case": name, **stats}) + "\n")
 
 
 def _same_as_alone(tracks, ct, sel_tracks, sel_clusters, ta, cta):
@@ -53,7 +46,7 @@ def test_full_timeframe_sampled_sectors():
         _same_as_alone(tracks, ct, np.isin(tracks["sector"], sectors), sel, ta, cta)
         stats = full_parity(t, sub, oracle.run(sub))
     stats.update(clusters_full=int(len(cl)), tracks_full=int(len(tracks)), sectors=list(sectors))
-    _record("timeframe_10ms_sectors_5_23", stats)
+    record_stats("timeframe_10ms_sectors_5_23", stats)
     assert len(tracks) > 2_000_000 and stats["tracks_compared"] > 0.8 * stats["tracks_ref"]
 
 
@@ -74,5 +67,5 @@ def test_full_batch_sampled_requests():
         for q in (int(np.argmax(sizes)), 97):
             stats = full_parity(t, reqs[q].clusters, oracle.run(reqs[q].clusters))
             stats.update(request=q, requests=256, clusters_batch=int(len(cl)))
-            _record(f"batch256_request_{q}", stats)
+            record_stats(f"batch256_request_{q}", stats)
             assert stats["tracks_compared"] > 0.8 * stats["tracks_ref"]

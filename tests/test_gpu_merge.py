@@ -2,8 +2,6 @@
 refit) against the FP64 oracle.  Pairs are compared on segments outside the
 exclusion shadow whose choices are clear (best chi2 not within 1e-3 of the
 second best on either side of the pair, and not within 1% of the cut)."""
-import json
-import os
 
 import numpy as np
 import pytest
@@ -11,16 +9,10 @@ import pytest
 import oracle
 import synth
 from oracle import merge
-from parity import PAR_TOL, COV_TOL, compare_follow, compare_selection, cov_rel_err, follow_result, par_rel_err
+from parity import (PAR_TOL, COV_TOL, compare_follow, compare_selection, cov_rel_err, follow_result, par_rel_err,
+                    record_stats)
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-
-
-def _record(name, stats):
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "parity_stats.jsonl"), "a") as f:
-        f.write(json.dumps({"case": name, **stats}) + "\n")
 
 
 def _near(a, b):
@@ -102,5 +94,5 @@ def test_merging_matches_the_oracle(which):
     stats.update(merge_pairs_checked=checked, merge_pair_mismatches=mism, merge_chains_gpu=int(len(gm["merged"])),
                  merge_chains_ref=int(len(mo["chains"])), merge_chains_compared=compared,
                  merge_par_err_max=float(max(pe_all)), merge_cov_err_max=float(max(ce_all)))
-    _record(f"merge_{which}", stats)
+    record_stats(f"merge_{which}", stats)
     assert stats["merge_par_err_max"] <= PAR_TOL and stats["merge_cov_err_max"] <= COV_TOL, stats

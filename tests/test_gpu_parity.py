@@ -1,23 +1,13 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
-import json
-import os
 
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from parity import full_parity
+from parity import full_parity, record_stats
 
 pytestmark = pytest.mark.gpu
-
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-
-
-def _record(name, stats):
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "parity_stats.jsonl"), "a") as f:
-        f.write(json.dumps({"case": name, **stats}) + "\n")
 
 
 @pytest.fixture(scope="module")
@@ -30,13 +20,13 @@ def trk():
 
 def test_one_sector(trk, sector_event, sector_oracle):
     stats = full_parity(trk, sector_event.clusters, sector_oracle)
-    _record("one_sector", stats)
+    record_stats("one_sector", stats)
     assert stats["tracks_compared"] > 50
 
 
 def test_six_sectors_both_sides(trk, small_event, small_oracle):
     stats = full_parity(trk, small_event.clusters, small_oracle)
-    _record("six_sectors", stats)
+    record_stats("six_sectors", stats)
     assert stats["tracks_compared"] > 200
 
 
@@ -44,7 +34,7 @@ def test_central_event_full_size(trk):
     ev = synth.central_event(seed=1)
     ref = oracle.run(ev.clusters)
     stats = full_parity(trk, ev.clusters, ref)
-    _record("central_event", stats)
+    record_stats("central_event", stats)
     assert stats["tracks_compared"] > 0.9 * stats["tracks_ref"]
 
 
@@ -62,7 +52,7 @@ def test_timeframe_slice(trk):
     ev = synth.timeframe(seed=2, length_ms=1.0)
     ref = oracle.run(ev.clusters)
     stats = full_parity(trk, ev.clusters, ref)
-    _record("timeframe_1ms", stats)
+    record_stats("timeframe_1ms", stats)
     assert stats["tracks_compared"] > 0.8 * stats["tracks_ref"]
 
 
@@ -72,7 +62,7 @@ def test_batch_of_requests(trk):
     off = np.concatenate([[0], np.cumsum([len(r.clusters) for r in reqs])])
     ref = oracle.run(cl, req_offsets=off)
     stats = full_parity(trk, cl, ref, req_offsets=off)
-    _record("batch12", stats)
+    record_stats("batch12", stats)
 
 
 def test_batch_result_equals_alone(trk):
@@ -152,6 +142,6 @@ def test_fp64_zone_keeps_assignments_of_the_fp64_oracle(trk):
             if not np.array_equal(g["f_hits"][t, :n], ref["f_hits"][t, :n]):
                 same[t] = False
         counts[zone] = int((~same & ~taint).sum())
-    _record("fp64_zone_effect", {"untainted_divergent_fp32_only": counts[0],
+    record_stats("fp64_zone_effect", {"untainted_divergent_fp32_only": counts[0],
                                  "untainted_divergent_with_zone": counts[max(counts)]})
     assert counts[max(counts)] == 0

@@ -5,8 +5,6 @@ except where a decision lies within its margin of a cut: momentum within
 0.1% of p_min, |dz/ds_T| within 1e-3 of tgl_max, the circle's reach within
 0.2 cm of the outermost row radius, the z distance within 0.2 cm of
 dz_leg.  Keep flags are compared on the clusters of the compared tracks."""
-import json
-import os
 
 import numpy as np
 import pytest
@@ -14,16 +12,9 @@ import pytest
 import oracle
 import synth
 from oracle import reject, vertex
-from parity import compare_follow, compare_selection, follow_result
+from parity import compare_follow, compare_selection, follow_result, record_stats
 
 pytestmark = pytest.mark.gpu
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-
-
-def _record(name, stats):
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "parity_stats.jsonl"), "a") as f:
-        f.write(json.dumps({"case": name, **stats}) + "\n")
 
 
 def _compare(name, cl, g, tracks, ct, gr, ref, orj):
@@ -51,7 +42,7 @@ def _compare(name, cl, g, tracks, ct, gr, ref, orj):
                  reject_class_mismatches=mism, reject_clusters_checked=int(sel.sum()),
                  reject_keep_mismatches=keep_mism, reject_fraction_gpu=float(1.0 - gr["cluster_keep"].mean()),
                  reject_fraction_oracle=float(1.0 - orj["keep"].mean()), **per)
-    _record(name, stats)
+    record_stats(name, stats)
     assert mism == 0 and keep_mism == 0, stats
     return stats
 

@@ -1,24 +1,14 @@
 """Vertex finding in the drift-time coordinate (Sec. 5) on the GPU against the
 FP64 oracle, on timeframe slices, through the C ABI."""
-import json
-import os
 
 import numpy as np
 import pytest
 
 import oracle
 import synth
-from parity import full_parity
+from parity import full_parity, record_stats
 
 pytestmark = pytest.mark.gpu
-
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
-
-
-def _record(name, stats):
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "parity_stats.jsonl"), "a") as f:
-        f.write(json.dumps({"case": name, **stats}) + "\n")
 
 
 @pytest.mark.parametrize("seed,length_ms", [(7, 0.3), (8, 1.0)])
@@ -28,7 +18,7 @@ def test_vertices_match_the_oracle(seed, length_ms):
     ref = oracle.run(ev.clusters)
     with tpc.Tracker(device=0) as t:
         stats = full_parity(t, ev.clusters, ref, vertices={})
-    _record(f"vertices_tf_{length_ms}ms", stats)
+    record_stats(f"vertices_tf_{length_ms}ms", stats)
     assert stats["vertices_compared"] >= 5
     assert stats["vertex_tracks_checked"] > 1000
 
