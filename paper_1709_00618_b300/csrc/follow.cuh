@@ -4,10 +4,10 @@
 // clusters and extending inward.
 //
 // The first `fp64_updates` Kalman updates after each (re)seed keep the
-// covariance in FP64; those operations are out of line (kalman.cuh) so that
-// the kernel body stays small enough for the instruction cache and the
-// binary32 path keeps its registers.  The lanes of a warp are consecutive
-// tracklets, which start on neighbouring rows, so their FP64 zones overlap.
+// covariance in FP64; only the zone kernels (phases 1 and 3) instantiate
+// that path, so the binary32 kernels keep their registers.  The lanes of a
+// warp are consecutive tracklets, which start on neighbouring rows, so their
+// FP64 zones overlap.
 #pragma once
 #include "kalman.cuh"
 #include "order.cuh"
@@ -118,6 +118,7 @@ struct Lane {
   uint32_t flags;
   bool seed_fail;
   bool tr;       // this tracklet is traced
+  bool snap;     // backward zone: sC is pending in the FP64 snapshot (zone_snap_take)
   Counts* cn;
   TrkState fwd;  // forward state after its last update
   // backward output: state after the last update
@@ -169,14 +170,34 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
                (float)chi2.value(), r0, r1);
 }
 
+// Output snapshot of the backward pass: the state after its last update.
+// Inside the FP64 zone the covariance is kept as FP64 in shared memory
+// (element i of a lane at snap[i * SNAP_STRIDE]) and rounded to binary32 once,
+// by zone_snap_take, instead of at every update: the FP64 pipe, which bounds
+// the zone, then does no conversions for updates that a later one replaces.
+constexpr int SNAP_STRIDE = 128;  // the largest block of the follow kernels
 template <bool Z>
 __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zone, const double* D, const float* C,
-                                            const Chi2Acc& chi2) {
+                                            const Chi2Acc& chi2, double* snap) {
   zone = Z && zone;
   w.sp = p;
-#pragma unroll
-  for (int i = 0; i < 15; i++) w.sC[i] = zone ? (float)D[i] : C[i];
   w.schi2 = chi2;
+  if (zone) {
+#pragma unroll
+    for (int i = 0; i < 15; i++) snap[i * SNAP_STRIDE] = D[i];
+    w.snap = true;
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 15; i++) w.sC[i] = C[i];
+  if (Z) w.snap = false;
+}
+__device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap) {
+  if (w.snap) {
+#pragma unroll
+    for (int i = 0; i < 15; i++) w.sC[i] = (float)snap[i * SNAP_STRIDE];
+    w.snap = false;
+  }
 }
 
 // One forward row step; false ends the pass.  The covariance is in D while
@@ -228,7 +249,8 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
 // One backward row step; false ends the pass.
 template <bool Z>
 __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, const float* sX, const float* sYH,
-                                         Lane& w, TrkState& p, double* D, float* C, Chi2Acc& chi2, LocalTally& tl) {
+                                         Lane& w, TrkState& p, double* D, float* C, Chi2Acc& chi2, LocalTally& tl,
+                                         double* snap) {
   const int r = p.row - 1;
   if (r < 0) return false;
   if (r >= 1 && r - 1 < w.r0) prefetch_l1(g.par + w.ubase + r - 1);  // the next step's row-sector parameters
@@ -259,7 +281,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
   lane_update<Z>(w, kc, p, zone, D, C, P, chi2, 1);
   if (zone) tl.upd64++;
   else tl.upd32++;
-  keep_output<Z>(w, p, w.nupd < kc.fp64_updates, D, C, chi2);
+  keep_output<Z>(w, p, w.nupd < kc.fp64_updates, D, C, chi2, snap);
   return true;
 }
 
@@ -471,8 +493,10 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
 __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W,
                                                    WorkOrder next, int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  __shared__ double sSnap[15 * SNAP_STRIDE];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
+  double* snap = sSnap + threadIdx.x;
   const Chunk ch = chunk_range(cn->n_tracklets, chunk, nchunk);
   LocalTally tl;
   double D[15];
@@ -490,6 +514,7 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
       w.hits = o.hits + t * NROW;
       w.hrow = o.hrow + t * NROW;
       w.cn = cn;
+      w.snap = false;
       if (!w.seed_fail) {
         p = w.fwd;
         chi2.reset();
@@ -507,12 +532,13 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
       lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
       if (zone0) tl.upd64++;
       else tl.upd32++;
-      keep_output<true>(w, p, w.nupd < kc.fp64_updates, D, C, chi2);
-      while (go && w.nupd < kc.fp64_updates) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
+      keep_output<true>(w, p, w.nupd < kc.fp64_updates, D, C, chi2, snap);
+      while (go && w.nupd < kc.fp64_updates) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap);
       if (w.nupd < kc.fp64_updates) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = (float)D[i];
       }
+      zone_snap_take(w, snap);
     }
     if (valid) work_store(W, t, w, p, C, chi2, go);
     order_count(next, t, valid, go ? p.row : 0);  // rows left inward
@@ -591,7 +617,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
       continue;
     }
     for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
-      go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl);
+      go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr);
   }
   tl.flush(cn, PH_FOLLOW_P4);
 }
