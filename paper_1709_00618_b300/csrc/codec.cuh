@@ -73,7 +73,7 @@ __device__ __noinline__ bool codec_track(const KConst& kc, const float* sX, cons
     nupd++;
     if (zone && nupd == kc.fp64_updates) {
 #pragma unroll
-      for (int k = 0; k < 15; k++) C[k] = (float)D[k];
+      for (int k = 0; k < 15; k++) C[k] = narrow(D[k]);
     }
   }
   return true;

@@ -161,7 +161,7 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
   w.nupd++;
   if (zone && w.nupd == kc.fp64_updates) {
 #pragma unroll
-    for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+    for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
   }
   if (w.tr)
     trace_line(w.cn, kc.trace, kc.trace_cap, (float)pass, (float)p.row, (float)w.nupd, p.y + p.yl,
@@ -195,7 +195,7 @@ __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zon
 __device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap) {
   if (w.snap) {
 #pragma unroll
-    for (int i = 0; i < 15; i++) w.sC[i] = (float)snap[i * SNAP_STRIDE];
+    for (int i = 0; i < 15; i++) w.sC[i] = narrow(snap[i * SNAP_STRIDE]);
     w.snap = false;
   }
 }
@@ -229,7 +229,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
     w.i++;
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
-    c = pick(g, w.ubase + r, r, p, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2], kc, sYH, w.flags,
+    c = pick(g, w.ubase + r, r, p, zone ? narrow(D[0]) : C[0], zone ? narrow(D[2]) : C[2], kc, sYH, w.flags,
              tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
   }
@@ -269,7 +269,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
     next_fwd_hit(w, g);
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
-    const int c = pick(g, w.ubase + r, r, p, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2], kc, sYH,
+    const int c = pick(g, w.ubase + r, r, p, zone ? narrow(D[0]) : C[0], zone ? narrow(D[2]) : C[2], kc, sYH,
                        w.flags, tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
     w.hits[w.nf + w.nb] = c;
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
       while (go && w.nupd < kc.fp64_updates) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
       if (w.nupd < kc.fp64_updates) {
 #pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }
       work_store(W, t, w, p, C, chi2, go);
     }
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
       while (go && w.nupd < kc.fp64_updates) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap);
       if (w.nupd < kc.fp64_updates) {
 #pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }
       zone_snap_take(w, snap);
     }

@@ -44,11 +44,6 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float d) {
   lo = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
   hi = s;
 }
-__device__ __forceinline__ void acc2(float& hi, float& lo, double d) {
-  const double v = ((double)hi + (double)lo) + d;
-  hi = (float)v;
-  lo = (float)(v - (double)hi);
-}
 
 // Square root and reciprocal of the binary32 Kalman arithmetic: the hardware
 // approximations (relative error about 1e-7, three orders below the parity
@@ -57,6 +52,39 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, double d) {
 __device__ __forceinline__ float ksqrt(float v) { return v * rsqrtf(v); }
 __device__ __forceinline__ float kinv(float v) { return __fdividef(1.0f, v); }
 __device__ __forceinline__ double kinv(double v) { return 1.0 / v; }
+
+// Conversions between binary32 and binary64 done with integer operations on
+// the IEEE 754 encodings (sign, biased exponent, fraction; binary32 bias 127,
+// binary64 bias 1023).  The FP64 zone is bound by the FP64 pipe (1/64 of the
+// FP32 rate on this part), which also executes the hardware conversions;
+// these sequences run on the integer pipes instead and give the same results
+// for zero, normal numbers, infinities and NaNs (binary32 subnormals, which the
+// zone's values never are, become zero).
+// Widening is exact: the 23 fraction bits move to the top of the 52.
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  const uint32_t e = u & 0x7F800000u;
+  const uint32_t mag = (u & 0x7FFFFFFFu) >> 3;  // exponent and the top 20 fraction bits, one word lower
+  const uint32_t hi_e = e == 0x7F800000u ? (mag | 0x7FF00000u) : mag + (896u << 20);  // rebias by 1023 - 127
+  const uint32_t hi = (u & 0x80000000u) | (e == 0u ? 0u : hi_e);
+  const uint32_t lo = e == 0u ? 0u : (u << 29);
+  return __hiloint2double((int)hi, (int)lo);
+}
+// Narrowing rounds to nearest, ties to even: the top 23 of the 52 fraction
+// bits are kept and the 29 discarded ones decide the increment, which may
+// carry into the exponent (up to infinity, as IEEE 754 overflow does).
+__device__ __forceinline__ float narrow(double d) {
+  const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  uint32_t r = ((uint32_t)(e - 896) << 23) + (((hi & 0x000FFFFFu) << 3) | (lo >> 29));
+  const uint32_t rest = lo & 0x1FFFFFFFu;
+  r += (rest > 0x10000000u || (rest == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  if (e == 0x7FF) r = ((hi & 0x000FFFFFu) | lo) ? 0x7FC00000u : 0x7F800000u;  // NaN, infinity
+  else if (e - 896 > 254) r = 0x7F800000u;                                        // overflow
+  else if (e - 896 < 1) r = 0u;                                                   // below the normal range
+  return __uint_as_float(sign | r);
+}
 
 // C <- J C J^T for the sparse first-order Jacobian of one propagation step.
 template <typename T>
@@ -200,7 +228,7 @@ __device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, cons
 // zone path, so they do not carry this code.
 __device__ __forceinline__ void cov_transport_d(double* D, float j02, float j04, float j24, float j12, float j13,
                                              float j14) {
-  cov_transport<double>(D, j02, j04, j24, j12, j13, j14);
+  cov_transport<double>(D, widen(j02), widen(j04), widen(j24), widen(j12), widen(j13), widen(j14));
 }
 
 struct UpdOut {
@@ -228,12 +256,12 @@ __device__ __forceinline__ UpdOut kalman_update_d(double* D, float r0, float r1,
 #pragma unroll
     for (int j = 0; j <= i; j++) D[TPC_CI(i, j)] = fma(-g0[i], k0[j], fma(-g1[i], k1[j], D[TPC_CI(i, j)]));
   UpdOut o;
-  o.d0 = (float)g0[0] * r0 + (float)g1[0] * r1;
-  o.d1 = (float)g0[1] * r0 + (float)g1[1] * r1;
-  o.d2 = (float)g0[2] * r0 + (float)g1[2] * r1;
-  o.d3 = (float)g0[3] * r0 + (float)g1[3] * r1;
-  o.d4 = (float)g0[4] * r0 + (float)g1[4] * r1;
-  const float i00 = (float)I00, i01 = (float)I01, i11 = (float)I11;
+  o.d0 = narrow(g0[0]) * r0 + narrow(g1[0]) * r1;
+  o.d1 = narrow(g0[1]) * r0 + narrow(g1[1]) * r1;
+  o.d2 = narrow(g0[2]) * r0 + narrow(g1[2]) * r1;
+  o.d3 = narrow(g0[3]) * r0 + narrow(g1[3]) * r1;
+  o.d4 = narrow(g0[4]) * r0 + narrow(g1[4]) * r1;
+  const float i00 = narrow(I00), i01 = narrow(I01), i11 = narrow(I11);
   o.chi2 = r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
   return o;
 }

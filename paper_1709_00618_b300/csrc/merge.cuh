@@ -393,13 +393,13 @@ __global__ void __launch_bounds__(128) k_merge_refit(const tpc_track* __restrict
         nupd++;
         if (zone && nupd == kc.fp64_updates) {
 #pragma unroll
-          for (int q = 0; q < 15; q++) C[q] = (float)D[q];
+          for (int q = 0; q < 15; q++) C[q] = narrow(D[q]);
         }
       }
     }
     if (ok && nupd < kc.fp64_updates) {
 #pragma unroll
-      for (int q = 0; q < 15; q++) C[q] = (float)D[q];
+      for (int q = 0; q < 15; q++) C[q] = narrow(D[q]);
     }
     const tpc_track I = tr[seg[0]];
     tpc_track out;

@@ -195,7 +195,7 @@ __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, 
     nupd++;
     if (zone && nupd == kc.fp64_updates) {
 #pragma unroll
-      for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+      for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
     }
     w.j++;
     w.advance();
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst
       nupd = 1;
       if (zone0 && nupd == ZONE) {
 #pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }
       w.j++;
       w.advance();
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst
       while (go && nupd < ZONE) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
       if (nupd < ZONE) {
 #pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = (float)D[i];
+        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }
     }
     order_count(next, m, valid, go && ok ? p.row - w.r_in : 0);  // rows left inward
