@@ -462,7 +462,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
     if (need & (1u << (threadIdx.x & 31))) {
       if (dirty) work_store(W, t, w, p, C, chi2, false);
       const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P2, chunk), need);
-      t = idx < ch.end ? order[idx] : T;
+      t = idx < ch.end ? (order ? order[idx] : idx) : T;
       dirty = false;
       if (t < T) {
         work_load(W, t, w, p, C, chi2);
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
     if (need & (1u << (threadIdx.x & 31))) {
       if (t >= 0) write_follow_output(o, t, w, __ldg(g.yz + tl_start[t]).y);
       const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P4, chunk), need);
-      t = idx < ch.end ? order[idx] : T;
+      t = idx < ch.end ? (order ? order[idx] : idx) : T;
       if (t < T) {
         go = work_load(W, t, w, p, C, chi2);
         w.hits = o.hits + t * NROW;

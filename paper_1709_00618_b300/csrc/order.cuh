@@ -4,7 +4,11 @@
 // producing kernel files each item under its remaining-row class (a
 // warp-aggregated histogram), k_order turns the classes into positions, and
 // the refilling kernel fetches order[0], order[1], ...  Every item is
-// independent, so the order changes no result.
+// independent, so the order changes no result.  On inputs that fill the GPU
+// the follow kernels take tracklets in index order instead (no order[]):
+// indices follow the clusters' (request, sector, row) order, so the
+// tracklets in flight share a few sectors' clusters, which then stay in L2,
+// and the tail of the kernel is short against its length.
 #pragma once
 #include "common.cuh"
 
@@ -25,6 +29,7 @@ struct WorkOrder {
 // Files item i (lanes with valid) under the class of `rem` remaining rows.
 // All 32 lanes of the warp make the call.
 __device__ __forceinline__ void order_count(const WorkOrder& o, int64_t i, bool valid, int rem) {
+  if (!o.key) return;  // index order
   const int b = NROW - 1 - min(max(rem, 0), NROW - 1);
   if (valid) o.key[i] = (uint8_t)b;
   const unsigned peers = __match_any_sync(FULL_MASK, valid ? b : -1);

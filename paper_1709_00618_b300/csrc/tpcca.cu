@@ -554,21 +554,27 @@ void enqueue_find(tpc_ctx* ctx) {
     FollowWork* W = ctx->ptr<FollowWork>(L.fwork);
     const int bf = ctx->block_follow;
     const int nc = ctx->prof ? 1 : effective_chunks(ctx);
-    int32_t* order = ctx->ptr<int32_t>(L.order);
+    // longest first below kLargeBatch clusters, where the longest tracklet
+    // bounds the refilling kernels; index order above (order.cuh)
+    const bool longest_first = ctx->n < kLargeBatch;
+    int32_t* order = longest_first ? ctx->ptr<int32_t>(L.order) : nullptr;
+    auto ord = [&](int phase, int c) { return longest_first ? work_order(ctx, phase, c) : WorkOrder{}; };
     auto follow_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
       k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, ctx->ctas_zone), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
-          ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, work_order(ctx, 0, c), c, nc, cn);
+          ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, ord(0, c), c, nc, cn);
       if (after_p1) cudaEventRecord(after_p1, st);
-      k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 0, c), &cn->n_tracklets, c, nc, cn);
+      if (longest_first)
+        k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 0, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(0);
       auto p2 = ctx->n >= kLargeBatch ? k_follow_p2<8> : k_follow_p2<4>;
       p2<<<persistent_grid(ctx, p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
       if (nc == 1) ctx->mark_k(1);
       k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, ctx->ctas_zone), bf, 0, st>>>(
-          grid_view(ctx), ctx->kc, follow_out(ctx), W, work_order(ctx, 1, c), c, nc, cn);
-      k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
+          grid_view(ctx), ctx->kc, follow_out(ctx), W, ord(1, c), c, nc, cn);
+      if (longest_first)
+        k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(2);
       auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<8> : k_follow_p4<4>;
       p4<<<persistent_grid(ctx, p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
