@@ -88,14 +88,14 @@ class ClockSampler:
 # Algorithmic work of the Kalman kernels, counted from the source per unit of
 # the device work counters (an FMA counts 2, an add, multiply, divide or
 # square root 1):
-#   helix step of the state with its Jacobian, binary32        76
-#   covariance transport J C J^T (51 FMA on the packed triangle) 102
+#   helix step of the state with its Jacobian, binary32        67
+#   covariance transport J C J^T (42 FMA on the packed triangle)  84
 #   Kalman update, gain and covariance (in the covariance type)  99
 #   Kalman update, residuals, state and chi2 (binary32)          56
 #   candidate cluster examined by the gated pick-up              10
 # FP32-zone work is all binary32; in the FP64 zone the transport and the
 # covariance part of the update run in binary64.
-FLOP_STATE, FLOP_TRANSPORT, FLOP_UPD_COV, FLOP_UPD_STATE, FLOP_CAND = 76, 102, 99, 56, 10
+FLOP_STATE, FLOP_TRANSPORT, FLOP_UPD_COV, FLOP_UPD_STATE, FLOP_CAND = 67, 84, 99, 56, 10
 # Algorithmic DRAM bytes per cluster of the memory-bound stages: grid 44
 # (the 16 B record read, 16 B of sorted output -- y/z, row-sector, input
 # index -- written, a 4 B bin index written and half of the records read

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) k_merge_pairs(const tpc_track* __restrict
             const float d[5] = {(p.y + p.yl) - B.par[0], (p.zref + (p.z + p.zl)) - B.par[1],
                                 (p.s + p.sl) - B.par[2], p.t - B.par[3], p.q - B.par[4]};
             if (!(fabsf(d[1]) <= mc.window)) continue;
-            cov_transport<float>(C, J.j02, J.j04, J.j24, J.j12, J.j13, J.j14);
+            cov_transport<float>(C, J.j02, J.j12, J.j13, J.kap);
 #pragma unroll
             for (int q = 0; q < 15; q++) C[q] += B.cov[q];
             const float c2 = chi2_5(d, C);
