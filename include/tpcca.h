@@ -98,7 +98,10 @@ typedef struct {
   double s_max;        /* |sin phi| limit of the propagation; 0.95 */
   double edge;         /* cm beyond the sector edge that end an extension; 2 */
   double taint_rel;    /* divergence margin for the taint flags; 2e-3 */
-  int32_t fp64_updates;/* Kalman updates after each seed done in FP64; 10 */
+  int32_t fp64_updates;/* Kalman updates after each seed done in FP64; 10.
+                          Outside the forward pass, up to as many again while
+                          the last one still more than halved the variance of
+                          sin phi, dz/ds_T or q/pT */
   int32_t reserved;
 } tpc_config;
 

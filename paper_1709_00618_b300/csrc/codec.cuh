@@ -47,12 +47,12 @@ __device__ __noinline__ bool codec_track(const KConst& kc, const float* sX, cons
   cov_seed<double>(D, kc);
   cov_seed<float>(C, kc);
   uint32_t flags = 0;
-  int nupd = 0;
+  int nupd = 0, zend = kc.fp64_updates;
   int row = h.row_out;
   for (int64_t i = 0; i < n; i++) {
     while (row > rows[i]) {
       row--;
-      if (!propagate_any(p, nupd < kc.fp64_updates, D, C, row, sX[row], kc, flags)) return false;
+      if (!propagate_any(p, nupd < zend, D, C, row, sX[row], kc, flags)) return false;
     }
     const int32_t py = (int32_t)rintf(__fmul_rn(p.y + p.yl, inv));
     const int32_t pz = (int32_t)rintf(__fmul_rn(p.zref + (p.z + p.zl), inv));
@@ -68,13 +68,8 @@ __device__ __noinline__ bool codec_track(const KConst& kc, const float* sX, cons
       ry[i] = a - py;
       rz[i] = b - pz;
     }
-    const bool zone = nupd < kc.fp64_updates;
-    update_any(p, zone, D, C, __fmul_rn((float)a, unit), __fmul_rn((float)b, unit), kc);
-    nupd++;
-    if (zone && nupd == kc.fp64_updates) {
-#pragma unroll
-      for (int k = 0; k < 15; k++) C[k] = narrow(D[k]);
-    }
+    zone_update(p, nupd < zend, D, C, __fmul_rn((float)a, unit), __fmul_rn((float)b, unit), kc, nupd, zend,
+                2 * kc.fp64_updates);
   }
   return true;
 }

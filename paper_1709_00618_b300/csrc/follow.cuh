@@ -4,8 +4,9 @@
 // clusters and extending inward.
 //
 // The first `fp64_updates` Kalman updates after each (re)seed keep the
-// covariance in FP64; only the zone kernels (phases 1 and 3) instantiate
-// that path, so the binary32 kernels keep their registers.  The lanes of a
+// covariance in FP64 (in the backward pass a few more while it is still
+// converging, zone_update); only the zone kernels (phases 1 and 3) instantiate that
+// path, so the binary32 kernels keep their registers.  The lanes of a
 // warp are consecutive tracklets, which start on neighbouring rows, so their
 // FP64 zones overlap.
 #pragma once
@@ -112,6 +113,7 @@ struct Lane {
   int kf;       // next forward hit to refit (backward)
   int misses;
   int nupd;     // updates since the last (re)seed
+  int zend;     // update count that ends the FP64 zone (zone_update)
   int nx_row;   // backward: row of forward hit kf (-1: none), its index and position, loaded a step ahead
   int nx_c;
   float2 nx_yz;
@@ -157,12 +159,7 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
                                             float2 P, Chi2Acc& chi2, int pass) {
   zone = Z && zone;
   const float r0 = residual_y(p, P.x), r1 = residual_z(p, P.y);
-  chi2.add(update_any(p, zone, D, C, P.x, P.y, kc));
-  w.nupd++;
-  if (zone && w.nupd == kc.fp64_updates) {
-#pragma unroll
-    for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
-  }
+  chi2.add(zone_update(p, zone, D, C, P.x, P.y, kc, w.nupd, w.zend, pass ? 2 * kc.fp64_updates : kc.fp64_updates));
   if (w.tr)
     trace_line(w.cn, kc.trace, kc.trace_cap, (float)pass, (float)p.row, (float)w.nupd, p.y + p.yl,
                p.zref + (p.z + p.zl), p.s + p.sl, p.t, p.q, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2],
@@ -210,7 +207,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
   if (r >= NROW) return false;
   if (r + 1 < NROW) prefetch_l1(g.par + w.ubase + r + 1);  // the next step's row-sector parameters
   const bool chain = w.i < w.L;
-  const bool zone = Z && w.nupd < kc.fp64_updates;
+  const bool zone = Z && w.nupd < w.zend;
   float2 Pc;
   int c = -1;
   if (chain) {  // the chain's cluster and the one after it are loaded while the state propagates
@@ -254,7 +251,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
   const int r = p.row - 1;
   if (r < 0) return false;
   if (r >= 1 && r - 1 < w.r0) prefetch_l1(g.par + w.ubase + r - 1);  // the next step's row-sector parameters
-  const bool zone = Z && w.nupd < kc.fp64_updates;
+  const bool zone = Z && w.nupd < w.zend;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (r >= w.r0) w.flags |= TF_BACK_FAIL;
     return false;
@@ -281,7 +278,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
   lane_update<Z>(w, kc, p, zone, D, C, P, chi2, 1);
   if (zone) tl.upd64++;
   else tl.upd32++;
-  keep_output<Z>(w, p, w.nupd < kc.fp64_updates, D, C, chi2, snap);
+  keep_output<Z>(w, p, w.nupd < w.zend, D, C, chi2, snap);
   return true;
 }
 
@@ -408,6 +405,7 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
       chi2.reset();
       reseed_cov(kc, D, C);
       w.nupd = 0;
+      w.zend = kc.fp64_updates;
     }
     __syncwarp();  // the zones of the warp's lanes start together
     if (valid) {
@@ -417,8 +415,8 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
       else tl.upd32++;
       w.fwd = p;
       go = true;
-      while (go && w.nupd < kc.fp64_updates) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
-      if (w.nupd < kc.fp64_updates) {
+      while (go && w.nupd < w.zend) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+      if (w.nupd < w.zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }
@@ -523,6 +521,7 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
         w.misses = 0;
         reseed_cov(kc, D, C);
         w.nupd = 0;
+        w.zend = kc.fp64_updates;
         go = true;
       }
     }
@@ -532,9 +531,9 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
       lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
       if (zone0) tl.upd64++;
       else tl.upd32++;
-      keep_output<true>(w, p, w.nupd < kc.fp64_updates, D, C, chi2, snap);
-      while (go && w.nupd < kc.fp64_updates) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap);
-      if (w.nupd < kc.fp64_updates) {
+      keep_output<true>(w, p, w.nupd < w.zend, D, C, chi2, snap);
+      while (go && w.nupd < w.zend) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap);
+      if (w.nupd < w.zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }

@@ -238,33 +238,55 @@ struct UpdOut {
   float chi2;                // r^T S^-1 r
 };
 
-// Kalman update of the FP64 covariance D for residual (r0, r1).
+// 1/v in binary64 for v in the binary32 normal range: the binary32
+// reciprocal of the narrowed v (relative error about 2^-23) refined by two
+// Newton-Raphson steps r <- r + r (1 - v r), each of which squares the
+// relative error, so that the result is within rounding of 1/v.
+__device__ __forceinline__ double krcp(double v) {
+  double r = widen(__frcp_rn(narrow(v)));
+  double e = fma(-v, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-v, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Kalman update of the FP64 covariance D for residual (r0, r1).  The
+// measurement covariance is V I, so the update with (y, z) equals an update
+// with y followed by one with z on the updated covariance (sequential
+// processing of uncorrelated measurement components): two rank-one
+// downdates with scalar gains, 50 binary64 operations with no 2x2 inverse.
+// The binary32 outputs are the state increment w0 r0 + w1 e1, where e1 is
+// the z residual after the y step, and the chi2 increment r0^2/s0 + e1^2/s1
+// (= r^T S^-1 r).
 __device__ __forceinline__ UpdOut kalman_update_d(double* D, float r0, float r1, double V) {
-  const double S00 = D[0] + V, S01 = D[1], S11 = D[2] + V;
-  const double idet = 1.0 / (S00 * S11 - S01 * S01);
-  const double I00 = S11 * idet, I01 = -S01 * idet, I11 = S00 * idet;
+  // y: gain w0 = C[:,y] / s0
+  const double s0 = D[0] + V, i0 = krcp(s0);
   const double k0[5] = {D[0], D[1], D[3], D[6], D[10]};
-  const double k1[5] = {D[1], D[2], D[4], D[7], D[11]};
-  double g0[5], g1[5];
+  double w0[5];
 #pragma unroll
-  for (int i = 0; i < 5; i++) {
-    g0[i] = k0[i] * I00 + k1[i] * I01;
-    g1[i] = k0[i] * I01 + k1[i] * I11;
-  }
-  // C -= G C[0:2,:], two fused multiply-adds per entry (the FP64 pipe is
-  // the bound of the zone)
+  for (int i = 0; i < 5; i++) w0[i] = k0[i] * i0;
 #pragma unroll
   for (int i = 0; i < 5; i++)
 #pragma unroll
-    for (int j = 0; j <= i; j++) D[TPC_CI(i, j)] = fma(-g0[i], k0[j], fma(-g1[i], k1[j], D[TPC_CI(i, j)]));
+    for (int j = 0; j <= i; j++) D[TPC_CI(i, j)] = fma(-w0[i], k0[j], D[TPC_CI(i, j)]);
+  // z on the updated covariance: gain w1 = C'[:,z] / s1
+  const double s1 = D[2] + V, i1 = krcp(s1);
+  const double k1[5] = {D[1], D[2], D[4], D[7], D[11]};
+  double w1[5];
+#pragma unroll
+  for (int i = 0; i < 5; i++) w1[i] = k1[i] * i1;
+#pragma unroll
+  for (int i = 0; i < 5; i++)
+#pragma unroll
+    for (int j = 0; j <= i; j++) D[TPC_CI(i, j)] = fma(-w1[i], k1[j], D[TPC_CI(i, j)]);
+  const float e1 = r1 - narrow(w0[1]) * r0;
   UpdOut o;
-  o.d0 = narrow(g0[0]) * r0 + narrow(g1[0]) * r1;
-  o.d1 = narrow(g0[1]) * r0 + narrow(g1[1]) * r1;
-  o.d2 = narrow(g0[2]) * r0 + narrow(g1[2]) * r1;
-  o.d3 = narrow(g0[3]) * r0 + narrow(g1[3]) * r1;
-  o.d4 = narrow(g0[4]) * r0 + narrow(g1[4]) * r1;
-  const float i00 = narrow(I00), i01 = narrow(I01), i11 = narrow(I11);
-  o.chi2 = r0 * (i00 * r0 + i01 * r1) + r1 * (i01 * r0 + i11 * r1);
+  o.d0 = narrow(w0[0]) * r0 + narrow(w1[0]) * e1;
+  o.d1 = narrow(w0[1]) * r0 + narrow(w1[1]) * e1;
+  o.d2 = narrow(w0[2]) * r0 + narrow(w1[2]) * e1;
+  o.d3 = narrow(w0[3]) * r0 + narrow(w1[3]) * e1;
+  o.d4 = narrow(w0[4]) * r0 + narrow(w1[4]) * e1;
+  o.chi2 = r0 * r0 * narrow(i0) + e1 * e1 * narrow(i1);
   return o;
 }
 
@@ -282,6 +304,34 @@ __device__ __forceinline__ float update_any(TrkState& p, bool zone, double* D, f
     return o.chi2;
   }
   return kalman_update<float>(p, C, my, mz, kc.V);
+}
+
+// The FP64 zone after a (re)seed holds the first kc.fp64_updates Kalman
+// updates.  In the passes whose covariance is an output (the backward pass,
+// the refits, the codec's fit) it holds, up to twice as many, further ones
+// while the last update still more than halved the variance of sin phi,
+// dz/ds_T or q/pT: the covariance is then still converging, and the next
+// update's subtraction C -= G C[0:2,:] would cancel leading digits of those
+// entries in binary32.  The forward pass, whose covariance only gates the
+// pick-up, keeps the fixed count.
+// zone_update makes one update (covariance in D inside the zone, else in C),
+// counts it in nupd and moves the covariance into C when the zone ends with
+// it; zend, kc.fp64_updates at the (re)seed, is the count that ends the zone,
+// zmax the largest it may become.
+__device__ __forceinline__ float zone_update(TrkState& p, bool zone, double* D, float* C, float my, float mz,
+                                             const KConst& kc, int& nupd, int& zend, int zmax) {
+  const double b5 = D[5], b9 = D[9], b14 = D[14];
+  const float x = update_any(p, zone, D, C, my, mz, kc);
+  nupd++;
+  if (zone && nupd == zend) {
+    if (zend < zmax && (b5 > 2.0 * D[5] || b9 > 2.0 * D[9] || b14 > 2.0 * D[14])) {
+      zend++;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+    }
+  }
+  return x;
 }
 
 // Propagation with the covariance in FP64 (zone) or FP32.

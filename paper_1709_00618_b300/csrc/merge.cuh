@@ -366,38 +366,31 @@ __global__ void __launch_bounds__(128) k_merge_refit(const tpc_track* __restrict
     cov_seed<float>(C, kc);
     Chi2Acc chi2;
     chi2.reset();
-    int nupd = 0;
+    int nupd = 0, zend = kc.fp64_updates;
     int row = O.last_row;
     for (int gi = ns - 1; ok && gi >= 0; gi--) {
       const tpc_track S = tr[seg[gi]];
       if (gi < ns - 1) {
         const float beta = sector_angle(S.sector) - sector_angle(tr[seg[gi + 1]].sector);
-        ok = nupd < kc.fp64_updates ? rotate_state<double>(p, D, beta) : rotate_state<float>(p, C, beta);
+        ok = nupd < zend ? rotate_state<double>(p, D, beta) : rotate_state<float>(p, C, beta);
         row = NROW;  // the next step goes to this segment's first cluster row
       }
       const int64_t off = S.cluster_offset, n = S.n_clusters;
       for (int64_t i = n - 1; ok && i >= 0; i--) {
         const tpc_cluster c = in[track_clusters[off + i]];
         if (row == NROW) {
-          const bool zone = nupd < kc.fp64_updates;
-          ok = propagate_any(p, zone, D, C, c.row, sX[c.row], kc, flags);
+          ok = propagate_any(p, nupd < zend, D, C, c.row, sX[c.row], kc, flags);
           row = c.row;
         }
         while (ok && row > c.row) {
           row--;
-          ok = propagate_any(p, nupd < kc.fp64_updates, D, C, row, sX[row], kc, flags);
+          ok = propagate_any(p, nupd < zend, D, C, row, sX[row], kc, flags);
         }
         if (!ok) break;
-        const bool zone = nupd < kc.fp64_updates;
-        chi2.add(update_any(p, zone, D, C, c.y, c.z, kc));
-        nupd++;
-        if (zone && nupd == kc.fp64_updates) {
-#pragma unroll
-          for (int q = 0; q < 15; q++) C[q] = narrow(D[q]);
-        }
+        chi2.add(zone_update(p, nupd < zend, D, C, c.y, c.z, kc, nupd, zend, 2 * kc.fp64_updates));
       }
     }
-    if (ok && nupd < kc.fp64_updates) {
+    if (ok && nupd < zend) {
 #pragma unroll
       for (int q = 0; q < 15; q++) C[q] = narrow(D[q]);
     }

@@ -177,10 +177,10 @@ struct RefitLane {
 template <bool Z>
 __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, const float* sX, RefitLane& w,
                                            TrkState& p, double* D, float* C, Chi2Acc& chi2, int& nupd, bool& ok,
-                                           uint32_t& flags, LocalTally& tl) {
+                                           uint32_t& flags, LocalTally& tl, int& zend) {
   const int r = p.row - 1;
   if (r < w.r_in) return false;
-  const bool zone = Z && nupd < kc.fp64_updates;
+  const bool zone = Z && nupd < zend;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, flags)) {
     ok = false;
     return false;
@@ -189,14 +189,9 @@ __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, 
   tl.prop64 += zone;
   if (w.cur_row == r) {
     const float2 P = w.cur_yz;
-    chi2.add(update_any(p, zone, D, C, P.x, P.y, kc));
+    chi2.add(zone_update(p, zone, D, C, P.x, P.y, kc, nupd, zend, 2 * kc.fp64_updates));
     if (zone) tl.upd64++;
     else tl.upd32++;
-    nupd++;
-    if (zone && nupd == kc.fp64_updates) {
-#pragma unroll
-      for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
-    }
     w.j++;
     w.advance();
   }
@@ -282,19 +277,15 @@ __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst
       cov_seed<double>(D, kc);
       cov_seed<float>(C, kc);
       const bool zone0 = ZONE > 0;
-      chi2.add(update_any(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc));
+      int zend = ZONE;
+      chi2.add(zone_update(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc, nupd, zend, 2 * ZONE));
       if (zone0) tl.upd64++;
       else tl.upd32++;
-      nupd = 1;
-      if (zone0 && nupd == ZONE) {
-#pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
-      }
       w.j++;
       w.advance();
       go = true;
-      while (go && nupd < ZONE) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
-      if (nupd < ZONE) {
+      while (go && nupd < zend) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend);
+      if (nupd < zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }
@@ -406,7 +397,8 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
       if (!__any_sync(FULL_MASK, live)) break;
       continue;
     }
-    if (go) go = refit_step<false>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl);
+    int zend = 0;  // the zone is over
+    if (go) go = refit_step<false>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend);
   }
   tl.flush(cn, PH_REFIT_P2);
 }
