@@ -320,6 +320,69 @@ __device__ __forceinline__ bool work_load(const FollowWork* W, int64_t t, Lane& 
   return s.go != 0;
 }
 
+// The binary32 phases touch only their half of the parked lane, so that
+// neither carries the other's state in registers (the 64-register builds
+// spilled it) nor moves it to and from memory.  Phase 2 reads the forward
+// fields and writes back what phase 3 uses (the forward state after its last
+// update, the forward hit count and the flags; phase 3 re-seeds, so the
+// running state, covariance and chi2 of phase 2 are not kept).  Phase 4 reads
+// the backward fields.
+__device__ __forceinline__ bool fwd_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
+                                         Chi2Acc& chi2) {
+  const FollowWork& s = W[t];
+  w.ubase = s.w.ubase;
+  w.L = s.w.L;
+  w.nf = s.w.nf;
+  w.k = s.w.k;
+  w.nk = s.w.nk;
+  w.i = s.w.i;
+  w.r_last = s.w.r_last;
+  w.misses = s.w.misses;
+  w.nupd = s.w.nupd;
+  w.flags = s.w.flags;
+  w.seed_fail = s.w.seed_fail;
+  w.tr = s.w.tr;
+  w.fwd = s.w.fwd;
+  p = s.p;
+#pragma unroll
+  for (int i = 0; i < 15; i++) C[i] = s.C[i];
+  chi2 = s.chi2;
+  return s.go != 0;
+}
+__device__ __forceinline__ void fwd_store(FollowWork* W, int64_t t, const Lane& w) {
+  FollowWork& s = W[t];
+  s.w.nf = w.nf;
+  s.w.flags = w.flags;
+  s.w.seed_fail = w.seed_fail;
+  s.w.fwd = w.fwd;
+}
+__device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
+                                         Chi2Acc& chi2) {
+  const FollowWork& s = W[t];
+  w.ubase = s.w.ubase;
+  w.r0 = s.w.r0;
+  w.nf = s.w.nf;
+  w.nb = s.w.nb;
+  w.kf = s.w.kf;
+  w.misses = s.w.misses;
+  w.nupd = s.w.nupd;
+  w.nx_row = s.w.nx_row;
+  w.nx_c = s.w.nx_c;
+  w.nx_yz = s.w.nx_yz;
+  w.flags = s.w.flags;
+  w.seed_fail = s.w.seed_fail;
+  w.tr = s.w.tr;
+  w.sp = s.w.sp;
+#pragma unroll
+  for (int i = 0; i < 15; i++) w.sC[i] = s.w.sC[i];
+  w.schi2 = s.w.schi2;
+  p = s.p;
+#pragma unroll
+  for (int i = 0; i < 15; i++) C[i] = s.C[i];
+  chi2 = s.chi2;
+  return s.go != 0;
+}
+
 // Work distribution of the persistent Kalman kernels: the lanes in `need`,
 // all of which make this call, take consecutive indices of *counter with one
 // atomic for the warp.
@@ -458,16 +521,15 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
   for (;;) {
     const unsigned need = refill_mask(live && !go, go, kc.refill);
     if (need & (1u << (threadIdx.x & 31))) {
-      if (dirty) work_store(W, t, w, p, C, chi2, false);
+      if (dirty) fwd_store(W, t, w);
       const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P2, chunk), need);
       t = idx < ch.end ? (order ? order[idx] : idx) : T;
       dirty = false;
       if (t < T) {
-        work_load(W, t, w, p, C, chi2);
+        go = fwd_load(W, t, w, p, C, chi2) && !w.seed_fail;
         w.hits = o.hits + t * NROW;
         w.hrow = o.hrow + t * NROW;
         w.cn = cn;
-        go = !w.seed_fail && W[t].go;
       } else {
         live = false;
       }
@@ -603,7 +665,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
       const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P4, chunk), need);
       t = idx < ch.end ? (order ? order[idx] : idx) : T;
       if (t < T) {
-        go = work_load(W, t, w, p, C, chi2);
+        go = bwd_load(W, t, w, p, C, chi2);
         w.hits = o.hits + t * NROW;
         w.hrow = o.hrow + t * NROW;
         w.cn = cn;
