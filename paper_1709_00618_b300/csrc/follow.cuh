@@ -168,15 +168,39 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
 }
 
 // Output snapshot of the backward pass: the state after its last update.
-// Inside the FP64 zone the covariance is kept as FP64 in shared memory
-// (element i of a lane at snap[i * SNAP_STRIDE]) and rounded to binary32 once,
-// by zone_snap_take, instead of at every update: the FP64 pipe, which bounds
-// the zone, then does no conversions for updates that a later one replaces.
+// Phase 3 keeps it in the lane, which it parks for phase 4; inside the FP64
+// zone the covariance is kept as FP64 in shared memory (element i of a lane
+// at snap[i * SNAP_STRIDE]) and rounded to binary32 once, by zone_snap_take,
+// instead of at every update: the FP64 pipe, which bounds the zone, then does
+// no conversions for updates that a later one replaces.  Phase 4 keeps the
+// snapshot in shared memory (out_put), since in registers it made the
+// 64-register build spill.
 constexpr int SNAP_STRIDE = 128;  // the largest block of the follow kernels
+// Shared-memory output slot of a phase-4 lane (word i at so[i * SNAP_STRIDE]):
+// row, y, z, sin phi, dz/ds_T, q/pT (the compensated sums), zref, the 15
+// covariance entries, the chi2 total (two words) and its binary32 part.
+constexpr int OUT_WORDS = 25;
+__device__ __forceinline__ void out_put(float* so, const TrkState& p, const float* C, const Chi2Acc& chi2) {
+  so[0] = __int_as_float(p.row);
+  so[1 * SNAP_STRIDE] = p.y + p.yl;
+  so[2 * SNAP_STRIDE] = p.z + p.zl;
+  so[3 * SNAP_STRIDE] = p.s + p.sl;
+  so[4 * SNAP_STRIDE] = p.t;
+  so[5 * SNAP_STRIDE] = p.q;
+  so[6 * SNAP_STRIDE] = p.zref;
+#pragma unroll
+  for (int i = 0; i < 15; i++) so[(7 + i) * SNAP_STRIDE] = C[i];
+  so[22 * SNAP_STRIDE] = __int_as_float(__double2hiint(chi2.total));
+  so[23 * SNAP_STRIDE] = __int_as_float(__double2loint(chi2.total));
+  so[24 * SNAP_STRIDE] = chi2.part;
+}
 template <bool Z>
 __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zone, const double* D, const float* C,
-                                            const Chi2Acc& chi2, double* snap) {
-  zone = Z && zone;
+                                            const Chi2Acc& chi2, double* snap, float* so) {
+  if (!Z) {
+    out_put(so, p, C, chi2);
+    return;
+  }
   w.sp = p;
   w.schi2 = chi2;
   if (zone) {
@@ -187,7 +211,7 @@ __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zon
   }
 #pragma unroll
   for (int i = 0; i < 15; i++) w.sC[i] = C[i];
-  if (Z) w.snap = false;
+  w.snap = false;
 }
 __device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap) {
   if (w.snap) {
@@ -247,7 +271,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
 template <bool Z>
 __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, const float* sX, const float* sYH,
                                          Lane& w, TrkState& p, double* D, float* C, Chi2Acc& chi2, LocalTally& tl,
-                                         double* snap) {
+                                         double* snap, float* so) {
   const int r = p.row - 1;
   if (r < 0) return false;
   if (r >= 1 && r - 1 < w.r0) prefetch_l1(g.par + w.ubase + r - 1);  // the next step's row-sector parameters
@@ -278,7 +302,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
   lane_update<Z>(w, kc, p, zone, D, C, P, chi2, 1);
   if (zone) tl.upd64++;
   else tl.upd32++;
-  keep_output<Z>(w, p, w.nupd < w.zend, D, C, chi2, snap);
+  keep_output<Z>(w, p, w.nupd < w.zend, D, C, chi2, snap, so);
   return true;
 }
 
@@ -357,7 +381,7 @@ __device__ __forceinline__ void fwd_store(FollowWork* W, int64_t t, const Lane& 
   s.w.fwd = w.fwd;
 }
 __device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
-                                         Chi2Acc& chi2) {
+                                         Chi2Acc& chi2, float* so) {
   const FollowWork& s = W[t];
   w.ubase = s.w.ubase;
   w.r0 = s.w.r0;
@@ -372,10 +396,12 @@ __device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w
   w.flags = s.w.flags;
   w.seed_fail = s.w.seed_fail;
   w.tr = s.w.tr;
-  w.sp = s.w.sp;
+  {
+    float sc[15];
 #pragma unroll
-  for (int i = 0; i < 15; i++) w.sC[i] = s.w.sC[i];
-  w.schi2 = s.w.schi2;
+    for (int i = 0; i < 15; i++) sc[i] = s.w.sC[i];
+    out_put(so, s.w.sp, sc, s.w.schi2);
+  }
   p = s.p;
 #pragma unroll
   for (int i = 0; i < 15; i++) C[i] = s.C[i];
@@ -593,8 +619,8 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
       lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
       if (zone0) tl.upd64++;
       else tl.upd32++;
-      keep_output<true>(w, p, w.nupd < w.zend, D, C, chi2, snap);
-      while (go && w.nupd < w.zend) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap);
+      keep_output<true>(w, p, w.nupd < w.zend, D, C, chi2, snap, nullptr);
+      while (go && w.nupd < w.zend) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, nullptr);
       if (w.nupd < w.zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
@@ -607,7 +633,9 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
   tl.flush(cn, PH_FOLLOW_P3);
 }
 
-__device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t t, const Lane& w, float zref0) {
+// Output of one tracklet from its phase-4 slot (out_put).
+__device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t t, const Lane& w, float zref0,
+                                                    const float* so) {
   if (w.seed_fail) {
     o.n[t] = 0;
     o.nf[t] = 0;
@@ -626,16 +654,16 @@ __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t 
   o.nf[t] = w.nf;
   o.nb[t] = w.nb;
   o.flags[t] = (int32_t)w.flags;
-  o.row[t] = w.sp.row;
-  o.par[t * 5 + 0] = w.sp.y + w.sp.yl;
-  o.par[t * 5 + 1] = w.sp.z + w.sp.zl;
-  o.par[t * 5 + 2] = w.sp.s + w.sp.sl;
-  o.par[t * 5 + 3] = w.sp.t;
-  o.par[t * 5 + 4] = w.sp.q;
-  o.zref[t] = w.sp.zref;
+  o.row[t] = __float_as_int(so[0]);
 #pragma unroll
-  for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = w.sC[i];
-  o.chi2[t] = w.schi2.value();
+  for (int i = 0; i < 5; i++) o.par[t * 5 + i] = so[(1 + i) * SNAP_STRIDE];
+  o.zref[t] = so[6 * SNAP_STRIDE];
+#pragma unroll
+  for (int i = 0; i < 15; i++) o.cov[t * 15 + i] = so[(7 + i) * SNAP_STRIDE];
+  Chi2Acc c;
+  c.total = __hiloint2double(__float_as_int(so[22 * SNAP_STRIDE]), __float_as_int(so[23 * SNAP_STRIDE]));
+  c.part = so[24 * SNAP_STRIDE];
+  o.chi2[t] = c.value();
 }
 
 // Phase 4: the rest of the backward pass (FP32, lanes refill as in phase
@@ -645,8 +673,10 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
                                                    int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  __shared__ float sOut[OUT_WORDS * SNAP_STRIDE];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
+  float* so = sOut + threadIdx.x;
   const int32_t T = cn->n_tracklets;
   const Chunk ch = chunk_range(T, chunk, nchunk);
   LocalTally tl;
@@ -661,11 +691,11 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
   for (;;) {
     const unsigned need = refill_mask(live && !go, go, kc.refill);
     if (need & (1u << (threadIdx.x & 31))) {
-      if (t >= 0) write_follow_output(o, t, w, __ldg(g.yz + tl_start[t]).y);
+      if (t >= 0) write_follow_output(o, t, w, __ldg(g.yz + tl_start[t]).y, so);
       const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P4, chunk), need);
       t = idx < ch.end ? (order ? order[idx] : idx) : T;
       if (t < T) {
-        go = bwd_load(W, t, w, p, C, chi2);
+        go = bwd_load(W, t, w, p, C, chi2, so);
         w.hits = o.hits + t * NROW;
         w.hrow = o.hrow + t * NROW;
         w.cn = cn;
@@ -678,7 +708,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
       continue;
     }
     for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
-      go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr);
+      go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr, so);
   }
   tl.flush(cn, PH_FOLLOW_P4);
 }
