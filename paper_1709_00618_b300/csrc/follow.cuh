@@ -174,7 +174,7 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
 // instead of at every update: the FP64 pipe, which bounds the zone, then does
 // no conversions for updates that a later one replaces.  Phase 4 keeps the
 // snapshot in shared memory (out_put), since in registers it made the
-// 64-register build spill.
+// large-input build (72 registers) spill.
 constexpr int SNAP_STRIDE = 128;  // the largest block of the follow kernels
 // Shared-memory output slot of a phase-4 lane (word i at so[i * SNAP_STRIDE]):
 // row, y, z, sin phi, dz/ds_T, q/pT (the compensated sums), zref, the 15
@@ -193,6 +193,37 @@ __device__ __forceinline__ void out_put(float* so, const TrkState& p, const floa
   so[22 * SNAP_STRIDE] = __int_as_float(__double2hiint(chi2.total));
   so[23 * SNAP_STRIDE] = __int_as_float(__double2loint(chi2.total));
   so[24 * SNAP_STRIDE] = chi2.part;
+}
+// A state in a lane's shared-memory slot (word i at s[i * SNAP_STRIDE]):
+// phase 2 keeps the forward state after its last update there.
+constexpr int TRK_WORDS = 11;
+__device__ __forceinline__ void trk_put(float* s, const TrkState& p) {
+  s[0] = p.x;
+  s[1 * SNAP_STRIDE] = __int_as_float(p.row);
+  s[2 * SNAP_STRIDE] = p.y;
+  s[3 * SNAP_STRIDE] = p.z;
+  s[4 * SNAP_STRIDE] = p.s;
+  s[5 * SNAP_STRIDE] = p.t;
+  s[6 * SNAP_STRIDE] = p.q;
+  s[7 * SNAP_STRIDE] = p.yl;
+  s[8 * SNAP_STRIDE] = p.zl;
+  s[9 * SNAP_STRIDE] = p.sl;
+  s[10 * SNAP_STRIDE] = p.zref;
+}
+__device__ __forceinline__ TrkState trk_get(const float* s) {
+  TrkState p;
+  p.x = s[0];
+  p.row = __float_as_int(s[1 * SNAP_STRIDE]);
+  p.y = s[2 * SNAP_STRIDE];
+  p.z = s[3 * SNAP_STRIDE];
+  p.s = s[4 * SNAP_STRIDE];
+  p.t = s[5 * SNAP_STRIDE];
+  p.q = s[6 * SNAP_STRIDE];
+  p.yl = s[7 * SNAP_STRIDE];
+  p.zl = s[8 * SNAP_STRIDE];
+  p.sl = s[9 * SNAP_STRIDE];
+  p.zref = s[10 * SNAP_STRIDE];
+  return p;
 }
 template <bool Z>
 __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zone, const double* D, const float* C,
@@ -226,7 +257,7 @@ __device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap) {
 template <bool Z>
 __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __restrict__ up_m, const KConst& kc,
                                          const float* sX, const float* sYH, Lane& w, TrkState& p, double* D,
-                                         float* C, Chi2Acc& chi2, LocalTally& tl) {
+                                         float* C, Chi2Acc& chi2, LocalTally& tl, float* sf) {
   const int r = p.row + 1;
   if (r >= NROW) return false;
   if (r + 1 < NROW) prefetch_l1(g.par + w.ubase + r + 1);  // the next step's row-sector parameters
@@ -261,7 +292,8 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
   w.hits[w.nf] = c;
   w.hrow[w.nf] = (uint8_t)r;
   w.nf++;
-  w.fwd = p;
+  if (Z) w.fwd = p;  // phase 1 parks it with the lane, phase 2 keeps it in shared memory
+  else trk_put(sf, p);
   w.r_last = r;
   w.misses = 0;
   return true;
@@ -345,14 +377,14 @@ __device__ __forceinline__ bool work_load(const FollowWork* W, int64_t t, Lane& 
 }
 
 // The binary32 phases touch only their half of the parked lane, so that
-// neither carries the other's state in registers (the 64-register builds
+// neither carries the other's state in registers (the large-input builds
 // spilled it) nor moves it to and from memory.  Phase 2 reads the forward
 // fields and writes back what phase 3 uses (the forward state after its last
 // update, the forward hit count and the flags; phase 3 re-seeds, so the
 // running state, covariance and chi2 of phase 2 are not kept).  Phase 4 reads
 // the backward fields.
 __device__ __forceinline__ bool fwd_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
-                                         Chi2Acc& chi2) {
+                                         Chi2Acc& chi2, float* sf) {
   const FollowWork& s = W[t];
   w.ubase = s.w.ubase;
   w.L = s.w.L;
@@ -366,19 +398,19 @@ __device__ __forceinline__ bool fwd_load(const FollowWork* W, int64_t t, Lane& w
   w.flags = s.w.flags;
   w.seed_fail = s.w.seed_fail;
   w.tr = s.w.tr;
-  w.fwd = s.w.fwd;
+  trk_put(sf, s.w.fwd);
   p = s.p;
 #pragma unroll
   for (int i = 0; i < 15; i++) C[i] = s.C[i];
   chi2 = s.chi2;
   return s.go != 0;
 }
-__device__ __forceinline__ void fwd_store(FollowWork* W, int64_t t, const Lane& w) {
+__device__ __forceinline__ void fwd_store(FollowWork* W, int64_t t, const Lane& w, const float* sf) {
   FollowWork& s = W[t];
   s.w.nf = w.nf;
   s.w.flags = w.flags;
   s.w.seed_fail = w.seed_fail;
-  s.w.fwd = w.fwd;
+  s.w.fwd = trk_get(sf);
 }
 __device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
                                          Chi2Acc& chi2, float* so) {
@@ -504,7 +536,7 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
       else tl.upd32++;
       w.fwd = p;
       go = true;
-      while (go && w.nupd < w.zend) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+      while (go && w.nupd < w.zend) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr);
       if (w.nupd < w.zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
@@ -517,9 +549,9 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
 }
 
 // Phase 2: the rest of the forward pass (covariance in FP32).  MINB: CTAs
-// per SM the registers are budgeted for -- 4 (128 registers, no spills)
-// where the longest tracklet bounds the kernel, 8 (64 registers, a few
-// spills, twice the resident warps) on inputs that fill the GPU.  A lane
+// per SM the registers are budgeted for -- 4 (no spills) where the longest
+// tracklet bounds the kernel, 6 here and 7 in phase 4 (80 and 72 registers,
+// a few spills, more resident warps) on inputs that fill the GPU.  A lane
 // that finishes a tracklet idles until kc.refill lanes of its warp have,
 // then they store their results and take new tracklets together, so that
 // the refill runs with many lanes at once and no lane waits for the longest
@@ -529,8 +561,10 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
                                                    int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  __shared__ float sFwd[TRK_WORDS * SNAP_STRIDE];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
+  float* sf = sFwd + threadIdx.x;
   const int32_t T = cn->n_tracklets;
   const Chunk ch = chunk_range(T, chunk, nchunk);
   LocalTally tl;
@@ -547,12 +581,12 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
   for (;;) {
     const unsigned need = refill_mask(live && !go, go, kc.refill);
     if (need & (1u << (threadIdx.x & 31))) {
-      if (dirty) fwd_store(W, t, w);
+      if (dirty) fwd_store(W, t, w, sf);
       const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P2, chunk), need);
       t = idx < ch.end ? (order ? order[idx] : idx) : T;
       dirty = false;
       if (t < T) {
-        go = fwd_load(W, t, w, p, C, chi2) && !w.seed_fail;
+        go = fwd_load(W, t, w, p, C, chi2, sf) && !w.seed_fail;
         w.hits = o.hits + t * NROW;
         w.hrow = o.hrow + t * NROW;
         w.cn = cn;
@@ -566,7 +600,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
     }
     if (go) {
       for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
-        go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl);
+        go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, sf);
       dirty = true;
     }
   }

@@ -567,7 +567,7 @@ void enqueue_find(tpc_ctx* ctx) {
       if (longest_first)
         k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 0, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(0);
-      auto p2 = ctx->n >= kLargeBatch ? k_follow_p2<8> : k_follow_p2<4>;
+      auto p2 = ctx->n >= kLargeBatch ? k_follow_p2<6> : k_follow_p2<4>;
       p2<<<persistent_grid(ctx, p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
       if (nc == 1) ctx->mark_k(1);
@@ -576,7 +576,7 @@ void enqueue_find(tpc_ctx* ctx) {
       if (longest_first)
         k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(2);
-      auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<8> : k_follow_p4<4>;
+      auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<7> : k_follow_p4<4>;
       p4<<<persistent_grid(ctx, p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
     };
