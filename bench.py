@@ -90,12 +90,14 @@ class ClockSampler:
 # square root 1):
 #   helix step of the state with its Jacobian, binary32        67
 #   covariance transport J C J^T (42 FMA on the packed triangle)  84
-#   Kalman update, gain and covariance (in the covariance type)  99
+#   Kalman update, gain and covariance, binary32 (2x2 inverse)  99
+#   Kalman update, gain and covariance, binary64 (a y and a z
+#     scalar downdate: 2 adds, 2 reciprocals, 10 mul, 30 FMA)     74
 #   Kalman update, residuals, state and chi2 (binary32)          56
 #   candidate cluster examined by the gated pick-up              10
 # FP32-zone work is all binary32; in the FP64 zone the transport and the
 # covariance part of the update run in binary64.
-FLOP_STATE, FLOP_TRANSPORT, FLOP_UPD_COV, FLOP_UPD_STATE, FLOP_CAND = 67, 84, 99, 56, 10
+FLOP_STATE, FLOP_TRANSPORT, FLOP_UPD_COV, FLOP_UPD_COV64, FLOP_UPD_STATE, FLOP_CAND = 67, 84, 99, 74, 56, 10
 # Algorithmic DRAM bytes per cluster of the memory-bound stages: grid 44
 # (the 16 B record read, 16 B of sorted output -- y/z, row-sector, input
 # index -- written, a 4 B bin index written and half of the records read
@@ -146,7 +148,7 @@ def kalman_flops(w):
     p32 = w["prop"] - w["prop64"]
     f32 = (FLOP_STATE + FLOP_TRANSPORT) * p32 + FLOP_STATE * w["prop64"] + \
         (FLOP_UPD_COV + FLOP_UPD_STATE) * w["upd32"] + FLOP_UPD_STATE * w["upd64"] + FLOP_CAND * w["cand"]
-    f64 = FLOP_TRANSPORT * w["prop64"] + FLOP_UPD_COV * w["upd64"]
+    f64 = FLOP_TRANSPORT * w["prop64"] + FLOP_UPD_COV64 * w["upd64"]
     return f32, f64
 
 
@@ -723,6 +725,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-timeframes", type=int, default=24)
     ap.add_argument("--serving-pool", type=int, default=4)
+    ap.add_argument("--timeframe-ms", type=float, default=0.0,
+                    help="time a continuous read-out timeframe of this length (50 kHz, seed 2 + rank) instead of "
+                         "the central event (for profiling inputs that fill the GPU)")
     ap.add_argument("--all-configs", action="store_true",
                     help="print the per-config table (one sector, central event, 10 ms timeframe) instead")
     args = ap.parse_args()
@@ -748,7 +753,12 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    ev = synth.central_event(seed=1 + rank)
+    if args.timeframe_ms > 0:
+        ev = synth.timeframe(seed=2 + rank, length_ms=args.timeframe_ms)
+        workload = f"{args.timeframe_ms:g} ms timeframe at 50 kHz, seed {2 + rank}"
+    else:
+        ev = synth.central_event(seed=1 + rank)
+        workload = "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1"
     cl = ev.clusters
     n = len(cl)
     stream = torch.cuda.Stream()
@@ -827,7 +837,7 @@ def main():
     served = events_through_server(host_in, n, local, events=max(4 * args.steps, 16), slots=4) if world == 1 else None
 
     clocks = clk.summary()
-    traffic = ncu_traffic()
+    traffic = ncu_traffic() if args.timeframe_ms <= 0 else {}  # the committed capture is of the central event
     roof, kernel_table = roofline(stages, kalman, n, alu, clocks, traffic if world == 1 else None)
     for k, v in kernel_table.items():
         v["traffic"] = traffic.get(k)
@@ -835,7 +845,7 @@ def main():
     line = {"metric": METRIC, "value": total_clusters / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1",
+            "config": {"workload": workload,
                        "clusters": n, "tracklets": counts["n_tracklets"], "tracks": counts["n_tracks"],
                        "tracklets_per_track": counts["n_tracklets"] / max(counts["n_tracks"], 1),
                        "l2": "flushed (256 MB write) between steps", "graph": True,
