@@ -30,6 +30,7 @@ RS_PARAMS_DTYPE = np.dtype([("z_lo", "<f4"), ("z_hi", "<f4"), ("inv_y", "<f4"), 
 TPC_OK, TPC_EINVAL, TPC_ENOMEM, TPC_ECUDA, TPC_ETIMEOUT, TPC_EOVERFLOW, TPC_EBUSY = range(7)
 _CODES = {1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EOVERFLOW", 6: "EBUSY"}
 TF_TAINT_ANY = 1 | 2 | 4 | 8
+TF_SEED_FAIL, TF_BACK_FAIL, TF_REFIT_FAIL = 16, 32, 64  # TPC_TF_* of tpcca.h
 
 # item -> (numpy dtype, columns)
 ITEMS = {"perm": (1, np.int32), "rs_of": (2, np.int32), "row_start": (3, np.int32), "rs_params": (4, RS_PARAMS_DTYPE),

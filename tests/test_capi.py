@@ -34,6 +34,14 @@ def test_default_config_is_the_reading():
     assert cfg.s_max == 0.95 and cfg.fp64_updates == 10 and abs(cfg.d_max - 1.0) < 1e-7
 
 
+def test_binding_flags_match_the_header():
+    txt = open(os.path.join(ROOT, "include", "tpcca.h")).read()
+    val = {k: int(v) for k, v in re.findall(r"\b(TPC_TF_[A-Z_]+|TPC_RJ_[A-Z_]+)\s*=\s*(\d+)", txt)}
+    assert val["TPC_TF_SEED_FAIL"] == tpc.TF_SEED_FAIL and val["TPC_TF_BACK_FAIL"] == tpc.TF_BACK_FAIL
+    assert val["TPC_TF_REFIT_FAIL"] == tpc.TF_REFIT_FAIL
+    assert tpc.TF_TAINT_ANY == sum(v for k, v in val.items() if k.startswith("TPC_TF_TAINT_"))
+
+
 def test_arena_size_grows_with_input():
     lib = tpc.load_library()
     a, b, c = lib.tpc_arena_bytes(1000, 1), lib.tpc_arena_bytes(1_000_000, 1), lib.tpc_arena_bytes(1_000_000, 4)

@@ -145,3 +145,36 @@ def test_fp64_zone_keeps_assignments_of_the_fp64_oracle(trk):
     record_stats("fp64_zone_effect", {"untainted_divergent_fp32_only": counts[0],
                                  "untainted_divergent_with_zone": counts[max(counts)]})
     assert counts[max(counts)] == 0
+
+
+def test_fp64_zone_length():
+    """The FP64 zone holds fp64_updates updates after each seed in the
+    forward pass, and from fp64_updates up to twice as many in the backward
+    pass and the refit, whose covariances are outputs (further updates while
+    the covariance is still converging).  Checked with the per-kernel work
+    counters against the update counts of the outputs: the backward pass
+    updates every forward hit and every hit it picks up (f_n), the refit
+    every owned cluster."""
+    import paper_1709_00618_b300 as tpc
+    from parity import follow_result
+    ev = synth.central_event(seed=1)
+    N = tpc.default_config().fp64_updates
+    with tpc.Tracker(device=0) as t:
+        t.set_profiling(True)
+        tracks, _, _ = t.track(ev.clusters)
+        kp = t.kalman_profile(times=False)
+        g = follow_result(t)
+    f_n = g["f_n"].astype(np.int64)
+    ok = (g["f_flags"] & (tpc.TF_SEED_FAIL | tpc.TF_BACK_FAIL)) == 0
+    p3 = kp["k_follow_p3"]["upd64"]
+    assert np.minimum(f_n[ok], N).sum() <= p3 <= np.minimum(f_n, 2 * N).sum()
+    assert kp["k_follow_p1"]["upd64"] <= N * len(f_n)
+    assert kp["k_follow_p2"]["upd64"] == kp["k_follow_p4"]["upd64"] == kp["k_refit_p2"]["upd64"] == 0
+    n = tracks["n_clusters"].astype(np.int64)
+    rok = (tracks["flags"] & tpc.TF_REFIT_FAIL) == 0
+    r1 = kp["k_refit_p1"]["upd64"]
+    assert np.minimum(n[rok], N).sum() <= r1 <= np.minimum(n, 2 * N).sum()
+    record_stats("fp64_zone_length", {"backward_fp64_updates": int(p3),
+                                      "backward_fixed_zone_ok": int(np.minimum(f_n[ok], N).sum()),
+                                      "refit_fp64_updates": int(r1),
+                                      "refit_fixed_zone_ok": int(np.minimum(n[rok], N).sum())})
