@@ -107,10 +107,11 @@ __global__ void k_track_clusters(const int32_t* __restrict__ track_tl, const int
 }
 
 // Track numbering in tracklet order; per-cluster assignment in load order
-// (W: one warp per tracklet, as k_own).
+// (W: one warp per tracklet, as k_own).  The owned hits are read from the
+// bit masks k_keep stored, so the owner keys are not read again.
 template <bool W>
 __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits,
-                         const uint64_t* __restrict__ owner, const int32_t* __restrict__ keep,
+                         const uint32_t* __restrict__ own_mask, const int32_t* __restrict__ keep,
                          const int32_t* __restrict__ tidx, const int32_t* __restrict__ perm,
                          const int32_t* __restrict__ nown, int32_t* __restrict__ tl_track,
                          int32_t* __restrict__ track_tl, int32_t* __restrict__ tcount,
@@ -118,7 +119,7 @@ __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restr
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
   if (gtid() == 0) cn->n_tracks = tidx[T];
-  const int lane = W ? (int)(threadIdx.x & 31) : 0, step = W ? 32 : 1;
+  const int lane = W ? (int)(threadIdx.x & 31) : 0;
   for (int64_t t = W ? gtid() >> 5 : gtid(); t < T; t += W ? gstride() >> 5 : gstride()) {
     if (!keep[t]) {
       if (lane == 0) tl_track[t] = -1;
@@ -131,10 +132,24 @@ __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restr
       tcount[idx] = nown[t];  // owned clusters per track, for the offsets of the refit's output
     }
     const int n = f_n[t];
-    const uint64_t key = track_key(n, (int)t);
     const int32_t* h = hits + t * NROW;
-    for (int i = lane; i < n; i += step)
-      if (__ldg((const unsigned long long*)owner + h[i]) == key) cluster_track[__ldg(perm + h[i])] = idx;
+    if (W) {  // lanes over the hits, the mask words shuffled from the first lanes
+      const uint32_t mw = lane < OWN_WORDS ? own_mask[t * OWN_WORDS + lane] : 0u;
+      for (int i0 = 0; i0 < n; i0 += 32) {
+        const uint32_t word = __shfl_sync(FULL_MASK, mw, i0 >> 5);
+        const int i = i0 + lane;
+        if (i < n && ((word >> lane) & 1u)) cluster_track[__ldg(perm + h[i])] = idx;
+      }
+    } else {
+      for (int w = 0; w < OWN_WORDS; w++) {
+        uint32_t word = own_mask[t * OWN_WORDS + w];
+        while (word) {
+          const int b = __ffs(word) - 1;
+          word &= word - 1;
+          cluster_track[__ldg(perm + h[w * 32 + b])] = idx;
+        }
+      }
+    }
   }
 }
 

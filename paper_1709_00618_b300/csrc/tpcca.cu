@@ -600,7 +600,7 @@ void enqueue_find(tpc_ctx* ctx) {
                            ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.own_rng),
                            cn);
   scan(ctx, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), LenSrc{&cn->n_tracklets, 0, 0}, nullptr);
-  (warp_sel ? k_assign<true> : k_assign<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint64_t>(L.owner),
+  (warp_sel ? k_assign<true> : k_assign<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint32_t>(L.own_mask),
                              ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), ctx->ptr<int32_t>(L.perm),
                              ctx->ptr<int32_t>(L.nown), ctx->ptr<int32_t>(L.tl_track), ctx->ptr<int32_t>(L.track_tl),
                              ctx->ptr<int32_t>(L.tcount), ctx->ptr<int32_t>(L.cluster_track), cn);
