@@ -4,9 +4,11 @@
 // The state is binary32 with z kept relative to a per-track reference (the
 // seed cluster's z) so that drift-time coordinates of ~2.5e4 cm keep their
 // resolution.  The covariance is a packed lower triangle; it is held in FP64
-// for the first `fp64_updates` updates after every (re)seed, where the seed
-// covariance is large and the subtraction C -= G C[0:2,:] cancels, and in
-// FP32 afterwards.  chi2 is accumulated in FP64.
+// for the first `fp64_updates` updates after every (re)seed (a few more while
+// it is still converging in the passes whose covariance is an output,
+// zone_update), where the seed covariance is large and the subtraction
+// C -= G C[0:2,:] cancels, and in FP32 afterwards.  chi2 is accumulated in
+// FP64.
 #pragma once
 #include "common.cuh"
 
@@ -51,7 +53,6 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float d) {
 // the grid and link stages keep).  ksqrt needs v > 0.
 __device__ __forceinline__ float ksqrt(float v) { return v * rsqrtf(v); }
 __device__ __forceinline__ float kinv(float v) { return __fdividef(1.0f, v); }
-__device__ __forceinline__ double kinv(double v) { return 1.0 / v; }
 
 // Conversions between binary32 and binary64 done with integer operations on
 // the IEEE 754 encodings (sign, biased exponent, fraction; binary32 bias 127,
@@ -344,15 +345,6 @@ __device__ __forceinline__ bool propagate_any(TrkState& p, bool zone, double* D,
   return true;
 }
 
-// Propagation with covariance transport in precision T.
-template <typename T>
-__device__ __forceinline__ bool propagate(TrkState& p, T* C, int row2, float x2, const KConst& kc, uint32_t& flags) {
-  Jac J;
-  if (!prop_state(p, row2, x2, kc, flags, &J)) return false;
-  cov_transport<T>(C, (T)J.j02, (T)J.j12, (T)J.j13, (T)J.kap);
-  return true;
-}
-
 template <typename T>
 __device__ __forceinline__ void cov_seed(T* C, const KConst& kc) {
 #pragma unroll
@@ -360,13 +352,6 @@ __device__ __forceinline__ void cov_seed(T* C, const KConst& kc) {
 #pragma unroll
   for (int i = 0; i < 5; i++) C[TPC_CI(i, i)] = (T)kc.c0[i];
 }
-
-template <typename T>
-__device__ __forceinline__ T meas_var(const KConst& kc);
-template <>
-__device__ __forceinline__ float meas_var<float>(const KConst& kc) { return kc.V; }
-template <>
-__device__ __forceinline__ double meas_var<double>(const KConst& kc) { return kc.Vd; }
 
 // Start a state at (y, z) with direction (s, t) and curvature q, z kept
 // relative to zref = z.
@@ -409,16 +394,6 @@ struct Chi2Acc {
 // Work tallies kept in registers by one thread.
 struct LocalTally {
   unsigned prop = 0, prop64 = 0, upd32 = 0, upd64 = 0, cand = 0;
-  template <typename T>
-  __device__ __forceinline__ void on_prop() {
-    prop++;
-    if (sizeof(T) == 8) prop64++;
-  }
-  template <typename T>
-  __device__ __forceinline__ void on_upd() {
-    if (sizeof(T) == 8) upd64++;
-    else upd32++;
-  }
   __device__ __forceinline__ void flush(Counts* cn, int phase) {
     Tally t;
     t.prop = prop;
