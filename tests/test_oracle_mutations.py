@@ -36,6 +36,17 @@ MUTANTS = {
         "    const int32_t *h = R->f_hits + (int64_t)t * NROW;\n    for (int i = 0; i < R->f_n[t]; i++)\n"
         "      if (key >= R->owner[h[i]] || (R->owner[h[i]] >> 32) == (key >> 32)) R->owner[h[i]] = key;"),
     "bin_scan_off_by_one": ("      while (p < b && it[p].bin < k) p++;", "      while (p < b && it[p].bin <= k) p++;"),
+    "chi2_cross_term_dropped": ("  s->chi2 += r0 * (I00 * r0 + I01 * r1) + r1 * (I01 * r0 + I11 * r1);",
+                                "  s->chi2 += r0 * I00 * r0 + r1 * I11 * r1;"),
+    "max_miss_off_by_one_outward": ("      misses = 0;\n    } else if (++misses >= cfg->max_miss) {",
+                                    "      misses = 0;\n    } else if (++misses > cfg->max_miss) {"),
+    "max_miss_off_by_one_inward": ("        misses = 0;\n      } else if (++misses >= cfg->max_miss) {",
+                                   "        misses = 0;\n      } else if (misses++ >= cfg->max_miss) {"),
+    "max_miss_one_short_outward": ("      misses = 0;\n    } else if (++misses >= cfg->max_miss) {",
+                                   "      misses = 0;\n    } else if (++misses >= cfg->max_miss - 1) {"),
+    "edge_margin_sign": ("  double lim = s->x * TAN10 + k->cfg->edge;", "  double lim = s->x * TAN10 - k->cfg->edge;"),
+    "edge_margin_dropped": ("  double lim = s->x * TAN10 + k->cfg->edge;", "  double lim = s->x * TAN10;"),
+    "edge_test_never_stops": ("  return fabs(s->p[0]) > lim;", "  return fabs(s->p[0]) > lim + 1e9;"),
 }
 
 

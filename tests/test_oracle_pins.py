@@ -401,3 +401,156 @@ def test_findable_efficiency_reported(small_event, small_oracle):
     eff = found / findable
     print(f"findable segments {findable}, efficiency {eff:.3f}")
     assert findable > 30 and eff > 0.8
+
+
+# ------------------------------------- stopping rules of the extension (a6)
+def _row_x():
+    return np.array([float(np.float32(85.2 + r * ((245.8 - 85.2) / 158.0))) for r in range(159)])
+
+
+def _line_clusters(rows, y_of_x, z_of_x, sector=0, ident=0):
+    x = _row_x()
+    rows = np.asarray(sorted(rows), dtype=np.int64)
+    c = np.zeros(len(rows), synth.CLUSTER_DTYPE)
+    c["y"], c["z"] = y_of_x(x[rows]), z_of_x(x[rows])
+    c["row"], c["sector"], c["id"] = rows, sector, ident
+    return c
+
+
+def _tracks_of(r, cl):
+    """Sets of rows of every found track (input order of the clusters)."""
+    out = []
+    for k in range(r["n_tracks"]):
+        out.append(sorted(cl["row"][r["cluster_track"] == k].tolist()))
+    return sorted(out)
+
+
+@pytest.mark.parametrize("max_miss,gap", [(5, 4), (5, 5), (3, 2), (3, 3), (5, 1)])
+def test_extension_bridges_fewer_than_max_miss_empty_rows(max_miss, gap):
+    """A track with `gap` consecutive empty rows: the extension ends after
+    max_miss consecutive rows without a cluster (Sec. 2 track following;
+    MAX_MISS is the reading's constant), so a gap shorter than max_miss is
+    bridged -- one track holds every cluster -- and a gap of max_miss rows
+    splits the track in two at the gap.  Noiseless straight tracks in the
+    default field; the inner piece's outward extension and the outer
+    piece's inward extension both meet the gap, and each tracklet's own
+    cluster list is checked as well as the selected tracks."""
+    cfg = oracle.default_config(max_miss=max_miss)
+    g0 = 60
+    rows = [r for r in range(159) if not g0 < r <= g0 + gap]
+    lines = [(-6.0, 0.02, 10.0, 0.3), (5.0, -0.03, 30.0, 0.5)]
+    for sec, (y0, b, z0, e) in enumerate(lines):
+        cl = _line_clusters(rows, lambda x: y0 + b * (x - 85.2), lambda x: z0 + e * (x - 85.2), sector=sec)
+        r = oracle.run(cl, cfg=cfg)
+        tracks = _tracks_of(r, cl)
+        inner = [q for q in rows if q <= g0]
+        outer = [q for q in rows if q > g0]
+        # two tracklets (the chains on either side of the gap), inner first;
+        # each one's own extension must bridge the gap, or stop at it
+        assert r["n_tracklets"] == 2
+        rows_sorted = cl["row"][r["perm"]]
+        held = [sorted(rows_sorted[r["f_hits"][t, :r["f_n"][t]]].tolist()) for t in range(2)]
+        if gap < max_miss:
+            assert held == [sorted(rows), sorted(rows)], (max_miss, gap, [len(h) for h in held])
+            assert tracks == [sorted(rows)], (max_miss, gap, [len(t) for t in tracks])
+        else:
+            assert held == [inner, outer], (max_miss, gap, [(h[0], h[-1]) for h in held])
+            assert tracks == sorted([inner, outer]), (max_miss, gap, [(t[0], t[-1]) for t in tracks])
+
+
+def _edge_lim(x):
+    return x * 0.17632698070846498 + 2.0
+
+
+def test_extension_stops_beyond_the_sector_edge_outward():
+    """A straight track leaving the wedge: full rows up to row 40 (the
+    chain), then a cluster on every other row (no chain there: links need
+    rows r-1 and r+1), past the edge and on to row 158.  The outward
+    extension takes every cluster while the predicted |y| is within x tan 10
+    + 2 cm and stops at the first row beyond it; no cluster there lies
+    within 0.05 cm of that limit."""
+    x = _row_x()
+    b, ra = 0.35, 40
+    ya = _edge_lim(x[ra]) - 3.0
+    rows = list(range(10, ra + 1)) + list(range(ra + 2, 159, 2))
+
+    def y_of(xx):
+        return ya + b * (xx - x[ra])
+    over = y_of(x) - _edge_lim(x)
+    assert np.all(np.abs(over[rows]) > 0.05) and over[158] > 5.0
+    cl = _line_clusters(rows, y_of, lambda xx: 20.0 + 0.4 * (xx - 85.2))
+    r = oracle.run(cl)
+    first_out = int(np.nonzero(over > 0)[0][0])
+    expect = [q for q in rows if q < first_out]
+    assert first_out > ra + 8 and len(expect) < len(rows) - 20
+    assert _tracks_of(r, cl) == [expect]
+
+
+def test_extension_stops_beyond_the_sector_edge_inward():
+    """The same for the inward extension of the backward pass: a track at
+    constant y = 20 cm is inside the wedge from row ~28 outward (the chain:
+    full rows 40..158) and beyond x tan 10 + 2 cm below row ~17; on every
+    other row below the chain it is picked up down to the last row within
+    the limit."""
+    x = _row_x()
+    y = 20.0
+    rows = list(range(0, 40, 2)) + list(range(40, 159))
+    over = y - _edge_lim(x)
+    assert np.all(np.abs(over[rows]) > 0.05)
+    cl = _line_clusters(rows, lambda xx: np.full_like(xx, y), lambda xx: 15.0 + 0.6 * (xx - 85.2))
+    r = oracle.run(cl)
+    last_out = int(np.nonzero(over > 0)[0][-1])
+    expect = [q for q in rows if q > last_out]
+    assert 10 < last_out < 30 and len(expect) < len(rows) - 5
+    assert _tracks_of(r, cl) == [expect]
+
+
+# ------------------------------------------------ chi2 increment r^T S^-1 r
+@pytest.mark.parametrize("sphi,tgl,res", [(0.8, 2.0, (0.7, -0.9)), (-0.6, -1.5, (0.3, 0.4)),
+                                          (0.2, 0.1, (-1.0, 0.5))])
+def test_chi2_equals_least_squares_minimum_of_the_linear_model(sphi, tgl, res):
+    """Bz = 0 makes the transport linear in the state deviations, so the
+    filter is exact for the linear Gaussian model: the accumulated chi2 (sum
+    of r^T S^-1 r over the updates) equals the minimum of the batch
+    least-squares objective (prior term plus measurement terms), and the
+    filtered state and covariance at the last row equal the least-squares
+    solution carried there.  A first measurement on the seed (zero residual)
+    and a second one offset by `res` ten rows further; with large |sin phi|
+    and dz/ds_T the predicted y and z errors are strongly correlated, so the
+    y-z term of S^-1 carries most of the chi2.  The least-squares side uses
+    the straight-line geometry y' = y + dx tan(phi), z' = z + dz/ds_T dx/cos(phi)
+    and its derivative, and numpy's solver."""
+    cfg = oracle.default_config(bz_kg=0.0)
+    x = _row_x()
+    r0, r1 = 30, 40
+    dx = x[r1] - x[r0]
+    p0 = np.array([3.0, 40.0, sphi, tgl, 0.0])
+    c = math.sqrt(1 - sphi ** 2)
+    f = p0 + np.array([dx * sphi / c, tgl * dx / c, 0, 0, 0])
+    m0 = p0[:2]
+    m1 = f[:2] + np.array(res)
+    p, cov, chi2 = oracle.kalman_fit([r0, r1], [m0[0], m1[0]], [m0[1], m1[1]], p0, cfg)
+    # linear model around p0: state deviation d at row r0, carried by J
+    J = np.eye(5)
+    J[0, 2] = dx / c ** 3
+    J[1, 2] = tgl * dx * sphi / c ** 3
+    J[1, 3] = dx / c
+    H = np.zeros((2, 5))
+    H[0, 0] = H[1, 1] = 1.0
+    V = cfg.sigma ** 2
+    C0inv = np.diag(1.0 / np.array(cfg.c0[:]))
+    N = C0inv + H.T @ H / V + (H @ J).T @ (H @ J) / V
+    rhs = (H @ J).T @ (m1 - f[:2]) / V
+    d = np.linalg.solve(N, rhs)
+    obj = d @ C0inv @ d + np.sum((H @ d) ** 2) / V + np.sum((m1 - f[:2] - H @ J @ d) ** 2) / V
+    assert abs(chi2 - obj) <= 1e-9 * obj, (chi2, obj)
+    assert np.allclose(p, f + J @ d, rtol=1e-9, atol=1e-9)
+    C = J @ np.linalg.inv(N) @ J.T
+    assert np.allclose(oracle.unpack_cov(cov), C, rtol=1e-8, atol=1e-12 * np.abs(C).max())
+    # the y-z correlation of the prediction matters: without its S^-1 term
+    # the chi2 would be far off (guards the test's own sensitivity)
+    Sp = H @ J @ np.linalg.inv(C0inv + H.T @ H / V) @ J.T @ H.T + V * np.eye(2)
+    r = m1 - f[:2]
+    diag_only = r[0] ** 2 / Sp[0, 0] + r[1] ** 2 / Sp[1, 1]
+    if abs(sphi * tgl) > 0.5:
+        assert abs(diag_only - obj) > 0.1 * obj
