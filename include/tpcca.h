@@ -97,7 +97,9 @@ typedef struct {
   double c0[5];        /* seed covariance diagonal; 100, 100, 1, 1, 100 */
   double s_max;        /* |sin phi| limit of the propagation; 0.95 */
   double edge;         /* cm beyond the sector edge that end an extension; 2 */
-  double taint_rel;    /* divergence margin for the taint flags; 2e-3 */
+  double taint_rel;    /* divergence margin for the taint flags; 1e-4: a pick whose second-best
+                          chi2 is within taint_rel (1 + best), or a candidate within
+                          taint_rel (1 + gate) of the gate, flags its tracklet */
   int32_t fp64_updates;/* Kalman updates after each seed done in FP64; 10.
                           Outside the forward pass, up to as many again while
                           the last one still more than halved the variance of
@@ -182,6 +184,52 @@ int tpc_get_tracks(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, in
  * going.  TPC_EOVERFLOW: device capacities overflowed (*n_out untouched)
  * or cap < *n_out (nothing copied). */
 int tpc_get_tracks_async(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, int32_t *cluster_track);
+
+/* ------------------------------------------------------ batched requests */
+/* Several independent requests (events or timeframes) tracked as one batch
+ * on one context, the way Sec. 2 processes several events at once to fill a
+ * GPU: the requests' clusters are copied from their own host buffers into
+ * the context (one copy per request), a2-a8 run as one CUDA-graph launch
+ * over the whole batch (tpc_run_graph), and each request's tracks and
+ * cluster assignment are copied into its own buffers.  Requests never share
+ * tracks, so each request's result equals the one it gets alone. */
+typedef struct {
+  int64_t id;                  /* caller-chosen, unique within the batch */
+  const tpc_cluster *clusters; /* host memory, n records; page-locked memory lets the copy run
+                                  asynchronously.  Must stay valid and unchanged until tpc_poll
+                                  reports the request done */
+  int64_t n;
+  tpc_track *tracks_out;       /* host memory, room for cap tracks (a track owns at least
+                                  n_min_track clusters, so n / n_min_track + 1 always suffices);
+                                  tracks as tpc_get_tracks writes them for the whole batch
+                                  (request = the request's position in the batch) */
+  int64_t cap;
+  int32_t *cluster_track_out;  /* host memory, n entries or NULL: index into this request's
+                                  tracks_out of every cluster's track (input order), -1 when
+                                  unassigned */
+  int64_t *n_tracks;           /* NULL, or receives the request's track count when it is done
+                                  (also when cap was too small) */
+} tpc_request;
+
+/* Enqueue the batch reqs[0..n) on the context's stream and return without
+ * waiting.  Buffers are owned by the caller and must stay valid until
+ * tpc_poll reports each request done.  TPC_EBUSY: the previous batch of
+ * this context is still in flight (its requests are forgotten once a new
+ * batch is accepted).  TPC_EINVAL: n < 1, bad sizes, null buffers or an id
+ * used twice.  TPC_ENOMEM: the batch does not fit the context's budget.
+ * While a batch is in flight the context's tpc_load_* calls return
+ * TPC_EBUSY; once it is done, tpc_get_tracks and tpc_get_stage show the
+ * whole batch. */
+int tpc_submit_batch(tpc_ctx *ctx, const tpc_request *reqs, int32_t n);
+
+/* Never waits.  *done = 1 once the request's results are in its buffers
+ * (the call then returns the request's status: TPC_OK, TPC_EOVERFLOW when
+ * its cap was too small -- nothing copied, *n_tracks set -- or the batch's
+ * error, e.g. TPC_EINVAL for a cluster that failed validation); *done = 0
+ * while it runs (TPC_OK).  A device capacity overflow reruns the batch once
+ * with the worst-case tracklet capacity.  TPC_EINVAL for an id that is not
+ * in the context's current batch. */
+int tpc_poll(tpc_ctx *ctx, int64_t request_id, int *done);
 
 /* Wait for the context's stream and report device-side errors. */
 int tpc_sync(tpc_ctx *ctx);

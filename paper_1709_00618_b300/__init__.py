@@ -94,6 +94,12 @@ _lib = None
 _VP, _I64, _I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
 
 
+class TpcRequest(ctypes.Structure):
+    """One request of tpc_submit_batch (pointers to host buffers)."""
+    _fields_ = [("id", _I64), ("clusters", _VP), ("n", _I64), ("tracks_out", _VP), ("cap", _I64),
+                ("cluster_track_out", _VP), ("n_tracks", _VP)]
+
+
 def load_library(path: str | None = None):
     """Load libtpcca.so (built in-tree by build()).  Raises if it is missing."""
     global _lib
@@ -153,6 +159,8 @@ def load_library(path: str | None = None):
         "tpc_server_drain": ([_VP, ctypes.c_double], ctypes.c_int),
         "tpc_server_stats": ([_VP, _VP], ctypes.c_int),
         "tpc_server_destroy": ([_VP], None),
+        "tpc_submit_batch": ([_VP, _VP, _I32], ctypes.c_int),
+        "tpc_poll": ([_VP, _I64, _VP], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -194,6 +202,8 @@ class Tracker:
                  arena=None, arena_clusters: int = 0, arena_requests: int = 1):
         self._lib = load_library()
         self._ctx = ctypes.c_void_p()
+        self._cfg = cfg
+        self._batch = {}
         self._arena_tensor = None
         self._stream_obj = stream
         sp = None
@@ -479,6 +489,51 @@ class Tracker:
         return dict(zip(("n", "n_req", "n_rs", "n_bins", "n_tracklets", "n_tracks", "status", "n_track_clusters"),
                         (int(v) for v in c)))
 
+    def submit_batch(self, requests):
+        """Submit independent requests as one batch (tpc_submit_batch) and
+        return at once.  requests: list of (id, clusters) or (id, clusters,
+        tracks_out, cluster_track_out) -- host buffers (numpy arrays or pinned
+        CPU torch tensors); missing result buffers are allocated.  Results
+        with poll()."""
+        reqs = (TpcRequest * len(requests))()
+        keep = []
+        n_min = max(self._n_min_track(), 1)
+        for k, rq in enumerate(requests):
+            rid, clusters = rq[0], rq[1]
+            cl = _records(clusters, CLUSTER_DTYPE, 0)
+            n = len(cl)
+            tr = _records(rq[2] if len(rq) > 2 and rq[2] is not None else np.zeros(n // n_min + 1, TRACK_DTYPE),
+                          TRACK_DTYPE, 0)
+            ct = _records(rq[3] if len(rq) > 3 and rq[3] is not None else np.zeros(n, np.int32), np.int32, n)
+            nt = np.full(1, -1, np.int64)
+            reqs[k].id, reqs[k].n, reqs[k].cap = rid, n, len(tr)
+            reqs[k].clusters = cl.ctypes.data if n else None
+            reqs[k].tracks_out = tr.ctypes.data if len(tr) else None
+            reqs[k].cluster_track_out = ct.ctypes.data if n else None
+            reqs[k].n_tracks = nt.ctypes.data
+            keep.append((rid, clusters, cl, tr, ct, nt))
+        self._ck(self._lib.tpc_submit_batch(self._ctx, reqs, len(requests)))
+        self._batch = {k[0]: k for k in keep}
+        self.n = sum(len(k[2]) for k in keep)
+        return self
+
+    def poll(self, request_id: int):
+        """(tracks, cluster_track) of a finished request of the submitted
+        batch -- views of its buffers -- or None while it runs.  Raises
+        TpcError when the request failed (e.g. TPC_EOVERFLOW: tracks_out too
+        small)."""
+        done = ctypes.c_int()
+        rc = self._lib.tpc_poll(self._ctx, request_id, ctypes.byref(done))
+        if rc != 0:
+            raise TpcError(rc, self._lib.tpc_last_error(self._ctx).decode())
+        if not done.value:
+            return None
+        _, _, _, tr, ct, nt = self._batch[request_id]
+        return tr[:int(nt[0])], ct
+
+    def _n_min_track(self) -> int:
+        return self._cfg.n_min_track if self._cfg is not None else default_config().n_min_track
+
     def get_into(self, tracks_out, cluster_track_out=None):
         """Wait and copy the results into caller buffers (numpy arrays or
         pinned CPU torch tensors); returns (tracks view, cluster_track)."""
@@ -671,13 +726,30 @@ def row_params_noalloc(d_clusters, req_offsets=None, out=None, stream=None) -> i
     """Per-row-sector grid records of device-resident clusters without any
     device allocation by the library (tpc_row_params_noalloc): for callers
     that may not allocate, e.g. under a memory budget owned by their host
-    framework.  d_clusters and out are CUDA tensors (out: n_req*36*159*32
-    bytes, caller-allocated).  Returns the status code."""
+    framework.  d_clusters and out are contiguous CUDA tensors on the same
+    device (out: n_req*36*159*32 bytes, caller-allocated).  The call runs
+    with that device current and, without `stream`, on torch's current
+    stream of it.  Returns the status code."""
+    import torch
     lib = load_library()
     n = d_clusters.numel() * d_clusters.element_size() // 16
     off = np.ascontiguousarray(np.asarray(req_offsets if req_offsets is not None else [0, n], dtype=np.int64))
-    sp = None
-    if stream is not None:
-        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
-    return lib.tpc_row_params_noalloc(d_clusters.data_ptr() if n else None, n, off.ctypes.data, len(off) - 1,
-                                      out.data_ptr(), sp)
+    n_req = len(off) - 1
+    need = n_req * 36 * 159 * 32
+    if not (d_clusters.is_cuda and out is not None and out.is_cuda):
+        raise ValueError("d_clusters and out must be CUDA tensors")
+    if d_clusters.device != out.device:
+        raise ValueError(f"d_clusters on {d_clusters.device}, out on {out.device}: one device expected")
+    if not (d_clusters.is_contiguous() and out.is_contiguous()):
+        raise ValueError("d_clusters and out must be contiguous")
+    if d_clusters.numel() * d_clusters.element_size() != 16 * n:
+        raise ValueError("d_clusters must hold whole 16-byte cluster records")
+    if out.numel() * out.element_size() < need:
+        raise ValueError(f"out holds {out.numel() * out.element_size()} bytes, {need} needed")
+    with torch.cuda.device(d_clusters.device):
+        if stream is None:
+            sp = torch.cuda.current_stream().cuda_stream
+        else:
+            sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        return lib.tpc_row_params_noalloc(d_clusters.data_ptr() if n else None, n, off.ctypes.data, n_req,
+                                          out.data_ptr(), sp)

@@ -23,12 +23,14 @@
 #include "codec.cuh"
 #include "merge.cuh"
 #include "reject.cuh"
+#include "batch.cuh"
 
 using namespace tpc;
 
 namespace {
 
 constexpr size_t ALIGN = 256;
+enum { BATCH_NONE = 0, BATCH_RUNNING = 1, BATCH_COPYING = 2, BATCH_DONE = 3 };
 inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 // Geometry of the reading: X_r = (float)(85.2 + r*((245.8-85.2)/158)),
@@ -43,18 +45,52 @@ void geometry_tables(float* x, float* yhi) {
   yhi[NROW] = yhi[NROW - 1];
 }
 
-std::mutex g_dev_mutex;
-std::vector<int> g_dev_ready;
+// Unique id of the calling thread's current CUDA context (0 when it cannot
+// be had).  Device-side state that belongs to the loaded module -- the row
+// tables and the allocation-free entry point's scratch array -- lives as
+// long as that context: after cudaDeviceReset the runtime creates a new
+// primary context with a new id, reloads the module, and the per-device
+// set-up below runs again instead of trusting an address of the old one.
+unsigned long long current_context_id() {
+  typedef int (*GetCurrent)(void**);
+  typedef int (*GetId)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (GetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (GetId)f;
+  });
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
 
+std::mutex g_dev_mutex;
+std::vector<unsigned long long> g_dev_ready;  // per device: context id the tables were uploaded in
+
+// Uploads the row tables once per device and context; the device must be
+// current.
 cudaError_t ensure_device_tables(int device) {
+  cudaError_t e = cudaSetDevice(device);  // also creates the device's primary context
+  if (e != cudaSuccess) return e;
+  const unsigned long long id = current_context_id();
   std::lock_guard<std::mutex> lk(g_dev_mutex);
   if ((int)g_dev_ready.size() <= device) g_dev_ready.resize(device + 1, 0);
-  if (g_dev_ready[device]) return cudaSuccess;
+  if (id != 0 && g_dev_ready[device] == id) return cudaSuccess;
   float x[NROW + 1], y[NROW + 1];
   geometry_tables(x, y);
-  cudaError_t e = cudaMemcpyToSymbol(g_row_x, x, sizeof(x));
+  e = cudaMemcpyToSymbol(g_row_x, x, sizeof(x));
   if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_row_yhi, y, sizeof(y));
-  if (e == cudaSuccess) g_dev_ready[device] = 1;
+  if (e == cudaSuccess) g_dev_ready[device] = id;
   return e;
 }
 
@@ -83,7 +119,7 @@ Caps default_caps(int64_t n, int32_t req) {
 
 // Offsets of every device array inside the arena.
 struct Layout {
-  size_t counts, req_off, in, rs_in, gbin, slot, tmp, perm, yz, rs_of, up, dn, up_m, dn_m, tie, flag, fidx, clen,
+  size_t counts, req_off, req_trk, in, rs_in, gbin, slot, tmp, perm, yz, rs_of, up, dn, up_m, dn_m, tie, flag, fidx, clen,
       cend, owner, cluster_track, track_clusters;
   size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
   size_t bin_cnt, bin_start;
@@ -109,6 +145,7 @@ Layout make_layout(const Caps& c) {
                M = (size_t)c.tracks;
   L.counts = take(sizeof(Counts));
   L.req_off = take(8 * (R + 1));
+  L.req_trk = take(8 * R);  // per request: first track, one past its last (tpc_submit_batch)
   L.in = take(16 * N);
   L.rs_in = take(4 * N);
   L.gbin = take(4 * N);
@@ -195,6 +232,18 @@ struct tpc_ctx {
   Counts* h_counts = nullptr;  // pinned mirror
   int64_t* h_req = nullptr;    // pinned request offsets
   int32_t h_req_cap = 0;
+  int32_t* h_req_trk = nullptr;  // pinned: per request first track, one past its last
+  // batch submitted with tpc_submit_batch, tracked by tpc_poll
+  struct BatchReq {
+    tpc_request r;
+    int64_t off = 0;  // first cluster of the request in the batch
+    int rc = TPC_OK;
+    bool done = false;
+  };
+  std::vector<BatchReq> batch;
+  int batch_state = 0;  // BATCH_*
+  bool batch_retried = false;
+  cudaEvent_t ev_batch = nullptr;
   // tuning
   int block_clusters = 256;
   int block_follow = 128;
@@ -387,8 +436,12 @@ int do_reserve(tpc_ctx* ctx, const Caps& want) {
   }
   if (ctx->h_req_cap < c.req + 1) {
     if (ctx->h_req) cudaFreeHost(ctx->h_req);
+    if (ctx->h_req_trk) cudaFreeHost(ctx->h_req_trk);
     ctx->h_req = nullptr;
+    ctx->h_req_trk = nullptr;
+    ctx->h_req_cap = 0;
     CK(cudaMallocHost(&ctx->h_req, sizeof(int64_t) * (c.req + 1)));
+    CK(cudaMallocHost(&ctx->h_req_trk, sizeof(int32_t) * 2 * (c.req + 1)));
     ctx->h_req_cap = c.req + 1;
   }
   return TPC_OK;
@@ -696,14 +749,19 @@ int check_status(tpc_ctx* ctx) {
   return TPC_OK;
 }
 
-int load_common(tpc_ctx* ctx, const tpc_cluster* c, const int64_t* off, int32_t n_req, int on_device) {
+// parts (optional): request q's clusters are copied from parts[q].clusters
+// (host memory) instead of from c + off[q].
+int load_common(tpc_ctx* ctx, const tpc_cluster* c, const int64_t* off, int32_t n_req, int on_device,
+                const tpc_request* parts = nullptr) {
   if (!ctx) return TPC_EINVAL;
+  if (ctx->batch_state == BATCH_RUNNING || ctx->batch_state == BATCH_COPYING)
+    return fail(ctx, TPC_EBUSY, "a batch submitted with tpc_submit_batch is still in flight");
   if (n_req < 1 || !off || off[0] != 0) return fail(ctx, TPC_EINVAL, "bad request offsets");
   for (int32_t q = 0; q < n_req; q++)
     if (off[q + 1] < off[q]) return fail(ctx, TPC_EINVAL, "request offsets must be non-decreasing");
   int64_t n = off[n_req];
   if (n < 0 || n >= 0x7FFFFFFF / 2) return fail(ctx, TPC_EINVAL, "cluster count %lld out of range", (long long)n);
-  if (n > 0 && !c) return fail(ctx, TPC_EINVAL, "null cluster pointer");
+  if (n > 0 && !c && !parts) return fail(ctx, TPC_EINVAL, "null cluster pointer");
   if ((int64_t)n_req * NSEC * NROW >= 0x7FFFFFFF / 2) return fail(ctx, TPC_EINVAL, "too many requests");
   Caps want = default_caps(n, n_req);
   want.bins = std::max(want.bins, ctx->caps.bins);
@@ -723,9 +781,15 @@ int load_common(tpc_ctx* ctx, const tpc_cluster* c, const int64_t* off, int32_t 
   CK(cudaMemcpyAsync(ctx->ptr<Counts>(L.counts), ctx->h_counts, sizeof(Counts), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(ctx->ptr<int64_t>(L.req_off), ctx->h_req, sizeof(int64_t) * (n_req + 1),
                      cudaMemcpyHostToDevice, ctx->stream));
-  if (n > 0)
+  if (parts) {
+    for (int32_t q = 0; q < n_req; q++)
+      if (off[q + 1] > off[q])
+        CK(cudaMemcpyAsync(ctx->ptr<tpc_cluster>(L.in) + off[q], parts[q].clusters,
+                           sizeof(tpc_cluster) * (off[q + 1] - off[q]), cudaMemcpyHostToDevice, ctx->stream));
+  } else if (n > 0) {
     CK(cudaMemcpyAsync(ctx->ptr<tpc_cluster>(L.in), c, sizeof(tpc_cluster) * n,
                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+  }
   ctx->n = n;
   ctx->n_req = n_req;
   ctx->loaded = true;
@@ -755,7 +819,7 @@ int tpc_default_config(tpc_config* c) {
   c->c0[4] = 100.0;
   c->s_max = 0.95;
   c->edge = 2.0;
-  c->taint_rel = 2e-3;
+  c->taint_rel = 1e-4;
   c->fp64_updates = 10;
   return TPC_OK;
 }
@@ -797,6 +861,8 @@ void tpc_destroy(tpc_ctx* ctx) {
   }
   if (ctx->h_counts) cudaFreeHost(ctx->h_counts);
   if (ctx->h_req) cudaFreeHost(ctx->h_req);
+  if (ctx->h_req_trk) cudaFreeHost(ctx->h_req_trk);
+  if (ctx->ev_batch) cudaEventDestroy(ctx->ev_batch);
   if (ctx->vtx_mem) cudaFree(ctx->vtx_mem);
   if (ctx->codec_mem) cudaFree(ctx->codec_mem);
   if (ctx->merge_mem) cudaFree(ctx->merge_mem);
@@ -954,6 +1020,156 @@ int tpc_get_tracks_async(tpc_ctx* ctx, tpc_track* out, int64_t cap, int64_t* n_o
     CK(cudaMemcpyAsync(cluster_track, ctx->ptr<int32_t>(L.cluster_track), sizeof(int32_t) * ctx->n,
                        cudaMemcpyDeviceToHost, ctx->stream));
   return TPC_OK;
+}
+
+// ---------------------------------------------- batched requests (a1-a9)
+namespace {
+
+// After the batch's graph: each request's track range and request-local
+// cluster->track indices (into the grid stage's dead per-cluster scratch),
+// the ranges copied to the host, and the completion event.
+int enqueue_batch_views(tpc_ctx* ctx) {
+  const Layout& L = ctx->L;
+  cudaStream_t s = ctx->stream;
+  Counts* cn = ctx->ptr<Counts>(L.counts);
+  const int bc = ctx->block_clusters;
+  CK(cudaMemsetAsync(ctx->ptr<int32_t>(L.req_trk), 0, sizeof(int32_t) * 2 * ctx->n_req, s));
+  k_req_tracks<<<grid_for(ctx, ctx->caps.tracks, bc), bc, 0, s>>>(ctx->ptr<tpc_track>(L.tracks),
+                                                                  ctx->ptr<int32_t>(L.req_trk), cn);
+  k_req_rebase<<<grid_for(ctx, std::max<int64_t>(ctx->n, 1), bc), bc, 0, s>>>(
+      ctx->ptr<int32_t>(L.cluster_track), ctx->ptr<int64_t>(L.req_off), ctx->ptr<int32_t>(L.req_trk),
+      ctx->ptr<int32_t>(L.slot), cn);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->h_req_trk, ctx->ptr<int32_t>(L.req_trk), sizeof(int32_t) * 2 * ctx->n_req,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaEventRecord(ctx->ev_batch, s));
+  return TPC_OK;
+}
+
+int launch_batch(tpc_ctx* ctx) {
+  const int32_t nq = (int32_t)ctx->batch.size();
+  std::vector<int64_t> off(nq + 1, 0);
+  std::vector<tpc_request> parts(nq);
+  for (int32_t q = 0; q < nq; q++) {
+    parts[q] = ctx->batch[q].r;
+    off[q + 1] = off[q] + parts[q].n;
+  }
+  int rc = load_common(ctx, nullptr, off.data(), nq, 0, parts.data());
+  if (rc == TPC_OK) rc = tpc_run_graph(ctx);
+  if (rc == TPC_OK) rc = enqueue_batch_views(ctx);
+  return rc;
+}
+
+// Marks every request done; rc is the outcome of those that have no error
+// of their own (a request whose cap was too small keeps TPC_EOVERFLOW).
+void finish_batch(tpc_ctx* ctx, int rc) {
+  for (auto& b : ctx->batch) {
+    if (!b.done && b.rc == TPC_OK) b.rc = rc;
+    b.done = true;
+  }
+  ctx->batch_state = BATCH_DONE;
+}
+
+// Moves the submitted batch on without waiting: once its graph has run,
+// enqueues each request's result copies; once those have landed, marks the
+// requests done.  A capacity overflow reruns the batch once with the
+// worst-case tracklet capacity.
+void advance_batch(tpc_ctx* ctx) {
+  if (ctx->batch_state != BATCH_RUNNING && ctx->batch_state != BATCH_COPYING) return;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) return finish_batch(ctx, TPC_ECUDA);
+  const cudaError_t q = cudaEventQuery(ctx->ev_batch);
+  if (q == cudaErrorNotReady) return;
+  if (q != cudaSuccess) {
+    fail(ctx, TPC_ECUDA, "batch: %s", cudaGetErrorString(q));
+    return finish_batch(ctx, TPC_ECUDA);
+  }
+  if (ctx->batch_state == BATCH_COPYING) return finish_batch(ctx, TPC_OK);
+  int rc = check_status(ctx);
+  if (rc == TPC_EOVERFLOW && !ctx->batch_retried) {
+    ctx->batch_retried = true;
+    ctx->batch_state = BATCH_NONE;  // lets load_common run
+    const Counts& hc = *ctx->h_counts;
+    rc = tpc_reserve(ctx, ctx->n, ctx->n_req, 2 * (int64_t)hc.n_bins, ctx->n / 3 + 16);
+    if (rc == TPC_OK) rc = launch_batch(ctx);
+    if (rc != TPC_OK) return finish_batch(ctx, rc);
+    ctx->batch_state = BATCH_RUNNING;
+    return;
+  }
+  if (rc != TPC_OK) return finish_batch(ctx, rc);
+  const Layout& L = ctx->L;
+  for (int32_t k = 0; k < (int32_t)ctx->batch.size(); k++) {
+    auto& b = ctx->batch[k];
+    const int32_t first = ctx->h_req_trk[2 * k], cnt = ctx->h_req_trk[2 * k + 1] - first;
+    if (b.r.n_tracks) *b.r.n_tracks = cnt;
+    if (cnt > b.r.cap) {
+      b.rc = fail(ctx, TPC_EOVERFLOW, "request %lld: %d tracks do not fit cap %lld", (long long)b.r.id, cnt,
+                  (long long)b.r.cap);
+      continue;
+    }
+    cudaError_t e = cudaSuccess;
+    if (cnt > 0)
+      e = cudaMemcpyAsync(b.r.tracks_out, ctx->ptr<tpc_track>(L.tracks) + first, sizeof(tpc_track) * cnt,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && b.r.cluster_track_out && b.r.n > 0)
+      e = cudaMemcpyAsync(b.r.cluster_track_out, ctx->ptr<int32_t>(L.slot) + b.off, sizeof(int32_t) * b.r.n,
+                          cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) {
+      fail(ctx, TPC_ECUDA, "batch copy: %s", cudaGetErrorString(e));
+      return finish_batch(ctx, TPC_ECUDA);
+    }
+  }
+  if (cudaEventRecord(ctx->ev_batch, ctx->stream) != cudaSuccess) return finish_batch(ctx, TPC_ECUDA);
+  ctx->batch_state = BATCH_COPYING;
+}
+
+}  // namespace
+
+int tpc_submit_batch(tpc_ctx* ctx, const tpc_request* reqs, int32_t n) {
+  if (!ctx) return TPC_EINVAL;
+  if (ctx->batch_state == BATCH_RUNNING || ctx->batch_state == BATCH_COPYING) {
+    advance_batch(ctx);
+    if (ctx->batch_state != BATCH_DONE) return fail(ctx, TPC_EBUSY, "the previous batch is still in flight");
+  }
+  if (n < 1 || !reqs) return fail(ctx, TPC_EINVAL, "empty batch");
+  int64_t total = 0;
+  for (int32_t q = 0; q < n; q++) {
+    const tpc_request& r = reqs[q];
+    if (r.n < 0 || (r.n > 0 && !r.clusters) || r.cap < 0 || (r.cap > 0 && !r.tracks_out))
+      return fail(ctx, TPC_EINVAL, "request %d: bad sizes or null buffers", q);
+    for (int32_t k = 0; k < q; k++)
+      if (reqs[k].id == r.id) return fail(ctx, TPC_EINVAL, "request id %lld appears twice", (long long)r.id);
+    total += r.n;
+  }
+  if (total >= 0x7FFFFFFF / 2) return fail(ctx, TPC_EINVAL, "cluster count %lld out of range", (long long)total);
+  CK(cudaSetDevice(ctx->device));
+  if (!ctx->ev_batch) CK(cudaEventCreateWithFlags(&ctx->ev_batch, cudaEventDisableTiming));
+  ctx->batch.assign(n, tpc_ctx::BatchReq{});
+  int64_t off = 0;
+  for (int32_t q = 0; q < n; q++) {
+    ctx->batch[q].r = reqs[q];
+    ctx->batch[q].off = off;
+    off += reqs[q].n;
+  }
+  ctx->batch_state = BATCH_NONE;
+  ctx->batch_retried = false;
+  const int rc = launch_batch(ctx);
+  if (rc != TPC_OK) {
+    ctx->batch.clear();
+    return rc;
+  }
+  ctx->batch_state = BATCH_RUNNING;
+  return TPC_OK;
+}
+
+int tpc_poll(tpc_ctx* ctx, int64_t request_id, int* done) {
+  if (!ctx || !done) return TPC_EINVAL;
+  int32_t k = -1;
+  for (int32_t q = 0; q < (int32_t)ctx->batch.size(); q++)
+    if (ctx->batch[q].r.id == request_id) k = q;
+  if (k < 0) return fail(ctx, TPC_EINVAL, "unknown request id %lld", (long long)request_id);
+  advance_batch(ctx);
+  *done = ctx->batch[k].done ? 1 : 0;
+  return *done ? ctx->batch[k].rc : TPC_OK;
 }
 
 int tpc_get_counts(tpc_ctx* ctx, int64_t counts[8]) {
@@ -1920,7 +2136,11 @@ __global__ void __launch_bounds__(1024) k_na_binbase(const NoallocScratch* s, in
 }
 
 std::mutex g_na_mutex;
-std::vector<void*> g_na_addr;  // device address of g_noalloc_scratch, per device
+struct NaAddr {
+  unsigned long long ctx_id = 0;  // context the address belongs to
+  void* addr = nullptr;           // device address of g_noalloc_scratch there
+};
+std::vector<NaAddr> g_na_addr;  // per device
 
 }  // namespace
 
@@ -1937,15 +2157,18 @@ extern "C" int tpc_row_params_noalloc(const tpc_cluster* d_clusters, int64_t n, 
   {
     // once per device, with that device current: the device address of the
     // scratch array (its name is only a host-side stand-in in host code)
+    // (again after the context was replaced, e.g. by cudaDeviceReset)
+    if (ensure_device_tables(dev) != cudaSuccess) return TPC_ECUDA;
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lk(g_na_mutex);
-    if ((int)g_na_addr.size() <= dev) g_na_addr.resize(dev + 1, nullptr);
-    if (!g_na_addr[dev]) {
-      if (ensure_device_tables(dev) != cudaSuccess) return TPC_ECUDA;
+    if ((int)g_na_addr.size() <= dev) g_na_addr.resize(dev + 1);
+    if (!g_na_addr[dev].addr || id == 0 || g_na_addr[dev].ctx_id != id) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TPC_ECUDA;
-      g_na_addr[dev] = p;
+      g_na_addr[dev].addr = p;
+      g_na_addr[dev].ctx_id = id;
     }
-    addr = g_na_addr[dev];
+    addr = g_na_addr[dev].addr;
   }
   NoallocScratch* s = reinterpret_cast<NoallocScratch*>(addr);
   cudaStream_t st = (cudaStream_t)cuda_stream;

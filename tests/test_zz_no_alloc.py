@@ -74,3 +74,22 @@ def test_noalloc_rejects_beyond_its_limit():
     # and the next valid call is unaffected by the previous one
     rc, got = _noalloc(ev.clusters, [0, n])
     assert rc == 0 and got.tobytes() == _reference(ev.clusters, [0, n]).tobytes()
+
+
+def test_noalloc_wrapper_refuses_bad_buffers():
+    """The binding checks what the C entry point cannot: the output's size,
+    contiguity and device, before any launch."""
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    ev = synth.one_sector(seed=0)
+    n = len(ev.clusters)
+    dev = torch.from_numpy(ev.clusters.view(np.uint8).copy()).cuda()
+    short = torch.empty(36 * 159 * 32 - 1, dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        tpc.row_params_noalloc(dev, [0, n], short)
+    strided = torch.empty(2 * 36 * 159 * 32, dtype=torch.uint8, device="cuda")[::2]
+    with pytest.raises(ValueError):
+        tpc.row_params_noalloc(dev, [0, n], strided)
+    with pytest.raises(ValueError):
+        tpc.row_params_noalloc(dev, [0, n], torch.empty(36 * 159 * 32, dtype=torch.uint8))
