@@ -68,7 +68,7 @@ void orc_default_config(orc_config *c) {
   c->c0[0] = 100.0; c->c0[1] = 100.0; c->c0[2] = 1.0; c->c0[3] = 1.0; c->c0[4] = 100.0;
   c->s_max = 0.95;
   c->edge = 2.0;
-  c->taint_rel = 2e-3;
+  c->taint_rel = 1e-4;
   c->trace_t = -1;
 }
 

@@ -9,7 +9,7 @@ import pytest
 import oracle
 import synth
 from oracle import merge
-from parity import (PAR_TOL, COV_TOL, compare_follow, compare_selection, cov_rel_err, follow_result, par_rel_err,
+from parity import (PAR_TOL, compare_follow, compare_selection, cov_rel_err, follow_result, par_rel_err,
                     record_stats)
 
 pytestmark = pytest.mark.gpu
@@ -95,4 +95,6 @@ def test_merging_matches_the_oracle(which):
                  merge_chains_ref=int(len(mo["chains"])), merge_chains_compared=compared,
                  merge_par_err_max=float(max(pe_all)), merge_cov_err_max=float(max(ce_all)))
     record_stats(f"merge_{which}", stats)
-    assert stats["merge_par_err_max"] <= PAR_TOL and stats["merge_cov_err_max"] <= COV_TOL, stats
+    # cov_rel_err is in units of each entry's bound (1e-3 relative, or 1e-4
+    # in correlation units for weak correlations): <= 1 passes
+    assert stats["merge_par_err_max"] <= PAR_TOL and stats["merge_cov_err_max"] <= 1.0, stats

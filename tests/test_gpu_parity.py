@@ -102,7 +102,9 @@ def test_edge_cases(trk):
     blob = np.zeros(3000, synth.CLUSTER_DTYPE)
     blob["row"], blob["sector"], blob["y"], blob["z"] = 80, 0, 3.0, 40.0
     cl = np.concatenate([dup, blob])
-    full_parity(trk, cl, oracle.run(cl))
+    # every third cluster duplicated: exact ties by construction, so the
+    # tie-tainted shadow is large on purpose and its bound is lifted here
+    full_parity(trk, cl, oracle.run(cl), shadow_max=1.0)
     # invalid cluster -> EINVAL, and the context stays usable
     bad = ev.clusters.copy()
     bad["row"][7] = 200
