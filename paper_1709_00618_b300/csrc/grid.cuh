@@ -153,12 +153,12 @@ __global__ void k_grid_scatter(const tpc_cluster* __restrict__ in, const int32_t
 // sqrt(2 A / n)); the count is quadratic only in the fullest bin.  The bin
 // of a record is recomputed from its position with the binning arithmetic
 // of k_grid_bin.  Also clears the selection stage's per-cluster arrays
-// (owner keys to 0, the cluster-to-track map to -1), which are as long as the
-// cluster list.
+// (owner keys -- 32- or 64-bit -- to 0, the cluster-to-track map to -1),
+// which are as long as the cluster list.
 __global__ void k_grid_order(const int4* __restrict__ rec, const RsParams* __restrict__ par,
                              const int32_t* __restrict__ bin_start, int32_t* __restrict__ perm,
-                             float2* __restrict__ yz, int32_t* __restrict__ rs_of, uint64_t* __restrict__ owner,
-                             int32_t* __restrict__ cluster_track, const Counts* cn) {
+                             float2* __restrict__ yz, int32_t* __restrict__ rs_of, void* __restrict__ owner,
+                             bool key32, int32_t* __restrict__ cluster_track, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t p = gtid(); p < n; p += gstride()) {
@@ -176,7 +176,8 @@ __global__ void k_grid_order(const int4* __restrict__ rec, const RsParams* __res
     perm[dst] = i;
     yz[dst] = make_float2(y, z);
     rs_of[dst] = rs;
-    owner[p] = 0ull;
+    if (key32) reinterpret_cast<uint32_t*>(owner)[p] = 0u;
+    else reinterpret_cast<uint64_t*>(owner)[p] = 0ull;
     cluster_track[p] = -1;
   }
 }

@@ -20,23 +20,20 @@ __device__ __forceinline__ void bin_range(float v0, float v1, float lo, float in
 // link windows minimising the squared deviation of the cluster from the d-u
 // chord, ties to the lower sorted index of d, then of u; accepted if
 // D <= d_max.  D is evaluated in binary32 with one rounding per operation in
-// the order of the reading, so the choice is reproducible bit for bit.
+// the order of the reading, so the choice is reproducible bit for bit; the
+// pick is a lexicographic minimum, so it does not depend on the order in
+// which candidates are visited.
 //
-// A group of NB_G lanes handles one cluster: the lanes scan the candidate
-// bins of both rows together, stage the in-window candidates in shared
-// memory, share the d x u pairs and merge their best pairs with shuffles,
-// so the work of a cluster no longer depends on one lane's loop lengths.
-// A cluster with more than NB_CAP in-window candidates on a row (dense
-// pile-ups) is finished by the group's first lane alone.
-#ifndef TPC_NB_G
-#define TPC_NB_G 4
-#endif
-#ifndef TPC_NB_CAP
-#define TPC_NB_CAP 16
-#endif
-constexpr int NB_G = TPC_NB_G;
-constexpr int NB_CAP = TPC_NB_CAP;
+// One lane per cluster, consecutive clusters of the sorted order in a warp
+// (neighbouring windows, so candidate loads hit in L1).  The lane scans the
+// bins of its row r+1 window once and keeps the in-window candidates in its
+// column of a shared list, then scans its row r-1 window and pairs every
+// in-window d with that list: the work is (scanned candidates of both rows)
+// + (pairs), not (in-window d) x (scanned u) as a nested scan would be.  A
+// lane with more than NB_ULIST in-window candidates on row r+1 (dense
+// pile-ups) falls back to the nested scan.
 constexpr int NB_THREADS = 256;
+constexpr int NB_ULIST = 8;
 
 struct PairPick {
   float best, second;
@@ -71,20 +68,24 @@ __device__ __forceinline__ bool in_window(float2 q, float2 me, float WY, float W
   return fabsf(__fsub_rn(q.x, me.x)) <= WY && fabsf(__fsub_rn(q.y, me.y)) <= WZ;
 }
 
-// One lane over all pairs (the fallback for dense windows).
-__device__ __noinline__ void serial_pairs(const float2* __restrict__ yz, const int32_t* __restrict__ bin_start,
-                                          float2 me, float f, float WY, float WZ, int bd_base, int bd_ny,
-                                          int dy0, int dy1, int dz0, int dz1, int bu_base, int bu_ny, int uy0,
-                                          int uy1, int uz0, int uz1, PairPick& b) {
-  for (int izd = dz0; izd <= dz1; izd++) {
-    const int rowd = bd_base + izd * bd_ny;
-    const int a = __ldg(bin_start + rowd + dy0), e = __ldg(bin_start + rowd + dy1 + 1);
+// A lane's search window on one candidate row (global bin numbering).
+struct NbWin {
+  int base, ny, y0, y1, z0, z1;
+};
+
+// All in-window (d, u) pairs of one centre cluster by a nested scan (the
+// fallback for dense windows).
+__device__ __noinline__ void nb_nested(const float2* __restrict__ yz, const int32_t* __restrict__ bin_start,
+                                       float2 me, float f, float WY, float WZ, NbWin wd, NbWin wu, PairPick& b) {
+  for (int izd = wd.z0; izd <= wd.z1; izd++) {
+    const int jd = wd.base + izd * wd.ny;
+    const int a = __ldg(bin_start + jd + wd.y0), e = __ldg(bin_start + jd + wd.y1 + 1);
     for (int d = a; d < e; d++) {
       const float2 pdv = __ldg(yz + d);
       if (!in_window(pdv, me, WY, WZ)) continue;
-      for (int izu = uz0; izu <= uz1; izu++) {
-        const int rowu = bu_base + izu * bu_ny;
-        const int a2 = __ldg(bin_start + rowu + uy0), e2 = __ldg(bin_start + rowu + uy1 + 1);
+      for (int izu = wu.z0; izu <= wu.z1; izu++) {
+        const int ju = wu.base + izu * wu.ny;
+        const int a2 = __ldg(bin_start + ju + wu.y0), e2 = __ldg(bin_start + ju + wu.y1 + 1);
         for (int u = a2; u < e2; u++) {
           const float2 puv = __ldg(yz + u);
           if (!in_window(puv, me, WY, WZ)) continue;
@@ -95,32 +96,6 @@ __device__ __noinline__ void serial_pairs(const float2* __restrict__ yz, const i
   }
 }
 
-// The group stages the in-window candidates of one row; returns their
-// count (> NB_CAP: too many, nothing beyond NB_CAP stored).
-__device__ __forceinline__ int stage_row(const float2* __restrict__ yz, const int32_t* __restrict__ bin_start,
-                                         float2 me, float WY, float WZ, int base, int ny, int y0, int y1, int z0,
-                                         int z1, float2* s_pos, int32_t* s_idx, int sub, unsigned gmask) {
-  int cnt = 0;
-  const unsigned below = gmask & ((1u << (threadIdx.x & 31)) - 1u);
-  for (int iz = z0; iz <= z1; iz++) {
-    const int row = base + iz * ny;
-    const int a = __ldg(bin_start + row + y0), e = __ldg(bin_start + row + y1 + 1);
-    for (int k0 = a; k0 < e; k0 += NB_G) {
-      const int k = k0 + sub;
-      float2 q = make_float2(0.0f, 0.0f);
-      const bool hit = k < e && in_window(q = __ldg(yz + min(k, e - 1)), me, WY, WZ);
-      const unsigned m = __ballot_sync(gmask, hit);
-      const int pos = cnt + __popc(m & below);
-      if (hit && pos < NB_CAP) {
-        s_pos[pos] = q;
-        s_idx[pos] = k;
-      }
-      cnt += __popc(m);
-    }
-  }
-  return cnt;
-}
-
 __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restrict__ yz,
                                                            const int32_t* __restrict__ rs_of,
                                                            const RsParams* __restrict__ par,
@@ -128,14 +103,13 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
                                                            int32_t* __restrict__ up, int32_t* __restrict__ dn,
                                                            uint8_t* __restrict__ tie, const Counts* cn) {
   if (fatal(cn)) return;
-  __shared__ float2 s_dp[NB_THREADS / NB_G][NB_CAP], s_up[NB_THREADS / NB_G][NB_CAP];
-  __shared__ int32_t s_di[NB_THREADS / NB_G][NB_CAP], s_ui[NB_THREADS / NB_G][NB_CAP];
+  // each thread's list of in-window row r+1 candidates, one column per thread
+  __shared__ float2 s_upos[NB_ULIST][NB_THREADS];
+  __shared__ int32_t s_uidx[NB_ULIST][NB_THREADS];
+  const int tid = threadIdx.x;
   const int64_t n = cn->n;
   const float WY = kc.wy, WZ = kc.wz;
-  const int sub = threadIdx.x & (NB_G - 1), grp = threadIdx.x / NB_G;
-  const unsigned gmask = ((1u << NB_G) - 1u) << ((threadIdx.x & 31) & ~(NB_G - 1));
-  const int64_t groups = gstride() / NB_G;
-  for (int64_t c = gtid() / NB_G; c < n; c += groups) {  // group-uniform
+  for (int64_t c = gtid(); c < n; c += gstride()) {
     const int rs = __ldg(rs_of + c);
     const int row = rs % NROW;
     PairPick b{__int_as_float(0x7F800000), __int_as_float(0x7F800000), -1, -1};
@@ -145,64 +119,60 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
         const float2 me = __ldg(yz + c);
         const float xm = g_row_x[row - 1], x0 = g_row_x[row], xp = g_row_x[row + 1];
         const float f = __fdiv_rn(__fsub_rn(x0, xm), __fsub_rn(xp, xm));
-        const float yld = -g_row_yhi[row - 1], ylu = -g_row_yhi[row + 1];
-        int dy0, dy1, dz0, dz1, uy0, uy1, uz0, uz1;
-        bin_range(me.x - WY, me.x + WY, yld, pd.inv_y, pd.n_y, dy0, dy1);
-        bin_range(me.y - WZ, me.y + WZ, pd.z_lo, pd.inv_z, pd.n_z, dz0, dz1);
-        bin_range(me.x - WY, me.x + WY, ylu, pu.inv_y, pu.n_y, uy0, uy1);
-        bin_range(me.y - WZ, me.y + WZ, pu.z_lo, pu.inv_z, pu.n_z, uz0, uz1);
-        const int nd = stage_row(yz, bin_start, me, WY, WZ, pd.bin_base, pd.n_y, dy0, dy1, dz0, dz1, s_dp[grp],
-                                 s_di[grp], sub, gmask);
-        const int nu = stage_row(yz, bin_start, me, WY, WZ, pu.bin_base, pu.n_y, uy0, uy1, uz0, uz1, s_up[grp],
-                                 s_ui[grp], sub, gmask);
-        __syncwarp(gmask);
-        if (nd > NB_CAP || nu > NB_CAP) {
-          if (sub == 0)
-            serial_pairs(yz, bin_start, me, f, WY, WZ, pd.bin_base, pd.n_y, dy0, dy1, dz0, dz1, pu.bin_base,
-                         pu.n_y, uy0, uy1, uz0, uz1, b);
-        } else {
-          for (int p = sub; p < nd * nu; p += NB_G) {
-            const int i = p / nu, j = p - i * nu;
-            pair_add(b, pair_dev(me, s_dp[grp][i], s_up[grp][j], f), s_di[grp][i], s_ui[grp][j]);
-          }
-          // merge the lanes' picks: the lexicographic minimum, and the
-          // smallest D of every other pair
-#pragma unroll
-          for (int o = NB_G / 2; o >= 1; o >>= 1) {
-            PairPick q;
-            q.best = __shfl_xor_sync(gmask, b.best, o);
-            q.second = __shfl_xor_sync(gmask, b.second, o);
-            q.d = __shfl_xor_sync(gmask, b.d, o);
-            q.u = __shfl_xor_sync(gmask, b.u, o);
-            if (q.d >= 0 && pair_before(q.best, q.d, q.u, b)) {
-              b.second = fminf(q.second, b.d >= 0 ? b.best : b.second);
-              b.best = q.best;
-              b.d = q.d;
-              b.u = q.u;
-            } else {
-              b.second = fminf(b.second, q.d >= 0 ? q.best : q.second);
-              b.second = fminf(b.second, q.second);
+        NbWin wd, wu;
+        wd.base = pd.bin_base;
+        wd.ny = pd.n_y;
+        wu.base = pu.bin_base;
+        wu.ny = pu.n_y;
+        bin_range(me.x - WY, me.x + WY, -g_row_yhi[row - 1], pd.inv_y, pd.n_y, wd.y0, wd.y1);
+        bin_range(me.y - WZ, me.y + WZ, pd.z_lo, pd.inv_z, pd.n_z, wd.z0, wd.z1);
+        bin_range(me.x - WY, me.x + WY, -g_row_yhi[row + 1], pu.inv_y, pu.n_y, wu.y0, wu.y1);
+        bin_range(me.y - WZ, me.y + WZ, pu.z_lo, pu.inv_z, pu.n_z, wu.z0, wu.z1);
+        // row r+1: the in-window candidates, in sorted order
+        int nu = 0;
+        for (int iz = wu.z0; iz <= wu.z1; iz++) {
+          const int j = wu.base + iz * wu.ny;
+          const int a = __ldg(bin_start + j + wu.y0), e = __ldg(bin_start + j + wu.y1 + 1);
+          for (int u = a; u < e; u++) {
+            const float2 q = __ldg(yz + u);
+            if (in_window(q, me, WY, WZ)) {
+              if (nu < NB_ULIST) {
+                s_upos[nu][tid] = q;
+                s_uidx[nu][tid] = u;
+              }
+              nu++;
             }
           }
         }
-        __syncwarp(gmask);  // the staged candidates are reused by the next cluster
+        if (nu > NB_ULIST) {
+          nb_nested(yz, bin_start, me, f, WY, WZ, wd, wu, b);
+        } else if (nu > 0) {
+          // row r-1: every in-window d against the list
+          for (int iz = wd.z0; iz <= wd.z1; iz++) {
+            const int j = wd.base + iz * wd.ny;
+            const int a = __ldg(bin_start + j + wd.y0), e = __ldg(bin_start + j + wd.y1 + 1);
+            for (int d = a; d < e; d++) {
+              const float2 q = __ldg(yz + d);
+              if (!in_window(q, me, WY, WZ)) continue;
+              for (int k = 0; k < nu; k++) pair_add(b, pair_dev(me, q, s_upos[k][tid], f), d, s_uidx[k][tid]);
+            }
+          }
+        }
       }
     }
-    if (sub == 0) {
-      int32_t bu = -1, bd = -1;
-      uint8_t tflag = 0;
-      if (b.d >= 0 && b.best <= kc.d_max) {
-        bd = b.d;
-        bu = b.u;
-        tflag = (b.second != __int_as_float(0x7F800000) &&
-                 fabsf(__fsub_rn(b.second, b.best)) <= __fmul_rn(1e-6f, fmaxf(b.best, 1e-12f)))
-                    ? 1
-                    : 0;
-      }
-      up[c] = bu;
-      dn[c] = bd;
-      tie[c] = tflag;
+    int32_t bu = -1, bd = -1;
+    uint8_t tflag = 0;
+    if (b.d >= 0 && b.best <= kc.d_max) {
+      bd = b.d;
+      bu = b.u;
+      tflag = (b.second != __int_as_float(0x7F800000) &&
+               fabsf(__fsub_rn(b.second, b.best)) <= __fmul_rn(1e-6f, fmaxf(b.best, 1e-12f)))
+                  ? 1
+                  : 0;
     }
+    up[c] = bu;
+    dn[c] = bd;
+    tie[c] = tflag;
   }
 }
 

@@ -7,27 +7,44 @@
 
 namespace tpc {
 
-__device__ __forceinline__ uint64_t track_key(int n, int t) {
+// Ownership key of tracklet t with n clusters: the larger key wins a
+// cluster, i.e. more clusters first, then the lower tracklet id.  64-bit:
+// n << 32 | (2^32 - 1 - t).  32-bit, while the tracklet capacity is below
+// 2^24 (n <= 159 < 2^8): n << 24 | (2^24 - 1 - t) -- the same order, half
+// the bytes and atomics of half the width.
+template <typename Key>
+__device__ __forceinline__ Key track_key(int n, int t);
+template <>
+__device__ __forceinline__ uint64_t track_key<uint64_t>(int n, int t) {
   return ((uint64_t)(uint32_t)n << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)t);
 }
+template <>
+__device__ __forceinline__ uint32_t track_key<uint32_t>(int n, int t) {
+  return ((uint32_t)n << 24) | (0xFFFFFFu - (uint32_t)t);
+}
+
+__device__ __forceinline__ void key_max(uint64_t* a, uint64_t k) {
+  atomicMax((unsigned long long*)a, (unsigned long long)k);
+}
+__device__ __forceinline__ void key_max(uint32_t* a, uint32_t k) { atomicMax((unsigned int*)a, (unsigned int)k); }
 
 // owner[c] = max key over the tracklets holding c.  W: one warp per
 // tracklet, the lanes over its hits (coalesced hit loads, 32 atomics in
 // flight; faster while the owner array is L2-resident); else one thread per
 // tracklet (a warp's 32 atomics then fall on neighbouring tracklets' rows:
 // better DRAM locality on inputs far larger than L2).
-template <bool W>
+template <bool W, typename Key>
 __global__ void k_own(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits, KConst kc,
-                      uint64_t* __restrict__ owner, const Counts* cn) {
+                      Key* __restrict__ owner, const Counts* cn) {
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
   const int lane = W ? (int)(threadIdx.x & 31) : 0, step = W ? 32 : 1;
   for (int64_t t = W ? gtid() >> 5 : gtid(); t < T; t += W ? gstride() >> 5 : gstride()) {
     const int n = f_n[t];
     if (n < kc.n_min_track) continue;
-    const uint64_t key = track_key(n, (int)t);
+    const Key key = track_key<Key>(n, (int)t);
     const int32_t* h = hits + t * NROW;
-    for (int i = lane; i < n; i += step) atomicMax((unsigned long long*)(owner + h[i]), (unsigned long long)key);
+    for (int i = lane; i < n; i += step) key_max(owner + h[i], key);
   }
 }
 
@@ -36,8 +53,9 @@ __global__ void k_own(const int32_t* __restrict__ f_n, const int32_t* __restrict
 // owned row range (r_in | r_out << 16), so that the refit and the output
 // stage need no ownership loads.
 constexpr int OWN_WORDS = 5;
+template <typename Key>
 __global__ void k_keep(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits,
-                       const uint8_t* __restrict__ hrow, const uint64_t* __restrict__ owner, KConst kc,
+                       const uint8_t* __restrict__ hrow, const Key* __restrict__ owner, KConst kc,
                        int32_t* __restrict__ keep, int32_t* __restrict__ nown, uint32_t* __restrict__ own_mask,
                        int32_t* __restrict__ own_rng, const Counts* cn) {
   if (fatal(cn)) return;
@@ -49,12 +67,12 @@ __global__ void k_keep(const int32_t* __restrict__ f_n, const int32_t* __restric
     unsigned r_in = NROW, r_out = 0;  // r_out: one past the outermost owned row
     uint32_t mw = 0;                  // lane w < OWN_WORDS: mask word w
     if (n >= kc.n_min_track) {
-      const uint64_t key = track_key(n, (int)t);
+      const Key key = track_key<Key>(n, (int)t);
       const int32_t* h = hits + t * NROW;
       const uint8_t* hr = hrow + t * NROW;
       for (int i0 = 0; i0 < n; i0 += 32) {
         const int i = i0 + lane;
-        const bool own = i < n && __ldg((const unsigned long long*)owner + h[i]) == key;
+        const bool own = i < n && __ldg(owner + h[i]) == key;
         const uint32_t b = __ballot_sync(FULL_MASK, own);
         if (lane == (i0 >> 5)) mw = b;
         kept += __popc(b);

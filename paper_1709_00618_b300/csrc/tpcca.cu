@@ -354,6 +354,8 @@ KConst make_kconst(const tpc_config& c, const Caps& caps) {
 // join costs weigh more; the autotuner tries both).
 constexpr int64_t kLargeBatch = int64_t(4) << 20;  // clusters from which the size default switches
 int effective_chunks(const tpc_ctx* ctx) { return ctx->chunks > 0 ? ctx->chunks : 1; }
+// 32-bit ownership keys while every tracklet id fits 24 bits (select.cuh).
+bool key32(const tpc_ctx* ctx) { return ctx->caps.tl < (int64_t(1) << 24); }
 // CTAs per SM of the refilling Kalman kernels: the tuned value, or by size
 // (a small batch is bound by its longest tracklet, a large one by throughput).
 int effective_ctas_follow(const tpc_ctx* ctx) {
@@ -581,10 +583,10 @@ void enqueue_find(tpc_ctx* ctx) {
                                    ctx->ptr<int4>(L.tmp), cn);
   k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<int4>(L.tmp), ctx->ptr<RsParams>(L.par), bin_start,
                                  ctx->ptr<int32_t>(L.perm), ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
-                                 ctx->ptr<uint64_t>(L.owner), ctx->ptr<int32_t>(L.cluster_track), cn);
+                                 ctx->ptr<void>(L.owner), key32(ctx), ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(1);
   // a3 neighbours
-  k_neighbours<<<grid_for(ctx, C.n * NB_G, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
+  k_neighbours<<<grid_for(ctx, C.n, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
                                   bin_start, ctx->kc, ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn),
                                   ctx->ptr<uint8_t>(L.tie), cn);
   ctx->mark(2);
@@ -646,12 +648,23 @@ void enqueue_find(tpc_ctx* ctx) {
   ctx->mark(4);
   // a7 selection
   const bool warp_sel = ctx->n < kLargeBatch;  // warp per tracklet while the owner array stays in L2
-  (warp_sel ? k_own<true> : k_own<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, ctx->ptr<uint64_t>(L.owner),
-                          cn);
-  k_keep<<<gTw, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint8_t>(L.hrow),
-                           ctx->ptr<uint64_t>(L.owner), ctx->kc, ctx->ptr<int32_t>(L.keep),
-                           ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask), ctx->ptr<int32_t>(L.own_rng),
-                           cn);
+  if (key32(ctx)) {
+    uint32_t* owner = ctx->ptr<uint32_t>(L.owner);
+    (warp_sel ? k_own<true, uint32_t> : k_own<false, uint32_t>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(
+        ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, owner, cn);
+    k_keep<uint32_t><<<gTw, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits),
+                                        ctx->ptr<uint8_t>(L.hrow), owner, ctx->kc, ctx->ptr<int32_t>(L.keep),
+                                        ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask),
+                                        ctx->ptr<int32_t>(L.own_rng), cn);
+  } else {
+    uint64_t* owner = ctx->ptr<uint64_t>(L.owner);
+    (warp_sel ? k_own<true, uint64_t> : k_own<false, uint64_t>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(
+        ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, owner, cn);
+    k_keep<uint64_t><<<gTw, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits),
+                                        ctx->ptr<uint8_t>(L.hrow), owner, ctx->kc, ctx->ptr<int32_t>(L.keep),
+                                        ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask),
+                                        ctx->ptr<int32_t>(L.own_rng), cn);
+  }
   scan(ctx, ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), LenSrc{&cn->n_tracklets, 0, 0}, nullptr);
   (warp_sel ? k_assign<true> : k_assign<false>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->ptr<uint32_t>(L.own_mask),
                              ctx->ptr<int32_t>(L.keep), ctx->ptr<int32_t>(L.tidx), ctx->ptr<int32_t>(L.perm),
@@ -1246,6 +1259,19 @@ int tpc_get_stage(tpc_ctx* ctx, int item, void* host_out, int64_t cap_bytes, int
     if (T) CK(cudaMemcpy(zr.data(), ctx->arena + L.f_zref, 4 * T, cudaMemcpyDeviceToHost));
     float* o = (float*)host_out;
     for (int64_t t = 0; t < T; t++) o[5 * t + 1] += zr[t];
+    return TPC_OK;
+  }
+  if (item == TPC_ITEM_OWNER && key32(ctx)) {
+    // 32-bit keys n << 24 | (2^24 - 1 - t), reported in the 64-bit form
+    // n << 32 | (2^32 - 1 - t); 0 (no owner) stays 0
+    std::vector<uint32_t> k32(n);
+    CK(cudaMemcpy(k32.data(), ctx->arena + off, 4 * n, cudaMemcpyDeviceToHost));
+    uint64_t* o = (uint64_t*)host_out;
+    for (int64_t i = 0; i < n; i++) {
+      const uint32_t k = k32[i];
+      const uint64_t t = 0xFFFFFFu - (k & 0xFFFFFFu);
+      o[i] = k ? ((uint64_t)(k >> 24) << 32) | (0xFFFFFFFFull - t) : 0ull;
+    }
     return TPC_OK;
   }
   CK(cudaMemcpy(host_out, ctx->arena + off, bytes, cudaMemcpyDeviceToHost));
