@@ -1,9 +1,12 @@
 """Benchmark of the B300 sector tracker.
 
-Default workload: one central Pb-Pb-like event (36 sectors, 8000 primaries +
-1600 secondaries, seed 1, ~1.0 M clusters).  A step is one pass of the whole
-hot path (load from a device-resident buffer, grid, CA links, tracklets,
-Kalman following, selection, refit) over that event.  Prints one JSON line.
+Default workload: a 10 ms continuous-readout timeframe at 50 kHz (about 500
+Pb-Pb collisions, z from drift time, seed 2, ~90 M clusters), the largest
+configuration that fits one GPU.  A step is one pass of the whole hot path
+(load from a device-resident buffer, grid, CA links, tracklets, Kalman
+following, selection, refit) over that timeframe.  Prints one JSON line;
+the central Pb-Pb-like event, tracking time against input size, batching
+and serving legs and the oracle's CPU baseline are extra keys of it.
 """
 from __future__ import annotations
 
@@ -124,10 +127,20 @@ def _source_hash():
     return m.hexdigest()
 
 
-def ncu_traffic():
+TRAFFIC_FILES = {"central": "kernel_traffic_central_event.txt", "timeframe": "kernel_traffic_timeframe_10ms.txt"}
+
+
+def ncu_traffic(workload: str):
     """DRAM bytes per launch of each profiled kernel from the committed ncu
-    summary, or {} when the kernels changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "kernel_traffic_central_event.txt")
+    summary of this workload, or {} when there is none or the kernels changed
+    since it was taken."""
+    if workload == CONFIG2:
+        key = "central"
+    elif workload == CONFIG3:
+        key = "timeframe"
+    else:
+        return {}
+    path = os.path.join(ROOT, "profiles", TRAFFIC_FILES[key])
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -195,28 +208,40 @@ def roofline(stages, kalman, n, alu, clocks, traffic=None):
     return line, table
 
 
-def cpu_baseline(cl):
-    """The FP64 oracle timed on this host's cores over the same event, and
-    on one core over six of its sectors."""
+def cpu_sample(cl, workload):
+    """A bounded sample of the workload for the oracle: the whole input up
+    to 1.5 M clusters, else the clusters of sectors 0 and 18 (one sector per
+    side), a labelled subset."""
+    import numpy as np
+    if len(cl) <= 1_500_000:
+        return cl, f"the whole input ({len(cl)} clusters)"
+    sub = cl[np.isin(cl["sector"], (0, 18))]
+    return sub, f"sectors 0 and 18 of the {workload} ({len(sub)} of {len(cl)} clusters), all stages a2-a8"
+
+
+def cpu_baseline(cl, workload, seconds=15.0):
+    """The FP64 oracle, as it stands, timed on this host's cores over a
+    bounded sample of the same workload (repeated for about `seconds`), and
+    on one core over part of it."""
     import numpy as np
 
     import oracle
     threads = os.cpu_count() or 1
-    oracle.run(cl[:1000], threads=threads)
+    sub, label = cpu_sample(cl, workload)
+    oracle.run(sub[:1000], threads=threads)
     times = []
-    t_end = time.perf_counter() + 15.0
+    t_end = time.perf_counter() + seconds
     while time.perf_counter() < t_end or not times:
         t0 = time.perf_counter()
-        oracle.run(cl, threads=threads)
+        oracle.run(sub, threads=threads)
         times.append(time.perf_counter() - t0)
-    sub = cl[np.isin(cl["sector"], (0, 1, 2, 18, 19, 20))]
+    one = sub[np.isin(sub["sector"], (0, 1, 2, 18, 19, 20))][:500_000]
     t0 = time.perf_counter()
-    oracle.run(sub, threads=1)
-    one = len(sub) / (time.perf_counter() - t0)
-    return {"value": len(cl) * len(times) / sum(times), "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"the full event ({len(cl)} clusters) x {len(times)} runs, all stages a2-a8",
-            "one_core": {"value": one, "sample": f"sectors 0-2 and 18-20 of the event ({len(sub)} clusters), "
-                                                 "1 thread"}}
+    oracle.run(one, threads=1)
+    one_rate = len(one) / (time.perf_counter() - t0)
+    return {"value": len(sub) * len(times) / sum(times), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{label} x {len(times)} runs",
+            "one_core": {"value": one_rate, "sample": f"{len(one)} clusters of that sample, 1 thread"}}
 
 
 def _entropy(v):
@@ -473,30 +498,30 @@ def cluster_rejection(local, flush):
 
 
 def run_reference(args):
-    """The oracle (plain FP64 C, all host cores) on the same workload."""
-    import numpy as np
-
+    """The reference arm: the FP64 oracle (plain C, all host cores), as it
+    stands, on the main line's workload; each step runs it over the same
+    bounded sample as the CPU baseline (the oracle over 90 M clusters would
+    take minutes per step)."""
     import oracle
-    import synth
-    ev = synth.central_event(seed=1)
-    n = len(ev.clusters)
+    ev, workload = workload_of(args, 0)
+    cl = ev.clusters
+    sub, label = cpu_sample(cl, workload)
     threads = os.cpu_count() or 1
-    oracle.run(ev.clusters, threads=threads)  # build + warm
+    oracle.run(sub[:1000], threads=threads)
     for _ in range(args.warmup):
-        pass
+        oracle.run(sub[:20000], threads=threads)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run(ev.clusters, threads=threads)
+        oracle.run(sub, threads=threads)
         times.append(time.perf_counter() - t0)
-    v = n * len(times) / sum(times)
+    v = len(sub) * len(times) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1",
-                                            "clusters": n},
+            "data": "synthetic", "config": {"workload": workload, "clusters": len(cl)},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": f"full event ({n} clusters) x {args.steps} runs"},
+                             "sample": f"{label}, one oracle run per step x {args.steps} steps"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -714,57 +739,38 @@ def serving_leg(local, n_timeframes=24, pool=4, loads=(0.5, 0.8, 1.0), headline=
             "by_load": by_load}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="b300")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batching", action="store_true")
-    ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-timeframes", type=int, default=24)
-    ap.add_argument("--serving-pool", type=int, default=4)
-    ap.add_argument("--timeframe-ms", type=float, default=0.0,
-                    help="time a continuous read-out timeframe of this length (50 kHz, seed 2 + rank) instead of "
-                         "the central event (for profiling inputs that fill the GPU)")
-    ap.add_argument("--all-configs", action="store_true",
-                    help="print the per-config table (one sector, central event, 10 ms timeframe) instead")
-    args = ap.parse_args()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    if args.impl == "reference":
-        if rank == 0:
-            run_reference(args)
-        return
+CONFIG3 = "10 ms continuous-readout timeframe at 50 kHz, 36 sectors, drift-time z, seed 2"
+CONFIG2 = "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1"
 
+
+def workload_of(args, rank):
+    """(event, workload name) of the bench's main line: the 10 ms timeframe
+    (the largest configuration that fits one GPU), or a timeframe of another
+    length, or the central event."""
+    import synth
+    if args.workload == "central":
+        return synth.central_event(seed=1 + rank), CONFIG2 if rank == 0 else CONFIG2.replace("seed 1", f"seed {1 + rank}")
+    ms = args.timeframe_ms if args.timeframe_ms > 0 else 10.0
+    name = CONFIG3 if ms == 10.0 else CONFIG3.replace("10 ms", f"{ms:g} ms")
+    return synth.timeframe(seed=2 + rank, length_ms=ms), name.replace("seed 2", f"seed {2 + rank}")
+
+
+def measure(cl, local, args, flush, world=1, clocks=True, e2e_steps=None):
+    """One workload through the whole path: W warm-up steps, K timed steps
+    (load from a device-resident copy + one graph replay of a2-a8, L2 flushed
+    before each, CUDA events on the library's stream, max over ranks), then
+    profiled plain runs for per-stage and per-Kalman-kernel times, and the
+    same metric end to end through the public API (page-locked host input ->
+    tracks and cluster assignment in page-locked host buffers)."""
     import numpy as np
     import torch
 
     import paper_1709_00618_b300 as tpc
     import synth
-
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if args.all_configs:
-        if rank == 0:
-            all_configs(local)
-        return
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    if args.timeframe_ms > 0:
-        ev = synth.timeframe(seed=2 + rank, length_ms=args.timeframe_ms)
-        workload = f"{args.timeframe_ms:g} ms timeframe at 50 kHz, seed {2 + rank}"
-    else:
-        ev = synth.central_event(seed=1 + rank)
-        workload = "central Pb-Pb-like event, 36 sectors, 8000+1600 tracks, seed 1"
-    cl = ev.clusters
     n = len(cl)
     stream = torch.cuda.Stream()
     trk = tpc.Tracker(device=local, stream=stream, arena="torch", arena_clusters=n)
     dev_in = torch.from_numpy(cl.view(np.uint8)).to(f"cuda:{local}")
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{local}")
 
     def step_device():
         trk.load(dev_in)
@@ -794,7 +800,6 @@ def main():
         torch.cuda.synchronize()
     t_step, total_clusters = combine_ranks(sum(times) / len(times), n, world, f"cuda:{local}")
     counts = trk.counts()
-    tracks, ct, _ = trk.get()
 
     # per-stage and per-Kalman-kernel device time: CUDA events recorded by the
     # library on its stream between the launches of plain (non-graph) runs of
@@ -817,7 +822,6 @@ def main():
         d["ms"] = statistics.median(r[name]["ms"] for r in kruns)
         kalman[name] = d
     work = trk.work()
-    alu = tpc.measure_alu_peaks(local)
 
     # end to end through the public API: pinned host input -> tracks + assignment in pinned host buffers
     pinned = torch.from_numpy(cl.view(np.uint8)).pin_memory()
@@ -825,42 +829,171 @@ def main():
     tr_buf = torch.zeros(counts["n_tracks"] + 4096, 128, dtype=torch.uint8).pin_memory()
     ct_buf = torch.zeros(n, dtype=torch.int32).pin_memory()
     e2e = []
-    for i in range(warm + args.steps):
+    k_e2e = e2e_steps if e2e_steps is not None else args.steps
+    for i in range(warm + k_e2e):
         t0 = time.perf_counter()
         trk.load(host_in)
         trk.run_graph()
-        tr, c2 = trk.get_into(tr_buf, ct_buf)
+        tr, _ = trk.get_into(tr_buf, ct_buf)
         if i >= warm:
             e2e.append(time.perf_counter() - t0)
     e2e_t, _ = combine_ranks(sum(e2e) / len(e2e), n, world, f"cuda:{local}")
     trk.close()
-    served = events_through_server(host_in, n, local, events=max(4 * args.steps, 16), slots=4) if world == 1 else None
+    del dev_in
+    return {"n": n, "t_step": t_step, "total_clusters": total_clusters, "counts": counts, "stages": stages,
+            "kalman": kalman, "work": work, "kernels_per_step": kernels_per_step, "clocks": clk.summary(),
+            "e2e": {"value": total_clusters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
+                    "d2h_bytes_per_step": 128 * len(tr) + 4 * n, "steps": k_e2e},
+            "host_in": host_in, "pinned": pinned}
 
-    clocks = clk.summary()
-    traffic = ncu_traffic() if args.timeframe_ms <= 0 else {}  # the committed capture is of the central event
-    roof, kernel_table = roofline(stages, kalman, n, alu, clocks, traffic if world == 1 else None)
+
+def time_vs_size(local, flush, known=(), reps=3):
+    """Tracking time against input size (Sec. 2: linear in the input size;
+    Sec. 5 for timeframes): device time of one graph replay (inputs resident,
+    L2 flushed, median of `reps`) for one sector, the central event and
+    timeframes of 0.3, 1 and 3 ms, plus the points in `known` ((name,
+    clusters, ms) measured by the caller); least-squares fit ms = a + b N and
+    the log-log slope over the inputs of 1 M clusters and more."""
+    import numpy as np
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    import synth
+    cases = [("one sector, 400 tracks, seed 0", lambda: synth.one_sector(seed=0).clusters),
+             (CONFIG2, lambda: synth.central_event(seed=1).clusters)]
+    for ms in (0.3, 1.0, 3.0):
+        cases.append((CONFIG3.replace("10 ms", f"{ms:g} ms"), lambda ms=ms: synth.timeframe(seed=2, length_ms=ms).clusters))
+    pts = []
+    for name, gen in cases:
+        cl = gen()
+        stream = torch.cuda.Stream()
+        with tpc.Tracker(device=local, stream=stream) as trk:
+            dev = torch.from_numpy(cl.view(np.uint8)).to(f"cuda:{local}")
+            for _ in range(3):
+                trk.load(dev).run_graph()
+            trk.sync()
+            dt = []
+            for _ in range(reps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                trk.load(dev).run_graph()
+                e1.record(stream)
+                e1.synchronize()
+                dt.append(e0.elapsed_time(e1))
+            pts.append({"workload": name, "clusters": len(cl), "ms": statistics.median(dt)})
+            del dev
+    for name, n, ms in known:
+        pts.append({"workload": name, "clusters": n, "ms": ms})
+    pts.sort(key=lambda p: p["clusters"])
+    N = np.array([p["clusters"] for p in pts], np.float64)
+    T = np.array([p["ms"] for p in pts], np.float64)
+    b, a = np.polyfit(N, T, 1)
+    pred = a + b * N
+    r2 = 1.0 - float(((T - pred) ** 2).sum() / ((T - T.mean()) ** 2).sum())
+    big = N >= 1e6
+    k = float(np.polyfit(np.log(N[big]), np.log(T[big]), 1)[0]) if big.sum() >= 2 else None
+    for p, q in zip(pts, pred):
+        p["fit_ms"] = float(q)
+        p["clusters_per_s"] = p["clusters"] / (p["ms"] / 1e3)
+    return {"points": pts, "fit": {"intercept_ms": float(a), "slope_ns_per_cluster": float(b * 1e6), "r2": r2,
+                                   "loglog_slope_from_1M_clusters": k},
+            "reading": "device time of one graph replay (inputs resident, L2 flushed, median of 3) against "
+                       "input clusters; linear in the input size means a log-log slope near 1 once the GPU is full"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="b300")
+    ap.add_argument("--workload", choices=("timeframe", "central"), default="timeframe",
+                    help="the main line's workload: the 10 ms continuous-readout timeframe (default) or the "
+                         "central event")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batching", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="main line only (no central-event line, size sweep or server stream)")
+    ap.add_argument("--serving-timeframes", type=int, default=24)
+    ap.add_argument("--serving-pool", type=int, default=4)
+    ap.add_argument("--timeframe-ms", type=float, default=0.0,
+                    help="length of the main line's timeframe (default 10 ms, seed 2 + rank)")
+    ap.add_argument("--all-configs", action="store_true",
+                    help="print the per-config table (one sector, central event, 10 ms timeframe) instead")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if args.all_configs:
+        if rank == 0:
+            all_configs(local)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ev, workload = workload_of(args, rank)
+    cl = ev.clusters
+    n = len(cl)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=f"cuda:{local}")
+    m = measure(cl, local, args, flush, world)
+    alu = tpc.measure_alu_peaks(local)
+    clocks = m["clocks"]
+    traffic = ncu_traffic(workload)
+    roof, kernel_table = roofline(m["stages"], m["kalman"], n, alu, clocks, traffic if world == 1 else None)
     for k, v in kernel_table.items():
         v["traffic"] = traffic.get(k)
     peaks, src = _peaks()
-    line = {"metric": METRIC, "value": total_clusters / t_step, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": workload,
-                       "clusters": n, "tracklets": counts["n_tracklets"], "tracks": counts["n_tracks"],
-                       "tracklets_per_track": counts["n_tracklets"] / max(counts["n_tracks"], 1),
-                       "l2": "flushed (256 MB write) between steps", "graph": True,
-                       "kernels_per_step": kernels_per_step},
+    counts = m["counts"]
+    line = {"metric": METRIC, "value": m["total_clusters"] / m["t_step"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * m["t_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload, "clusters": n},
+            "workload_detail": {"tracklets": counts["n_tracklets"], "tracks": counts["n_tracks"],
+                                "tracklets_per_track": counts["n_tracklets"] / max(counts["n_tracks"], 1),
+                                "l2": "inputs larger than L2, and L2 flushed (256 MB write) between steps",
+                                "graph": True, "kernels_per_step": m["kernels_per_step"]},
             "clocks": clocks,
             "alu_peaks_measured": alu,
-            "e2e": {"value": total_clusters / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
-                    "d2h_bytes_per_step": 128 * len(tr) + 4 * n},
-            "e2e_server": served,
-            "gpu_launches": kernels_per_step * args.steps,
+            "e2e": m["e2e"],
+            "gpu_launches": m["kernels_per_step"] * args.steps,
             "roofline": roof,
             "kernels": kernel_table,
-            "stages_ms": {k: round(v, 4) for k, v in stages.items()},
-            "work": work,
+            "stages_ms": {k: round(v, 4) for k, v in m["stages"].items()},
+            "work": m["work"],
             "peaks_source": src}
+    if world == 1 and not args.no_extras:
+        host_in = m.pop("host_in")
+        line["e2e_server"] = events_through_server(host_in, n, local, events=8 if n > 4_000_000 else 16,
+                                                   slots=3 if n > 4_000_000 else 4)
+        del host_in
+        m.pop("pinned")
+        import synth
+        synth_central = synth.central_event(seed=1).clusters
+        mc = measure(synth_central, local, args, flush, world)
+        rc, tc = roofline(mc["stages"], mc["kalman"], len(synth_central), alu, mc["clocks"],
+                          ncu_traffic(CONFIG2))
+        ce = {"workload": CONFIG2, "clusters": len(synth_central), "value": mc["total_clusters"] / mc["t_step"],
+              "ms_per_step": 1e3 * mc["t_step"], "steps": args.steps, "e2e": mc["e2e"], "roofline": rc,
+              "stages_ms": {k: round(v, 4) for k, v in mc["stages"].items()},
+              "tracks": mc["counts"]["n_tracks"], "clocks": mc["clocks"]}
+        line["central_event"] = ce
+        line["time_vs_size"] = time_vs_size(local, flush, known=((workload, n, 1e3 * m["t_step"]),))
+    else:
+        m.pop("host_in", None)
+        m.pop("pinned", None)
     if world == 1 and not args.no_batching:
         line["batching"] = batching_leg(local, flush)
     if world == 1 and not args.no_serving:
@@ -868,7 +1001,7 @@ def main():
         torch.cuda.empty_cache()
         line["serving"] = serving_leg(local, n_timeframes=args.serving_timeframes, pool=args.serving_pool)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(cl)
+        line["cpu_baseline"] = cpu_baseline(cl, workload)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
