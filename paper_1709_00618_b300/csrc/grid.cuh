@@ -93,9 +93,31 @@ __global__ void k_grid_params(const int32_t* __restrict__ cnt, const uint32_t* _
   }
 }
 
-// After the scans: store bin_base into the params and check the capacity.
+// The sort runs in two levels.  Level one moves every record from load
+// order into its bucket: buckets are ranges of whole row-sectors in sorted
+// order, a row-sector going to bucket (its first sorted position) >>
+// bucket_shift, so a bucket holds about 2^bucket_shift clusters (at most
+// GRID_BUCKETS buckets).  Level two counts bins and scatters inside one
+// bucket at a time, so its random accesses stay in L2.
+constexpr int GRID_BUCKETS = 64;
+struct GridBuckets {
+  int32_t base[GRID_BUCKETS];  // first sorted position of each bucket
+  int32_t fill[GRID_BUCKETS];  // records placed so far
+};
+
+// Bucket exponent for n clusters: 2^21 clusters (32 MB of records), or more
+// so that at most GRID_BUCKETS buckets are needed.
+__host__ __device__ inline int grid_bucket_shift(int64_t n) {
+  int sh = 21;
+  while ((n >> sh) >= GRID_BUCKETS) sh++;
+  return sh;
+}
+
+// After the scans: store bin_base into the params, check the capacity, set
+// the bucket bases and clear the bin counts.
 __global__ void k_grid_finish_params(RsParams* __restrict__ par, const int32_t* __restrict__ bin_base,
-                                     Counts* cn, int64_t bins_cap, int32_t* __restrict__ bin_cnt) {
+                                     const int32_t* __restrict__ rs_start, Counts* cn, int64_t bins_cap,
+                                     int32_t* __restrict__ bin_cnt, GridBuckets* __restrict__ bk) {
   if (fatal(cn)) return;
   int32_t nrs = cn->n_rs;
   int32_t nb = bin_base[nrs];
@@ -104,7 +126,13 @@ __global__ void k_grid_finish_params(RsParams* __restrict__ par, const int32_t* 
     if (gtid() == 0) atomicOr(&cn->status, ST_EOVERFLOW);
     return;
   }
-  for (int64_t rs = gtid(); rs < nrs; rs += gstride()) par[rs].bin_base = bin_base[rs];
+  const int sh = grid_bucket_shift(cn->n);
+  if (gtid() < GRID_BUCKETS) bk->fill[gtid()] = 0;
+  for (int64_t rs = gtid(); rs < nrs; rs += gstride()) {
+    par[rs].bin_base = bin_base[rs];
+    const int b = rs_start[rs] >> sh;
+    if (rs == 0 || (rs_start[rs - 1] >> sh) != b) bk->base[b] = rs_start[rs];
+  }
   for (int64_t b = gtid(); b <= nb; b += gstride()) bin_cnt[b] = 0;
 }
 
@@ -115,50 +143,92 @@ __device__ __forceinline__ int bin_coord(float v, float lo, float inv, int nb) {
   return __float2int_rz(f);
 }
 
-// Global bin of every cluster and its (arrival-order) slot in that bin.
-__global__ void k_grid_bin(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ rs_in,
-                           const RsParams* __restrict__ par, int32_t* __restrict__ bin_cnt,
-                           int32_t* __restrict__ gbin, int32_t* __restrict__ slot, const Counts* cn) {
+// Level one: record {load index, y, z, row-sector} of every cluster into
+// its bucket.  A block takes GRID_TILE clusters at a time, counts them per
+// bucket in shared memory and claims each bucket's range with one atomic, so
+// a bucket receives contiguous runs from each tile.
+constexpr int GRID_TILE_PER_THREAD = 4;
+__global__ void k_grid_bucket(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ rs_in,
+                              const int32_t* __restrict__ rs_start, GridBuckets* __restrict__ bk,
+                              int4* __restrict__ rec_b, const Counts* cn) {
   if (fatal(cn)) return;
+  __shared__ int32_t s_cnt[GRID_BUCKETS], s_base[GRID_BUCKETS];
   const int64_t n = cn->n;
-  for (int64_t i = gtid(); i < n; i += gstride()) {
-    float2 yz = __ldg(reinterpret_cast<const float2*>(in + i));
-    int rs = rs_in[i];
-    RsParams p = par[rs];
-    int row = rs % NROW;
-    int iy = bin_coord(yz.x, -g_row_yhi[row], p.inv_y, p.n_y);
-    int iz = bin_coord(yz.y, p.z_lo, p.inv_z, p.n_z);
-    int gb = p.bin_base + iz * p.n_y + iy;
-    gbin[i] = gb;
-    slot[i] = atomicAdd(&bin_cnt[gb], 1);
+  const int sh = grid_bucket_shift(n);
+  const int64_t tile = (int64_t)blockDim.x * GRID_TILE_PER_THREAD;
+  for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < n; t0 += (int64_t)gridDim.x * tile) {  // block-uniform
+    if (threadIdx.x < GRID_BUCKETS) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int b[GRID_TILE_PER_THREAD], r[GRID_TILE_PER_THREAD];
+    int rs[GRID_TILE_PER_THREAD];
+#pragma unroll
+    for (int k = 0; k < GRID_TILE_PER_THREAD; k++) {
+      const int64_t i = t0 + (int64_t)k * blockDim.x + threadIdx.x;
+      b[k] = -1;
+      rs[k] = -1;
+      if (i < n && (rs[k] = rs_in[i]) >= 0) {
+        b[k] = rs_start[rs[k]] >> sh;
+        r[k] = atomicAdd(&s_cnt[b[k]], 1);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < GRID_BUCKETS) {
+      const int c = s_cnt[threadIdx.x];
+      s_base[threadIdx.x] = c ? bk->base[threadIdx.x] + atomicAdd(&bk->fill[threadIdx.x], c) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GRID_TILE_PER_THREAD; k++) {
+      if (b[k] < 0) continue;
+      const int64_t i = t0 + (int64_t)k * blockDim.x + threadIdx.x;
+      const int4 raw = __ldg(reinterpret_cast<const int4*>(in) + i);
+      rec_b[s_base[b[k]] + r[k]] = make_int4((int32_t)i, raw.x, raw.y, rs[k]);
+    }
+    __syncthreads();
   }
 }
 
-// Each cluster's record {load index, y, z, row-sector} written at its place
-// in its bin (arrival order inside the bin), so that the ordering below
-// reads every record it needs from around its own position.
-__global__ void k_grid_scatter(const tpc_cluster* __restrict__ in, const int32_t* __restrict__ rs_in,
-                               const int32_t* __restrict__ gbin, const int32_t* __restrict__ slot,
-                               const int32_t* __restrict__ bin_start, int4* __restrict__ rec, const Counts* cn) {
+// Level two, in bucket order: the global bin of every record and its
+// (arrival-order) slot in that bin.
+__global__ void k_grid_bin(const int4* __restrict__ rec_b, const RsParams* __restrict__ par,
+                           int32_t* __restrict__ bin_cnt, int32_t* __restrict__ gbin, int32_t* __restrict__ slot,
+                           const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
-  for (int64_t i = gtid(); i < n; i += gstride()) {
-    const int4 raw = __ldg(reinterpret_cast<const int4*>(in) + i);
-    rec[bin_start[gbin[i]] + slot[i]] = make_int4((int32_t)i, raw.x, raw.y, rs_in[i]);
+  for (int64_t p = gtid(); p < n; p += gstride()) {
+    const int4 r = rec_b[p];
+    const int rs = r.w;
+    const RsParams P = load_params(par + rs);
+    const int row = rs % NROW;
+    const int iy = bin_coord(__int_as_float(r.y), -g_row_yhi[row], P.inv_y, P.n_y);
+    const int iz = bin_coord(__int_as_float(r.z), P.z_lo, P.inv_z, P.n_z);
+    const int gb = P.bin_base + iz * P.n_y + iy;
+    gbin[p] = gb;
+    slot[p] = atomicAdd(&bin_cnt[gb], 1);
   }
+}
+
+// Each record written at its place in its bin (arrival order inside the
+// bin), so that the ordering below reads every record it needs from around
+// its own position; the writes of a bucket fall inside its own range.
+__global__ void k_grid_scatter(const int4* __restrict__ rec_b, const int32_t* __restrict__ gbin,
+                               const int32_t* __restrict__ slot, const int32_t* __restrict__ bin_start,
+                               int4* __restrict__ rec, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int64_t n = cn->n;
+  for (int64_t p = gtid(); p < n; p += gstride()) rec[bin_start[gbin[p]] + slot[p]] = rec_b[p];
 }
 
 // Stable order inside each bin: rank = number of bin members with a smaller
 // load index.  Bins hold about two clusters on average (the bin edge is
 // sqrt(2 A / n)); the count is quadratic only in the fullest bin.  The bin
 // of a record is recomputed from its position with the binning arithmetic
-// of k_grid_bin.  Also clears the selection stage's per-cluster arrays
-// (owner keys -- 32- or 64-bit -- to 0, the cluster-to-track map to -1),
-// which are as long as the cluster list.
+// of k_grid_bin.  Also clears the cluster-to-track map (-1), which is as
+// long as the cluster list.
 __global__ void k_grid_order(const int4* __restrict__ rec, const RsParams* __restrict__ par,
                              const int32_t* __restrict__ bin_start, int32_t* __restrict__ perm,
-                             float2* __restrict__ yz, int32_t* __restrict__ rs_of, void* __restrict__ owner,
-                             bool key32, int32_t* __restrict__ cluster_track, const Counts* cn) {
+                             float2* __restrict__ yz, int32_t* __restrict__ rs_of,
+                             int32_t* __restrict__ cluster_track, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t p = gtid(); p < n; p += gstride()) {
@@ -176,8 +246,6 @@ __global__ void k_grid_order(const int4* __restrict__ rec, const RsParams* __res
     perm[dst] = i;
     yz[dst] = make_float2(y, z);
     rs_of[dst] = rs;
-    if (key32) reinterpret_cast<uint32_t*>(owner)[p] = 0u;
-    else reinterpret_cast<uint64_t*>(owner)[p] = 0ull;
     cluster_track[p] = -1;
   }
 }

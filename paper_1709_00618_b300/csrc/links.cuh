@@ -176,15 +176,18 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
   }
 }
 
-// a4: keep the links both ends agree on.
+// a4: keep the links both ends agree on.  Also clears the selection's
+// owner keys (32- or 64-bit), whose space the grid stage used until now.
 __global__ void k_clean(const int32_t* __restrict__ up, const int32_t* __restrict__ dn, int32_t* __restrict__ up_m,
-                        int32_t* __restrict__ dn_m, const Counts* cn) {
+                        int32_t* __restrict__ dn_m, void* __restrict__ owner, bool key32, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t c = gtid(); c < n; c += gstride()) {
     const int u = up[c], d = dn[c];
     up_m[c] = (u >= 0 && __ldg(dn + u) == (int)c) ? u : -1;
     dn_m[c] = (d >= 0 && __ldg(up + d) == (int)c) ? d : -1;
+    if (key32) reinterpret_cast<uint32_t*>(owner)[c] = 0u;
+    else reinterpret_cast<uint64_t*>(owner)[c] = 0ull;
   }
 }
 

@@ -107,19 +107,23 @@ Caps default_caps(int64_t n, int32_t req) {
   Caps c;
   c.n = std::max<int64_t>(n, 1024);
   c.req = std::max<int32_t>(req, 1);
-  c.bins = 2 * c.n + 2048 * c.nrs();
+  // Grid bins: about n/2 in total plus, per row-sector, a few for an empty
+  // one and of order sqrt(n_r dz / 2 wy) for a long drift range; the
+  // default holds the measured events, timeframes and batches with room to
+  // spare, and an overflow (reported, never truncated) is retried with
+  // tpc_reserve.
+  c.bins = 2 * c.n + 16 * c.nrs() + 4096;
   // Tracklets: chains are disjoint and hold >= 3 clusters, so n/3 can never
-  // overflow; measured events and timeframes give 0.06 per cluster, so the
-  // default is n/6 and an overflow (reported, never truncated) is retried
-  // with tpc_reserve.
-  c.tl = c.n / 6 + 1024;
+  // overflow; measured events, timeframes and batches give 0.064 per
+  // cluster, so the default is n/12 and an overflow is retried the same way.
+  c.tl = c.n / 12 + 1024;
   c.tracks = c.tl;  // tracks are a subset of the tracklets
   return c;
 }
 
 // Offsets of every device array inside the arena.
 struct Layout {
-  size_t counts, req_off, req_trk, in, rs_in, gbin, slot, tmp, perm, yz, rs_of, up, dn, up_m, dn_m, tie, flag, fidx, clen,
+  size_t counts, req_off, req_trk, buckets, in, rs_in, gbin, slot, tmp, perm, yz, rs_of, up, dn, up_m, dn_m, tie, flag, fidx, clen,
       cend, owner, cluster_track, track_clusters;
   size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
   size_t bin_cnt, bin_start;
@@ -146,26 +150,33 @@ Layout make_layout(const Caps& c) {
   L.counts = take(sizeof(Counts));
   L.req_off = take(8 * (R + 1));
   L.req_trk = take(8 * R);  // per request: first track, one past its last (tpc_submit_batch)
+  L.buckets = take(sizeof(GridBuckets));
   L.in = take(16 * N);
+  // Arrays that live only in the grid stage share their space with arrays
+  // that are first written after it: rs_in with track_clusters (a8);
+  // gbin | slot with flag | fidx (a5); the sorted records (tmp) with owner
+  // (a7; cleared in a4) | clen | cend (a5).
   L.rs_in = take(4 * N);
-  L.gbin = take(4 * N);
-  L.slot = take(4 * N);
+  L.track_clusters = L.rs_in;
+  L.gbin = take(8 * (N + 1));
+  L.slot = L.gbin + 4 * (N + 1);
+  L.flag = L.gbin;
+  L.fidx = L.slot;
   L.tmp = take(16 * N);  // records of the grid's counting sort
+  L.owner = L.tmp;
+  L.clen = L.tmp + 8 * N;
+  L.cend = L.tmp + 12 * N;
   L.perm = take(4 * N);
   L.yz = take(8 * N);
   L.rs_of = take(4 * N);
+  // up, dn, up_m, dn_m are contiguous: during the grid stage, before the
+  // links exist, the 16 N bytes from up on hold the bucketed records
   L.up = take(4 * N);
   L.dn = take(4 * N);
   L.up_m = take(4 * N);
   L.dn_m = take(4 * N);
   L.tie = take(N);
-  L.flag = take(4 * (N + 1));
-  L.fidx = take(4 * (N + 1));
-  L.clen = take(4 * N);
-  L.cend = take(4 * N);
-  L.owner = take(8 * N);
   L.cluster_track = take(4 * N);
-  L.track_clusters = take(4 * N);
   L.rs_cnt = take(4 * (NRS + 1));
   L.rs_start = take(4 * (NRS + 1));
   L.zmin = take(4 * NRS);
@@ -573,17 +584,21 @@ void enqueue_find(tpc_ctx* ctx) {
   LenSrc lrs{&cn->n_rs, 0, 0};
   scan(ctx, rs_cnt, ctx->ptr<int32_t>(L.rs_start), lrs, nullptr, C.nrs());
   scan(ctx, nbins, bin_base, lrs, nullptr, C.nrs());
-  k_grid_finish_params<<<gR, bc, 0, s>>>(ctx->ptr<RsParams>(L.par), bin_base, cn, C.bins, bin_cnt);
-  k_grid_bin<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.rs_in), ctx->ptr<RsParams>(L.par),
-                               bin_cnt, ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), cn);
+  GridBuckets* bk = ctx->ptr<GridBuckets>(L.buckets);
+  int4* rec_b = ctx->ptr<int4>(L.up);  // the link arrays' space, free until a3
+  k_grid_finish_params<<<gR, bc, 0, s>>>(ctx->ptr<RsParams>(L.par), bin_base, ctx->ptr<int32_t>(L.rs_start), cn,
+                                         C.bins, bin_cnt, bk);
+  k_grid_bucket<<<grid_for(ctx, (C.n + GRID_TILE_PER_THREAD - 1) / GRID_TILE_PER_THREAD, bc), bc, 0, s>>>(
+      ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.rs_in), ctx->ptr<int32_t>(L.rs_start), bk, rec_b, cn);
+  k_grid_bin<<<gN, bc, 0, s>>>(rec_b, ctx->ptr<RsParams>(L.par), bin_cnt, ctx->ptr<int32_t>(L.gbin),
+                               ctx->ptr<int32_t>(L.slot), cn);
   LenSrc lb{&cn->n_bins, 0, 0};
   scan(ctx, bin_cnt, bin_start, lb, nullptr);
-  k_grid_scatter<<<gN, bc, 0, s>>>(ctx->ptr<tpc_cluster>(L.in), ctx->ptr<int32_t>(L.rs_in),
-                                   ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
+  k_grid_scatter<<<gN, bc, 0, s>>>(rec_b, ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
                                    ctx->ptr<int4>(L.tmp), cn);
   k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<int4>(L.tmp), ctx->ptr<RsParams>(L.par), bin_start,
                                  ctx->ptr<int32_t>(L.perm), ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
-                                 ctx->ptr<void>(L.owner), key32(ctx), ctx->ptr<int32_t>(L.cluster_track), cn);
+                                 ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(1);
   // a3 neighbours
   k_neighbours<<<grid_for(ctx, C.n, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
@@ -592,7 +607,7 @@ void enqueue_find(tpc_ctx* ctx) {
   ctx->mark(2);
   // a4 + a5
   k_clean<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn), ctx->ptr<int32_t>(L.up_m),
-                            ctx->ptr<int32_t>(L.dn_m), cn);
+                            ctx->ptr<int32_t>(L.dn_m), ctx->ptr<void>(L.owner), key32(ctx), cn);
   k_chains<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up_m), ctx->ptr<int32_t>(L.dn_m), ctx->kc, ctx->ptr<int32_t>(L.flag),
                              ctx->ptr<int32_t>(L.clen), ctx->ptr<int32_t>(L.cend), cn);
   scan(ctx, ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), LenSrc{&cn->n32, 0, 0}, nullptr);
