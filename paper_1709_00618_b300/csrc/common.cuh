@@ -63,7 +63,7 @@ struct Counts {
   unsigned long long n_cand;    // candidate clusters examined by the gated pick-up
   unsigned long long n_prop64;  // propagations done with the FP64 covariance
   int32_t trace_n;              // trace records written
-  int32_t pad3;
+  int32_t n_starts;             // chain starts (clusters with a kept upward link and none downward)
   unsigned long long pad2[2];
   // the same counters per Kalman kernel (PH_*): {prop, upd32, upd64, cand, prop64}
   unsigned long long phase_work[6][5];

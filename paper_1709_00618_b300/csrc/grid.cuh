@@ -99,16 +99,16 @@ __global__ void k_grid_params(const int32_t* __restrict__ cnt, const uint32_t* _
 // bucket_shift, so a bucket holds about 2^bucket_shift clusters (at most
 // GRID_BUCKETS buckets).  Level two counts bins and scatters inside one
 // bucket at a time, so its random accesses stay in L2.
-constexpr int GRID_BUCKETS = 64;
+constexpr int GRID_BUCKETS = 512;
 struct GridBuckets {
   int32_t base[GRID_BUCKETS];  // first sorted position of each bucket
   int32_t fill[GRID_BUCKETS];  // records placed so far
 };
 
-// Bucket exponent for n clusters: 2^21 clusters (32 MB of records), or more
+// Bucket exponent for n clusters: 2^18 clusters (4 MB of records), or more
 // so that at most GRID_BUCKETS buckets are needed.
 __host__ __device__ inline int grid_bucket_shift(int64_t n) {
-  int sh = 21;
+  int sh = 18;
   while ((n >> sh) >= GRID_BUCKETS) sh++;
   return sh;
 }
@@ -127,7 +127,7 @@ __global__ void k_grid_finish_params(RsParams* __restrict__ par, const int32_t* 
     return;
   }
   const int sh = grid_bucket_shift(cn->n);
-  if (gtid() < GRID_BUCKETS) bk->fill[gtid()] = 0;
+  for (int64_t q = gtid(); q < GRID_BUCKETS; q += gstride()) bk->fill[q] = 0;
   for (int64_t rs = gtid(); rs < nrs; rs += gstride()) {
     par[rs].bin_base = bin_base[rs];
     const int b = rs_start[rs] >> sh;
@@ -157,7 +157,7 @@ __global__ void k_grid_bucket(const tpc_cluster* __restrict__ in, const int32_t*
   const int sh = grid_bucket_shift(n);
   const int64_t tile = (int64_t)blockDim.x * GRID_TILE_PER_THREAD;
   for (int64_t t0 = (int64_t)blockIdx.x * tile; t0 < n; t0 += (int64_t)gridDim.x * tile) {  // block-uniform
-    if (threadIdx.x < GRID_BUCKETS) s_cnt[threadIdx.x] = 0;
+    for (int b = threadIdx.x; b < GRID_BUCKETS; b += blockDim.x) s_cnt[b] = 0;
     __syncthreads();
     int b[GRID_TILE_PER_THREAD], r[GRID_TILE_PER_THREAD];
     int rs[GRID_TILE_PER_THREAD];
@@ -172,9 +172,9 @@ __global__ void k_grid_bucket(const tpc_cluster* __restrict__ in, const int32_t*
       }
     }
     __syncthreads();
-    if (threadIdx.x < GRID_BUCKETS) {
-      const int c = s_cnt[threadIdx.x];
-      s_base[threadIdx.x] = c ? bk->base[threadIdx.x] + atomicAdd(&bk->fill[threadIdx.x], c) : 0;
+    for (int q = threadIdx.x; q < GRID_BUCKETS; q += blockDim.x) {
+      const int c = s_cnt[q];
+      s_base[q] = c ? bk->base[q] + atomicAdd(&bk->fill[q], c) : 0;
     }
     __syncthreads();
 #pragma unroll

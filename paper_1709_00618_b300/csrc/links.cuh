@@ -176,65 +176,75 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
   }
 }
 
-// a4: keep the links both ends agree on.  Also clears the selection's
+// a4: keep the links both ends agree on, and flag the chain starts (a kept
+// upward link and no kept downward link).  Also clears the selection's
 // owner keys (32- or 64-bit), whose space the grid stage used until now.
 __global__ void k_clean(const int32_t* __restrict__ up, const int32_t* __restrict__ dn, int32_t* __restrict__ up_m,
-                        int32_t* __restrict__ dn_m, void* __restrict__ owner, bool key32, const Counts* cn) {
+                        int32_t* __restrict__ dn_m, int32_t* __restrict__ start, void* __restrict__ owner,
+                        bool key32, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t c = gtid(); c < n; c += gstride()) {
     const int u = up[c], d = dn[c];
-    up_m[c] = (u >= 0 && __ldg(dn + u) == (int)c) ? u : -1;
-    dn_m[c] = (d >= 0 && __ldg(up + d) == (int)c) ? d : -1;
+    const int um = (u >= 0 && __ldg(dn + u) == (int)c) ? u : -1;
+    const int dm = (d >= 0 && __ldg(up + d) == (int)c) ? d : -1;
+    up_m[c] = um;
+    dn_m[c] = dm;
+    start[c] = um >= 0 && dm < 0;
     if (key32) reinterpret_cast<uint32_t*>(owner)[c] = 0u;
     else reinterpret_cast<uint64_t*>(owner)[c] = 0ull;
   }
 }
 
-// a5: a cluster with a kept upward link and no kept downward link starts a
-// chain; walk it over the kept links (one dependent load per cluster) and
-// flag chains of at least min_chain clusters.
-__global__ void k_chains(const int32_t* __restrict__ up_m, const int32_t* __restrict__ dn_m, KConst kc,
+// The chain starts in sorted order (start[] scanned into sidx[]).
+__global__ void k_start_list(const int32_t* __restrict__ start, const int32_t* __restrict__ sidx,
+                             int32_t* __restrict__ starts, const Counts* cn) {
+  if (fatal(cn)) return;
+  const int64_t n = cn->n;
+  for (int64_t c = gtid(); c < n; c += gstride())
+    if (start[c]) starts[sidx[c]] = (int32_t)c;
+}
+
+// a5: walk every chain from its start over the kept links (one dependent
+// load per cluster), one thread per start so that every lane walks, and
+// flag the chains of at least min_chain clusters (indexed like starts[]).
+__global__ void k_chains(const int32_t* __restrict__ up_m, const int32_t* __restrict__ starts, KConst kc,
                          int32_t* __restrict__ flag, int32_t* __restrict__ clen, int32_t* __restrict__ cend,
                          const Counts* cn) {
   if (fatal(cn)) return;
-  const int64_t n = cn->n;
-  for (int64_t c = gtid(); c < n; c += gstride()) {
-    int f = 0;
-    if (up_m[c] >= 0 && dn_m[c] < 0) {
-      int len = 1, k = (int)c;
-      for (int uk = __ldg(up_m + k); uk >= 0; uk = __ldg(up_m + k)) {
-        k = uk;
-        len++;
-      }
-      if (len >= kc.min_chain) {
-        f = 1;
-        clen[c] = len;
-        cend[c] = k;
-      }
+  const int32_t S = cn->n_starts;
+  for (int64_t j = gtid(); j < S; j += gstride()) {
+    int len = 1, k = starts[j];
+    for (int uk = __ldg(up_m + k); uk >= 0; uk = __ldg(up_m + k)) {
+      k = uk;
+      len++;
     }
-    flag[c] = f;
+    flag[j] = len >= kc.min_chain;
+    clen[j] = len;
+    cend[j] = k;
   }
 }
 
+// Tracklets in the sorted order of their start cluster (idx: flag scanned).
 __global__ void k_tracklet_compact(const int32_t* __restrict__ flag, const int32_t* __restrict__ idx,
-                                   const int32_t* __restrict__ clen, const int32_t* __restrict__ cend,
-                                   int32_t* __restrict__ tl_start, int32_t* __restrict__ tl_len,
-                                   int32_t* __restrict__ tl_end, Counts* cn, int64_t tl_cap) {
+                                   const int32_t* __restrict__ starts, const int32_t* __restrict__ clen,
+                                   const int32_t* __restrict__ cend, int32_t* __restrict__ tl_start,
+                                   int32_t* __restrict__ tl_len, int32_t* __restrict__ tl_end, Counts* cn,
+                                   int64_t tl_cap) {
   if (fatal(cn)) return;
-  const int64_t n = cn->n;
-  int32_t total = idx[n];
+  const int32_t S = cn->n_starts;
+  int32_t total = idx[S];
   if (gtid() == 0) cn->n_tracklets = total;
   if (total > tl_cap) {
     if (gtid() == 0) atomicOr(&cn->status, ST_EOVERFLOW);
     return;
   }
-  for (int64_t c = gtid(); c < n; c += gstride()) {
-    if (!flag[c]) continue;
-    int t = idx[c];
-    tl_start[t] = (int32_t)c;
-    tl_len[t] = clen[c];
-    tl_end[t] = cend[c];
+  for (int64_t j = gtid(); j < S; j += gstride()) {
+    if (!flag[j]) continue;
+    int t = idx[j];
+    tl_start[t] = starts[j];
+    tl_len[t] = clen[j];
+    tl_end[t] = cend[j];
   }
 }
 

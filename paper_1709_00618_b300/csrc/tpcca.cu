@@ -123,7 +123,7 @@ Caps default_caps(int64_t n, int32_t req) {
 
 // Offsets of every device array inside the arena.
 struct Layout {
-  size_t counts, req_off, req_trk, buckets, in, rs_in, gbin, slot, tmp, perm, yz, rs_of, up, dn, up_m, dn_m, tie, flag, fidx, clen,
+  size_t counts, req_off, req_trk, buckets, starts, in, rs_in, gbin, slot, tmp, perm, yz, rs_of, up, dn, up_m, dn_m, tie, flag, fidx, clen,
       cend, owner, cluster_track, track_clusters;
   size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
   size_t bin_cnt, bin_start;
@@ -176,6 +176,7 @@ Layout make_layout(const Caps& c) {
   L.up_m = take(4 * N);
   L.dn_m = take(4 * N);
   L.tie = take(N);
+  L.starts = take(4 * (N / 2 + 1));  // chain starts: chains are disjoint and hold >= 2 clusters
   L.cluster_track = take(4 * N);
   L.rs_cnt = take(4 * (NRS + 1));
   L.rs_start = take(4 * (NRS + 1));
@@ -606,12 +607,20 @@ void enqueue_find(tpc_ctx* ctx) {
                                   ctx->ptr<uint8_t>(L.tie), cn);
   ctx->mark(2);
   // a4 + a5
+  // chain starts flagged in k_clean, listed in sorted order; one walk per
+  // start; the kept chains compacted in the same order (flag and fidx hold
+  // the per-cluster start flags, then the per-start keep flags)
+  int32_t* starts = ctx->ptr<int32_t>(L.starts);
+  const int gS = grid_for(ctx, C.n / 2 + 1, bc);
   k_clean<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn), ctx->ptr<int32_t>(L.up_m),
-                            ctx->ptr<int32_t>(L.dn_m), ctx->ptr<void>(L.owner), key32(ctx), cn);
-  k_chains<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.up_m), ctx->ptr<int32_t>(L.dn_m), ctx->kc, ctx->ptr<int32_t>(L.flag),
+                            ctx->ptr<int32_t>(L.dn_m), ctx->ptr<int32_t>(L.flag), ctx->ptr<void>(L.owner), key32(ctx),
+                            cn);
+  scan(ctx, ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), LenSrc{&cn->n32, 0, 0}, &cn->n_starts);
+  k_start_list<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), starts, cn);
+  k_chains<<<gS, bc, 0, s>>>(ctx->ptr<int32_t>(L.up_m), starts, ctx->kc, ctx->ptr<int32_t>(L.flag),
                              ctx->ptr<int32_t>(L.clen), ctx->ptr<int32_t>(L.cend), cn);
-  scan(ctx, ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), LenSrc{&cn->n32, 0, 0}, nullptr);
-  k_tracklet_compact<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx),
+  scan(ctx, ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), LenSrc{&cn->n_starts, 0, 0}, nullptr);
+  k_tracklet_compact<<<gS, bc, 0, s>>>(ctx->ptr<int32_t>(L.flag), ctx->ptr<int32_t>(L.fidx), starts,
                                        ctx->ptr<int32_t>(L.clen), ctx->ptr<int32_t>(L.cend),
                                        ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len),
                                        ctx->ptr<int32_t>(L.tl_end), cn, C.tl);
@@ -910,13 +919,48 @@ size_t tpc_arena_bytes(int64_t n_clusters, int32_t n_requests) {
   return make_layout(default_caps(n_clusters, n_requests)).total;
 }
 
-int tpc_reserve(tpc_ctx* ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets) {
-  if (!ctx || n_clusters < 0 || n_requests < 0 || n_bins < 0 || n_tracklets < 0) return TPC_EINVAL;
+size_t tpc_arena_bytes_for(int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets) {
+  Caps c = default_caps(n_clusters, n_requests);
+  if (n_bins > 0) c.bins = std::max(c.bins, n_bins);
+  if (n_tracklets > 0) c.tl = std::max(c.tl, n_tracklets);
+  c.tracks = std::max(c.tracks, c.tl);
+  return make_layout(c).total;
+}
+
+namespace {
+Caps reserve_caps(const tpc_ctx* ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets) {
   Caps want = default_caps(std::max<int64_t>(n_clusters, ctx->caps.n), std::max(n_requests, ctx->caps.req));
   if (n_bins) want.bins = n_bins;
   if (n_tracklets) want.tl = n_tracklets;
   want.tracks = std::max(want.tracks, want.tl);
-  return do_reserve(ctx, want);
+  return want;
+}
+}  // namespace
+
+int tpc_reserve(tpc_ctx* ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets) {
+  if (!ctx || n_clusters < 0 || n_requests < 0 || n_bins < 0 || n_tracklets < 0) return TPC_EINVAL;
+  return do_reserve(ctx, reserve_caps(ctx, n_clusters, n_requests, n_bins, n_tracklets));
+}
+
+int tpc_reserve_bytes(tpc_ctx* ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets,
+                      size_t* bytes) {
+  if (!ctx || !bytes || n_clusters < 0 || n_requests < 0 || n_bins < 0 || n_tracklets < 0) return TPC_EINVAL;
+  const Caps want = reserve_caps(ctx, n_clusters, n_requests, n_bins, n_tracklets);
+  const Caps& c = ctx->caps;
+  const bool grow = want.n > c.n || want.req > c.req || want.bins > c.bins || want.tl > c.tl ||
+                    want.tracks > c.tracks || ctx->arena == nullptr;
+  if (!grow) {
+    *bytes = ctx->arena_bytes;
+    return TPC_OK;
+  }
+  Caps m = c;  // do_reserve takes the larger of the current and the wanted capacity
+  m.n = std::max(c.n, want.n);
+  m.req = std::max(c.req, want.req);
+  m.bins = std::max(c.bins, want.bins);
+  m.tl = std::max(c.tl, want.tl);
+  m.tracks = std::max(c.tracks, want.tracks);
+  *bytes = make_layout(m).total;
+  return TPC_OK;
 }
 
 int tpc_load_clusters(tpc_ctx* ctx, const tpc_cluster* c, int64_t n, int on_device) {
