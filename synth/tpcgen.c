@@ -139,11 +139,11 @@ static void sample_track(const gen_params *p, int64_t i, int secondary, double t
  * (from the vertex to the point of the circle farthest from the beam axis)
  * and, for a looper, inside legs-1 further half-turns (no energy loss: the
  * particle stays on its helix).  The truth flags hold the leg (0: the first)
- * in bits 1 and up.  If out != NULL the clusters (and truth) are written;
- * returns the count.
+ * in bits 1 and up.  The first `cap` clusters (and truth) are written to out
+ * (NULL: none); returns the count, which may exceed cap.
  */
 static int64_t track_hits(const gen_params *p, const track_t *tr, int64_t label, gen_cluster *out,
-                          gen_truth *truth) {
+                          gen_truth *truth, int64_t cap) {
   const double K = 0.299792458e-3 * p->bz_kg;
   double kappa = -K * tr->q / tr->pt; /* signed curvature dphi/ds */
   double R = 1.0 / fabs(kappa);
@@ -204,7 +204,7 @@ static int64_t track_hits(const gen_params *p, const track_t *tr, int64_t label,
           tgl = z >= 0.0 ? -tr->t : tr->t;
           if (zs >= tf_zmax) continue; /* arrives after the end of the timeframe */
         }
-        if (out) {
+        if (out && n < cap) {
           gen_cluster *c = &out[n];
           c->y = (float)(yloc + p->sigma_y * gauss(key, 8 * ctr + 2));
           c->z = (float)(zs + p->sigma_z * gauss(key, 8 * ctr + 3));
@@ -278,14 +278,53 @@ int gen_run(const gen_params *p, gen_cluster **clusters, gen_truth **truth, int6
   int64_t ntr = 0;
   track_t *tracks = NULL;
   if (build_tracks(p, &tracks, &ntr) != 0) return -1;
-  /* 2. count, scan, fill (deterministic for any thread count) */
-  int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(ntr + 1));
-  if (!off) { free(tracks); return -1; }
-#pragma omp parallel for schedule(dynamic, 64) num_threads(p->n_threads > 0 ? p->n_threads : 1)
-  for (int64_t i = 0; i < ntr; i++) off[i + 1] = track_hits(p, &tracks[i], i, NULL, NULL);
-  off[0] = 0;
-  for (int64_t i = 0; i < ntr; i++) off[i + 1] += off[i];
-  int64_t nhit = off[ntr];
+  /* 2. the tracks' clusters, one pass: fixed chunks of tracks, each into
+     its own growing buffer, then concatenated in track order (the output
+     does not depend on the thread count) */
+  const int64_t CH = 1024;
+  const int64_t nchunks = (ntr + CH - 1) / CH;
+  typedef struct {
+    gen_cluster *c;
+    gen_truth *t;
+    int64_t n, cap;
+    int fail;
+  } chunk_buf;
+  chunk_buf *cb = (chunk_buf *)calloc((size_t)(nchunks > 0 ? nchunks : 1), sizeof(chunk_buf));
+  if (!cb) { free(tracks); return -1; }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(p->n_threads > 0 ? p->n_threads : 1)
+  for (int64_t k = 0; k < nchunks; k++) {
+    chunk_buf *b = &cb[k];
+    const int64_t i1 = (k + 1) * CH < ntr ? (k + 1) * CH : ntr;
+    for (int64_t i = k * CH; i < i1 && !b->fail; i++) {
+      for (;;) {
+        const int64_t room = b->cap - b->n;
+        const int64_t got = track_hits(p, &tracks[i], i, b->c ? b->c + b->n : NULL,
+                                       b->t ? b->t + b->n : NULL, room);
+        if (got <= room) {
+          b->n += got;
+          break;
+        }
+        int64_t nc = 2 * b->cap > b->n + got + 256 ? 2 * b->cap : b->n + got + 256;
+        gen_cluster *c2 = (gen_cluster *)realloc(b->c, sizeof(gen_cluster) * (size_t)nc);
+        gen_truth *t2 = NULL;
+        if (c2) b->c = c2;
+        if (truth) {
+          t2 = (gen_truth *)realloc(b->t, sizeof(gen_truth) * (size_t)nc);
+          if (t2) b->t = t2;
+        }
+        if (!c2 || (truth && !t2)) {
+          b->fail = 1;
+          break;
+        }
+        b->cap = nc;
+      }
+    }
+  }
+  int64_t nhit = 0, bad = 0;
+  for (int64_t k = 0; k < nchunks; k++) {
+    nhit += cb[k].n;
+    bad |= cb[k].fail;
+  }
   int64_t nnoise = (int64_t)floor(p->noise_frac * (double)nhit + 0.5);
   int nsel = 0;
   int selected[36];
@@ -293,11 +332,32 @@ int gen_run(const gen_params *p, gen_cluster **clusters, gen_truth **truth, int6
     if ((p->sector_mask >> s) & 1ull) selected[nsel++] = s;
   if (nsel == 0) nnoise = 0;
   int64_t ntot = nhit + nnoise;
-  gen_cluster *out = (gen_cluster *)malloc(sizeof(gen_cluster) * (size_t)(ntot > 0 ? ntot : 1));
-  gen_truth *tru = truth ? (gen_truth *)malloc(sizeof(gen_truth) * (size_t)(ntot > 0 ? ntot : 1)) : NULL;
-  if (!out || (truth && !tru)) { free(out); free(tru); free(off); free(tracks); return -1; }
-#pragma omp parallel for schedule(dynamic, 64) num_threads(p->n_threads > 0 ? p->n_threads : 1)
-  for (int64_t i = 0; i < ntr; i++) track_hits(p, &tracks[i], i, out + off[i], tru ? tru + off[i] : NULL);
+  gen_cluster *out = bad ? NULL : (gen_cluster *)malloc(sizeof(gen_cluster) * (size_t)(ntot > 0 ? ntot : 1));
+  gen_truth *tru = truth && !bad ? (gen_truth *)malloc(sizeof(gen_truth) * (size_t)(ntot > 0 ? ntot : 1)) : NULL;
+  if (!out || (truth && !tru)) {
+    free(out); free(tru);
+    for (int64_t k = 0; k < nchunks; k++) { free(cb[k].c); free(cb[k].t); }
+    free(cb); free(tracks);
+    return -1;
+  }
+  int64_t *coff = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nchunks + 1));
+  if (!coff) {
+    free(out); free(tru);
+    for (int64_t k = 0; k < nchunks; k++) { free(cb[k].c); free(cb[k].t); }
+    free(cb); free(tracks);
+    return -1;
+  }
+  coff[0] = 0;
+  for (int64_t k = 0; k < nchunks; k++) coff[k + 1] = coff[k] + cb[k].n;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(p->n_threads > 0 ? p->n_threads : 1)
+  for (int64_t k = 0; k < nchunks; k++) {
+    if (cb[k].n) memcpy(out + coff[k], cb[k].c, sizeof(gen_cluster) * (size_t)cb[k].n);
+    if (tru && cb[k].n) memcpy(tru + coff[k], cb[k].t, sizeof(gen_truth) * (size_t)cb[k].n);
+    free(cb[k].c);
+    free(cb[k].t);
+  }
+  free(coff);
+  free(cb);
   /* 3. uniform noise clusters in the selected sectors */
   double tf_zmax = p->vdrift * p->tf_length_us;
   for (int64_t k = 0; k < nnoise; k++) {
@@ -323,7 +383,6 @@ int gen_run(const gen_params *p, gen_cluster **clusters, gen_truth **truth, int6
       g->z = z;
     }
   }
-  free(off);
   free(tracks);
   *clusters = out;
   if (truth) *truth = tru;
