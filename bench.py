@@ -626,29 +626,78 @@ def batching_leg(local, flush, n_requests=256, reps=3):
     return out
 
 
-def serving_leg(local, n_timeframes=24, pool=4, loads=(0.5, 0.8, 1.0), headline=0.8, slots=4,
-                budget_gb=120.0, ring=6, seed=4):
+def _generate_pool(seed, n_distinct, min_ms, max_ms, out_dir):
+    """Child process: the serving pool's timeframes, saved as .npy files."""
+    import numpy as np
+
+    import synth
+    rng = np.random.default_rng(seed)
+    lengths = [float(rng.uniform(min_ms, max_ms)) for _ in range(n_distinct)]
+    for i, ms in enumerate(lengths):
+        cl = synth.timeframe(seed=seed * 1000 + i, length_ms=ms).clusters
+        np.save(os.path.join(out_dir, f"tf{i:03d}.npy"), cl)
+        with open(os.path.join(out_dir, f"tf{i:03d}.ms"), "w") as f:
+            f.write(repr(ms))
+
+
+class ServingPool:
+    """Distinct seeded timeframes (lengths uniform in [min_ms, max_ms], the
+    config-5 generator) made by a spawned child process while the bench's
+    GPU legs run; load() waits for them."""
+
+    def __init__(self, seed=4, n_distinct=16, min_ms=1.0, max_ms=20.0):
+        import multiprocessing as mp
+        import tempfile
+        self.seed, self.n = seed, n_distinct
+        base = "/dev/shm" if os.path.isdir("/dev/shm") else None
+        self.dir = tempfile.mkdtemp(prefix="tpc_pool_", dir=base)
+        self.proc = mp.get_context("spawn").Process(target=_generate_pool,
+                                                    args=(seed, n_distinct, min_ms, max_ms, self.dir))
+        self.proc.start()
+        self.t0 = time.perf_counter()
+
+    def load(self):
+        """[(clusters, length_ms)] in pool order; removes the files."""
+        import shutil
+
+        import numpy as np
+        self.proc.join()
+        if self.proc.exitcode != 0:
+            raise RuntimeError("timeframe pool generation failed")
+        gen_s = time.perf_counter() - self.t0
+        out = []
+        for i in range(self.n):
+            cl = np.load(os.path.join(self.dir, f"tf{i:03d}.npy"))
+            with open(os.path.join(self.dir, f"tf{i:03d}.ms")) as f:
+                out.append((cl, float(f.read())))
+        shutil.rmtree(self.dir, ignore_errors=True)
+        return out, gen_s
+
+
+def serving_leg(local, pool, n_arrivals=500, loads=(0.5, 0.8, 1.0), headline=0.8, other_arrivals=64, slots=6,
+                budget_gb=120.0, ring=8, seed=4):
     """Poisson stream of continuous-readout timeframes (lengths uniform in
     1-20 ms at 50 kHz) through the continuous-batching server, against
     sequential plain processing of the same stream, at several offered
     loads (arrival rate = load x the sequential plain capacity, measured
-    first).  Timeframes are drawn from a pool of distinct seeded timeframes;
-    inputs and result buffers are page-locked host memory in both arms
-    (`ring` result buffers for the server: a request waits for a free one).
-    Latency: arrival to results (tracks and cluster assignment) in host
-    memory."""
+    first).  Arrivals replay a pool of distinct seeded timeframes (a
+    ServingPool); the headline load takes n_arrivals arrivals, the others
+    other_arrivals.  Inputs and result buffers are page-locked host memory in
+    both arms (`ring` result buffers for the server: a request waits for a
+    free one).  Latency: arrival to results (tracks and cluster assignment)
+    in host memory."""
     import numpy as np
     import torch
 
     import paper_1709_00618_b300 as tpc
     import synth
-    tfs = synth.timeframe_stream(seed=seed, n_distinct=pool)
-    pinned = [torch.from_numpy(t.clusters.view(np.uint8)).pin_memory() for t in tfs]
+    tfs, gen_s = pool.load()
+    pinned = [torch.from_numpy(cl.view(np.uint8)).pin_memory() for cl, _ in tfs]
+    lengths = [ms for _, ms in tfs]
+    del tfs
     host = [p.numpy().view(synth.CLUSTER_DTYPE) for p in pinned]
     sizes = [len(h) for h in host]
-    rng = np.random.default_rng(seed + 1)
-    order = rng.integers(0, pool, size=n_timeframes)
-    gaps = rng.exponential(1.0, size=n_timeframes)  # unit-rate gaps, scaled per load
+    npool = len(host)
 
     # sequential plain service time of each pool entry (after one warm run)
     trk = tpc.Tracker(device=local)
@@ -657,42 +706,37 @@ def serving_leg(local, n_timeframes=24, pool=4, loads=(0.5, 0.8, 1.0), headline=
     big_ct = torch.zeros(max(sizes), dtype=torch.int32).pin_memory()
     tr_buf = torch.zeros(max(sizes) // 10 + 1, 128, dtype=torch.uint8).pin_memory()
     for h in host:
-        trk.load(h).find().fit()
-        tr, _ = trk.get_into(tr_buf, big_ct[:len(h)])
+        tr, _ = trk.track_into(h, tr_buf, big_ct[:len(h)])
         n_tracks.append(len(tr))
         t0 = time.perf_counter()
-        trk.load(h).find().fit()
-        trk.get_into(tr_buf, big_ct[:len(h)])
+        trk.track_into(h, tr_buf, big_ct[:len(h)])
         serv.append(time.perf_counter() - t0)
-    mean_s = float(np.mean([serv[i] for i in order]))
-    total = int(sum(sizes[i] for i in order))
     cap = int(1.25 * max(n_tracks)) + 1024
     bufs = [(torch.zeros(cap, 128, dtype=torch.uint8).pin_memory(),
              torch.zeros(max(sizes), dtype=torch.int32).pin_memory()) for _ in range(ring)]
 
-    def plain_arm(arrivals):
+    def plain_arm(order, arrivals):
         lat = []
         t_start = time.perf_counter()
-        for k in range(n_timeframes):
+        for k in range(len(order)):
             now = time.perf_counter() - t_start
             if now < arrivals[k]:
                 time.sleep(arrivals[k] - now)
             h = host[order[k]]
-            trk.load(h).find().fit()
-            trk.get_into(tr_buf, big_ct[:len(h)])
+            trk.track_into(h, tr_buf, big_ct[:len(h)])
             lat.append(time.perf_counter() - t_start - arrivals[k])
         return lat, time.perf_counter() - t_start
 
-    def served_arm(arrivals):
+    def served_arm(order, arrivals):
         # latency = (submission - arrival) + the server's submission-to-results time
         free = list(range(ring))
         srv = tpc.Server(device=local, max_slots=slots, hbm_budget=int(budget_gb * 2**30))
         lat, late, owner, pending = [], {}, {}, set()
         t_start = time.perf_counter()
-        k = 0
-        while k < n_timeframes or pending:
+        k, m = 0, len(order)
+        while k < m or pending:
             now = time.perf_counter() - t_start
-            while k < n_timeframes and arrivals[k] <= now and free:
+            while k < m and arrivals[k] <= now and free:
                 b = free.pop()
                 h = host[order[k]]
                 if srv.submit(k, pinned[order[k]], tracks_out=bufs[b][0], cluster_track_out=bufs[b][1][:len(h)]):
@@ -715,28 +759,35 @@ def serving_leg(local, n_timeframes=24, pool=4, loads=(0.5, 0.8, 1.0), headline=
         return lat, span, st
 
     by_load = {}
-    for load in loads:
-        arrivals = np.cumsum(gaps) * (mean_s / load)
+    for li, load in enumerate(loads):
+        m = n_arrivals if load == headline else other_arrivals
+        rng = np.random.default_rng(seed + 1 + li)
+        order = rng.integers(0, npool, size=m)
+        mean_s = float(np.mean([serv[i] for i in order]))
+        arrivals = np.cumsum(rng.exponential(1.0, size=m)) * (mean_s / load)
         arrivals -= arrivals[0]
-        lat_p, span_p = plain_arm(arrivals)
-        lat_s, span_s, st = served_arm(arrivals)
+        total = int(sum(sizes[i] for i in order))
+        lat_p, span_p = plain_arm(order, arrivals)
+        lat_s, span_s, st = served_arm(order, arrivals)
         by_load[str(load)] = {
-            "arrival_rate_hz": load / mean_s,
+            "arrivals": m, "arrival_rate_hz": load / mean_s, "clusters": total,
             "plain": {"latency_ms_p50": 1e3 * _pct(lat_p, 50), "latency_ms_p99": 1e3 * _pct(lat_p, 99),
-                      "clusters_per_s": total / span_p},
+                      "clusters_per_s": total / span_p, "samples": len(lat_p)},
             "served": {"latency_ms_p50": 1e3 * _pct(lat_s, 50), "latency_ms_p99": 1e3 * _pct(lat_s, 99),
                        "clusters_per_s": total / span_s, "peak_running": st["peak_running"],
-                       "arena_gb": st["arena_bytes"] / 2**30}}
+                       "arena_gb": st["arena_bytes"] / 2**30, "samples": len(lat_s)}}
     trk.close()
     head = by_load[str(headline)]
-    return {"workload": f"Poisson stream of {n_timeframes} timeframes drawn from {pool} distinct seeded "
-                        f"timeframes of 1-20 ms at 50 kHz (seed {seed}); offered loads {list(loads)} of the "
-                        f"sequential plain capacity (headline {headline}); {slots} slots, {budget_gb:g} GB HBM "
-                        f"budget; page-locked inputs and outputs in both arms",
-            "timeframe_clusters": sizes, "timeframe_ms": [round(t.params.tf_length_us / 1e3, 3) for t in tfs],
+    return {"workload": f"Poisson stream of timeframes drawn from {npool} distinct seeded timeframes of 1-20 ms "
+                        f"at 50 kHz (seed {seed}); {n_arrivals} arrivals at the headline load {headline} of the "
+                        f"sequential plain capacity, {other_arrivals} at the other loads {list(loads)}; {slots} "
+                        f"slots, {budget_gb:g} GB HBM budget; page-locked inputs and outputs in both arms",
+            "deviation": f"config 5 runs 2000 timeframes; this replays {npool} distinct ones {n_arrivals} times at "
+                         f"the headline load",
+            "pool_generation_s": gen_s,
+            "timeframe_clusters": sizes, "timeframe_ms": [round(v, 3) for v in lengths],
             "timeframe_tracks": n_tracks, "service_ms_plain": [round(1e3 * v, 2) for v in serv],
-            "clusters": total, "headline_load": headline, "plain": head["plain"], "served": head["served"],
-            "by_load": by_load}
+            "headline_load": headline, "plain": head["plain"], "served": head["served"], "by_load": by_load}
 
 
 CONFIG3 = "10 ms continuous-readout timeframe at 50 kHz, 36 sectors, drift-time z, seed 2"
@@ -917,8 +968,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="main line only (no central-event line, size sweep or server stream)")
-    ap.add_argument("--serving-timeframes", type=int, default=24)
-    ap.add_argument("--serving-pool", type=int, default=4)
+    ap.add_argument("--serving-arrivals", type=int, default=500,
+                    help="arrivals of the serving leg at its headline load")
+    ap.add_argument("--serving-pool", type=int, default=16, help="distinct timeframes the serving leg replays")
     ap.add_argument("--timeframe-ms", type=float, default=0.0,
                     help="length of the main line's timeframe (default 10 ms, seed 2 + rank)")
     ap.add_argument("--all-configs", action="store_true",
@@ -930,6 +982,11 @@ def main():
         if rank == 0:
             run_reference(args)
         return
+
+    # the serving leg's timeframes are generated by a spawned process while
+    # the GPU legs run
+    pool = ServingPool(n_distinct=args.serving_pool) if world == 1 and not args.no_serving and \
+        not args.all_configs else None
 
     import torch
 
@@ -999,7 +1056,7 @@ def main():
     if world == 1 and not args.no_serving:
         del flush
         torch.cuda.empty_cache()
-        line["serving"] = serving_leg(local, n_timeframes=args.serving_timeframes, pool=args.serving_pool)
+        line["serving"] = serving_leg(local, pool, n_arrivals=args.serving_arrivals)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(cl, workload)
     if rank == 0:

@@ -132,6 +132,10 @@ const char *tpc_last_error(tpc_ctx *ctx);
  * n_requests requests (0 = library defaults for the internal capacities). */
 size_t tpc_arena_bytes(int64_t n_clusters, int32_t n_requests);
 
+/* The same for explicit grid-bin and tracklet capacities (0: the default,
+ * which is also the least), e.g. the arena of a retry after TPC_EOVERFLOW. */
+size_t tpc_arena_bytes_for(int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets);
+
 /* Size the context for at least n_clusters / n_requests (and, when nonzero,
  * the given grid-bin and tracklet capacities).  Called implicitly by the
  * load functions; call it explicitly to retry after TPC_EOVERFLOW. */
@@ -139,6 +143,12 @@ int tpc_reserve(tpc_ctx *ctx, int64_t n_clusters, int32_t n_requests, int64_t n_
 
 /* Device bytes the context's arena holds now (0 before the first load). */
 int tpc_get_arena_bytes(tpc_ctx *ctx, size_t *bytes);
+
+/* Device bytes the context's arena would hold after tpc_reserve with these
+ * arguments (its current size when that reserve would not grow it).  Host
+ * arithmetic only: allocates nothing and does not touch the device. */
+int tpc_reserve_bytes(tpc_ctx *ctx, int64_t n_clusters, int32_t n_requests, int64_t n_bins, int64_t n_tracklets,
+                      size_t *bytes);
 
 /* ------------------------------------------------------------ the hot path */
 /* a1: copy n clusters (host or device pointer) into the context as one

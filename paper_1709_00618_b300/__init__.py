@@ -583,6 +583,23 @@ class Tracker:
             out = out.reshape(-1, 15)
         return out
 
+    def track_into(self, clusters, tracks_out, cluster_track_out=None):
+        """load + find + fit + get_into (one request), retrying a capacity
+        overflow once with the worst-case capacities, as track()."""
+        for attempt in range(2):
+            self.load(clusters).find().fit()
+            try:
+                return self.get_into(tracks_out, cluster_track_out)
+            except TpcError as e:
+                if e.code != TPC_EOVERFLOW or attempt:
+                    raise
+                c = self.counts()
+                if not c["status"] & 2:  # not a device capacity (the caller's buffer is too small)
+                    raise
+                self.reserve(n_clusters=self.n, n_requests=1, n_bins=max(2 * c["n_bins"], 0),
+                             n_tracklets=self.n // 3 + 16)
+        raise AssertionError("unreachable")
+
     def track(self, clusters, req_offsets=None, graph: bool = False):
         """load + find + fit (+ graph) + get.  A capacity overflow (more
         tracklets or grid bins than reserved; reported, never truncated) is

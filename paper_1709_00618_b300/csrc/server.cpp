@@ -10,9 +10,12 @@
 // tracklet and track buffers) between requests and grows it only for a
 // larger request (stream-ordered, so other slots keep running); idle slots
 // give their arenas back when the budget would otherwise block the head of
-// the queue.  The worker never waits on the GPU: it polls one CUDA event per
+// the queue (outside the server's lock).  The worker polls one CUDA event per
 // slot, then enqueues the copy of the results into the caller's buffers and
-// polls again, so one request's copies overlap the others' kernels.
+// polls again, so one request's copies overlap the others' kernels.  A
+// request whose run overflowed a device capacity goes back to the head of
+// the queue with the worst-case capacities and is admitted again under the
+// same budget and free-memory checks.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,10 +51,11 @@ struct Request {
   int rc = TPC_OK;
   int64_t n_tracks = -1;
   bool retried = false;
+  int64_t retry_bins = 0, retry_tl = 0;  // capacities of a rerun after a device capacity overflow
   Clock::time_point t_submit, t_start, t_done;
 };
 
-enum { SL_FREE = 0, SL_RUN = 1, SL_COPY = 2 };
+enum { SL_FREE = 0, SL_RUN = 1, SL_COPY = 2, SL_TRIM = 3 };
 
 struct Slot {
   tpc_ctx* ctx = nullptr;
@@ -82,11 +86,11 @@ struct tpc_server {
   int64_t admitted = 0, completed = 0, peak_running = 0;
 
   void loop();
-  int pick_slot_locked(size_t need, bool* any_busy);
+  int pick_slot_locked(const Request* r, size_t* grow_out, bool* any_busy, bool* blocked_by_budget);
   bool admit_one();
   void advance(Slot& s);
   void complete(Slot& s, int rc);
-  int trim_idle_locked(size_t want);
+  bool trim_idle(size_t want);
   int launch(Slot& s);
   void account(Slot& s);
 };
@@ -101,52 +105,73 @@ void tpc_server::account(Slot& s) {
   s.arena = b;
 }
 
-// Recreate idle slots' contexts (dropping their arenas) until `want` more
-// bytes fit the budget.  Returns the number of slots trimmed.
-int tpc_server::trim_idle_locked(size_t want) {
-  int trimmed = 0;
-  for (Slot& s : slots) {
-    if (budget == 0 || reserved + want <= budget) break;
-    if (s.phase != SL_FREE || s.arena == 0) continue;
-    tpc_destroy(s.ctx);
-    s.ctx = nullptr;
-    reserved -= s.arena;
-    s.arena = 0;
-    tpc_ctx* fresh = nullptr;
-    if (tpc_create(&fresh, &cfg, device, s.stream, 0) == TPC_OK) s.ctx = fresh;
-    trimmed++;
+// Drops the arenas of idle slots (destroying and re-creating their
+// contexts) until `want` more bytes fit the budget.  The slots are taken out
+// under the lock and rebuilt outside it, so tpc_server_submit and _poll never
+// wait on the device meanwhile.  Returns whether any slot was trimmed.
+bool tpc_server::trim_idle(size_t want) {
+  std::vector<Slot*> victims;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    size_t freed = 0;
+    for (Slot& s : slots) {
+      if (budget == 0 || reserved - freed + want <= budget) break;
+      if (s.phase != SL_FREE || s.arena == 0 || !s.ctx) continue;
+      s.phase = SL_TRIM;  // not picked while it is rebuilt
+      freed += s.arena;
+      victims.push_back(&s);
+    }
   }
-  return trimmed;
+  for (Slot* s : victims) {
+    tpc_destroy(s->ctx);  // frees the arena
+    s->ctx = nullptr;
+    tpc_ctx* fresh = nullptr;
+    if (tpc_create(&fresh, &cfg, device, s->stream, 0) == TPC_OK) s->ctx = fresh;  // else rebuilt when next picked
+    std::lock_guard<std::mutex> lk(mu);
+    reserved -= s->arena;
+    s->arena = 0;
+    s->phase = SL_FREE;
+  }
+  return !victims.empty();
 }
 
-// A free slot for a request needing `need` arena bytes: the smallest one
-// that already holds enough, else the largest one, grown within the budget
-// and the free device memory.
-int tpc_server::pick_slot_locked(size_t need, bool* any_busy) {
+// A free slot for request r and the bytes its arena must grow by: the
+// smallest arena that needs no growth, else the slot that grows least,
+// within the budget and the free device memory.  *blocked_by_budget: a slot
+// could take r if idle arenas were dropped.
+int tpc_server::pick_slot_locked(const Request* r, size_t* grow_out, bool* any_busy, bool* blocked_by_budget) {
   *any_busy = false;
-  int fits = -1, grows = -1;
+  *blocked_by_budget = false;
+  int best = -1;
+  size_t best_grow = 0;
   for (size_t i = 0; i < slots.size(); i++) {
-    const Slot& s = slots[i];
+    Slot& s = slots[i];
     if (s.phase != SL_FREE) {
-      *any_busy = true;
+      *any_busy = *any_busy || s.phase != SL_TRIM;
       continue;
     }
-    if (!s.ctx) continue;
-    if (s.arena >= need && (fits < 0 || s.arena < slots[fits].arena)) fits = (int)i;
-    if (grows < 0 || s.arena > slots[grows].arena) grows = (int)i;
+    if (!s.ctx) {  // a context that could not be re-created after a trim: try again
+      tpc_ctx* fresh = nullptr;
+      if (tpc_create(&fresh, &cfg, device, s.stream, 0) != TPC_OK) continue;
+      s.ctx = fresh;
+    }
+    size_t after = 0;
+    if (tpc_reserve_bytes(s.ctx, r->n, 1, r->retry_bins, r->retry_tl, &after) != TPC_OK) continue;
+    const size_t grow = after > s.arena ? after - s.arena : 0;
+    if (best < 0 || grow < best_grow || (grow == best_grow && s.arena < slots[best].arena)) {
+      best = (int)i;
+      best_grow = grow;
+    }
   }
-  if (fits >= 0) return fits;
-  if (grows < 0) return -1;
-  size_t grow = need - slots[grows].arena;
-  if (budget && reserved + grow > budget) {
-    trim_idle_locked(grow);
-    if (!slots[grows].ctx) return -1;
-    grow = need - std::min(need, slots[grows].arena);
-    if (reserved + grow > budget) return -1;
+  if (best < 0) return -1;
+  if (budget && reserved + best_grow > budget) {
+    *blocked_by_budget = true;
+    return -1;
   }
   size_t free_b = 0, total_b = 0;
-  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || grow + kHeadroom > free_b) return -1;
-  return grows;
+  if (best_grow && (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || best_grow + kHeadroom > free_b)) return -1;
+  *grow_out = best_grow;
+  return best;
 }
 
 int tpc_server::launch(Slot& s) {
@@ -161,13 +186,14 @@ bool tpc_server::admit_one() {
   Request* r = nullptr;
   Slot* s = nullptr;
   size_t grow = 0;
+  size_t trim_want = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
     if (queue.empty()) return false;
     r = queue.front();
-    const size_t need = tpc_arena_bytes(r->n, 1);
-    bool any_busy = false;
-    const int pick = pick_slot_locked(need, &any_busy);
+    const size_t need = tpc_arena_bytes_for(r->n, 1, r->retry_bins, r->retry_tl);
+    bool any_busy = false, blocked = false;
+    const int pick = pick_slot_locked(r, &grow, &any_busy, &blocked);
     if (pick < 0) {
       if (!any_busy && budget && need > budget) {  // can never fit
         queue.pop_front();
@@ -178,28 +204,27 @@ bool tpc_server::admit_one() {
         cv_done.notify_all();
         return true;
       }
-      return false;
+      if (!blocked) return false;
+      trim_want = need;
+    } else {
+      s = &slots[pick];
+      reserved += grow;  // booked now; account() corrects it to the arena's real size
+      s->arena += grow;
+      queue.pop_front();
+      r->state = RQ_RUNNING;
+      r->t_start = Clock::now();
+      s->req = r;
+      s->phase = SL_RUN;
+      admitted++;
+      int64_t running = 0;
+      for (const Slot& t : slots) running += t.phase == SL_RUN || t.phase == SL_COPY;
+      peak_running = std::max(peak_running, running);
     }
-    s = &slots[pick];
-    grow = need > s->arena ? need - s->arena : 0;
-    reserved += grow;
-    s->arena += grow;
-    queue.pop_front();
-    r->state = RQ_RUNNING;
-    r->t_start = Clock::now();
-    s->req = r;
-    s->phase = SL_RUN;
-    admitted++;
-    int64_t running = 0;
-    for (const Slot& t : slots) running += t.phase != SL_FREE;
-    peak_running = std::max(peak_running, running);
   }
+  if (!s) return trim_idle(trim_want);  // the budget blocks the head: drop idle arenas, then try again
   // enqueue outside the lock: arena growth, copy in, graph, completion event
-  int rc = TPC_OK;
-  if (grow) {
-    rc = tpc_reserve(s->ctx, r->n, 1, 0, 0);
-    account(*s);
-  }
+  int rc = tpc_reserve(s->ctx, r->n, 1, r->retry_bins, r->retry_tl);
+  account(*s);
   if (rc == TPC_OK) rc = launch(*s);
   if (rc != TPC_OK) complete(*s, rc);
   return true;
@@ -227,13 +252,19 @@ void tpc_server::advance(Slot& s) {
   int64_t nt = -1;
   int rc = tpc_get_tracks_async(s.ctx, r->out, r->cap, &nt, r->cluster_track);
   if (rc == TPC_EOVERFLOW && nt < 0 && !r->retried) {
-    // a device capacity (tracklets) overflowed: rerun once on this slot
-    // with the worst-case capacity, without waiting
+    // a device capacity (grid bins, tracklets) overflowed: the request goes
+    // back to the head of the queue with the worst-case capacities, and is
+    // admitted again like any other (budget, free memory)
+    int64_t counts[8] = {0};
+    tpc_get_counts(s.ctx, counts);
+    std::lock_guard<std::mutex> lk(mu);
     r->retried = true;
-    rc = tpc_reserve(s.ctx, r->n, 1, 0, r->n / 3 + 16);
-    account(s);
-    if (rc == TPC_OK) rc = launch(s);
-    if (rc != TPC_OK) complete(s, rc);
+    r->retry_bins = 2 * std::max<int64_t>(counts[3], 1);
+    r->retry_tl = r->n / 3 + 16;
+    r->state = RQ_QUEUED;
+    s.req = nullptr;
+    s.phase = SL_FREE;
+    queue.push_front(r);
     return;
   }
   r->n_tracks = nt;
@@ -249,7 +280,7 @@ void tpc_server::loop() {
   while (!stop.load()) {
     bool active = false;
     for (Slot& s : slots) {
-      if (s.phase == SL_FREE) continue;
+      if (s.phase == SL_FREE || s.phase == SL_TRIM) continue;
       active = true;
       const cudaError_t q = cudaEventQuery(s.done);
       if (q == cudaSuccess) advance(s);

@@ -47,6 +47,26 @@ def test_central_event_graph_equals_plain(trk):
     assert a.tobytes() == b.tobytes() == c.tobytes()
 
 
+def test_twenty_repeats_are_byte_identical(trk):
+    """Determinism: 20 runs of the central event (graph and plain launches
+    alternating) give byte-identical tracks, cluster assignments, links,
+    tracklets and follow outputs, so no atomic or scatter order leaks into
+    a result."""
+    ev = synth.central_event(seed=1)
+    names = ("perm", "up", "dn", "tie", "tl_start", "tl_len", "f_n", "f_hits", "f_par", "f_cov", "f_chi2",
+             "tl_track")
+    ref = None
+    for k in range(20):
+        tracks, ct, _ = trk.track(ev.clusters, graph=bool(k % 2))
+        got = [tracks.tobytes(), ct.tobytes()] + [trk.stage(nm).tobytes() for nm in names]
+        if ref is None:
+            ref = got
+            assert len(tracks) > 20000
+        else:
+            for nm, a, b in zip(("tracks", "cluster_track") + names, ref, got):
+                assert a == b, f"run {k}: {nm} differs"
+
+
 def test_timeframe_slice(trk):
     """Continuous read-out: z is the drift coordinate up to ~2.5e3 cm here."""
     ev = synth.timeframe(seed=2, length_ms=1.0)
