@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
     _fields_ = [("bz_kg", ctypes.c_double), ("sigma", ctypes.c_double), ("d_max", ctypes.c_float),
                 ("min_chain", ctypes.c_int), ("max_miss", ctypes.c_int), ("n_min_track", ctypes.c_int),
                 ("gate", ctypes.c_double), ("c0", ctypes.c_double * 5), ("s_max", ctypes.c_double),
-                ("edge", ctypes.c_double), ("taint_rel", ctypes.c_double), ("trace_t", ctypes.c_int)]
+                ("edge", ctypes.c_double), ("taint_rel", ctypes.c_double), ("trace_t", ctypes.c_int),
+                ("link_skip", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -55,6 +55,7 @@ typedef struct {
   double edge;       /* cm beyond the sector edge that ends an extension */
   double taint_rel;  /* margin of the near-tie / near-gate flags */
   int trace_t;       /* tracklet whose updates are recorded (-1: none) */
+  int link_skip;     /* 1: a cluster without an accepted r-1/r+1 pair may link across one empty row */
 } orc_config;
 
 void orc_default_config(orc_config *c) {
@@ -70,6 +71,7 @@ void orc_default_config(orc_config *c) {
   c->edge = 2.0;
   c->taint_rel = 1e-4;
   c->trace_t = -1;
+  c->link_skip = 0;
 }
 
 /* ------------------------------------------------------------- geometry */
@@ -83,9 +85,6 @@ static void init_tables(void) {
     YHI32[r] = (float)(row_x64(r) * TAN10);
   }
 }
-/* Link search windows: 2.0 and 2.5 row pitches plus 0.5 cm. */
-static float window_y(void) { return (float)(2.0 * ((245.8 - 85.2) / 158.0) + 0.5); }
-static float window_z(void) { return (float)(2.5 * ((245.8 - 85.2) / 158.0) + 0.5); }
 
 /* ----------------------------------------------------------- result set */
 typedef struct {
@@ -271,11 +270,81 @@ static float line_dev(float yd, float zd, float yc, float zc, float yu, float zu
   return dy * dy + dz * dz;
 }
 
+/* Link windows for a candidate k rows away: k times the one-row slope
+   allowance plus the resolution margin (the reading's windows for k = 1). */
+static float window_y_k(int k) { return (float)(k * 2.0 * ((245.8 - 85.2) / 158.0) + 0.5); }
+static float window_z_k(int k) { return (float)(k * 2.5 * ((245.8 - 85.2) / 158.0) + 0.5); }
+
+/* The clusters of row-sector rs2 inside the window of (yc, zc), appended to
+   *lst (brute: every cluster of the row-sector is tested, no grid). */
+static void window_list(const orc_result *R, int32_t rs2, float yc, float zc, float WY, float WZ, int brute,
+                        int32_t **lst, int *cnt, int *cap) {
+  int32_t a0 = 0, a1 = 0;
+  int iy0 = 0, iy1 = 0, iz0 = 0, iz1 = 0;
+  if (brute) {
+    a0 = R->row_start[rs2];
+    a1 = R->row_start[rs2 + 1];
+  } else if (!box_bins(R, rs2, (double)yc - WY, (double)yc + WY, (double)zc - WZ, (double)zc + WZ, &iy0, &iy1,
+                       &iz0, &iz1)) {
+    return;
+  }
+  for (int iz = iz0; iz <= (brute ? iz0 : iz1); iz++)
+    for (int iy = iy0; iy <= (brute ? iy0 : iy1); iy++) {
+      if (!brute) {
+        int64_t gb = R->bin_base[rs2] + (int64_t)iz * R->n_y[rs2] + iy;
+        a0 = R->bin_start[gb];
+        a1 = R->bin_start[gb + 1];
+      }
+      for (int32_t k = a0; k < a1; k++)
+        if (fabsf(R->sy[k] - yc) <= WY && fabsf(R->sz[k] - zc) <= WZ) {
+          if (*cnt == *cap) {
+            *cap *= 2;
+            *lst = (int32_t *)realloc(*lst, sizeof(int32_t) * (size_t)*cap);
+          }
+          (*lst)[(*cnt)++] = k;
+        }
+    }
+}
+
+typedef struct {
+  float best, second;
+  int32_t d, u;
+} pair_pick;
+
+/* Every (d, u) pair of the two lists into the pick: the lexicographic
+   minimum of (D, d, u) and the smallest D of the other pairs. */
+static void pick_pairs(const orc_result *R, float yc, float zc, float f, const int32_t *cd, int nd,
+                       const int32_t *cu, int nu, pair_pick *b) {
+  for (int i = 0; i < nd; i++)
+    for (int j = 0; j < nu; j++) {
+      int32_t d = cd[i], u = cu[j];
+      float D = line_dev(R->sy[d], R->sz[d], yc, zc, R->sy[u], R->sz[u], f);
+      int better = D < b->best || (D == b->best && (d < b->d || (d == b->d && u < b->u)));
+      if (b->d < 0 || better) {
+        if (b->d >= 0) b->second = fminf(b->second, b->best);
+        b->best = D;
+        b->d = d;
+        b->u = u;
+      } else {
+        b->second = fminf(b->second, D);
+      }
+    }
+}
+
+/* a3: for each cluster on rows 1..157 the best straight-line pair (d on
+   row r-1, u on row r+1).  With link_skip (the next-row variant against
+   duplicate tracklets), a cluster on rows 2..156 without an accepted pair
+   takes the best pair skipping one row on one side -- (r-2, r+1) or
+   (r-1, r+2) -- and, failing that, on both sides (r-2, r+2); windows scale
+   with the row distance and the chord fraction is that of the rows
+   involved.  The smallest skip is tried first: on a straight line a pair
+   further out is as good, and would break the chain. */
 static void neighbours(const orc_config *cfg, orc_result *R, int brute) {
   int64_t n = R->n;
-  const float WY = window_y(), WZ = window_z();
-  int cap_d = 256, cap_u = 256;
-  int32_t *cd = (int32_t *)malloc(sizeof(int32_t) * cap_d), *cu = (int32_t *)malloc(sizeof(int32_t) * cap_u);
+  const float WY1 = window_y_k(1), WZ1 = window_z_k(1), WY2 = window_y_k(2), WZ2 = window_z_k(2);
+  int cap[4] = {256, 256, 256, 256};
+  int32_t *lst[4];
+  for (int i = 0; i < 4; i++) lst[i] = (int32_t *)malloc(sizeof(int32_t) * cap[i]);
   for (int64_t c = 0; c < n; c++) {
     R->up[c] = R->dn[c] = -1;
     R->tie[c] = 0;
@@ -284,63 +353,36 @@ static void neighbours(const orc_config *cfg, orc_result *R, int brute) {
     int32_t rs = R->rs_of[c], row = rs % NROW;
     if (row < 1 || row > NROW - 2) continue;
     float yc = R->sy[c], zc = R->sz[c];
+    /* lists: 0 row r-1, 1 row r+1, 2 row r-2, 3 row r+2 */
+    int cnt[4] = {0, 0, 0, 0};
+    window_list(R, rs - 1, yc, zc, WY1, WZ1, brute, &lst[0], &cnt[0], &cap[0]);
+    window_list(R, rs + 1, yc, zc, WY1, WZ1, brute, &lst[1], &cnt[1], &cap[1]);
+    pair_pick b = {INFINITY, INFINITY, -1, -1};
     float f = (X32[row] - X32[row - 1]) / (X32[row + 1] - X32[row - 1]);
-    /* candidate lists on the rows below and above */
-    int nd = 0, nu = 0;
-    for (int side = 0; side < 2; side++) {
-      int32_t rs2 = side ? rs + 1 : rs - 1;
-      int32_t **lst = side ? &cu : &cd;
-      int *cntp = side ? &nu : &nd, *capp = side ? &cap_u : &cap_d;
-      int32_t a0 = 0, a1 = 0;
-      int iy0 = 0, iy1 = 0, iz0 = 0, iz1 = 0;
-      if (brute) {
-        a0 = R->row_start[rs2];
-        a1 = R->row_start[rs2 + 1];
-      } else if (!box_bins(R, rs2, (double)yc - WY, (double)yc + WY, (double)zc - WZ, (double)zc + WZ, &iy0, &iy1,
-                           &iz0, &iz1)) {
-        continue;
-      }
-      for (int iz = iz0; iz <= (brute ? iz0 : iz1); iz++)
-        for (int iy = iy0; iy <= (brute ? iy0 : iy1); iy++) {
-          if (!brute) {
-            int64_t gb = R->bin_base[rs2] + (int64_t)iz * R->n_y[rs2] + iy;
-            a0 = R->bin_start[gb];
-            a1 = R->bin_start[gb + 1];
-          }
-          for (int32_t k = a0; k < a1; k++)
-            if (fabsf(R->sy[k] - yc) <= WY && fabsf(R->sz[k] - zc) <= WZ) {
-              if (*cntp == *capp) {
-                *capp *= 2;
-                *lst = (int32_t *)realloc(*lst, sizeof(int32_t) * (size_t)*capp);
-              }
-              (*lst)[(*cntp)++] = k;
-            }
+    pick_pairs(R, yc, zc, f, lst[0], cnt[0], lst[1], cnt[1], &b);
+    if (cfg->link_skip && !(b.d >= 0 && b.best <= cfg->d_max) && row >= 2 && row <= NROW - 3) {
+      b.best = b.second = INFINITY;
+      b.d = b.u = -1;
+      window_list(R, rs - 2, yc, zc, WY2, WZ2, brute, &lst[2], &cnt[2], &cap[2]);
+      window_list(R, rs + 2, yc, zc, WY2, WZ2, brute, &lst[3], &cnt[3], &cap[3]);
+      const int dr[3] = {-2, -1, -2}, ur[3] = {1, 2, 2}, dl[3] = {2, 0, 2}, ul[3] = {1, 3, 3};
+      for (int m = 0; m < 3; m++) {
+        if (m == 2) {  /* both sides skipped: only without an accepted one-sided skip */
+          if (b.d >= 0 && b.best <= cfg->d_max) break;
+          b.best = b.second = INFINITY;
+          b.d = b.u = -1;
         }
+        float fm = (X32[row] - X32[row + dr[m]]) / (X32[row + ur[m]] - X32[row + dr[m]]);
+        pick_pairs(R, yc, zc, fm, lst[dl[m]], cnt[dl[m]], lst[ul[m]], cnt[ul[m]], &b);
+      }
     }
-    float best = INFINITY, second = INFINITY;
-    int32_t bd = -1, bu = -1;
-    for (int i = 0; i < nd; i++)
-      for (int j = 0; j < nu; j++) {
-        int32_t d = cd[i], u = cu[j];
-        float D = line_dev(R->sy[d], R->sz[d], yc, zc, R->sy[u], R->sz[u], f);
-        int better = D < best || (D == best && (d < bd || (d == bd && u < bu)));
-        if (bd < 0 || better) {
-          if (bd >= 0) second = fminf(second, best);
-          best = D;
-          bd = d;
-          bu = u;
-        } else {
-          second = fminf(second, D);
-        }
-      }
-    if (bd >= 0 && best <= cfg->d_max) {
-      R->up[c] = bu;
-      R->dn[c] = bd;
-      R->tie[c] = (second < INFINITY && fabsf(second - best) <= 1e-6f * fmaxf(best, 1e-12f)) ? 1 : 0;
+    if (b.d >= 0 && b.best <= cfg->d_max) {
+      R->up[c] = b.u;
+      R->dn[c] = b.d;
+      R->tie[c] = (b.second < INFINITY && fabsf(b.second - b.best) <= 1e-6f * fmaxf(b.best, 1e-12f)) ? 1 : 0;
     }
   }
-  free(cd);
-  free(cu);
+  for (int i = 0; i < 4; i++) free(lst[i]);
 }
 
 /* ===================================================== a4 link cleaning */
@@ -542,8 +584,9 @@ static void follow_one(const kctx *k, orc_result *R, int32_t t) {
   chain[0] = c0;
   for (int i = 1; i < L; i++) chain[i] = R->up_m[chain[i - 1]];
   int32_t cl = chain[L - 1];
+  const int r_end = R->rs_of[cl] % NROW; /* r0 + L - 1 unless links skip rows */
   /* seed from the chord first -> last chain cluster */
-  double x0 = X32[r0], x1 = X32[r0 + L - 1];
+  double x0 = X32[r0], x1 = X32[r_end];
   double dX = x1 - x0, dY = (double)R->sy[cl] - R->sy[c0], dZ = (double)R->sz[cl] - R->sz[c0];
   double Lc = sqrt(dX * dX + dY * dY);
   kstate s;
@@ -556,19 +599,25 @@ static void follow_one(const kctx *k, orc_result *R, int32_t t) {
   reset_cov(k, &s);
   traced_update(k, R, t, 0, r0, &s, R->sy[c0], R->sz[c0]);
   hits[nf++] = c0;
+  /* over the chain row by row: an update on every row holding the chain's
+     next cluster (a row the links skipped is only crossed) */
+  int r = r0;
   for (int i = 1; i < L; i++) {
-    if (!propagate(k, &s, X32[r0 + i], &flags)) {
-      R->f_n[t] = 0; R->f_nf[t] = 0; R->f_nb[t] = 0; R->f_flags[t] = flags | F_SEED_FAIL; R->f_row[t] = r0;
-      memset(R->f_par + 5 * (int64_t)t, 0, 5 * sizeof(double));
-      memset(R->f_cov + 15 * (int64_t)t, 0, 15 * sizeof(double));
-      R->f_chi2[t] = 0;
-      return;
+    const int ri = R->rs_of[chain[i]] % NROW;
+    while (r < ri) {
+      if (!propagate(k, &s, X32[++r], &flags)) {
+        R->f_n[t] = 0; R->f_nf[t] = 0; R->f_nb[t] = 0; R->f_flags[t] = flags | F_SEED_FAIL; R->f_row[t] = r0;
+        memset(R->f_par + 5 * (int64_t)t, 0, 5 * sizeof(double));
+        memset(R->f_cov + 15 * (int64_t)t, 0, 15 * sizeof(double));
+        R->f_chi2[t] = 0;
+        return;
+      }
     }
-    traced_update(k, R, t, 0, r0 + i, &s, R->sy[chain[i]], R->sz[chain[i]]);
+    traced_update(k, R, t, 0, ri, &s, R->sy[chain[i]], R->sz[chain[i]]);
     hits[nf++] = chain[i];
   }
   kstate saved = s;
-  int r_last = r0 + L - 1, misses = 0;
+  int r_last = r_end, misses = 0;
   for (int r = r_last + 1; r < NROW; r++) {
     if (!propagate(k, &s, X32[r], &flags)) break;
     if (outside_sector(k, &s, &flags)) break;

@@ -23,10 +23,10 @@ MUTANTS = {
                                   "      for (int m = 0; m < 5; m++) a += T[i][m] * J[m][j];"),
     "gain_uses_wrong_column": ("    G[i][1] = s->C[i][0] * I01 + s->C[i][1] * I11;",
                                "    G[i][1] = s->C[i][1] * I01 + s->C[i][0] * I11;"),
-    "link_tiebreak_reversed": ("        int better = D < best || (D == best && (d < bd || (d == bd && u < bu)));",
-                               "        int better = D < best || (D == best && (d > bd || (d == bd && u > bu)));"),
-    "link_window_y_too_small": ("static float window_y(void) { return (float)(2.0 * ((245.8 - 85.2) / 158.0) + 0.5); }",
-                                "static float window_y(void) { return (float)(1.0 * ((245.8 - 85.2) / 158.0) + 0.5); }"),
+    "link_tiebreak_reversed": ("      int better = D < b->best || (D == b->best && (d < b->d || (d == b->d && u < b->u)));",
+                               "      int better = D < b->best || (D == b->best && (d > b->d || (d == b->d && u > b->u)));"),
+    "link_window_y_too_small": ("static float window_y_k(int k) { return (float)(k * 2.0 * ((245.8 - 85.2) / 158.0) + 0.5); }",
+                                "static float window_y_k(int k) { return (float)(k * 1.0 * ((245.8 - 85.2) / 158.0) + 0.5); }"),
     "clean_one_sided": ("    R->up_m[c] = (u >= 0 && R->dn[u] == c) ? u : -1;", "    R->up_m[c] = u;"),
     "owner_prefers_higher_id": (
         "    uint64_t key = ((uint64_t)(uint32_t)R->f_n[t] << 32) | (uint64_t)(0xFFFFFFFFu - (uint32_t)t);\n"
@@ -47,6 +47,15 @@ MUTANTS = {
     "edge_margin_sign": ("  double lim = s->x * TAN10 + k->cfg->edge;", "  double lim = s->x * TAN10 - k->cfg->edge;"),
     "edge_margin_dropped": ("  double lim = s->x * TAN10 + k->cfg->edge;", "  double lim = s->x * TAN10;"),
     "edge_test_never_stops": ("  return fabs(s->p[0]) > lim;", "  return fabs(s->p[0]) > lim + 1e9;"),
+    "link_skip_window_not_scaled": ("WY2 = window_y_k(2), WZ2 = window_z_k(2);", "WY2 = window_y_k(1), WZ2 = window_z_k(1);"),
+    "link_skip_despite_adjacent_pair": (
+        "    if (cfg->link_skip && !(b.d >= 0 && b.best <= cfg->d_max) && row >= 2 && row <= NROW - 3) {",
+        "    if (cfg->link_skip && row >= 2 && row <= NROW - 3) {"),
+    "link_skip_both_sides_not_last": ("          if (b.d >= 0 && b.best <= cfg->d_max) break;\n          b.best = b.second = INFINITY;",
+                                      "          if (0) break;\n          b.best = b.second;"),
+    "link_skip_adjacent_chord_fraction": (
+        "        float fm = (X32[row] - X32[row + dr[m]]) / (X32[row + ur[m]] - X32[row + dr[m]]);",
+        "        float fm = f;"),
 }
 
 

@@ -554,3 +554,117 @@ def test_chi2_equals_least_squares_minimum_of_the_linear_model(sphi, tgl, res):
     diag_only = r[0] ** 2 / Sp[0, 0] + r[1] ** 2 / Sp[1, 1]
     if abs(sphi * tgl) > 0.5:
         assert abs(diag_only - obj) > 0.1 * obj
+
+
+# ------------------------------------- next-row variant of the links (a3)
+WY2 = np.float32(2 * 2.0 * ((245.8 - 85.2) / 158.0) + 0.5)
+WZ2 = np.float32(2 * 2.5 * ((245.8 - 85.2) / 158.0) + 0.5)
+
+
+def _brute_links_skip(r, d_max=1.0):
+    """All-triplet search with the next-row variant, in binary32, no grid:
+    the r-1/r+1 pairs first; a cluster on rows 2..156 without an accepted
+    one takes the lexicographic minimum of (D, d, u) over the one-sided
+    skips (r-2, r+1), (r-1, r+2), and without an accepted one of those over
+    (r-2, r+2); windows scaled by the row distance."""
+    x, _ = oracle.tables()
+    up, dn, tie = _brute_links(r, d_max)
+    sy, sz, rs = r["sy"], r["sz"], r["rs_of"]
+    win = {1: (WY, WZ), 2: (WY2, WZ2)}
+    for c in range(r["n"]):
+        row = rs[c] % 159
+        if up[c] >= 0 or row < 2 or row > 156:
+            continue
+        best = None
+        Ds = []
+        for dr, ur in ((-2, 1), (-1, 2), (-2, 2)):
+            if ur - dr == 4:  # both sides skipped
+                if best is not None and best[0] <= np.float32(d_max):
+                    break
+                best, Ds = None, []
+            wd, wu = win[-dr], win[ur]
+            d = np.nonzero((rs == rs[c] + dr) & (np.abs(sy - sy[c]) <= wd[0]) & (np.abs(sz - sz[c]) <= wd[1]))[0]
+            u = np.nonzero((rs == rs[c] + ur) & (np.abs(sy - sy[c]) <= wu[0]) & (np.abs(sz - sz[c]) <= wu[1]))[0]
+            if len(d) == 0 or len(u) == 0:
+                continue
+            f = np.float32((x[row] - x[row + dr]) / (x[row + ur] - x[row + dr]))
+            for dd in d:
+                for uu in u:
+                    ey = (sy[dd] - sy[c]) + (sy[uu] - sy[dd]) * f
+                    ez = (sz[dd] - sz[c]) + (sz[uu] - sz[dd]) * f
+                    D = np.float32(ey * ey + ez * ez)
+                    Ds.append(D)
+                    if best is None or (D, dd, uu) < best:
+                        best = (D, dd, uu)
+        if best is not None and best[0] <= np.float32(d_max):
+            dn[c], up[c] = best[1], best[2]
+            Ds.sort()
+            second = Ds[1] if len(Ds) > 1 else None
+            tie[c] = second is not None and abs(second - best[0]) <= np.float32(1e-6) * max(best[0], np.float32(1e-12))
+    return up, dn, tie
+
+
+def test_link_skip_equals_all_triplet_brute_force():
+    cfg = oracle.default_config(link_skip=1)
+    for seed in (31, 32, 33):
+        ev = synth.generate(synth.GenParams(seed=seed, n_primaries=14, n_secondaries=0, sectors=(5,),
+                                            phi_min=math.radians(100), phi_max=math.radians(120),
+                                            phi_radius=85.2, noise_frac=0.1, row_eff=0.8))
+        cl = np.concatenate([ev.clusters, ev.clusters[::7]])  # exact ties
+        r = oracle.run(cl, stop_after="neighbours", cfg=cfg)
+        up, dn, tie = _brute_links_skip(r)
+        assert np.array_equal(r["up"], up) and np.array_equal(r["dn"], dn) and np.array_equal(r["tie"], tie)
+        rows = r["rs_of"] % 159
+        skipped = (up >= 0) & (rows[np.maximum(up, 0)] - rows == 2) | (dn >= 0) & (rows - rows[np.maximum(dn, 0)] == 2)
+        assert skipped.sum() > 5  # the variant is exercised
+        base = oracle.run(cl, stop_after="neighbours")
+        # clusters with an accepted adjacent pair keep it
+        keep = base["up"] >= 0
+        assert np.array_equal(r["up"][keep], base["up"][keep]) and np.array_equal(r["dn"][keep], base["dn"][keep])
+
+
+def test_link_skip_chains_bridge_single_missing_rows():
+    """Straight tracks with every seventh row missing: with the variant each
+    track is one chain over all its clusters on rows 1..157; without it the
+    chains break at every gap (runs of six rows: chains of four)."""
+    rows = [q for q in range(159) if q % 7 != 3]
+    ev = synth.straight_lines(seed=4, n_lines=5, spacing=5.0, max_slope=0.05, rows=rows)
+    lab = ev.clusters["id"]
+    for skip in (0, 1):
+        r = oracle.run(ev.clusters, stop_after="tracklets", cfg=oracle.default_config(link_skip=skip))
+        lab_sorted = lab[r["perm"]]
+        if skip:
+            assert r["n_tracklets"] == 5
+            for s0, L in zip(r["tl_start"], r["tl_len"]):
+                inside = [q for q in rows if 1 <= q <= 157]
+                assert L == len(inside) and (lab_sorted == lab_sorted[s0]).sum() >= L
+        else:
+            assert r["n_tracklets"] >= 5 * 20 and np.all(r["tl_len"] <= 4)
+
+
+def test_link_skip_cuts_duplicate_tracklets_on_noiseless_tracks():
+    """Noiseless tracks at 90% row efficiency, where every missing row
+    breaks an r-1/r+1 chain: with the variant the follow stage starts from
+    less than half as many tracklets per track, and still at least 98% of
+    the found tracks are exactly one true segment with all its clusters
+    (without it: all of them; a wider two-row window occasionally carries a
+    chain across a neighbouring track at a gap)."""
+    p = synth.GenParams(seed=6, n_primaries=200, n_secondaries=0, sectors=tuple(range(36)), sigma_y=0.0,
+                        sigma_z=0.0, row_eff=0.9, noise_frac=0.0, pt_min=0.3)
+    ev = synth.generate(p, truth=True)
+    c, t = ev.clusters, ev.truth
+    res, whole = {}, {}
+    for skip in (0, 1):
+        r = oracle.run(c, cfg=oracle.default_config(link_skip=skip))
+        ct = r["cluster_track"]
+        assert r["n_tracks"] > 100
+        good = 0
+        for k in range(r["n_tracks"]):
+            idx = np.nonzero(ct == k)[0]
+            labs = np.unique(t["track"][idx])
+            seg = np.nonzero((t["track"] == labs[0]) & (c["sector"] == c["sector"][idx[0]]))[0]
+            good += len(labs) == 1 and len(seg) == len(idx)
+        whole[skip] = good / r["n_tracks"]
+        res[skip] = r["n_tracklets"] / r["n_tracks"]
+    assert whole[0] == 1.0 and whole[1] >= 0.98, whole
+    assert res[1] < 0.5 * res[0], res
