@@ -954,6 +954,44 @@ def time_vs_size(local, flush, known=(), reps=3):
                        "input clusters; linear in the input size means a log-log slope near 1 once the GPU is full"}
 
 
+def link_skip_leg(local, flush, cases, reps=5):
+    """The next-row variant of the links (link_skip = 1) against the default
+    reading on the same inputs: tracklets per track and the device time of
+    one graph replay (inputs resident, L2 flushed, median of reps)."""
+    import numpy as np
+    import torch
+
+    import paper_1709_00618_b300 as tpc
+    out = {}
+    for name, cl in cases:
+        dev = torch.from_numpy(cl.view(np.uint8)).to(f"cuda:{local}")
+        row = {"clusters": len(cl)}
+        for skip in (0, 1):
+            stream = torch.cuda.Stream()
+            with tpc.Tracker(device=local, stream=stream, cfg=tpc.default_config(link_skip=skip)) as trk:
+                for _ in range(3):
+                    trk.load(dev).run_graph()
+                trk.sync()
+                dt = []
+                for _ in range(reps):
+                    with torch.cuda.stream(stream):
+                        flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    trk.load(dev).run_graph()
+                    e1.record(stream)
+                    e1.synchronize()
+                    dt.append(e0.elapsed_time(e1))
+                c = trk.counts()
+            row["variant" if skip else "default"] = {
+                "ms": statistics.median(dt), "clusters_per_s": len(cl) / (statistics.median(dt) / 1e3),
+                "tracklets": c["n_tracklets"], "tracks": c["n_tracks"],
+                "tracklets_per_track": c["n_tracklets"] / max(c["n_tracks"], 1)}
+        out[name] = row
+        del dev
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1048,6 +1086,7 @@ def main():
               "tracks": mc["counts"]["n_tracks"], "clocks": mc["clocks"]}
         line["central_event"] = ce
         line["time_vs_size"] = time_vs_size(local, flush, known=((workload, n, 1e3 * m["t_step"]),))
+        line["link_skip_variant"] = link_skip_leg(local, flush, ((CONFIG2, synth_central), (workload, cl)))
     else:
         m.pop("host_in", None)
         m.pop("pinned", None)

@@ -104,7 +104,14 @@ typedef struct {
                           Outside the forward pass, up to as many again while
                           the last one still more than halved the variance of
                           sin phi, dz/ds_T or q/pT */
-  int32_t reserved;
+  int32_t link_skip;   /* 0 (default): links join rows r-1 and r+1 only.  1: the
+                          next-row variant against duplicate tracklets -- a
+                          cluster on rows 2..156 without an accepted r-1/r+1 pair
+                          takes the best pair skipping one row on one or both
+                          sides, (r-2, r+1), (r-1, r+2) or (r-2, r+2), with windows
+                          scaled by the row distance; chains then cross the
+                          skipped rows and track following only propagates
+                          through them */
 } tpc_config;
 
 /* Fills cfg with the defaults above. */

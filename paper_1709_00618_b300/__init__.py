@@ -87,7 +87,7 @@ class TpcConfig(ctypes.Structure):
                 ("min_chain", ctypes.c_int32), ("max_miss", ctypes.c_int32), ("n_min_track", ctypes.c_int32),
                 ("gate", ctypes.c_double), ("c0", ctypes.c_double * 5), ("s_max", ctypes.c_double),
                 ("edge", ctypes.c_double), ("taint_rel", ctypes.c_double), ("fp64_updates", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("link_skip", ctypes.c_int32)]
 
 
 _lib = None

@@ -106,7 +106,9 @@ struct KConst {
   float V;          // sigma^2
   double Vd;
   float d_max;
-  float wy, wz;     // link windows
+  float wy, wz;     // link windows (one row)
+  float wy2, wz2;   // link windows two rows away (link_skip)
+  int32_t link_skip;
   float gate;
   float c0[5];
   float s_max;

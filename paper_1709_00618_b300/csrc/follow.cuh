@@ -265,10 +265,14 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
   const bool zone = Z && w.nupd < w.zend;
   float2 Pc;
   int c = -1;
+  bool cross = false;  // a row the chain's links skipped (link_skip): crossed without an update
   if (chain) {  // the chain's cluster and the one after it are loaded while the state propagates
     c = w.nk;
-    Pc = __ldg(g.yz + c);
-    w.nk = w.i + 1 < w.L ? __ldg(up_m + c) : -1;
+    if (kc.link_skip) cross = __ldg(g.rs_of + c) % NROW != r;
+    if (!cross) {
+      Pc = __ldg(g.yz + c);
+      w.nk = w.i + 1 < w.L ? __ldg(up_m + c) : -1;
+    }
   }
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
     if (chain) w.seed_fail = true;
@@ -276,6 +280,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
   }
   tl.prop++;
   tl.prop64 += zone;
+  if (cross) return true;
   if (chain) {
     w.k = c;
     w.i++;
@@ -508,7 +513,9 @@ __global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __
       w.r0 = rs0 % NROW;
       const float2 P0 = __ldg(g.yz + c0), P1 = __ldg(g.yz + cl);
       {
-        const float x0 = sX[w.r0], x1 = sX[w.r0 + w.L - 1];
+        // the chain's last row: r0 + L - 1 unless its links skip rows
+        const int r_end = kc.link_skip ? __ldg(g.rs_of + cl) % NROW : w.r0 + w.L - 1;
+        const float x0 = sX[w.r0], x1 = sX[r_end];
         const float dX = x1 - x0, dY = P1.x - P0.x, dZ = P1.y - P0.y;
         const float Lc = sqrtf(dX * dX + dY * dY);
         seed_state(p, w.r0, x0, P0.x, P0.y, dY / Lc, dZ / Lc, 0.0f);

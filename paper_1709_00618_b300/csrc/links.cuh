@@ -96,6 +96,58 @@ __device__ __noinline__ void nb_nested(const float2* __restrict__ yz, const int3
   }
 }
 
+// The next-row variant (link_skip), for a cluster without an accepted
+// r-1/r+1 pair: the best pair skipping one row on one side, (r-2, r+1) or
+// (r-1, r+2), and failing that on both sides, (r-2, r+2) -- the smallest
+// skip first, as a further pair on a straight line is as good and would
+// break the chain.  Windows scale with the row distance and the chord
+// fraction is that of the rows involved (nested scans by one lane: the
+// clusters that need it are a minority).
+__device__ __noinline__ void nb_skip(const float2* __restrict__ yz, const int32_t* __restrict__ bin_start,
+                                     const RsParams* __restrict__ par, int rs, int row, float2 me, const KConst& kc,
+                                     PairPick& b) {
+  const int dr[3] = {-2, -1, -2}, ur[3] = {1, 2, 2};
+  for (int m = 0; m < 3; m++) {
+    if (m == 2) {  // both sides skipped: only without an accepted one-sided skip
+      if (b.d >= 0 && b.best <= kc.d_max) break;
+      b = PairPick{__int_as_float(0x7F800000), __int_as_float(0x7F800000), -1, -1};
+    }
+    const int rd = row + dr[m], ru = row + ur[m];
+    const RsParams pd = load_params(par + rs + dr[m]), pu = load_params(par + rs + ur[m]);
+    if (pd.count == 0 || pu.count == 0) continue;
+    const float xd = g_row_x[rd], x0 = g_row_x[row], xu = g_row_x[ru];
+    const float f = __fdiv_rn(__fsub_rn(x0, xd), __fsub_rn(xu, xd));
+    const float WYd = dr[m] == -2 ? kc.wy2 : kc.wy, WZd = dr[m] == -2 ? kc.wz2 : kc.wz;
+    const float WYu = ur[m] == 2 ? kc.wy2 : kc.wy, WZu = ur[m] == 2 ? kc.wz2 : kc.wz;
+    NbWin wd, wu;
+    wd.base = pd.bin_base;
+    wd.ny = pd.n_y;
+    wu.base = pu.bin_base;
+    wu.ny = pu.n_y;
+    bin_range(me.x - WYd, me.x + WYd, -g_row_yhi[rd], pd.inv_y, pd.n_y, wd.y0, wd.y1);
+    bin_range(me.y - WZd, me.y + WZd, pd.z_lo, pd.inv_z, pd.n_z, wd.z0, wd.z1);
+    bin_range(me.x - WYu, me.x + WYu, -g_row_yhi[ru], pu.inv_y, pu.n_y, wu.y0, wu.y1);
+    bin_range(me.y - WZu, me.y + WZu, pu.z_lo, pu.inv_z, pu.n_z, wu.z0, wu.z1);
+    for (int izd = wd.z0; izd <= wd.z1; izd++) {
+      const int jd = wd.base + izd * wd.ny;
+      const int a = __ldg(bin_start + jd + wd.y0), e = __ldg(bin_start + jd + wd.y1 + 1);
+      for (int d = a; d < e; d++) {
+        const float2 pdv = __ldg(yz + d);
+        if (!in_window(pdv, me, WYd, WZd)) continue;
+        for (int izu = wu.z0; izu <= wu.z1; izu++) {
+          const int ju = wu.base + izu * wu.ny;
+          const int a2 = __ldg(bin_start + ju + wu.y0), e2 = __ldg(bin_start + ju + wu.y1 + 1);
+          for (int u = a2; u < e2; u++) {
+            const float2 puv = __ldg(yz + u);
+            if (!in_window(puv, me, WYu, WZu)) continue;
+            pair_add(b, pair_dev(me, pdv, puv, f), d, u);
+          }
+        }
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restrict__ yz,
                                                            const int32_t* __restrict__ rs_of,
                                                            const RsParams* __restrict__ par,
@@ -158,6 +210,10 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
             }
           }
         }
+      }
+      if (kc.link_skip && !(b.d >= 0 && b.best <= kc.d_max) && row >= 2 && row <= NROW - 3) {
+        b = PairPick{__int_as_float(0x7F800000), __int_as_float(0x7F800000), -1, -1};
+        nb_skip(yz, bin_start, par, rs, row, __ldg(yz + c), kc, b);
       }
     }
     int32_t bu = -1, bd = -1;

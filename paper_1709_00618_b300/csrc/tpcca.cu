@@ -347,6 +347,9 @@ KConst make_kconst(const tpc_config& c, const Caps& caps) {
   k.d_max = c.d_max;
   k.wy = (float)(2.0 * ((245.8 - 85.2) / 158.0) + 0.5);
   k.wz = (float)(2.5 * ((245.8 - 85.2) / 158.0) + 0.5);
+  k.wy2 = (float)(2 * 2.0 * ((245.8 - 85.2) / 158.0) + 0.5);
+  k.wz2 = (float)(2 * 2.5 * ((245.8 - 85.2) / 158.0) + 0.5);
+  k.link_skip = c.link_skip;
   k.gate = (float)c.gate;
   for (int i = 0; i < 5; i++) k.c0[i] = (float)c.c0[i];
   k.s_max = (float)c.s_max;
@@ -513,7 +516,7 @@ int create_common(tpc_ctx** out, const tpc_config* cfg, int device, void* stream
 bool config_ok(const tpc_config& c) {
   return std::isfinite(c.bz_kg) && c.sigma > 0 && c.d_max >= 0 && c.min_chain >= 2 && c.min_chain <= NROW &&
          c.max_miss >= 1 && c.n_min_track >= 1 && c.n_min_track <= NROW && c.gate > 0 && c.s_max > 0 &&
-         c.s_max < 1 && c.fp64_updates >= 0 && c.taint_rel >= 0;
+         c.s_max < 1 && c.fp64_updates >= 0 && c.taint_rel >= 0 && (c.link_skip == 0 || c.link_skip == 1);
 }
 
 // Exclusive scan of a device-resident length; cap: an upper bound of the
@@ -858,6 +861,7 @@ int tpc_default_config(tpc_config* c) {
   c->edge = 2.0;
   c->taint_rel = 1e-4;
   c->fp64_updates = 10;
+  c->link_skip = 0;
   return TPC_OK;
 }
 

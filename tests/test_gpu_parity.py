@@ -67,6 +67,23 @@ def test_twenty_repeats_are_byte_identical(trk):
                 assert a == b, f"run {k}: {nm} differs"
 
 
+def test_link_skip_variant_parity():
+    """The next-row variant of the links (link_skip = 1 on both sides):
+    links, tracklets, follow, selection and refit against the FP64 oracle
+    run with the same setting, on the central event (plain launches) and a
+    1 ms timeframe (the graph)."""
+    import paper_1709_00618_b300 as tpc
+    cases = (("central_event", synth.central_event(seed=1).clusters, False),
+             ("timeframe_1ms", synth.timeframe(seed=2, length_ms=1.0).clusters, True))
+    for name, cl, graph in cases:
+        ref = oracle.run(cl, cfg=oracle.default_config(link_skip=1))
+        with tpc.Tracker(device=0, cfg=tpc.default_config(link_skip=1)) as t:
+            stats = full_parity(t, cl, ref, graph=graph)
+        stats["tracklets_per_track"] = len(ref["tl_start"]) / max(int(ref["n_tracks"]), 1)
+        record_stats(f"link_skip_{name}", stats)
+        assert stats["tracks_compared"] > 0.9 * stats["tracks_ref"]
+
+
 def test_timeframe_slice(trk):
     """Continuous read-out: z is the drift coordinate up to ~2.5e3 cm here."""
     ev = synth.timeframe(seed=2, length_ms=1.0)
