@@ -208,15 +208,15 @@ __global__ void k_grid_bin(const int4* __restrict__ rec_b, const RsParams* __res
   }
 }
 
-// Each record written at its place in its bin (arrival order inside the
-// bin), so that the ordering below reads every record it needs from around
-// its own position; the writes of a bucket fall inside its own range.
-__global__ void k_grid_scatter(const int4* __restrict__ rec_b, const int32_t* __restrict__ gbin,
-                               const int32_t* __restrict__ slot, const int32_t* __restrict__ bin_start,
-                               int4* __restrict__ rec, const Counts* cn) {
+// Each record's bucket position written at its place in its bin (arrival
+// order inside the bin): 4 bytes per cluster, and the writes of a bucket
+// fall inside its own range.
+__global__ void k_grid_scatter(const int32_t* __restrict__ gbin, const int32_t* __restrict__ slot,
+                               const int32_t* __restrict__ bin_start, int32_t* __restrict__ at,
+                               const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
-  for (int64_t p = gtid(); p < n; p += gstride()) rec[bin_start[gbin[p]] + slot[p]] = rec_b[p];
+  for (int64_t p = gtid(); p < n; p += gstride()) at[bin_start[gbin[p]] + slot[p]] = (int32_t)p;
 }
 
 // Stable order inside each bin: rank = number of bin members with a smaller
@@ -225,14 +225,14 @@ __global__ void k_grid_scatter(const int4* __restrict__ rec_b, const int32_t* __
 // of a record is recomputed from its position with the binning arithmetic
 // of k_grid_bin.  Also clears the cluster-to-track map (-1), which is as
 // long as the cluster list.
-__global__ void k_grid_order(const int4* __restrict__ rec, const RsParams* __restrict__ par,
-                             const int32_t* __restrict__ bin_start, int32_t* __restrict__ perm,
-                             float2* __restrict__ yz, int32_t* __restrict__ rs_of,
+__global__ void k_grid_order(const int4* __restrict__ rec_b, const int32_t* __restrict__ at,
+                             const RsParams* __restrict__ par, const int32_t* __restrict__ bin_start,
+                             int32_t* __restrict__ perm, float2* __restrict__ yz, int32_t* __restrict__ rs_of,
                              int32_t* __restrict__ cluster_track, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t p = gtid(); p < n; p += gstride()) {
-    const int4 r = rec[p];
+    const int4 r = rec_b[at[p]];
     const int i = r.x, rs = r.w;
     const float y = __int_as_float(r.y), z = __int_as_float(r.z);
     const RsParams P = load_params(par + rs);
@@ -241,7 +241,7 @@ __global__ void k_grid_order(const int4* __restrict__ rec, const RsParams* __res
                    bin_coord(y, -g_row_yhi[row], P.inv_y, P.n_y);
     const int a = bin_start[gb], b = bin_start[gb + 1];
     int rank = 0;
-    for (int q = a; q < b; q++) rank += rec[q].x < i;
+    for (int q = a; q < b; q++) rank += rec_b[at[q]].x < i;
     const int dst = a + rank;
     perm[dst] = i;
     yz[dst] = make_float2(y, z);

@@ -44,7 +44,13 @@ __global__ void k_own(const int32_t* __restrict__ f_n, const int32_t* __restrict
     if (n < kc.n_min_track) continue;
     const Key key = track_key<Key>(n, (int)t);
     const int32_t* h = hits + t * NROW;
-    for (int i = lane; i < n; i += step) key_max(owner + h[i], key);
+    // owner keys only grow, so a read through the non-coherent cache that
+    // already shows a key at least ours (possibly an older, smaller one would
+    // only cost an atomic) means this tracklet cannot win that cluster
+    for (int i = lane; i < n; i += step) {
+      Key* o = owner + h[i];
+      if (__ldg(o) < key) key_max(o, key);
+    }
   }
 }
 

@@ -598,9 +598,9 @@ void enqueue_find(tpc_ctx* ctx) {
                                ctx->ptr<int32_t>(L.slot), cn);
   LenSrc lb{&cn->n_bins, 0, 0};
   scan(ctx, bin_cnt, bin_start, lb, nullptr);
-  k_grid_scatter<<<gN, bc, 0, s>>>(rec_b, ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
-                                   ctx->ptr<int4>(L.tmp), cn);
-  k_grid_order<<<gN, bc, 0, s>>>(ctx->ptr<int4>(L.tmp), ctx->ptr<RsParams>(L.par), bin_start,
+  k_grid_scatter<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
+                                   ctx->ptr<int32_t>(L.tmp), cn);
+  k_grid_order<<<gN, bc, 0, s>>>(rec_b, ctx->ptr<int32_t>(L.tmp), ctx->ptr<RsParams>(L.par), bin_start,
                                  ctx->ptr<int32_t>(L.perm), ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
                                  ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(1);
