@@ -211,10 +211,6 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
           }
         }
       }
-      if (kc.link_skip && !(b.d >= 0 && b.best <= kc.d_max) && row >= 2 && row <= NROW - 3) {
-        b = PairPick{__int_as_float(0x7F800000), __int_as_float(0x7F800000), -1, -1};
-        nb_skip(yz, bin_start, par, rs, row, __ldg(yz + c), kc, b);
-      }
     }
     int32_t bu = -1, bd = -1;
     uint8_t tflag = 0;
@@ -229,6 +225,32 @@ __global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restr
     up[c] = bu;
     dn[c] = bd;
     tie[c] = tflag;
+  }
+}
+
+// The next-row variant's second pass (launched only with link_skip): every
+// cluster on rows 2..156 that k_neighbours left without an accepted pair.
+__global__ void k_neighbours_skip(const float2* __restrict__ yz, const int32_t* __restrict__ rs_of,
+                                  const RsParams* __restrict__ par, const int32_t* __restrict__ bin_start, KConst kc,
+                                  int32_t* __restrict__ up, int32_t* __restrict__ dn, uint8_t* __restrict__ tie,
+                                  const Counts* cn) {
+  if (fatal(cn)) return;
+  const int64_t n = cn->n;
+  for (int64_t c = gtid(); c < n; c += gstride()) {
+    if (up[c] >= 0) continue;
+    const int rs = __ldg(rs_of + c);
+    const int row = rs % NROW;
+    if (row < 2 || row > NROW - 3) continue;
+    PairPick b{__int_as_float(0x7F800000), __int_as_float(0x7F800000), -1, -1};
+    nb_skip(yz, bin_start, par, rs, row, __ldg(yz + c), kc, b);
+    if (b.d >= 0 && b.best <= kc.d_max) {
+      up[c] = b.u;
+      dn[c] = b.d;
+      tie[c] = (b.second != __int_as_float(0x7F800000) &&
+                fabsf(__fsub_rn(b.second, b.best)) <= __fmul_rn(1e-6f, fmaxf(b.best, 1e-12f)))
+                   ? 1
+                   : 0;
+    }
   }
 }
 

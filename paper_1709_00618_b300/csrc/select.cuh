@@ -59,13 +59,48 @@ __global__ void k_own(const int32_t* __restrict__ f_n, const int32_t* __restrict
 // owned row range (r_in | r_out << 16), so that the refit and the output
 // stage need no ownership loads.
 constexpr int OWN_WORDS = 5;
-template <typename Key>
+// W: one warp per tracklet, lanes over its hits (below 4 Mi clusters);
+// else one thread per tracklet, so that a warp's loads of hit i of 32
+// consecutive tracklets fall on one row, close together (as k_own).
+template <bool W, typename Key>
 __global__ void k_keep(const int32_t* __restrict__ f_n, const int32_t* __restrict__ hits,
                        const uint8_t* __restrict__ hrow, const Key* __restrict__ owner, KConst kc,
                        int32_t* __restrict__ keep, int32_t* __restrict__ nown, uint32_t* __restrict__ own_mask,
                        int32_t* __restrict__ own_rng, const Counts* cn) {
   if (fatal(cn)) return;
   const int32_t T = cn->n_tracklets;
+  if (!W) {
+    for (int64_t t = gtid(); t < T; t += gstride()) {
+      const int n = f_n[t];
+      int kept = 0;
+      unsigned r_in = NROW, r_out = 0;
+      if (n >= kc.n_min_track) {
+        const Key key = track_key<Key>(n, (int)t);
+        const int32_t* h = hits + t * NROW;
+        const uint8_t* hr = hrow + t * NROW;
+        uint32_t* m = own_mask + t * OWN_WORDS;
+        for (int w = 0; w < OWN_WORDS; w++) {  // 32 hit slots per mask word
+          uint32_t word = 0;
+          const int i1 = min(n, 32 * (w + 1));
+          for (int i = 32 * w; i < i1; i++) {
+            if (__ldg(owner + h[i]) == key) {
+              word |= 1u << (i & 31);
+              kept++;
+              const unsigned r = hr[i];
+              r_in = min(r_in, r);
+              r_out = max(r_out, r + 1);
+            }
+          }
+          m[w] = word;
+        }
+      }
+      const int k = kept >= kc.n_min_track;
+      keep[t] = k;
+      nown[t] = k ? kept : 0;
+      if (k) own_rng[t] = (int)r_in | (((int)r_out - 1) << 16);
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
   for (int64_t t = gtid() >> 5; t < T; t += gstride() >> 5) {  // one warp per tracklet, lanes over hits
     const int n = f_n[t];

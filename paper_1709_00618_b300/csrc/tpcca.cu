@@ -608,6 +608,10 @@ void enqueue_find(tpc_ctx* ctx) {
   k_neighbours<<<grid_for(ctx, C.n, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
                                   bin_start, ctx->kc, ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn),
                                   ctx->ptr<uint8_t>(L.tie), cn);
+  if (ctx->cfg.link_skip)
+    k_neighbours_skip<<<gN, bc, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
+                                        ctx->ptr<RsParams>(L.par), bin_start, ctx->kc, ctx->ptr<int32_t>(L.up),
+                                        ctx->ptr<int32_t>(L.dn), ctx->ptr<uint8_t>(L.tie), cn);
   ctx->mark(2);
   // a4 + a5
   // chain starts flagged in k_clean, listed in sorted order; one walk per
@@ -679,7 +683,8 @@ void enqueue_find(tpc_ctx* ctx) {
     uint32_t* owner = ctx->ptr<uint32_t>(L.owner);
     (warp_sel ? k_own<true, uint32_t> : k_own<false, uint32_t>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(
         ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, owner, cn);
-    k_keep<uint32_t><<<gTw, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits),
+    (warp_sel ? k_keep<true, uint32_t> : k_keep<false, uint32_t>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(
+                                        ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits),
                                         ctx->ptr<uint8_t>(L.hrow), owner, ctx->kc, ctx->ptr<int32_t>(L.keep),
                                         ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask),
                                         ctx->ptr<int32_t>(L.own_rng), cn);
@@ -687,7 +692,8 @@ void enqueue_find(tpc_ctx* ctx) {
     uint64_t* owner = ctx->ptr<uint64_t>(L.owner);
     (warp_sel ? k_own<true, uint64_t> : k_own<false, uint64_t>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(
         ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits), ctx->kc, owner, cn);
-    k_keep<uint64_t><<<gTw, bc, 0, s>>>(ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits),
+    (warp_sel ? k_keep<true, uint64_t> : k_keep<false, uint64_t>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(
+                                        ctx->ptr<int32_t>(L.f_n), ctx->ptr<int32_t>(L.hits),
                                         ctx->ptr<uint8_t>(L.hrow), owner, ctx->kc, ctx->ptr<int32_t>(L.keep),
                                         ctx->ptr<int32_t>(L.nown), ctx->ptr<uint32_t>(L.own_mask),
                                         ctx->ptr<int32_t>(L.own_rng), cn);
