@@ -53,9 +53,12 @@ __global__ void k_grid_count(const tpc_cluster* __restrict__ in, const int64_t* 
     int rs = (q * NSEC + (int)sec) * NROW + (int)row;
     rs_in[i] = rs;
     atomicAdd(&cnt[rs], 1);
-    uint32_t zo = f2ord(z);
-    atomicMin(&zmin[rs], zo);
-    atomicMax(&zmax[rs], zo);
+    // the range only widens, so a read (through the non-coherent cache:
+    // possibly an older, wider value, which costs only an atomic) already
+    // inside it means the cluster cannot move that bound
+    const uint32_t zo = f2ord(z);
+    if (zo < __ldg(zmin + rs)) atomicMin(&zmin[rs], zo);
+    if (zo > __ldg(zmax + rs)) atomicMax(&zmax[rs], zo);
   }
 }
 
@@ -190,6 +193,8 @@ __global__ void k_grid_bucket(const tpc_cluster* __restrict__ in, const int32_t*
 
 // Level two, in bucket order: the global bin of every record and its
 // (arrival-order) slot in that bin.
+// Level two, in bucket order: the global bin of every record and its
+// (arrival-order) slot in that bin.
 __global__ void k_grid_bin(const int4* __restrict__ rec_b, const RsParams* __restrict__ par,
                            int32_t* __restrict__ bin_cnt, int32_t* __restrict__ gbin, int32_t* __restrict__ slot,
                            const Counts* cn) {
@@ -208,31 +213,33 @@ __global__ void k_grid_bin(const int4* __restrict__ rec_b, const RsParams* __res
   }
 }
 
-// Each record's bucket position written at its place in its bin (arrival
-// order inside the bin): 4 bytes per cluster, and the writes of a bucket
-// fall inside its own range.
-__global__ void k_grid_scatter(const int32_t* __restrict__ gbin, const int32_t* __restrict__ slot,
-                               const int32_t* __restrict__ bin_start, int32_t* __restrict__ at,
-                               const Counts* cn) {
+// Each record moved to its place in its bin (arrival order inside the bin):
+// the writes of a bucket fall inside its own range of the sorted array, so
+// they gather in L2 into whole lines.
+__global__ void k_grid_scatter(const int4* __restrict__ rec_b, const int32_t* __restrict__ gbin,
+                               const int32_t* __restrict__ slot, const int32_t* __restrict__ bin_start,
+                               int4* __restrict__ rec_s, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
-  for (int64_t p = gtid(); p < n; p += gstride()) at[bin_start[gbin[p]] + slot[p]] = (int32_t)p;
+  for (int64_t p = gtid(); p < n; p += gstride()) rec_s[bin_start[gbin[p]] + slot[p]] = rec_b[p];
 }
 
-// Stable order inside each bin: rank = number of bin members with a smaller
-// load index.  Bins hold about two clusters on average (the bin edge is
-// sqrt(2 A / n)); the count is quadratic only in the fullest bin.  The bin
-// of a record is recomputed from its position with the binning arithmetic
-// of k_grid_bin.  Also clears the cluster-to-track map (-1), which is as
-// long as the cluster list.
-__global__ void k_grid_order(const int4* __restrict__ rec_b, const int32_t* __restrict__ at,
-                             const RsParams* __restrict__ par, const int32_t* __restrict__ bin_start,
-                             int32_t* __restrict__ perm, float2* __restrict__ yz, int32_t* __restrict__ rs_of,
+// Stable order inside each bin: the record at sorted position p goes to
+// a + rank, a the bin's first position and rank the number of bin members
+// with a smaller load index.  Bins hold about two clusters on average (the
+// bin edge is sqrt(2 A / n)), and the members sit next to p, so the count
+// reads the lines that neighbouring threads read anyway; it is quadratic
+// only in the fullest bin.  The bin of a record is recomputed with the
+// binning arithmetic of k_grid_bin.  Also clears the cluster-to-track map
+// (-1), which is as long as the cluster list.
+__global__ void k_grid_order(const int4* __restrict__ rec_s, const RsParams* __restrict__ par,
+                             const int32_t* __restrict__ bin_start, int32_t* __restrict__ perm,
+                             float2* __restrict__ yz, int32_t* __restrict__ rs_of,
                              int32_t* __restrict__ cluster_track, const Counts* cn) {
   if (fatal(cn)) return;
   const int64_t n = cn->n;
   for (int64_t p = gtid(); p < n; p += gstride()) {
-    const int4 r = rec_b[at[p]];
+    const int4 r = rec_s[p];
     const int i = r.x, rs = r.w;
     const float y = __int_as_float(r.y), z = __int_as_float(r.z);
     const RsParams P = load_params(par + rs);
@@ -241,7 +248,7 @@ __global__ void k_grid_order(const int4* __restrict__ rec_b, const int32_t* __re
                    bin_coord(y, -g_row_yhi[row], P.inv_y, P.n_y);
     const int a = bin_start[gb], b = bin_start[gb + 1];
     int rank = 0;
-    for (int q = a; q < b; q++) rank += rec_b[at[q]].x < i;
+    for (int q = a; q < b; q++) rank += __ldg(&rec_s[q].x) < i;
     const int dst = a + rank;
     perm[dst] = i;
     yz[dst] = make_float2(y, z);

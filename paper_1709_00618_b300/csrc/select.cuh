@@ -28,6 +28,10 @@ __device__ __forceinline__ void key_max(uint64_t* a, uint64_t k) {
 }
 __device__ __forceinline__ void key_max(uint32_t* a, uint32_t k) { atomicMax((unsigned int*)a, (unsigned int)k); }
 
+// Hits a thread-per-tracklet selection kernel (k_keep, k_assign) loads at
+// once: SEL_BATCH independent loads in flight instead of one dependent chain.
+constexpr int SEL_BATCH = 8;
+
 // owner[c] = max key over the tracklets holding c.  W: one warp per
 // tracklet, the lanes over its hits (coalesced hit loads, 32 atomics in
 // flight; faster while the owner array is L2-resident); else one thread per
@@ -82,13 +86,23 @@ __global__ void k_keep(const int32_t* __restrict__ f_n, const int32_t* __restric
         for (int w = 0; w < OWN_WORDS; w++) {  // 32 hit slots per mask word
           uint32_t word = 0;
           const int i1 = min(n, 32 * (w + 1));
-          for (int i = 32 * w; i < i1; i++) {
-            if (__ldg(owner + h[i]) == key) {
-              word |= 1u << (i & 31);
-              kept++;
-              const unsigned r = hr[i];
-              r_in = min(r_in, r);
-              r_out = max(r_out, r + 1);
+          for (int i0 = 32 * w; i0 < i1; i0 += SEL_BATCH) {  // SEL_BATCH keys in flight, as k_own
+            int c[SEL_BATCH];
+            bool own[SEL_BATCH];
+#pragma unroll
+            for (int k = 0; k < SEL_BATCH; k++) c[k] = i0 + k < i1 ? h[i0 + k] : -1;
+#pragma unroll
+            for (int k = 0; k < SEL_BATCH; k++) own[k] = c[k] >= 0 && __ldg(owner + c[k]) == key;
+#pragma unroll
+            for (int k = 0; k < SEL_BATCH; k++) {
+              if (own[k]) {
+                const int i = i0 + k;
+                word |= 1u << (i & 31);
+                kept++;
+                const unsigned r = hr[i];
+                r_in = min(r_in, r);
+                r_out = max(r_out, r + 1);
+              }
             }
           }
           m[w] = word;
@@ -199,13 +213,25 @@ __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restr
         const int i = i0 + lane;
         if (i < n && ((word >> lane) & 1u)) cluster_track[__ldg(perm + h[i])] = idx;
       }
-    } else {
+    } else {  // SEL_BATCH owned hits at a time: their indices, then their load-order positions
       for (int w = 0; w < OWN_WORDS; w++) {
         uint32_t word = own_mask[t * OWN_WORDS + w];
         while (word) {
-          const int b = __ffs(word) - 1;
-          word &= word - 1;
-          cluster_track[__ldg(perm + h[w * 32 + b])] = idx;
+          int c[SEL_BATCH];
+#pragma unroll
+          for (int k = 0; k < SEL_BATCH; k++) {
+            c[k] = -1;
+            if (word) {
+              c[k] = h[w * 32 + __ffs(word) - 1];
+              word &= word - 1;
+            }
+          }
+          int d[SEL_BATCH];
+#pragma unroll
+          for (int k = 0; k < SEL_BATCH; k++) d[k] = c[k] >= 0 ? __ldg(perm + c[k]) : -1;
+#pragma unroll
+          for (int k = 0; k < SEL_BATCH; k++)
+            if (d[k] >= 0) cluster_track[d[k]] = idx;
         }
       }
     }

@@ -404,6 +404,13 @@ int grid_for(const tpc_ctx* ctx, int64_t items, int threads, int per_sm = 16) {
   return (int)std::max<int64_t>(1, std::min(b, cap));
 }
 
+// One item per thread, all items in one grid.  For items of uneven work
+// (tracklets of 10 to 159 hits) a block ends with its own items and the next
+// one starts, where a grid-stride loop would keep every block to its
+// slowest thread per stride; for uniform items the capped grid's
+// grid-stride loop is faster (no block launch per 256 items).
+int grid_lin(int64_t items, int threads) { return (int)std::max<int64_t>(1, (items + threads - 1) / threads); }
+
 int do_reserve(tpc_ctx* ctx, const Caps& want) {
   Caps c = ctx->caps;
   bool grow = want.n > c.n || want.req > c.req || want.bins > c.bins || want.tl > c.tl || want.tracks > c.tracks ||
@@ -568,7 +575,7 @@ void enqueue_find(tpc_ctx* ctx) {
   Counts* cn = ctx->ptr<Counts>(L.counts);
   const int bc = ctx->block_clusters;
   const int gN = grid_for(ctx, C.n, bc), gR = grid_for(ctx, C.nrs(), bc);
-  const int gT = grid_for(ctx, C.tl, bc);
+  int gT = grid_for(ctx, C.tl, bc);
   const int gTw = grid_for(ctx, C.tl * 32, bc);  // warp-per-tracklet kernels
   int32_t* rs_cnt = ctx->ptr<int32_t>(L.rs_cnt);
   int32_t* nbins = ctx->ptr<int32_t>(L.nbins);
@@ -598,10 +605,13 @@ void enqueue_find(tpc_ctx* ctx) {
                                ctx->ptr<int32_t>(L.slot), cn);
   LenSrc lb{&cn->n_bins, 0, 0};
   scan(ctx, bin_cnt, bin_start, lb, nullptr);
-  k_grid_scatter<<<gN, bc, 0, s>>>(ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start,
-                                   ctx->ptr<int32_t>(L.tmp), cn);
-  k_grid_order<<<gN, bc, 0, s>>>(rec_b, ctx->ptr<int32_t>(L.tmp), ctx->ptr<RsParams>(L.par), bin_start,
-                                 ctx->ptr<int32_t>(L.perm), ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
+  int4* rec_s = ctx->ptr<int4>(L.tmp);  // the records in (row-sector, bin) order, arrival order in a bin
+  // (one record per thread: measured faster for these 16-byte scattered
+  // writes than the capped grid)
+  k_grid_scatter<<<grid_lin(C.n, bc), bc, 0, s>>>(rec_b, ctx->ptr<int32_t>(L.gbin), ctx->ptr<int32_t>(L.slot), bin_start, rec_s,
+                                   cn);
+  k_grid_order<<<gN, bc, 0, s>>>(rec_s, ctx->ptr<RsParams>(L.par), bin_start, ctx->ptr<int32_t>(L.perm),
+                                 ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
                                  ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(1);
   // a3 neighbours
@@ -679,6 +689,7 @@ void enqueue_find(tpc_ctx* ctx) {
   ctx->mark(4);
   // a7 selection
   const bool warp_sel = ctx->n < kLargeBatch;  // warp per tracklet while the owner array stays in L2
+  if (!warp_sel) gT = grid_lin(C.tl, bc);  // thread per tracklet: one tracklet per thread
   if (key32(ctx)) {
     uint32_t* owner = ctx->ptr<uint32_t>(L.owner);
     (warp_sel ? k_own<true, uint32_t> : k_own<false, uint32_t>)<<<warp_sel ? gTw : gT, bc, 0, s>>>(
