@@ -55,7 +55,7 @@ struct Counts {
   uint32_t status;    // ST_* bits
   int32_t n_track_clusters;
   int32_t n32;         // clusters as int32 (length source of the per-cluster scans)
-  int32_t work_next[12];  // work counters of the persistent Kalman kernels, [PH_* x chunk]
+  int32_t work_next[14];  // work counters of the persistent Kalman kernels, [fetch phase x chunk]
   // work counters of the follow (a6) and refit (a8) kernels
   unsigned long long n_prop;    // helix propagations with covariance transport
   unsigned long long n_upd32;   // FP32 Kalman updates
@@ -71,11 +71,19 @@ struct Counts {
 
 // Kalman kernels, in launch order, for the per-kernel work counters.
 enum { PH_FOLLOW_P1 = 0, PH_FOLLOW_P2, PH_FOLLOW_P3, PH_FOLLOW_P4, PH_REFIT_P1, PH_REFIT_P2, PH_COUNT };
+// Phase 4r fetches its tracklets with a counter of its own; its work is
+// tallied with phase 4 (the backward pass's binary32 part).
+constexpr int PH_FOLLOW_P4R = PH_COUNT;
+constexpr int PH_FETCH = PH_COUNT + 1;  // work counters per chunk
 
 // The Kalman stage may split its items into chunks whose zone and FP32
 // kernels run concurrently on two streams (the FP64 pipe of one chunk's
 // zone beside the other's FP32 work); chunk c of nc covers [begin, end).
 constexpr int MAX_CHUNKS = 2;
+static_assert(PH_FETCH * MAX_CHUNKS <= (int)(sizeof(((Counts*)nullptr)->work_next) / sizeof(int32_t)),
+              "a work counter per Kalman kernel and chunk");
+static_assert(PH_COUNT <= (int)(sizeof(((Counts*)nullptr)->phase_work) / sizeof(((Counts*)nullptr)->phase_work[0])),
+              "tallies per Kalman kernel");
 struct Chunk {
   int32_t begin, end;
 };

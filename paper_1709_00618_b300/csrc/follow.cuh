@@ -176,10 +176,11 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
 // snapshot in shared memory (out_put), since in registers it made the
 // large-input build (72 registers) spill.
 constexpr int SNAP_STRIDE = 128;  // the largest block of the follow kernels
-// Shared-memory output slot of a phase-4 lane (word i at so[i * SNAP_STRIDE]):
-// row, y, z, sin phi, dz/ds_T, q/pT (the compensated sums), zref, the 15
-// covariance entries, the chi2 total (two words) and its binary32 part.
-constexpr int OUT_WORDS = 25;
+constexpr int OUT_WORDS = 25;     // words of a lane's output snapshot (out_put)
+// Shared-memory output slot of a phase-4 lane (word i at so[i * SNAP_STRIDE],
+// OUT_WORDS words): row, y, z, sin phi, dz/ds_T, q/pT (the compensated
+// sums), zref, the 15 covariance entries, the chi2 total (two words) and its
+// binary32 part.
 __device__ __forceinline__ void out_put(float* so, const TrkState& p, const float* C, const Chi2Acc& chi2) {
   so[0] = __int_as_float(p.row);
   so[1 * SNAP_STRIDE] = p.y + p.yl;
@@ -304,8 +305,14 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
   return true;
 }
 
-// One backward row step; false ends the pass.
-template <bool Z>
+// One backward row step; false ends the pass.  Rows r >= r0 refit the
+// forward clusters (an update where a forward cluster sits), rows below
+// extend the tracklet inward with the gated pick-up.  M: BW_ANY takes both
+// kinds of step; BW_REFIT is only ever called for a refit row (phase 4r) and
+// BW_EXTEND only for an extension row (phase 4, after phase 4r), so each of
+// those kernels carries one kind's code.
+enum { BW_ANY = 0, BW_REFIT, BW_EXTEND };
+template <bool Z, int M = BW_ANY>
 __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, const float* sX, const float* sYH,
                                          Lane& w, TrkState& p, double* D, float* C, Chi2Acc& chi2, LocalTally& tl,
                                          double* snap, float* so) {
@@ -314,13 +321,13 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
   if (r >= 1 && r - 1 < w.r0) prefetch_l1(g.par + w.ubase + r - 1);  // the next step's row-sector parameters
   const bool zone = Z && w.nupd < w.zend;
   if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
-    if (r >= w.r0) w.flags |= TF_BACK_FAIL;
+    if (M == BW_REFIT || (M == BW_ANY && r >= w.r0)) w.flags |= TF_BACK_FAIL;
     return false;
   }
   tl.prop++;
   tl.prop64 += zone;
   float2 P;
-  if (r >= w.r0) {
+  if (M == BW_REFIT || (M == BW_ANY && r >= w.r0)) {
     if (w.nx_row != r) return true;
     P = w.nx_yz;
     w.kf--;
@@ -357,7 +364,9 @@ struct FollowWork {
   float C[15];
   Chi2Acc chi2;
   int32_t go;
-  int32_t pad[3];
+  int32_t out_ok;          // phase 4r left the output snapshot in out
+  int32_t pad[2];
+  float out[OUT_WORDS];    // the backward pass's output snapshot, as out_put lays it out
 };
 
 __device__ __forceinline__ void work_store(FollowWork* W, int64_t t, const Lane& w, const TrkState& p,
@@ -369,6 +378,7 @@ __device__ __forceinline__ void work_store(FollowWork* W, int64_t t, const Lane&
   for (int i = 0; i < 15; i++) s.C[i] = C[i];
   s.chi2 = chi2;
   s.go = go;
+  s.out_ok = 0;
 }
 __device__ __forceinline__ bool work_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
                                           Chi2Acc& chi2) {
@@ -433,7 +443,10 @@ __device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w
   w.flags = s.w.flags;
   w.seed_fail = s.w.seed_fail;
   w.tr = s.w.tr;
-  {
+  if (s.out_ok) {
+#pragma unroll
+    for (int i = 0; i < OUT_WORDS; i++) so[i * SNAP_STRIDE] = s.out[i];
+  } else {
     float sc[15];
 #pragma unroll
     for (int i = 0; i < 15; i++) sc[i] = s.w.sC[i];
@@ -444,6 +457,28 @@ __device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w
   for (int i = 0; i < 15; i++) C[i] = s.C[i];
   chi2 = s.chi2;
   return s.go != 0;
+}
+
+// Phase 4r parks what its refit steps changed for phase 4: the running
+// state, covariance and chi2, the forward-hit cursor, the flags, whether the
+// pass goes on, and the output snapshot (left in out, marked by out_ok).
+__device__ __forceinline__ void bwd_store(FollowWork* W, int64_t t, const Lane& w, const TrkState& p,
+                                          const float* C, const Chi2Acc& chi2, const float* so, bool go) {
+  FollowWork& s = W[t];
+  s.w.kf = w.kf;
+  s.w.nupd = w.nupd;
+  s.w.nx_row = w.nx_row;
+  s.w.nx_c = w.nx_c;
+  s.w.nx_yz = w.nx_yz;
+  s.w.flags = w.flags;
+  s.p = p;
+#pragma unroll
+  for (int i = 0; i < 15; i++) s.C[i] = C[i];
+  s.chi2 = chi2;
+  s.go = go;
+#pragma unroll
+  for (int i = 0; i < OUT_WORDS; i++) s.out[i] = so[i * SNAP_STRIDE];
+  s.out_ok = 1;
 }
 
 // Work distribution of the persistent Kalman kernels: the lanes in `need`,
@@ -674,6 +709,68 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
   tl.flush(cn, PH_FOLLOW_P3);
 }
 
+// Phase 4r: the binary32 refit of the forward clusters below the FP64 zone
+// (rows from the zone's end down to the chain's first row r0; an update
+// wherever a forward cluster sits).  Apart from phase 4 its warps take no
+// candidate searches, so their lanes step together; phase 4 takes the
+// inward extension below r0.  Lanes refill as in phase 2; a tracklet whose
+// refit rows are done (or whose pass ended) is parked again only if it
+// advanced.
+template <int MINB>
+__global__ void __launch_bounds__(128, MINB) k_follow_p4r(GridView g, KConst kc, FollowOut o, FollowWork* W,
+                                                    const int32_t* __restrict__ order, int chunk, int nchunk,
+                                                    Counts* cn) {
+  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  __shared__ float sOut[OUT_WORDS * SNAP_STRIDE];
+  load_tables(sX, sYH);
+  if (fatal(cn)) return;
+  float* so = sOut + threadIdx.x;
+  const int32_t T = cn->n_tracklets;
+  const Chunk ch = chunk_range(T, chunk, nchunk);
+  LocalTally tl;
+  double D[15];  // unused in this phase (the zone is over)
+  float C[15];
+  Lane w;
+  TrkState p;
+  Chi2Acc chi2;
+  chi2.reset();
+  int64_t t = -1;
+  bool go = false;     // the lane's tracklet has refit rows left
+  bool pass = false;   // its backward pass goes on
+  bool live = true;
+  bool dirty = false;
+  for (;;) {
+    const unsigned need = refill_mask(live && !go, go, kc.refill);
+    if (need & (1u << (threadIdx.x & 31))) {
+      if (dirty) bwd_store(W, t, w, p, C, chi2, so, pass);
+      const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_FOLLOW_P4R, chunk), need);
+      t = idx < ch.end ? (order ? order[idx] : idx) : T;
+      dirty = false;
+      if (t < T) {
+        pass = bwd_load(W, t, w, p, C, chi2, so);
+        w.hits = o.hits + t * NROW;
+        w.hrow = o.hrow + t * NROW;
+        w.cn = cn;
+        go = pass && p.row > w.r0;
+      } else {
+        live = false;
+      }
+    }
+    if (!__any_sync(FULL_MASK, go)) {
+      if (!__any_sync(FULL_MASK, live)) break;
+      continue;
+    }
+    if (go) {
+      for (int k = 0; k < max(kc.inner_steps, 1) && go; k++) {
+        pass = bwd_step<false, BW_REFIT>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr, so);
+        go = pass && p.row > w.r0;
+      }
+      dirty = true;
+    }
+  }
+  tl.flush(cn, PH_FOLLOW_P4);
+}
+
 // Output of one tracklet from its phase-4 slot (out_put).
 __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t t, const Lane& w, float zref0,
                                                     const float* so) {
@@ -707,8 +804,9 @@ __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t 
   o.chi2[t] = c.value();
 }
 
-// Phase 4: the rest of the backward pass (FP32, lanes refill as in phase
-// 2) and the outputs.
+// Phase 4: the rest of the backward pass, the inward extension below the
+// chain's first row (FP32, lanes refill as in phase 2; phase 4r has made
+// every refit row), and the outputs.
 template <int MINB>
 __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
@@ -749,7 +847,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
       continue;
     }
     for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
-      go = bwd_step<false>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr, so);
+      go = bwd_step<false, BW_EXTEND>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr, so);
   }
   tl.flush(cn, PH_FOLLOW_P4);
 }

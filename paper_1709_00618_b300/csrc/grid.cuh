@@ -24,7 +24,16 @@ __device__ __forceinline__ int find_request(const int64_t* __restrict__ off, int
 
 __global__ void k_rs_init(int32_t* __restrict__ cnt, uint32_t* __restrict__ zmin, uint32_t* __restrict__ zmax,
                           int32_t* __restrict__ obins, Counts* cn) {
-  if (gtid() < PH_COUNT) cn->work_next[gtid()] = 0;  // work counters of the Kalman kernels
+  // Per-run scalars: a run on the same loaded batch (a second tpc_find_tracks,
+  // a graph replay, the autotuner's trials) starts from the state a load
+  // leaves.  Work counters of every Kalman kernel and chunk, status, tallies.
+  if (gtid() < PH_FETCH * MAX_CHUNKS) cn->work_next[gtid()] = 0;
+  if (gtid() < PH_COUNT * 5) (&cn->phase_work[0][0])[gtid()] = 0ull;
+  if (gtid() == 0) {
+    cn->status = 0u;
+    cn->n_prop = cn->n_upd32 = cn->n_upd64 = cn->n_cand = cn->n_prop64 = 0ull;
+    cn->trace_n = 0;
+  }
   for (int64_t i = gtid(); i < ORD_WORDS; i += gstride()) obins[i] = 0;  // their work-order histograms
   int32_t nrs = cn->n_rs;
   for (int64_t i = gtid(); i < nrs; i += gstride()) {

@@ -643,7 +643,7 @@ void enqueue_find(tpc_ctx* ctx) {
                                        ctx->ptr<int32_t>(L.tl_end), cn, C.tl);
   ctx->mark(3);
   // a6 follow: per chunk, zone (p1) -> order -> FP32 (p2) -> zone (p3) ->
-  // order -> FP32 (p4).  With two chunks the second runs on the auxiliary
+  // order -> FP32 refit rows (p4r) -> FP32 extension and outputs (p4).  With two chunks the second runs on the auxiliary
   // stream one kernel behind the first, so that one chunk's FP64 zone shares
   // the SMs with the other's FP32 phase.
   {
@@ -672,6 +672,9 @@ void enqueue_find(tpc_ctx* ctx) {
       if (longest_first)
         k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(2);
+      auto p4r = ctx->n >= kLargeBatch ? k_follow_p4r<7> : k_follow_p4r<4>;
+      p4r<<<persistent_grid(ctx, p4r, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
+          grid_view(ctx), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
       auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<7> : k_follow_p4<4>;
       p4<<<persistent_grid(ctx, p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, order, c, nc, cn);

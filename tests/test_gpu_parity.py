@@ -67,6 +67,30 @@ def test_twenty_repeats_are_byte_identical(trk):
                 assert a == b, f"run {k}: {nm} differs"
 
 
+def test_rerun_without_reload_repeats_every_kernel(trk):
+    """A second find + fit on the same loaded batch (as the autotuner's
+    trials and repeated tpc_find_tracks calls make) starts from the state of
+    a load: every Kalman kernel does the same work again (its work counter
+    and tallies are reset per run) and the results are the same bytes."""
+    ev = synth.central_event(seed=1)
+    trk.load(ev.clusters)
+    runs = []
+    for k in range(3):
+        if k < 2:
+            trk.find().fit()
+        else:
+            trk.run_graph()
+        trk.sync()
+        tracks, ct, _ = trk.get()
+        runs.append((trk.kalman_profile(times=False), trk.work(), tracks.tobytes(), ct.tobytes()))
+    for name, w in runs[0][0].items():
+        assert w["prop"] > 0 or name in ("k_follow_p2",), name
+    for prof, work, tb, cb in runs[1:]:
+        assert prof == runs[0][0]
+        assert work == runs[0][1]
+        assert tb == runs[0][2] and cb == runs[0][3]
+
+
 def test_link_skip_variant_parity():
     """The next-row variant of the links (link_skip = 1 on both sides):
     links, tracklets, follow, selection and refit against the FP64 oracle
