@@ -120,13 +120,9 @@ struct Lane {
   uint32_t flags;
   bool seed_fail;
   bool tr;       // this tracklet is traced
-  bool snap;     // backward zone: sC is pending in the FP64 snapshot (zone_snap_take)
+  bool snap;     // backward zone: the output covariance is pending in the FP64 snapshot (zone_snap_take)
   Counts* cn;
   TrkState fwd;  // forward state after its last update
-  // backward output: state after the last update
-  TrkState sp;
-  float sC[15];
-  Chi2Acc schi2;
 };
 
 // Loads forward hit kf for the backward refit, one step before its use.
@@ -167,21 +163,21 @@ __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState&
                (float)chi2.value(), r0, r1);
 }
 
-// Output snapshot of the backward pass: the state after its last update.
-// Phase 3 keeps it in the lane, which it parks for phase 4; inside the FP64
-// zone the covariance is kept as FP64 in shared memory (element i of a lane
-// at snap[i * SNAP_STRIDE]) and rounded to binary32 once, by zone_snap_take,
-// instead of at every update: the FP64 pipe, which bounds the zone, then does
-// no conversions for updates that a later one replaces.  Phase 4 keeps the
-// snapshot in shared memory (out_put), since in registers it made the
-// large-input build (72 registers) spill.
+// Output snapshot of the backward pass: the state after its last update,
+// kept in the lane's shared-memory output slot (out_put) by every backward
+// kernel and parked with the tracklet between them (FollowWork::out), so
+// that it takes no registers.  Inside the FP64 zone the covariance is kept
+// as FP64 in shared memory (element i of a lane at snap[i * SNAP_STRIDE]) and
+// rounded to binary32 into the slot once, by zone_snap_take, instead of at
+// every update: the FP64 pipe, which bounds the zone, then does no
+// conversions for updates that a later one replaces.
 constexpr int SNAP_STRIDE = 128;  // the largest block of the follow kernels
 constexpr int OUT_WORDS = 25;     // words of a lane's output snapshot (out_put)
 // Shared-memory output slot of a phase-4 lane (word i at so[i * SNAP_STRIDE],
 // OUT_WORDS words): row, y, z, sin phi, dz/ds_T, q/pT (the compensated
 // sums), zref, the 15 covariance entries, the chi2 total (two words) and its
 // binary32 part.
-__device__ __forceinline__ void out_put(float* so, const TrkState& p, const float* C, const Chi2Acc& chi2) {
+__device__ __forceinline__ void out_put_state(float* so, const TrkState& p, const Chi2Acc& chi2) {
   so[0] = __int_as_float(p.row);
   so[1 * SNAP_STRIDE] = p.y + p.yl;
   so[2 * SNAP_STRIDE] = p.z + p.zl;
@@ -189,11 +185,14 @@ __device__ __forceinline__ void out_put(float* so, const TrkState& p, const floa
   so[4 * SNAP_STRIDE] = p.t;
   so[5 * SNAP_STRIDE] = p.q;
   so[6 * SNAP_STRIDE] = p.zref;
-#pragma unroll
-  for (int i = 0; i < 15; i++) so[(7 + i) * SNAP_STRIDE] = C[i];
   so[22 * SNAP_STRIDE] = __int_as_float(__double2hiint(chi2.total));
   so[23 * SNAP_STRIDE] = __int_as_float(__double2loint(chi2.total));
   so[24 * SNAP_STRIDE] = chi2.part;
+}
+__device__ __forceinline__ void out_put(float* so, const TrkState& p, const float* C, const Chi2Acc& chi2) {
+  out_put_state(so, p, chi2);
+#pragma unroll
+  for (int i = 0; i < 15; i++) so[(7 + i) * SNAP_STRIDE] = C[i];
 }
 // A state in a lane's shared-memory slot (word i at s[i * SNAP_STRIDE]):
 // phase 2 keeps the forward state after its last update there.
@@ -229,26 +228,20 @@ __device__ __forceinline__ TrkState trk_get(const float* s) {
 template <bool Z>
 __device__ __forceinline__ void keep_output(Lane& w, const TrkState& p, bool zone, const double* D, const float* C,
                                             const Chi2Acc& chi2, double* snap, float* so) {
-  if (!Z) {
-    out_put(so, p, C, chi2);
-    return;
-  }
-  w.sp = p;
-  w.schi2 = chi2;
-  if (zone) {
+  if (Z && zone) {
+    out_put_state(so, p, chi2);
 #pragma unroll
     for (int i = 0; i < 15; i++) snap[i * SNAP_STRIDE] = D[i];
     w.snap = true;
     return;
   }
-#pragma unroll
-  for (int i = 0; i < 15; i++) w.sC[i] = C[i];
-  w.snap = false;
+  out_put(so, p, C, chi2);
+  if (Z) w.snap = false;
 }
-__device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap) {
+__device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap, float* so) {
   if (w.snap) {
 #pragma unroll
-    for (int i = 0; i < 15; i++) w.sC[i] = narrow(snap[i * SNAP_STRIDE]);
+    for (int i = 0; i < 15; i++) so[(7 + i) * SNAP_STRIDE] = narrow(snap[i * SNAP_STRIDE]);
     w.snap = false;
   }
 }
@@ -364,8 +357,7 @@ struct FollowWork {
   float C[15];
   Chi2Acc chi2;
   int32_t go;
-  int32_t out_ok;          // phase 4r left the output snapshot in out
-  int32_t pad[2];
+  int32_t pad[3];
   float out[OUT_WORDS];    // the backward pass's output snapshot, as out_put lays it out
 };
 
@@ -378,17 +370,39 @@ __device__ __forceinline__ void work_store(FollowWork* W, int64_t t, const Lane&
   for (int i = 0; i < 15; i++) s.C[i] = C[i];
   s.chi2 = chi2;
   s.go = go;
-  s.out_ok = 0;
 }
-__device__ __forceinline__ bool work_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p, float* C,
-                                          Chi2Acc& chi2) {
+// Phase 3 reads what its re-seed and backward zone use and writes back only
+// what it changes and the later phases read (a whole-lane load and store
+// would keep the lane's forward fields in registers through the zone).
+__device__ __forceinline__ void zone_bwd_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p) {
   const FollowWork& s = W[t];
-  w = s.w;
-  p = s.p;
+  w.ubase = s.w.ubase;
+  w.r0 = s.w.r0;
+  w.nf = s.w.nf;
+  w.nb = s.w.nb;
+  w.flags = s.w.flags;
+  w.seed_fail = s.w.seed_fail;
+  w.tr = s.w.tr;
+  p = s.w.fwd;
+}
+__device__ __forceinline__ void zone_bwd_store(FollowWork* W, int64_t t, const Lane& w, const TrkState& p,
+                                               const float* C, const Chi2Acc& chi2, const float* so, bool go) {
+  FollowWork& s = W[t];
+  s.w.nb = w.nb;
+  s.w.kf = w.kf;
+  s.w.misses = w.misses;
+  s.w.nupd = w.nupd;
+  s.w.nx_row = w.nx_row;
+  s.w.nx_c = w.nx_c;
+  s.w.nx_yz = w.nx_yz;
+  s.w.flags = w.flags;
+  s.p = p;
 #pragma unroll
-  for (int i = 0; i < 15; i++) C[i] = s.C[i];
-  chi2 = s.chi2;
-  return s.go != 0;
+  for (int i = 0; i < 15; i++) s.C[i] = C[i];
+  s.chi2 = chi2;
+  s.go = go;
+#pragma unroll
+  for (int i = 0; i < OUT_WORDS; i++) s.out[i] = so[i * SNAP_STRIDE];
 }
 
 // The binary32 phases touch only their half of the parked lane, so that
@@ -443,15 +457,8 @@ __device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w
   w.flags = s.w.flags;
   w.seed_fail = s.w.seed_fail;
   w.tr = s.w.tr;
-  if (s.out_ok) {
 #pragma unroll
-    for (int i = 0; i < OUT_WORDS; i++) so[i * SNAP_STRIDE] = s.out[i];
-  } else {
-    float sc[15];
-#pragma unroll
-    for (int i = 0; i < 15; i++) sc[i] = s.w.sC[i];
-    out_put(so, s.w.sp, sc, s.w.schi2);
-  }
+  for (int i = 0; i < OUT_WORDS; i++) so[i * SNAP_STRIDE] = s.out[i];  // (unused after a seed failure)
   p = s.p;
 #pragma unroll
   for (int i = 0; i < 15; i++) C[i] = s.C[i];
@@ -461,7 +468,7 @@ __device__ __forceinline__ bool bwd_load(const FollowWork* W, int64_t t, Lane& w
 
 // Phase 4r parks what its refit steps changed for phase 4: the running
 // state, covariance and chi2, the forward-hit cursor, the flags, whether the
-// pass goes on, and the output snapshot (left in out, marked by out_ok).
+// pass goes on, and the output snapshot.
 __device__ __forceinline__ void bwd_store(FollowWork* W, int64_t t, const Lane& w, const TrkState& p,
                                           const float* C, const Chi2Acc& chi2, const float* so, bool go) {
   FollowWork& s = W[t];
@@ -478,7 +485,6 @@ __device__ __forceinline__ void bwd_store(FollowWork* W, int64_t t, const Lane& 
   s.go = go;
 #pragma unroll
   for (int i = 0; i < OUT_WORDS; i++) s.out[i] = so[i * SNAP_STRIDE];
-  s.out_ok = 1;
 }
 
 // Work distribution of the persistent Kalman kernels: the lanes in `need`,
@@ -656,9 +662,11 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
                                                    WorkOrder next, int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   __shared__ double sSnap[15 * SNAP_STRIDE];
+  __shared__ float sOut[OUT_WORDS * SNAP_STRIDE];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
   double* snap = sSnap + threadIdx.x;
+  float* so = sOut + threadIdx.x;
   const Chunk ch = chunk_range(cn->n_tracklets, chunk, nchunk);
   LocalTally tl;
   double D[15];
@@ -672,13 +680,12 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
     Chi2Acc chi2;
     bool go = false;
     if (valid) {
-      work_load(W, t, w, p, C, chi2);
+      zone_bwd_load(W, t, w, p);
       w.hits = o.hits + t * NROW;
       w.hrow = o.hrow + t * NROW;
       w.cn = cn;
       w.snap = false;
       if (!w.seed_fail) {
-        p = w.fwd;
         chi2.reset();
         w.kf = w.nf - 2;
         next_fwd_hit(w, g);
@@ -695,15 +702,18 @@ __global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, Follow
       lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
       if (zone0) tl.upd64++;
       else tl.upd32++;
-      keep_output<true>(w, p, w.nupd < w.zend, D, C, chi2, snap, nullptr);
-      while (go && w.nupd < w.zend) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, nullptr);
+      keep_output<true>(w, p, w.nupd < w.zend, D, C, chi2, snap, so);
+      while (go && w.nupd < w.zend) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, so);
       if (w.nupd < w.zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
       }
-      zone_snap_take(w, snap);
+      zone_snap_take(w, snap, so);
     }
-    if (valid) work_store(W, t, w, p, C, chi2, go);
+    if (valid) {
+      if (w.seed_fail) W[t].go = 0;  // the later phases read only the lane's forward fields
+      else zone_bwd_store(W, t, w, p, C, chi2, so, go);
+    }
     order_count(next, t, valid, go ? p.row : 0);  // rows left inward
   }
   tl.flush(cn, PH_FOLLOW_P3);
