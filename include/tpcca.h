@@ -353,7 +353,8 @@ typedef struct {
                                  (multiple of 32, at most 1024) */
   int32_t block_follow;       /* threads per block of the Kalman kernels (multiple of 32, at most 128) */
   int32_t ctas_per_sm_zone;   /* most CTAs per SM of the Kalman kernels running FP64 zones; their grids are
-                                 one wave of resident CTAs (64: as many as fit) */
+                                 one wave of resident CTAs (64: as many as fit); reported as 0 while the
+                                 default applies: 4 from 4 Mi loaded clusters on, else 2 */
   int32_t ctas_per_sm_follow; /* the same for the Kalman kernels that refill lanes (FP32 phases); reported
                                  as 0 while the default applies: 64 from 4 Mi loaded clusters on, else 2 */
   int32_t refill;             /* idle lanes of a warp of a refilling kernel that trigger the warp's common
@@ -373,7 +374,7 @@ int tpc_set_tuning(tpc_ctx *ctx, const tpc_tuning *t);
 /* Autotuner: with a representative batch loaded, times tpc_find_tracks +
  * tpc_fit_tracks (median of reps runs, CUDA events on the context's stream)
  * over block_clusters {128, 256, 512}, block_follow {64, 96, 128},
- * ctas_per_sm_zone {1, 2, 3}, ctas_per_sm_follow {2, 3, 64}, refill
+ * ctas_per_sm_zone {2, 3, 4}, ctas_per_sm_follow {2, 3, 64}, refill
  * {1, 4, 8, 16} and chunks {1, 2} by coordinate descent from the current
  * shapes, keeps the fastest and reports it in *best and *best_ms (either
  * may be NULL).  The results of the loaded batch are overwritten (rerun

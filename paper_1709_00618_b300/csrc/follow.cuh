@@ -519,7 +519,7 @@ __device__ __forceinline__ void load_tables(float* sX, float* sYH) {
 // Phase 1: seed and the forward pass while its covariance is in FP64.  A
 // warp takes 32 consecutive tracklets at a time and starts their zones
 // together; the grid is the resident capacity (one wave).
-__global__ void __launch_bounds__(128) k_follow_p1(GridView g, const int32_t* __restrict__ tl_start,
+__global__ void __launch_bounds__(128, 4) k_follow_p1(GridView g, const int32_t* __restrict__ tl_start,
                                                    const int32_t* __restrict__ tl_len,
                                                    const int32_t* __restrict__ tl_end,
                                                    const int32_t* __restrict__ up_m, KConst kc, FollowOut o,
@@ -658,7 +658,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
 // Phase 3: re-seed at the outermost forward cluster and run the backward
 // pass while its covariance is in FP64 (warps take 32 tracklets at a time,
 // as phase 1).
-__global__ void __launch_bounds__(128) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W,
+__global__ void __launch_bounds__(128, 4) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W,
                                                    WorkOrder next, int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   __shared__ double sSnap[15 * SNAP_STRIDE];
@@ -814,10 +814,12 @@ __device__ __forceinline__ void write_follow_output(const FollowOut& o, int64_t 
   o.chi2[t] = c.value();
 }
 
-// Phase 4: the rest of the backward pass, the inward extension below the
-// chain's first row (FP32, lanes refill as in phase 2; phase 4r has made
-// every refit row), and the outputs.
-template <int MINB>
+// Phase 4: the rest of the backward pass (FP32, lanes refill as in phase 2)
+// and the outputs.  M = BW_EXTEND after phase 4r, which has made every refit
+// row: the inward extension below the chain's first row.  M = BW_ANY without
+// phase 4r, on batches bound by their longest tracklet, where a second
+// kernel between refit and extension would lengthen that tracklet's path.
+template <int MINB, int M>
 __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32_t* __restrict__ tl_start, KConst kc,
                                                    FollowOut o, FollowWork* W, const int32_t* __restrict__ order,
                                                    int chunk, int nchunk, Counts* cn) {
@@ -857,7 +859,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4(GridView g, const int32
       continue;
     }
     for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
-      go = bwd_step<false, BW_EXTEND>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr, so);
+      go = bwd_step<false, M>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr, so);
   }
   tl.flush(cn, PH_FOLLOW_P4);
 }

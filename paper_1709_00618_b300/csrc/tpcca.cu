@@ -259,7 +259,7 @@ struct tpc_ctx {
   // tuning
   int block_clusters = 256;
   int block_follow = 128;
-  int ctas_zone = 2;     // cap on CTAs per SM of the FP64-zone Kalman kernels
+  int ctas_zone = 0;     // cap on CTAs per SM of the FP64-zone Kalman kernels (0: by size)
   int ctas_follow = 0;   // cap on CTAs per SM of the refilling Kalman kernels (64: occupancy; 0: by size)
   int refill = 8;        // idle lanes that trigger a warp's refill
   int chunks = 0;        // Kalman-stage chunks (2: zone and FP32 kernels of different chunks overlap; 0: 1)
@@ -376,6 +376,14 @@ bool key32(const tpc_ctx* ctx) { return ctx->caps.tl < (int64_t(1) << 24); }
 int effective_ctas_follow(const tpc_ctx* ctx) {
   if (ctx->ctas_follow > 0) return ctx->ctas_follow;
   return ctx->n >= kLargeBatch ? 64 : 2;
+}
+// CTAs per SM of the FP64-zone kernels: the tuned value, or by size (a small
+// batch's zone kernels end with the tracklets of their last wave, so fewer
+// resident warps shorten the tail; on a large batch the FP64 pipe needs as
+// many warps as the zone's registers allow, four 128-thread CTAs).
+int effective_ctas_zone(const tpc_ctx* ctx) {
+  if (ctx->ctas_zone > 0) return ctx->ctas_zone;
+  return ctx->n >= kLargeBatch ? 4 : 2;
 }
 
 WorkOrder work_order(tpc_ctx* ctx, int phase, int chunk) {
@@ -656,7 +664,7 @@ void enqueue_find(tpc_ctx* ctx) {
     int32_t* order = longest_first ? ctx->ptr<int32_t>(L.order) : nullptr;
     auto ord = [&](int phase, int c) { return longest_first ? work_order(ctx, phase, c) : WorkOrder{}; };
     auto follow_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
-      k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, ctx->ctas_zone), bf, 0, st>>>(
+      k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
           ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, ord(0, c), c, nc, cn);
       if (after_p1) cudaEventRecord(after_p1, st);
@@ -667,15 +675,17 @@ void enqueue_find(tpc_ctx* ctx) {
       p2<<<persistent_grid(ctx, p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
       if (nc == 1) ctx->mark_k(1);
-      k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, ctx->ctas_zone), bf, 0, st>>>(
+      k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->kc, follow_out(ctx), W, ord(1, c), c, nc, cn);
       if (longest_first)
         k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(2);
-      auto p4r = ctx->n >= kLargeBatch ? k_follow_p4r<7> : k_follow_p4r<4>;
-      p4r<<<persistent_grid(ctx, p4r, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
-          grid_view(ctx), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
-      auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<7> : k_follow_p4<4>;
+      // large batches: the refit rows (p4r) and the extension (p4) in two
+      // kernels, so that no warp mixes them; small ones: both in p4
+      if (ctx->n >= kLargeBatch)
+        k_follow_p4r<7><<<persistent_grid(ctx, k_follow_p4r<7>, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
+            grid_view(ctx), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
+      auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<7, BW_EXTEND> : k_follow_p4<4, BW_ANY>;
       p4<<<persistent_grid(ctx, p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
     };
@@ -755,7 +765,7 @@ void enqueue_fit(tpc_ctx* ctx) {
     RefitWork* RW = ctx->ptr<RefitWork>(L.rwork);
     const int nc = ctx->prof ? 1 : effective_chunks(ctx);
     auto refit_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
-      k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, ctx->ctas_zone), bf, 0, st>>>(
+      k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
           grid_view(ctx), in, ctx->kc, RW, work_order(ctx, 2, c), c, nc, cn);
       if (after_p1) cudaEventRecord(after_p1, st);
       k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, st>>>(work_order(ctx, 2, c), &cn->n_tracks, c, nc, cn);
@@ -1411,12 +1421,13 @@ int tpc_autotune(tpc_ctx* ctx, int32_t reps, tpc_tuning* best_out, float* best_m
     return check_status(ctx);
   };
   // candidates per field, in the order of tpc_tuning
-  static const int kCand[6][4] = {{128, 256, 512, 0}, {64, 96, 128, 0}, {1, 2, 3, 0},
+  static const int kCand[6][4] = {{128, 256, 512, 0}, {64, 96, 128, 0}, {2, 3, 4, 0},
                                   {2, 3, 64, 0},      {1, 4, 8, 16},    {1, 2, 0, 0}};
   static const int kNCand[6] = {3, 3, 3, 3, 4, 2};
   tpc_tuning cur;
   get_tuning(ctx, &cur);
   if (cur.chunks <= 0) cur.chunks = effective_chunks(ctx);
+  if (cur.ctas_per_sm_zone <= 0) cur.ctas_per_sm_zone = effective_ctas_zone(ctx);
   if (cur.ctas_per_sm_follow <= 0) cur.ctas_per_sm_follow = effective_ctas_follow(ctx);
   int best[6] = {cur.block_clusters, cur.block_follow, cur.ctas_per_sm_zone, cur.ctas_per_sm_follow, cur.refill,
                  cur.chunks};

@@ -127,7 +127,7 @@ def test_autotuned_shapes_give_the_same_result():
         choice, ms = t.autotune(cl, reps=1)
         assert choice["block_clusters"] in (128, 256, 512)
         assert choice["block_follow"] in (64, 96, 128)
-        assert choice["ctas_per_sm_zone"] in (1, 2, 3)
+        assert choice["ctas_per_sm_zone"] in (2, 3, 4)
         assert choice["ctas_per_sm_follow"] in (2, 3, 64)
         assert choice["refill"] in (1, 4, 8, 16)
         assert choice["chunks"] in (1, 2)
