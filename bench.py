@@ -883,9 +883,7 @@ def measure(cl, local, args, flush, world=1, clocks=True, e2e_steps=None):
     k_e2e = e2e_steps if e2e_steps is not None else args.steps
     for i in range(warm + k_e2e):
         t0 = time.perf_counter()
-        trk.load(host_in)
-        trk.run_graph()
-        tr, _ = trk.get_into(tr_buf, ct_buf)
+        tr, _ = trk.track_host(host_in, tr_buf, ct_buf)  # tpc_track_host: one call, host to host
         if i >= warm:
             e2e.append(time.perf_counter() - t0)
     e2e_t, _ = combine_ranks(sum(e2e) / len(e2e), n, world, f"cuda:{local}")

@@ -191,6 +191,19 @@ int tpc_run_graph(tpc_ctx *ctx);
 int tpc_get_tracks(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, int32_t *cluster_track,
                    int32_t *track_clusters);
 
+/* One request host to host (a1-a9 in one call): copies n clusters from host
+ * memory in (page-locked memory lets the copy run at full speed), finds and
+ * fits the tracks, and copies the tracks into out (room for cap) and the
+ * cluster assignment into cluster_track (optional, n entries, as
+ * tpc_get_tracks).  The assignment is final after the selection (a7), so its
+ * copy runs on a stream of its own while the refit (a8) computes (with a
+ * page-locked cluster_track; a pageable one makes the copy wait for the
+ * host); the call returns when both copies have landed.  Same results and errors as
+ * tpc_load_clusters + tpc_find_tracks + tpc_fit_tracks + tpc_get_tracks;
+ * after an error the contents of cluster_track are undefined. */
+int tpc_track_host(tpc_ctx *ctx, const tpc_cluster *clusters, int64_t n, tpc_track *out, int64_t cap,
+                   int64_t *n_out, int32_t *cluster_track);
+
 /* Non-blocking form of tpc_get_tracks for a run that has completed (the
  * caller has seen its stream idle, e.g. through an event recorded after
  * tpc_run_graph): reports device-side errors and *n_out as tpc_get_tracks,

@@ -155,6 +155,7 @@ def load_library(path: str | None = None):
         "tpc_server_poll": ([_VP, _I64, _VP], ctypes.c_int),
         "tpc_server_result": ([_VP, _I64, _VP, _VP], ctypes.c_int),
         "tpc_get_tracks_async": ([_VP, _VP, _I64, _VP, _VP], ctypes.c_int),
+        "tpc_track_host": ([_VP, _VP, _I64, _VP, _I64, _VP, _VP], ctypes.c_int),
         "tpc_get_arena_bytes": ([_VP, _VP], ctypes.c_int),
         "tpc_server_drain": ([_VP, ctypes.c_double], ctypes.c_int),
         "tpc_server_stats": ([_VP, _VP], ctypes.c_int),
@@ -598,6 +599,33 @@ class Tracker:
                     raise
                 self.reserve(n_clusters=self.n, n_requests=1, n_bins=max(2 * c["n_bins"], 0),
                              n_tracklets=self.n // 3 + 16)
+        raise AssertionError("unreachable")
+
+    def track_host(self, clusters, tracks_out, cluster_track_out=None):
+        """tpc_track_host: host clusters (numpy structured array) in, tracks and
+        cluster assignment out, in one call whose assignment copy overlaps the
+        refit (page-locked output buffers keep the copies asynchronous);
+        retries a device capacity overflow once with the worst-case
+        capacities, as track_into.  Returns (tracks view, cluster_track)."""
+        clusters = np.ascontiguousarray(clusters)
+        n = len(clusters)
+        tr = _records(tracks_out, TRACK_DTYPE, 0)
+        ct = _records(cluster_track_out, np.int32, n)
+        nout = ctypes.c_int64()
+        for attempt in range(2):
+            self._keep_in = clusters
+            rc = self._lib.tpc_track_host(self._ctx, _ptr(clusters) if n else None, n,
+                                          tr.ctypes.data if len(tr) else None, len(tr), ctypes.byref(nout),
+                                          ct.ctypes.data if ct is not None and n else None)
+            self.n = n
+            if rc == TPC_EOVERFLOW and not attempt:
+                c = self.counts()
+                if c["status"] & 2:  # a device capacity, not the caller's buffer
+                    self.reserve(n_clusters=n, n_requests=1, n_bins=max(2 * c["n_bins"], 0),
+                                 n_tracklets=n // 3 + 16)
+                    continue
+            self._ck(rc)
+            return tr[:nout.value], ct
         raise AssertionError("unreachable")
 
     def track(self, clusters, req_offsets=None, graph: bool = False):

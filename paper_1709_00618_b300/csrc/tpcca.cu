@@ -267,6 +267,10 @@ struct tpc_ctx {
   int graph_ctas = 0;
   bool graph_large = false;  // the size class the graph's kernel variants were chosen for
   cudaStream_t aux = nullptr;       // second stream of the chunked Kalman stage
+  // tpc_track_host: the stream of the cluster assignment's copy-out, which
+  // overlaps the refit, and its fork and join events (created on first use)
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ev_sel = nullptr, ev_copied = nullptr;
   // vertex finding (tpc_find_vertices): its own buffer, allocated on first use
   void* vtx_mem = nullptr;
   int64_t vtx_tracks_cap = 0;
@@ -920,6 +924,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->aux) cudaStreamSynchronize(ctx->aux);
+  if (ctx->copy) cudaStreamSynchronize(ctx->copy);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   for (int i = 0; i < 7; i++)
@@ -941,6 +946,9 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (ctx->h_merge_n) cudaFreeHost(ctx->h_merge_n);
   if (ctx->h_vtx_n) cudaFreeHost(ctx->h_vtx_n);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->copy) cudaStreamDestroy(ctx->copy);
+  if (ctx->ev_sel) cudaEventDestroy(ctx->ev_sel);
+  if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
   for (int i = 0; i < 4; i++)
     if (ctx->ev_chunk[i]) cudaEventDestroy(ctx->ev_chunk[i]);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -1104,6 +1112,38 @@ int tpc_get_arena_bytes(tpc_ctx* ctx, size_t* bytes) {
   if (!ctx || !bytes) return TPC_EINVAL;
   *bytes = ctx->arena ? ctx->arena_bytes : 0;
   return TPC_OK;
+}
+
+int tpc_track_host(tpc_ctx* ctx, const tpc_cluster* clusters, int64_t n, tpc_track* out, int64_t cap,
+                   int64_t* n_out, int32_t* cluster_track) {
+  if (!ctx) return TPC_EINVAL;
+  int rc = tpc_load_clusters(ctx, clusters, n, 0);
+  if (rc) return rc;
+  if (!ctx->copy) {
+    if (cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_sel, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming) != cudaSuccess)
+      return fail(ctx, TPC_ECUDA, "copy stream: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  enqueue_find(ctx);
+  CK(cudaGetLastError());
+  ctx->found = true;
+  // the assignment is final once a7 has run: copy it out on the copy
+  // stream while a8 runs on the context's stream
+  const bool ct = cluster_track && ctx->n > 0;
+  if (ct) {
+    CK(cudaEventRecord(ctx->ev_sel, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->copy, ctx->ev_sel, 0));
+    CK(cudaMemcpyAsync(cluster_track, ctx->ptr<int32_t>(ctx->L.cluster_track), sizeof(int32_t) * ctx->n,
+                       cudaMemcpyDeviceToHost, ctx->copy));
+    CK(cudaEventRecord(ctx->ev_copied, ctx->copy));
+  }
+  enqueue_fit(ctx);
+  CK(cudaGetLastError());
+  ctx->fitted = true;
+  ctx->fit_gen++;
+  if (ct) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied, 0));  // later work on the stream waits for the copy
+  return tpc_get_tracks(ctx, out, cap, n_out, nullptr, nullptr);
 }
 
 int tpc_get_tracks_async(tpc_ctx* ctx, tpc_track* out, int64_t cap, int64_t* n_out, int32_t* cluster_track) {
