@@ -91,6 +91,27 @@ def test_rerun_without_reload_repeats_every_kernel(trk):
         assert tb == runs[0][2] and cb == runs[0][3]
 
 
+def test_large_batch_shapes_give_the_same_bytes():
+    """From 4 Mi clusters the Kalman stage runs its large-input shapes (index
+    order, the backward refit rows in a kernel of their own, four zone CTAs
+    per SM); split in two chunks on two streams, with one zone CTA per SM or
+    with refilling at once, it must give the same bytes."""
+    import paper_1709_00618_b300 as tpc
+    ev = synth.timeframe(seed=2, length_ms=0.6)
+    assert len(ev.clusters) >= 4 << 20
+    names = ("f_n", "f_hits", "f_par", "f_cov", "f_chi2", "tl_track")
+    with tpc.Tracker(device=0) as t:
+        ref_tracks, ref_ct, _ = t.track(ev.clusters, graph=True)
+        ref = [t.stage(nm).tobytes() for nm in names]
+        for shape in (dict(chunks=2), dict(chunks=2, ctas_per_sm_zone=1, refill=1), dict(ctas_per_sm_follow=3)):
+            t.set_tuning(**shape)
+            for graph in (False, True):
+                tracks, ct, _ = t.track(ev.clusters, graph=graph)
+                assert tracks.tobytes() == ref_tracks.tobytes(), shape
+                assert np.array_equal(ct, ref_ct), shape
+                assert [t.stage(nm).tobytes() for nm in names] == ref, shape
+
+
 def test_link_skip_variant_parity():
     """The next-row variant of the links (link_skip = 1 on both sides):
     links, tracklets, follow, selection and refit against the FP64 oracle
