@@ -148,7 +148,10 @@ __device__ __noinline__ void nb_skip(const float2* __restrict__ yz, const int32_
   }
 }
 
-__global__ void __launch_bounds__(NB_THREADS) k_neighbours(const float2* __restrict__ yz,
+// Six blocks per SM (40 registers, a few spilled): more resident lanes hide
+// more of each lane's dependent loads (10 ms timeframe 8.66 -> 8.11 ms against
+// five blocks at 48 registers; eight blocks at 32 registers spill more).
+__global__ void __launch_bounds__(NB_THREADS, 6) k_neighbours(const float2* __restrict__ yz,
                                                            const int32_t* __restrict__ rs_of,
                                                            const RsParams* __restrict__ par,
                                                            const int32_t* __restrict__ bin_start, KConst kc,
