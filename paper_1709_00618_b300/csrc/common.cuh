@@ -132,8 +132,8 @@ struct KConst {
   // the warp fetches new work for them together (1: refill at once)
   int32_t refill;
   // row steps a refilling Kalman kernel's lanes take between the warp's
-  // refill checks (fewer warp-wide votes on inputs bound by the longest
-  // tracklet; 1 on large inputs, where idle lanes cost throughput)
+  // refill checks (16 on inputs bound by the longest tracklet: fewer
+  // warp-wide votes; 4 on large inputs, where lanes idle until the check)
   int32_t inner_steps;
 };
 

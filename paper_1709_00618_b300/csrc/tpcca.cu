@@ -594,7 +594,7 @@ void enqueue_find(tpc_ctx* ctx) {
   int32_t* bin_base = ctx->ptr<int32_t>(L.bin_base);
   int32_t* bin_cnt = ctx->ptr<int32_t>(L.bin_cnt);
   int32_t* bin_start = ctx->ptr<int32_t>(L.bin_start);
-  ctx->kc.inner_steps = ctx->n < kLargeBatch ? 16 : 1;
+  ctx->kc.inner_steps = ctx->n < kLargeBatch ? 16 : 4;  // 10 ms timeframe: 1 step 69.0 ms, 2 68.7, 4 68.6, 8 68.8
   ctx->mark(0);
   // a2 grid
   k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax),
