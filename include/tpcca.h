@@ -195,10 +195,13 @@ int tpc_get_tracks(tpc_ctx *ctx, tpc_track *out, int64_t cap, int64_t *n_out, in
  * memory in (page-locked memory lets the copy run at full speed), finds and
  * fits the tracks, and copies the tracks into out (room for cap) and the
  * cluster assignment into cluster_track (optional, n entries, as
- * tpc_get_tracks).  The assignment is final after the selection (a7), so its
- * copy runs on a stream of its own while the refit (a8) computes (with a
- * page-locked cluster_track; a pageable one makes the copy wait for the
- * host); the call returns when both copies have landed.  Same results and errors as
+ * tpc_get_tracks).  From 4 Mi clusters on, the assignment's copy, which is
+ * final after the selection (a7), runs on a stream of its own while the
+ * refit (a8) computes (with a page-locked cluster_track; a pageable one makes
+ * the copy wait for the host); below that a2-a8 run as the context's CUDA
+ * graph (tpc_run_graph, unless the context was created on the legacy default
+ * stream) and both copies follow.  The call returns when both copies have
+ * landed.  Same results and errors as
  * tpc_load_clusters + tpc_find_tracks + tpc_fit_tracks + tpc_get_tracks;
  * after an error the contents of cluster_track are undefined. */
 int tpc_track_host(tpc_ctx *ctx, const tpc_cluster *clusters, int64_t n, tpc_track *out, int64_t cap,

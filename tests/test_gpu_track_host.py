@@ -17,12 +17,15 @@ def _reference(tpc, clusters):
     return tracks, ct
 
 
-@pytest.mark.parametrize("pinned", [False, True])
-def test_track_host_equals_the_step_by_step_calls(pinned):
+@pytest.mark.parametrize("pinned,large", [(False, False), (True, False), (True, True)])
+def test_track_host_equals_the_step_by_step_calls(pinned, large):
+    """Below 4 Mi clusters the copies follow the refit; from 4 Mi clusters
+    (a 0.6 ms timeframe) the assignment's copy overlaps it."""
     import torch
 
     import paper_1709_00618_b300 as tpc
-    ev = synth.central_event(seed=1)
+    ev = synth.timeframe(seed=2, length_ms=0.6) if large else synth.central_event(seed=1)
+    assert (len(ev.clusters) >= 4 << 20) == large
     ref_tracks, ref_ct = _reference(tpc, ev.clusters)
     n = len(ev.clusters)
     if pinned:
