@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
     if (need & (1u << (threadIdx.x & 31))) {
       if (m >= 0) write_track(in, sX, m, RW[m], p, C, chi2, ok, flags, out);
       const int64_t idx = ch.begin + warp_fetch(work_counter(cn, PH_REFIT_P2, chunk), need);
-      m = idx < ch.end ? order[idx] : M;
+      m = idx < ch.end ? (order ? order[idx] : idx) : M;
       if (m < M) load(m);
       else live = false;
     }

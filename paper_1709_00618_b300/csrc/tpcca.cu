@@ -768,14 +768,18 @@ void enqueue_fit(tpc_ctx* ctx) {
     RefitIn in = refit_in(ctx);
     RefitWork* RW = ctx->ptr<RefitWork>(L.rwork);
     const int nc = ctx->prof ? 1 : effective_chunks(ctx);
+    // longest first below kLargeBatch clusters, index order above (as a6)
+    const bool longest_first = ctx->n < kLargeBatch;
     auto refit_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
       k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
-          grid_view(ctx), in, ctx->kc, RW, work_order(ctx, 2, c), c, nc, cn);
+          grid_view(ctx), in, ctx->kc, RW, longest_first ? work_order(ctx, 2, c) : WorkOrder{}, c, nc, cn);
       if (after_p1) cudaEventRecord(after_p1, st);
-      k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, st>>>(work_order(ctx, 2, c), &cn->n_tracks, c, nc, cn);
+      if (longest_first)
+        k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, st>>>(work_order(ctx, 2, c), &cn->n_tracks, c, nc, cn);
       if (nc == 1) ctx->mark_k(4);
       k_refit_p2<<<persistent_grid(ctx, k_refit_p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
-          grid_view(ctx), in, ctx->kc, RW, ctx->ptr<int32_t>(L.order), ctx->ptr<tpc_track>(L.tracks), c, nc, cn);
+          grid_view(ctx), in, ctx->kc, RW, longest_first ? ctx->ptr<int32_t>(L.order) : nullptr,
+          ctx->ptr<tpc_track>(L.tracks), c, nc, cn);
     };
     ctx->mark_k(3);
     if (nc == 1) {
