@@ -121,6 +121,7 @@ struct Lane {
   bool seed_fail;
   bool tr;       // this tracklet is traced
   bool snap;     // backward zone: the output covariance is pending in the FP64 snapshot (zone_snap_take)
+  bool dg;       // zone: the FP64 covariance is the diagonal one the seed's first update left (until a propagation)
   Counts* cn;
   TrkState fwd;  // forward state after its last update
 };
@@ -152,10 +153,11 @@ __device__ __noinline__ void trace_line(Counts* cn, float* trace, int cap, float
 // in C); records a trace line when the lane is traced.
 template <bool Z>
 __device__ __forceinline__ void lane_update(Lane& w, const KConst& kc, TrkState& p, bool zone, double* D, float* C,
-                                            float2 P, Chi2Acc& chi2, int pass) {
+                                            float2 P, Chi2Acc& chi2, int pass, bool diag = false) {
   zone = Z && zone;
   const float r0 = residual_y(p, P.x), r1 = residual_z(p, P.y);
-  chi2.add(zone_update(p, zone, D, C, P.x, P.y, kc, w.nupd, w.zend, pass ? 2 * kc.fp64_updates : kc.fp64_updates));
+  chi2.add(zone_update(p, zone, D, C, P.x, P.y, kc, w.nupd, w.zend, pass ? 2 * kc.fp64_updates : kc.fp64_updates,
+                       diag));
   if (w.tr)
     trace_line(w.cn, kc.trace, kc.trace_cap, (float)pass, (float)p.row, (float)w.nupd, p.y + p.yl,
                p.zref + (p.z + p.zl), p.s + p.sl, p.t, p.q, zone ? (float)D[0] : C[0], zone ? (float)D[2] : C[2],
@@ -268,10 +270,11 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
       w.nk = w.i + 1 < w.L ? __ldg(up_m + c) : -1;
     }
   }
-  if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
+  if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags, Z && w.dg)) {
     if (chain) w.seed_fail = true;
     return false;
   }
+  if (Z) w.dg = false;
   tl.prop++;
   tl.prop64 += zone;
   if (cross) return true;
@@ -313,10 +316,11 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
   if (r < 0) return false;
   if (r >= 1 && r - 1 < w.r0) prefetch_l1(g.par + w.ubase + r - 1);  // the next step's row-sector parameters
   const bool zone = Z && w.nupd < w.zend;
-  if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags)) {
+  if (!propagate_any(p, zone, D, C, r, sX[r], kc, w.flags, Z && w.dg)) {
     if (M == BW_REFIT || (M == BW_ANY && r >= w.r0)) w.flags |= TF_BACK_FAIL;
     return false;
   }
+  if (Z) w.dg = false;
   tl.prop++;
   tl.prop64 += zone;
   float2 P;
@@ -579,7 +583,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p1(GridView g, const int32_t*
     __syncwarp();  // the zones of the warp's lanes start together
     if (valid) {
       const bool zone0 = kc.fp64_updates > 0;
-      lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + tl_start[t]), chi2, 0);
+      lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + tl_start[t]), chi2, 0, true);  // diagonal seed covariance
+      w.dg = zone0;
       if (zone0) tl.upd64++;
       else tl.upd32++;
       w.fwd = p;
@@ -699,7 +704,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p3(GridView g, KConst kc, Fol
     __syncwarp();  // the zones of the warp's lanes start together
     if (go) {
       const bool zone0 = kc.fp64_updates > 0;
-      lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1);
+      lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1, true);  // diagonal seed
+      w.dg = zone0;
       if (zone0) tl.upd64++;
       else tl.upd32++;
       keep_output<true>(w, p, w.nupd < w.zend, D, C, chi2, snap, so);

@@ -230,8 +230,65 @@ __device__ __forceinline__ bool prop_state(TrkState& p, int row2, float x2, cons
 // covariance stays in registers (out of line it went through local memory,
 // 5-13% slower); the binary32 kernels instantiate the row steps without the
 // zone path, so they do not carry this code.
+// The transport of cov_transport written with explicit fused multiply-adds
+// (an expression a + b c + d e is fma(d, e, fma(b, c, a))), so that
+// cov_transport_d_diag below can be derived from it operation by operation.
 __device__ __forceinline__ void cov_transport_d(double* D, const Jac& J) {
-  cov_transport<double>(D, widen(J.j02), widen(J.j12), widen(J.j13), widen(J.kap));
+  const double j02 = widen(J.j02), j12 = widen(J.j12), j13 = widen(J.j13), kap = widen(J.kap);
+  const double c00 = D[0], c10 = D[1], c11 = D[2], c20 = D[3], c21 = D[4], c22 = D[5], c30 = D[6], c31 = D[7],
+               c32 = D[8], c33 = D[9], c40 = D[10], c41 = D[11], c42 = D[12], c43 = D[13], c44 = D[14];
+  const double u0 = fma(kap, c40, c20), u1 = fma(kap, c41, c21), u2 = fma(kap, c42, c22), u3 = fma(kap, c43, c32),
+               u4 = fma(kap, c44, c42);
+  const double a00 = fma(j02, u0, c00), a02 = fma(j02, u2, c20), a04 = fma(j02, u4, c40);
+  const double a10 = fma(j13, c30, fma(j12, u0, c10));
+  const double a11 = fma(j13, c31, fma(j12, u1, c11));
+  const double a12 = fma(j13, c32, fma(j12, u2, c21));
+  const double a13 = fma(j13, c33, fma(j12, u3, c31));
+  const double a14 = fma(j13, c43, fma(j12, u4, c41));
+  const double a20 = fma(kap, c40, u0), a21 = fma(kap, c41, u1), a22 = fma(kap, c42, u2), a23 = fma(kap, c43, u3),
+               a24 = fma(kap, c44, u4);
+  const double v0 = fma(kap, a04, a02), v1 = fma(kap, a14, a12), v2 = fma(kap, a24, a22);
+  D[0] = fma(j02, v0, a00);
+  D[1] = fma(j02, v1, a10);
+  D[2] = fma(j13, a13, fma(j12, v1, a11));
+  D[3] = fma(j02, v2, a20);
+  D[4] = fma(j13, a23, fma(j12, v2, a21));
+  D[5] = fma(kap, a24, v2);
+  D[6] = fma(j02, u3, c30);
+  D[7] = fma(j13, c33, fma(j12, u3, c31));
+  D[8] = fma(kap, c43, u3);
+  D[10] = fma(j02, u4, c40);
+  D[11] = fma(j13, c43, fma(j12, u4, c41));
+  D[12] = fma(kap, c44, u4);
+}
+
+// cov_transport_d of a diagonal D (off-diagonal entries +0, diagonal ones
+// positive): the first transport after a (re)seed, whose first update leaves
+// the seed covariance diagonal.  Every operation of cov_transport_d whose
+// result is fixed by the zeros is left out -- b (+0) + x is x for x positive
+// or an fma result, and fma(b, +0, +0) is +0 in round to nearest -- and the
+// others are the same operations on the same operands, so the result is the
+// same to the bit: 17 fused multiply-adds instead of 42.
+__device__ __forceinline__ void cov_transport_d_diag(double* D, const Jac& J) {
+  const double j02 = widen(J.j02), j12 = widen(J.j12), j13 = widen(J.j13), kap = widen(J.kap);
+  const double c00 = D[0], c11 = D[2], c22 = D[5], c33 = D[9], c44 = D[14];
+  const double u4 = fma(kap, c44, 0.0);
+  const double a02 = fma(j02, c22, 0.0), a04 = fma(j02, u4, 0.0);
+  const double a12 = fma(j12, c22, 0.0), a13 = fma(j13, c33, 0.0), a14 = fma(j12, u4, 0.0);
+  const double a24 = fma(kap, c44, u4);
+  const double v0 = fma(kap, a04, a02), v1 = fma(kap, a14, a12), v2 = fma(kap, a24, c22);
+  D[0] = fma(j02, v0, c00);
+  D[1] = fma(j02, v1, 0.0);
+  D[2] = fma(j13, a13, fma(j12, v1, c11));
+  D[3] = fma(j02, v2, 0.0);
+  D[4] = fma(j12, v2, 0.0);
+  D[5] = fma(kap, a24, v2);
+  D[6] = 0.0;
+  D[7] = a13;
+  D[8] = 0.0;
+  D[10] = a04;
+  D[11] = a14;
+  D[12] = a24;
 }
 
 struct UpdOut {
@@ -291,12 +348,38 @@ __device__ __forceinline__ UpdOut kalman_update_d(double* D, float r0, float r1,
   return o;
 }
 
-// One Kalman update of the state with covariance in FP64 (zone) or FP32.
+// kalman_update_d of a diagonal D (the first update after a (re)seed): the
+// y step then changes only C_yy and the z step only C_zz, every other gain
+// entry is +0 and every other downdate adds -0 to its entry, which leaves it
+// unchanged; the binary32 outputs are the same expressions of the same gains.
+// 14 binary64 operations instead of 50, the same result to the bit.
+__device__ __forceinline__ UpdOut kalman_update_d_diag(double* D, float r0, float r1, double V) {
+  const double s0 = D[0] + V, i0 = krcp(s0);
+  const double w00 = D[0] * i0;
+  D[0] = fma(-w00, D[0], D[0]);
+  const double s1 = D[2] + V, i1 = krcp(s1);
+  const double w11 = D[2] * i1;
+  D[2] = fma(-w11, D[2], D[2]);
+  const double w0[5] = {w00, 0.0, 0.0, 0.0, 0.0}, w1[5] = {0.0, w11, 0.0, 0.0, 0.0};
+  const float e1 = r1 - narrow(w0[1]) * r0;
+  UpdOut o;
+  o.d0 = narrow(w0[0]) * r0 + narrow(w1[0]) * e1;
+  o.d1 = narrow(w0[1]) * r0 + narrow(w1[1]) * e1;
+  o.d2 = narrow(w0[2]) * r0 + narrow(w1[2]) * e1;
+  o.d3 = narrow(w0[3]) * r0 + narrow(w1[3]) * e1;
+  o.d4 = narrow(w0[4]) * r0 + narrow(w1[4]) * e1;
+  o.chi2 = r0 * r0 * narrow(i0) + e1 * e1 * narrow(i1);
+  return o;
+}
+
+// One Kalman update of the state with covariance in FP64 (zone) or FP32;
+// diag: the zone's covariance is known to be diagonal (the first update
+// after a (re)seed).
 __device__ __forceinline__ float update_any(TrkState& p, bool zone, double* D, float* C, float my, float mz,
-                                             const KConst& kc) {
+                                             const KConst& kc, bool diag = false) {
   if (zone) {
     const float r0 = residual_y(p, my), r1 = residual_z(p, mz);
-    const UpdOut o = kalman_update_d(D, r0, r1, kc.Vd);
+    const UpdOut o = diag ? kalman_update_d_diag(D, r0, r1, kc.Vd) : kalman_update_d(D, r0, r1, kc.Vd);
     acc2(p.y, p.yl, o.d0);
     acc2(p.z, p.zl, o.d1);
     acc2(p.s, p.sl, o.d2);
@@ -320,9 +403,9 @@ __device__ __forceinline__ float update_any(TrkState& p, bool zone, double* D, f
 // it; zend, kc.fp64_updates at the (re)seed, is the count that ends the zone,
 // zmax the largest it may become.
 __device__ __forceinline__ float zone_update(TrkState& p, bool zone, double* D, float* C, float my, float mz,
-                                             const KConst& kc, int& nupd, int& zend, int zmax) {
+                                             const KConst& kc, int& nupd, int& zend, int zmax, bool diag = false) {
   const double b5 = D[5], b9 = D[9], b14 = D[14];
-  const float x = update_any(p, zone, D, C, my, mz, kc);
+  const float x = update_any(p, zone, D, C, my, mz, kc, diag);
   nupd++;
   if (zone && nupd == zend) {
     if (zend < zmax && (b5 > 2.0 * D[5] || b9 > 2.0 * D[9] || b14 > 2.0 * D[14])) {
@@ -335,12 +418,15 @@ __device__ __forceinline__ float zone_update(TrkState& p, bool zone, double* D, 
   return x;
 }
 
-// Propagation with the covariance in FP64 (zone) or FP32.
+// Propagation with the covariance in FP64 (zone) or FP32; diag: the zone's
+// covariance is known to be diagonal (the first propagation after a
+// (re)seed, which follows the first update).
 __device__ __forceinline__ bool propagate_any(TrkState& p, bool zone, double* D, float* C, int row2, float x2,
-                                              const KConst& kc, uint32_t& flags) {
+                                              const KConst& kc, uint32_t& flags, bool diag = false) {
   Jac J;
   if (!prop_state(p, row2, x2, kc, flags, &J)) return false;
-  if (zone) cov_transport_d(D, J);
+  if (zone && diag) cov_transport_d_diag(D, J);
+  else if (zone) cov_transport_d(D, J);
   else cov_transport<float>(C, J.j02, J.j12, J.j13, J.kap);
   return true;
 }

@@ -277,14 +277,15 @@ struct RefitLane {
 template <bool Z>
 __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, const float* sX, RefitLane& w,
                                            TrkState& p, double* D, float* C, Chi2Acc& chi2, int& nupd, bool& ok,
-                                           uint32_t& flags, LocalTally& tl, int& zend) {
+                                           uint32_t& flags, LocalTally& tl, int& zend, bool& dg) {
   const int r = p.row - 1;
   if (r < w.r_in) return false;
   const bool zone = Z && nupd < zend;
-  if (!propagate_any(p, zone, D, C, r, sX[r], kc, flags)) {
+  if (!propagate_any(p, zone, D, C, r, sX[r], kc, flags, Z && dg)) {
     ok = false;
     return false;
   }
+  dg = false;
   tl.prop++;
   tl.prop64 += zone;
   if (w.cur_row == r) {
@@ -326,7 +327,7 @@ struct RefitIn {
 
 // Phase 1 of the refit: carry the follow state to the outermost owned row
 // (state only), then the updates with the covariance in FP64.
-__global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, WorkOrder next,
+__global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, WorkOrder next,
                                                   int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
@@ -378,13 +379,14 @@ __global__ void __launch_bounds__(128) k_refit_p1(GridView g, RefitIn in, KConst
       cov_seed<float>(C, kc);
       const bool zone0 = ZONE > 0;
       int zend = ZONE;
-      chi2.add(zone_update(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc, nupd, zend, 2 * ZONE));
+      chi2.add(zone_update(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc, nupd, zend, 2 * ZONE, true));  // diagonal seed
+      bool dg = zone0;
       if (zone0) tl.upd64++;
       else tl.upd32++;
       w.j++;
       w.advance();
       go = true;
-      while (go && nupd < zend) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend);
+      while (go && nupd < zend) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg);
       if (nupd < zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
@@ -498,7 +500,8 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
       continue;
     }
     int zend = 0;  // the zone is over
-    if (go) go = refit_step<false>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend);
+    bool dg = false;  // no FP64 zone in this phase
+    if (go) go = refit_step<false>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg);
   }
   tl.flush(cn, PH_REFIT_P2);
 }
