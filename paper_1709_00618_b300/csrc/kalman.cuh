@@ -296,14 +296,14 @@ struct UpdOut {
   float chi2;                // r^T S^-1 r
 };
 
-// 1/v in binary64 for v in the binary32 normal range: the binary32
-// reciprocal r of the narrowed v (relative error about 2^-23) refined by
-// one third-order step r (1 + e + e^2) with e = 1 - v r, the first terms of
-// r / (1 - e) = 1/v, which cubes the relative error (to about 2^-69), so
-// that the result is within rounding of 1/v: three dependent binary64
-// operations, where two Newton-Raphson steps take four.
+// 1/v in binary64 for v in the binary32 normal range: the hardware's
+// approximate binary32 reciprocal r of the narrowed v (relative error a few
+// 2^-23) refined by one third-order step r (1 + e + e^2) with e = 1 - v r,
+// the first terms of r / (1 - e) = 1/v, which cubes the relative error (to
+// about 2^-63), so that the result is within rounding of 1/v: three
+// dependent binary64 operations, where two Newton-Raphson steps take four.
 __device__ __forceinline__ double krcp(double v) {
-  const double r = widen(__frcp_rn(narrow(v)));
+  const double r = widen(kinv(narrow(v)));
   const double e = fma(-v, r, 1.0);
   return fma(r, fma(e, e, e), r);
 }
