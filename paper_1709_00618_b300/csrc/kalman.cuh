@@ -296,14 +296,22 @@ struct UpdOut {
   float chi2;                // r^T S^-1 r
 };
 
-// 1/v in binary64 for v in the binary32 normal range: the hardware's
-// approximate binary32 reciprocal r of the narrowed v (relative error a few
-// 2^-23) refined by one third-order step r (1 + e + e^2) with e = 1 - v r,
+// 1/v in binary64 for positive v in the binary32 normal range: the
+// hardware's approximate binary32 reciprocal r of v truncated to binary32
+// (relative error a few 2^-23) refined by one third-order step
+// r (1 + e + e^2) with e = 1 - v r,
 // the first terms of r / (1 - e) = 1/v, which cubes the relative error (to
 // about 2^-63), so that the result is within rounding of 1/v: three
 // dependent binary64 operations, where two Newton-Raphson steps take four.
 __device__ __forceinline__ double krcp(double v) {
-  const double r = widen(kinv(narrow(v)));
+  // the seed needs neither rounding nor special cases (v is a positive
+  // binary32 normal): v's top 32 significant bits as a binary32 (truncated,
+  // exponent rebiased by 1023 - 127 = 896), its approximate reciprocal, and
+  // that binary32 widened exactly (fraction to the top of the 52 bits)
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t f = ((hi - (896u << 20)) << 3) | (lo >> 29);
+  const uint32_t u = __float_as_uint(kinv(__uint_as_float(f)));
+  const double r = __hiloint2double((int)((u >> 3) + (896u << 20)), (int)(u << 29));
   const double e = fma(-v, r, 1.0);
   return fma(r, fma(e, e, e), r);
 }
