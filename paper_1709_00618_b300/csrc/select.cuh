@@ -246,9 +246,10 @@ __global__ void k_assign(const int32_t* __restrict__ f_n, const int32_t* __restr
 struct RefitLane {
   const int32_t* h;
   const uint8_t* hr;
-  int n, nf, j, cur, r_in;
-  int cur_row;      // row of the next owned hit (prefetched)
-  float2 cur_yz;    // its position (prefetched)
+  int n, nf, j, r_in;
+  int cur_row;      // row of the next owned hit (-1: none)
+  float2 cur_yz;    // its position
+  int nn_row, nn_c; // row (-1: none) and index of the owned hit after it
   uint32_t m[OWN_WORDS];
   const float2* yz;
   __device__ __forceinline__ bool owned(int slot) const {
@@ -258,19 +259,48 @@ struct RefitLane {
       if ((slot >> 5) == k) w = m[k];
     return (w >> (slot & 31)) & 1u;
   }
-  // next owned hit in update order, its row and position fetched ahead
-  __device__ __forceinline__ void advance() {
-    cur = -1;
-    cur_row = -1;
+  // The next owned hit in update order (row and position) is loaded ahead
+  // of its use.  The FP64 zone (phase 1), bound by its FP64 pipe, loads it
+  // in one stage (take: index, then position); the binary32 phase 2, whose
+  // row steps wait on their loads, in two (advance): taking a hit issues its
+  // successor's position load from an index loaded one take earlier
+  // (nn_*), so that no take waits for a load it issues.
+  // next_owned: the next owned slot at or after j (-1: none), j past it.
+  __device__ __forceinline__ int next_owned() {
     for (; j < n; j++) {
       const int slot = j < nf ? nf - 1 - j : j;
       if (owned(slot)) {
-        cur = slot;
-        cur_row = hr[slot];
-        cur_yz = __ldg(yz + h[slot]);
-        return;
+        j++;
+        return slot;
       }
     }
+    return -1;
+  }
+  __device__ __forceinline__ void load_after() {
+    const int slot = next_owned();
+    if (slot >= 0) {
+      nn_row = hr[slot];
+      nn_c = h[slot];
+    } else {
+      nn_row = -1;
+    }
+  }
+  // one stage: the next owned hit into cur_*
+  __device__ __forceinline__ void take() {
+    const int slot = next_owned();
+    if (slot >= 0) {
+      cur_row = hr[slot];
+      cur_yz = __ldg(yz + h[slot]);
+    } else {
+      cur_row = -1;
+    }
+  }
+  // two stages: the hit in nn_* into cur_*, the one after it into nn_*
+  // (after load_after has primed nn_*)
+  __device__ __forceinline__ void advance() {
+    cur_row = nn_row;
+    if (cur_row >= 0) cur_yz = __ldg(yz + nn_c);
+    load_after();
   }
 };
 
@@ -293,8 +323,8 @@ __device__ __forceinline__ bool refit_step(const GridView& g, const KConst& kc, 
     chi2.add(zone_update(p, zone, D, C, P.x, P.y, kc, nupd, zend, 2 * kc.fp64_updates));
     if (zone) tl.upd64++;
     else tl.upd32++;
-    w.j++;
-    w.advance();
+    if (Z) w.take();
+    else w.advance();
   }
   return true;
 }
@@ -374,7 +404,7 @@ __global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KCo
     __syncwarp();  // start the FP64 zone with the whole warp
     if (ok) {
       w.j = 0;
-      w.advance();  // the outermost owned hit, on row r_out
+      w.take();  // the outermost owned hit, on row r_out
       cov_seed<double>(D, kc);
       cov_seed<float>(C, kc);
       const bool zone0 = ZONE > 0;
@@ -383,8 +413,7 @@ __global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KCo
       bool dg = zone0;
       if (zone0) tl.upd64++;
       else tl.upd32++;
-      w.j++;
-      w.advance();
+      w.take();
       go = true;
       while (go && nupd < zend) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg);
       if (nupd < zend) {
@@ -483,6 +512,7 @@ __global__ void __launch_bounds__(128) k_refit_p2(GridView g, RefitIn in, KConst
     ok = s.ok != 0;
     go = s.go != 0;
     flags = (uint32_t)s.flags;
+    if (go) w.load_after();  // phase 1 loaded the next hit in one stage
   };
   // lanes refill together once kc.refill of them are idle (as the follow
   // phases 2 and 4)
