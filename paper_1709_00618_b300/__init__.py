@@ -51,7 +51,7 @@ class TpcError(RuntimeError):
 class TpcTuning(ctypes.Structure):
     _fields_ = [("block_clusters", ctypes.c_int32), ("block_follow", ctypes.c_int32),
                 ("ctas_per_sm_zone", ctypes.c_int32), ("ctas_per_sm_follow", ctypes.c_int32),
-                ("refill", ctypes.c_int32), ("chunks", ctypes.c_int32)]
+                ("refill", ctypes.c_int32), ("chunks", ctypes.c_int32), ("zone_rows", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: int(getattr(self, k)) for k, _ in self._fields_}

@@ -409,6 +409,34 @@ __device__ __forceinline__ void zone_bwd_store(FollowWork* W, int64_t t, const L
   for (int i = 0; i < OUT_WORDS; i++) s.out[i] = so[i * SNAP_STRIDE];
 }
 
+// A backward zone parked by phase 3 (zone_bwd_store, plus zend), for its
+// zone tail kernel: the fields the zone's row steps use, and the output
+// snapshot into the lane's shared-memory slot.
+__device__ __forceinline__ void zone_tail_bwd_load(const FollowWork* W, int64_t t, Lane& w, TrkState& p,
+                                                   Chi2Acc& chi2, float* so) {
+  const FollowWork& s = W[t];
+  w.ubase = s.w.ubase;
+  w.r0 = s.w.r0;
+  w.nf = s.w.nf;
+  w.nb = s.w.nb;
+  w.kf = s.w.kf;
+  w.misses = s.w.misses;
+  w.nupd = s.w.nupd;
+  w.zend = s.w.zend;
+  w.nx_row = s.w.nx_row;
+  w.nx_c = s.w.nx_c;
+  w.nx_yz = s.w.nx_yz;
+  w.flags = s.w.flags;
+  w.seed_fail = false;
+  w.tr = s.w.tr;
+  w.snap = false;
+  w.dg = false;
+  p = s.p;
+  chi2 = s.chi2;
+#pragma unroll
+  for (int i = 0; i < OUT_WORDS; i++) so[i * SNAP_STRIDE] = s.out[i];
+}
+
 // The binary32 phases touch only their half of the parked lane, so that
 // neither carries the other's state in registers (the large-input builds
 // spilled it) nor moves it to and from memory.  Phase 2 reads the forward
@@ -520,15 +548,66 @@ __device__ __forceinline__ void load_tables(float* sX, float* sYH) {
   __syncthreads();
 }
 
-// Phase 1: seed and the forward pass while its covariance is in FP64.  A
-// warp takes 32 consecutive tracklets at a time and starts their zones
-// together; the grid is the resident capacity (one wave).
+// Zone tails.  A zone kernel's warp runs its 32 tracklets' zones in step,
+// so each warp ran to its longest zone while most lanes had ended theirs at
+// about ten steps (the pick-up's misses and rows without a forward cluster
+// lengthen a few): 22-26% of the lane slots of the FP64 instructions were
+// idle, and the FP64 pipe spends the same time on an instruction whatever
+// its active lanes.  So a zone kernel takes kc.zone_steps steps in step and
+// parks a tracklet whose zone is still open (its FP64 covariance in a list
+// slot of its own); a tail kernel then finishes those zones, 32 parked
+// tracklets to a warp.  Chunk c of nc owns slots [c cap / nc, (c+1) cap / nc)
+// of a pass's list; a tracklet that finds its chunk's slots taken finishes
+// its zone in place.
+struct ZoneTail {
+  int32_t* list;  // [2 * cap] tracklet of each slot (pass 0: forward, 1: backward)
+  double* cov;    // [2 * cap * 15] its FP64 covariance
+};
+__device__ __forceinline__ int64_t tail_base(const KConst& kc, int pass, int chunk, int nchunk) {
+  return pass * kc.zone_tail_cap + kc.zone_tail_cap * chunk / nchunk;
+}
+__device__ __forceinline__ int64_t tail_size(const KConst& kc, int chunk, int nchunk) {
+  return kc.zone_tail_cap * (chunk + 1) / nchunk - kc.zone_tail_cap * chunk / nchunk;
+}
+// A list slot for each lane with pend (all 32 lanes make the call; one
+// atomic per warp); -1 for the others and when the chunk's slots are taken.
+__device__ __forceinline__ int64_t tail_claim(const KConst& kc, Counts* cn, int pass, int chunk, int nchunk,
+                                              bool pend) {
+  const unsigned m = __ballot_sync(FULL_MASK, pend);
+  if (!m) return -1;
+  const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&cn->zone_pend[pass * MAX_CHUNKS + chunk], __popc(m));
+  base = __shfl_sync(FULL_MASK, base, leader);
+  const int64_t k = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+  return pend && k < tail_size(kc, chunk, nchunk) ? tail_base(kc, pass, chunk, nchunk) + k : -1;
+}
+__device__ __forceinline__ void tail_park(const ZoneTail& zt, int64_t slot, int64_t t, const double* D) {
+  zt.list[slot] = (int32_t)t;
+#pragma unroll
+  for (int i = 0; i < 15; i++) zt.cov[slot * 15 + i] = D[i];
+}
+// Zone steps of one lane: up to cap steps (0: until the zone or the pass
+// ends).  True while the pass goes on.
+__device__ __forceinline__ bool fwd_zone(const GridView& g, const int32_t* __restrict__ up_m, const KConst& kc,
+                                         const float* sX, const float* sYH, Lane& w, TrkState& p, double* D,
+                                         float* C, Chi2Acc& chi2, LocalTally& tl, int cap) {
+  bool go = true;
+  for (int k = 0; go && w.nupd < w.zend && (cap == 0 || k < cap); k++)
+    go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr);
+  return go;
+}
+
+// Phase 1: seed and the forward pass while its covariance is in FP64 (the
+// first kc.zone_steps[0] row steps of the zone; the rest in the tail kernel
+// k_follow_p1t).  A warp takes 32 consecutive tracklets at a time and starts
+// their zones together; the grid is the resident capacity (one wave).
 __global__ void __launch_bounds__(128, 4) k_follow_p1(GridView g, const int32_t* __restrict__ tl_start,
                                                    const int32_t* __restrict__ tl_len,
                                                    const int32_t* __restrict__ tl_end,
                                                    const int32_t* __restrict__ up_m, KConst kc, FollowOut o,
-                                                   FollowWork* W, WorkOrder next, int chunk, int nchunk,
-                                                   Counts* cn) {
+                                                   FollowWork* W, ZoneTail zt, WorkOrder next, int chunk,
+                                                   int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   load_tables(sX, sYH);
   if (fatal(cn)) return;
@@ -589,7 +668,64 @@ __global__ void __launch_bounds__(128, 4) k_follow_p1(GridView g, const int32_t*
       else tl.upd32++;
       w.fwd = p;
       go = true;
-      while (go && w.nupd < w.zend) go = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr);
+    }
+    // round 0: the in-step rows; round 1: the rest of a zone that found no
+    // tail slot (one copy of the row step in the code)
+    int64_t slot = -1;
+#pragma unroll 1
+    for (int round = 0; round < 2; round++) {
+      if (go && slot < 0) go = fwd_zone(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, round ? 0 : kc.zone_steps[0]);
+      if (round) break;
+      slot = tail_claim(kc, cn, 0, chunk, nchunk, go && w.nupd < w.zend);
+    }
+    if (valid) {
+      if (slot >= 0) {
+        tail_park(zt, slot, t, D);
+      } else if (w.nupd < w.zend) {
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+      }
+      work_store(W, t, w, p, C, chi2, go);
+    }
+    order_count(next, t, valid && slot < 0, go ? NROW - 1 - p.row : 0);  // rows left outward
+  }
+  tl.flush(cn, PH_FOLLOW_P1);
+}
+
+// Zone tail of phase 1: the forward zones phase 1 parked, 32 to a warp,
+// each to the end of its zone (or of its pass).
+__global__ void __launch_bounds__(128, 4) k_follow_p1t(GridView g, const int32_t* __restrict__ up_m, KConst kc,
+                                                    FollowWork* W, ZoneTail zt, WorkOrder next, int chunk,
+                                                    int nchunk, Counts* cn) {
+  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  load_tables(sX, sYH);
+  if (fatal(cn)) return;
+  const int64_t n = min((int64_t)cn->zone_pend[0 * MAX_CHUNKS + chunk], tail_size(kc, chunk, nchunk));
+  const int64_t base = tail_base(kc, 0, chunk, nchunk);
+  LocalTally tl;
+  double D[15];
+  float C[15];
+  for (;;) {
+    const int64_t k = warp_fetch(work_counter(cn, PH_FOLLOW_P1T, chunk), FULL_MASK);
+    if (__shfl_sync(FULL_MASK, k, 0) >= n) break;
+    const bool valid = k < n;
+    int64_t t = 0;
+    Lane w;
+    TrkState p;
+    Chi2Acc chi2;
+    bool go = false;
+    if (valid) {
+      t = zt.list[base + k];
+      const FollowWork& s = W[t];
+      w = s.w;
+      p = s.p;
+      chi2 = s.chi2;
+#pragma unroll
+      for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
+    }
+    __syncwarp();
+    if (valid) {
+      go = fwd_zone(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, 0);
       if (w.nupd < w.zend) {
 #pragma unroll
         for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
@@ -660,11 +796,34 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
   tl.flush(cn, PH_FOLLOW_P2);
 }
 
+__device__ __forceinline__ bool bwd_zone(const GridView& g, const KConst& kc, const float* sX, const float* sYH,
+                                         Lane& w, TrkState& p, double* D, float* C, Chi2Acc& chi2, LocalTally& tl,
+                                         double* snap, float* so, int cap) {
+  bool go = true;
+  for (int k = 0; go && w.nupd < w.zend && (cap == 0 || k < cap); k++)
+    go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, so);
+  return go;
+}
+// The end of a backward zone kernel's tracklet: its FP64 covariance moved
+// to C if the pass ended inside the zone, the output snapshot taken, and
+// what the later phases read parked.
+__device__ __forceinline__ void zone_bwd_end(FollowWork* W, int64_t t, Lane& w, const TrkState& p, const double* D,
+                                             float* C, const Chi2Acc& chi2, const double* snap, float* so, bool go) {
+  if (w.nupd < w.zend) {
+#pragma unroll
+    for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+  }
+  zone_snap_take(w, snap, so);
+  zone_bwd_store(W, t, w, p, C, chi2, so, go);
+}
+
 // Phase 3: re-seed at the outermost forward cluster and run the backward
 // pass while its covariance is in FP64 (warps take 32 tracklets at a time,
-// as phase 1).
+// as phase 1; the zone's first kc.zone_steps[1] steps, the rest in the tail
+// kernel k_follow_p3t).
 __global__ void __launch_bounds__(128, 4) k_follow_p3(GridView g, KConst kc, FollowOut o, FollowWork* W,
-                                                   WorkOrder next, int chunk, int nchunk, Counts* cn) {
+                                                   ZoneTail zt, WorkOrder next, int chunk, int nchunk,
+                                                   Counts* cn) {
   __shared__ float sX[NROW + 1], sYH[NROW + 1];
   __shared__ double sSnap[15 * SNAP_STRIDE];
   __shared__ float sOut[OUT_WORDS * SNAP_STRIDE];
@@ -702,23 +861,76 @@ __global__ void __launch_bounds__(128, 4) k_follow_p3(GridView g, KConst kc, Fol
       }
     }
     __syncwarp();  // the zones of the warp's lanes start together
-    if (go) {
+    const bool run = go;
+    if (run) {
       const bool zone0 = kc.fp64_updates > 0;
       lane_update<true>(w, kc, p, zone0, D, C, __ldg(g.yz + w.hits[w.nf - 1]), chi2, 1, true);  // diagonal seed
       w.dg = zone0;
       if (zone0) tl.upd64++;
       else tl.upd32++;
       keep_output<true>(w, p, w.nupd < w.zend, D, C, chi2, snap, so);
-      while (go && w.nupd < w.zend) go = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, so);
-      if (w.nupd < w.zend) {
-#pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
-      }
-      zone_snap_take(w, snap, so);
     }
+    // round 0: the in-step rows; round 1: the rest of a zone that found no
+    // tail slot (one copy of the row step in the code)
+    int64_t slot = -1;
+#pragma unroll 1
+    for (int round = 0; round < 2; round++) {
+      if (go && slot < 0) go = bwd_zone(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, so, round ? 0 : kc.zone_steps[1]);
+      if (round) break;
+      slot = tail_claim(kc, cn, 1, chunk, nchunk, go && w.nupd < w.zend);
+    }
+    if (run) {
+      if (slot >= 0) {
+        tail_park(zt, slot, t, D);
+        W[t].w.zend = w.zend;
+      }
+      zone_bwd_end(W, t, w, p, D, C, chi2, snap, so, go);
+    } else if (valid) {
+      W[t].go = 0;  // a seed failure: the later phases read only the lane's forward fields
+    }
+    order_count(next, t, valid && slot < 0, go ? p.row : 0);  // rows left inward
+  }
+  tl.flush(cn, PH_FOLLOW_P3);
+}
+
+// Zone tail of phase 3: the backward zones phase 3 parked, 32 to a warp.
+__global__ void __launch_bounds__(128, 4) k_follow_p3t(GridView g, KConst kc, FollowOut o, FollowWork* W,
+                                                    ZoneTail zt, WorkOrder next, int chunk, int nchunk,
+                                                    Counts* cn) {
+  __shared__ float sX[NROW + 1], sYH[NROW + 1];
+  __shared__ double sSnap[15 * SNAP_STRIDE];
+  __shared__ float sOut[OUT_WORDS * SNAP_STRIDE];
+  load_tables(sX, sYH);
+  if (fatal(cn)) return;
+  double* snap = sSnap + threadIdx.x;
+  float* so = sOut + threadIdx.x;
+  const int64_t n = min((int64_t)cn->zone_pend[1 * MAX_CHUNKS + chunk], tail_size(kc, chunk, nchunk));
+  const int64_t base = tail_base(kc, 1, chunk, nchunk);
+  LocalTally tl;
+  double D[15];
+  float C[15];
+  for (;;) {
+    const int64_t k = warp_fetch(work_counter(cn, PH_FOLLOW_P3T, chunk), FULL_MASK);
+    if (__shfl_sync(FULL_MASK, k, 0) >= n) break;
+    const bool valid = k < n;
+    int64_t t = 0;
+    Lane w;
+    TrkState p;
+    Chi2Acc chi2;
+    bool go = false;
     if (valid) {
-      if (w.seed_fail) W[t].go = 0;  // the later phases read only the lane's forward fields
-      else zone_bwd_store(W, t, w, p, C, chi2, so, go);
+      t = zt.list[base + k];
+      zone_tail_bwd_load(W, t, w, p, chi2, so);
+      w.hits = o.hits + t * NROW;
+      w.hrow = o.hrow + t * NROW;
+      w.cn = cn;
+#pragma unroll
+      for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
+    }
+    __syncwarp();
+    if (valid) {
+      go = bwd_zone(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, so, 0);
+      zone_bwd_end(W, t, w, p, D, C, chi2, snap, so, go);
     }
     order_count(next, t, valid, go ? p.row : 0);  // rows left inward
   }

@@ -127,7 +127,7 @@ struct Layout {
       cend, owner, cluster_track, track_clusters;
   size_t rs_cnt, rs_start, zmin, zmax, par, nbins, bin_base;
   size_t bin_cnt, bin_start;
-  size_t own_mask, own_rng, fwork, rwork, okey, order, obins;
+  size_t own_mask, own_rng, fwork, rwork, okey, order, obins, ztail_list, ztail_cov;
   size_t tl_start, tl_len, tl_end, f_n, f_nf, f_nb, f_flags, f_row, hits, hrow, f_par, f_zref, f_cov, f_chi2, keep,
       tidx, nown, tl_track, track_tl, tcount, toff, tracks;
   size_t parts;
@@ -136,6 +136,10 @@ struct Layout {
 };
 
 constexpr int TRACE_RECORDS = 2048;
+// Slots per pass of the zone tail lists (follow.cuh): about 10% of the
+// zones outlast the zone kernels' in-step rows; a tracklet that finds no
+// slot finishes its zone in place.
+size_t zone_tail_cap(size_t T) { return T / 4 + 64; }
 
 Layout make_layout(const Caps& c) {
   Layout L{};
@@ -206,6 +210,8 @@ Layout make_layout(const Caps& c) {
   L.nown = take(4 * T);
   L.own_mask = take(4 * OWN_WORDS * T);
   L.fwork = take(sizeof(FollowWork) * T);
+  L.ztail_list = take(4 * 2 * zone_tail_cap(T));
+  L.ztail_cov = take(8 * 15 * 2 * zone_tail_cap(T));
   L.rwork = take(sizeof(RefitWork) * M);
   L.okey = take(std::max(T, M));
   L.order = take(4 * std::max(T, M));
@@ -263,6 +269,7 @@ struct tpc_ctx {
   int ctas_follow = 0;   // cap on CTAs per SM of the refilling Kalman kernels (64: occupancy; 0: by size)
   int refill = 8;        // idle lanes that trigger a warp's refill
   int chunks = 0;        // Kalman-stage chunks (2: zone and FP32 kernels of different chunks overlap; 0: 1)
+  int zone_rows = 0;     // zone rows in step before the zone tail kernels (0: by size; NROW or more: no tails)
   int graph_chunks = 0;  // chunks and refilling-kernel CTAs per SM of the captured graph
   int graph_ctas = 0;
   bool graph_large = false;  // the size class the graph's kernel variants were chosen for
@@ -345,6 +352,7 @@ int fail(tpc_ctx* c, int code, const char* fmt, ...) {
 KConst make_kconst(const tpc_config& c, const Caps& caps) {
   KConst k{};
   k.inner_steps = 1;
+  k.zone_tail_cap = (int64_t)zone_tail_cap((size_t)caps.tl);
   k.K = (float)(0.299792458e-3 * c.bz_kg);
   k.V = (float)(c.sigma * c.sigma);
   k.Vd = c.sigma * c.sigma;
@@ -595,6 +603,14 @@ void enqueue_find(tpc_ctx* ctx) {
   int32_t* bin_cnt = ctx->ptr<int32_t>(L.bin_cnt);
   int32_t* bin_start = ctx->ptr<int32_t>(L.bin_start);
   ctx->kc.inner_steps = ctx->n < kLargeBatch ? 16 : 4;  // 10 ms timeframe: 1 step 69.0 ms, 2 68.7, 4 68.6, 8 68.8
+  // zone rows in step before a zone goes to the tail kernels (follow.cuh):
+  // on the 10 ms timeframe p1 10.03 ms without, 9.50 with 9 rows, 9.72 with
+  // 10; p3 11.20 without, 10.46 with 9, 10.27 with 10, 10.75 with 11.  Below
+  // kLargeBatch clusters none (central event: the tail kernels lengthen the
+  // follow stage, 1.43 -> 1.49 ms)
+  ctx->kc.zone_steps[0] = ctx->n < kLargeBatch ? 0 : 9;
+  ctx->kc.zone_steps[1] = ctx->n < kLargeBatch ? 0 : 10;
+  if (ctx->zone_rows > 0) ctx->kc.zone_steps[0] = ctx->kc.zone_steps[1] = ctx->zone_rows < NROW ? ctx->zone_rows : 0;
   ctx->mark(0);
   // a2 grid
   k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax),
@@ -660,6 +676,7 @@ void enqueue_find(tpc_ctx* ctx) {
   // the SMs with the other's FP32 phase.
   {
     FollowWork* W = ctx->ptr<FollowWork>(L.fwork);
+    const ZoneTail zt{ctx->ptr<int32_t>(L.ztail_list), ctx->ptr<double>(L.ztail_cov)};
     const int bf = ctx->block_follow;
     const int nc = ctx->prof ? 1 : effective_chunks(ctx);
     // longest first below kLargeBatch clusters, where the longest tracklet
@@ -670,7 +687,10 @@ void enqueue_find(tpc_ctx* ctx) {
     auto follow_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
       k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
-          ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, ord(0, c), c, nc, cn);
+          ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, zt, ord(0, c), c, nc, cn);
+      if (ctx->kc.zone_steps[0] > 0)
+        k_follow_p1t<<<persistent_grid(ctx, k_follow_p1t, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
+            grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, W, zt, ord(0, c), c, nc, cn);
       if (after_p1) cudaEventRecord(after_p1, st);
       if (longest_first)
         k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 0, c), &cn->n_tracklets, c, nc, cn);
@@ -680,7 +700,10 @@ void enqueue_find(tpc_ctx* ctx) {
           grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
       if (nc == 1) ctx->mark_k(1);
       k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
-          grid_view(ctx), ctx->kc, follow_out(ctx), W, ord(1, c), c, nc, cn);
+          grid_view(ctx), ctx->kc, follow_out(ctx), W, zt, ord(1, c), c, nc, cn);
+      if (ctx->kc.zone_steps[1] > 0)
+        k_follow_p3t<<<persistent_grid(ctx, k_follow_p3t, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
+            grid_view(ctx), ctx->kc, follow_out(ctx), W, zt, ord(1, c), c, nc, cn);
       if (longest_first)
         k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
       if (nc == 1) ctx->mark_k(2);
@@ -1435,6 +1458,7 @@ void get_tuning(const tpc_ctx* ctx, tpc_tuning* t) {
   t->ctas_per_sm_follow = ctx->ctas_follow;
   t->refill = ctx->refill;
   t->chunks = ctx->chunks;
+  t->zone_rows = ctx->zone_rows;
 }
 void apply_tuning(tpc_ctx* ctx, const tpc_tuning* t) {
   if (t->block_clusters > 0) ctx->block_clusters = t->block_clusters;
@@ -1443,6 +1467,7 @@ void apply_tuning(tpc_ctx* ctx, const tpc_tuning* t) {
   if (t->ctas_per_sm_follow > 0) ctx->ctas_follow = t->ctas_per_sm_follow;
   if (t->refill > 0) ctx->refill = ctx->kc.refill = t->refill;
   if (t->chunks > 0) ctx->chunks = t->chunks;
+  if (t->zone_rows > 0) ctx->zone_rows = t->zone_rows;
   if (ctx->graph) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
@@ -1487,8 +1512,8 @@ int tpc_autotune(tpc_ctx* ctx, int32_t reps, tpc_tuning* best_out, float* best_m
   if (cur.ctas_per_sm_follow <= 0) cur.ctas_per_sm_follow = effective_ctas_follow(ctx);
   int best[6] = {cur.block_clusters, cur.block_follow, cur.ctas_per_sm_zone, cur.ctas_per_sm_follow, cur.refill,
                  cur.chunks};
-  auto as_tuning = [](const int* v) {
-    tpc_tuning t;
+  auto as_tuning = [&cur](const int* v) {
+    tpc_tuning t = cur;  // fields the autotuner does not vary keep their values
     t.block_clusters = v[0];
     t.block_follow = v[1];
     t.ctas_per_sm_zone = v[2];

@@ -94,8 +94,11 @@ def test_rerun_without_reload_repeats_every_kernel(trk):
 def test_large_batch_shapes_give_the_same_bytes():
     """From 4 Mi clusters the Kalman stage runs its large-input shapes (index
     order, the backward refit rows in a kernel of their own, four zone CTAs
-    per SM); split in two chunks on two streams, with one zone CTA per SM or
-    with refilling at once, it must give the same bytes."""
+    per SM, zones finished by the zone tail kernels); split in two chunks on
+    two streams, with one zone CTA per SM, with refilling at once, or with
+    other zone rows in step (1: most zones parked, the tail lists full and
+    the rest finished in place; 159: no tail kernels), it must give the same
+    bytes."""
     import paper_1709_00618_b300 as tpc
     ev = synth.timeframe(seed=2, length_ms=0.6)
     assert len(ev.clusters) >= 4 << 20
@@ -103,13 +106,33 @@ def test_large_batch_shapes_give_the_same_bytes():
     with tpc.Tracker(device=0) as t:
         ref_tracks, ref_ct, _ = t.track(ev.clusters, graph=True)
         ref = [t.stage(nm).tobytes() for nm in names]
-        for shape in (dict(chunks=2), dict(chunks=2, ctas_per_sm_zone=1, refill=1), dict(ctas_per_sm_follow=3)):
+        for shape in (dict(chunks=2), dict(chunks=2, ctas_per_sm_zone=1, refill=1), dict(ctas_per_sm_follow=3),
+                      dict(zone_rows=1), dict(zone_rows=4, chunks=1), dict(zone_rows=159)):
             t.set_tuning(**shape)
             for graph in (False, True):
                 tracks, ct, _ = t.track(ev.clusters, graph=graph)
                 assert tracks.tobytes() == ref_tracks.tobytes(), shape
                 assert np.array_equal(ct, ref_ct), shape
                 assert [t.stage(nm).tobytes() for nm in names] == ref, shape
+
+
+def test_zone_tails_on_small_batches_give_the_same_bytes():
+    """Below 4 Mi clusters the zones run to their ends in the zone kernels;
+    with zone tail kernels (tracklets filed for the longest-first order by
+    the tail kernel that ends their zone) the results must not change."""
+    import paper_1709_00618_b300 as tpc
+    cl = synth.central_event(seed=1).clusters
+    names = ("f_n", "f_hits", "f_par", "f_cov", "f_chi2", "tl_track")
+    with tpc.Tracker(device=0) as t:
+        ref_tracks, ref_ct, _ = t.track(cl)
+        ref = [t.stage(nm).tobytes() for nm in names]
+        for rows in (1, 3, 9):
+            t.set_tuning(zone_rows=rows)
+            for graph in (False, True):
+                tracks, ct, _ = t.track(cl, graph=graph)
+                assert tracks.tobytes() == ref_tracks.tobytes(), rows
+                assert np.array_equal(ct, ref_ct), rows
+                assert [t.stage(nm).tobytes() for nm in names] == ref, rows
 
 
 def test_link_skip_variant_parity():
