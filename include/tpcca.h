@@ -379,10 +379,11 @@ typedef struct {
                                  on two streams, one kernel apart, so that one half's FP64 zone shares the
                                  SMs with the other half's FP32 phase (profiled runs use 1); reported as 0
                                  while the default (1) applies */
-  int32_t zone_rows;          /* row steps the FP64-zone kernels take with a warp's 32 tracklets in step before
-                                 a zone still open goes on in a zone tail kernel, 32 such tracklets to a warp
-                                 (both passes; 159 or more: no tail kernels); reported as 0 while the default
-                                 applies: 9 forward and 10 backward from 4 Mi loaded clusters on, else none */
+  int32_t zone_rows;          /* row steps the FP64-zone kernels take with a warp's 32 tracklets (tracks) in
+                                 step before a zone still open goes on in a zone tail kernel, 32 such items to
+                                 a warp (follow forward and backward passes and refit; 159 or more: no tail
+                                 kernels); reported as 0 while the default applies: 9 forward, 10 backward and
+                                 10 in the refit from 4 Mi loaded clusters on, else none */
 } tpc_tuning;
 
 int tpc_get_tuning(tpc_ctx *ctx, tpc_tuning *t);

@@ -55,8 +55,8 @@ struct Counts {
   uint32_t status;    // ST_* bits
   int32_t n_track_clusters;
   int32_t n32;         // clusters as int32 (length source of the per-cluster scans)
-  int32_t work_next[18];  // work counters of the persistent Kalman kernels, [fetch phase x chunk]
-  int32_t zone_pend[4];   // tracklets deferred to a zone tail kernel, [pass x chunk] (follow.cuh)
+  int32_t work_next[20];  // work counters of the persistent Kalman kernels, [fetch phase x chunk]
+  int32_t zone_pend[6];   // items deferred to a zone tail kernel, [pass x chunk] (follow.cuh)
   // work counters of the follow (a6) and refit (a8) kernels
   unsigned long long n_prop;    // helix propagations with covariance transport
   unsigned long long n_upd32;   // FP32 Kalman updates
@@ -72,12 +72,14 @@ struct Counts {
 
 // Kalman kernels, in launch order, for the per-kernel work counters.
 enum { PH_FOLLOW_P1 = 0, PH_FOLLOW_P2, PH_FOLLOW_P3, PH_FOLLOW_P4, PH_REFIT_P1, PH_REFIT_P2, PH_COUNT };
-// Phase 4r and the zone tail kernels of phases 1 and 3 fetch their work
-// with counters of their own; their work is tallied with phases 4, 1 and 3.
+// Phase 4r and the zone tail kernels of follow phases 1 and 3 and of refit
+// phase 1 fetch their work with counters of their own; their work is
+// tallied with follow phases 4, 1 and 3 and refit phase 1.
 constexpr int PH_FOLLOW_P4R = PH_COUNT;
 constexpr int PH_FOLLOW_P1T = PH_COUNT + 1;
 constexpr int PH_FOLLOW_P3T = PH_COUNT + 2;
-constexpr int PH_FETCH = PH_COUNT + 3;  // work counters per chunk
+constexpr int PH_REFIT_P1T = PH_COUNT + 3;
+constexpr int PH_FETCH = PH_COUNT + 4;  // work counters per chunk
 
 // The Kalman stage may split its items into chunks whose zone and FP32
 // kernels run concurrently on two streams (the FP64 pipe of one chunk's
@@ -139,10 +141,10 @@ struct KConst {
   // warp-wide votes; 4 on large inputs, where lanes idle until the check)
   int32_t inner_steps;
   // row steps the zone kernels take with a warp's 32 tracklets in step,
-  // [forward, backward]; a zone still open after them goes on in the zone
-  // tail kernel (0: no limit), whose list holds up to zone_tail_cap
-  // tracklets per pass
-  int32_t zone_steps[2];
+  // [follow forward, follow backward, refit]; a zone still open after them
+  // goes on in the zone tail kernel (0: no limit), whose list holds up to
+  // zone_tail_cap items per pass
+  int32_t zone_steps[3];
   int64_t zone_tail_cap;
 };
 

@@ -560,8 +560,8 @@ __device__ __forceinline__ void load_tables(float* sX, float* sYH) {
 // of a pass's list; a tracklet that finds its chunk's slots taken finishes
 // its zone in place.
 struct ZoneTail {
-  int32_t* list;  // [2 * cap] tracklet of each slot (pass 0: forward, 1: backward)
-  double* cov;    // [2 * cap * 15] its FP64 covariance
+  int32_t* list;  // [3 * cap] item of each slot (pass 0: follow forward, 1: follow backward, 2: refit)
+  double* cov;    // [3 * cap * 15] its FP64 covariance
 };
 __device__ __forceinline__ int64_t tail_base(const KConst& kc, int pass, int chunk, int nchunk) {
   return pass * kc.zone_tail_cap + kc.zone_tail_cap * chunk / nchunk;

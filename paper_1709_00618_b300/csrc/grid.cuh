@@ -28,7 +28,7 @@ __global__ void k_rs_init(int32_t* __restrict__ cnt, uint32_t* __restrict__ zmin
   // a graph replay, the autotuner's trials) starts from the state a load
   // leaves.  Work counters of every Kalman kernel and chunk, status, tallies.
   if (gtid() < PH_FETCH * MAX_CHUNKS) cn->work_next[gtid()] = 0;
-  if (gtid() < 2 * MAX_CHUNKS) cn->zone_pend[gtid()] = 0;
+  if (gtid() < 3 * MAX_CHUNKS) cn->zone_pend[gtid()] = 0;
   if (gtid() < PH_COUNT * 5) (&cn->phase_work[0][0])[gtid()] = 0ull;
   if (gtid() == 0) {
     cn->status = 0u;

@@ -335,7 +335,7 @@ struct RefitWork {
   TrkState p;
   float C[15];
   Chi2Acc chi2;
-  int32_t nupd, ok, go, flags, r_out, nown, unit, t;
+  int32_t nupd, ok, go, flags, r_out, nown, unit, t, zend;
 };
 
 struct RefitIn {
@@ -355,10 +355,24 @@ struct RefitIn {
   const int32_t* toff;
 };
 
+// Zone row steps of one refit lane: up to cap (0: until the zone or the
+// refit ends).  True while the refit goes on.
+__device__ __forceinline__ bool refit_zone(const GridView& g, const KConst& kc, const float* sX, RefitLane& w,
+                                           TrkState& p, double* D, float* C, Chi2Acc& chi2, int& nupd, bool& ok,
+                                           uint32_t& flags, LocalTally& tl, int& zend, bool& dg, int cap) {
+  bool go = true;
+  for (int k = 0; go && nupd < zend && (cap == 0 || k < cap); k++)
+    go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg);
+  return go;
+}
+
 // Phase 1 of the refit: carry the follow state to the outermost owned row
-// (state only), then the updates with the covariance in FP64.
-__global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, WorkOrder next,
-                                                  int chunk, int nchunk, Counts* cn) {
+// (state only), then the updates with the covariance in FP64 (the zone's
+// first kc.zone_steps[2] rows with a warp's 32 tracks in step, the rest of
+// an open zone in the zone tail kernel k_refit_p1t, as the follow stage's
+// zone kernels do).
+__global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KConst kc, RefitWork* RW, ZoneTail zt,
+                                                  WorkOrder next, int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1];
   for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
   __syncthreads();
@@ -399,29 +413,40 @@ __global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KCo
       ok = prop_state(p, r, sX[r], kc, flags, nullptr);
     Chi2Acc chi2;
     chi2.reset();
-    int nupd = 0;
-    bool go = false;
+    int nupd = 0, zend = ZONE;
+    bool go = false, dg = false;
+    const bool run = ok;
     __syncwarp();  // start the FP64 zone with the whole warp
-    if (ok) {
+    if (run) {
       w.j = 0;
       w.take();  // the outermost owned hit, on row r_out
       cov_seed<double>(D, kc);
       cov_seed<float>(C, kc);
       const bool zone0 = ZONE > 0;
-      int zend = ZONE;
       chi2.add(zone_update(p, zone0, D, C, w.cur_yz.x, w.cur_yz.y, kc, nupd, zend, 2 * ZONE, true));  // diagonal seed
-      bool dg = zone0;
+      dg = zone0;
       if (zone0) tl.upd64++;
       else tl.upd32++;
       w.take();
       go = true;
-      while (go && nupd < zend) go = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg);
-      if (nupd < zend) {
-#pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
-      }
     }
-    order_count(next, m, valid, go && ok ? p.row - w.r_in : 0);  // rows left inward
+    // round 0: the in-step rows; round 1: the rest of a zone that found no
+    // tail slot (one copy of the row step in the code)
+    int64_t slot = -1;
+#pragma unroll 1
+    for (int round = 0; round < 2; round++) {
+      if (go && slot < 0)
+        go = refit_zone(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg, round ? 0 : kc.zone_steps[2]);
+      if (round) break;
+      slot = tail_claim(kc, cn, 2, chunk, nchunk, go && nupd < zend);
+    }
+    if (slot >= 0) {
+      tail_park(zt, slot, m, D);
+    } else if (run && nupd < zend) {
+#pragma unroll
+      for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+    }
+    order_count(next, m, valid && slot < 0, go && ok ? p.row - w.r_in : 0);  // rows left inward
     if (!valid) continue;
     RefitWork& s = RW[m];
     s.w = w;
@@ -437,6 +462,67 @@ __global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KCo
     s.nown = in.nown[t];
     s.unit = __ldg(g.rs_of + w.h[0]) / NROW;
     s.t = t;
+    s.zend = zend;
+  }
+  tl.flush(cn, PH_REFIT_P1);
+}
+
+// Zone tail of refit phase 1: the zones phase 1 parked, 32 to a warp.
+__global__ void __launch_bounds__(128, 4) k_refit_p1t(GridView g, KConst kc, RefitWork* RW, ZoneTail zt,
+                                                   WorkOrder next, int chunk, int nchunk, Counts* cn) {
+  __shared__ float sX[NROW + 1];
+  for (int i = threadIdx.x; i < NROW; i += blockDim.x) sX[i] = g_row_x[i];
+  __syncthreads();
+  if (fatal(cn)) return;
+  const int64_t n = min((int64_t)cn->zone_pend[2 * MAX_CHUNKS + chunk], tail_size(kc, chunk, nchunk));
+  const int64_t base = tail_base(kc, 2, chunk, nchunk);
+  LocalTally tl;
+  double D[15];
+  float C[15];
+  for (;;) {
+    const int64_t k = warp_fetch(work_counter(cn, PH_REFIT_P1T, chunk), FULL_MASK);
+    if (__shfl_sync(FULL_MASK, k, 0) >= n) break;
+    const bool valid = k < n;
+    int64_t m = 0;
+    RefitLane w;
+    TrkState p;
+    Chi2Acc chi2;
+    int nupd = 0, zend = 0;
+    bool ok = false, go = false, dg = false;
+    uint32_t flags = 0;
+    if (valid) {
+      m = zt.list[base + k];
+      const RefitWork& s = RW[m];
+      w = s.w;
+      p = s.p;
+      chi2 = s.chi2;
+      nupd = s.nupd;
+      zend = s.zend;
+      flags = (uint32_t)s.flags;
+      ok = true;
+#pragma unroll
+      for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
+    }
+    __syncwarp();
+    if (valid) {
+      go = refit_zone(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg, 0);
+      if (nupd < zend) {
+#pragma unroll
+        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+      }
+      RefitWork& s = RW[m];
+      s.w = w;
+      s.p = p;
+#pragma unroll
+      for (int i = 0; i < 15; i++) s.C[i] = C[i];
+      s.chi2 = chi2;
+      s.nupd = nupd;
+      s.ok = ok;
+      s.go = go && ok;
+      s.flags = (int32_t)flags;
+      s.zend = zend;
+    }
+    order_count(next, m, valid, go && ok ? p.row - w.r_in : 0);  // rows left inward
   }
   tl.flush(cn, PH_REFIT_P1);
 }

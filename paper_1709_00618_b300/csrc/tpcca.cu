@@ -210,8 +210,8 @@ Layout make_layout(const Caps& c) {
   L.nown = take(4 * T);
   L.own_mask = take(4 * OWN_WORDS * T);
   L.fwork = take(sizeof(FollowWork) * T);
-  L.ztail_list = take(4 * 2 * zone_tail_cap(T));
-  L.ztail_cov = take(8 * 15 * 2 * zone_tail_cap(T));
+  L.ztail_list = take(4 * 3 * zone_tail_cap(T));  // follow forward, follow backward, refit (M <= T)
+  L.ztail_cov = take(8 * 15 * 3 * zone_tail_cap(T));
   L.rwork = take(sizeof(RefitWork) * M);
   L.okey = take(std::max(T, M));
   L.order = take(4 * std::max(T, M));
@@ -610,7 +610,9 @@ void enqueue_find(tpc_ctx* ctx) {
   // follow stage, 1.43 -> 1.49 ms)
   ctx->kc.zone_steps[0] = ctx->n < kLargeBatch ? 0 : 9;
   ctx->kc.zone_steps[1] = ctx->n < kLargeBatch ? 0 : 10;
-  if (ctx->zone_rows > 0) ctx->kc.zone_steps[0] = ctx->kc.zone_steps[1] = ctx->zone_rows < NROW ? ctx->zone_rows : 0;
+  ctx->kc.zone_steps[2] = ctx->n < kLargeBatch ? 0 : 10;
+  if (ctx->zone_rows > 0)
+    for (int i = 0; i < 3; i++) ctx->kc.zone_steps[i] = ctx->zone_rows < NROW ? ctx->zone_rows : 0;
   ctx->mark(0);
   // a2 grid
   k_rs_init<<<gR, bc, 0, s>>>(rs_cnt, ctx->ptr<uint32_t>(L.zmin), ctx->ptr<uint32_t>(L.zmax),
@@ -794,8 +796,13 @@ void enqueue_fit(tpc_ctx* ctx) {
     // longest first below kLargeBatch clusters, index order above (as a6)
     const bool longest_first = ctx->n < kLargeBatch;
     auto refit_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
+      const ZoneTail zt{ctx->ptr<int32_t>(L.ztail_list), ctx->ptr<double>(L.ztail_cov)};
+      const WorkOrder o2 = longest_first ? work_order(ctx, 2, c) : WorkOrder{};
       k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
-          grid_view(ctx), in, ctx->kc, RW, longest_first ? work_order(ctx, 2, c) : WorkOrder{}, c, nc, cn);
+          grid_view(ctx), in, ctx->kc, RW, zt, o2, c, nc, cn);
+      if (ctx->kc.zone_steps[2] > 0)
+        k_refit_p1t<<<persistent_grid(ctx, k_refit_p1t, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
+            grid_view(ctx), ctx->kc, RW, zt, o2, c, nc, cn);
       if (after_p1) cudaEventRecord(after_p1, st);
       if (longest_first)
         k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, st>>>(work_order(ctx, 2, c), &cn->n_tracks, c, nc, cn);
