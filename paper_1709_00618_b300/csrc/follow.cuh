@@ -692,8 +692,10 @@ __global__ void __launch_bounds__(128, 4) k_follow_p1(GridView g, const int32_t*
   tl.flush(cn, PH_FOLLOW_P1);
 }
 
-// Zone tail of phase 1: the forward zones phase 1 parked, 32 to a warp,
-// each to the end of its zone (or of its pass).
+// Zone tail of phase 1: the forward zones phase 1 parked, each to the end
+// of its zone (or of its pass).  Their remaining rows differ widely (1 to
+// 10 and more), so the lanes refill as phase 2's do; a refill loads a parked
+// state and makes no FP64 operation.
 __global__ void __launch_bounds__(128, 4) k_follow_p1t(GridView g, const int32_t* __restrict__ up_m, KConst kc,
                                                     FollowWork* W, ZoneTail zt, WorkOrder next, int chunk,
                                                     int nchunk, Counts* cn) {
@@ -705,34 +707,47 @@ __global__ void __launch_bounds__(128, 4) k_follow_p1t(GridView g, const int32_t
   LocalTally tl;
   double D[15];
   float C[15];
+  Lane w;
+  TrkState p;
+  Chi2Acc chi2;
+  int64_t t = -1;     // tracklet held by the lane (-1: none)
+  bool zgo = false;   // its zone has rows left
+  bool pass = false;  // its pass goes on
+  bool live = true;   // the lane may still get work
   for (;;) {
-    const int64_t k = warp_fetch(work_counter(cn, PH_FOLLOW_P1T, chunk), FULL_MASK);
-    if (__shfl_sync(FULL_MASK, k, 0) >= n) break;
-    const bool valid = k < n;
-    int64_t t = 0;
-    Lane w;
-    TrkState p;
-    Chi2Acc chi2;
-    bool go = false;
-    if (valid) {
-      t = zt.list[base + k];
-      const FollowWork& s = W[t];
-      w = s.w;
-      p = s.p;
-      chi2 = s.chi2;
+    const unsigned need = refill_mask(live && !zgo, zgo, kc.refill);
+    if (need & (1u << (threadIdx.x & 31))) {
+      if (t >= 0) {
+        if (w.nupd < w.zend) {  // the pass ended inside the zone
 #pragma unroll
-      for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
-    }
-    __syncwarp();
-    if (valid) {
-      go = fwd_zone(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, 0);
-      if (w.nupd < w.zend) {
-#pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+          for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+        }
+        work_store(W, t, w, p, C, chi2, pass);
       }
-      work_store(W, t, w, p, C, chi2, go);
+      order_count(next, t, t >= 0, pass ? NROW - 1 - p.row : 0, need);  // rows left outward
+      const int64_t k = warp_fetch(work_counter(cn, PH_FOLLOW_P1T, chunk), need);
+      t = -1;
+      live = k < n;
+      if (live) {
+        t = zt.list[base + k];
+        const FollowWork& s = W[t];
+        w = s.w;
+        p = s.p;
+        chi2 = s.chi2;
+#pragma unroll
+        for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
+        pass = true;
+        zgo = w.nupd < w.zend;
+      }
     }
-    order_count(next, t, valid, go ? NROW - 1 - p.row : 0);  // rows left outward
+    if (!__any_sync(FULL_MASK, zgo)) {
+      if (!__any_sync(FULL_MASK, live)) break;
+      continue;
+    }
+    if (zgo) {
+      pass = fwd_step<true>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr);
+      zgo = pass && w.nupd < w.zend;
+    }
   }
   tl.flush(cn, PH_FOLLOW_P1);
 }
@@ -893,7 +908,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p3(GridView g, KConst kc, Fol
   tl.flush(cn, PH_FOLLOW_P3);
 }
 
-// Zone tail of phase 3: the backward zones phase 3 parked, 32 to a warp.
+// Zone tail of phase 3: the backward zones phase 3 parked, lanes refilling
+// as in k_follow_p1t.
 __global__ void __launch_bounds__(128, 4) k_follow_p3t(GridView g, KConst kc, FollowOut o, FollowWork* W,
                                                     ZoneTail zt, WorkOrder next, int chunk, int nchunk,
                                                     Counts* cn) {
@@ -909,30 +925,39 @@ __global__ void __launch_bounds__(128, 4) k_follow_p3t(GridView g, KConst kc, Fo
   LocalTally tl;
   double D[15];
   float C[15];
+  Lane w;
+  TrkState p;
+  Chi2Acc chi2;
+  int64_t t = -1;
+  bool zgo = false, pass = false, live = true;
   for (;;) {
-    const int64_t k = warp_fetch(work_counter(cn, PH_FOLLOW_P3T, chunk), FULL_MASK);
-    if (__shfl_sync(FULL_MASK, k, 0) >= n) break;
-    const bool valid = k < n;
-    int64_t t = 0;
-    Lane w;
-    TrkState p;
-    Chi2Acc chi2;
-    bool go = false;
-    if (valid) {
-      t = zt.list[base + k];
-      zone_tail_bwd_load(W, t, w, p, chi2, so);
-      w.hits = o.hits + t * NROW;
-      w.hrow = o.hrow + t * NROW;
-      w.cn = cn;
+    const unsigned need = refill_mask(live && !zgo, zgo, kc.refill);
+    if (need & (1u << (threadIdx.x & 31))) {
+      if (t >= 0) zone_bwd_end(W, t, w, p, D, C, chi2, snap, so, pass);
+      order_count(next, t, t >= 0, pass ? p.row : 0, need);  // rows left inward
+      const int64_t k = warp_fetch(work_counter(cn, PH_FOLLOW_P3T, chunk), need);
+      t = -1;
+      live = k < n;
+      if (live) {
+        t = zt.list[base + k];
+        zone_tail_bwd_load(W, t, w, p, chi2, so);
+        w.hits = o.hits + t * NROW;
+        w.hrow = o.hrow + t * NROW;
+        w.cn = cn;
 #pragma unroll
-      for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
+        for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
+        pass = true;
+        zgo = w.nupd < w.zend;
+      }
     }
-    __syncwarp();
-    if (valid) {
-      go = bwd_zone(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, so, 0);
-      zone_bwd_end(W, t, w, p, D, C, chi2, snap, so, go);
+    if (!__any_sync(FULL_MASK, zgo)) {
+      if (!__any_sync(FULL_MASK, live)) break;
+      continue;
     }
-    order_count(next, t, valid, go ? p.row : 0);  // rows left inward
+    if (zgo) {
+      pass = bwd_step<true>(g, kc, sX, sYH, w, p, D, C, chi2, tl, snap, so);
+      zgo = pass && w.nupd < w.zend;
+    }
   }
   tl.flush(cn, PH_FOLLOW_P3);
 }

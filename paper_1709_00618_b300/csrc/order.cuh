@@ -27,12 +27,13 @@ struct WorkOrder {
 };
 
 // Files item i (lanes with valid) under the class of `rem` remaining rows.
-// All 32 lanes of the warp make the call.
-__device__ __forceinline__ void order_count(const WorkOrder& o, int64_t i, bool valid, int rem) {
+// All lanes of `mask` make the call.
+__device__ __forceinline__ void order_count(const WorkOrder& o, int64_t i, bool valid, int rem,
+                                            unsigned mask = FULL_MASK) {
   if (!o.key) return;  // index order
   const int b = NROW - 1 - min(max(rem, 0), NROW - 1);
   if (valid) o.key[i] = (uint8_t)b;
-  const unsigned peers = __match_any_sync(FULL_MASK, valid ? b : -1);
+  const unsigned peers = __match_any_sync(mask, valid ? b : -1);
   if (valid && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&o.hist[b], __popc(peers));
 }
 

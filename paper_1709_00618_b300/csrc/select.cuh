@@ -467,7 +467,8 @@ __global__ void __launch_bounds__(128, 4) k_refit_p1(GridView g, RefitIn in, KCo
   tl.flush(cn, PH_REFIT_P1);
 }
 
-// Zone tail of refit phase 1: the zones phase 1 parked, 32 to a warp.
+// Zone tail of refit phase 1: the zones phase 1 parked, lanes refilling as
+// in the follow stage's zone tail kernels.
 __global__ void __launch_bounds__(128, 4) k_refit_p1t(GridView g, KConst kc, RefitWork* RW, ZoneTail zt,
                                                    WorkOrder next, int chunk, int nchunk, Counts* cn) {
   __shared__ float sX[NROW + 1];
@@ -479,50 +480,63 @@ __global__ void __launch_bounds__(128, 4) k_refit_p1t(GridView g, KConst kc, Ref
   LocalTally tl;
   double D[15];
   float C[15];
+  RefitLane w;
+  TrkState p;
+  Chi2Acc chi2;
+  int nupd = 0, zend = 0;
+  bool ok = false, dg = false;
+  uint32_t flags = 0;
+  int64_t m = -1;
+  bool zgo = false, pass = false, live = true;
   for (;;) {
-    const int64_t k = warp_fetch(work_counter(cn, PH_REFIT_P1T, chunk), FULL_MASK);
-    if (__shfl_sync(FULL_MASK, k, 0) >= n) break;
-    const bool valid = k < n;
-    int64_t m = 0;
-    RefitLane w;
-    TrkState p;
-    Chi2Acc chi2;
-    int nupd = 0, zend = 0;
-    bool ok = false, go = false, dg = false;
-    uint32_t flags = 0;
-    if (valid) {
-      m = zt.list[base + k];
-      const RefitWork& s = RW[m];
-      w = s.w;
-      p = s.p;
-      chi2 = s.chi2;
-      nupd = s.nupd;
-      zend = s.zend;
-      flags = (uint32_t)s.flags;
-      ok = true;
+    const unsigned need = refill_mask(live && !zgo, zgo, kc.refill);
+    if (need & (1u << (threadIdx.x & 31))) {
+      if (m >= 0) {
+        if (nupd < zend) {
 #pragma unroll
-      for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
-    }
-    __syncwarp();
-    if (valid) {
-      go = refit_zone(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg, 0);
-      if (nupd < zend) {
+          for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+        }
+        RefitWork& s = RW[m];
+        s.w = w;
+        s.p = p;
 #pragma unroll
-        for (int i = 0; i < 15; i++) C[i] = narrow(D[i]);
+        for (int i = 0; i < 15; i++) s.C[i] = C[i];
+        s.chi2 = chi2;
+        s.nupd = nupd;
+        s.ok = ok;
+        s.go = pass && ok;
+        s.flags = (int32_t)flags;
+        s.zend = zend;
       }
-      RefitWork& s = RW[m];
-      s.w = w;
-      s.p = p;
+      order_count(next, m, m >= 0, pass && ok ? p.row - w.r_in : 0, need);  // rows left inward
+      const int64_t k = warp_fetch(work_counter(cn, PH_REFIT_P1T, chunk), need);
+      m = -1;
+      live = k < n;
+      if (live) {
+        m = zt.list[base + k];
+        const RefitWork& s = RW[m];
+        w = s.w;
+        p = s.p;
+        chi2 = s.chi2;
+        nupd = s.nupd;
+        zend = s.zend;
+        flags = (uint32_t)s.flags;
+        ok = true;
+        dg = false;
 #pragma unroll
-      for (int i = 0; i < 15; i++) s.C[i] = C[i];
-      s.chi2 = chi2;
-      s.nupd = nupd;
-      s.ok = ok;
-      s.go = go && ok;
-      s.flags = (int32_t)flags;
-      s.zend = zend;
+        for (int i = 0; i < 15; i++) D[i] = zt.cov[(base + k) * 15 + i];
+        pass = true;
+        zgo = nupd < zend;
+      }
     }
-    order_count(next, m, valid, go && ok ? p.row - w.r_in : 0);  // rows left inward
+    if (!__any_sync(FULL_MASK, zgo)) {
+      if (!__any_sync(FULL_MASK, live)) break;
+      continue;
+    }
+    if (zgo) {
+      pass = refit_step<true>(g, kc, sX, w, p, D, C, chi2, nupd, ok, flags, tl, zend, dg);
+      zgo = pass && nupd < zend;
+    }
   }
   tl.flush(cn, PH_REFIT_P1);
 }

@@ -272,7 +272,7 @@ struct tpc_ctx {
   int zone_rows = 0;     // zone rows in step before the zone tail kernels (0: by size; NROW or more: no tails)
   int graph_chunks = 0;  // chunks and refilling-kernel CTAs per SM of the captured graph
   int graph_ctas = 0;
-  bool graph_large = false;  // the size class the graph's kernel variants were chosen for
+  int graph_class = -1;  // the size class (size_class) the graph's kernel variants were chosen for
   cudaStream_t aux = nullptr;       // second stream of the chunked Kalman stage
   // tpc_track_host: the stream of the cluster assignment's copy-out, which
   // overlaps the refit, and its fork and join events (created on first use)
@@ -380,6 +380,10 @@ KConst make_kconst(const tpc_config& c, const Caps& caps) {
 // overlap gains under 1% on 16 M clusters and loses on 1 M, where launch and
 // join costs weigh more; the autotuner tries both).
 constexpr int64_t kLargeBatch = int64_t(4) << 20;  // clusters from which the size default switches
+constexpr int64_t kZoneTailBwd = int64_t(16) << 20;  // clusters from which the backward zone has a tail kernel
+constexpr int64_t kZoneTailFwd = int64_t(48) << 20;  // ... the forward and refit zones
+// The input-size class that picks kernel variants and launch shapes.
+int size_class(int64_t n) { return (n >= kLargeBatch) + (n >= kZoneTailBwd) + (n >= kZoneTailFwd); }
 int effective_chunks(const tpc_ctx* ctx) { return ctx->chunks > 0 ? ctx->chunks : 1; }
 // 32-bit ownership keys while every tracklet id fits 24 bits (select.cuh).
 bool key32(const tpc_ctx* ctx) { return ctx->caps.tl < (int64_t(1) << 24); }
@@ -603,14 +607,17 @@ void enqueue_find(tpc_ctx* ctx) {
   int32_t* bin_cnt = ctx->ptr<int32_t>(L.bin_cnt);
   int32_t* bin_start = ctx->ptr<int32_t>(L.bin_start);
   ctx->kc.inner_steps = ctx->n < kLargeBatch ? 16 : 4;  // 10 ms timeframe: 1 step 69.0 ms, 2 68.7, 4 68.6, 8 68.8
-  // zone rows in step before a zone goes to the tail kernels (follow.cuh):
-  // on the 10 ms timeframe p1 10.03 ms without, 9.50 with 9 rows, 9.72 with
-  // 10; p3 11.20 without, 10.46 with 9, 10.27 with 10, 10.75 with 11.  Below
-  // kLargeBatch clusters none (central event: the tail kernels lengthen the
-  // follow stage, 1.43 -> 1.49 ms)
-  ctx->kc.zone_steps[0] = ctx->n < kLargeBatch ? 0 : 9;
-  ctx->kc.zone_steps[1] = ctx->n < kLargeBatch ? 0 : 10;
-  ctx->kc.zone_steps[2] = ctx->n < kLargeBatch ? 0 : 10;
+  // zone rows in step before a zone goes to the tail kernels (follow.cuh).
+  // 10 ms timeframe (90 M clusters): p1 10.06 ms without tails, 9.26 with 9
+  // rows; p3 11.25 without, 10.03 with 10; refit p1 4.09 without, 3.75 with
+  // 10.  A tail kernel costs a launch whose last lanes run alone, so on
+  // smaller inputs the tails gain less: 3 ms timeframe (25.5 M) p1 3.06 ->
+  // 3.15, p3 3.26 -> 3.09, refit p1 1.28 -> 1.31; 1 ms (8.3 M) all three
+  // slower.  Hence the backward pass's tail from 16 Mi clusters, the forward
+  // pass's and the refit's from 48 Mi.
+  ctx->kc.zone_steps[0] = ctx->n < kZoneTailFwd ? 0 : 9;
+  ctx->kc.zone_steps[1] = ctx->n < kZoneTailBwd ? 0 : 10;
+  ctx->kc.zone_steps[2] = ctx->n < kZoneTailFwd ? 0 : 10;
   if (ctx->zone_rows > 0)
     for (int i = 0; i < 3; i++) ctx->kc.zone_steps[i] = ctx->zone_rows < NROW ? ctx->zone_rows : 0;
   ctx->mark(0);
@@ -1074,7 +1081,7 @@ int tpc_run_graph(tpc_ctx* ctx) {
   if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "no clusters loaded");
   CK(cudaSetDevice(ctx->device));
   if (ctx->graph && (ctx->graph_chunks != effective_chunks(ctx) || ctx->graph_ctas != effective_ctas_follow(ctx) ||
-                     ctx->graph_large != (ctx->n >= kLargeBatch))) {
+                     ctx->graph_class != size_class(ctx->n))) {
     cudaGraphExecDestroy(ctx->graph);
     ctx->graph = nullptr;
   }
@@ -1093,7 +1100,7 @@ int tpc_run_graph(tpc_ctx* ctx) {
     ctx->graph_kernels = count_kernel_nodes(g);
     ctx->graph_chunks = effective_chunks(ctx);
     ctx->graph_ctas = effective_ctas_follow(ctx);
-    ctx->graph_large = ctx->n >= kLargeBatch;
+    ctx->graph_class = size_class(ctx->n);
     e = cudaGraphInstantiate(&ctx->graph, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
