@@ -821,6 +821,8 @@ def measure(cl, local, args, flush, world=1, clocks=True, e2e_steps=None):
     n = len(cl)
     stream = torch.cuda.Stream()
     trk = tpc.Tracker(device=local, stream=stream, arena="torch", arena_clusters=n)
+    if getattr(args, "zone_rows", 0) > 0:
+        trk.set_tuning(zone_rows=args.zone_rows)
     dev_in = torch.from_numpy(cl.view(np.uint8)).to(f"cuda:{local}")
 
     def step_device():
@@ -1009,6 +1011,9 @@ def main():
     ap.add_argument("--serving-pool", type=int, default=16, help="distinct timeframes the serving leg replays")
     ap.add_argument("--timeframe-ms", type=float, default=0.0,
                     help="length of the main line's timeframe (default 10 ms, seed 2 + rank)")
+    ap.add_argument("--zone-rows", type=int, default=0,
+                    help="zone rows in step before the zone tail kernels (tpc_tuning.zone_rows; 0: the library's "
+                         "default by input size); a launch shape, results unchanged")
     ap.add_argument("--all-configs", action="store_true",
                     help="print the per-config table (one sector, central event, 10 ms timeframe) instead")
     args = ap.parse_args()
@@ -1057,7 +1062,8 @@ def main():
             "workload_detail": {"tracklets": counts["n_tracklets"], "tracks": counts["n_tracks"],
                                 "tracklets_per_track": counts["n_tracklets"] / max(counts["n_tracks"], 1),
                                 "l2": "inputs larger than L2, and L2 flushed (256 MB write) between steps",
-                                "graph": True, "kernels_per_step": m["kernels_per_step"]},
+                                "graph": True, "kernels_per_step": m["kernels_per_step"],
+                                **({"zone_rows": args.zone_rows} if args.zone_rows > 0 else {})},
             "clocks": clocks,
             "alu_peaks_measured": alu,
             "e2e": m["e2e"],
