@@ -54,9 +54,11 @@ __device__ __forceinline__ void axis_range(float v, float w, float lo, float inv
   i1 = !(f1 >= 0.0f) ? 0 : (f1 > top ? nb - 1 : (int)f1);
 }
 
+constexpr int PICK_BATCH = 4;  // candidate loads a pick issues together
 // Best cluster of row-sector rs for the predicted state: minimum chi2 =
 // dy^2/Syy + dz^2/Szz within the gate, ties to the lower sorted index.
 // Near-ties and near-gate candidates raise the taint flags.
+template <bool BATCH>
 __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const TrkState& p, float cyy, float czz,
                                     const KConst& kc, const float* sYH, uint32_t& flags, unsigned& ncand) {
   const RsParams P = load_params(g.par + rs);
@@ -70,31 +72,73 @@ __device__ __forceinline__ int pick(const GridView& g, int rs, int row, const Tr
   const float gate = kc.gate, eps = kc.taint;
   float b1v = __int_as_float(0x7F800000), b2v = b1v;
   int best = -1;
-  for (int iz = iz0; iz <= iz1; iz++) {
-    const int base = P.bin_base + iz * P.n_y;
-    const int a = __ldg(g.bin_start + base + iy0), b = __ldg(g.bin_start + base + iy1 + 1);
-    ncand += (unsigned)(b - a);
-    auto consider = [&](float2 q, int c) {
-      const float dy = (q.x - p.y) - p.yl;
-      const float dz = ((q.y - p.zref) - p.z) - p.zl;
-      const float chi = dy * dy * iSyy + dz * dz * iSzz;
-      if (fabsf(chi - gate) <= eps * (1.0f + gate)) flags |= TF_GATE;
-      if (!(chi <= gate)) return;
-      if (chi < b1v || (chi == b1v && c < best)) {
-        b2v = b1v;
-        b1v = chi;
-        best = c;
-      } else if (chi < b2v) {
-        b2v = chi;
-      }
-    };
-    int c = a;  // two candidates' loads in flight at a time, taken in index order
-    for (; c + 1 < b; c += 2) {
-      const float2 q0 = __ldg(g.yz + c), q1 = __ldg(g.yz + c + 1);
-      consider(q0, c);
-      consider(q1, c + 1);
+  auto consider = [&](float2 q, int c) {
+    const float dy = (q.x - p.y) - p.yl;
+    const float dz = ((q.y - p.zref) - p.z) - p.zl;
+    const float chi = dy * dy * iSyy + dz * dz * iSzz;
+    if (fabsf(chi - gate) <= eps * (1.0f + gate)) flags |= TF_GATE;
+    if (!(chi <= gate)) return;
+    if (chi < b1v || (chi == b1v && c < best)) {
+      b2v = b1v;
+      b1v = chi;
+      best = c;
+    } else if (chi < b2v) {
+      b2v = chi;
     }
-    if (c < b) consider(__ldg(g.yz + c), c);
+  };
+  // The pick does not depend on the order in which candidates are taken, so
+  // (BATCH) a window of up to three z-rows of bins loads the three bin
+  // ranges in one round and then its candidates PICK_BATCH at a time across
+  // the z-rows (one round per batch instead of one per z-row and candidate
+  // pair: a binary32 row step waited on up to six dependent rounds to L2).
+  // The FP64-zone kernels, bound by their FP64 pipe, keep the z-row loop and
+  // its registers.
+  if (BATCH && iz1 - iz0 < 3) {
+    int a0, n0, a1 = 0, n1 = 0, a2 = 0, n2 = 0;
+    {
+      const int base = P.bin_base + iz0 * P.n_y;
+      a0 = __ldg(g.bin_start + base + iy0);
+      n0 = __ldg(g.bin_start + base + iy1 + 1);
+      if (iz1 > iz0) {
+        a1 = __ldg(g.bin_start + base + P.n_y + iy0);
+        n1 = __ldg(g.bin_start + base + P.n_y + iy1 + 1);
+      }
+      if (iz1 > iz0 + 1) {
+        a2 = __ldg(g.bin_start + base + 2 * P.n_y + iy0);
+        n2 = __ldg(g.bin_start + base + 2 * P.n_y + iy1 + 1);
+      }
+      n0 -= a0;
+      n1 -= a1;
+      n2 -= a2;
+    }
+    const int tot = n0 + n1 + n2;
+    ncand += (unsigned)tot;
+    for (int j0 = 0; j0 < tot; j0 += PICK_BATCH) {
+      int c[PICK_BATCH];
+      float2 q[PICK_BATCH];
+#pragma unroll
+      for (int k = 0; k < PICK_BATCH; k++) {
+        const int j = j0 + k;
+        c[k] = j < n0 ? a0 + j : (j < n0 + n1 ? a1 + (j - n0) : a2 + (j - n0 - n1));
+        if (j < tot) q[k] = __ldg(g.yz + c[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < PICK_BATCH; k++)
+        if (j0 + k < tot) consider(q[k], c[k]);
+    }
+  } else {
+    for (int iz = iz0; iz <= iz1; iz++) {
+      const int base = P.bin_base + iz * P.n_y;
+      const int a = __ldg(g.bin_start + base + iy0), b = __ldg(g.bin_start + base + iy1 + 1);
+      ncand += (unsigned)(b - a);
+      int c = a;  // two candidates' loads in flight at a time
+      for (; c + 1 < b; c += 2) {
+        const float2 q0 = __ldg(g.yz + c), q1 = __ldg(g.yz + c + 1);
+        consider(q0, c);
+        consider(q1, c + 1);
+      }
+      if (c < b) consider(__ldg(g.yz + c), c);
+    }
   }
   if (best >= 0 && b2v != __int_as_float(0x7F800000) && b2v - b1v <= eps * (1.0f + b1v)) flags |= TF_TIE;
   return best;
@@ -249,8 +293,11 @@ __device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap, floa
 }
 
 // One forward row step; false ends the pass.  The covariance is in D while
-// fewer than fp64_updates updates have been made since the seed.
-template <bool Z>
+// fewer than fp64_updates updates have been made since the seed.  PB: the
+// pick loads its candidates in batches (pick); phase 2's build for inputs
+// that fill the GPU keeps the z-row loop (its 80 registers spilled the
+// batches: 8.22 -> 8.81 ms on the 10 ms timeframe).
+template <bool Z, bool PB = false>
 __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __restrict__ up_m, const KConst& kc,
                                          const float* sX, const float* sYH, Lane& w, TrkState& p, double* D,
                                          float* C, Chi2Acc& chi2, LocalTally& tl, float* sf) {
@@ -283,7 +330,7 @@ __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __res
     w.i++;
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
-    c = pick(g, w.ubase + r, r, p, zone ? narrow(D[0]) : C[0], zone ? narrow(D[2]) : C[2], kc, sYH, w.flags,
+    c = pick<PB>(g, w.ubase + r, r, p, zone ? narrow(D[0]) : C[0], zone ? narrow(D[2]) : C[2], kc, sYH, w.flags,
              tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
   }
@@ -331,7 +378,7 @@ __device__ __forceinline__ bool bwd_step(const GridView& g, const KConst& kc, co
     next_fwd_hit(w, g);
   } else {
     if (outside_sector(p, kc, w.flags)) return false;
-    const int c = pick(g, w.ubase + r, r, p, zone ? narrow(D[0]) : C[0], zone ? narrow(D[2]) : C[2], kc, sYH,
+    const int c = pick<!Z>(g, w.ubase + r, r, p, zone ? narrow(D[0]) : C[0], zone ? narrow(D[2]) : C[2], kc, sYH,
                        w.flags, tl.cand);
     if (c < 0) return ++w.misses < kc.max_miss;
     w.hits[w.nf + w.nb] = c;
@@ -804,7 +851,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
     }
     if (go) {
       for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
-        go = fwd_step<false>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, sf);
+        go = fwd_step<false, MINB == 4>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, sf);
       dirty = true;
     }
   }
