@@ -382,7 +382,7 @@ typedef struct {
   int32_t zone_rows;          /* row steps the FP64-zone kernels take with a warp's 32 tracklets (tracks) in
                                  step before a zone still open goes on in a zone tail kernel, 32 such items to
                                  a warp (follow forward and backward passes and refit; 159 or more: no tail
-                                 kernels); reported as 0 while the default applies: 10 backward from 16 Mi
+                                 kernels); reported as 0 while the default applies: 9 backward from 16 Mi
                                  loaded clusters on, 9 forward and 10 in the refit from 48 Mi on, else none */
 } tpc_tuning;
 

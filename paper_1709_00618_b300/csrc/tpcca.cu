@@ -609,14 +609,14 @@ void enqueue_find(tpc_ctx* ctx) {
   ctx->kc.inner_steps = ctx->n < kLargeBatch ? 16 : 4;  // 10 ms timeframe: 1 step 69.0 ms, 2 68.7, 4 68.6, 8 68.8
   // zone rows in step before a zone goes to the tail kernels (follow.cuh).
   // 10 ms timeframe (90 M clusters): p1 10.06 ms without tails, 9.26 with 9
-  // rows; p3 11.25 without, 10.03 with 10; refit p1 4.09 without, 3.75 with
-  // 10.  A tail kernel costs a launch whose last lanes run alone, so on
+  // rows (9.65 with 10); p3 11.25 without, 10.03 with 10, 9.92 with 9; refit
+  // p1 4.09 without, 3.75 with 10.  A tail kernel costs a launch whose last lanes run alone, so on
   // smaller inputs the tails gain less: 3 ms timeframe (25.5 M) p1 3.06 ->
   // 3.15, p3 3.26 -> 3.09, refit p1 1.28 -> 1.31; 1 ms (8.3 M) all three
   // slower.  Hence the backward pass's tail from 16 Mi clusters, the forward
   // pass's and the refit's from 48 Mi.
   ctx->kc.zone_steps[0] = ctx->n < kZoneTailFwd ? 0 : 9;
-  ctx->kc.zone_steps[1] = ctx->n < kZoneTailBwd ? 0 : 10;
+  ctx->kc.zone_steps[1] = ctx->n < kZoneTailBwd ? 0 : 9;
   ctx->kc.zone_steps[2] = ctx->n < kZoneTailFwd ? 0 : 10;
   if (ctx->zone_rows > 0)
     for (int i = 0; i < 3; i++) ctx->kc.zone_steps[i] = ctx->zone_rows < NROW ? ctx->zone_rows : 0;
