@@ -172,10 +172,13 @@ def kernel_rooflines(stages, kalman, n, alu):
     peaks, src = _peaks()
     p32, p64 = alu["fp32_tflops"], alu["fp64_tflops"]
     out = {}
+    import paper_1709_00618_b300 as tpc
     for name, d in kalman.items():
+        if d["prop"] == 0 or d["ms"] <= 0:
+            continue  # not launched at this input size
         t = d["ms"] / 1e3
         f32, f64 = kalman_flops(d)
-        zone = name in ("k_follow_p1", "k_follow_p3", "k_refit_p1")
+        zone = name in tpc.Tracker.ZONE_KERNELS
         if zone:
             ach = f64 / t / 1e12
             e = {"bound": "alu", "achieved": ach, "peak": p64, "unit": "TFLOP/s (FP64)", "frac": ach / p64,

@@ -310,13 +310,17 @@ int tpc_get_stage_times(tpc_ctx *ctx, float ms[6]);
 int tpc_get_work(tpc_ctx *ctx, uint64_t work[5]);
 
 /* Per Kalman kernel, in launch order -- [0] follow seed + forward FP64 zone,
- * [1] follow forward FP32, [2] follow backward re-seed + FP64 zone, [3]
- * follow backward FP32 + output, [4] refit FP64 zone, [5] refit FP32 +
- * output -- ms[k]: device time of the last profiled run (events between the
- * launches; ms may be NULL), work[5k..5k+4]: that kernel's share of the
+ * [1] its zone tail, [2] follow forward FP32, [3] follow backward re-seed +
+ * FP64 zone, [4] its zone tail, [5] follow backward FP32 refit rows, [6]
+ * follow backward FP32 (extension) + output, [7] refit FP64 zone, [8] its
+ * zone tail, [9] refit FP32 + output -- ms[k]: device time of the last
+ * profiled run (events between the launches; a work-order pass counts with
+ * the kernel before it; a kernel the batch's size does not launch has
+ * about 0; ms may be NULL), work[5k..5k+4]: that kernel's share of the
  * counters of tpc_get_work in the same order (work may be NULL).  Waits for
  * the stream. */
-int tpc_get_kalman_profile(tpc_ctx *ctx, float ms[6], uint64_t work[30]);
+#define TPC_KALMAN_KERNELS 10
+int tpc_get_kalman_profile(tpc_ctx *ctx, float ms[TPC_KALMAN_KERNELS], uint64_t work[5 * TPC_KALMAN_KERNELS]);
 
 /* Measured issue rates of the FP32 and FP64 fused multiply-add pipes of
  * device `device` (TFLOP/s, an FMA counting 2): 8 independent FMA chains

@@ -363,13 +363,17 @@ class Tracker:
         self._ck(self._lib.tpc_get_work(self._ctx, w.ctypes.data))
         return dict(zip(("prop", "upd32", "upd64", "cand", "prop64"), (int(v) for v in w)))
 
-    KALMAN_KERNELS = ("k_follow_p1", "k_follow_p2", "k_follow_p3", "k_follow_p4", "k_refit_p1", "k_refit_p2")
+    KALMAN_KERNELS = ("k_follow_p1", "k_follow_p1t", "k_follow_p2", "k_follow_p3", "k_follow_p3t", "k_follow_p4r",
+                      "k_follow_p4", "k_refit_p1", "k_refit_p1t", "k_refit_p2")
+    # the kernels whose covariance is in FP64 (the zone kernels and their tails)
+    ZONE_KERNELS = ("k_follow_p1", "k_follow_p1t", "k_follow_p3", "k_follow_p3t", "k_refit_p1", "k_refit_p1t")
 
     def kalman_profile(self, times: bool = True) -> dict:
         """Per Kalman kernel: device ms of the last profiled run (when
-        times) and its work counters."""
-        ms = np.zeros(6, np.float32)
-        w = np.zeros(30, np.uint64)
+        times) and its work counters (zero for a kernel the batch's size
+        does not launch)."""
+        ms = np.zeros(len(self.KALMAN_KERNELS), np.float32)
+        w = np.zeros(5 * len(self.KALMAN_KERNELS), np.uint64)
         self._ck(self._lib.tpc_get_kalman_profile(self._ctx, ms.ctypes.data if times else None, w.ctypes.data))
         out = {}
         for k, name in enumerate(self.KALMAN_KERNELS):

@@ -43,6 +43,8 @@ __device__ __forceinline__ RsParams load_params(const RsParams* p) {
   return r;
 }
 
+constexpr int PH_COUNT_MAX = 10;  // Kalman kernels with work counters (PH_*, below)
+
 // Scalars of a run that live in device memory so that graph-captured
 // kernels read the sizes of whatever batch is loaded.
 struct Counts {
@@ -67,19 +69,26 @@ struct Counts {
   int32_t n_starts;             // chain starts (clusters with a kept upward link and none downward)
   unsigned long long pad2[2];
   // the same counters per Kalman kernel (PH_*): {prop, upd32, upd64, cand, prop64}
-  unsigned long long phase_work[6][5];
+  unsigned long long phase_work[PH_COUNT_MAX][5];
 };
 
-// Kalman kernels, in launch order, for the per-kernel work counters.
-enum { PH_FOLLOW_P1 = 0, PH_FOLLOW_P2, PH_FOLLOW_P3, PH_FOLLOW_P4, PH_REFIT_P1, PH_REFIT_P2, PH_COUNT };
-// Phase 4r and the zone tail kernels of follow phases 1 and 3 and of refit
-// phase 1 fetch their work with counters of their own; their work is
-// tallied with follow phases 4, 1 and 3 and refit phase 1.
-constexpr int PH_FOLLOW_P4R = PH_COUNT;
-constexpr int PH_FOLLOW_P1T = PH_COUNT + 1;
-constexpr int PH_FOLLOW_P3T = PH_COUNT + 2;
-constexpr int PH_REFIT_P1T = PH_COUNT + 3;
-constexpr int PH_FETCH = PH_COUNT + 4;  // work counters per chunk
+// Kalman kernels, in launch order: their work counters (one per chunk) and
+// their tallies.  A kernel that a batch's size does not launch (the zone
+// tails, phase 4r) keeps zero work.
+enum {
+  PH_FOLLOW_P1 = 0,
+  PH_FOLLOW_P1T,
+  PH_FOLLOW_P2,
+  PH_FOLLOW_P3,
+  PH_FOLLOW_P3T,
+  PH_FOLLOW_P4R,
+  PH_FOLLOW_P4,
+  PH_REFIT_P1,
+  PH_REFIT_P1T,
+  PH_REFIT_P2,
+  PH_COUNT
+};
+constexpr int PH_FETCH = PH_COUNT;  // work counters per chunk
 
 // The Kalman stage may split its items into chunks whose zone and FP32
 // kernels run concurrently on two streams (the FP64 pipe of one chunk's
@@ -87,7 +96,7 @@ constexpr int PH_FETCH = PH_COUNT + 4;  // work counters per chunk
 constexpr int MAX_CHUNKS = 2;
 static_assert(PH_FETCH * MAX_CHUNKS <= (int)(sizeof(((Counts*)nullptr)->work_next) / sizeof(int32_t)),
               "a work counter per Kalman kernel and chunk");
-static_assert(PH_COUNT <= (int)(sizeof(((Counts*)nullptr)->phase_work) / sizeof(((Counts*)nullptr)->phase_work[0])),
+static_assert(PH_COUNT == PH_COUNT_MAX,
               "tallies per Kalman kernel");
 struct Chunk {
   int32_t begin, end;

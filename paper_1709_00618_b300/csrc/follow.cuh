@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(128, 4) k_follow_p1t(GridView g, const int32_t
       zgo = pass && w.nupd < w.zend;
     }
   }
-  tl.flush(cn, PH_FOLLOW_P1);
+  tl.flush(cn, PH_FOLLOW_P1T);
 }
 
 // Phase 2: the rest of the forward pass (covariance in FP32).  MINB: CTAs
@@ -1006,7 +1006,7 @@ __global__ void __launch_bounds__(128, 4) k_follow_p3t(GridView g, KConst kc, Fo
       zgo = pass && w.nupd < w.zend;
     }
   }
-  tl.flush(cn, PH_FOLLOW_P3);
+  tl.flush(cn, PH_FOLLOW_P3T);
 }
 
 // Phase 4r: the binary32 refit of the forward clusters below the FP64 zone
@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4r(GridView g, KConst kc,
       dirty = true;
     }
   }
-  tl.flush(cn, PH_FOLLOW_P4);
+  tl.flush(cn, PH_FOLLOW_P4R);
 }
 
 // Output of one tracklet from its phase-4 slot (out_put).

@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(128, 4) k_refit_p1t(GridView g, KConst kc, Ref
       zgo = pass && nupd < zend;
     }
   }
-  tl.flush(cn, PH_REFIT_P1);
+  tl.flush(cn, PH_REFIT_P1T);
 }
 
 __device__ __forceinline__ void write_track(const RefitIn& in, const float* sX, int64_t m, const RefitWork& s,

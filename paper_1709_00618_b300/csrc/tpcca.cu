@@ -314,7 +314,8 @@ struct tpc_ctx {
   bool prof = false;
   bool prof_valid = false;
   cudaEvent_t ev[7] = {};
-  cudaEvent_t evk[6] = {};  // after follow p1, p2, p3; before refit p1; after refit p1, p2
+  // after follow p1, p1t, p2, p3, p3t, p4r; before refit p1; after refit p1, p1t, p2
+  cudaEvent_t evk[PH_COUNT] = {};
   int32_t graph_kernels = 0;  // kernel nodes of the captured graph
   std::string err;
 
@@ -694,33 +695,49 @@ void enqueue_find(tpc_ctx* ctx) {
     int32_t* order = longest_first ? ctx->ptr<int32_t>(L.order) : nullptr;
     auto ord = [&](int phase, int c) { return longest_first ? work_order(ctx, phase, c) : WorkOrder{}; };
     auto follow_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
+      // profiled runs (one chunk) mark the end of every Kalman kernel (a
+      // k_order counts with the kernel before it; a kernel the batch's size
+      // does not launch gets an empty interval)
+      auto mk = [&](int i) {
+        if (nc == 1) ctx->mark_k(i);
+      };
+      auto order_after = [&](int phase) {
+        if (longest_first)
+          k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, phase, c), &cn->n_tracklets, c, nc, cn);
+      };
+      const bool tail1 = ctx->kc.zone_steps[0] > 0, tail3 = ctx->kc.zone_steps[1] > 0;
       k_follow_p1<<<persistent_grid(ctx, k_follow_p1, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->ptr<int32_t>(L.tl_len), ctx->ptr<int32_t>(L.tl_end),
           ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, zt, ord(0, c), c, nc, cn);
-      if (ctx->kc.zone_steps[0] > 0)
+      if (!tail1) order_after(0);
+      mk(0);
+      if (tail1) {
         k_follow_p1t<<<persistent_grid(ctx, k_follow_p1t, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
             grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, W, zt, ord(0, c), c, nc, cn);
+        order_after(0);
+      }
       if (after_p1) cudaEventRecord(after_p1, st);
-      if (longest_first)
-        k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 0, c), &cn->n_tracklets, c, nc, cn);
-      if (nc == 1) ctx->mark_k(0);
+      mk(1);
       auto p2 = ctx->n >= kLargeBatch ? k_follow_p2<6> : k_follow_p2<4>;
       p2<<<persistent_grid(ctx, p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
-      if (nc == 1) ctx->mark_k(1);
+      mk(2);
       k_follow_p3<<<persistent_grid(ctx, k_follow_p3, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->kc, follow_out(ctx), W, zt, ord(1, c), c, nc, cn);
-      if (ctx->kc.zone_steps[1] > 0)
+      if (!tail3) order_after(1);
+      mk(3);
+      if (tail3) {
         k_follow_p3t<<<persistent_grid(ctx, k_follow_p3t, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
             grid_view(ctx), ctx->kc, follow_out(ctx), W, zt, ord(1, c), c, nc, cn);
-      if (longest_first)
-        k_order<<<grid_for(ctx, C.tl, bc), bc, 0, st>>>(work_order(ctx, 1, c), &cn->n_tracklets, c, nc, cn);
-      if (nc == 1) ctx->mark_k(2);
+        order_after(1);
+      }
+      mk(4);
       // large batches: the refit rows (p4r) and the extension (p4) in two
       // kernels, so that no warp mixes them; small ones: both in p4
       if (ctx->n >= kLargeBatch)
         k_follow_p4r<7><<<persistent_grid(ctx, k_follow_p4r<7>, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
             grid_view(ctx), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
+      mk(5);
       auto p4 = ctx->n >= kLargeBatch ? k_follow_p4<7, BW_EXTEND> : k_follow_p4<4, BW_ANY>;
       p4<<<persistent_grid(ctx, p4, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.tl_start), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
@@ -805,20 +822,27 @@ void enqueue_fit(tpc_ctx* ctx) {
     auto refit_chunk = [&](cudaStream_t st, int c, cudaEvent_t after_p1) {
       const ZoneTail zt{ctx->ptr<int32_t>(L.ztail_list), ctx->ptr<double>(L.ztail_cov)};
       const WorkOrder o2 = longest_first ? work_order(ctx, 2, c) : WorkOrder{};
+      const bool tail = ctx->kc.zone_steps[2] > 0;
+      auto order_after = [&]() {
+        if (longest_first)
+          k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, st>>>(work_order(ctx, 2, c), &cn->n_tracks, c, nc, cn);
+      };
       k_refit_p1<<<persistent_grid(ctx, k_refit_p1, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
           grid_view(ctx), in, ctx->kc, RW, zt, o2, c, nc, cn);
-      if (ctx->kc.zone_steps[2] > 0)
+      if (!tail) order_after();
+      if (nc == 1) ctx->mark_k(7);
+      if (tail) {
         k_refit_p1t<<<persistent_grid(ctx, k_refit_p1t, bf, effective_ctas_zone(ctx)), bf, 0, st>>>(
             grid_view(ctx), ctx->kc, RW, zt, o2, c, nc, cn);
+        order_after();
+      }
       if (after_p1) cudaEventRecord(after_p1, st);
-      if (longest_first)
-        k_order<<<grid_for(ctx, C.tracks, bc), bc, 0, st>>>(work_order(ctx, 2, c), &cn->n_tracks, c, nc, cn);
-      if (nc == 1) ctx->mark_k(4);
+      if (nc == 1) ctx->mark_k(8);
       k_refit_p2<<<persistent_grid(ctx, k_refit_p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), in, ctx->kc, RW, longest_first ? ctx->ptr<int32_t>(L.order) : nullptr,
           ctx->ptr<tpc_track>(L.tracks), c, nc, cn);
     };
-    ctx->mark_k(3);
+    ctx->mark_k(6);
     if (nc == 1) {
       refit_chunk(s, 0, nullptr);
     } else {
@@ -828,7 +852,7 @@ void enqueue_fit(tpc_ctx* ctx) {
       cudaEventRecord(ctx->ev_chunk[3], ctx->aux);
       cudaStreamWaitEvent(s, ctx->ev_chunk[3], 0);
     }
-    ctx->mark_k(5);
+    ctx->mark_k(9);
   }
   k_track_clusters<<<grid_for(ctx, C.tracks * 32, bc), bc, 0, s>>>(ctx->ptr<int32_t>(L.track_tl), ctx->ptr<int32_t>(L.f_n),
                                      ctx->ptr<int32_t>(L.f_nf), ctx->ptr<int32_t>(L.hits),
@@ -970,7 +994,7 @@ void tpc_destroy(tpc_ctx* ctx) {
   if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
   for (int i = 0; i < 7; i++)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  for (int i = 0; i < 6; i++)
+  for (int i = 0; i < PH_COUNT; i++)
     if (ctx->evk[i]) cudaEventDestroy(ctx->evk[i]);
   if (ctx->own_arena && ctx->arena) {
     cudaFreeAsync(ctx->arena, ctx->stream);
@@ -1594,7 +1618,7 @@ int tpc_set_profiling(tpc_ctx* ctx, int on) {
   CK(cudaSetDevice(ctx->device));
   if (on && !ctx->ev[0]) {
     for (int i = 0; i < 7; i++) CK(cudaEventCreate(&ctx->ev[i]));
-    for (int i = 0; i < 6; i++) CK(cudaEventCreate(&ctx->evk[i]));
+    for (int i = 0; i < PH_COUNT; i++) CK(cudaEventCreate(&ctx->evk[i]));
   }
   ctx->prof = on != 0;
   ctx->prof_valid = false;
@@ -1610,15 +1634,17 @@ int tpc_get_stage_times(tpc_ctx* ctx, float ms[6]) {
   return TPC_OK;
 }
 
-int tpc_get_kalman_profile(tpc_ctx* ctx, float ms[6], uint64_t work[30]) {
+int tpc_get_kalman_profile(tpc_ctx* ctx, float ms[TPC_KALMAN_KERNELS], uint64_t work[5 * TPC_KALMAN_KERNELS]) {
+  static_assert(TPC_KALMAN_KERNELS == PH_COUNT, "the header's kernel count");
   if (!ctx || (!ms && !work)) return TPC_EINVAL;
   CK(cudaSetDevice(ctx->device));
   CK(cudaStreamSynchronize(ctx->stream));
   if (ms) {
     if (!ctx->prof_valid) return fail(ctx, TPC_EINVAL, "no profiled run (tpc_set_profiling, then find + fit)");
-    const cudaEvent_t b[6] = {ctx->ev[3], ctx->evk[0], ctx->evk[1], ctx->evk[2], ctx->evk[3], ctx->evk[4]};
-    const cudaEvent_t e[6] = {ctx->evk[0], ctx->evk[1], ctx->evk[2], ctx->ev[4], ctx->evk[4], ctx->evk[5]};
-    for (int i = 0; i < 6; i++) CK(cudaEventElapsedTime(&ms[i], b[i], e[i]));
+    const cudaEvent_t* k = ctx->evk;
+    const cudaEvent_t b[PH_COUNT] = {ctx->ev[3], k[0], k[1], k[2], k[3], k[4], k[5], k[6], k[7], k[8]};
+    const cudaEvent_t e[PH_COUNT] = {k[0], k[1], k[2], k[3], k[4], k[5], ctx->ev[4], k[7], k[8], k[9]};
+    for (int i = 0; i < PH_COUNT; i++) CK(cudaEventElapsedTime(&ms[i], b[i], e[i]));
   }
   if (work) {
     if (!ctx->loaded) return fail(ctx, TPC_EINVAL, "nothing loaded");

@@ -211,7 +211,8 @@ def test_kernel_profile_adds_up():
         assert sum(d[key] for d in kp.values()) == work[key], key
     assert kp["k_follow_p1"]["upd64"] > 0 and kp["k_follow_p2"]["upd32"] > 0 and kp["k_refit_p2"]["upd32"] > 0
     assert kp["k_follow_p2"]["upd64"] == 0 and kp["k_follow_p4"]["upd64"] == 0 and kp["k_refit_p2"]["upd64"] == 0
-    follow = sum(kp[k]["ms"] for k in ("k_follow_p1", "k_follow_p2", "k_follow_p3", "k_follow_p4"))
+    assert kp["k_follow_p4r"]["upd64"] == 0
+    follow = sum(v["ms"] for k, v in kp.items() if k.startswith("k_follow"))
     assert abs(follow - st["follow"]) < 1e-3 + 1e-3 * st["follow"]
-    assert kp["k_refit_p1"]["ms"] + kp["k_refit_p2"]["ms"] <= st["refit"] + 1e-3
+    assert sum(v["ms"] for k, v in kp.items() if k.startswith("k_refit")) <= st["refit"] + 1e-3
     assert 30 <= nk <= 60
