@@ -295,8 +295,8 @@ __device__ __forceinline__ void zone_snap_take(Lane& w, const double* snap, floa
 // One forward row step; false ends the pass.  The covariance is in D while
 // fewer than fp64_updates updates have been made since the seed.  PB: the
 // pick loads its candidates in batches (pick); phase 2's build for inputs
-// that fill the GPU keeps the z-row loop (its 80 registers spilled the
-// batches: 8.22 -> 8.81 ms on the 10 ms timeframe).
+// that fill the GPU keeps the z-row loop (in its register budget the
+// batches spilled: 8.22 -> 8.81 ms on the 10 ms timeframe).
 template <bool Z, bool PB = false>
 __device__ __forceinline__ bool fwd_step(const GridView& g, const int32_t* __restrict__ up_m, const KConst& kc,
                                          const float* sX, const float* sYH, Lane& w, TrkState& p, double* D,
@@ -801,8 +801,8 @@ __global__ void __launch_bounds__(128, 4) k_follow_p1t(GridView g, const int32_t
 
 // Phase 2: the rest of the forward pass (covariance in FP32).  MINB: CTAs
 // per SM the registers are budgeted for -- 4 (no spills) where the longest
-// tracklet bounds the kernel, 6 here and 7 in phase 4 (80 and 72 registers,
-// a few spills, more resident warps) on inputs that fill the GPU.  A lane
+// tracklet bounds the kernel, 7 here and in phase 4 (72 registers, more
+// resident warps) on inputs that fill the GPU.  A lane
 // that finishes a tracklet idles until kc.refill lanes of its warp have,
 // then they store their results and take new tracklets together, so that
 // the refill runs with many lanes at once and no lane waits for the longest
@@ -838,9 +838,6 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
       dirty = false;
       if (t < T) {
         go = fwd_load(W, t, w, p, C, chi2, sf) && !w.seed_fail;
-        w.hits = o.hits + t * NROW;
-        w.hrow = o.hrow + t * NROW;
-        w.cn = cn;
       } else {
         live = false;
       }
@@ -850,8 +847,14 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p2(GridView g, const int32
       continue;
     }
     if (go) {
-      for (int k = 0; k < max(kc.inner_steps, 1) && go; k++)
+      for (int k = 0; k < max(kc.inner_steps, 1) && go; k++) {
+        // the lane's output pointers are formed at each step from t, not
+        // kept across the refill logic (4 + 2 registers: no spills at 72)
+        w.hits = o.hits + t * NROW;
+        w.hrow = o.hrow + t * NROW;
+        w.cn = cn;
         go = fwd_step<false, MINB == 4>(g, up_m, kc, sX, sYH, w, p, D, C, chi2, tl, sf);
+      }
       dirty = true;
     }
   }
@@ -1048,9 +1051,6 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4r(GridView g, KConst kc,
       dirty = false;
       if (t < T) {
         pass = bwd_load(W, t, w, p, C, chi2, so);
-        w.hits = o.hits + t * NROW;
-        w.hrow = o.hrow + t * NROW;
-        w.cn = cn;
         go = pass && p.row > w.r0;
       } else {
         live = false;
@@ -1062,6 +1062,9 @@ __global__ void __launch_bounds__(128, MINB) k_follow_p4r(GridView g, KConst kc,
     }
     if (go) {
       for (int k = 0; k < max(kc.inner_steps, 1) && go; k++) {
+        w.hits = o.hits + t * NROW;  // formed at each step, as in phase 2
+        w.hrow = o.hrow + t * NROW;
+        w.cn = cn;
         pass = bwd_step<false, BW_REFIT>(g, kc, sX, sYH, w, p, D, C, chi2, tl, nullptr, so);
         go = pass && p.row > w.r0;
       }

@@ -718,7 +718,7 @@ void enqueue_find(tpc_ctx* ctx) {
       }
       if (after_p1) cudaEventRecord(after_p1, st);
       mk(1);
-      auto p2 = ctx->n >= kLargeBatch ? k_follow_p2<6> : k_follow_p2<4>;
+      auto p2 = ctx->n >= kLargeBatch ? k_follow_p2<7> : k_follow_p2<4>;
       p2<<<persistent_grid(ctx, p2, bf, effective_ctas_follow(ctx)), bf, 0, st>>>(
           grid_view(ctx), ctx->ptr<int32_t>(L.up_m), ctx->kc, follow_out(ctx), W, order, c, nc, cn);
       mk(2);
