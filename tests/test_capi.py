@@ -88,3 +88,18 @@ def test_server_arguments_are_checked_without_a_device():
         lib.tpc_server_destroy(srv)
         pytest.skip("a GPU is present")
     assert rc == tpc.TPC_ECUDA
+
+
+def test_binding_structs_match_the_header():
+    """The binding's mirror of tpc_tuning has the header's fields in order,
+    and its Kalman kernel names the header's count (tpc_get_kalman_profile
+    fills TPC_KALMAN_KERNELS times and 5 counters each)."""
+    txt = open(os.path.join(ROOT, "include", "tpcca.h")).read()
+    end = txt.index("} tpc_tuning;")
+    body = txt[txt.rindex("typedef struct {", 0, end):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"int32_t\s+([a-z_0-9]+)\s*;", body)
+    assert fields == [name for name, _ in tpc.TpcTuning._fields_]
+    n = int(re.search(r"#define TPC_KALMAN_KERNELS (\d+)", txt).group(1))
+    assert n == len(tpc.Tracker.KALMAN_KERNELS)
+    assert set(tpc.Tracker.ZONE_KERNELS) <= set(tpc.Tracker.KALMAN_KERNELS)
