@@ -119,11 +119,18 @@ PATH_KERNEL_SOURCES = ("common.cuh", "scan.cuh", "grid.cuh", "links.cuh", "kalma
 
 
 def _source_hash():
+    """sha256 of the path's kernel sources with their comments and blank
+    lines left out, so that a traffic file taken on them stays valid across
+    edits of the comments alone."""
     import hashlib
+    import re
     m = hashlib.sha256()
     for f in PATH_KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1709_00618_b300", "csrc", f), "rb") as fh:
-            m.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1709_00618_b300", "csrc", f), encoding="utf-8") as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        lines = (re.sub(r"//.*$", "", ln).rstrip() for ln in src.splitlines())
+        m.update("\n".join(ln for ln in lines if ln).encode())
     return m.hexdigest()
 
 

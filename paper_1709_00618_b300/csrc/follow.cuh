@@ -602,8 +602,8 @@ __device__ __forceinline__ void load_tables(float* sX, float* sYH) {
 // idle, and the FP64 pipe spends the same time on an instruction whatever
 // its active lanes.  So a zone kernel takes kc.zone_steps steps in step and
 // parks a tracklet whose zone is still open (its FP64 covariance in a list
-// slot of its own); a tail kernel then finishes those zones, 32 parked
-// tracklets to a warp.  Chunk c of nc owns slots [c cap / nc, (c+1) cap / nc)
+// slot of its own); a tail kernel then finishes those zones with lanes that
+// refill from the list.  Chunk c of nc owns slots [c cap / nc, (c+1) cap / nc)
 // of a pass's list; a tracklet that finds its chunk's slots taken finishes
 // its zone in place.
 struct ZoneTail {
