@@ -652,8 +652,11 @@ void enqueue_find(tpc_ctx* ctx) {
                                  ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of),
                                  ctx->ptr<int32_t>(L.cluster_track), cn);
   ctx->mark(1);
-  // a3 neighbours
-  k_neighbours<<<grid_for(ctx, C.n, NB_THREADS), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
+  // a3 neighbours: a grid-stride grid of 128 blocks per SM, so that blocks
+  // that reach dense regions (longer candidate scans) are outnumbered by
+  // blocks still to start (10 ms timeframe: 16 blocks per SM 8.17 ms, 24
+  // 7.89, 36 7.64, 64 7.41, 128 7.34; one wave of 6 blocks per SM 9.25)
+  k_neighbours<<<grid_for(ctx, C.n, NB_THREADS, 128), NB_THREADS, 0, s>>>(ctx->ptr<float2>(L.yz), ctx->ptr<int32_t>(L.rs_of), ctx->ptr<RsParams>(L.par),
                                   bin_start, ctx->kc, ctx->ptr<int32_t>(L.up), ctx->ptr<int32_t>(L.dn),
                                   ctx->ptr<uint8_t>(L.tie), cn);
   if (ctx->cfg.link_skip)
